@@ -1,0 +1,385 @@
+// ORACLE (test infrastructure only): plain sequential race checker.
+//
+// Only the test suite, __graft_entry__.smoke() and bench.py's CPU baseline
+// leg may build, load or call this file.  It shares no code with the GPU
+// path.  It is written for obviousness, not speed: threads run one after the
+// other, shared accesses go into std::map-based logs, and conflicts are
+// classified by looking at the logged accesses of each cell directly.
+//
+// What it computes (Distefano & Dubreil, Sec. 4 "Concrete Semantics" and the
+// race Definition that closes it):
+//   * thread-local rules of Sec. 4 for v:=e, a[v]:=e, v:=a[v], assert,
+//     assume and barrier, with ⊥ for out-of-bounds accesses (Table 1's
+//     bounds premise) and failed asserts, ⊤ for a failed assume;
+//   * global semantics of Sec. 4: all threads of the kernel run to the same
+//     barrier (the barrier-release rule), the end of the kernel being an
+//     implicit barrier;
+//   * the race rule of Sec. 4 / Sec. 1: a barrier interval is racy when the
+//     shared state it produces is not the same for every schedule; several
+//     threads writing one value to a cell is benign.
+// Readings where the paper is silent (one canonical run instead of every
+// schedule, per-thread last writes, read/write conflicts, witnesses, commit
+// order, arithmetic) are the ones listed in the project's design notes; each
+// is restated next to the code that implements it below.
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kl_frontend.hpp"
+
+namespace orc {
+
+enum Cls : uint32_t {
+  C_WW_RACE = 1, C_WW_BENIGN = 2, C_RW_RACE = 3,
+  C_OOB = 16, C_ASSERT = 17, C_DIVERGENCE = 18
+};
+enum Status : int32_t {
+  ST_RACE_FREE = 0, ST_RACY = 1, ST_OOB = 2, ST_ASSERT = 3, ST_DIVERGENCE = 4
+};
+
+struct Record {  // 10 x u32, field order fixed so reports compare bytewise
+  uint32_t interval, space, wg, addr, cls, t_a, t_b, n_readers, n_writers, n_accesses;
+};
+
+struct Report {
+  int32_t status = ST_RACE_FREE;
+  uint32_t n_intervals = 0;
+  uint64_t n_access = 0, n_global = 0, n_local = 0;
+  std::vector<Record> records;
+  std::vector<int32_t> final_global;
+};
+
+struct Access {
+  uint32_t gtid;
+  bool write;
+  int32_t value;  // value written, or value the read observed
+};
+
+// A shared cell: (space, work-group for local memory, flat address in space).
+using Cell = std::tuple<uint32_t, uint32_t, uint32_t>;
+
+enum TStatus { RUNNING, AT_BARRIER, EXITED, DEAD };
+struct Thread {
+  int node;  // node to execute next (AT_BARRIER: the barrier node)
+  TStatus st;
+  std::vector<int32_t> vars;
+};
+
+struct Checker {
+  Program prog;
+  Cfg cfg;
+  uint32_t G, S;
+  std::vector<int64_t> mem_len;   // per memory object
+  std::vector<uint64_t> mem_base; // flat base inside its space
+  uint64_t global_total = 0, local_total = 0;
+  std::vector<int32_t> global_snap;  // committed global memory
+  std::vector<int32_t> local_snap;   // committed local memory, G x local_total
+  std::vector<Thread> th;
+  Report rep;
+
+  // per interval
+  std::map<Cell, std::vector<Access>> log;
+  std::vector<Record> errors;
+
+  int32_t committed(const Cell &c) const {
+    if (std::get<0>(c) == 0) return global_snap[std::get<2>(c)];
+    return local_snap[(uint64_t)std::get<1>(c) * local_total + std::get<2>(c)];
+  }
+  void commit_cell(const Cell &c, int32_t v) {
+    if (std::get<0>(c) == 0) global_snap[std::get<2>(c)] = v;
+    else local_snap[(uint64_t)std::get<1>(c) * local_total + std::get<2>(c)] = v;
+  }
+
+  // Choose the successor of node k: one successor is taken as is; several
+  // successors are assume-guarded alternatives, of which the one whose
+  // condition holds is taken.  None holding means the path has no
+  // continuation (⊤), returned as -1.
+  int next_node(int k, const Env &env) const {
+    const Node &n = cfg.nodes[k];
+    if (n.succ.size() == 1) return n.succ[0];
+    for (int s : n.succ) {
+      const Node &c = cfg.nodes[s];
+      if (eval(*c.val, env) != 0) return s;
+    }
+    return -1;
+  }
+
+  // Run one thread from its current node to a barrier, exit or abort.
+  // Reads see the thread's own latest write of this interval if it made one,
+  // else the value committed at the last barrier (delayed visibility).
+  void run_thread(uint32_t gtid, uint32_t interval) {
+    Thread &t = th[gtid];
+    const uint32_t wg = gtid / S, tid = gtid % S;
+    Env env{&t.vars, tid, wg, S, G, &mem_len};
+    std::map<Cell, int32_t> own;  // this thread's writes in this interval
+    int k = t.node;
+    if (t.st == AT_BARRIER) {  // resume after the barrier it waited at
+      t.st = RUNNING;
+      k = next_node(k, env);
+      if (k < 0) { t.st = DEAD; return; }
+    }
+    for (;;) {
+      const Node &n = cfg.nodes[k];
+      switch (n.kind) {
+        case N_START:
+        case N_NOP:
+          break;
+        case N_EXIT:
+          t.st = EXITED;
+          t.node = k;
+          return;
+        case N_BARRIER:
+          t.st = AT_BARRIER;
+          t.node = k;
+          return;
+        case N_ASSIGN:
+          t.vars[n.var] = eval(*n.val, env);
+          break;
+        case N_ASSUME:
+          if (eval(*n.val, env) == 0) { t.st = DEAD; return; }  // ⊤
+          break;
+        case N_ASSERT:
+          if (eval(*n.val, env) == 0) {  // ⊥
+            errors.push_back({interval, 0, 0, 0, C_ASSERT, gtid, (uint32_t)n.id, 0, 0, 0});
+            t.st = DEAD;
+            return;
+          }
+          break;
+        case N_LOAD:
+        case N_STORE: {
+          const Mem &m = prog.mems[n.mem];
+          int32_t idx = eval(*n.idx, env);
+          int32_t val = 0;
+          if (n.kind == N_STORE) val = eval(*n.val, env);
+          if (idx < 0 || (int64_t)idx >= mem_len[n.mem]) {  // ⊥: out of bounds
+            errors.push_back({interval, (uint32_t)m.space, m.space ? wg : 0u, (uint32_t)idx,
+                              C_OOB, gtid, (uint32_t)n.mem, 0, 0, 0});
+            t.st = DEAD;
+            return;
+          }
+          Cell c{(uint32_t)m.space, m.space ? wg : 0u, (uint32_t)(mem_base[n.mem] + (uint64_t)idx)};
+          if (n.kind == N_STORE) {
+            own[c] = val;
+            log[c].push_back({gtid, true, val});
+          } else {
+            auto it = own.find(c);
+            int32_t v = it != own.end() ? it->second : committed(c);
+            log[c].push_back({gtid, false, v});
+            t.vars[n.var] = v;
+          }
+          rep.n_access++;
+          if (m.space == 0) rep.n_global++;
+          else rep.n_local++;
+          break;
+        }
+      }
+      k = next_node(k, env);
+      if (k < 0) { t.st = DEAD; return; }
+    }
+  }
+
+  // Classify the accesses of one cell in one interval.
+  //  * WW: take each writer thread's LAST write to the cell.  Two writers
+  //    whose last values differ: WW_RACE, witness (smallest writer, smallest
+  //    writer whose last value differs from it).  Two or more writers, all
+  //    last values equal: WW_BENIGN, witness (two smallest writers).
+  //  * RW: a read by thread r that observed o conflicts with a write of
+  //    value v != o by another thread j.  Witness: the lexicographically
+  //    smallest such (r, j).
+  void classify_cell(uint32_t interval, const Cell &c, const std::vector<Access> &acc) {
+    std::map<uint32_t, std::vector<int32_t>> writes, reads;  // per thread, program order
+    for (const Access &a : acc) (a.write ? writes : reads)[a.gtid].push_back(a.value);
+    Record base{interval, std::get<0>(c), std::get<1>(c), std::get<2>(c), 0, 0, 0,
+                (uint32_t)reads.size(), (uint32_t)writes.size(), (uint32_t)acc.size()};
+    if (writes.size() >= 2) {
+      uint32_t w1 = writes.begin()->first;
+      int32_t l1 = writes.begin()->second.back();
+      bool race = false;
+      uint32_t tb = 0;
+      for (auto &w : writes) {
+        if (w.second.back() != l1) { race = true; tb = w.first; break; }
+      }
+      Record r = base;
+      if (race) { r.cls = C_WW_RACE; r.t_a = w1; r.t_b = tb; }
+      else { r.cls = C_WW_BENIGN; r.t_a = w1; r.t_b = std::next(writes.begin())->first; }
+      rep.records.push_back(r);
+    }
+    if (!reads.empty() && !writes.empty()) {
+      // conflict(r, j) <=> some observed o of r and some written v of j differ
+      // <=> not (r observed exactly one value c and j wrote only c).
+      std::map<uint32_t, std::set<int32_t>> wset;
+      for (auto &w : writes) wset[w.first] = std::set<int32_t>(w.second.begin(), w.second.end());
+      bool found = false;
+      uint32_t best_r = 0, best_j = 0;
+      for (auto &rd : reads) {  // ascending reader
+        std::set<int32_t> obs(rd.second.begin(), rd.second.end());
+        for (auto &w : wset) {  // ascending writer
+          if (w.first == rd.first) continue;
+          bool same = obs.size() == 1 && w.second.size() == 1 && *obs.begin() == *w.second.begin();
+          if (!same) { found = true; best_j = w.first; break; }
+        }
+        if (found) { best_r = rd.first; break; }
+      }
+      if (found) {
+        Record r = base;
+        r.cls = C_RW_RACE;
+        r.t_a = best_r;
+        r.t_b = best_j;
+        rep.records.push_back(r);
+      }
+    }
+  }
+
+  void run(bool reverse) {
+    const uint32_t N = G * S;
+    th.assign(N, Thread{cfg.start, RUNNING, std::vector<int32_t>(cfg.n_vars, 0)});
+    for (uint32_t interval = 0;; interval++) {
+      log.clear();
+      errors.clear();
+      for (uint32_t i = 0; i < N; i++) {
+        uint32_t g = reverse ? N - 1 - i : i;
+        if (th[g].st == RUNNING || th[g].st == AT_BARRIER) run_thread(g, interval);
+      }
+      rep.n_intervals = interval + 1;
+      // classify every touched cell, in (space, wg, addr) order
+      for (auto &kv : log) classify_cell(interval, kv.first, kv.second);
+      // barrier agreement (Sec. 4 barrier-release rule): every thread that
+      // is still alive must stop at the same barrier, or all must exit.
+      std::map<uint32_t, std::pair<uint32_t, uint32_t>> stops;  // stop id -> (min gtid, count)
+      bool any_barrier = false;
+      for (uint32_t g = 0; g < N; g++) {
+        uint32_t id;
+        // a thread that reached exit stops at the implicit final barrier;
+        // once one has, the run ends, so no earlier exits are still around
+        if (th[g].st == AT_BARRIER) { id = (uint32_t)cfg.nodes[th[g].node].id; any_barrier = true; }
+        else if (th[g].st == EXITED) id = 0xFFFFFFFFu;
+        else continue;
+        auto it = stops.find(id);
+        if (it == stops.end()) stops[id] = {g, 1};
+        else it->second.second++;
+      }
+      bool diverged = stops.size() >= 2;
+      if (diverged) {
+        for (auto &s : stops)
+          errors.push_back({interval, 0, 0, 0, C_DIVERGENCE, s.second.first, s.first, 0, 0, s.second.second});
+      }
+      std::sort(errors.begin(), errors.end(), [](const Record &a, const Record &b) {
+        return std::tie(a.cls, a.t_a) < std::tie(b.cls, b.t_a);
+      });
+      interval_errors.insert(interval_errors.end(), errors.begin(), errors.end());
+      // commit: each written cell takes the last write of its highest-gtid
+      // writer (the schedule that runs threads in gtid order).
+      for (auto &kv : log) {
+        bool any = false;
+        uint32_t top = 0;
+        for (const Access &a : kv.second)
+          if (a.write && (!any || a.gtid > top)) { top = a.gtid; any = true; }
+        if (!any) continue;
+        int32_t v = 0;
+        for (const Access &a : kv.second)  // a thread's accesses sit in program order
+          if (a.write && a.gtid == top) v = a.value;
+        commit_cell(kv.first, v);
+      }
+      if (diverged || !any_barrier) break;
+    }
+    // report: race records already sorted by (interval, space, wg, addr, cls);
+    // error records follow, sorted by (interval, kind, gtid).
+    bool racy = false, div = false, as = false, oob = false;
+    for (auto &r : rep.records) racy |= (r.cls == C_WW_RACE || r.cls == C_RW_RACE);
+    for (auto &e : interval_errors) {
+      div |= e.cls == C_DIVERGENCE;
+      as |= e.cls == C_ASSERT;
+      oob |= e.cls == C_OOB;
+      rep.records.push_back(e);
+    }
+    rep.status = racy ? ST_RACY : div ? ST_DIVERGENCE : as ? ST_ASSERT : oob ? ST_OOB : ST_RACE_FREE;
+    rep.final_global = global_snap;
+  }
+
+  std::vector<Record> interval_errors;
+};
+
+}  // namespace orc
+
+// ------------------------------------------------------------------ C API
+using namespace orc;
+
+struct OracleHandle {
+  Report rep;
+};
+
+extern "C" {
+
+// Run the checker.  global_len/global_init give one int32 array per `global`
+// declaration, in declaration order.  reverse != 0 runs the threads of every
+// interval in descending gtid order (the report must not change).
+// Returns 0 on success, 1 on a parse error (message in err), 2 on a bad
+// launch shape or input.
+int oracle_check(const char *src, uint32_t groups, uint32_t group_size, uint32_t n_global,
+                 const uint64_t *global_len, const int32_t *const *global_init, int reverse,
+                 void **out, char *err, size_t err_len) {
+  *out = nullptr;
+  try {
+    Checker ck;
+    ck.prog = Parser(src).parse();
+    ck.cfg = CfgBuilder(ck.prog).build();
+    ck.G = groups;
+    ck.S = group_size;
+    if (groups == 0 || group_size == 0 || (uint64_t)groups * group_size > (1ull << 26)) {
+      snprintf(err, err_len, "bad launch shape");
+      return 2;
+    }
+    uint32_t gi = 0;
+    for (auto &m : ck.prog.mems) {
+      if (m.space == 0) {
+        if (gi >= n_global) { snprintf(err, err_len, "missing global input"); return 2; }
+        ck.mem_len.push_back((int64_t)global_len[gi]);
+        ck.mem_base.push_back(ck.global_total);
+        ck.global_total += global_len[gi];
+        gi++;
+      } else {
+        ck.mem_len.push_back(m.decl_len);
+        ck.mem_base.push_back(ck.local_total);
+        ck.local_total += (uint64_t)m.decl_len;
+      }
+    }
+    if (gi != n_global) { snprintf(err, err_len, "global input count mismatch"); return 2; }
+    ck.global_snap.assign(ck.global_total, 0);
+    gi = 0;
+    for (size_t i = 0; i < ck.prog.mems.size(); i++) {
+      if (ck.prog.mems[i].space != 0) continue;
+      for (uint64_t j = 0; j < global_len[gi]; j++) ck.global_snap[ck.mem_base[i] + j] = global_init[gi][j];
+      gi++;
+    }
+    ck.local_snap.assign((uint64_t)groups * ck.local_total, 0);
+    ck.run(reverse != 0);
+    auto *h = new OracleHandle{std::move(ck.rep)};
+    *out = h;
+    return 0;
+  } catch (const ParseError &e) {
+    snprintf(err, err_len, "%s", e.what());
+    return 1;
+  } catch (const std::exception &e) {
+    snprintf(err, err_len, "%s", e.what());
+    return 2;
+  }
+}
+
+int32_t oracle_status(void *h) { return ((OracleHandle *)h)->rep.status; }
+uint32_t oracle_n_intervals(void *h) { return ((OracleHandle *)h)->rep.n_intervals; }
+uint64_t oracle_n_access(void *h) { return ((OracleHandle *)h)->rep.n_access; }
+uint64_t oracle_n_global(void *h) { return ((OracleHandle *)h)->rep.n_global; }
+uint64_t oracle_n_local(void *h) { return ((OracleHandle *)h)->rep.n_local; }
+uint64_t oracle_n_records(void *h) { return ((OracleHandle *)h)->rep.records.size(); }
+const void *oracle_records(void *h) { return ((OracleHandle *)h)->rep.records.data(); }
+uint64_t oracle_final_len(void *h) { return ((OracleHandle *)h)->rep.final_global.size(); }
+const int32_t *oracle_final(void *h) { return ((OracleHandle *)h)->rep.final_global.data(); }
+void oracle_free(void *h) { delete (OracleHandle *)h; }
+
+}  // extern "C"

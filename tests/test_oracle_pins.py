@@ -1,0 +1,336 @@
+"""Pins for the CPU oracle: values fixed by the paper and by mathematics.
+
+Nothing here trusts the oracle's own code: expected values are hand-derived
+from the paper's figures (fixtures in tests/golden), closed forms for
+affine access patterns, the definition of int32 arithmetic, and the
+brute-force interleaving explorer, which runs the paper's Sec. 4 global
+semantics literally over every schedule.
+"""
+import numpy as np
+import pytest
+
+from paper_1308_3203_gb300 import workloads as W
+from tests.golden import golden
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def rec(interval, addr, cls, t_a, t_b, nr, nw, na, space=0, wg=0):
+    return [interval, space, wg, addr, cls, t_a, t_b, nr, nw, na]
+
+
+# ---------------------------------------------------------------- goldens
+
+@pytest.mark.parametrize("name", golden.names())
+def test_golden_fixture(oracle, name):
+    g = golden.load(name)
+    r = oracle.check(g["src"], g["groups"], g["group_size"], g["globals"])
+    for k, v in g["expect"].items():
+        assert r[k] == v, (k, r[k], v)
+    np.testing.assert_array_equal(r["records"], g["records"])
+    np.testing.assert_array_equal(r["final"], g["final"])
+
+
+FIG1 = golden.load("fig1_n6.txt")["src"]
+FIG2 = golden.load("fig2_n4.txt")["src"]
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 12])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fig1_closed_form(oracle, n, seed):
+    """Fig. 1: OOB for work-items 0 and n-1; in interval 1 a read/write race
+    at R[k+1] (reader k, writer k+1) exactly when 2*R0[k+2] != R0[k+1], where
+    R0 is R after interval 0, for k = 1..n-3."""
+    rng = np.random.default_rng(seed)
+    A = rng.integers(-5, 5, n).astype(np.int32)
+    B = rng.integers(-5, 5, n).astype(np.int32)
+    R = rng.integers(-5, 5, n).astype(np.int32)
+    if seed == 1:  # make some cells agree so that both outcomes occur
+        A[:] = 0
+        B[:] = 0
+        R[:] = 0
+    r = oracle.check(FIG1, 1, n, [A, B, R])
+    R0 = R.astype(np.int64).copy()
+    for k in range(1, n - 1):
+        R0[k] = A[k - 1] + B[k + 1]
+    baseR = 2 * n
+    exp = []
+    for k in range(1, n - 2):
+        if 2 * R0[k + 2] != R0[k + 1]:
+            exp.append(rec(1, baseR + k + 1, 3, k, k + 1, 1, 1, 2))
+    exp.append(rec(0, 2**32 - 1, 16, 0, 0, 0, 0, 0))
+    exp.append(rec(0, n, 16, n - 1, 1, 0, 0, 0))
+    np.testing.assert_array_equal(r["records"], np.array(exp, dtype=np.uint32).reshape(-1, 10))
+    Rf = R0.copy()
+    for k in range(1, n - 1):
+        Rf[k] = 2 * R0[k + 1]
+    np.testing.assert_array_equal(r["final"], np.concatenate([A, B, Rf.astype(np.int32)]))
+    assert r["status"] == (1 if any(e[4] == 3 for e in exp) else 2)
+    assert r["n_intervals"] == 2
+    assert r["n_access"] == 3 * (n - 2) + 1 + 2 * (n - 2)
+
+
+def test_fig2_schedules_reach_both_values_of_g(oracle):
+    """Sec. 6.1: 'g can in practice have the value 0 or the value 1'."""
+    n = 3
+    e = oracle.explore(FIG2, 1, n, [np.ones(n + 1, np.int32), np.array([5], np.int32)])
+    assert not e["overflow"]
+    gs = sorted(int(f[-1]) for f in e["finals"])
+    assert gs == [0, 1]
+    assert e["end_states"][0] == 1 and e["end_states"][1] == 2
+    assert e["deviated"] == [False, True, False]
+    # variant where the last cell is 0: one final memory, reads still racy
+    A = np.ones(n + 1, np.int32)
+    A[n] = 0
+    e = oracle.explore(FIG2, 1, n, [A, np.array([5], np.int32)])
+    assert len(e["finals"]) == 1 and int(e["finals"][0][-1]) == 1
+    assert e["deviated"][1]
+
+
+# ---------------------------------------------------------------- arithmetic
+
+ARITH = [
+    ("2147483647 + 1", -2147483648),
+    ("-2147483648 - 1", 2147483647),
+    ("65536 * 65536", 0),
+    ("65537 * 65537", 131073),
+    ("-7 / 2", -3), ("7 / -2", -3), ("-7 / -2", 3), ("7 / 0", 0),
+    ("-7 % 3", 2), ("7 % -3", 1), ("-7 % -3", 2), ("7 % 0", 0), ("6 % 3", 0),
+    ("-2147483648 / -1", -2147483648), ("-2147483648 % -1", 0),
+    ("-2147483648 % 3", 1),
+    ("3 < 5", 1), ("5 <= 5", 1), ("5 > 5", 0), ("5 >= 6", 0), ("4 == 4", 1), ("4 != 4", 0),
+    ("-1 < 0", 1),
+    ("3 && 0", 0), ("3 && -1", 1), ("0 || 0", 0), ("0 || 7", 1), ("!0", 1), ("!9", 0),
+    ("-(-5)", 5), ("4294967295", -1), ("2147483648", -2147483648),
+    ("2 + 3 * 4", 14), ("(2 + 3) * 4", 20), ("10 - 3 - 2", 5), ("100 / 10 / 5", 2),
+    ("1 < 2 == 1", 1), ("1 + 2 < 4 && 5 > 3", 1), ("!1 + 1", 1), ("-3 % 5 * 2", 4),
+]
+
+
+def test_int32_arithmetic(oracle):
+    body = "\n".join(f"  A[{i}] = {e};" for i, (e, _) in enumerate(ARITH))
+    src = f"kernel arith(global int A[]) {{\n{body}\n}}\n"
+    r = oracle.check(src, 1, 1, [np.zeros(len(ARITH), np.int32)])
+    assert r["status"] == 0 and len(r["records"]) == 0
+    np.testing.assert_array_equal(r["final"], np.array([v for _, v in ARITH], dtype=np.int32))
+
+
+def test_builtins_and_private_state(oracle):
+    src = """kernel ids(global int A[], global int B[]) {
+  if (gtid == 6) {
+    A[0] = tid; A[1] = wg; A[2] = gtid; A[3] = gsize; A[4] = ngroups;
+    A[5] = size(A); A[6] = size(B); A[7] = x;
+    x = 3; x = x * x; A[8] = x;
+    for i in 2 .. 5 { y = y + i; }
+    A[9] = y; A[10] = i;
+    for j in 5 .. 2 { y = 100; }
+    A[11] = j; A[12] = y;
+  }
+}
+"""
+    r = oracle.check(src, 3, 4, [np.zeros(13, np.int32), np.zeros(5, np.int32)])
+    np.testing.assert_array_equal(r["final"][:13], [2, 1, 6, 4, 3, 13, 5, 0, 9, 9, 5, 5, 9])
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("a", [0, 1, 2])
+@pytest.mark.parametrize("n", [1, 2, 5, 64, 129, 200, 256])
+@pytest.mark.parametrize("c,d", [(0, 3), (1, 0), (-3, 7), (2**25, 1)])
+def test_affine_store_closed_form(oracle, a, n, c, d):
+    """A[(a*tid + b) % 256] = c*tid + d by n work-items in one interval.
+    a = 0: one cell, benign iff c = 0 (or one writer), witness (0, 1);
+    a = 1: no collision; a = 2: tid and tid+128 collide, values differ iff
+    128*c != 0 mod 2^32."""
+    b = 17
+    src = f"kernel aff(global int A[]) {{\n  A[({a} * tid + {b}) % 256] = {c} * tid + {d};\n}}\n"
+    r = oracle.check(src, 1, n, [np.zeros(256, np.int32)])
+    exp = []
+    if a == 0 and n >= 2:
+        exp.append(rec(0, b, 2 if c == 0 else 1, 0, 1, 0, n, n))
+    if a == 2:
+        for cell in range(256):
+            ts = [t for t in range(n) if (2 * t + b) % 256 == cell]
+            if len(ts) == 2:
+                benign = (128 * c) % 2**32 == 0
+                exp.append(rec(0, cell, 2 if benign else 1, ts[0], ts[1], 0, 2, 2))
+        assert len(exp) == max(0, n - 128)
+    np.testing.assert_array_equal(r["records"], np.array(exp, dtype=np.uint32).reshape(-1, 10))
+
+
+# ---------------------------------------------------------------- rule details
+
+def _run(oracle, body, n, A, groups=1, decl="global int A[]"):
+    src = f"kernel t({decl}) {{\n{body}\n}}\n"
+    return oracle.check(src, groups, n, [np.array(A, np.int32)])
+
+
+def test_ww_uses_last_write_of_each_thread(oracle):
+    # thread 0 writes 6 then 5, thread 1 writes 5: the cell ends 5 either way
+    r = _run(oracle, "if (tid == 0) { A[0] = 6; A[0] = 5; }\nif (tid == 1) { A[0] = 5; }", 2, [0])
+    np.testing.assert_array_equal(r["records"], [rec(0, 0, 2, 0, 1, 0, 2, 3)])
+    # last values 5,5,6,5: race, witness (smallest writer, first differing)
+    r = _run(oracle, "A[0] = 5;\nif (tid == 2) { A[0] = 6; }", 4, [0])
+    np.testing.assert_array_equal(r["records"], [rec(0, 0, 1, 0, 2, 0, 4, 5)])
+
+
+def test_rw_witness_is_smallest_conflicting_pair(oracle):
+    body = "x = A[0];\nif (tid == 2) { A[0] = 7; }\nif (tid == 3) { A[0] = 9; }"
+    # every work-item reads 7; writer 2 writes 7 (no conflict), writer 3 writes 9
+    r = _run(oracle, body, 4, [7])
+    np.testing.assert_array_equal(r["records"], [rec(0, 0, 1, 2, 3, 4, 2, 6),
+                                                 rec(0, 0, 3, 0, 3, 4, 2, 6)])
+    r = _run(oracle, "if (tid != 0) { x = A[0]; }\n" + body.split("\n", 1)[1], 4, [7])
+    np.testing.assert_array_equal(r["records"][1], rec(0, 0, 3, 1, 3, 3, 2, 5))
+    # a reader that wrote the cell itself sees its own value; only others count
+    body2 = "if (tid == 3) { A[0] = 9; x = A[0]; }\nif (tid == 1) { A[0] = 9; }"
+    r = _run(oracle, body2, 4, [7])
+    np.testing.assert_array_equal(r["records"], [rec(0, 0, 2, 1, 3, 1, 2, 3)])
+    body3 = "if (tid == 3) { A[0] = 8; x = A[0]; }\nif (tid == 1) { A[0] = 9; }"
+    r = _run(oracle, body3, 4, [7])
+    np.testing.assert_array_equal(r["records"], [rec(0, 0, 1, 1, 3, 1, 2, 3),
+                                                 rec(0, 0, 3, 3, 1, 1, 2, 3)])
+    # reads of a cell nobody else writes: never a race
+    r = _run(oracle, "x = A[tid];\nA[tid] = x + 1;", 4, [1, 2, 3, 4])
+    assert len(r["records"]) == 0
+    np.testing.assert_array_equal(r["final"], [2, 3, 4, 5])
+
+
+def test_reads_see_snapshot_and_own_writes(oracle):
+    # thread 1 writes A[0] = 5 while thread 0 reads A[0] twice around its own write
+    body = ("if (tid == 0) { x = A[0]; A[1] = x; A[0] = 3; y = A[0]; A[2] = y; }\n"
+            "if (tid == 1) { A[0] = 5; }\nbarrier;\nif (tid == 0) { z = A[0]; A[3] = z; }")
+    r = _run(oracle, body, 2, [9, 0, 0, 0])
+    # commit: the highest writer (1) wins -> A[0] = 5 after the barrier
+    np.testing.assert_array_equal(r["final"], [5, 9, 3, 5])
+    recs = r["records"]
+    assert [tuple(x[[0, 3, 4, 5, 6]]) for x in recs] == [(0, 0, 1, 0, 1), (0, 0, 3, 0, 1)]
+
+
+def test_commit_takes_highest_writer_last_write(oracle):
+    r = _run(oracle, "if (tid == 0) { A[0] = 1; }\nif (tid == 2) { A[0] = 3; A[0] = 4; }\n"
+                     "if (tid == 1) { A[0] = 2; }", 3, [0])
+    assert r["final"][0] == 4
+
+
+def test_errors_assert_assume_divergence(oracle):
+    r = _run(oracle, "assert(tid != 1);\nassert(tid != 2);\nA[tid] = 1;", 4, [0, 0, 0, 0])
+    np.testing.assert_array_equal(r["records"], [rec(0, 0, 17, 1, 0, 0, 0, 0),
+                                                 rec(0, 0, 17, 2, 1, 0, 0, 0)])
+    assert r["status"] == 3
+    np.testing.assert_array_equal(r["final"], [1, 0, 0, 1])
+    r = _run(oracle, "assume(tid != 1);\nA[tid] = 1;", 3, [0, 0, 0])
+    assert len(r["records"]) == 0 and r["status"] == 0
+    np.testing.assert_array_equal(r["final"], [1, 0, 1])
+    # barrier inside a branch: work-items 0,1 wait at barrier 0, 2,3 at barrier 1
+    r = _run(oracle, "if (tid < 2) { barrier; } else { barrier; }\nA[tid] = 1;", 4, [0] * 4)
+    np.testing.assert_array_equal(r["records"], [rec(0, 0, 18, 0, 0, 0, 0, 2),
+                                                 rec(0, 0, 18, 2, 1, 0, 0, 2)])
+    assert r["status"] == 4 and r["n_intervals"] == 1
+    # some work-items exit while others wait
+    r = _run(oracle, "if (tid == 0) { barrier; }", 3, [0])
+    np.testing.assert_array_equal(r["records"], [rec(0, 0, 18, 0, 0, 0, 0, 1),
+                                                 rec(0, 0, 18, 1, 2**32 - 1, 0, 0, 2)])
+
+
+def test_local_memory_is_per_group(oracle):
+    src = ("kernel t(global int A[], local int L[2]) {\n  L[0] = tid;\n  barrier;\n"
+           "  A[gtid] = L[0];\n  if (tid == 0) { L[1] = wg; }\n}\n")
+    r = oracle.check(src, 3, 2, [np.zeros(6, np.int32)])
+    # two writers per group with values 0, 1: a race in each group's own cell
+    # witnesses are global ids (gtid = wg * gsize + tid)
+    np.testing.assert_array_equal(r["records"], [rec(0, 0, 1, 2 * w, 2 * w + 1, 0, 2, 2,
+                                                     space=1, wg=w) for w in range(3)])
+    np.testing.assert_array_equal(r["final"], [1] * 6)
+    assert r["n_local"] == 6 + 6 + 3 and r["n_global"] == 6
+
+
+def test_local_oob_and_empty(oracle):
+    src = "kernel t(global int A[], local int L[2]) {\n  L[tid] = 1;\n}\n"
+    r = oracle.check(src, 2, 3, [np.zeros(1, np.int32)])
+    np.testing.assert_array_equal(r["records"], [rec(0, 2, 16, 2, 1, 0, 0, 0, space=1, wg=0),
+                                                 rec(0, 2, 16, 5, 1, 0, 0, 0, space=1, wg=1)])
+    r = oracle.check("kernel e() { }", 4, 32, [])
+    assert r["status"] == 0 and r["n_access"] == 0 and r["n_intervals"] == 1
+    r = oracle.check("kernel e(global int A[]) { A[tid] = 1; }", 1, 3, [np.zeros(0, np.int32)])
+    assert r["status"] == 2 and len(r["records"]) == 3
+
+
+@pytest.mark.parametrize("bad", [
+    "kernel k(global int A[]) { A[0] = ; }",
+    "kernel k(global int A[4]) { }",
+    "kernel k(local int L[]) { }",
+    "kernel k() { B[0] = 1; }",
+    "kernel k() { for i in 0 .. 3 { i = 2; } }",
+    "kernel k() { for i in 0 .. 3 { for i in 0 .. 2 { } } }",
+    "kernel k() { tid = 1; }",
+    "kernel k() { x = 99999999999; }",
+    "kernel k(global int A[], global int A[]) { }",
+    "kernel k() { x = 1 }",
+])
+def test_parse_errors(oracle, bad):
+    with pytest.raises(oracle.OracleError):
+        oracle.check(bad, 1, 1, [np.zeros(1, np.int32)] * bad.count("global"))
+
+
+# ---------------------------------------------------------------- metamorphic
+
+@pytest.mark.parametrize("seed", range(20))
+def test_thread_order_does_not_matter(oracle, seed):
+    i = W.small_kernel(seed)
+    a = oracle.check(i.src, i.groups, i.group_size, i.globals)
+    b = oracle.check(i.src, i.groups, i.group_size, i.globals, reverse=True)
+    np.testing.assert_array_equal(a["records"], b["records"])
+    np.testing.assert_array_equal(a["final"], b["final"])
+
+
+def test_thread_order_does_not_matter_large(oracle):
+    i = W.large_kernel(0, groups=4, group_size=64, global_len=4096, local_len=256, n_stmts=80)
+    a = oracle.check(i.src, i.groups, i.group_size, i.globals)
+    b = oracle.check(i.src, i.groups, i.group_size, i.globals, reverse=True)
+    assert a["n_access"] > 1000
+    np.testing.assert_array_equal(a["records"], b["records"])
+    np.testing.assert_array_equal(a["final"], b["final"])
+
+
+# ---------------------------------------------------------------- brute force
+
+def _first_flagged(records):
+    races = [r for r in records if r[4] in (1, 3)]
+    return min((int(r[0]) for r in races), default=None)
+
+
+@pytest.mark.parametrize("chunk", range(8))
+def test_bruteforce_schedules(oracle, chunk):
+    """I1: no race record -> every schedule reaches one shared state at every
+    barrier, reads never depend on the schedule, and the final memory is the
+    oracle's.  I2: the first flagged interval holds a write/write race and
+    no read/write race -> two schedules reach different shared states at its
+    barrier.  I3: it holds a read/write race -> some schedule changes a read."""
+    seen = {"free": 0, "ww": 0, "rw": 0}
+    for seed in range(chunk * 60, chunk * 60 + 60):
+        i = W.tiny_kernel(seed)
+        r = oracle.check(i.src, i.groups, i.group_size, i.globals)
+        e = oracle.explore(i.src, i.groups, i.group_size, i.globals)
+        assert not e["overflow"], seed
+        k = _first_flagged(r["records"])
+        diverges = any(x[4] == 18 for x in r["records"])
+        upto = r["n_intervals"] if k is None else k
+        for j in range(upto):
+            assert e["end_states"][j] == 1, (seed, j, i.src)
+            assert not e["deviated"][j], (seed, j, i.src)
+        if k is None:
+            seen["free"] += 1
+            assert e["diverged"] == diverges, (seed, i.src)
+            if not diverges:
+                assert len(e["finals"]) == 1, (seed, i.src)
+                np.testing.assert_array_equal(e["finals"][0], r["final"])
+            continue
+        classes = {int(x[4]) for x in r["records"] if x[0] == k}
+        if 3 in classes:
+            seen["rw"] += 1
+            assert e["deviated"][k], (seed, i.src)
+        else:
+            seen["ww"] += 1
+            assert e["end_states"][k] >= 2, (seed, i.src)
+    assert seen["free"] and seen["rw"], seen
