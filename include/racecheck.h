@@ -1,0 +1,171 @@
+/*
+ * racecheck.h - C ABI of the GB300 concrete race checker.
+ *
+ * The library runs every work-item of an instance of a kernel written in the
+ * minimal OpenCL kernel language of Distefano & Dubreil, "Detecting Data
+ * Races on OpenCL Kernels with Symbolic Execution" (Sec. 3: expressions,
+ * booleans and commands v:=e, a[v]:=e, v:=a[v], barrier, assume, assert;
+ * a kernel is a control-flow graph from a unique start to a unique exit),
+ * under the concrete SIMD semantics of Sec. 4 (thread-local rules, barrier
+ * release, the race rule and the Definition of a race), on one sm_103a GPU.
+ * Each barrier interval's shared accesses are logged in device memory and
+ * classified: several work-items writing the same value to a cell is benign
+ * (Sec. 1; Sec. 4 after the race rule), differing values are a race.
+ *
+ * Conventions for every entry point:
+ *  - return value: RC_OK (0) or an RC_E_* code; no exception crosses the ABI;
+ *    rc_last_error() gives a message for the calling thread's last failure;
+ *  - a race is a successful check (report status RC_RACY), not an error;
+ *  - objects returned through out-pointers are owned by the library and are
+ *    released with the matching rc_*_free; inputs are read during the call
+ *    and never retained after it returns;
+ *  - all device work runs on the caller's CUDA stream (rc_input.cuda_stream,
+ *    NULL = legacy default stream); the call synchronises that stream before
+ *    it returns;
+ *  - the library keeps device workspaces between calls (grown on demand,
+ *    released by rc_release_workspace); calls from several host threads are
+ *    serialised internally.
+ */
+#ifndef RACECHECK_H
+#define RACECHECK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes */
+#define RC_OK 0
+#define RC_E_PARSE 1     /* source text is not a valid kernel               */
+#define RC_E_INVALID 2   /* bad argument, launch shape, input or bytecode   */
+#define RC_E_CAPACITY 3  /* instance needs more device memory than allowed  */
+#define RC_E_CUDA 4      /* a CUDA runtime call failed                      */
+#define RC_E_TIMEOUT 5   /* a bounded device wait ran out                   */
+#define RC_E_NOMEM 6     /* host allocation failed                          */
+
+/* ---- report status (rc_report.status) */
+#define RC_RACE_FREE 0        /* no race, no error                                  */
+#define RC_RACY 1             /* at least one WW_RACE or RW_RACE record             */
+#define RC_ERROR_OOB 2        /* out-of-bounds access (Sec. 5 Table 1 premise), no race */
+#define RC_ERROR_ASSERT 3     /* failed assert (Sec. 4 assert rule), no race        */
+#define RC_ERROR_DIVERGENCE 4 /* work-items stopped at different barriers, no race  */
+
+/* ---- record classes (rc_record.cls) */
+#define RC_WW_RACE 1    /* two writers' last values in the interval differ       */
+#define RC_WW_BENIGN 2  /* >= 2 writers, all last values equal (benign, Sec. 1)  */
+#define RC_RW_RACE 3    /* a read observed o, another work-item wrote v != o     */
+#define RC_OOB 16       /* error: access outside 0 <= index < size(array)        */
+#define RC_ASSERT_FAIL 17
+#define RC_DIVERGENCE 18
+
+/* Options for rc_input.flags */
+#define RC_WANT_FINAL_MEMORY 1u /* fill rc_report.final_global            */
+
+typedef struct rc_bytecode rc_bytecode; /* opaque, library-owned */
+
+/* Static facts about a compiled kernel. */
+typedef struct {
+  uint32_t n_insn;        /* bytecode instructions                          */
+  uint32_t n_regs;        /* registers per work-item (variables + temps)    */
+  uint32_t n_vars;        /* named private variables                        */
+  uint32_t n_mems;        /* memory objects (global + local), declared order */
+  uint32_t n_global;      /* global memory objects = inputs rc_check wants  */
+  uint32_t n_barriers;    /* barrier statements                             */
+  uint32_t n_asserts;     /* assert statements                              */
+  uint32_t local_cells;   /* int32 cells of local memory per work-group     */
+  uint64_t max_access_per_interval; /* static bound per work-item           */
+  uint64_t max_write_per_interval;  /* static bound per work-item           */
+} rc_bytecode_info;
+
+/* Input of one instance.  global_len[i] / global_init[i] give the length
+ * and the initial int32 contents of the i-th `global` declaration (declared
+ * order).  on_device != 0: global_init pointers are device pointers;
+ * otherwise host pointers (pageable or pinned).  cuda_stream is a
+ * cudaStream_t or NULL. */
+typedef struct {
+  uint32_t n_global;
+  const uint64_t *global_len;
+  const int32_t *const *global_init;
+  int on_device;
+  void *cuda_stream;
+  uint32_t flags;
+} rc_input;
+
+/* One report record: ten uint32 fields, fixed order.
+ *  race records (cls 1..3): the cell (space 0 = global, 1 = local; wg = the
+ *    work-group owning a local cell, 0 for global; addr = flat index in the
+ *    space, arrays laid out in declared order), the barrier interval, the
+ *    witness pair (t_a, t_b) of global work-item ids, distinct readers and
+ *    writers, and the number of accesses to the cell in the interval;
+ *  OOB: space/wg of the array, addr = the index (two's complement), t_a =
+ *    the work-item, t_b = the array's declaration index;
+ *  ASSERT_FAIL: t_a = the work-item, t_b = assert ordinal (source order);
+ *  DIVERGENCE: one record per stop point, t_a = smallest work-item stopped
+ *    there, t_b = barrier ordinal (0xFFFFFFFF = exit), n_accesses = how many
+ *    work-items stopped there.
+ * Race records come first, sorted by (interval, space, wg, addr, cls);
+ * error records follow, sorted by (interval, cls, t_a). */
+typedef struct {
+  uint32_t interval, space, wg, addr, cls, t_a, t_b, n_readers, n_writers, n_accesses;
+} rc_record;
+
+typedef struct {
+  int32_t status;         /* RC_RACE_FREE .. RC_ERROR_DIVERGENCE */
+  uint32_t n_intervals;   /* barrier intervals executed          */
+  uint64_t n_access;      /* shared accesses performed           */
+  uint64_t n_global;      /* ... of which to global memory       */
+  uint64_t n_local;       /* ... of which to local memory        */
+  uint64_t n_records;
+  rc_record *records;
+  uint64_t final_len;     /* global cells (sum of global_len)    */
+  int32_t *final_global;  /* final global memory, or NULL        */
+} rc_report;
+
+/* Compile kernel source text (Sec. 3 grammar, see the package docs for the
+ * surface syntax).  On RC_E_PARSE a message is written to err (if err_len >
+ * 0).  *out receives a new bytecode object on success. */
+int rc_compile(const char *src, size_t len, rc_bytecode **out, char *err, size_t err_len);
+
+/* Fill *info with static facts about bc. */
+int rc_bytecode_info_get(const rc_bytecode *bc, rc_bytecode_info *info);
+
+/* Check one instance: groups x group_size work-items (1 <= group_size <=
+ * 1024, groups * group_size <= 2^26) run bc on `in`.  *out receives a new
+ * report.  Errors: RC_E_INVALID (shape, input count/lengths, local memory
+ * too large), RC_E_CAPACITY, RC_E_CUDA. */
+int rc_check(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in,
+             rc_report **out);
+
+/* Check n independent instances; out must hold n report pointers.  Reports
+ * are identical to n rc_check calls.  On error no report is returned. */
+int rc_check_batch(const rc_bytecode *const *bcs, const uint32_t *groups,
+                   const uint32_t *group_size, const rc_input *inputs, size_t n,
+                   rc_report **out);
+
+void rc_bytecode_free(rc_bytecode *bc);
+void rc_report_free(rc_report *rep);
+const char *rc_strerror(int code);
+const char *rc_last_error(void);
+
+/* Release every device workspace the library holds. */
+int rc_release_workspace(void);
+
+/* Classification strategy for later calls: 0 = automatic (size-based),
+ * 1 = radix sort of the whole log + segmented scan, 2 = shadow-cell owner
+ * table + sort of shared cells only.  Returns RC_E_INVALID for other values. */
+int rc_set_strategy(int strategy);
+
+/* Kernel timing: when enabled, the library brackets its kernels with CUDA
+ * events on the caller's stream and accumulates, per kernel kind, launches,
+ * device milliseconds and algorithmic bytes.  kind: 0 interpreter, 1 log
+ * classification (sort or shadow path), 2 commit.  Reset clears the sums. */
+int rc_profile_enable(int on);
+int rc_profile_reset(void);
+int rc_profile_get(int kind, uint64_t *launches, double *ms, double *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RACECHECK_H */

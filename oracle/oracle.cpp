@@ -51,6 +51,7 @@ struct Report {
   int32_t status = ST_RACE_FREE;
   uint32_t n_intervals = 0;
   uint64_t n_access = 0, n_global = 0, n_local = 0;
+  uint64_t max_acc = 0, max_wr = 0;  // most accesses / writes of one thread in one interval
   std::vector<Record> records;
   std::vector<int32_t> final_global;
 };
@@ -118,6 +119,11 @@ struct Checker {
     const uint32_t wg = gtid / S, tid = gtid % S;
     Env env{&t.vars, tid, wg, S, G, &mem_len};
     std::map<Cell, int32_t> own;  // this thread's writes in this interval
+    uint64_t nacc = 0, nwr = 0;
+    struct Tally {  // record this thread's counts however the run ends
+      Report &r; uint64_t &a, &w;
+      ~Tally() { r.max_acc = std::max(r.max_acc, a); r.max_wr = std::max(r.max_wr, w); }
+    } tally{rep, nacc, nwr};
     int k = t.node;
     if (t.st == AT_BARRIER) {  // resume after the barrier it waited at
       t.st = RUNNING;
@@ -174,6 +180,8 @@ struct Checker {
             t.vars[n.var] = v;
           }
           rep.n_access++;
+          nacc++;
+          if (n.kind == N_STORE) nwr++;
           if (m.space == 0) rep.n_global++;
           else rep.n_local++;
           break;
@@ -376,6 +384,8 @@ uint32_t oracle_n_intervals(void *h) { return ((OracleHandle *)h)->rep.n_interva
 uint64_t oracle_n_access(void *h) { return ((OracleHandle *)h)->rep.n_access; }
 uint64_t oracle_n_global(void *h) { return ((OracleHandle *)h)->rep.n_global; }
 uint64_t oracle_n_local(void *h) { return ((OracleHandle *)h)->rep.n_local; }
+uint64_t oracle_max_acc(void *h) { return ((OracleHandle *)h)->rep.max_acc; }
+uint64_t oracle_max_wr(void *h) { return ((OracleHandle *)h)->rep.max_wr; }
 uint64_t oracle_n_records(void *h) { return ((OracleHandle *)h)->rep.records.size(); }
 const void *oracle_records(void *h) { return ((OracleHandle *)h)->rep.records.data(); }
 uint64_t oracle_final_len(void *h) { return ((OracleHandle *)h)->rep.final_global.size(); }

@@ -62,6 +62,7 @@ def _load():
         for name, rt in [("oracle_status", i32), ("oracle_n_intervals", u32),
                          ("oracle_n_access", u64), ("oracle_n_global", u64),
                          ("oracle_n_local", u64), ("oracle_n_records", u64),
+                         ("oracle_max_acc", u64), ("oracle_max_wr", u64),
                          ("oracle_records", vp), ("oracle_final_len", u64),
                          ("oracle_final", vp)]:
             getattr(lib, name).restype = rt
@@ -123,7 +124,8 @@ def check(src: str, groups: int, group_size: int, globals_, reverse: bool = Fals
             ctypes.memmove(fin.ctypes.data, lib.oracle_final(h), nfin * 4)
         return dict(status=lib.oracle_status(h), n_intervals=lib.oracle_n_intervals(h),
                     n_access=lib.oracle_n_access(h), n_global=lib.oracle_n_global(h),
-                    n_local=lib.oracle_n_local(h), records=recs, final=fin)
+                    n_local=lib.oracle_n_local(h), records=recs, final=fin,
+                    max_acc=lib.oracle_max_acc(h), max_wr=lib.oracle_max_wr(h))
     finally:
         lib.oracle_free(h)
 

@@ -1,0 +1,655 @@
+// Host runtime and C ABI: instance set-up, the barrier-interval loop, the
+// barrier agreement check, report assembly, device workspaces and timing.
+//
+// Per barrier interval (Distefano & Dubreil, Sec. 4): run every live
+// work-item to its next barrier or exit (interpreter kernel), classify the
+// interval's logged accesses and commit its writes (sort + segmented
+// classification, or the shadow owner table path), then apply the barrier
+// release rule: all work-items that are still alive must stop at the same
+// barrier, or all must exit; anything else is reported as divergence and
+// ends the run.  The end of the kernel is an implicit barrier, so the last
+// interval is classified too.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/racecheck.h"
+#include "device.cuh"
+
+struct rc_bytecode {
+  rc::Program prog;
+};
+
+namespace rc {
+namespace {
+
+thread_local std::string g_last_error;
+std::mutex g_mu;
+int g_strategy = 0;
+
+struct Fail {
+  int code;
+  std::string msg;
+};
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      throw Fail{RC_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};      \
+  } while (0)
+
+// ---------------------------------------------------------------- workspace
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  template <class T>
+  T *get(size_t n) {
+    size_t bytes = std::max<size_t>(n * sizeof(T), 256);
+    if (bytes > cap) {
+      if (p) CK(cudaFree(p));
+      p = nullptr;
+      cap = 0;
+      size_t want = bytes + bytes / 4;
+      if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+          cudaGetLastError();
+          throw Fail{RC_E_CAPACITY, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+        }
+        want = bytes;
+      }
+      cap = want;
+    }
+    return static_cast<T *>(p);
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+struct HostBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  template <class T>
+  T *get(size_t n) {
+    size_t bytes = std::max<size_t>(n * sizeof(T), 256);
+    if (bytes > cap) {
+      if (p) cudaFreeHost(p);
+      p = nullptr;
+      CK(cudaMallocHost(&p, bytes));
+      cap = bytes;
+    }
+    return static_cast<T *>(p);
+  }
+};
+
+struct Workspace {
+  DevBuf code, mems, snap, regs, pc, st, ow, loga, logb, head, runidx, sum, khead, keyidx, nrec,
+      recoff, out, scan, errs, stats, owner, owcnt, compact;
+  HostBuf hstats, hrecs;
+  bool configured = false;
+  uint32_t epoch = 0;
+  void release_all() {
+    for (DevBuf *b : {&code, &mems, &snap, &regs, &pc, &st, &ow, &loga, &logb, &head, &runidx, &sum,
+                      &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
+                      &owcnt, &compact})
+      b->release();
+    epoch = 0;
+  }
+};
+Workspace g_ws;
+
+// ---------------------------------------------------------------- profiling
+struct Prof {
+  bool on = false;
+  uint64_t launches[3] = {0, 0, 0};
+  double ms[3] = {0, 0, 0};
+  double bytes[3] = {0, 0, 0};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+Prof g_prof;
+
+void prof_events() {
+  if (!g_prof.ev[0])
+    for (auto &e : g_prof.ev) CK(cudaEventCreate(&e));
+}
+
+// stats block layout (uint32 words)
+enum : uint32_t { ST_LOGCNT = 0, ST_ACC = 2, ST_FLAGS = 6, ST_ERRCNT = 7, ST_SCRATCH = 8, ST_STOPS = 10 };
+
+uint32_t bitwidth(uint64_t v) {  // bits needed to represent values < v (v >= 1)
+  uint32_t b = 0;
+  while (b < 64 && (v - 1) >> b) b++;
+  return std::max<uint32_t>(b, 1);
+}
+
+struct Instance {
+  const Program *p;
+  uint32_t G, S;
+  uint64_t N;
+  const rc_input *in;
+  cudaStream_t s;
+};
+
+struct Layout {
+  std::vector<MemInfo> mems;
+  uint64_t GT = 0, LT = 0, keys = 0;
+};
+
+Layout make_layout(const Program &p, const rc_input *in, uint32_t G) {
+  Layout L;
+  uint32_t gi = 0;
+  for (const MemDecl &m : p.mems) {
+    MemInfo mi{};
+    mi.space = m.space;
+    if (m.space == 0) {
+      uint64_t len = in->global_len[gi++];
+      if (len > 0x7FFFFFFFull) throw Fail{RC_E_INVALID, "global array longer than 2^31-1"};
+      mi.len = (uint32_t)len;
+      mi.base = (uint32_t)L.GT;
+      L.GT += len;
+    } else {
+      mi.len = (uint32_t)m.decl_len;
+      mi.base = (uint32_t)L.LT;
+      L.LT += (uint64_t)m.decl_len;
+    }
+    if (L.GT >= 0xFFFFFFFFull || L.LT >= 0xFFFFFFFFull) throw Fail{RC_E_INVALID, "memory too large"};
+    L.mems.push_back(mi);
+  }
+  L.keys = L.GT + (uint64_t)G * L.LT;
+  if (L.keys >= 0xFFFFFFFFull) throw Fail{RC_E_INVALID, "global + local cells must stay below 2^32"};
+  return L;
+}
+
+int pick_strategy(uint64_t n_log) {
+  if (g_strategy) return g_strategy;
+  (void)n_log;
+  return 2;
+}
+
+// Classify records already sorted by (cell, work-item): run reduce, per-cell
+// classification with commit, and ordered emission of the records.
+void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t interval, const Layout &L,
+                  int32_t *snap, uint32_t *hstats, std::vector<OutRec> &races, cudaStream_t s) {
+  uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(n), scan_tmp_words(n)));
+  uint32_t *head = W.head.get<uint32_t>(n), *runidx = W.runidx.get<uint32_t>(n);
+  launch_run_heads(sorted, n, head, s);
+  scan_exclusive(head, runidx, n, tmp, s);
+  Summary *sum = W.sum.get<Summary>(n);
+  uint32_t *khead = W.khead.get<uint32_t>(n), *keyidx = W.keyidx.get<uint32_t>(n);
+  launch_run_reduce(sorted, n, head, runidx, sum, khead, s);
+  CK(cudaMemcpyAsync(hstats, runidx + n - 1, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hstats + 1, head + n - 1, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const uint64_t nsum = (uint64_t)hstats[0] + hstats[1];
+  scan_exclusive(khead, keyidx, nsum, tmp, s);
+  CK(cudaMemcpyAsync(hstats, keyidx + nsum - 1, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hstats + 1, khead + nsum - 1, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const uint64_t nkeys = (uint64_t)hstats[0] + hstats[1];
+  uint32_t *nrec = W.nrec.get<uint32_t>(nkeys), *recoff = W.recoff.get<uint32_t>(nkeys);
+  ClassifyArgs ca{interval, (uint32_t)L.GT, (uint32_t)std::max<uint64_t>(L.LT, 1), snap};
+  launch_key_classify(sum, nsum, khead, keyidx, nrec, ca, s);
+  scan_exclusive(nrec, recoff, nkeys, tmp, s);
+  CK(cudaMemcpyAsync(hstats, recoff + nkeys - 1, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hstats + 1, nrec + nkeys - 1, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const uint64_t nrecs = (uint64_t)hstats[0] + hstats[1];
+  if (nrecs == 0) return;
+  OutRec *out = W.out.get<OutRec>(nrecs);
+  launch_key_emit(sum, nsum, khead, keyidx, nrec, recoff, out, ca, s);
+  size_t old = races.size();
+  races.resize(old + nrecs);
+  CK(cudaMemcpyAsync(races.data() + old, out, nrecs * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+// Sort path: the whole interval log is sorted and classified.
+void classify_sorted(Workspace &W, LogRec *log, uint64_t n, uint64_t keys, uint64_t N, uint32_t interval,
+                     const Layout &L, int32_t *snap, uint32_t *hstats, std::vector<OutRec> &races,
+                     cudaStream_t s) {
+  if (n == 0) return;
+  uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(n), scan_tmp_words(n)));
+  LogRec *other = W.logb.get<LogRec>(n);
+  LogRec *sorted = sort_log(log, other, n, bitwidth(N), bitwidth(keys) + bitwidth(N), tmp, s);
+  classify_run(W, sorted, n, interval, L, snap, hstats, races, s);
+}
+
+// Owner table of 2 words per cell; entries tagged with an older epoch count
+// as empty, so the table is cleared only when it is (re)allocated or the
+// epoch counter wraps.
+unsigned long long *shadow_table(Workspace &W, uint64_t keys, cudaStream_t s) {
+  const size_t before = W.owner.cap;
+  unsigned long long *t = W.owner.get<unsigned long long>(2 * keys);
+  if (W.owner.cap != before || W.epoch == 0) {
+    CK(cudaMemsetAsync(t, 0, W.owner.cap, s));
+    W.epoch = 0;
+  }
+  return t;
+}
+
+uint32_t shadow_next_epoch(Workspace &W, cudaStream_t s) {
+  if (W.epoch >= 0xFFFFFFF0u) {
+    CK(cudaMemsetAsync(W.owner.p, 0, W.owner.cap, s));
+    W.epoch = 0;
+  }
+  return ++W.epoch;
+}
+
+// Shadow path: commit single-writer cells from the own-write tables, send
+// the log records of shared written cells through the exact sort path.
+void classify_shadow(Workspace &W, const LogRec *log, uint64_t n, uint64_t keys, uint64_t N,
+                     uint32_t interval, const Layout &L, int32_t *snap, const unsigned long long *owner,
+                     uint32_t epoch, const uint2 *ow, const uint32_t *ow_count, uint32_t *dcount,
+                     uint32_t *hstats, std::vector<OutRec> &races, cudaStream_t s) {
+  launch_shadow_commit(ow, ow_count, N, (uint32_t)N, owner, epoch, snap, s);
+  if (n == 0) return;
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(dcount);
+  CK(cudaMemsetAsync(cnt, 0, 8, s));
+  LogRec *shared = W.logb.get<LogRec>(n);
+  launch_shadow_compact(log, n, owner, epoch, shared, cnt, s);
+  CK(cudaMemcpyAsync(hstats, cnt, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const uint64_t m = *reinterpret_cast<uint64_t *>(hstats);
+  if (m == 0) return;
+  // sort the shared records, ping-ponging between logb and the compact buffer
+  uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(m), scan_tmp_words(m)));
+  LogRec *other = W.compact.get<LogRec>(m);
+  LogRec *sorted = sort_log(shared, other, m, bitwidth(N), bitwidth(keys) + bitwidth(N), tmp, s);
+  classify_run(W, sorted, m, interval, L, snap, hstats, races, s);
+}
+
+rc_report *run_instance(const Instance &I) {
+  Workspace &W = g_ws;
+  const Program &P = *I.p;
+  cudaStream_t s = I.s;
+  if (!W.configured) {
+    CK(interp_configure());
+    W.configured = true;
+  }
+  Layout L = make_layout(P, I.in, I.G);
+  const uint64_t N = I.N;
+  const size_t smem = interp_smem_bytes((uint32_t)P.code.size(), (uint32_t)P.mems.size(), P.n_regs, I.S);
+  if (smem > 227 * 1024) throw Fail{RC_E_INVALID, "kernel too large for shared memory at this group size"};
+  const uint64_t cap = N * std::max<uint64_t>(P.max_access_per_interval, 1);
+  const uint64_t capw = std::max<uint64_t>(P.max_write_per_interval, 1);
+  if (cap >= 0xFFFFFFFFull) throw Fail{RC_E_CAPACITY, "interval log bound exceeds 2^32 records"};
+  const uint64_t need = cap * sizeof(LogRec) * 2 + cap * (sizeof(Summary) + 24) + N * capw * 8;
+  if (need > (uint64_t)200 << 30) throw Fail{RC_E_CAPACITY, "instance needs more than 200 GiB of workspace"};
+
+  // ---- set-up: program, memory snapshot, work-item state
+  Insn *dcode = W.code.get<Insn>(P.code.size());
+  MemInfo *dmems = W.mems.get<MemInfo>(std::max<size_t>(L.mems.size(), 1));
+  CK(cudaMemcpyAsync(dcode, P.code.data(), P.code.size() * sizeof(Insn), cudaMemcpyHostToDevice, s));
+  if (!L.mems.empty())
+    CK(cudaMemcpyAsync(dmems, L.mems.data(), L.mems.size() * sizeof(MemInfo), cudaMemcpyHostToDevice, s));
+  int32_t *snap = W.snap.get<int32_t>(std::max<uint64_t>(L.keys, 1));
+  {
+    uint32_t gi = 0;
+    for (size_t m = 0; m < P.mems.size(); m++) {
+      if (P.mems[m].space != 0) continue;
+      const uint64_t len = I.in->global_len[gi];
+      if (len) {
+        if (!I.in->global_init || !I.in->global_init[gi]) throw Fail{RC_E_INVALID, "missing global input"};
+        CK(cudaMemcpyAsync(snap + L.mems[m].base, I.in->global_init[gi], len * 4,
+                           I.in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      }
+      gi++;
+    }
+    if (L.keys > L.GT) CK(cudaMemsetAsync(snap + L.GT, 0, (L.keys - L.GT) * 4, s));
+  }
+  int32_t *regs = W.regs.get<int32_t>(N * P.n_regs);
+  uint32_t *pc = W.pc.get<uint32_t>(N), *st = W.st.get<uint32_t>(N);
+  CK(cudaMemsetAsync(regs, 0, N * P.n_regs * 4, s));
+  CK(cudaMemsetAsync(pc, 0, N * 4, s));
+  CK(cudaMemsetAsync(st, 0, N * 4, s));
+  uint2 *ow = W.ow.get<uint2>(N * capw);
+  LogRec *log = W.loga.get<LogRec>(cap);
+  const uint32_t err_cap = (uint32_t)std::min<uint64_t>(N, 1u << 24);
+  OutRec *errs = W.errs.get<OutRec>(err_cap);
+  const uint32_t nstops = P.n_barriers + 1;
+  const size_t stat_words = ST_STOPS + 2 * nstops;
+  uint32_t *dstats = W.stats.get<uint32_t>(stat_words);
+  uint32_t *hstats = W.hstats.get<uint32_t>(stat_words + 8);
+  CK(cudaMemsetAsync(dstats, 0, stat_words * 4, s));
+
+  const int strategy = pick_strategy(cap);
+  unsigned long long *owner = nullptr;
+  if (strategy == 2) owner = shadow_table(W, L.keys, s);
+  uint32_t *ow_cnt = W.owcnt.get<uint32_t>(N);
+
+  std::vector<OutRec> races, errors;
+  uint32_t interval = 0;
+  uint64_t prev_acc[2] = {0, 0};
+  for (;; interval++) {
+    CK(cudaMemsetAsync(dstats + ST_LOGCNT, 0, 8, s));
+    CK(cudaMemsetAsync(dstats + ST_FLAGS, 0, 8, s));
+    CK(cudaMemsetAsync(dstats + ST_STOPS, 0xFF, nstops * 4, s));
+    CK(cudaMemsetAsync(dstats + ST_STOPS + nstops, 0, nstops * 4, s));
+    InterpArgs a{};
+    a.code = dcode;
+    a.mems = dmems;
+    a.n_insn = (uint32_t)P.code.size();
+    a.n_regs = P.n_regs;
+    a.n_mems = (uint32_t)P.mems.size();
+    a.n_barriers = P.n_barriers;
+    a.S = I.S;
+    a.G = I.G;
+    a.group0 = 0;
+    a.GT = (uint32_t)L.GT;
+    a.LT = (uint32_t)L.LT;
+    a.interval = interval;
+    a.snap = snap;
+    a.regs = regs;
+    a.pc = pc;
+    a.st = st;
+    a.ow = ow;
+    a.capw = (uint32_t)std::min<uint64_t>(capw, 0xFFFFFFFFu);
+    a.ow_stride = (uint32_t)N;
+    a.log = log;
+    a.log_count = reinterpret_cast<unsigned long long *>(dstats + ST_LOGCNT);
+    a.log_cap = cap;
+    a.errs = errs;
+    a.err_count = dstats + ST_ERRCNT;
+    a.err_cap = err_cap;
+    a.stop_min = dstats + ST_STOPS;
+    a.stop_cnt = dstats + ST_STOPS + nstops;
+    a.acc = reinterpret_cast<unsigned long long *>(dstats + ST_ACC);
+    a.flags = dstats + ST_FLAGS;
+    a.ow_count = ow_cnt;
+    a.owner = owner;
+    a.epoch = strategy == 2 ? shadow_next_epoch(W, s) : 0;
+    if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
+    launch_interp(a, I.G, smem, s);
+    CK(cudaGetLastError());
+    if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], s));
+    CK(cudaMemcpyAsync(hstats, dstats, stat_words * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t nlog = *reinterpret_cast<uint64_t *>(hstats + ST_LOGCNT);
+    const uint32_t flags = hstats[ST_FLAGS];
+    if (flags) throw Fail{RC_E_CAPACITY, "interval log, own-write table or error log overflowed"};
+    const uint64_t acc_g = *reinterpret_cast<uint64_t *>(hstats + ST_ACC);
+    const uint64_t acc_l = *reinterpret_cast<uint64_t *>(hstats + ST_ACC + 2);
+    std::vector<uint32_t> stop_min(hstats + ST_STOPS, hstats + ST_STOPS + nstops);
+    std::vector<uint32_t> stop_cnt(hstats + ST_STOPS + nstops, hstats + ST_STOPS + 2 * nstops);
+    const uint32_t nerr = std::min(hstats[ST_ERRCNT], err_cap);
+    if (g_prof.on) {
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, g_prof.ev[0], g_prof.ev[1]));
+      g_prof.launches[0]++;
+      g_prof.ms[0] += ms;
+      g_prof.bytes[0] += 12.0 * (double)(acc_g - prev_acc[0]);
+      CK(cudaEventRecord(g_prof.ev[2], s));
+    }
+    // ---- classification + commit
+    if (strategy == 2) {
+      classify_shadow(W, log, nlog, L.keys, N, interval, L, snap, owner, a.epoch, ow, ow_cnt,
+                      dstats + ST_SCRATCH, hstats + stat_words, races, s);
+    } else {
+      classify_sorted(W, log, nlog, L.keys, N, interval, L, snap, hstats + stat_words, races, s);
+    }
+    if (g_prof.on) {
+      CK(cudaEventRecord(g_prof.ev[3], s));
+      CK(cudaEventSynchronize(g_prof.ev[3]));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, g_prof.ev[2], g_prof.ev[3]));
+      g_prof.launches[1]++;
+      g_prof.ms[1] += ms;
+      g_prof.bytes[1] += 12.0 * (double)(acc_g - prev_acc[0]);
+    }
+    prev_acc[0] = acc_g;
+    prev_acc[1] = acc_l;
+    // ---- error records of this interval
+    if (nerr) {
+      std::vector<OutRec> e(nerr);
+      CK(cudaMemcpyAsync(e.data(), errs, nerr * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::sort(e.begin(), e.end(), [](const OutRec &x, const OutRec &y) {
+        return x.cls != y.cls ? x.cls < y.cls : x.t_a < y.t_a;
+      });
+      errors.insert(errors.end(), e.begin(), e.end());
+    }
+    // ---- barrier agreement (barrier-release rule of Sec. 4)
+    uint32_t n_points = 0;
+    bool any_barrier = false;
+    for (uint32_t k = 0; k < nstops; k++) {
+      if (!stop_cnt[k]) continue;
+      n_points++;
+      if (k < P.n_barriers) any_barrier = true;
+    }
+    if (n_points >= 2) {
+      std::vector<OutRec> dv;
+      for (uint32_t k = 0; k < nstops; k++) {
+        if (!stop_cnt[k]) continue;
+        dv.push_back(OutRec{interval, 0, 0, 0, CLS_DIVERGENCE, stop_min[k],
+                            k < P.n_barriers ? k : 0xFFFFFFFFu, 0, 0, stop_cnt[k]});
+      }
+      std::sort(dv.begin(), dv.end(), [](const OutRec &x, const OutRec &y) { return x.t_a < y.t_a; });
+      // divergence sorts after ASSERT/OOB of the same interval (by class)
+      errors.insert(errors.end(), dv.begin(), dv.end());
+      break;
+    }
+    if (!any_barrier) break;
+  }
+
+  // ---- report
+  rc_report *rep = static_cast<rc_report *>(std::calloc(1, sizeof(rc_report)));
+  if (!rep) throw Fail{RC_E_NOMEM, "report allocation failed"};
+  const uint64_t acc_g = prev_acc[0], acc_l = prev_acc[1];
+  rep->n_intervals = interval + 1;
+  rep->n_global = acc_g;
+  rep->n_local = acc_l;
+  rep->n_access = acc_g + acc_l;
+  bool racy = false, div = false, as = false, oob = false;
+  for (const OutRec &r : races) racy |= r.cls == CLS_WW_RACE || r.cls == CLS_RW_RACE;
+  for (const OutRec &r : errors) {
+    div |= r.cls == CLS_DIVERGENCE;
+    as |= r.cls == CLS_ASSERT;
+    oob |= r.cls == CLS_OOB;
+  }
+  rep->status = racy ? RC_RACY : div ? RC_ERROR_DIVERGENCE : as ? RC_ERROR_ASSERT : oob ? RC_ERROR_OOB : RC_RACE_FREE;
+  rep->n_records = races.size() + errors.size();
+  if (rep->n_records) {
+    rep->records = static_cast<rc_record *>(std::malloc(rep->n_records * sizeof(rc_record)));
+    if (!rep->records) {
+      std::free(rep);
+      throw Fail{RC_E_NOMEM, "report allocation failed"};
+    }
+    static_assert(sizeof(rc_record) == sizeof(OutRec), "record layout");
+    std::memcpy(rep->records, races.data(), races.size() * sizeof(OutRec));
+    std::memcpy(rep->records + races.size(), errors.data(), errors.size() * sizeof(OutRec));
+  }
+  rep->final_len = L.GT;
+  if ((I.in->flags & RC_WANT_FINAL_MEMORY) && L.GT) {
+    rep->final_global = static_cast<int32_t *>(std::malloc(L.GT * 4));
+    if (!rep->final_global) {
+      std::free(rep->records);
+      std::free(rep);
+      throw Fail{RC_E_NOMEM, "report allocation failed"};
+    }
+    CK(cudaMemcpyAsync(rep->final_global, snap, L.GT * 4, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return rep;
+}
+
+void check_args(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in) {
+  if (!bc || !in) throw Fail{RC_E_INVALID, "null bytecode or input"};
+  if (groups == 0 || group_size == 0 || group_size > 1024) throw Fail{RC_E_INVALID, "bad launch shape"};
+  if ((uint64_t)groups * group_size > (1ull << 26)) throw Fail{RC_E_INVALID, "more than 2^26 work-items"};
+  if (in->n_global != bc->prog.n_global) throw Fail{RC_E_INVALID, "input count differs from the kernel's global declarations"};
+  if (in->n_global && !in->global_len) throw Fail{RC_E_INVALID, "missing global lengths"};
+}
+
+int fail_code(const Fail &f) {
+  g_last_error = f.msg;
+  return f.code;
+}
+
+}  // namespace
+}  // namespace rc
+
+using namespace rc;
+
+extern "C" {
+
+int rc_compile(const char *src, size_t len, rc_bytecode **out, char *err, size_t err_len) {
+  if (!out || !src) return RC_E_INVALID;
+  *out = nullptr;
+  try {
+    rc_bytecode *b = new rc_bytecode{compile_program(std::string(src, len))};
+    *out = b;
+    return RC_OK;
+  } catch (const CompileError &e) {
+    g_last_error = e.msg;
+    if (err && err_len) std::snprintf(err, err_len, "%s", e.msg.c_str());
+    return RC_E_PARSE;
+  } catch (const std::bad_alloc &) {
+    return RC_E_NOMEM;
+  }
+}
+
+int rc_bytecode_info_get(const rc_bytecode *bc, rc_bytecode_info *info) {
+  if (!bc || !info) return RC_E_INVALID;
+  const Program &p = bc->prog;
+  std::memset(info, 0, sizeof(*info));
+  info->n_insn = (uint32_t)p.code.size();
+  info->n_regs = p.n_regs;
+  info->n_vars = p.n_vars;
+  info->n_mems = (uint32_t)p.mems.size();
+  info->n_global = p.n_global;
+  info->n_barriers = p.n_barriers;
+  info->n_asserts = p.n_asserts;
+  uint64_t lc = 0;
+  for (const MemDecl &m : p.mems)
+    if (m.space == 1) lc += (uint64_t)m.decl_len;
+  info->local_cells = (uint32_t)std::min<uint64_t>(lc, 0xFFFFFFFFu);
+  info->max_access_per_interval = p.max_access_per_interval;
+  info->max_write_per_interval = p.max_write_per_interval;
+  return RC_OK;
+}
+
+int rc_check(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in,
+             rc_report **out) {
+  if (!out) return RC_E_INVALID;
+  *out = nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  try {
+    check_args(bc, groups, group_size, in);
+    if (g_prof.on) prof_events();
+    Instance I{&bc->prog, groups, group_size, (uint64_t)groups * group_size, in,
+               static_cast<cudaStream_t>(in->cuda_stream)};
+    *out = run_instance(I);
+    return RC_OK;
+  } catch (const Fail &f) {
+    return fail_code(f);
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return RC_E_NOMEM;
+  }
+}
+
+int rc_check_batch(const rc_bytecode *const *bcs, const uint32_t *groups, const uint32_t *group_size,
+                   const rc_input *inputs, size_t n, rc_report **out) {
+  if (!out || (n && (!bcs || !groups || !group_size || !inputs))) return RC_E_INVALID;
+  for (size_t i = 0; i < n; i++) out[i] = nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  size_t done = 0;
+  try {
+    for (size_t i = 0; i < n; i++) check_args(bcs[i], groups[i], group_size[i], &inputs[i]);
+    if (g_prof.on) prof_events();
+    for (; done < n; done++) {
+      Instance I{&bcs[done]->prog, groups[done], group_size[done],
+                 (uint64_t)groups[done] * group_size[done], &inputs[done],
+                 static_cast<cudaStream_t>(inputs[done].cuda_stream)};
+      out[done] = run_instance(I);
+    }
+    return RC_OK;
+  } catch (const Fail &f) {
+    for (size_t i = 0; i < done; i++) {
+      rc_report_free(out[i]);
+      out[i] = nullptr;
+    }
+    return fail_code(f);
+  } catch (const std::bad_alloc &) {
+    for (size_t i = 0; i < done; i++) {
+      rc_report_free(out[i]);
+      out[i] = nullptr;
+    }
+    g_last_error = "host allocation failed";
+    return RC_E_NOMEM;
+  }
+}
+
+void rc_bytecode_free(rc_bytecode *bc) { delete bc; }
+
+void rc_report_free(rc_report *rep) {
+  if (!rep) return;
+  std::free(rep->records);
+  std::free(rep->final_global);
+  std::free(rep);
+}
+
+const char *rc_strerror(int code) {
+  switch (code) {
+    case RC_OK: return "ok";
+    case RC_E_PARSE: return "kernel source does not parse";
+    case RC_E_INVALID: return "invalid argument, shape, input or bytecode";
+    case RC_E_CAPACITY: return "instance exceeds device capacity";
+    case RC_E_CUDA: return "CUDA runtime error";
+    case RC_E_TIMEOUT: return "bounded device wait ran out";
+    case RC_E_NOMEM: return "host out of memory";
+    default: return "unknown error";
+  }
+}
+
+const char *rc_last_error(void) { return g_last_error.c_str(); }
+
+int rc_release_workspace(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_ws.release_all();
+  return RC_OK;
+}
+
+int rc_set_strategy(int strategy) {
+  if (strategy < 0 || strategy > 2) return RC_E_INVALID;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_strategy = strategy;
+  return RC_OK;
+}
+
+int rc_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_prof.on = on != 0;
+  return RC_OK;
+}
+
+int rc_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (int k = 0; k < 3; k++) {
+    g_prof.launches[k] = 0;
+    g_prof.ms[k] = 0;
+    g_prof.bytes[k] = 0;
+  }
+  return RC_OK;
+}
+
+int rc_profile_get(int kind, uint64_t *launches, double *ms, double *bytes) {
+  if (kind < 0 || kind > 2) return RC_E_INVALID;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (launches) *launches = g_prof.launches[kind];
+  if (ms) *ms = g_prof.ms[kind];
+  if (bytes) *bytes = g_prof.bytes[kind];
+  return RC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,248 @@
+"""Python binding of libracecheck.so (argument marshalling only).
+
+Every step of a check runs in the CUDA library; this module converts numpy
+arrays or torch tensors to the pointers and lengths of the C ABI declared in
+include/racecheck.h and turns reports into numpy arrays.  If the library has
+not been built, importing functions here raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libracecheck.so")
+
+RECORD_FIELDS = ("interval", "space", "wg", "addr", "cls", "t_a", "t_b",
+                 "n_readers", "n_writers", "n_accesses")
+WW_RACE, WW_BENIGN, RW_RACE = 1, 2, 3
+OOB, ASSERT_FAIL, DIVERGENCE = 16, 17, 18
+RACE_FREE, RACY, ERROR_OOB, ERROR_ASSERT, ERROR_DIVERGENCE = 0, 1, 2, 3, 4
+STRATEGY_AUTO, STRATEGY_SORT, STRATEGY_SHADOW = 0, 1, 2
+RC_WANT_FINAL_MEMORY = 1
+
+
+class RaceCheckError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rc error {code}: {msg}")
+        self.code = code
+
+
+class _Input(ctypes.Structure):
+    _fields_ = [("n_global", ctypes.c_uint32),
+                ("global_len", ctypes.POINTER(ctypes.c_uint64)),
+                ("global_init", ctypes.POINTER(ctypes.c_void_p)),
+                ("on_device", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p),
+                ("flags", ctypes.c_uint32)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_intervals", ctypes.c_uint32),
+                ("n_access", ctypes.c_uint64), ("n_global", ctypes.c_uint64),
+                ("n_local", ctypes.c_uint64), ("n_records", ctypes.c_uint64),
+                ("records", ctypes.c_void_p), ("final_len", ctypes.c_uint64),
+                ("final_global", ctypes.c_void_p)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ("n_insn", "n_regs", "n_vars", "n_mems", "n_global", "n_barriers", "n_asserts",
+                 "local_cells")] + [("max_access_per_interval", ctypes.c_uint64),
+                                    ("max_write_per_interval", ctypes.c_uint64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libracecheck.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1308_3203_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, c_int = ctypes.c_void_p, ctypes.c_int
+        lib.rc_compile.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(vp),
+                                   ctypes.c_char_p, ctypes.c_size_t]
+        lib.rc_bytecode_info_get.argtypes = [vp, ctypes.POINTER(_Info)]
+        lib.rc_check.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input),
+                                 ctypes.POINTER(ctypes.POINTER(_Report))]
+        lib.rc_check_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_Input),
+                                       ctypes.c_size_t, ctypes.POINTER(ctypes.POINTER(_Report))]
+        lib.rc_bytecode_free.argtypes = [vp]
+        lib.rc_bytecode_free.restype = None
+        lib.rc_report_free.argtypes = [ctypes.POINTER(_Report)]
+        lib.rc_report_free.restype = None
+        lib.rc_strerror.argtypes = [c_int]
+        lib.rc_strerror.restype = ctypes.c_char_p
+        lib.rc_last_error.argtypes = []
+        lib.rc_last_error.restype = ctypes.c_char_p
+        lib.rc_set_strategy.argtypes = [c_int]
+        lib.rc_profile_enable.argtypes = [c_int]
+        lib.rc_profile_get.argtypes = [c_int, ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+        for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
+                  "rc_set_strategy", "rc_profile_enable", "rc_profile_reset", "rc_profile_get",
+                  "rc_release_workspace"):
+            getattr(lib, f).restype = c_int
+        _lib = lib
+        return lib
+
+
+def _raise(code: int):
+    lib = load()
+    raise RaceCheckError(code, lib.rc_last_error().decode(errors="replace")
+                         or lib.rc_strerror(code).decode())
+
+
+class Bytecode:
+    """A compiled kernel (library-owned bytecode)."""
+
+    def __init__(self, handle, src: str):
+        self._h = handle
+        self.src = src
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = _Info()
+        rc = load().rc_bytecode_info_get(self._h, ctypes.byref(i))
+        if rc:
+            _raise(rc)
+        return {n: getattr(i, n) for n, _ in _Info._fields_}
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.rc_bytecode_free(self._h)
+            self._h = None
+
+
+def compile(src: str) -> Bytecode:  # noqa: A001 - the paper's rc_compile
+    lib = load()
+    h = ctypes.c_void_p()
+    err = ctypes.create_string_buffer(1024)
+    b = src.encode()
+    rc = lib.rc_compile(b, len(b), ctypes.byref(h), err, 1024)
+    if rc:
+        raise RaceCheckError(rc, err.value.decode(errors="replace"))
+    return Bytecode(h, src)
+
+
+def _is_torch_cuda(x) -> bool:
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+def _marshal(globals_, stream, want_final):
+    keep = []
+    lens, ptrs = [], []
+    on_device = bool(globals_) and all(_is_torch_cuda(g) for g in globals_)
+    for g in globals_:
+        if on_device:
+            if str(g.dtype) != "torch.int32" or not g.is_contiguous():
+                raise ValueError("device inputs must be contiguous int32 tensors")
+            keep.append(g)
+            lens.append(g.numel())
+            ptrs.append(g.data_ptr())
+        else:
+            a = np.ascontiguousarray(np.asarray(g.cpu() if hasattr(g, "cpu") else g, dtype=np.int32))
+            keep.append(a)
+            lens.append(a.size)
+            ptrs.append(a.ctypes.data if a.size else None)
+    n = len(keep)
+    clens = (ctypes.c_uint64 * max(n, 1))(*lens)
+    cptrs = (ctypes.c_void_p * max(n, 1))(*ptrs)
+    if stream is None and on_device:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    inp = _Input(n, clens, cptrs, 1 if on_device else 0,
+                 ctypes.c_void_p(int(stream) if stream else 0),
+                 RC_WANT_FINAL_MEMORY if want_final else 0)
+    return inp, (keep, clens, cptrs)
+
+
+def _report(p) -> dict:
+    r = p.contents
+    recs = np.zeros((r.n_records, 10), dtype=np.uint32)
+    if r.n_records:
+        ctypes.memmove(recs.ctypes.data, r.records, r.n_records * 40)
+    fin = None
+    if r.final_global:
+        fin = np.zeros(r.final_len, dtype=np.int32)
+        ctypes.memmove(fin.ctypes.data, r.final_global, r.final_len * 4)
+    out = dict(status=r.status, n_intervals=r.n_intervals, n_access=r.n_access,
+               n_global=r.n_global, n_local=r.n_local, records=recs, final=fin)
+    load().rc_report_free(p)
+    return out
+
+
+def check(bc: Bytecode, groups: int, group_size: int, globals_, stream=None,
+          want_final: bool = True) -> dict:
+    """Check one instance.  ``globals_``: one int32 array per ``global``
+    declaration (numpy / host tensors, or contiguous int32 CUDA tensors)."""
+    lib = load()
+    inp, keep = _marshal(globals_, stream, want_final)
+    out = ctypes.POINTER(_Report)()
+    rc = lib.rc_check(bc.handle, groups, group_size, ctypes.byref(inp), ctypes.byref(out))
+    del keep
+    if rc:
+        _raise(rc)
+    return _report(out)
+
+
+def check_batch(items, want_final: bool = True) -> list:
+    """Check many instances: items = [(bytecode, groups, group_size, globals)]."""
+    lib = load()
+    n = len(items)
+    hs = (ctypes.c_void_p * max(n, 1))(*[it[0].handle.value for it in items])
+    gs = (ctypes.c_uint32 * max(n, 1))(*[it[1] for it in items])
+    ss = (ctypes.c_uint32 * max(n, 1))(*[it[2] for it in items])
+    inputs = (_Input * max(n, 1))()
+    keep = []
+    for i, it in enumerate(items):
+        inp, k = _marshal(it[3], None, want_final)
+        inputs[i] = inp
+        keep.append(k)
+    outs = (ctypes.POINTER(_Report) * max(n, 1))()
+    rc = lib.rc_check_batch(hs, gs, ss, inputs, n, outs)
+    if rc:
+        _raise(rc)
+    return [_report(outs[i]) for i in range(n)]
+
+
+def set_strategy(k: int) -> None:
+    rc = load().rc_set_strategy(k)
+    if rc:
+        _raise(rc)
+
+
+def profile_enable(on: bool = True) -> None:
+    load().rc_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    load().rc_profile_reset()
+
+
+def profile_get(kind: int) -> dict:
+    n = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    by = ctypes.c_double()
+    rc = load().rc_profile_get(kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by))
+    if rc:
+        _raise(rc)
+    return dict(launches=n.value, ms=ms.value, bytes=by.value)
+
+
+def release_workspace() -> None:
+    load().rc_release_workspace()

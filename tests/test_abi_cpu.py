@@ -1,0 +1,96 @@
+"""Host-side checks of the C ABI library (no GPU compute calls)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1308_3203_gb300 import build as gpu_build
+from paper_1308_3203_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rc():
+    gpu_build.build()
+    from paper_1308_3203_gb300 import racecheck
+    racecheck.load()
+    return racecheck
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(rc_\w+)\s*\(", text, re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol(rc):
+    lib = ctypes.CDLL(rc.LIB_PATH)
+    syms = declared_symbols()
+    assert {"rc_compile", "rc_check", "rc_check_batch", "rc_report_free"} <= syms
+    for s in sorted(syms):
+        assert hasattr(lib, s), s
+
+
+def test_compile_reports_static_facts(rc):
+    b = rc.compile("kernel k(global int A[], local int L[8], global int g) {\n"
+                   "  x = A[tid];\n  barrier;\n  for i in 0 .. 4 { L[i] = x + A[i]; }\n"
+                   "  assert(x >= 0);\n  g = x;\n}\n")
+    i = b.info()
+    assert i["n_mems"] == 3 and i["n_global"] == 2 and i["n_barriers"] == 1
+    assert i["n_asserts"] == 1 and i["local_cells"] == 8
+    # interval 0: one read; interval 1: 4 x (read + write) + write of g
+    assert i["max_access_per_interval"] == 9
+    assert i["max_write_per_interval"] == 5
+
+
+@pytest.mark.parametrize("bad", [
+    "kernel k(global int A[]) { A[0] = ; }",
+    "kernel k(global int A[4]) { }",
+    "kernel k(local int L[]) { }",
+    "kernel k() { B[0] = 1; }",
+    "kernel k() { for i in 0 .. 3 { i = 2; } }",
+    "kernel k() { for i in 0 .. 3 { for i in 0 .. 2 { } } }",
+    "kernel k() { tid = 1; }",
+    "kernel k() { x = 99999999999; }",
+    "kernel k(global int A[], global int A[]) { }",
+    "kernel k() { x = 1 }",
+    "kernel k() { x = 1; } trailing",
+    "kernel k() { x = @; }",
+])
+def test_compile_rejects_bad_programs(rc, bad):
+    with pytest.raises(rc.RaceCheckError) as e:
+        rc.compile(bad)
+    assert e.value.code == 1
+
+
+def test_static_bounds_cover_every_run(rc, oracle):
+    """The per-interval access/write bounds the runtime sizes its logs with
+    are never exceeded by a real run (checked against the oracle)."""
+    for s in range(25):
+        for f in (W.small_kernel(s),
+                  W.large_kernel(s, groups=2, group_size=64, global_len=4096, local_len=256),
+                  W.stress_kernel(s, groups=2, group_size=64),
+                  W.tiny_kernel(s)):
+            o = oracle.check(f.src, f.groups, f.group_size, f.globals)
+            i = rc.compile(f.src).info()
+            assert o["max_acc"] <= i["max_access_per_interval"], f.name
+            assert o["max_wr"] <= i["max_write_per_interval"], f.name
+
+
+def test_bad_arguments_rejected_without_gpu_work(rc):
+    b = rc.compile("kernel k(global int A[]) { A[tid] = 1; }")
+    with pytest.raises(rc.RaceCheckError) as e:
+        rc.check(b, 0, 32, [np.zeros(4, np.int32)])
+    assert e.value.code == 2
+    with pytest.raises(rc.RaceCheckError):
+        rc.check(b, 1, 2048, [np.zeros(4, np.int32)])
+    with pytest.raises(rc.RaceCheckError):
+        rc.check(b, 1, 32, [])
+    with pytest.raises(rc.RaceCheckError):
+        rc.set_strategy(7)

@@ -1,0 +1,165 @@
+"""GPU parity: reports of the CUDA path through the C ABI against the oracle.
+
+Race reports are integer results, so the bar is bit-exact equality of every
+record (interval, cell, class, witness pair, counts), the status, the access
+counters and the final global memory.  Each case runs under both
+classification strategies (full sort, shadow owner table).
+"""
+import numpy as np
+import pytest
+
+from paper_1308_3203_gb300 import workloads as W
+from tests.golden import golden
+
+pytestmark = pytest.mark.gpu
+
+STRATEGIES = (1, 2)
+
+
+@pytest.fixture(scope="module")
+def rc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1308_3203_gb300 import build as gpu_build
+    gpu_build.build()
+    from paper_1308_3203_gb300 import racecheck
+    racecheck.load()
+    yield racecheck
+    racecheck.set_strategy(0)
+
+
+def same(got, want, what=""):
+    for k in ("status", "n_intervals", "n_access", "n_global", "n_local"):
+        assert got[k] == want[k], (what, k, got[k], want[k])
+    np.testing.assert_array_equal(got["records"], want["records"], err_msg=what)
+    np.testing.assert_array_equal(got["final"], want["final"], err_msg=what)
+
+
+def run_both(rc, oracle, inst, strategies=STRATEGIES):
+    want = oracle.check(inst.src, inst.groups, inst.group_size, inst.globals)
+    bc = rc.compile(inst.src)
+    for s in strategies:
+        rc.set_strategy(s)
+        got = rc.check(bc, inst.groups, inst.group_size, inst.globals)
+        same(got, want, f"{inst.name} strategy {s}")
+    rc.set_strategy(0)
+    return want
+
+
+@pytest.mark.parametrize("name", golden.names())
+def test_golden(rc, name):
+    g = golden.load(name)
+    bc = rc.compile(g["src"])
+    for s in STRATEGIES:
+        rc.set_strategy(s)
+        r = rc.check(bc, g["groups"], g["group_size"], g["globals"])
+        for k, v in g["expect"].items():
+            assert r[k] == v, (name, s, k)
+        np.testing.assert_array_equal(r["records"], g["records"])
+        np.testing.assert_array_equal(r["final"], g["final"])
+    rc.set_strategy(0)
+
+
+@pytest.mark.parametrize("chunk", range(5))
+def test_small_kernels(rc, oracle, chunk):
+    """1 group x 64, 1 barrier, 32 statements over A[256] (seeds 0..199)."""
+    for seed in range(chunk * 40, chunk * 40 + 40):
+        run_both(rc, oracle, W.small_kernel(seed))
+
+
+def test_tiny_kernels(rc, oracle):
+    for seed in range(150):
+        run_both(rc, oracle, W.tiny_kernel(seed))
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("shape", [(8, 256), (3, 100), (5, 1), (1, 1024), (33, 32)])
+def test_large_kernels_reduced(rc, oracle, seed, shape):
+    """Config-2 statement mix (loops, local memory, planted collisions) at
+    shapes the oracle finishes quickly, incl. ragged group sizes."""
+    G, S = shape
+    inst = W.large_kernel(seed, groups=G, group_size=S, global_len=max(16 * G * S, 4096),
+                          local_len=16 * S)
+    run_both(rc, oracle, inst)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_stress_kernels_reduced(rc, oracle, seed):
+    """Config-5 statement mix (nested loops, branches on loaded values)."""
+    run_both(rc, oracle, W.stress_kernel(seed, groups=16, group_size=1024))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_batch_shapes(rc, oracle, seed):
+    """Config-3 kernels (uneven shapes) through rc_check_batch."""
+    insts = W.batch_kernels(seed, 12)
+    insts = [i for i in insts if i.n_threads * 300 < 2_000_000][:6]
+    want = [oracle.check(i.src, i.groups, i.group_size, i.globals) for i in insts]
+    bcs = [rc.compile(i.src) for i in insts]
+    for s in STRATEGIES:
+        rc.set_strategy(s)
+        got = rc.check_batch([(b, i.groups, i.group_size, i.globals) for b, i in zip(bcs, insts)])
+        for g, w, i in zip(got, want, insts):
+            same(g, w, i.name)
+    rc.set_strategy(0)
+
+
+EDGE = [
+    ("kernel e() { }", 2, 3, []),
+    ("kernel e(global int A[]) { A[tid] = tid; }", 1, 1, [np.zeros(1, np.int32)]),
+    ("kernel e(global int A[]) { A[tid] = 1; }", 2, 3, [np.zeros(0, np.int32)]),
+    ("kernel e(global int A[]) { A[0] = tid; }", 4, 1024, [np.zeros(1, np.int32)]),
+    ("kernel e(global int A[]) { x = A[0]; A[0] = 3; }", 7, 999, [np.array([3], np.int32)]),
+    ("kernel e(global int A[]) { if (tid < 2) { barrier; } else { barrier; } A[tid] = 1; }",
+     1, 4, [np.zeros(4, np.int32)]),
+    ("kernel e(global int A[]) { if (tid == 0) { barrier; } }", 1, 3, [np.zeros(1, np.int32)]),
+    ("kernel e(global int A[]) { assert(tid != 1); assume(tid != 2); A[tid] = 1; }",
+     2, 4, [np.zeros(8, np.int32)]),
+    ("kernel e(global int A[], local int L[2]) { L[tid] = 1; barrier; A[gtid] = L[tid % 2]; }",
+     3, 3, [np.zeros(9, np.int32)]),
+    ("kernel e(global int A[], local int L[4]) { L[0] = tid; barrier; A[gtid] = L[0]; "
+     "if (tid == 0) { L[1] = wg; } }", 5, 2, [np.zeros(10, np.int32)]),
+    ("kernel e(global int A[]) { for i in 0 .. 40 { barrier; A[(gtid + i) % size(A)] = i; } }",
+     2, 64, [np.zeros(128, np.int32)]),
+    ("kernel e(global int A[]) { x = 2147483647; A[tid] = x + tid; A[tid + 4] = -2147483648 / -1; "
+     "A[tid + 8] = -7 % 3; A[tid + 12] = 7 / 0; }", 1, 4, [np.zeros(16, np.int32)]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(EDGE)))
+def test_edge_cases(rc, oracle, case):
+    src, G, S, glob = EDGE[case]
+    run_both(rc, oracle, W.Instance(f"edge{case}", src, G, S, glob))
+
+
+def test_device_inputs_and_stream(rc, oracle):
+    import torch
+    inst = W.large_kernel(1, groups=4, group_size=128, global_len=8192, local_len=512)
+    want = oracle.check(inst.src, inst.groups, inst.group_size, inst.globals)
+    bc = rc.compile(inst.src)
+    s = torch.cuda.Stream()
+    dev = [torch.from_numpy(a).cuda() for a in inst.globals]
+    with torch.cuda.stream(s):
+        got = rc.check(bc, inst.groups, inst.group_size, dev)
+    same(got, want)
+    # the caller's device input is not modified
+    np.testing.assert_array_equal(dev[0].cpu().numpy(), inst.globals[0])
+
+
+def test_repeat_calls_reuse_workspace(rc, oracle):
+    a = W.large_kernel(2, groups=8, group_size=64, global_len=8192, local_len=256)
+    b = W.small_kernel(3)
+    wa = oracle.check(a.src, a.groups, a.group_size, a.globals)
+    wb = oracle.check(b.src, b.groups, b.group_size, b.globals)
+    ba, bb = rc.compile(a.src), rc.compile(b.src)
+    for _ in range(3):
+        same(rc.check(ba, a.groups, a.group_size, a.globals), wa)
+        same(rc.check(bb, b.groups, b.group_size, b.globals), wb)
+
+
+def test_large_kernel_full_size(rc, oracle):
+    """1024 groups x 256, 8 barriers, 200 statements, global int[4M], local
+    int[4096] per group: the full report against the oracle (both strategies)."""
+    inst = W.large_kernel(0)
+    want = run_both(rc, oracle, inst)
+    assert want["n_access"] > 10_000_000
