@@ -1,0 +1,272 @@
+"""Benchmark: race-checked accesses per second on one GB300.
+
+One step = one full race check (every barrier interval: interpreter, log
+classification, commit, barrier agreement, report) of the large synthetic
+instance: 1024 work-groups x 256 work-items, 8 barriers, 200 statements with
+constant-trip loops, a global int32[4M] array and a local int32[4096] array
+per group (seed = rank).  Timed with CUDA events on the launching stream,
+each step bracketed by a barrier and a synchronize, L2 flushed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank checks its own instance (replicas: the
+single-instance path has no exchange step); value = all ranks' accesses /
+the slowest rank's time.  --impl reference times the CPU oracle on a bounded
+sample of the same instance (first groups only) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "race-checked accesses/s"
+UNIT = "accesses/s"
+WORKLOAD = ("large instance: 1024 groups x 256 work-items, 8 barriers, 200 statements "
+            "(loops of 1-16 trips), global int32[4M], local int32[4096] per group, "
+            "~5%+5% planted racy/benign stores")
+# oracle sample: the same program and input, first groups only
+SAMPLE_GROUPS = 96
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--strategy", type=int, default=0, help="0 auto, 1 sort, 2 shadow")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args, world, rank):
+    """CPU oracle on the host cores, bounded sample of the same workload."""
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_1308_3203_gb300 import workloads as W
+    inst = W.large_kernel(0)
+    oracle.build()
+    times, acc = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.check(inst.src, SAMPLE_GROUPS, inst.group_size, inst.globals)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            acc += r["n_access"]
+    v = acc / sum(times)
+    sample = (f"same program and input, first {SAMPLE_GROUPS} of 1024 groups "
+              f"({r['n_access']} accesses per step), single-threaded")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline():
+    from oracle import oracle
+    from paper_1308_3203_gb300 import workloads as W
+    inst = W.large_kernel(0)
+    oracle.build()
+    t0 = time.perf_counter()
+    acc, n = 0, 0
+    while time.perf_counter() - t0 < 12.0 or n == 0:
+        r = oracle.check(inst.src, SAMPLE_GROUPS, inst.group_size, inst.globals)
+        acc += r["n_access"]
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": acc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"same program and input, first {SAMPLE_GROUPS} of 1024 groups, "
+                      f"{n} run(s) in {dt:.1f} s, single-threaded"}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_1308_3203_gb300 import build as gpu_build
+    from paper_1308_3203_gb300 import racecheck as rc
+    from paper_1308_3203_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gpu_build.build()
+    rc.load()
+    rc.set_strategy(args.strategy)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+
+    inst = W.large_kernel(rank)
+    bc = rc.compile(inst.src)
+    dev_in = [torch.from_numpy(a).cuda() for a in inst.globals]
+    host_in = [torch.from_numpy(a).pin_memory() for a in inst.globals]
+    host_np = [t.numpy() for t in host_in]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(inputs, k):
+        tot, last = 0.0, None
+        for _ in range(k):
+            flush.zero_()
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            last = rc.check(bc, inst.groups, inst.group_size, inputs, stream=stream.cuda_stream,
+                            want_final=False)
+            b.record(stream)
+            barrier()
+            tot += a.elapsed_time(b)
+        return tot, last
+
+    for _ in range(args.warmup):
+        rc.check(bc, inst.groups, inst.group_size, dev_in, want_final=False)
+    torch.cuda.synchronize()
+
+    # ---- device-resident inputs (value)
+    rc.profile_reset()
+    rc.profile_enable(True)
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = rc.kernel_launches()
+    ms, rep = timed(dev_in, args.steps)
+    launches = rc.kernel_launches() - l0
+    clk = clocks.stop()
+    rc.profile_enable(False)
+    prof = [rc.profile_get(k) for k in range(3)]
+
+    # ---- host inputs through the C ABI (e2e): H2D of the inputs and D2H of
+    # the report inside the timed region
+    ms_e2e, rep_e2e = timed(host_np, args.steps)
+
+    acc_step = rep["n_access"]
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms, ms_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, ms_e2e = float(t[0]), float(t[1])
+        a = torch.tensor([acc_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(a)
+        acc_all = float(a[0])
+    else:
+        acc_all = float(acc_step)
+    value = acc_all * args.steps / (t_max / 1e3)
+    e2e = acc_all * args.steps / (ms_e2e / 1e3)
+
+    # roofline: the interpreter kernel (one launch per barrier interval).
+    # Algorithmic bytes: 12 B per global access logged (cell, work-item|rw,
+    # value) -- the log write half of the 24 B per global access the
+    # log/classify path must move.
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    p0 = prof[0]
+    interp_ms = p0["ms"] / max(p0["launches"], 1)
+    achieved = (p0["bytes"] / max(p0["launches"], 1)) / (interp_ms / 1e3) / 1e9 if interp_ms else 0.0
+    roof = {"kernel": "interp_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s",
+            "avg_launch_ms": interp_ms,
+            "classify_ms_per_interval": prof[1]["ms"] / max(prof[1]["launches"], 1),
+            "classify_algorithmic_gbs": (prof[1]["bytes"] / max(prof[1]["ms"], 1e-9)) / 1e6}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "accesses_per_step": acc_step,
+                   "global_accesses_per_step": rep["n_global"],
+                   "strategy": {0: "auto", 1: "sort", 2: "shadow"}[args.strategy],
+                   "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "e2e": {"value": e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(a.nbytes for a in host_np)),
+                "d2h_bytes_per_step": int(rep_e2e["records"].nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

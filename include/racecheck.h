@@ -165,6 +165,10 @@ int rc_profile_enable(int on);
 int rc_profile_reset(void);
 int rc_profile_get(int kind, uint64_t *launches, double *ms, double *bytes);
 
+/* Number of CUDA kernels the library has launched since it was loaded
+ * (every launch counts, whatever the profiling state). */
+uint64_t rc_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

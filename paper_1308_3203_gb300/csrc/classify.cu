@@ -213,20 +213,24 @@ unsigned blocks_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThread
 }  // namespace
 
 void launch_run_heads(const LogRec *r, uint64_t n, uint32_t *head, cudaStream_t s) {
+  if (n) count_launch();
   if (n) run_heads_kernel<<<blocks_for(n), kThreads, 0, s>>>(r, n, head);
 }
 void launch_run_reduce(const LogRec *r, uint64_t n, const uint32_t *head, const uint32_t *runidx,
                        Summary *sum, uint32_t *khead, cudaStream_t s) {
+  if (n) count_launch();
   if (n) run_reduce_kernel<<<blocks_for(n), kThreads, 0, s>>>(r, n, head, runidx, sum, khead);
 }
 void launch_key_classify(const Summary *sum, uint64_t nsum, const uint32_t *khead,
                          const uint32_t *keyidx, uint32_t *nrec, const ClassifyArgs &a,
                          cudaStream_t s) {
+  if (nsum) count_launch();
   if (nsum) key_classify_kernel<<<blocks_for(nsum), kThreads, 0, s>>>(sum, nsum, khead, keyidx, nrec, a);
 }
 void launch_key_emit(const Summary *sum, uint64_t nsum, const uint32_t *khead,
                      const uint32_t *keyidx, const uint32_t *nrec, const uint32_t *recoff,
                      OutRec *out, const ClassifyArgs &a, cudaStream_t s) {
+  if (nsum) count_launch();
   if (nsum)
     key_emit_kernel<<<blocks_for(nsum), kThreads, 0, s>>>(sum, nsum, khead, keyidx, nrec, recoff, out, a);
 }

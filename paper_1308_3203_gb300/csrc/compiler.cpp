@@ -247,16 +247,26 @@ class Compiler {
 
   // every name in the body that is not reserved and not a memory object is
   // a private variable (implicitly declared, initially 0)
+  static int builtin_reg(Op op) {
+    switch (op) {
+      case OP_TID: return REG_TID;
+      case OP_WG: return REG_WG;
+      case OP_GTID: return REG_GTID;
+      case OP_GSIZE: return REG_GSIZE;
+      default: return REG_NGROUPS;
+    }
+  }
+
   void collect_vars() {
     for (size_t j = i_; j < tk_.size(); j++) {
       const Token &t = tk_[j];
       if (t.kind != Token::NAME || reserved().count(t.s) || mems_.count(t.s)) continue;
       if (!vars_.count(t.s)) {
-        int r = (int)vars_.size();
+        int r = kBuiltinRegs + (int)vars_.size();
         vars_[t.s] = r;
       }
     }
-    next_tmp_ = (int)vars_.size();
+    next_tmp_ = kBuiltinRegs + (int)vars_.size();
     max_reg_ = next_tmp_;
   }
 
@@ -265,13 +275,13 @@ class Compiler {
     max_reg_ = std::max(max_reg_, next_tmp_);
     return r;
   }
-  bool is_tmp(int r) const { return r >= (int)vars_.size(); }
+  bool is_tmp(int r) const { return r >= kBuiltinRegs + (int)vars_.size(); }
   void release(int r) {
     if (is_tmp(r) && r == next_tmp_ - 1) next_tmp_--;
   }
 
-  int emit(Op op, int d, int a, int b, int32_t imm) {
-    Insn in{(uint8_t)op, (uint8_t)d, (uint8_t)a, (uint8_t)b, imm};
+  int emit(Op op, int d, int a, int b, int32_t imm, int32_t imm2 = 0) {
+    Insn in{(uint8_t)op, (uint8_t)d, (uint8_t)a, (uint8_t)b, imm, imm2, 0};
     p_.code.push_back(in);
     return (int)p_.code.size() - 1;
   }
@@ -413,7 +423,7 @@ class Compiler {
     switch (op) {
       case OP_ADD: iop = OP_ADDI; return true;
       case OP_MUL: iop = OP_MULI; return true;
-      case OP_SUB: iop = swapped ? OP_RSUBI : OP_SUBI; return true;
+      case OP_SUB: iop = swapped ? OP_RSUBI : OP_ADDI; return true;  // a - c == a + (-c) mod 2^32
       case OP_DIV: if (swapped) return false; iop = OP_DIVI; return true;
       case OP_MOD: if (swapped) return false; iop = OP_MODI; return true;
       case OP_LT: iop = swapped ? OP_GTI : OP_LTI; return true;
@@ -424,6 +434,92 @@ class Compiler {
       case OP_NE: iop = OP_NEI; return true;
       default: return false;
     }
+  }
+
+  // Index of a shared access.  Constants around the index fold into the
+  // LD/ST operands: `e + c` gives index = REG + c, and `c2 + (e + c1) % 2^k`
+  // gives index = ((REG + c1) & (2^k - 1)) + c2 (the Euclidean modulus by a
+  // power of two is that mask); the folded forms wrap exactly as the
+  // expression does.
+  struct Index {
+    int32_t c1 = 0, c2 = 0;
+    bool am = false;
+    uint32_t k = 0;
+    uint32_t ctl(uint32_t mem) const {
+      return (am ? (CTL_AM | (k << CTL_K_SHIFT)) : 0u) | (mem << CTL_MEM_SHIFT);
+    }
+  };
+  static bool split_const(const Ex *e, const Ex *&rest, int32_t &c) {
+    if (e->k != Ex::BIN) return false;
+    if (e->op == OP_ADD && e->r->k == Ex::CONST) { rest = e->l.get(); c = e->r->c; return true; }
+    if (e->op == OP_ADD && e->l->k == Ex::CONST) { rest = e->r.get(); c = e->l->c; return true; }
+    if (e->op == OP_SUB && e->r->k == Ex::CONST) {
+      rest = e->l.get();
+      c = (int32_t)(0u - (uint32_t)e->r->c);
+      return true;
+    }
+    return false;
+  }
+  static bool pow2_mod(const Ex *e, uint32_t &k) {
+    if (e->k != Ex::BIN || e->op != OP_MOD || e->r->k != Ex::CONST) return false;
+    const uint32_t m = e->r->c < 0 ? 0u - (uint32_t)e->r->c : (uint32_t)e->r->c;
+    if (m == 0 || (m & (m - 1)) != 0) return false;
+    k = 0;
+    while ((1u << k) != m) k++;
+    return true;
+  }
+  int gen_index(const Ex *e, Index &ix) {
+    ix = Index();
+    const Ex *inner = e;
+    int32_t c2 = 0;
+    if (!split_const(e, inner, c2)) {
+      inner = e;
+      c2 = 0;
+    }
+    uint32_t k = 0;
+    if (pow2_mod(inner, k)) {
+      ix.am = true;
+      ix.k = k;
+      ix.c2 = c2;
+      const Ex *base = inner->l.get();
+      int32_t c1 = 0;
+      if (!split_const(base, base, c1)) c1 = 0;
+      ix.c1 = c1;
+      return gen(base, -1);
+    }
+    ix.c1 = c2;
+    return gen(inner, -1);
+  }
+
+  static bool is_mul_const(const Ex *e) {
+    return e->k == Ex::BIN && e->op == OP_MUL && (e->r->k == Ex::CONST || e->l->k == Ex::CONST);
+  }
+
+  // Emit a branch taken when condition c is false; returns its index (the
+  // caller patches imm2).  A comparison with a constant becomes one fused
+  // compare-and-branch instruction.
+  int branch_if_false(const Ex *c) {
+    static const Op cmp[] = {OP_LT, OP_LE, OP_GT, OP_GE, OP_EQ, OP_NE};
+    static const Op bf[] = {OP_BFLTI, OP_BFLEI, OP_BFGTI, OP_BFGEI, OP_BFEQI, OP_BFNEI};
+    static const Op mirror[] = {OP_BFGTI, OP_BFGEI, OP_BFLTI, OP_BFLEI, OP_BFEQI, OP_BFNEI};
+    if (c->k == Ex::BIN) {
+      for (int k = 0; k < 6; k++) {
+        if (c->op != cmp[k]) continue;
+        if (c->r->k == Ex::CONST) {
+          int ra = gen(c->l.get(), -1);
+          release(ra);
+          return emit(bf[k], 0, ra, 0, c->r->c);
+        }
+        if (c->l->k == Ex::CONST) {
+          int rb = gen(c->r.get(), -1);
+          release(rb);
+          return emit(mirror[k], 0, rb, 0, c->l->c);
+        }
+      }
+    }
+    int r = gen(c, -1);
+    release(r);
+    return emit(OP_BZ, 0, r, 0, 0);
   }
 
   int gen(const Ex *e, int dst) {
@@ -439,21 +535,27 @@ class Compiler {
           return dst;
         }
         return e->reg;
-      case Ex::BUILTIN: {
-        int d = dst >= 0 ? dst : tmp();
-        emit(e->op, d, 0, 0, 0);
-        return d;
+      case Ex::BUILTIN: {  // built-ins live in the fixed registers 0..kBuiltinRegs-1
+        const int r = builtin_reg(e->op);
+        if (dst >= 0 && dst != r) {
+          emit(OP_MOV, dst, r, 0, 0);
+          return dst;
+        }
+        return r;
       }
       case Ex::SIZE: {
         int d = dst >= 0 ? dst : tmp();
-        emit(OP_SIZE, d, 0, 0, e->mem);
+        int k = emit(OP_SIZE, d, 0, 0, 0, 0);
+        p_.code[k].ctl = (uint32_t)e->mem << CTL_MEM_SHIFT;
         return d;
       }
       case Ex::LOAD: {
-        int ri = gen(e->l.get(), -1);
+        Index ix;
+        int ri = gen_index(e->l.get(), ix);
         release(ri);
         int d = dst >= 0 ? dst : tmp();
-        emit(OP_LD, d, ri, 0, e->mem);
+        int k = emit(OP_LD, d, ri, 0, ix.c1, ix.c2);
+        p_.code[k].ctl = ix.ctl((uint32_t)e->mem);
         return d;
       }
       case Ex::UN: {
@@ -470,7 +572,14 @@ class Compiler {
           int ra = gen(e->l.get(), -1);
           release(ra);
           int d = dst >= 0 ? dst : tmp();
-          emit(iop, d, ra, 0, e->r->c);
+          int32_t c = e->r->c;
+          if (e->op == OP_SUB) c = (int32_t)(0u - (uint32_t)c);
+          uint32_t m = c < 0 ? 0u - (uint32_t)c : (uint32_t)c;  // |c| (2^31 for INT_MIN)
+          if (e->op == OP_MOD && m != 0 && (m & (m - 1)) == 0) {
+            emit(OP_ANDI, d, ra, 0, (int32_t)(m - 1));  // Euclidean a mod 2^k == a & (2^k - 1)
+          } else {
+            emit(iop, d, ra, 0, c);
+          }
           return d;
         }
         if (e->l->k == Ex::CONST && imm_form(e->op, iop, true)) {
@@ -479,6 +588,24 @@ class Compiler {
           int d = dst >= 0 ? dst : tmp();
           emit(iop, d, rb, 0, e->l->c);
           return d;
+        }
+        if (e->op == OP_ADD) {  // e1 * c + e2 and e2 + e1 * c: one multiply-add
+          const Ex *mul = nullptr, *other = nullptr;
+          bool mul_first = false;
+          if (is_mul_const(e->l.get())) { mul = e->l.get(); other = e->r.get(); mul_first = true; }
+          else if (is_mul_const(e->r.get())) { mul = e->r.get(); other = e->l.get(); }
+          if (mul) {
+            const Ex *factor = mul->r->k == Ex::CONST ? mul->l.get() : mul->r.get();
+            const int32_t c = mul->r->k == Ex::CONST ? mul->r->c : mul->l->c;
+            int rx, ry;
+            if (mul_first) { rx = gen(factor, -1); ry = gen(other, -1); }
+            else { ry = gen(other, -1); rx = gen(factor, -1); }
+            release(mul_first ? ry : rx);
+            release(mul_first ? rx : ry);
+            int d = dst >= 0 ? dst : tmp();
+            emit(OP_MADI, d, rx, ry, c);
+            return d;
+          }
         }
         int ra = gen(e->l.get(), -1);
         int rb = gen(e->r.get(), -1);
@@ -542,19 +669,17 @@ class Compiler {
       punct("(");
       ExP c = expr();
       punct(")");
-      int r = gen(c.get(), -1);
-      release(r);
-      int bz = emit(OP_BZ, 0, r, 0, 0);
+      int bz = branch_if_false(c.get());
       Bound ta, tw, ea, ew;
       body(ta, tw);
       if (at_word("else")) {
         i_++;
         int j = emit(OP_JMP, 0, 0, 0, 0);
-        p_.code[bz].imm = here();
+        p_.code[bz].imm2 = here();
         body(ea, ew);
-        p_.code[j].imm = here();
+        p_.code[j].imm2 = here();
       } else {
-        p_.code[bz].imm = here();
+        p_.code[bz].imm2 = here();
       }
       acc = seq(Bound::accesses(count_loads(c.get())), alt(ta, ea));
       wr = alt(tw, ew);
@@ -575,19 +700,16 @@ class Compiler {
       bool nhi = take("-");
       int32_t hi = (int32_t)(uint32_t)number();
       if (nhi) hi = (int32_t)(0u - (uint32_t)hi);
+      // v := lo; if !(v < hi) skip; body; v := v + 1; if (v < hi) repeat
       emit(OP_MOVI, reg, 0, 0, lo);
-      int head = here();
-      int t = tmp();
-      emit(OP_LTI, t, reg, 0, hi);
-      release(t);
-      int bz = emit(OP_BZ, 0, t, 0, 0);
+      int bz = emit(OP_BFLTI, 0, reg, 0, hi);
+      int body_pc = here();
       loops_.push_back(reg);
       Bound ba, bw;
       block(ba, bw);
       loops_.pop_back();
-      emit(OP_ADDI, reg, reg, 0, 1);
-      emit(OP_JMP, 0, 0, 0, head);
-      p_.code[bz].imm = here();
+      emit(OP_LOOP, reg, reg, 0, hi, body_pc);
+      p_.code[bz].imm2 = here();
       int64_t trips = std::max<int64_t>(0, (int64_t)hi - (int64_t)lo);
       acc = loop(ba, trips);
       wr = loop(bw, trips);
@@ -610,11 +732,13 @@ class Compiler {
       punct("=");
       ExP val = expr();
       punct(";");
-      int ri = gen(idx.get(), -1);
+      Index ix;
+      int ri = gen_index(idx.get(), ix);
       int rv = gen(val.get(), -1);
       release(rv);
       release(ri);
-      emit(OP_ST, 0, ri, rv, m->second);
+      int k = emit(OP_ST, 0, ri, rv, ix.c1, ix.c2);
+      p_.code[k].ctl = ix.ctl((uint32_t)m->second);
       acc = Bound::accesses(count_loads(idx.get()) + count_loads(val.get()) + 1);
       wr = Bound::accesses(1);
       return;
@@ -633,9 +757,78 @@ class Compiler {
 
 }  // namespace
 
+bool predecode(const Insn &in, uint32_t &ctl) {
+  enum : uint32_t { P0 = 0, P1 = 1u << AL_P_SHIFT, PM = 2u << AL_P_SHIFT, Q1 = 1u << AL_Q_SHIFT,
+                    QM = 2u << AL_Q_SHIFT, W = AL_WRITE, COND = 1u << AL_MODE_SHIFT,
+                    ALWAYS = 2u << AL_MODE_SHIFT };
+  const uint32_t LTc = AL_CMP | AL_LT, EQc = AL_CMP | AL_EQ, I = AL_INV, Y = AL_YIMM;
+  auto cls = [](CtlClass c, uint32_t extra = 0) { return extra | ((uint32_t)c << CTL_CLASS_SHIFT); };
+  switch (in.op) {
+    case OP_NOP: ctl = 0; return in.imm == 0;                       // arith = 0, not written
+    case OP_MOVI: ctl = W; return true;                              // C = imm
+    case OP_MOV: ctl = P1 | W; return in.imm == 0;                   // x
+    case OP_ADD: ctl = P1 | Q1 | W; return in.imm == 0;
+    case OP_SUB: ctl = P1 | QM | W; return in.imm == 0;
+    case OP_MUL: ctl = AL_M | W; return in.imm == 0;
+    case OP_ADDI: ctl = P1 | W; return true;                         // x + imm
+    case OP_MULI: ctl = AL_PIMM | W; return true;                    // imm * x
+    case OP_ANDI: ctl = P1 | AL_MASKIMM | W; return true;            // x & imm
+    case OP_RSUBI: ctl = PM | W; return true;                        // -x + imm
+    case OP_MADI: ctl = AL_PIMM | Q1 | W; return true;               // imm * x + yr
+    case OP_NEG: ctl = PM | W; return in.imm == 0;
+    case OP_LT: ctl = LTc | W; return true;
+    case OP_LE: ctl = LTc | AL_EQ | W; return true;
+    case OP_GT: ctl = LTc | AL_EQ | I | W; return true;
+    case OP_GE: ctl = LTc | I | W; return true;
+    case OP_EQ: ctl = EQc | W; return true;
+    case OP_NE: ctl = EQc | I | W; return true;
+    case OP_LTI: ctl = LTc | Y | W; return true;
+    case OP_LEI: ctl = LTc | AL_EQ | Y | W; return true;
+    case OP_GTI: ctl = LTc | AL_EQ | I | Y | W; return true;
+    case OP_GEI: ctl = LTc | I | Y | W; return true;
+    case OP_EQI: ctl = EQc | Y | W; return true;
+    case OP_NEI: ctl = EQc | I | Y | W; return true;
+    case OP_NOT: ctl = EQc | Y | W; return in.imm == 0;              // x == 0
+    case OP_JMP: ctl = ALWAYS; return true;
+    case OP_BZ: ctl = EQc | Y | COND; return in.imm == 0;             // taken if x == 0
+    case OP_BFLTI: ctl = LTc | I | Y | COND; return true;             // taken if !(x < imm)
+    case OP_BFLEI: ctl = LTc | AL_EQ | I | Y | COND; return true;     // taken if !(x <= imm)
+    case OP_BFGTI: ctl = LTc | AL_EQ | Y | COND; return true;         // taken if !(x > imm)
+    case OP_BFGEI: ctl = LTc | Y | COND; return true;                 // taken if !(x >= imm)
+    case OP_BFEQI: ctl = EQc | I | Y | COND; return true;             // taken if !(x == imm)
+    case OP_BFNEI: ctl = EQc | Y | COND; return true;                 // taken if !(x != imm)
+    case OP_LOOP: ctl = P1 | AL_CONE | W | COND | AL_LOOPCOND; return in.d == in.a;  // d = a + 1; taken if d < imm
+    case OP_LAND: ctl = cls(CC_LOGIC, 0); return true;
+    case OP_LOR: ctl = cls(CC_LOGIC, 1); return true;
+    case OP_DIV: ctl = cls(CC_DIVMOD, 0); return true;
+    case OP_MOD: ctl = cls(CC_DIVMOD, DM_MOD); return true;
+    case OP_DIVI: ctl = cls(CC_DIVMOD, DM_YIMM); return true;
+    case OP_MODI: ctl = cls(CC_DIVMOD, DM_MOD | DM_YIMM); return true;
+    case OP_SIZE: ctl = cls(CC_SIZE); return true;
+    case OP_LD: ctl = cls(CC_LD); return true;
+    case OP_ST: ctl = cls(CC_ST); return true;
+    case OP_ASSUME: ctl = cls(CC_ASSUME); return true;
+    case OP_ASSERT: ctl = cls(CC_ASSERT); return true;
+    case OP_BARRIER: ctl = cls(CC_BARRIER); return true;
+    case OP_EXIT: ctl = cls(CC_EXIT); return true;
+    default: return false;  // built-in opcodes are registers now; anything else is invalid
+  }
+}
+
+uint32_t operand_bits(const Insn &in) {
+  if (in.op == OP_LD || in.op == OP_ST) return CTL_AM | (0x1Fu << CTL_K_SHIFT) | (0xFFu << CTL_MEM_SHIFT);
+  if (in.op == OP_SIZE) return 0xFFu << CTL_MEM_SHIFT;
+  return 0;
+}
+
 Program compile_program(const std::string &src) {
   Compiler c(src);
   Program p = c.run();
+  for (Insn &in : p.code) {
+    uint32_t base = 0;
+    if (!predecode(in, base)) throw CompileError{"internal: cannot decode an emitted instruction"};
+    in.ctl = base | (in.ctl & operand_bits(in));
+  }
   std::string err = validate_program(p);
   if (!err.empty()) throw CompileError{"internal: " + err};
   return p;
@@ -644,21 +837,24 @@ Program compile_program(const std::string &src) {
 std::string validate_program(const Program &p) {
   if (p.code.empty() || p.code.back().op != OP_EXIT) return "program must end with EXIT";
   if (p.n_regs == 0 || p.n_regs > 255) return "bad register count";
+  if (p.code.size() > (1u << 20)) return "program longer than 2^20 instructions";
   const int n = (int)p.code.size();
   for (int k = 0; k < n; k++) {
     const Insn &in = p.code[k];
-    if (in.op >= OP_COUNT) return "bad opcode at " + std::to_string(k);
+    uint32_t ctl = 0;
+    if (in.op >= OP_COUNT || !predecode(in, ctl)) return "bad opcode at " + std::to_string(k);
+    if (ctl != (in.ctl & ~operand_bits(in))) return "bad control word at " + std::to_string(k);
+    const bool uses_mem = in.op == OP_LD || in.op == OP_ST || in.op == OP_SIZE;
+    if (uses_mem && (in.ctl >> CTL_MEM_SHIFT) >= p.mems.size()) return "bad memory id at " + std::to_string(k);
     if (in.d >= p.n_regs || in.a >= p.n_regs || in.b >= p.n_regs) return "bad register at " + std::to_string(k);
     switch (in.op) {
       case OP_JMP:
       case OP_BZ:
-        if (in.imm < 0 || in.imm >= n) return "bad jump target at " + std::to_string(k);
+      case OP_BFLTI: case OP_BFLEI: case OP_BFGTI: case OP_BFGEI: case OP_BFEQI: case OP_BFNEI:
+      case OP_LOOP:
+        if (in.imm2 < 0 || in.imm2 >= n) return "bad jump target at " + std::to_string(k);
         break;
-      case OP_LD:
-      case OP_ST:
-      case OP_SIZE:
-        if (in.imm < 0 || in.imm >= (int32_t)p.mems.size()) return "bad memory id at " + std::to_string(k);
-        break;
+
       case OP_BARRIER:
         if (in.imm < 0 || (uint32_t)in.imm >= p.n_barriers) return "bad barrier id at " + std::to_string(k);
         break;
@@ -669,6 +865,7 @@ std::string validate_program(const Program &p) {
         break;
     }
   }
+  if (p.mems.size() > 256) return "more than 256 memory objects";
   for (const MemDecl &m : p.mems) {
     if (m.space > 1) return "bad memory space";
     if (m.space == 1 && (m.decl_len < 0 || m.decl_len > (1 << 24))) return "bad local length";

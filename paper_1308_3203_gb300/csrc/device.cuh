@@ -51,11 +51,13 @@ struct InterpArgs {
   const int32_t *snap;     // committed memory, indexed by key
   int32_t *regs;           // [n_regs][N] registers of every work-item
   uint32_t *pc, *st;       // [N]
-  uint2 *ow;               // own-write table [capw][ow_stride] (key, value)
-  uint32_t capw, ow_stride;
-  LogRec *log;
-  unsigned long long *log_count;
-  unsigned long long log_cap;
+  uint2 *ow;               // own-write table [capw][ow_stride] (key, value); entries
+  uint32_t capw, ow_stride; // below ow_slots live in shared memory during the run
+  uint32_t ow_slots;
+  LogRec *log;                    // one slice of warp_slice records per warp
+  uint32_t *warp_count;           // [n_cta * warps_per_cta] records each warp logged
+  uint32_t warps_per_cta;
+  unsigned long long warp_slice;  // 32 * (static bound of accesses per interval)
   OutRec *errs;
   uint32_t *err_count;
   uint32_t err_cap;
@@ -63,53 +65,61 @@ struct InterpArgs {
   unsigned long long *acc;        // [0] global accesses, [1] local accesses
   uint32_t *flags;                // bit 0 log full, bit 1 own-write table full, bit 2 error log full
   uint32_t *ow_count;             // [N] own-write entries per work-item
-  unsigned long long *owner;      // shadow owner table (nullptr: not used)
-  uint32_t epoch;
+  uint32_t *owner;                // shadow owner table (nullptr: not used)
+  uint32_t tag;
 };
 
 // ---- shadow owner table (shadow.cu)
-// Two 64-bit words per cell: [2*key] = writer, [2*key+1] = reader.  A word
-// holds (epoch << 32 | gtid) of the only work-item that wrote (read) the cell
-// in the current interval, (epoch << 32 | kNone) once two or more did, and
-// anything with an older epoch means "nobody yet".
-__device__ __forceinline__ void shadow_claim(unsigned long long *p, uint32_t epoch, uint32_t gtid) {
-  const unsigned long long mine = ((unsigned long long)epoch << 32) | gtid;
-  const unsigned long long shared = ((unsigned long long)epoch << 32) | 0xFFFFFFFFull;
-  unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(p);
-  for (int it = 0; it < 4; it++) {
-    if ((uint32_t)(cur >> 32) != epoch) {
-      const unsigned long long prev = atomicCAS(p, cur, mine);
-      if (prev == cur) return;
-      cur = prev;
-      continue;
-    }
-    if ((uint32_t)cur == gtid || (uint32_t)cur == 0xFFFFFFFFu) return;
-    break;
-  }
-  atomicExch(p, shared);
+// Four 32-bit words per cell: [4k] max writer, [4k+1] min writer, [4k+2] max
+// reader, [4k+3] min reader.  A word holds (tag << 26 | id) where id is the
+// work-item (max words) or kIdMask - work-item (min words), so atomicMax
+// keeps the largest / smallest work-item of the current interval.  The tag
+// (1..63) grows every interval, so any word with an older tag counts as
+// empty; the table is cleared when the tag wraps.  Claims are fire-and-forget
+// reductions: no round trip on the interpreter's critical path.
+constexpr uint32_t kIdMask = (1u << 26) - 1;
+__device__ __forceinline__ void shadow_claim(uint32_t *owner, uint32_t key, bool write, uint32_t tag,
+                                             uint32_t gtid) {
+  uint32_t *w = owner + 4ull * key + (write ? 0 : 2);
+  atomicMax(w, (tag << 26) | gtid);
+  atomicMax(w + 1, (tag << 26) | (kIdMask - gtid));
 }
 
 // Cells that need the exact (sorted) classification: written by two or more
 // work-items, or written by one and read by another.
-__device__ __forceinline__ bool shadow_needs_exact(const unsigned long long *owner, uint32_t key, uint32_t epoch) {
-  const unsigned long long w = owner[2ull * key], r = owner[2ull * key + 1];
-  if ((uint32_t)(w >> 32) != epoch) return false;
-  const uint32_t wg = (uint32_t)w;
-  if (wg == 0xFFFFFFFFu) return true;
-  if ((uint32_t)(r >> 32) != epoch) return false;
-  return (uint32_t)r != wg;
+__device__ __forceinline__ bool shadow_needs_exact(const uint32_t *owner, uint32_t key, uint32_t tag) {
+  const uint4 o = reinterpret_cast<const uint4 *>(owner)[key];
+  if ((o.x >> 26) != tag) return false;  // nobody wrote the cell
+  const uint32_t wmax = o.x & kIdMask, wmin = kIdMask - (o.y & kIdMask);
+  if (wmax != wmin) return true;
+  if ((o.z >> 26) != tag) return false;  // one writer, no reader
+  const uint32_t rmax = o.z & kIdMask, rmin = kIdMask - (o.w & kIdMask);
+  return rmax != wmax || rmin != wmax;
 }
 
-void launch_shadow_compact(const LogRec *log, uint64_t n, const unsigned long long *owner, uint32_t epoch,
-                           LogRec *out, unsigned long long *count, cudaStream_t s);
+// log: n_slices warp slices of `slice` records, count[i] valid in slice i
+void launch_shadow_compact(const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
+                           const uint32_t *owner, uint32_t tag, LogRec *out, unsigned long long *total,
+                           cudaStream_t s);
 void launch_shadow_commit(const uint2 *ow, const uint32_t *ow_count, uint64_t N, uint32_t ow_stride,
-                          const unsigned long long *owner, uint32_t epoch, int32_t *snap, cudaStream_t s);
+                          const uint32_t *owner, uint32_t tag, int32_t *snap, cudaStream_t s);
+// copy the used part of every slice into one dense array (offs = exclusive scan of count)
+void launch_densify(const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
+                    const uint32_t *offs, LogRec *out, cudaStream_t s);
+
+// Kernels launched by the library since load (every launch site adds one).
+void count_launch();
 
 enum Flag : uint32_t { FLAG_LOG_FULL = 1, FLAG_OW_FULL = 2, FLAG_ERR_FULL = 4 };
 
 void launch_interp(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStream_t s);
-size_t interp_smem_bytes(uint32_t n_insn, uint32_t n_mems, uint32_t n_regs, uint32_t S);
+size_t interp_smem_bytes(uint32_t n_mems, uint32_t n_regs, uint32_t S, uint32_t ow_slots);
 cudaError_t interp_configure();
+constexpr uint32_t kConstCodeInsns = 4000;  // programs up to this size run from constant memory
+// copy bytecode to constant memory (no-op for larger programs); stream-ordered
+cudaError_t interp_upload_code(const Insn *host_code, uint32_t n_insn, cudaStream_t s);
+constexpr size_t kMaxSmemPerBlock = 227 * 1024;  // opt-in shared memory per CTA on sm_103
+size_t interp_max_dynamic_smem();  // valid after interp_configure()
 
 // ---- scan / sort (sort.cu)
 // exclusive prefix sum of n uint32 values; tmp must hold scan_tmp_words(n)

@@ -21,34 +21,22 @@ namespace cg = cooperative_groups;
 namespace rc {
 namespace {
 
-__device__ __forceinline__ int32_t idiv(int32_t a, int32_t b) {
+__device__ __forceinline__ int32_t idiv(int32_t a, int32_t b) {  // truncating; x / 0 = 0
   if (b == 0) return 0;
   if (a == INT32_MIN && b == -1) return INT32_MIN;  // 2^31 wraps
   return a / b;
 }
-__device__ __forceinline__ int32_t imod(int32_t a, int32_t b) {  // Euclidean, in [0, |b|)
+__device__ __forceinline__ int32_t imod(int32_t a, int32_t b) {  // Euclidean, in [0, |b|); x % 0 = 0
   if (b == 0) return 0;
-  int64_t m = b < 0 ? -(int64_t)b : (int64_t)b;
-  int64_t r = (int64_t)a % m;
-  if (r < 0) r += m;
-  return (int32_t)r;
+  const uint32_t m = b < 0 ? 0u - (uint32_t)b : (uint32_t)b;
+  if ((int32_t)m > 0) {
+    const int32_t r = a % (int32_t)m;
+    return r < 0 ? r + (int32_t)m : r;
+  }
+  return a & 0x7FFFFFFF;  // |b| = 2^31
 }
 __device__ __forceinline__ uint64_t bloom_bit(uint32_t key) {
   return 1ull << ((key * 2654435761u) >> 26);
-}
-
-__device__ __forceinline__ void append_log(const InterpArgs &A, uint32_t key, uint32_t tw, int32_t v,
-                                           uint32_t seq) {
-  cg::coalesced_group g = cg::coalesced_threads();
-  unsigned long long base = 0;
-  if (g.thread_rank() == 0) base = atomicAdd(A.log_count, (unsigned long long)g.size());
-  base = g.shfl(base, 0);
-  unsigned long long pos = base + g.thread_rank();
-  if (pos < A.log_cap) {
-    reinterpret_cast<uint4 *>(A.log)[pos] = make_uint4(key, tw, (uint32_t)v, seq);
-  } else {
-    atomicOr(A.flags, FLAG_LOG_FULL);
-  }
 }
 
 __device__ __forceinline__ void append_err(const InterpArgs &A, const OutRec &r) {
@@ -57,21 +45,29 @@ __device__ __forceinline__ void append_err(const InterpArgs &A, const OutRec &r)
   else atomicOr(A.flags, FLAG_ERR_FULL);
 }
 
-__global__ void __launch_bounds__(1024) interp_kernel(InterpArgs A) {
+// Bytecode of the instance being checked when it fits (the warp fetches
+// one instruction per step at a warp-uniform address: the constant cache's
+// broadcast case).  Larger programs are read from global memory.
+__constant__ uint4 c_code[kConstCodeInsns];
+
+template <bool kConst>
+__global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint2 *code = reinterpret_cast<uint2 *>(smem);
-  MemInfo *mems = reinterpret_cast<MemInfo *>(code + A.n_insn);
-  int32_t *rf = reinterpret_cast<int32_t *>(mems + A.n_mems);
+  const uint4 *__restrict__ code = reinterpret_cast<const uint4 *>(A.code);
+  MemInfo *mems = reinterpret_cast<MemInfo *>(smem);
+  int32_t *rf = reinterpret_cast<int32_t *>(mems + A.n_mems);  // [n_regs][S]
+  uint32_t *owk = reinterpret_cast<uint32_t *>(rf + A.n_regs * A.S);  // [ow_slots][S] keys
+  int32_t *owv = reinterpret_cast<int32_t *>(owk + A.ow_slots * A.S);  // [ow_slots][S] values
 
   const uint32_t S = A.S;
   const uint32_t tid = threadIdx.x;
-  for (uint32_t k = tid; k < A.n_insn; k += blockDim.x) code[k] = reinterpret_cast<const uint2 *>(A.code)[k];
   for (uint32_t k = tid; k < A.n_mems; k += blockDim.x) mems[k] = A.mems[k];
 
   const uint32_t wg = A.group0 + blockIdx.x;
   const uint32_t gtid = wg * S + tid;
   const uint64_t N = (uint64_t)A.G * S;
   const uint32_t lt = gtid - A.group0 * S;  // index in this launch's own-write table
+  const uint32_t slots = A.ow_slots;
   uint32_t st = A.st[gtid];
   uint32_t pc = A.pc[gtid];
   if (st == TS_BARRIER) {  // resume after the barrier it waited at
@@ -79,161 +75,235 @@ __global__ void __launch_bounds__(1024) interp_kernel(InterpArgs A) {
     pc += 1;
   }
   if (st == TS_RUN) {
-    for (uint32_t r = 0; r < A.n_regs; r++) rf[r * S + tid] = A.regs[(uint64_t)r * N + gtid];
+    for (uint32_t r = kBuiltinRegs; r < A.n_regs; r++) rf[r * S + tid] = A.regs[(uint64_t)r * N + gtid];
+    rf[REG_TID * S + tid] = (int32_t)tid;
+    rf[REG_WG * S + tid] = (int32_t)wg;
+    rf[REG_GTID * S + tid] = (int32_t)gtid;
+    rf[REG_GSIZE * S + tid] = (int32_t)S;
+    rf[REG_NGROUPS * S + tid] = (int32_t)A.G;
   }
   __syncthreads();
 
 #define REG(i) rf[(uint32_t)(i) * S + tid]
-  uint32_t nglob = 0, nloc = 0, seq = 0, nw = 0, stop = kNone;
+  uint32_t nloc = 0, seq = 0, nw = 0;  // global accesses = seq - nloc
   uint64_t bloom = 0;
   const uint32_t lbase = A.GT + wg * A.LT;
+  const bool ran = st == TS_RUN;
+  bool running = ran;
+  const uint32_t wbase = tid & ~31u;
+  const uint32_t lanes = S - wbase >= 32 ? 0xFFFFFFFFu : ((1u << (S - wbase)) - 1u);
 
-  if (st == TS_RUN) {
-    for (;;) {
-      const uint2 raw = code[pc];
-      const uint32_t op = raw.x & 0xFFu, d = (raw.x >> 8) & 0xFFu, ra = (raw.x >> 16) & 0xFFu,
-                     rb = raw.x >> 24;
-      const int32_t imm = (int32_t)raw.y;
-      pc++;
-      switch (op) {
-        case OP_NOP: break;
-        case OP_MOVI: REG(d) = imm; break;
-        case OP_MOV: REG(d) = REG(ra); break;
-        case OP_ADD: REG(d) = (int32_t)((uint32_t)REG(ra) + (uint32_t)REG(rb)); break;
-        case OP_SUB: REG(d) = (int32_t)((uint32_t)REG(ra) - (uint32_t)REG(rb)); break;
-        case OP_MUL: REG(d) = (int32_t)((uint32_t)REG(ra) * (uint32_t)REG(rb)); break;
-        case OP_DIV: REG(d) = idiv(REG(ra), REG(rb)); break;
-        case OP_MOD: REG(d) = imod(REG(ra), REG(rb)); break;
-        case OP_ADDI: REG(d) = (int32_t)((uint32_t)REG(ra) + (uint32_t)imm); break;
-        case OP_SUBI: REG(d) = (int32_t)((uint32_t)REG(ra) - (uint32_t)imm); break;
-        case OP_MULI: REG(d) = (int32_t)((uint32_t)REG(ra) * (uint32_t)imm); break;
-        case OP_DIVI: REG(d) = idiv(REG(ra), imm); break;
-        case OP_MODI: REG(d) = imod(REG(ra), imm); break;
-        case OP_RSUBI: REG(d) = (int32_t)((uint32_t)imm - (uint32_t)REG(ra)); break;
-        case OP_LT: REG(d) = REG(ra) < REG(rb); break;
-        case OP_LE: REG(d) = REG(ra) <= REG(rb); break;
-        case OP_GT: REG(d) = REG(ra) > REG(rb); break;
-        case OP_GE: REG(d) = REG(ra) >= REG(rb); break;
-        case OP_EQ: REG(d) = REG(ra) == REG(rb); break;
-        case OP_NE: REG(d) = REG(ra) != REG(rb); break;
-        case OP_LTI: REG(d) = REG(ra) < imm; break;
-        case OP_LEI: REG(d) = REG(ra) <= imm; break;
-        case OP_GTI: REG(d) = REG(ra) > imm; break;
-        case OP_GEI: REG(d) = REG(ra) >= imm; break;
-        case OP_EQI: REG(d) = REG(ra) == imm; break;
-        case OP_NEI: REG(d) = REG(ra) != imm; break;
-        case OP_LAND: REG(d) = (REG(ra) != 0) && (REG(rb) != 0); break;
-        case OP_LOR: REG(d) = (REG(ra) != 0) || (REG(rb) != 0); break;
-        case OP_NEG: REG(d) = (int32_t)(0u - (uint32_t)REG(ra)); break;
-        case OP_NOT: REG(d) = REG(ra) == 0; break;
-        case OP_TID: REG(d) = (int32_t)tid; break;
-        case OP_WG: REG(d) = (int32_t)wg; break;
-        case OP_GTID: REG(d) = (int32_t)gtid; break;
-        case OP_GSIZE: REG(d) = (int32_t)S; break;
-        case OP_NGROUPS: REG(d) = (int32_t)A.G; break;
-        case OP_SIZE: REG(d) = (int32_t)mems[imm].len; break;
-        case OP_JMP: pc = (uint32_t)imm; break;
-        case OP_BZ: if (REG(ra) == 0) pc = (uint32_t)imm; break;
-        case OP_LD:
-        case OP_ST: {
-          const MemInfo m = mems[imm];
-          const int32_t idx = REG(ra);
-          if ((uint32_t)idx >= m.len) {  // ⊥: out of bounds, the work-item stops
-            OutRec e{A.interval, m.space, m.space ? wg : 0u, (uint32_t)idx, CLS_OOB, gtid, (uint32_t)imm, 0, 0, 0};
-            append_err(A, e);
-            st = TS_DEAD;
-            goto done;
-          }
-          const uint32_t key = (m.space ? lbase : 0u) + m.base + (uint32_t)idx;
-          const uint64_t bit = bloom_bit(key);
-          int32_t slot = -1;
-          if (bloom & bit) {
-            for (int32_t k = (int32_t)nw - 1; k >= 0; k--) {
-              if (A.ow[(uint64_t)k * A.ow_stride + lt].x == key) { slot = k; break; }
-            }
-          }
-          if (A.owner) shadow_claim(A.owner + 2ull * key + (op == OP_LD ? 1 : 0), A.epoch, gtid);
-          if (op == OP_LD) {
-            const int32_t v = slot >= 0 ? (int32_t)A.ow[(uint64_t)slot * A.ow_stride + lt].y : A.snap[key];
-            REG(d) = v;
-            append_log(A, key, gtid, v, seq++);
-          } else {
-            const int32_t v = REG(rb);
-            if (slot >= 0) {
-              A.ow[(uint64_t)slot * A.ow_stride + lt].y = (uint32_t)v;
-            } else if (nw < A.capw) {
-              A.ow[(uint64_t)nw * A.ow_stride + lt] = make_uint2(key, (uint32_t)v);
-              nw++;
-              bloom |= bit;
-            } else {
-              atomicOr(A.flags, FLAG_OW_FULL);
-            }
-            append_log(A, key, gtid | 0x80000000u, v, seq++);
-          }
-          if (m.space) nloc++;
-          else nglob++;
-          break;
-        }
-        case OP_ASSUME:
-          if (REG(ra) == 0) { st = TS_DEAD; goto done; }  // ⊤: no continuation
-          break;
-        case OP_ASSERT:
-          if (REG(ra) == 0) {  // ⊥
-            OutRec e{A.interval, 0, 0, 0, CLS_ASSERT, gtid, (uint32_t)imm, 0, 0, 0};
-            append_err(A, e);
-            st = TS_DEAD;
-            goto done;
-          }
-          break;
-        case OP_BARRIER:
-          st = TS_BARRIER;
-          stop = (uint32_t)imm;
-          pc -= 1;  // remember the barrier itself
-          goto done;
-        case OP_EXIT:
-        default:
-          st = TS_EXIT;
-          stop = A.n_barriers;
-          pc -= 1;
-          goto done;
+  // Min-PC reconvergence: every iteration the warp executes the instruction
+  // at the smallest bytecode pc among its running lanes; lanes that are
+  // ahead (past a branch or a loop the others are still in) wait at their
+  // pc, so lanes that followed different paths meet again at the join point.
+  // The instruction is fetched and decoded once for the warp and every lane
+  // takes the same dispatch branch; only the side effects are predicated on
+  // the lane being at that pc.
+  // Each warp appends to its own log slice: the ballot of the lanes that
+  // log in a step gives every lane its slot, and the slice fill level is a
+  // warp-uniform register (no atomics).
+  const uint32_t warp = tid >> 5, lane_lt = (1u << (tid & 31u)) - 1u;
+  uint4 *const wlog = reinterpret_cast<uint4 *>(A.log) +
+                      ((uint64_t)blockIdx.x * A.warps_per_cta + warp) * A.warp_slice;
+  uint32_t wfill = 0;
+
+  for (;;) {
+    const uint32_t minpc = __reduce_min_sync(lanes, running ? pc : kNone);
+    if (minpc == kNone) break;
+    const uint4 raw = kConst ? c_code[minpc] : __ldg(code + minpc);
+    const bool act = running && pc == minpc;
+    const uint32_t d = (raw.x >> 8) & 0xFFu, ra = (raw.x >> 16) & 0xFFu, rb = raw.x >> 24;
+    const int32_t imm = (int32_t)raw.y;
+    const uint32_t tgt = raw.z, ctl = raw.w;
+    const uint32_t cls = (ctl >> CTL_CLASS_SHIFT) & 0xFu;
+    const int32_t x = REG(ra);
+    const int32_t yr = REG(rb);
+    if (cls == CC_ALU) {  // arithmetic, moves, comparisons, branches: one branch-free formula
+      const uint32_t pcode = (ctl >> AL_P_SHIFT) & 3u, qcode = (ctl >> AL_Q_SHIFT) & 3u;
+      const uint32_t P = (ctl & AL_PIMM) ? (uint32_t)imm : (pcode & 1u) - (pcode >> 1);
+      const uint32_t Q = (qcode & 1u) - (qcode >> 1);
+      const uint32_t C = (ctl & AL_CONE) ? 1u : (ctl & (AL_PIMM | AL_MASKIMM)) ? 0u : (uint32_t)imm;
+      const uint32_t M = (ctl & AL_M) ? (uint32_t)yr : 0u;
+      const uint32_t mask = (ctl & AL_MASKIMM) ? (uint32_t)imm : 0xFFFFFFFFu;
+      const uint32_t ux = (uint32_t)x;
+      const int32_t arith = (int32_t)((ux * M + ux * P + (uint32_t)yr * Q + C) & mask);
+      const int32_t y = (ctl & AL_YIMM) ? imm : yr;
+      const bool c = (((x < y) && (ctl & AL_LT)) || ((x == y) && (ctl & AL_EQ))) != ((ctl & AL_INV) != 0);
+      const int32_t r = (ctl & AL_CMP) ? (int32_t)c : arith;
+      const bool cond = (ctl & AL_LOOPCOND) ? (arith < imm) : c;
+      const uint32_t mode = (ctl >> AL_MODE_SHIFT) & 3u;
+      const bool take = mode == 2u || (mode == 1u && cond);
+      if (act) {
+        if (ctl & AL_WRITE) REG(d) = r;
+        pc = take ? tgt : pc + 1;
       }
+      continue;
+    }
+    if (cls == CC_LD || cls == CC_ST) {
+      const MemInfo m = mems[ctl >> CTL_MEM_SHIFT];  // (LD/ST class: operand bits)
+      uint32_t ui = (uint32_t)x + (uint32_t)imm;
+      if (ctl & CTL_AM) ui &= ((2u << ((ctl >> CTL_K_SHIFT) & 0x1Fu)) - 1u) >> 1;  // 2^k - 1
+      const int32_t idx = (int32_t)(ui + (uint32_t)tgt);
+      const bool inb = (uint32_t)idx < m.len;
+      const uint32_t logging = __ballot_sync(lanes, act && inb);
+      const uint32_t slot_pos = wfill + __popc(logging & lane_lt);
+      wfill += __popc(logging);
+      if (!act) continue;
+      pc++;
+      if (!inb) {  // ⊥: out of bounds, the work-item stops
+        OutRec e{A.interval, m.space, m.space ? wg : 0u, (uint32_t)idx, CLS_OOB, gtid,
+                 ctl >> CTL_MEM_SHIFT, 0, 0, 0};
+        append_err(A, e);
+        st = TS_DEAD;
+        running = false;
+        continue;
+      }
+      const uint32_t key = (m.space ? lbase : 0u) + m.base + (uint32_t)idx;
+      // own-write table: the first `slots` distinct cells in shared memory, the rest in global
+      const uint64_t bit = bloom_bit(key);
+      int32_t slot = -1;
+      if (bloom & bit) {
+        const uint32_t ns = nw < slots ? nw : slots;
+        for (uint32_t k = 0; k < ns; k++)
+          if (owk[k * S + tid] == key) { slot = (int32_t)k; break; }
+        if (slot < 0)
+          for (uint32_t k = slots; k < nw; k++)
+            if (A.ow[(uint64_t)k * A.ow_stride + lt].x == key) { slot = (int32_t)k; break; }
+      }
+      if (A.owner) shadow_claim(A.owner, key, cls == CC_ST, A.tag, gtid);
+      int32_t v;
+      if (cls == CC_LD) {
+        if (slot < 0) v = __ldg(A.snap + key);
+        else if ((uint32_t)slot < slots) v = owv[slot * S + tid];
+        else v = (int32_t)A.ow[(uint64_t)slot * A.ow_stride + lt].y;
+        REG(d) = v;
+      } else {
+        v = yr;
+        if (slot >= 0) {
+          if ((uint32_t)slot < slots) owv[slot * S + tid] = v;
+          else A.ow[(uint64_t)slot * A.ow_stride + lt].y = (uint32_t)v;
+        } else if (nw < slots) {
+          owk[nw * S + tid] = key;
+          owv[nw * S + tid] = v;
+          nw++;
+          bloom |= bit;
+        } else if (nw < A.capw) {
+          A.ow[(uint64_t)nw * A.ow_stride + lt] = make_uint2(key, (uint32_t)v);
+          nw++;
+          bloom |= bit;
+        } else {
+          atomicOr(A.flags, FLAG_OW_FULL);
+        }
+      }
+      if (slot_pos < A.warp_slice)  // always true: the slice holds the static per-interval bound
+        wlog[slot_pos] = make_uint4(key, gtid | (cls == CC_ST ? 0x80000000u : 0u), (uint32_t)v, seq);
+      else
+        atomicOr(A.flags, FLAG_LOG_FULL);
+      seq++;
+      nloc += m.space;
+      continue;
+    }
+    if (!act) continue;
+    pc++;
+    switch (cls) {
+      case CC_DIVMOD: {
+        const int32_t y = (ctl & DM_YIMM) ? imm : yr;
+        REG(d) = (ctl & DM_MOD) ? imod(x, y) : idiv(x, y);
+        break;
+      }
+      case CC_LOGIC:  // (x != 0) and / or (yr != 0)
+        REG(d) = (ctl & 1u) ? ((x != 0) || (yr != 0)) : ((x != 0) && (yr != 0));
+        break;
+      case CC_SIZE:
+        REG(d) = (int32_t)mems[ctl >> CTL_MEM_SHIFT].len;
+        break;
+      case CC_ASSUME:
+        if (x == 0) {  // ⊤: no continuation
+          st = TS_DEAD;
+          running = false;
+        }
+        break;
+      case CC_ASSERT:
+        if (x == 0) {  // ⊥
+          OutRec e{A.interval, 0, 0, 0, CLS_ASSERT, gtid, (uint32_t)imm, 0, 0, 0};
+          append_err(A, e);
+          st = TS_DEAD;
+          running = false;
+        }
+        break;
+      case CC_BARRIER:
+        st = TS_BARRIER;
+        pc -= 1;  // remember the barrier itself
+        running = false;
+        break;
+      default:  // CC_EXIT
+        st = TS_EXIT;
+        pc -= 1;
+        running = false;
+        break;
     }
   }
-done:
 #undef REG
-  if (stop != kNone) {
+  if (st == TS_BARRIER || (st == TS_EXIT && ran)) {
+    // stop point: barrier ordinal, or n_barriers for the exit
+    const uint32_t stop = st == TS_BARRIER ? (uint32_t)(kConst ? c_code[pc].y : __ldg(code + pc).y) : A.n_barriers;
     atomicMin(&A.stop_min[stop], gtid);
     atomicAdd(&A.stop_cnt[stop], 1u);
   }
   A.st[gtid] = st;
   A.pc[gtid] = pc;
   A.ow_count[gtid] = nw;
+  {  // spill the shared-memory own-write slots so the commit kernel sees every entry
+    const uint32_t ns = nw < slots ? nw : slots;
+    for (uint32_t k = 0; k < ns; k++)
+      A.ow[(uint64_t)k * A.ow_stride + lt] = make_uint2(owk[k * S + tid], (uint32_t)owv[k * S + tid]);
+  }
   if (st == TS_BARRIER) {
-    for (uint32_t r = 0; r < A.n_regs; r++) A.regs[(uint64_t)r * N + gtid] = rf[r * S + tid];
+    for (uint32_t r = kBuiltinRegs; r < A.n_regs; r++) A.regs[(uint64_t)r * N + gtid] = rf[r * S + tid];
   }
   // access counters: one atomic per warp
-  const uint32_t wbase = tid & ~31u;
-  const uint32_t live = S - wbase >= 32 ? 0xFFFFFFFFu : ((1u << (S - wbase)) - 1u);
-  __syncwarp(live);
-  const uint32_t sg = __reduce_add_sync(live, nglob), sl = __reduce_add_sync(live, nloc);
+  __syncwarp(lanes);
+  const uint32_t sg = __reduce_add_sync(lanes, seq - nloc), sl = __reduce_add_sync(lanes, nloc);
   if ((tid & 31u) == 0) {
     if (sg) atomicAdd(&A.acc[0], (unsigned long long)sg);
     if (sl) atomicAdd(&A.acc[1], (unsigned long long)sl);
   }
+  if ((tid & 31u) == 0)
+    A.warp_count[(uint64_t)blockIdx.x * A.warps_per_cta + warp] = wfill < A.warp_slice ? wfill : (uint32_t)A.warp_slice;
 }
 
 }  // namespace
 
-size_t interp_smem_bytes(uint32_t n_insn, uint32_t n_mems, uint32_t n_regs, uint32_t S) {
-  return (size_t)n_insn * 8 + (size_t)n_mems * sizeof(MemInfo) + (size_t)n_regs * S * 4;
+size_t interp_smem_bytes(uint32_t n_mems, uint32_t n_regs, uint32_t S, uint32_t ow_slots) {
+  return (size_t)n_mems * sizeof(MemInfo) + (size_t)n_regs * S * 4 + (size_t)ow_slots * S * 8;
 }
 
+size_t g_interp_static_smem = 0;
+
 cudaError_t interp_configure() {
-  return cudaFuncSetAttribute(interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncAttributes fa, fb;
+  cudaError_t e = cudaFuncGetAttributes(&fa, interp_kernel<true>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fb, interp_kernel<false>);
+  if (e != cudaSuccess) return e;
+  g_interp_static_smem = fa.sharedSizeBytes > fb.sharedSizeBytes ? fa.sharedSizeBytes : fb.sharedSizeBytes;
+  const int dyn = (int)(kMaxSmemPerBlock - g_interp_static_smem);
+  e = cudaFuncSetAttribute(interp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(interp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  return e;
+}
+
+size_t interp_max_dynamic_smem() { return kMaxSmemPerBlock - g_interp_static_smem; }
+
+cudaError_t interp_upload_code(const Insn *host_code, uint32_t n_insn, cudaStream_t s) {
+  if (n_insn > kConstCodeInsns) return cudaSuccess;
+  return cudaMemcpyToSymbolAsync(c_code, host_code, (size_t)n_insn * sizeof(Insn), 0, cudaMemcpyHostToDevice, s);
 }
 
 void launch_interp(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStream_t s) {
-  interp_kernel<<<n_groups, a.S, smem, s>>>(a);
+  count_launch();
+  if (a.n_insn <= kConstCodeInsns) interp_kernel<true><<<n_groups, a.S, smem, s>>>(a);
+  else interp_kernel<false><<<n_groups, a.S, smem, s>>>(a);
 }
 
 }  // namespace rc

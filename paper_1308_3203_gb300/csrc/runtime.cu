@@ -13,13 +13,14 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
 #include <vector>
 
-#include "../../include/racecheck.h"
+#include "racecheck.h"
 #include "device.cuh"
 
 struct rc_bytecode {
@@ -30,6 +31,7 @@ namespace rc {
 namespace {
 
 thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
 std::mutex g_mu;
 int g_strategy = 0;
 
@@ -94,14 +96,14 @@ struct HostBuf {
 
 struct Workspace {
   DevBuf code, mems, snap, regs, pc, st, ow, loga, logb, head, runidx, sum, khead, keyidx, nrec,
-      recoff, out, scan, errs, stats, owner, owcnt, compact;
+      recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff;
   HostBuf hstats, hrecs;
   bool configured = false;
   uint32_t epoch = 0;
   void release_all() {
     for (DevBuf *b : {&code, &mems, &snap, &regs, &pc, &st, &ow, &loga, &logb, &head, &runidx, &sum,
                       &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
-                      &owcnt, &compact})
+                      &owcnt, &compact, &ctacnt, &ctaoff})
       b->release();
     epoch = 0;
   }
@@ -213,23 +215,31 @@ void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t inter
   CK(cudaStreamSynchronize(s));
 }
 
-// Sort path: the whole interval log is sorted and classified.
-void classify_sorted(Workspace &W, LogRec *log, uint64_t n, uint64_t keys, uint64_t N, uint32_t interval,
-                     const Layout &L, int32_t *snap, uint32_t *hstats, std::vector<OutRec> &races,
-                     cudaStream_t s) {
+// Sort path: the whole interval log is made dense, sorted and classified.
+void classify_sorted(Workspace &W, LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
+                     uint64_t keys, uint64_t N, uint32_t interval, const Layout &L, int32_t *snap,
+                     uint32_t *hstats, std::vector<OutRec> &races, cudaStream_t s) {
+  uint32_t *offs = W.ctaoff.get<uint32_t>(n_slices);
+  uint32_t *tmp = W.scan.get<uint32_t>(scan_tmp_words(n_slices));
+  scan_exclusive(count, offs, n_slices, tmp, s);
+  CK(cudaMemcpyAsync(hstats, offs + n_slices - 1, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hstats + 1, count + n_slices - 1, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const uint64_t n = (uint64_t)hstats[0] + hstats[1];
   if (n == 0) return;
-  uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(n), scan_tmp_words(n)));
-  LogRec *other = W.logb.get<LogRec>(n);
-  LogRec *sorted = sort_log(log, other, n, bitwidth(N), bitwidth(keys) + bitwidth(N), tmp, s);
+  LogRec *dense = W.logb.get<LogRec>(n);
+  launch_densify(log, n_slices, slice, count, offs, dense, s);
+  tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(n), scan_tmp_words(n)));
+  LogRec *sorted = sort_log(dense, log, n, bitwidth(N), bitwidth(keys) + bitwidth(N), tmp, s);
   classify_run(W, sorted, n, interval, L, snap, hstats, races, s);
 }
 
-// Owner table of 2 words per cell; entries tagged with an older epoch count
-// as empty, so the table is cleared only when it is (re)allocated or the
-// epoch counter wraps.
-unsigned long long *shadow_table(Workspace &W, uint64_t keys, cudaStream_t s) {
+// Owner table of 4 words per cell (see shadow_claim); words tagged with an
+// older tag count as empty, so the table is cleared only when it is
+// (re)allocated or the 6-bit tag wraps.
+uint32_t *shadow_table(Workspace &W, uint64_t keys, cudaStream_t s) {
   const size_t before = W.owner.cap;
-  unsigned long long *t = W.owner.get<unsigned long long>(2 * keys);
+  uint32_t *t = W.owner.get<uint32_t>(4 * keys);
   if (W.owner.cap != before || W.epoch == 0) {
     CK(cudaMemsetAsync(t, 0, W.owner.cap, s));
     W.epoch = 0;
@@ -237,8 +247,8 @@ unsigned long long *shadow_table(Workspace &W, uint64_t keys, cudaStream_t s) {
   return t;
 }
 
-uint32_t shadow_next_epoch(Workspace &W, cudaStream_t s) {
-  if (W.epoch >= 0xFFFFFFF0u) {
+uint32_t shadow_next_tag(Workspace &W, cudaStream_t s) {
+  if (W.epoch >= 63) {
     CK(cudaMemsetAsync(W.owner.p, 0, W.owner.cap, s));
     W.epoch = 0;
   }
@@ -247,21 +257,20 @@ uint32_t shadow_next_epoch(Workspace &W, cudaStream_t s) {
 
 // Shadow path: commit single-writer cells from the own-write tables, send
 // the log records of shared written cells through the exact sort path.
-void classify_shadow(Workspace &W, const LogRec *log, uint64_t n, uint64_t keys, uint64_t N,
-                     uint32_t interval, const Layout &L, int32_t *snap, const unsigned long long *owner,
-                     uint32_t epoch, const uint2 *ow, const uint32_t *ow_count, uint32_t *dcount,
-                     uint32_t *hstats, std::vector<OutRec> &races, cudaStream_t s) {
-  launch_shadow_commit(ow, ow_count, N, (uint32_t)N, owner, epoch, snap, s);
-  if (n == 0) return;
+void classify_shadow(Workspace &W, const LogRec *log, uint32_t n_slices, uint64_t slice,
+                     const uint32_t *count, uint64_t keys, uint64_t N, uint32_t interval,
+                     const Layout &L, int32_t *snap, const uint32_t *owner, uint32_t tag, const uint2 *ow,
+                     const uint32_t *ow_count, uint32_t *dcount, uint32_t *hstats,
+                     std::vector<OutRec> &races, cudaStream_t s) {
+  launch_shadow_commit(ow, ow_count, N, (uint32_t)N, owner, tag, snap, s);
   unsigned long long *cnt = reinterpret_cast<unsigned long long *>(dcount);
   CK(cudaMemsetAsync(cnt, 0, 8, s));
-  LogRec *shared = W.logb.get<LogRec>(n);
-  launch_shadow_compact(log, n, owner, epoch, shared, cnt, s);
+  LogRec *shared = W.logb.get<LogRec>((uint64_t)n_slices * slice);
+  launch_shadow_compact(log, n_slices, slice, count, owner, tag, shared, cnt, s);
   CK(cudaMemcpyAsync(hstats, cnt, 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const uint64_t m = *reinterpret_cast<uint64_t *>(hstats);
   if (m == 0) return;
-  // sort the shared records, ping-ponging between logb and the compact buffer
   uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(m), scan_tmp_words(m)));
   LogRec *other = W.compact.get<LogRec>(m);
   LogRec *sorted = sort_log(shared, other, m, bitwidth(N), bitwidth(keys) + bitwidth(N), tmp, s);
@@ -278,9 +287,22 @@ rc_report *run_instance(const Instance &I) {
   }
   Layout L = make_layout(P, I.in, I.G);
   const uint64_t N = I.N;
-  const size_t smem = interp_smem_bytes((uint32_t)P.code.size(), (uint32_t)P.mems.size(), P.n_regs, I.S);
-  if (smem > 227 * 1024) throw Fail{RC_E_INVALID, "kernel too large for shared memory at this group size"};
-  const uint64_t cap = N * std::max<uint64_t>(P.max_access_per_interval, 1);
+  // own-write slots in shared memory: as many as fit (up to 8) while keeping
+  // at least two CTAs, or 2048 threads, per SM
+  const size_t base_smem = interp_smem_bytes((uint32_t)P.mems.size(), P.n_regs, I.S, 0);
+  if (base_smem > interp_max_dynamic_smem())
+    throw Fail{RC_E_INVALID, "kernel too large for shared memory at this group size"};
+  const uint32_t ctas_per_sm = std::max<uint32_t>(2, 2048 / I.S);
+  const size_t budget = std::min<size_t>(interp_max_dynamic_smem(), 224 * 1024 / ctas_per_sm - 1024);
+  uint32_t ow_slots = 0;
+  while (ow_slots < 8 && ow_slots < P.max_write_per_interval &&
+         base_smem + (size_t)(ow_slots + 1) * I.S * 8 <= budget)
+    ow_slots++;
+  const size_t smem = base_smem + (size_t)ow_slots * I.S * 8;
+  const uint32_t wpc = (I.S + 31) / 32;               // warps per work-group
+  const uint32_t n_slices = I.G * wpc;                 // one log slice per warp
+  const uint64_t slice = 32ull * std::max<uint64_t>(P.max_access_per_interval, 1);
+  const uint64_t cap = (uint64_t)n_slices * slice;     // >= N * bound: the log cannot overflow
   const uint64_t capw = std::max<uint64_t>(P.max_write_per_interval, 1);
   if (cap >= 0xFFFFFFFFull) throw Fail{RC_E_CAPACITY, "interval log bound exceeds 2^32 records"};
   const uint64_t need = cap * sizeof(LogRec) * 2 + cap * (sizeof(Summary) + 24) + N * capw * 8;
@@ -290,6 +312,7 @@ rc_report *run_instance(const Instance &I) {
   Insn *dcode = W.code.get<Insn>(P.code.size());
   MemInfo *dmems = W.mems.get<MemInfo>(std::max<size_t>(L.mems.size(), 1));
   CK(cudaMemcpyAsync(dcode, P.code.data(), P.code.size() * sizeof(Insn), cudaMemcpyHostToDevice, s));
+  CK(interp_upload_code(P.code.data(), (uint32_t)P.code.size(), s));
   if (!L.mems.empty())
     CK(cudaMemcpyAsync(dmems, L.mems.data(), L.mems.size() * sizeof(MemInfo), cudaMemcpyHostToDevice, s));
   int32_t *snap = W.snap.get<int32_t>(std::max<uint64_t>(L.keys, 1));
@@ -323,15 +346,15 @@ rc_report *run_instance(const Instance &I) {
   CK(cudaMemsetAsync(dstats, 0, stat_words * 4, s));
 
   const int strategy = pick_strategy(cap);
-  unsigned long long *owner = nullptr;
+  uint32_t *owner = nullptr;
   if (strategy == 2) owner = shadow_table(W, L.keys, s);
+  uint32_t *warp_count = W.ctacnt.get<uint32_t>(n_slices);
   uint32_t *ow_cnt = W.owcnt.get<uint32_t>(N);
 
   std::vector<OutRec> races, errors;
   uint32_t interval = 0;
   uint64_t prev_acc[2] = {0, 0};
   for (;; interval++) {
-    CK(cudaMemsetAsync(dstats + ST_LOGCNT, 0, 8, s));
     CK(cudaMemsetAsync(dstats + ST_FLAGS, 0, 8, s));
     CK(cudaMemsetAsync(dstats + ST_STOPS, 0xFF, nstops * 4, s));
     CK(cudaMemsetAsync(dstats + ST_STOPS + nstops, 0, nstops * 4, s));
@@ -355,9 +378,11 @@ rc_report *run_instance(const Instance &I) {
     a.ow = ow;
     a.capw = (uint32_t)std::min<uint64_t>(capw, 0xFFFFFFFFu);
     a.ow_stride = (uint32_t)N;
+    a.ow_slots = ow_slots;
     a.log = log;
-    a.log_count = reinterpret_cast<unsigned long long *>(dstats + ST_LOGCNT);
-    a.log_cap = cap;
+    a.warp_count = warp_count;
+    a.warps_per_cta = wpc;
+    a.warp_slice = slice;
     a.errs = errs;
     a.err_count = dstats + ST_ERRCNT;
     a.err_cap = err_cap;
@@ -367,14 +392,13 @@ rc_report *run_instance(const Instance &I) {
     a.flags = dstats + ST_FLAGS;
     a.ow_count = ow_cnt;
     a.owner = owner;
-    a.epoch = strategy == 2 ? shadow_next_epoch(W, s) : 0;
+    a.tag = strategy == 2 ? shadow_next_tag(W, s) : 0;
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
     launch_interp(a, I.G, smem, s);
     CK(cudaGetLastError());
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], s));
     CK(cudaMemcpyAsync(hstats, dstats, stat_words * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const uint64_t nlog = *reinterpret_cast<uint64_t *>(hstats + ST_LOGCNT);
     const uint32_t flags = hstats[ST_FLAGS];
     if (flags) throw Fail{RC_E_CAPACITY, "interval log, own-write table or error log overflowed"};
     const uint64_t acc_g = *reinterpret_cast<uint64_t *>(hstats + ST_ACC);
@@ -392,10 +416,11 @@ rc_report *run_instance(const Instance &I) {
     }
     // ---- classification + commit
     if (strategy == 2) {
-      classify_shadow(W, log, nlog, L.keys, N, interval, L, snap, owner, a.epoch, ow, ow_cnt,
-                      dstats + ST_SCRATCH, hstats + stat_words, races, s);
+      classify_shadow(W, log, n_slices, slice, warp_count, L.keys, N, interval, L, snap, owner, a.tag, ow,
+                      ow_cnt, dstats + ST_SCRATCH, hstats + stat_words, races, s);
     } else {
-      classify_sorted(W, log, nlog, L.keys, N, interval, L, snap, hstats + stat_words, races, s);
+      classify_sorted(W, log, n_slices, slice, warp_count, L.keys, N, interval, L, snap, hstats + stat_words,
+                      races, s);
     }
     if (g_prof.on) {
       CK(cudaEventRecord(g_prof.ev[3], s));
@@ -496,6 +521,9 @@ int fail_code(const Fail &f) {
 }
 
 }  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 }  // namespace rc
 
 using namespace rc;
@@ -642,6 +670,8 @@ int rc_profile_reset(void) {
   }
   return RC_OK;
 }
+
+uint64_t rc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int rc_profile_get(int kind, uint64_t *launches, double *ms, double *bytes) {
   if (kind < 0 || kind > 2) return RC_E_INVALID;

@@ -17,43 +17,70 @@ namespace cg = cooperative_groups;
 namespace rc {
 namespace {
 
-__global__ void shadow_compact_kernel(const LogRec *log, uint64_t n, const unsigned long long *owner,
-                                      uint32_t epoch, LogRec *out, unsigned long long *count) {
-  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint4 r = reinterpret_cast<const uint4 *>(log)[i];
-  if (!shadow_needs_exact(owner, r.x, epoch)) return;
-  cg::coalesced_group g = cg::coalesced_threads();
-  unsigned long long base = 0;
-  if (g.thread_rank() == 0) base = atomicAdd(count, (unsigned long long)g.size());
-  base = g.shfl(base, 0);
-  reinterpret_cast<uint4 *>(out)[base + g.thread_rank()] = r;
+// one warp per log slice, 8 slices per block
+__global__ void shadow_compact_kernel(const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
+                                      const uint32_t *owner, uint32_t tag, LogRec *out,
+                                      unsigned long long *total) {
+  const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= n_slices) return;
+  const uint32_t n = count[w];
+  const uint4 *src = reinterpret_cast<const uint4 *>(log) + (uint64_t)w * slice;
+  for (uint32_t i = threadIdx.x & 31u; i < n; i += 32) {
+    const uint4 r = src[i];
+    if (!shadow_needs_exact(owner, r.x, tag)) continue;
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned long long base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(total, (unsigned long long)g.size());
+    base = g.shfl(base, 0);
+    reinterpret_cast<uint4 *>(out)[base + g.thread_rank()] = r;
+  }
 }
 
 __global__ void shadow_commit_kernel(const uint2 *ow, const uint32_t *ow_count, uint64_t N, uint32_t ow_stride,
-                                     const unsigned long long *owner, uint32_t epoch, int32_t *snap) {
+                                     const uint32_t *owner, uint32_t tag, int32_t *snap) {
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N) return;
   const uint32_t nw = ow_count[t];
-  const unsigned long long mine = ((unsigned long long)epoch << 32) | (uint32_t)t;
+  const uint32_t hi = (tag << 26) | (uint32_t)t, lo = (tag << 26) | (kIdMask - (uint32_t)t);
   for (uint32_t k = 0; k < nw; k++) {
     const uint2 e = ow[(uint64_t)k * ow_stride + t];
-    if (owner[2ull * e.x] == mine) snap[e.x] = (int32_t)e.y;
+    const uint2 w = reinterpret_cast<const uint2 *>(owner)[2ull * e.x];  // writer max, writer min
+    if (w.x == hi && w.y == lo) snap[e.x] = (int32_t)e.y;  // this work-item is the only writer
   }
+}
+
+__global__ void densify_kernel(const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
+                               const uint32_t *offs, LogRec *out) {
+  const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= n_slices) return;
+  const uint32_t n = count[w];
+  const uint4 *src = reinterpret_cast<const uint4 *>(log) + (uint64_t)w * slice;
+  uint4 *dst = reinterpret_cast<uint4 *>(out) + offs[w];
+  for (uint32_t i = threadIdx.x & 31u; i < n; i += 32) dst[i] = src[i];
 }
 
 }  // namespace
 
-void launch_shadow_compact(const LogRec *log, uint64_t n, const unsigned long long *owner, uint32_t epoch,
-                           LogRec *out, unsigned long long *count, cudaStream_t s) {
-  if (n) shadow_compact_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(log, n, owner, epoch, out, count);
+void launch_shadow_compact(const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
+                           const uint32_t *owner, uint32_t tag, LogRec *out, unsigned long long *total,
+                           cudaStream_t s) {
+  if (!n_slices) return;
+  count_launch();
+  shadow_compact_kernel<<<(n_slices + 7) / 8, 256, 0, s>>>(log, n_slices, slice, count, owner, tag, out, total);
 }
 
 void launch_shadow_commit(const uint2 *ow, const uint32_t *ow_count, uint64_t N, uint32_t ow_stride,
-                          const unsigned long long *owner, uint32_t epoch, int32_t *snap, cudaStream_t s) {
-  if (N)
-    shadow_commit_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ow, ow_count, N, ow_stride, owner, epoch,
-                                                                     snap);
+                          const uint32_t *owner, uint32_t tag, int32_t *snap, cudaStream_t s) {
+  if (!N) return;
+  count_launch();
+  shadow_commit_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ow, ow_count, N, ow_stride, owner, tag, snap);
+}
+
+void launch_densify(const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
+                    const uint32_t *offs, LogRec *out, cudaStream_t s) {
+  if (!n_slices) return;
+  count_launch();
+  densify_kernel<<<(n_slices + 7) / 8, 256, 0, s>>>(log, n_slices, slice, count, offs, out);
 }
 
 }  // namespace rc

@@ -162,12 +162,15 @@ void scan_exclusive(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp
   if (n == 0) return;
   const uint64_t t = tiles_of(n);
   if (t == 1) {
+    count_launch();
     tile_scan_kernel<<<1, kThreads, 0, s>>>(in, n, out, nullptr);
     return;
   }
   uint32_t *sums = tmp, *soffs = tmp + t;
+  count_launch();
   tile_sum_kernel<<<(unsigned)t, kThreads, 0, s>>>(in, n, sums);
   scan_exclusive(sums, soffs, t, tmp + 2 * t, s);
+  count_launch();
   tile_scan_kernel<<<(unsigned)t, kThreads, 0, s>>>(in, n, out, soffs);
 }
 
@@ -183,8 +186,10 @@ LogRec *sort_log(LogRec *a, LogRec *b, uint64_t n, uint32_t gbits, uint32_t bits
   const uint64_t h = 256ull * ntiles;
   uint32_t *hist = tmp, *offs = tmp + h, *stmp = tmp + 2 * h;
   for (uint32_t shift = 0; shift < bits; shift += 8) {
+    count_launch();
     radix_hist_kernel<<<ntiles, kThreads, 0, s>>>(a, n, gbits, shift, hist, ntiles);
     scan_exclusive(hist, offs, h, stmp, s);
+    count_launch();
     radix_scatter_kernel<<<ntiles, kThreads, 0, s>>>(a, b, n, gbits, shift, offs, ntiles);
     LogRec *t = a;
     a = b;

@@ -90,6 +90,8 @@ def load() -> ctypes.CDLL:
         lib.rc_profile_get.argtypes = [c_int, ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]
+        lib.rc_kernel_launches.argtypes = []
+        lib.rc_kernel_launches.restype = ctypes.c_uint64
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
                   "rc_set_strategy", "rc_profile_enable", "rc_profile_reset", "rc_profile_get",
                   "rc_release_workspace"):
@@ -246,3 +248,8 @@ def profile_get(kind: int) -> dict:
 
 def release_workspace() -> None:
     load().rc_release_workspace()
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched since it was loaded."""
+    return int(load().rc_kernel_launches())

@@ -163,3 +163,11 @@ def test_large_kernel_full_size(rc, oracle):
     inst = W.large_kernel(0)
     want = run_both(rc, oracle, inst)
     assert want["n_access"] > 10_000_000
+
+
+def test_long_program_runs_from_global_memory(rc, oracle):
+    """Programs longer than the constant-memory bytecode window run from
+    global memory; the report must not change."""
+    inst = W.large_kernel(7, groups=4, group_size=64, global_len=4096, local_len=256, n_stmts=3000)
+    assert rc.compile(inst.src).info()["n_insn"] > 4000
+    run_both(rc, oracle, inst)
