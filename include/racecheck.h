@@ -149,6 +149,31 @@ void rc_report_free(rc_report *rep);
 const char *rc_strerror(int code);
 const char *rc_last_error(void);
 
+/* One shared access as the checker logs it (16 bytes):
+ *   cell   flat cell index (global cells first, arrays in declared order,
+ *          then local cells, work-group major)
+ *   item   global work-item id in bits 0..30, 1 in bit 31 for a write
+ *   value  value written, or value the read observed
+ *   seq    position of the access in its work-item's barrier interval */
+typedef struct {
+  uint32_t cell, item;
+  int32_t value;
+  uint32_t seq;
+} rc_access;
+
+/* Sort n access records by (cell, work-item id), stably, on the device: the
+ * first step of the exact classification of one barrier interval (records
+ * of one cell become contiguous, and within a cell those of one work-item,
+ * in input order).  in and out are device pointers to n records each, must
+ * not overlap, and in is not modified.  cell_bits / item_bits: the cells are
+ * below 2^cell_bits and the work-item ids below 2^item_bits (item_bits <= 31,
+ * cell_bits + item_bits <= 58; fewer bits mean fewer 8-bit passes).  Runs on
+ * cuda_stream and synchronises it.  Scratch memory comes from the library's
+ * workspace (grown on demand).  Errors: RC_E_INVALID for bad sizes or null
+ * pointers with n > 0, RC_E_CAPACITY, RC_E_CUDA. */
+int rc_sort_accesses(const rc_access *in, rc_access *out, uint64_t n, uint32_t cell_bits, uint32_t item_bits,
+                     void *cuda_stream);
+
 /* Release every device workspace the library holds. */
 int rc_release_workspace(void);
 

@@ -130,6 +130,9 @@ void scan_exclusive(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp
 size_t sort_tmp_words(uint64_t n);
 LogRec *sort_log(LogRec *a, LogRec *b, uint64_t n, uint32_t gbits, uint32_t bits, uint32_t *tmp,
                  cudaStream_t s);
+// same sort from `in` (not written) into `out`, ping-ponging through scratch (n records)
+void sort_log_into(const LogRec *in, LogRec *out, LogRec *scratch, uint64_t n, uint32_t gbits, uint32_t bits,
+                   uint32_t *tmp, cudaStream_t s);
 
 // ---- classification (classify.cu)
 struct ClassifyArgs {

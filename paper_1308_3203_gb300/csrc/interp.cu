@@ -119,23 +119,48 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
     const uint32_t cls = (ctl >> CTL_CLASS_SHIFT) & 0xFu;
     const int32_t x = REG(ra);
     const int32_t yr = REG(rb);
-    if (cls == CC_ALU) {  // arithmetic, moves, comparisons, branches: one branch-free formula
-      const uint32_t pcode = (ctl >> AL_P_SHIFT) & 3u, qcode = (ctl >> AL_Q_SHIFT) & 3u;
-      const uint32_t P = (ctl & AL_PIMM) ? (uint32_t)imm : (pcode & 1u) - (pcode >> 1);
-      const uint32_t Q = (qcode & 1u) - (qcode >> 1);
-      const uint32_t C = (ctl & AL_CONE) ? 1u : (ctl & (AL_PIMM | AL_MASKIMM)) ? 0u : (uint32_t)imm;
-      const uint32_t M = (ctl & AL_M) ? (uint32_t)yr : 0u;
-      const uint32_t mask = (ctl & AL_MASKIMM) ? (uint32_t)imm : 0xFFFFFFFFu;
-      const uint32_t ux = (uint32_t)x;
-      const int32_t arith = (int32_t)((ux * M + ux * P + (uint32_t)yr * Q + C) & mask);
-      const int32_t y = (ctl & AL_YIMM) ? imm : yr;
-      const bool c = (((x < y) && (ctl & AL_LT)) || ((x == y) && (ctl & AL_EQ))) != ((ctl & AL_INV) != 0);
-      const int32_t r = (ctl & AL_CMP) ? (int32_t)c : arith;
-      const bool cond = (ctl & AL_LOOPCOND) ? (arith < imm) : c;
-      const uint32_t mode = (ctl >> AL_MODE_SHIFT) & 3u;
-      const bool take = mode == 2u || (mode == 1u && cond);
+    if (cls == CC_ALU) {  // arithmetic, moves, comparisons, branches
+      const uint32_t ux = (uint32_t)x, uy = (uint32_t)yr, ui = (uint32_t)imm;
+      int32_t r;
+      switch (raw.x & 0xFFu) {  // warp-uniform; branch forms leave r != 0 when taken
+        case OP_MOVI: r = imm; break;
+        case OP_MOV: r = x; break;
+        case OP_ADD: r = (int32_t)(ux + uy); break;
+        case OP_SUB: r = (int32_t)(ux - uy); break;
+        case OP_MUL: r = (int32_t)(ux * uy); break;
+        case OP_ADDI: r = (int32_t)(ux + ui); break;
+        case OP_MULI: r = (int32_t)(ux * ui); break;
+        case OP_ANDI: r = x & imm; break;
+        case OP_RSUBI: r = (int32_t)(ui - ux); break;
+        case OP_MADI: r = (int32_t)(ux * ui + uy); break;
+        case OP_NEG: r = (int32_t)(0u - ux); break;
+        case OP_NOT: r = x == 0; break;
+        case OP_LT: r = x < yr; break;
+        case OP_LE: r = x <= yr; break;
+        case OP_GT: r = x > yr; break;
+        case OP_GE: r = x >= yr; break;
+        case OP_EQ: r = x == yr; break;
+        case OP_NE: r = x != yr; break;
+        case OP_LTI: r = x < imm; break;
+        case OP_LEI: r = x <= imm; break;
+        case OP_GTI: r = x > imm; break;
+        case OP_GEI: r = x >= imm; break;
+        case OP_EQI: r = x == imm; break;
+        case OP_NEI: r = x != imm; break;
+        case OP_BZ: r = x == 0; break;
+        case OP_BFLTI: r = !(x < imm); break;
+        case OP_BFLEI: r = !(x <= imm); break;
+        case OP_BFGTI: r = !(x > imm); break;
+        case OP_BFGEI: r = !(x >= imm); break;
+        case OP_BFEQI: r = x != imm; break;
+        case OP_BFNEI: r = x == imm; break;
+        case OP_LOOP: r = (int32_t)(ux + 1u); break;
+        default: r = 1; break;  // OP_JMP, OP_NOP
+      }
       if (act) {
         if (ctl & AL_WRITE) REG(d) = r;
+        const uint32_t mode = (ctl >> AL_MODE_SHIFT) & 3u;
+        const bool take = mode == 2u || (mode == 1u && ((ctl & AL_LOOPCOND) ? r < imm : r != 0));
         pc = take ? tgt : pc + 1;
       }
       continue;

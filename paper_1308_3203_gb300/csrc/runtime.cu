@@ -96,14 +96,14 @@ struct HostBuf {
 
 struct Workspace {
   DevBuf code, mems, snap, regs, pc, st, ow, loga, logb, head, runidx, sum, khead, keyidx, nrec,
-      recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff;
+      recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff, sortscr;
   HostBuf hstats, hrecs;
   bool configured = false;
   uint32_t epoch = 0;
   void release_all() {
     for (DevBuf *b : {&code, &mems, &snap, &regs, &pc, &st, &ow, &loga, &logb, &head, &runidx, &sum,
                       &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
-                      &owcnt, &compact, &ctacnt, &ctaoff})
+                      &owcnt, &compact, &ctacnt, &ctaoff, &sortscr})
       b->release();
     epoch = 0;
   }
@@ -641,6 +641,29 @@ const char *rc_strerror(int code) {
 }
 
 const char *rc_last_error(void) { return g_last_error.c_str(); }
+
+int rc_sort_accesses(const rc_access *in, rc_access *out, uint64_t n, uint32_t cell_bits, uint32_t item_bits,
+                     void *cuda_stream) {
+  static_assert(sizeof(rc_access) == sizeof(LogRec), "access record layout");
+  if (n == 0) return RC_OK;
+  if (!in || !out || item_bits > 31 || cell_bits + item_bits > 58 || n >= 0xFFFFFFFFull) {
+    g_last_error = "rc_sort_accesses: bad pointers or sizes";
+    return RC_E_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  try {
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    LogRec *scratch = g_ws.sortscr.get<LogRec>(n);
+    uint32_t *tmp = g_ws.scan.get<uint32_t>(sort_tmp_words(n));
+    sort_log_into(reinterpret_cast<const LogRec *>(in), reinterpret_cast<LogRec *>(out), scratch, n,
+                  std::max<uint32_t>(item_bits, 1), cell_bits + std::max<uint32_t>(item_bits, 1), tmp, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return RC_OK;
+  } catch (const Fail &f) {
+    return fail_code(f);
+  }
+}
 
 int rc_release_workspace(void) {
   std::lock_guard<std::mutex> lk(g_mu);

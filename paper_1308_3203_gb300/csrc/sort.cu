@@ -179,6 +179,30 @@ size_t sort_tmp_words(uint64_t n) {
   return 2 * h + scan_tmp_words(h);
 }
 
+void sort_log_into(const LogRec *in, LogRec *out, LogRec *scratch, uint64_t n, uint32_t gbits, uint32_t bits,
+                   uint32_t *tmp, cudaStream_t s) {
+  const uint32_t passes = n <= 1 ? 0 : (bits + 7) / 8;
+  if (passes == 0) {
+    if (n) cudaMemcpyAsync(out, in, n * sizeof(LogRec), cudaMemcpyDeviceToDevice, s);
+    return;
+  }
+  // pass order chosen so that the last pass writes `out` and `in` is never written
+  const uint32_t ntiles = (uint32_t)tiles_of(n);
+  const uint64_t h = 256ull * ntiles;
+  uint32_t *hist = tmp, *offs = tmp + h, *stmp = tmp + 2 * h;
+  const LogRec *src = in;
+  LogRec *dst = (passes % 2) ? out : scratch;
+  for (uint32_t p = 0, shift = 0; p < passes; p++, shift += 8) {
+    count_launch();
+    radix_hist_kernel<<<ntiles, kThreads, 0, s>>>(src, n, gbits, shift, hist, ntiles);
+    scan_exclusive(hist, offs, h, stmp, s);
+    count_launch();
+    radix_scatter_kernel<<<ntiles, kThreads, 0, s>>>(src, dst, n, gbits, shift, offs, ntiles);
+    src = dst;
+    dst = dst == out ? scratch : out;
+  }
+}
+
 LogRec *sort_log(LogRec *a, LogRec *b, uint64_t n, uint32_t gbits, uint32_t bits, uint32_t *tmp,
                  cudaStream_t s) {
   if (n <= 1) return a;

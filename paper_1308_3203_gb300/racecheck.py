@@ -90,6 +90,8 @@ def load() -> ctypes.CDLL:
         lib.rc_profile_get.argtypes = [c_int, ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]
+        lib.rc_sort_accesses.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, vp]
+        lib.rc_sort_accesses.restype = c_int
         lib.rc_kernel_launches.argtypes = []
         lib.rc_kernel_launches.restype = ctypes.c_uint64
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
@@ -253,3 +255,18 @@ def release_workspace() -> None:
 def kernel_launches() -> int:
     """Kernels the library has launched since it was loaded."""
     return int(load().rc_kernel_launches())
+
+
+def sort_accesses(records_in, records_out, cell_bits: int, item_bits: int, stream=None) -> None:
+    """Sort device access records (int32 CUDA tensors of shape [n, 4]: cell,
+    item|write<<31, value, seq) by (cell, work-item) into records_out."""
+    n = records_in.shape[0]
+    if records_out.shape != records_in.shape:
+        raise ValueError("records_out must have the shape of records_in")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = load().rc_sort_accesses(ctypes.c_void_p(records_in.data_ptr()), ctypes.c_void_p(records_out.data_ptr()),
+                                 n, cell_bits, item_bits, ctypes.c_void_p(int(stream) if stream else 0))
+    if rc:
+        _raise(rc)
