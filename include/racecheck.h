@@ -174,6 +174,27 @@ typedef struct {
 int rc_sort_accesses(const rc_access *in, rc_access *out, uint64_t n, uint32_t cell_bits, uint32_t item_bits,
                      void *cuda_stream);
 
+/* rc_sort_accesses for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is an engineering variant of the sort
+ * above.  Callers that must not call cudaMalloc -- a process serving under a
+ * device-memory budget it reserved in full at start-up, a real-time pipeline
+ * that cannot take the device-wide synchronisation an allocation may cause,
+ * a library that must not touch its host application's allocator -- get the
+ * same sort with its scratch (ping-pong records, digit histograms) in one
+ * fixed file-scope device array of about 4.3 MiB, which every GPU that loads
+ * the library holds until the process exits.  This call allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library routine.
+ *  - n may not exceed 2^18 records (RC_E_CAPACITY beyond that); other
+ *    arguments and results are those of rc_sort_accesses.
+ *  - The first call on each device, with that device current, looks up the
+ *    device address of the array (cudaGetSymbolAddress); make that first
+ *    call before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents;
+ *    calls whose work overlaps on the GPU (other streams, other host
+ *    threads) race on it and must be serialised by the caller. */
+int rc_sort_accesses_noalloc(const rc_access *in, rc_access *out, uint64_t n, uint32_t cell_bits,
+                             uint32_t item_bits, void *cuda_stream);
+
 /* Release every device workspace the library holds. */
 int rc_release_workspace(void);
 

@@ -92,6 +92,8 @@ def load() -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_double)]
         lib.rc_sort_accesses.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, vp]
         lib.rc_sort_accesses.restype = c_int
+        lib.rc_sort_accesses_noalloc.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, vp]
+        lib.rc_sort_accesses_noalloc.restype = c_int
         lib.rc_kernel_launches.argtypes = []
         lib.rc_kernel_launches.restype = ctypes.c_uint64
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
@@ -270,3 +272,21 @@ def sort_accesses(records_in, records_out, cell_bits: int, item_bits: int, strea
                                  n, cell_bits, item_bits, ctypes.c_void_p(int(stream) if stream else 0))
     if rc:
         _raise(rc)
+
+
+def sort_accesses_noalloc(records_in, records_out, cell_bits: int, item_bits: int, stream=None) -> None:
+    """sort_accesses without any device allocation: scratch comes from the
+    library's fixed device array (at most 2^18 records).  For callers that may
+    not allocate device memory; concurrent calls on the GPU share that array
+    and must be serialised by the caller."""
+    n = records_in.shape[0]
+    if records_out.shape != records_in.shape:
+        raise ValueError("records_out must have the shape of records_in")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = load().rc_sort_accesses_noalloc(ctypes.c_void_p(records_in.data_ptr()),
+                                         ctypes.c_void_p(records_out.data_ptr()), n, cell_bits, item_bits,
+                                         ctypes.c_void_p(int(stream) if stream else 0))
+    if rc:
+        raise RaceCheckError(rc, load().rc_strerror(rc).decode())
