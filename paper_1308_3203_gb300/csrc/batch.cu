@@ -1,0 +1,354 @@
+// Batched checking: many kernel instances per launch.
+//
+// Every instance keeps its own bytecode, launch shape, cells, registers,
+// own-write table and log slices; the device sees them through a table of
+// descriptors.  Work is cut into warp tasks -- 32 consecutive work-items of
+// one instance -- which a persistent grid pulls from an atomic counter, so
+// instances of very different sizes balance across the GPU.  One launch runs
+// one barrier interval of every instance that is still active (instances
+// progress in lock-step rounds); classification then runs once over the
+// shared cell space of the round, whose cells are the instances' cells laid
+// end to end.  The interpreter step is the single-instance one (min-PC
+// reconvergence, indexed LD/ST, ballot-ranked log appends, owner claims);
+// see interp.cu for the semantics it implements.
+#include <cooperative_groups.h>
+
+#include "device.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rc {
+namespace {
+
+__device__ __forceinline__ int32_t bidiv(int32_t a, int32_t b) {
+  if (b == 0) return 0;
+  if (a == INT32_MIN && b == -1) return INT32_MIN;
+  return a / b;
+}
+__device__ __forceinline__ int32_t bimod(int32_t a, int32_t b) {
+  if (b == 0) return 0;
+  const uint32_t m = b < 0 ? 0u - (uint32_t)b : (uint32_t)b;
+  if ((int32_t)m > 0) {
+    const int32_t r = a % (int32_t)m;
+    return r < 0 ? r + (int32_t)m : r;
+  }
+  return a & 0x7FFFFFFF;
+}
+__device__ __forceinline__ uint64_t bbloom(uint32_t key) { return 1ull << ((key * 2654435761u) >> 26); }
+
+__device__ __forceinline__ void batch_err(const BatchArgs &A, uint32_t k, const OutRec &r) {
+  const uint32_t pos = atomicAdd(A.err_count, 1u);
+  if (pos < A.err_cap) {
+    A.errs[pos] = r;
+    A.err_kernel[pos] = k;
+  } else {
+    atomicOr(A.flags, FLAG_ERR_FULL);
+  }
+}
+
+constexpr uint32_t kBatchThreads = 256;
+
+__global__ void __launch_bounds__(kBatchThreads, 4) batch_interp_kernel(BatchArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t RS = kBatchThreads;  // register-file stride
+  int32_t *rf = reinterpret_cast<int32_t *>(smem);                  // [max_regs][RS]
+  uint32_t *owk = reinterpret_cast<uint32_t *>(rf + A.max_regs * RS);  // [ow_slots][RS]
+  int32_t *owv = reinterpret_cast<int32_t *>(owk + A.ow_slots * RS);
+  const uint32_t t = threadIdx.x, lane = t & 31u, lane_lt = (1u << lane) - 1u;
+  const uint32_t slots = A.ow_slots;
+#define REG(i) rf[(uint32_t)(i) * RS + t]
+
+  for (;;) {
+    // ---- next warp task
+    uint32_t task = 0;
+    if (lane == 0) task = atomicAdd(A.next_task, 1u);
+    task = __shfl_sync(0xFFFFFFFFu, task, 0);
+    if (task >= A.n_tasks) break;
+    const uint32_t k = A.task_kernel[task];
+    const BatchDesc D = A.desc[k];
+    if (!D.active) continue;  // finished instance: nothing to run, its slices stay unread
+    const uint32_t lw = task - D.task_off;                 // warp of the instance
+    const uint32_t gl = lw * 32 + lane;                    // instance-local work-item id
+    const bool exists = (uint64_t)gl < D.N;
+    const uint32_t lanes = __ballot_sync(0xFFFFFFFFu, exists);
+    if (!exists) continue;
+    const uint32_t S = D.S, tid = gl % S, wg = gl / S;
+    const uint32_t lbase = (uint32_t)D.key_base + D.GT + wg * D.LT;
+    const uint4 *code = reinterpret_cast<const uint4 *>(A.code) + D.code_off;
+    const uint4 *mems = reinterpret_cast<const uint4 *>(A.mems) + D.mems_off;
+    uint32_t st = A.st[D.state_off + gl];
+    uint32_t pc = A.pc[D.state_off + gl];
+    if (st == TS_BARRIER) {
+      st = TS_RUN;
+      pc += 1;
+    }
+    const bool ran = st == TS_RUN;
+    if (ran) {
+      for (uint32_t r = kBuiltinRegs; r < D.n_regs; r++) REG(r) = A.regs[D.reg_off + (uint64_t)r * D.N + gl];
+      REG(REG_TID) = (int32_t)tid;
+      REG(REG_WG) = (int32_t)wg;
+      REG(REG_GTID) = (int32_t)gl;
+      REG(REG_GSIZE) = (int32_t)S;
+      REG(REG_NGROUPS) = (int32_t)D.G;
+    }
+    __syncwarp(lanes);
+    uint32_t nloc = 0, seq = 0, nw = 0, wfill = 0;
+    uint64_t bloom = 0;
+    bool running = ran;
+    uint4 *const wlog = reinterpret_cast<uint4 *>(A.log) + D.slice_off + (uint64_t)lw * D.slice;
+    uint2 *const ow = A.ow + D.ow_off;
+
+    for (;;) {
+      const uint32_t minpc = __reduce_min_sync(lanes, running ? pc : kNone);
+      if (minpc == kNone) break;
+      const uint4 raw = __ldg(code + minpc);
+      const bool act = running && pc == minpc;
+      const uint32_t d = (raw.x >> 8) & 0xFFu, ra = (raw.x >> 16) & 0xFFu, rb = raw.x >> 24;
+      const int32_t imm = (int32_t)raw.y;
+      const uint32_t tgt = raw.z, ctl = raw.w;
+      const uint32_t cls = (ctl >> CTL_CLASS_SHIFT) & 0xFu;
+      const int32_t x = REG(ra);
+      const int32_t yr = REG(rb);
+      if (cls == CC_ALU) {
+        const uint32_t ux = (uint32_t)x, uy = (uint32_t)yr, ui = (uint32_t)imm;
+        int32_t r;
+        switch (raw.x & 0xFFu) {
+          case OP_MOVI: r = imm; break;
+          case OP_MOV: r = x; break;
+          case OP_ADD: r = (int32_t)(ux + uy); break;
+          case OP_SUB: r = (int32_t)(ux - uy); break;
+          case OP_MUL: r = (int32_t)(ux * uy); break;
+          case OP_ADDI: r = (int32_t)(ux + ui); break;
+          case OP_MULI: r = (int32_t)(ux * ui); break;
+          case OP_ANDI: r = x & imm; break;
+          case OP_RSUBI: r = (int32_t)(ui - ux); break;
+          case OP_MADI: r = (int32_t)(ux * ui + uy); break;
+          case OP_NEG: r = (int32_t)(0u - ux); break;
+          case OP_NOT: r = x == 0; break;
+          case OP_LT: r = x < yr; break;
+          case OP_LE: r = x <= yr; break;
+          case OP_GT: r = x > yr; break;
+          case OP_GE: r = x >= yr; break;
+          case OP_EQ: r = x == yr; break;
+          case OP_NE: r = x != yr; break;
+          case OP_LTI: r = x < imm; break;
+          case OP_LEI: r = x <= imm; break;
+          case OP_GTI: r = x > imm; break;
+          case OP_GEI: r = x >= imm; break;
+          case OP_EQI: r = x == imm; break;
+          case OP_NEI: r = x != imm; break;
+          case OP_BZ: r = x == 0; break;
+          case OP_BFLTI: r = !(x < imm); break;
+          case OP_BFLEI: r = !(x <= imm); break;
+          case OP_BFGTI: r = !(x > imm); break;
+          case OP_BFGEI: r = !(x >= imm); break;
+          case OP_BFEQI: r = x != imm; break;
+          case OP_BFNEI: r = x == imm; break;
+          case OP_LOOP: r = (int32_t)(ux + 1u); break;
+          default: r = 1; break;
+        }
+        if (act) {
+          if (ctl & AL_WRITE) REG(d) = r;
+          const uint32_t mode = (ctl >> AL_MODE_SHIFT) & 3u;
+          const bool take = mode == 2u || (mode == 1u && ((ctl & AL_LOOPCOND) ? r < imm : r != 0));
+          pc = take ? tgt : pc + 1;
+        }
+        continue;
+      }
+      if (cls == CC_LD || cls == CC_ST) {
+        const uint4 mm = __ldg(mems + (ctl >> CTL_MEM_SHIFT));  // MemInfo: len, base, space
+        uint32_t ui = (uint32_t)x + (uint32_t)imm;
+        if (ctl & CTL_AM) ui &= ((2u << ((ctl >> CTL_K_SHIFT) & 0x1Fu)) - 1u) >> 1;
+        const int32_t idx = (int32_t)(ui + tgt);
+        const bool inb = (uint32_t)idx < mm.x;
+        const uint32_t logging = __ballot_sync(lanes, act && inb);
+        const uint32_t slot_pos = wfill + __popc(logging & lane_lt);
+        wfill += __popc(logging);
+        if (!act) continue;
+        pc++;
+        if (!inb) {
+          OutRec e{A.interval, mm.z, mm.z ? wg : 0u, (uint32_t)idx, CLS_OOB, gl, ctl >> CTL_MEM_SHIFT, 0, 0, 0};
+          batch_err(A, k, e);
+          st = TS_DEAD;
+          running = false;
+          continue;
+        }
+        const uint32_t key = (mm.z ? lbase : (uint32_t)D.key_base) + mm.y + (uint32_t)idx;
+        const uint64_t bit = bbloom(key);
+        int32_t slot = -1;
+        if (bloom & bit) {
+          const uint32_t ns = nw < slots ? nw : slots;
+          for (uint32_t q = 0; q < ns; q++)
+            if (owk[q * RS + t] == key) { slot = (int32_t)q; break; }
+          if (slot < 0)
+            for (uint32_t q = slots; q < nw; q++)
+              if (ow[(uint64_t)q * D.N + gl].x == key) { slot = (int32_t)q; break; }
+        }
+        if (A.owner) shadow_claim(A.owner, key, cls == CC_ST, A.tag, gl);
+        int32_t v;
+        if (cls == CC_LD) {
+          if (slot < 0) v = __ldg(A.snap + key);
+          else if ((uint32_t)slot < slots) v = owv[slot * RS + t];
+          else v = (int32_t)ow[(uint64_t)slot * D.N + gl].y;
+          REG(d) = v;
+        } else {
+          v = yr;
+          if (slot >= 0) {
+            if ((uint32_t)slot < slots) owv[slot * RS + t] = v;
+            else ow[(uint64_t)slot * D.N + gl].y = (uint32_t)v;
+          } else if (nw < slots) {
+            owk[nw * RS + t] = key;
+            owv[nw * RS + t] = v;
+            nw++;
+            bloom |= bit;
+          } else if (nw < D.capw) {
+            ow[(uint64_t)nw * D.N + gl] = make_uint2(key, (uint32_t)v);
+            nw++;
+            bloom |= bit;
+          } else {
+            atomicOr(A.flags, FLAG_OW_FULL);
+          }
+        }
+        if (slot_pos < D.slice)
+          wlog[slot_pos] = make_uint4(key, gl | (cls == CC_ST ? 0x80000000u : 0u), (uint32_t)v, seq);
+        else
+          atomicOr(A.flags, FLAG_LOG_FULL);
+        seq++;
+        nloc += mm.z;
+        continue;
+      }
+      if (!act) continue;
+      pc++;
+      switch (cls) {
+        case CC_DIVMOD: {
+          const int32_t y = (ctl & DM_YIMM) ? imm : yr;
+          REG(d) = (ctl & DM_MOD) ? bimod(x, y) : bidiv(x, y);
+          break;
+        }
+        case CC_LOGIC:
+          REG(d) = (ctl & 1u) ? ((x != 0) || (yr != 0)) : ((x != 0) && (yr != 0));
+          break;
+        case CC_SIZE:
+          REG(d) = (int32_t)__ldg(mems + (ctl >> CTL_MEM_SHIFT)).x;
+          break;
+        case CC_ASSUME:
+          if (x == 0) {
+            st = TS_DEAD;
+            running = false;
+          }
+          break;
+        case CC_ASSERT:
+          if (x == 0) {
+            OutRec e{A.interval, 0, 0, 0, CLS_ASSERT, gl, (uint32_t)imm, 0, 0, 0};
+            batch_err(A, k, e);
+            st = TS_DEAD;
+            running = false;
+          }
+          break;
+        case CC_BARRIER:
+          st = TS_BARRIER;
+          pc -= 1;
+          running = false;
+          break;
+        default:
+          st = TS_EXIT;
+          pc -= 1;
+          running = false;
+          break;
+      }
+    }
+    // ---- end of this warp task
+    if (st == TS_BARRIER || (st == TS_EXIT && ran)) {
+      const uint32_t stop = st == TS_BARRIER ? (uint32_t)__ldg(code + pc).y : D.n_barriers;
+      atomicMin(&A.stop_min[D.stop_off + stop], gl);
+      atomicAdd(&A.stop_cnt[D.stop_off + stop], 1u);
+    }
+    A.st[D.state_off + gl] = st;
+    A.pc[D.state_off + gl] = pc;
+    A.ow_count[D.state_off + gl] = nw;
+    {
+      const uint32_t ns = nw < slots ? nw : slots;
+      for (uint32_t q = 0; q < ns; q++) ow[(uint64_t)q * D.N + gl] = make_uint2(owk[q * RS + t], (uint32_t)owv[q * RS + t]);
+    }
+    if (st == TS_BARRIER)
+      for (uint32_t r = kBuiltinRegs; r < D.n_regs; r++) A.regs[D.reg_off + (uint64_t)r * D.N + gl] = REG(r);
+    __syncwarp(lanes);
+    const uint32_t sg = __reduce_add_sync(lanes, seq - nloc), sl = __reduce_add_sync(lanes, nloc);
+    if (lane == __ffs(lanes) - 1) {
+      if (sg) atomicAdd(&A.acc[2ull * k], (unsigned long long)sg);
+      if (sl) atomicAdd(&A.acc[2ull * k + 1], (unsigned long long)sl);
+      A.warp_count[task] = wfill < D.slice ? wfill : (uint32_t)D.slice;
+    }
+  }
+#undef REG
+}
+
+// One warp per warp task: slices of inactive instances hold nothing this round.
+__global__ void batch_compact_kernel(BatchArgs A, LogRec *out, unsigned long long *total) {
+  const uint32_t task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (task >= A.n_tasks) return;
+  const uint32_t k = A.task_kernel[task];
+  if (!A.desc[k].active) return;
+  const BatchDesc &D = A.desc[k];
+  const uint32_t n = A.warp_count[task];
+  const uint4 *src = reinterpret_cast<const uint4 *>(A.log) + D.slice_off + (uint64_t)(task - D.task_off) * D.slice;
+  for (uint32_t i = threadIdx.x & 31u; i < n; i += 32) {
+    const uint4 r = src[i];
+    if (A.owner && !shadow_needs_exact(A.owner, r.x, A.tag)) continue;
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned long long base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(total, (unsigned long long)g.size());
+    base = g.shfl(base, 0);
+    reinterpret_cast<uint4 *>(out)[base + g.thread_rank()] = r;
+  }
+}
+
+// One thread per work-item of every active instance (task-major).
+__global__ void batch_commit_kernel(BatchArgs A) {
+  const uint32_t task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (task >= A.n_tasks) return;
+  const uint32_t k = A.task_kernel[task];
+  const BatchDesc &D = A.desc[k];
+  if (!D.active) return;
+  const uint32_t gl = (task - D.task_off) * 32 + (threadIdx.x & 31u);
+  if ((uint64_t)gl >= D.N) return;
+  const uint32_t nw = A.ow_count[D.state_off + gl];
+  const uint32_t hi = (A.tag << 26) | gl, lo = (A.tag << 26) | (kIdMask - gl);
+  for (uint32_t q = 0; q < nw; q++) {
+    const uint2 e = A.ow[D.ow_off + (uint64_t)q * D.N + gl];
+    const uint2 w = reinterpret_cast<const uint2 *>(A.owner)[2ull * e.x];
+    if (w.x == hi && w.y == lo) A.snap[e.x] = (int32_t)e.y;
+  }
+}
+
+}  // namespace
+
+size_t batch_smem_bytes(uint32_t max_regs, uint32_t ow_slots) {
+  return ((size_t)max_regs + 2ull * ow_slots) * kBatchThreads * 4;
+}
+
+cudaError_t batch_configure() {
+  return cudaFuncSetAttribute(batch_interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kMaxSmemPerBlock);
+}
+
+uint32_t batch_threads() { return kBatchThreads; }
+
+void launch_batch_interp(const BatchArgs &a, uint32_t grid, size_t smem, cudaStream_t s) {
+  count_launch();
+  batch_interp_kernel<<<grid, kBatchThreads, smem, s>>>(a);
+}
+
+void launch_batch_compact(const BatchArgs &a, LogRec *out, unsigned long long *total, cudaStream_t s) {
+  if (!a.n_tasks) return;
+  count_launch();
+  batch_compact_kernel<<<(a.n_tasks + 7) / 8, 256, 0, s>>>(a, out, total);
+}
+
+void launch_batch_commit(const BatchArgs &a, cudaStream_t s) {
+  if (!a.n_tasks || !a.owner) return;
+  count_launch();
+  batch_commit_kernel<<<(a.n_tasks + 7) / 8, 256, 0, s>>>(a);
+}
+
+}  // namespace rc

@@ -163,18 +163,31 @@ __device__ CellResult classify_cell(const Summary *sum, uint64_t b, uint64_t nsu
 }
 
 __device__ __forceinline__ OutRec make_rec(const ClassifyArgs &a, uint32_t key, uint32_t cls, uint32_t ta,
-                                           uint32_t tb, const CellResult &c) {
+                                           uint32_t tb, const CellResult &c, uint32_t p) {
   OutRec o;
   o.interval = a.interval;
-  if (key < a.GT) {
+  uint32_t GT = a.GT, LT = a.LT;
+  if (a.n_kernels) {  // batch: find the instance owning the cell (binary search on first cells)
+    uint32_t lo = 0, hi = a.n_kernels;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) / 2;
+      if (a.kbase[mid] <= key) lo = mid;
+      else hi = mid;
+    }
+    key -= (uint32_t)a.kbase[lo];
+    GT = a.kGT[lo];
+    LT = a.kLT[lo] ? a.kLT[lo] : 1;
+    a.rec_kernel[p] = lo;
+  }
+  if (key < GT) {
     o.space = 0;
     o.wg = 0;
     o.addr = key;
   } else {
-    const uint32_t l = key - a.GT;
+    const uint32_t l = key - GT;
     o.space = 1;
-    o.wg = l / a.LT;
-    o.addr = l % a.LT;
+    o.wg = l / LT;
+    o.addr = l % LT;
   }
   o.cls = cls;
   o.t_a = ta;
@@ -204,8 +217,11 @@ __global__ void key_emit_kernel(const Summary *sum, uint64_t nsum, const uint32_
   const CellResult c = classify_cell(sum, i, nsum);
   uint32_t p = recoff[k];
   const uint32_t key = sum[i].key;
-  if (c.ww_cls) out[p++] = make_rec(a, key, c.ww_cls, c.ww_a, c.ww_b, c);
-  if (c.rw_a != kNone) out[p++] = make_rec(a, key, CLS_RW_RACE, c.rw_a, c.rw_b, c);
+  if (c.ww_cls) {
+    out[p] = make_rec(a, key, c.ww_cls, c.ww_a, c.ww_b, c, p);
+    p++;
+  }
+  if (c.rw_a != kNone) out[p] = make_rec(a, key, CLS_RW_RACE, c.rw_a, c.rw_b, c, p);
 }
 
 unsigned blocks_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }

@@ -121,6 +121,50 @@ cudaError_t interp_upload_code(const Insn *host_code, uint32_t n_insn, cudaStrea
 constexpr size_t kMaxSmemPerBlock = 227 * 1024;  // opt-in shared memory per CTA on sm_103
 size_t interp_max_dynamic_smem();  // valid after interp_configure()
 
+// ---- batched checking (batch.cu)
+struct BatchDesc {  // one instance of a batch
+  uint32_t code_off, mems_off, n_regs, n_barriers;
+  uint32_t S, G, GT, LT;
+  uint32_t capw, stop_off, task_off, active;
+  uint64_t N;          // work-items
+  uint64_t key_base;   // first cell of the instance in the batch's cell space
+  uint64_t reg_off;    // registers [n_regs][N] start here
+  uint64_t state_off;  // pc / st / own-write counts start here
+  uint64_t ow_off;     // own-write table [capw][N] starts here
+  uint64_t slice_off;  // first log record of the instance's warp slices
+  uint64_t slice;      // records per warp slice (32 * static bound)
+};
+
+struct BatchArgs {
+  BatchDesc *desc;
+  const uint32_t *task_kernel;  // warp task -> instance
+  uint32_t n_tasks;
+  uint32_t *next_task;          // persistent-grid task counter (zero before each launch)
+  const Insn *code;             // all instances' bytecode, end to end
+  const MemInfo *mems;          // all instances' memory tables
+  uint32_t max_regs, ow_slots, interval, tag;
+  int32_t *snap;
+  int32_t *regs;
+  uint32_t *pc, *st, *ow_count;
+  uint2 *ow;
+  LogRec *log;
+  uint32_t *warp_count;         // per warp task
+  OutRec *errs;
+  uint32_t *err_kernel, *err_count;
+  uint32_t err_cap;
+  uint32_t *stop_min, *stop_cnt;
+  unsigned long long *acc;      // [2 * instances]: global, local accesses
+  uint32_t *flags;
+  uint32_t *owner;              // shadow owner table over the batch's cells (nullptr: sort path)
+};
+
+size_t batch_smem_bytes(uint32_t max_regs, uint32_t ow_slots);
+cudaError_t batch_configure();
+uint32_t batch_threads();
+void launch_batch_interp(const BatchArgs &a, uint32_t grid, size_t smem, cudaStream_t s);
+void launch_batch_compact(const BatchArgs &a, LogRec *out, unsigned long long *total, cudaStream_t s);
+void launch_batch_commit(const BatchArgs &a, cudaStream_t s);
+
 // ---- scan / sort (sort.cu)
 // exclusive prefix sum of n uint32 values; tmp must hold scan_tmp_words(n)
 size_t scan_tmp_words(uint64_t n);
@@ -138,6 +182,11 @@ void sort_log_into(const LogRec *in, LogRec *out, LogRec *scratch, uint64_t n, u
 struct ClassifyArgs {
   uint32_t interval, GT, LT;
   int32_t *snap;  // committed memory, updated in place
+  // batches: cells of several instances end to end; records name their instance
+  uint32_t n_kernels = 0;
+  const uint64_t *kbase = nullptr;  // sorted first cell of each instance
+  const uint32_t *kGT = nullptr, *kLT = nullptr;
+  uint32_t *rec_kernel = nullptr;   // instance of each emitted record
 };
 void launch_run_heads(const LogRec *r, uint64_t n, uint32_t *head, cudaStream_t s);
 void launch_run_reduce(const LogRec *r, uint64_t n, const uint32_t *head, const uint32_t *runidx,

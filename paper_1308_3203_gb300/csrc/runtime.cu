@@ -96,14 +96,16 @@ struct HostBuf {
 
 struct Workspace {
   DevBuf code, mems, snap, regs, pc, st, ow, loga, logb, head, runidx, sum, khead, keyidx, nrec,
-      recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff, sortscr;
+      recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff, sortscr, reckern,
+      bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc;
   HostBuf hstats, hrecs;
-  bool configured = false;
+  bool configured = false, batch_configured = false;
   uint32_t epoch = 0;
   void release_all() {
     for (DevBuf *b : {&code, &mems, &snap, &regs, &pc, &st, &ow, &loga, &logb, &head, &runidx, &sum,
                       &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
-                      &owcnt, &compact, &ctacnt, &ctaoff, &sortscr})
+                      &owcnt, &compact, &ctacnt, &ctaoff, &sortscr, &reckern, &bdesc, &bcode,
+                      &bmems, &btask, &bkbase, &bkgt, &bklt, &berrk, &shared_acc})
       b->release();
     epoch = 0;
   }
@@ -180,8 +182,16 @@ int pick_strategy(uint64_t n_log) {
 
 // Classify records already sorted by (cell, work-item): run reduce, per-cell
 // classification with commit, and ordered emission of the records.
+struct BatchMap {  // cell space of a batch: instance first cells and sizes (device)
+  uint32_t n = 0;
+  const uint64_t *kbase = nullptr;
+  const uint32_t *kGT = nullptr, *kLT = nullptr;
+  std::vector<uint32_t> *kernel_of = nullptr;  // receives the instance of every record
+};
+
 void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t interval, const Layout &L,
-                  int32_t *snap, uint32_t *hstats, std::vector<OutRec> &races, cudaStream_t s) {
+                  int32_t *snap, uint32_t *hstats, std::vector<OutRec> &races, cudaStream_t s,
+                  const BatchMap *bm = nullptr) {
   uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(n), scan_tmp_words(n)));
   uint32_t *head = W.head.get<uint32_t>(n), *runidx = W.runidx.get<uint32_t>(n);
   launch_run_heads(sorted, n, head, s);
@@ -200,6 +210,12 @@ void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t inter
   const uint64_t nkeys = (uint64_t)hstats[0] + hstats[1];
   uint32_t *nrec = W.nrec.get<uint32_t>(nkeys), *recoff = W.recoff.get<uint32_t>(nkeys);
   ClassifyArgs ca{interval, (uint32_t)L.GT, (uint32_t)std::max<uint64_t>(L.LT, 1), snap};
+  if (bm) {
+    ca.n_kernels = bm->n;
+    ca.kbase = bm->kbase;
+    ca.kGT = bm->kGT;
+    ca.kLT = bm->kLT;
+  }
   launch_key_classify(sum, nsum, khead, keyidx, nrec, ca, s);
   scan_exclusive(nrec, recoff, nkeys, tmp, s);
   CK(cudaMemcpyAsync(hstats, recoff + nkeys - 1, 4, cudaMemcpyDeviceToHost, s));
@@ -208,10 +224,15 @@ void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t inter
   const uint64_t nrecs = (uint64_t)hstats[0] + hstats[1];
   if (nrecs == 0) return;
   OutRec *out = W.out.get<OutRec>(nrecs);
+  if (bm) ca.rec_kernel = W.reckern.get<uint32_t>(nrecs);
   launch_key_emit(sum, nsum, khead, keyidx, nrec, recoff, out, ca, s);
   size_t old = races.size();
   races.resize(old + nrecs);
   CK(cudaMemcpyAsync(races.data() + old, out, nrecs * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
+  if (bm) {
+    bm->kernel_of->resize(old + nrecs);
+    CK(cudaMemcpyAsync(bm->kernel_of->data() + old, ca.rec_kernel, nrecs * 4, cudaMemcpyDeviceToHost, s));
+  }
   CK(cudaStreamSynchronize(s));
 }
 
@@ -275,6 +296,76 @@ void classify_shadow(Workspace &W, const LogRec *log, uint32_t n_slices, uint64_
   LogRec *other = W.compact.get<LogRec>(m);
   LogRec *sorted = sort_log(shared, other, m, bitwidth(N), bitwidth(keys) + bitwidth(N), tmp, s);
   classify_run(W, sorted, m, interval, L, snap, hstats, races, s);
+}
+
+// Report of one instance: race records (already in cell order), error
+// records, counters, status (Sec. 4: racy iff a WW or RW race record) and,
+// if asked, the final global memory read from the device snapshot.
+rc_report *make_report(const std::vector<OutRec> &races, const std::vector<OutRec> &errors, uint32_t n_intervals,
+                       uint64_t acc_g, uint64_t acc_l, uint64_t GT, const int32_t *final_dev, cudaStream_t s) {
+  rc_report *rep = static_cast<rc_report *>(std::calloc(1, sizeof(rc_report)));
+  if (!rep) throw Fail{RC_E_NOMEM, "report allocation failed"};
+  rep->n_intervals = n_intervals;
+  rep->n_global = acc_g;
+  rep->n_local = acc_l;
+  rep->n_access = acc_g + acc_l;
+  bool racy = false, div = false, as = false, oob = false;
+  for (const OutRec &x : races) racy |= x.cls == CLS_WW_RACE || x.cls == CLS_RW_RACE;
+  for (const OutRec &x : errors) {
+    div |= x.cls == CLS_DIVERGENCE;
+    as |= x.cls == CLS_ASSERT;
+    oob |= x.cls == CLS_OOB;
+  }
+  rep->status = racy ? RC_RACY : div ? RC_ERROR_DIVERGENCE : as ? RC_ERROR_ASSERT : oob ? RC_ERROR_OOB : RC_RACE_FREE;
+  rep->n_records = races.size() + errors.size();
+  if (rep->n_records) {
+    rep->records = static_cast<rc_record *>(std::malloc(rep->n_records * sizeof(rc_record)));
+    if (!rep->records) {
+      std::free(rep);
+      throw Fail{RC_E_NOMEM, "report allocation failed"};
+    }
+    static_assert(sizeof(rc_record) == sizeof(OutRec), "record layout");
+    if (!races.empty()) std::memcpy(rep->records, races.data(), races.size() * sizeof(OutRec));
+    if (!errors.empty()) std::memcpy(rep->records + races.size(), errors.data(), errors.size() * sizeof(OutRec));
+  }
+  rep->final_len = GT;
+  if (final_dev && GT) {
+    rep->final_global = static_cast<int32_t *>(std::malloc(GT * 4));
+    if (!rep->final_global) {
+      std::free(rep->records);
+      std::free(rep);
+      throw Fail{RC_E_NOMEM, "report allocation failed"};
+    }
+    CK(cudaMemcpyAsync(rep->final_global, final_dev, GT * 4, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return rep;
+}
+
+// Stop points of one interval -> divergence records (Sec. 4 barrier-release
+// rule: every live work-item must wait at the same barrier, or all exit).
+// Returns true when the run goes on to another interval.
+bool barrier_agreement(uint32_t interval, uint32_t n_barriers, const uint32_t *stop_min, const uint32_t *stop_cnt,
+                       std::vector<OutRec> &errors) {
+  uint32_t n_points = 0;
+  bool any_barrier = false;
+  for (uint32_t k = 0; k <= n_barriers; k++) {
+    if (!stop_cnt[k]) continue;
+    n_points++;
+    if (k < n_barriers) any_barrier = true;
+  }
+  if (n_points >= 2) {
+    std::vector<OutRec> dv;
+    for (uint32_t k = 0; k <= n_barriers; k++) {
+      if (!stop_cnt[k]) continue;
+      dv.push_back(OutRec{interval, 0, 0, 0, CLS_DIVERGENCE, stop_min[k], k < n_barriers ? k : 0xFFFFFFFFu, 0, 0,
+                          stop_cnt[k]});
+    }
+    std::sort(dv.begin(), dv.end(), [](const OutRec &x, const OutRec &y) { return x.t_a < y.t_a; });
+    errors.insert(errors.end(), dv.begin(), dv.end());  // after this interval's OOB/ASSERT (class order)
+    return false;
+  }
+  return any_barrier;
 }
 
 rc_report *run_instance(const Instance &I) {
@@ -444,67 +535,267 @@ rc_report *run_instance(const Instance &I) {
       errors.insert(errors.end(), e.begin(), e.end());
     }
     // ---- barrier agreement (barrier-release rule of Sec. 4)
-    uint32_t n_points = 0;
-    bool any_barrier = false;
-    for (uint32_t k = 0; k < nstops; k++) {
-      if (!stop_cnt[k]) continue;
-      n_points++;
-      if (k < P.n_barriers) any_barrier = true;
-    }
-    if (n_points >= 2) {
-      std::vector<OutRec> dv;
-      for (uint32_t k = 0; k < nstops; k++) {
-        if (!stop_cnt[k]) continue;
-        dv.push_back(OutRec{interval, 0, 0, 0, CLS_DIVERGENCE, stop_min[k],
-                            k < P.n_barriers ? k : 0xFFFFFFFFu, 0, 0, stop_cnt[k]});
-      }
-      std::sort(dv.begin(), dv.end(), [](const OutRec &x, const OutRec &y) { return x.t_a < y.t_a; });
-      // divergence sorts after ASSERT/OOB of the same interval (by class)
-      errors.insert(errors.end(), dv.begin(), dv.end());
-      break;
-    }
-    if (!any_barrier) break;
+    if (!barrier_agreement(interval, P.n_barriers, stop_min.data(), stop_cnt.data(), errors)) break;
   }
 
-  // ---- report
-  rc_report *rep = static_cast<rc_report *>(std::calloc(1, sizeof(rc_report)));
-  if (!rep) throw Fail{RC_E_NOMEM, "report allocation failed"};
-  const uint64_t acc_g = prev_acc[0], acc_l = prev_acc[1];
-  rep->n_intervals = interval + 1;
-  rep->n_global = acc_g;
-  rep->n_local = acc_l;
-  rep->n_access = acc_g + acc_l;
-  bool racy = false, div = false, as = false, oob = false;
-  for (const OutRec &r : races) racy |= r.cls == CLS_WW_RACE || r.cls == CLS_RW_RACE;
-  for (const OutRec &r : errors) {
-    div |= r.cls == CLS_DIVERGENCE;
-    as |= r.cls == CLS_ASSERT;
-    oob |= r.cls == CLS_OOB;
+  return make_report(races, errors, interval + 1, prev_acc[0], prev_acc[1], L.GT,
+                     (I.in->flags & RC_WANT_FINAL_MEMORY) ? snap : nullptr, s);
+}
+
+// ---------------------------------------------------------------- batches
+struct BatchItem {
+  const Program *p;
+  uint32_t G, S;
+  uint64_t N;
+  const rc_input *in;
+  Layout L;
+  uint64_t B, capw, warps, bytes;
+};
+
+BatchItem plan_item(const rc_bytecode *bc, uint32_t G, uint32_t S, const rc_input *in) {
+  BatchItem it;
+  it.p = &bc->prog;
+  it.G = G;
+  it.S = S;
+  it.N = (uint64_t)G * S;
+  it.in = in;
+  it.L = make_layout(bc->prog, in, G);
+  it.B = std::max<uint64_t>(bc->prog.max_access_per_interval, 1);
+  it.capw = std::max<uint64_t>(bc->prog.max_write_per_interval, 1);
+  it.warps = (it.N + 31) / 32;
+  // cells (snapshot + owner table), registers/state/own writes, two logs
+  it.bytes = it.L.keys * 20 + it.N * (4ull * bc->prog.n_regs + 12 + 8 * it.capw) + it.warps * 32 * it.B * 32;
+  return it;
+}
+
+// Check instances [0, n) of `items` together: every round runs one barrier
+// interval of every instance still active, in one persistent interpreter
+// launch, then one classification over the shared cell space.
+void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy, rc_report **out) {
+  Workspace &W = g_ws;
+  if (!W.batch_configured) {
+    CK(batch_configure());
+    W.batch_configured = true;
   }
-  rep->status = racy ? RC_RACY : div ? RC_ERROR_DIVERGENCE : as ? RC_ERROR_ASSERT : oob ? RC_ERROR_OOB : RC_RACE_FREE;
-  rep->n_records = races.size() + errors.size();
-  if (rep->n_records) {
-    rep->records = static_cast<rc_record *>(std::malloc(rep->n_records * sizeof(rc_record)));
-    if (!rep->records) {
-      std::free(rep);
-      throw Fail{RC_E_NOMEM, "report allocation failed"};
+  const uint32_t n = (uint32_t)items.size();
+  std::vector<BatchDesc> desc(n);
+  std::vector<Insn> code;
+  std::vector<MemInfo> mems;
+  std::vector<uint32_t> task_kernel;
+  std::vector<uint64_t> kbase(n);
+  std::vector<uint32_t> kGT(n), kLT(n);
+  uint64_t keys = 0, regs = 0, state = 0, owe = 0, logrecs = 0;
+  uint32_t stops = 0, max_regs = kBuiltinRegs, max_writes = 1;
+  uint64_t maxN = 1;
+  for (uint32_t k = 0; k < n; k++) {
+    const BatchItem &it = items[k];
+    BatchDesc &D = desc[k];
+    D.code_off = (uint32_t)code.size();
+    code.insert(code.end(), it.p->code.begin(), it.p->code.end());
+    D.mems_off = (uint32_t)mems.size();
+    mems.insert(mems.end(), it.L.mems.begin(), it.L.mems.end());
+    D.n_regs = it.p->n_regs;
+    D.n_barriers = it.p->n_barriers;
+    D.S = it.S;
+    D.G = it.G;
+    D.GT = (uint32_t)it.L.GT;
+    D.LT = (uint32_t)it.L.LT;
+    D.capw = (uint32_t)std::min<uint64_t>(it.capw, 0xFFFFFFFFu);
+    D.stop_off = stops;
+    D.task_off = (uint32_t)task_kernel.size();
+    D.active = 1;
+    D.N = it.N;
+    D.key_base = keys;
+    D.reg_off = regs;
+    D.state_off = state;
+    D.ow_off = owe;
+    D.slice = 32 * it.B;
+    D.slice_off = logrecs;
+    kbase[k] = keys;
+    kGT[k] = D.GT;
+    kLT[k] = D.LT;
+    task_kernel.insert(task_kernel.end(), it.warps, k);
+    keys += it.L.keys;
+    regs += it.N * it.p->n_regs;
+    state += it.N;
+    owe += it.N * it.capw;
+    logrecs += it.warps * D.slice;
+    stops += it.p->n_barriers + 1;
+    max_regs = std::max(max_regs, it.p->n_regs);
+    max_writes = (uint32_t)std::max<uint64_t>(max_writes, it.capw);
+    maxN = std::max(maxN, it.N);
+  }
+  const uint32_t n_tasks = (uint32_t)task_kernel.size();
+  // device copies
+  BatchDesc *ddesc = W.bdesc.get<BatchDesc>(n);
+  Insn *dcode = W.bcode.get<Insn>(code.size());
+  MemInfo *dmems = W.bmems.get<MemInfo>(std::max<size_t>(mems.size(), 1));
+  uint32_t *dtask = W.btask.get<uint32_t>(n_tasks);
+  uint64_t *dkbase = W.bkbase.get<uint64_t>(n);
+  uint32_t *dkgt = W.bkgt.get<uint32_t>(n), *dklt = W.bklt.get<uint32_t>(n);
+  CK(cudaMemcpyAsync(dcode, code.data(), code.size() * sizeof(Insn), cudaMemcpyHostToDevice, s));
+  if (!mems.empty()) CK(cudaMemcpyAsync(dmems, mems.data(), mems.size() * sizeof(MemInfo), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dtask, task_kernel.data(), n_tasks * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dkbase, kbase.data(), n * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dkgt, kGT.data(), n * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dklt, kLT.data(), n * 4, cudaMemcpyHostToDevice, s));
+  int32_t *snap = W.snap.get<int32_t>(std::max<uint64_t>(keys, 1));
+  for (uint32_t k = 0; k < n; k++) {  // inputs, then zeroed local memory
+    const BatchItem &it = items[k];
+    uint32_t gi = 0;
+    for (size_t m = 0; m < it.p->mems.size(); m++) {
+      if (it.p->mems[m].space != 0) continue;
+      const uint64_t len = it.in->global_len[gi];
+      if (len) {
+        if (!it.in->global_init || !it.in->global_init[gi]) throw Fail{RC_E_INVALID, "missing global input"};
+        CK(cudaMemcpyAsync(snap + kbase[k] + it.L.mems[m].base, it.in->global_init[gi], len * 4,
+                           it.in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      }
+      gi++;
     }
-    static_assert(sizeof(rc_record) == sizeof(OutRec), "record layout");
-    std::memcpy(rep->records, races.data(), races.size() * sizeof(OutRec));
-    std::memcpy(rep->records + races.size(), errors.data(), errors.size() * sizeof(OutRec));
+    if (it.L.keys > it.L.GT) CK(cudaMemsetAsync(snap + kbase[k] + it.L.GT, 0, (it.L.keys - it.L.GT) * 4, s));
   }
-  rep->final_len = L.GT;
-  if ((I.in->flags & RC_WANT_FINAL_MEMORY) && L.GT) {
-    rep->final_global = static_cast<int32_t *>(std::malloc(L.GT * 4));
-    if (!rep->final_global) {
-      std::free(rep->records);
-      std::free(rep);
-      throw Fail{RC_E_NOMEM, "report allocation failed"};
+  int32_t *dregs = W.regs.get<int32_t>(std::max<uint64_t>(regs, 1));
+  uint32_t *dpc = W.pc.get<uint32_t>(state), *dst = W.st.get<uint32_t>(state), *dowc = W.owcnt.get<uint32_t>(state);
+  CK(cudaMemsetAsync(dregs, 0, regs * 4, s));
+  CK(cudaMemsetAsync(dpc, 0, state * 4, s));
+  CK(cudaMemsetAsync(dst, 0, state * 4, s));
+  uint2 *dow = W.ow.get<uint2>(std::max<uint64_t>(owe, 1));
+  LogRec *dlog = W.loga.get<LogRec>(std::max<uint64_t>(logrecs, 1));
+  uint32_t *dwc = W.ctacnt.get<uint32_t>(n_tasks);
+  const uint32_t err_cap = (uint32_t)std::min<uint64_t>(state, 1u << 26);
+  OutRec *derrs = W.errs.get<OutRec>(err_cap);
+  uint32_t *derrk = W.berrk.get<uint32_t>(err_cap);
+  // stats: [0..1] acc is separate; words: flags, err_count, next_task, pad, compact count (2), stops...
+  const size_t stat_words = 8 + 2 * (size_t)stops;
+  uint32_t *dstats = W.stats.get<uint32_t>(stat_words);
+  uint32_t *hstats = W.hstats.get<uint32_t>(stat_words + 8);
+  unsigned long long *dacc = reinterpret_cast<unsigned long long *>(W.shared_acc.get<uint64_t>(2ull * n));
+  CK(cudaMemsetAsync(dacc, 0, 16ull * n, s));
+  uint32_t *owner = strategy == 2 ? shadow_table(W, keys, s) : nullptr;
+  // own-write slots in shared memory (up to 8) with 4 CTAs of the interpreter per SM
+  uint32_t ow_slots = 0;
+  while (ow_slots < 8 && ow_slots < max_writes && batch_smem_bytes(max_regs, ow_slots + 1) <= 50 * 1024) ow_slots++;
+  const size_t smem = batch_smem_bytes(max_regs, ow_slots);
+  if (smem > kMaxSmemPerBlock) throw Fail{RC_E_INVALID, "batch needs too many registers per work-item"};
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
+  const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((n_tasks + 7) / 8, (uint32_t)sms * 4));
+
+  std::vector<std::vector<OutRec>> races(n), errors(n);
+  std::vector<uint32_t> n_intervals(n, 0);
+  uint32_t active = n;
+  std::vector<uint64_t> acc(2ull * n);
+  std::vector<OutRec> rr;
+  std::vector<uint32_t> rk;
+  for (uint32_t round = 0; active; round++) {
+    CK(cudaMemcpyAsync(ddesc, desc.data(), n * sizeof(BatchDesc), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(dstats, 0, 8 * 4, s));
+    CK(cudaMemsetAsync(dstats + 8, 0xFF, stops * 4, s));
+    CK(cudaMemsetAsync(dstats + 8 + stops, 0, stops * 4, s));
+    BatchArgs a{};
+    a.desc = ddesc;
+    a.task_kernel = dtask;
+    a.n_tasks = n_tasks;
+    a.next_task = dstats + 2;
+    a.code = dcode;
+    a.mems = dmems;
+    a.max_regs = max_regs;
+    a.ow_slots = ow_slots;
+    a.interval = round;
+    a.tag = owner ? shadow_next_tag(W, s) : 0;
+    a.snap = snap;
+    a.regs = dregs;
+    a.pc = dpc;
+    a.st = dst;
+    a.ow_count = dowc;
+    a.ow = dow;
+    a.log = dlog;
+    a.warp_count = dwc;
+    a.errs = derrs;
+    a.err_kernel = derrk;
+    a.err_count = dstats + 1;
+    a.err_cap = err_cap;
+    a.stop_min = dstats + 8;
+    a.stop_cnt = dstats + 8 + stops;
+    a.acc = dacc;
+    a.flags = dstats;
+    a.owner = owner;
+    if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
+    launch_batch_interp(a, grid, smem, s);
+    CK(cudaGetLastError());
+    if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], s));
+    CK(cudaMemcpyAsync(hstats, dstats, stat_words * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(acc.data(), dacc, 16ull * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hstats[0]) throw Fail{RC_E_CAPACITY, "batch log, own-write table or error log overflowed"};
+    if (g_prof.on) {
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, g_prof.ev[0], g_prof.ev[1]));
+      g_prof.launches[0]++;
+      g_prof.ms[0] += ms;
+      CK(cudaEventRecord(g_prof.ev[2], s));
     }
-    CK(cudaMemcpyAsync(rep->final_global, snap, L.GT * 4, cudaMemcpyDeviceToHost, s));
+    // ---- classification + commit over the shared cell space
+    launch_batch_commit(a, s);
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(dstats + 4);
+    LogRec *picked = W.logb.get<LogRec>(std::max<uint64_t>(logrecs, 1));
+    launch_batch_compact(a, picked, cnt, s);
+    CK(cudaMemcpyAsync(hstats + stat_words, cnt, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t m = *reinterpret_cast<uint64_t *>(hstats + stat_words);
+    rr.clear();
+    rk.clear();
+    if (m) {
+      uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(m), scan_tmp_words(m)));
+      LogRec *other = W.compact.get<LogRec>(m);
+      LogRec *sorted = sort_log(picked, other, m, bitwidth(maxN), bitwidth(keys) + bitwidth(maxN), tmp, s);
+      Layout none;
+      BatchMap bm{n, dkbase, dkgt, dklt, &rk};
+      classify_run(W, sorted, m, round, none, snap, hstats + stat_words, rr, s, &bm);
+    }
+    if (g_prof.on) {
+      CK(cudaEventRecord(g_prof.ev[3], s));
+      CK(cudaEventSynchronize(g_prof.ev[3]));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, g_prof.ev[2], g_prof.ev[3]));
+      g_prof.launches[1]++;
+      g_prof.ms[1] += ms;
+    }
+    for (size_t i = 0; i < rr.size(); i++) races[rk[i]].push_back(rr[i]);
+    const uint32_t nerr = std::min(hstats[1], err_cap);
+    if (nerr) {
+      std::vector<OutRec> e(nerr);
+      std::vector<uint32_t> ek(nerr);
+      CK(cudaMemcpyAsync(e.data(), derrs, nerr * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(ek.data(), derrk, nerr * 4, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::vector<std::vector<OutRec>> per(n);
+      for (uint32_t i = 0; i < nerr; i++) per[ek[i]].push_back(e[i]);
+      for (uint32_t k = 0; k < n; k++) {
+        if (per[k].empty()) continue;
+        std::sort(per[k].begin(), per[k].end(), [](const OutRec &x, const OutRec &y) {
+          return x.cls != y.cls ? x.cls < y.cls : x.t_a < y.t_a;
+        });
+        errors[k].insert(errors[k].end(), per[k].begin(), per[k].end());
+      }
+    }
+    // ---- per-instance barrier agreement
+    for (uint32_t k = 0; k < n; k++) {
+      if (!desc[k].active) continue;
+      const uint32_t *smin = hstats + 8 + desc[k].stop_off, *scnt = hstats + 8 + stops + desc[k].stop_off;
+      if (!barrier_agreement(round, desc[k].n_barriers, smin, scnt, errors[k])) {
+        desc[k].active = 0;
+        n_intervals[k] = round + 1;
+        active--;
+      }
+    }
   }
-  CK(cudaStreamSynchronize(s));
-  return rep;
+  for (uint32_t k = 0; k < n; k++) {
+    const BatchItem &it = items[k];
+    out[k] = make_report(races[k], errors[k], n_intervals[k], acc[2 * k], acc[2 * k + 1], it.L.GT,
+                         (it.in->flags & RC_WANT_FINAL_MEMORY) ? snap + kbase[k] : nullptr, s);
+  }
 }
 
 void check_args(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in) {
@@ -591,25 +882,41 @@ int rc_check_batch(const rc_bytecode *const *bcs, const uint32_t *groups, const 
   if (!out || (n && (!bcs || !groups || !group_size || !inputs))) return RC_E_INVALID;
   for (size_t i = 0; i < n; i++) out[i] = nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
-  size_t done = 0;
   try {
-    for (size_t i = 0; i < n; i++) check_args(bcs[i], groups[i], group_size[i], &inputs[i]);
+    std::vector<BatchItem> items;
+    items.reserve(n);
+    for (size_t i = 0; i < n; i++) {
+      check_args(bcs[i], groups[i], group_size[i], &inputs[i]);
+      items.push_back(plan_item(bcs[i], groups[i], group_size[i], &inputs[i]));
+    }
     if (g_prof.on) prof_events();
-    for (; done < n; done++) {
-      Instance I{&bcs[done]->prog, groups[done], group_size[done],
-                 (uint64_t)groups[done] * group_size[done], &inputs[done],
-                 static_cast<cudaStream_t>(inputs[done].cuda_stream)};
-      out[done] = run_instance(I);
+    // sub-batches: instances in order while the cell space stays below 2^31
+    // and the estimated workspace below the batch budget
+    const uint64_t budget = (uint64_t)48 << 30;
+    size_t i = 0;
+    while (i < n) {
+      size_t j = i;
+      uint64_t cells = 0, bytes = 0;
+      while (j < n && (j == i || (cells + items[j].L.keys < (1ull << 31) && bytes + items[j].bytes <= budget))) {
+        cells += items[j].L.keys;
+        bytes += items[j].bytes;
+        j++;
+      }
+      if (cells >= (1ull << 31) || bytes > ((uint64_t)200 << 30)) throw Fail{RC_E_CAPACITY, "instance too large for a batch"};
+      std::vector<BatchItem> sub(items.begin() + i, items.begin() + j);
+      const int strategy = g_strategy ? g_strategy : 2;
+      run_batch(sub, static_cast<cudaStream_t>(inputs[i].cuda_stream), strategy, out + i);
+      i = j;
     }
     return RC_OK;
   } catch (const Fail &f) {
-    for (size_t i = 0; i < done; i++) {
+    for (size_t i = 0; i < n; i++) {
       rc_report_free(out[i]);
       out[i] = nullptr;
     }
     return fail_code(f);
   } catch (const std::bad_alloc &) {
-    for (size_t i = 0; i < done; i++) {
+    for (size_t i = 0; i < n; i++) {
       rc_report_free(out[i]);
       out[i] = nullptr;
     }

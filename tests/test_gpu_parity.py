@@ -171,3 +171,20 @@ def test_long_program_runs_from_global_memory(rc, oracle):
     inst = W.large_kernel(7, groups=4, group_size=64, global_len=4096, local_len=256, n_stmts=3000)
     assert rc.compile(inst.src).info()["n_insn"] > 4000
     run_both(rc, oracle, inst)
+
+
+def test_batch_mixed_instances(rc, oracle):
+    """One rc_check_batch over instances of every kind (different programs,
+    shapes, barrier counts, errors, divergence): each report equals the
+    oracle's for that instance alone."""
+    insts = [W.small_kernel(s) for s in range(12)] + [W.tiny_kernel(s) for s in range(12)]
+    insts += [W.large_kernel(s, groups=3, group_size=100, global_len=4800, local_len=1600) for s in range(3)]
+    insts += [W.Instance(f"edge{i}", *EDGE[i]) for i in range(len(EDGE))]
+    want = [oracle.check(i.src, i.groups, i.group_size, i.globals) for i in insts]
+    bcs = [rc.compile(i.src) for i in insts]
+    for s in STRATEGIES:
+        rc.set_strategy(s)
+        got = rc.check_batch([(b, i.groups, i.group_size, i.globals) for b, i in zip(bcs, insts)])
+        for g, w, i in zip(got, want, insts):
+            same(g, w, f"{i.name} strategy {s}")
+    rc.set_strategy(0)
