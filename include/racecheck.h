@@ -203,6 +203,22 @@ int rc_release_workspace(void);
  * table + sort of shared cells only.  Returns RC_E_INVALID for other values. */
 int rc_set_strategy(int strategy);
 
+/* Autotuner of the classification strategy (strategy 0 above).  Per size
+ * class -- single instances by work-items and per-interval access bound,
+ * batches by warp tasks and bound -- an undecided class alternates the two
+ * exact strategies on successive intervals (or batch rounds), times each,
+ * and keeps the cheaper one after two samples of each.  Decisions persist in
+ * a JSON file: cache_path, or NULL for the default ($RC_TUNE_CACHE, else
+ * $XDG_CACHE_HOME/racecheck_autotune.json, else
+ * ~/.cache/racecheck_autotune.json), or "" for no file. */
+int rc_autotune_config(const char *cache_path);
+/* Forget every decision held in memory (the cache file is not touched). */
+int rc_autotune_reset(void);
+/* Decision for a size class: kind 0 single (a = work-items, b = accesses per
+ * work-item per interval bound), kind 1 batch (a = warp tasks, b = bound);
+ * returns 1 (sort), 2 (shadow) or 0 if undecided. */
+int rc_autotune_lookup(int kind, uint64_t a, uint64_t b);
+
 /* Kernel timing: when enabled, the library brackets its kernels with CUDA
  * events on the caller's stream and accumulates, per kernel kind, launches,
  * device milliseconds and algorithmic bytes.  kind: 0 interpreter, 1 log

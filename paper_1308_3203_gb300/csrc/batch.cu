@@ -56,6 +56,9 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_interp_kernel(BatchArg
   int32_t *owv = reinterpret_cast<int32_t *>(owk + A.ow_slots * RS);
   const uint32_t t = threadIdx.x, lane = t & 31u, lane_lt = (1u << lane) - 1u;
   const uint32_t slots = A.ow_slots;
+  // round state lives in device memory so one captured launch serves every round
+  const uint32_t interval = A.round[0], tag = A.round[1];
+  uint32_t *const owner = A.round[2] ? A.owner : nullptr;
 #define REG(i) rf[(uint32_t)(i) * RS + t]
 
   for (;;) {
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_interp_kernel(BatchArg
         if (!act) continue;
         pc++;
         if (!inb) {
-          OutRec e{A.interval, mm.z, mm.z ? wg : 0u, (uint32_t)idx, CLS_OOB, gl, ctl >> CTL_MEM_SHIFT, 0, 0, 0};
+          OutRec e{interval, mm.z, mm.z ? wg : 0u, (uint32_t)idx, CLS_OOB, gl, ctl >> CTL_MEM_SHIFT, 0, 0, 0};
           batch_err(A, k, e);
           st = TS_DEAD;
           running = false;
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_interp_kernel(BatchArg
             for (uint32_t q = slots; q < nw; q++)
               if (ow[(uint64_t)q * D.N + gl].x == key) { slot = (int32_t)q; break; }
         }
-        if (A.owner) shadow_claim(A.owner, key, cls == CC_ST, A.tag, gl);
+        if (owner) shadow_claim(owner, key, cls == CC_ST, tag, gl);
         int32_t v;
         if (cls == CC_LD) {
           if (slot < 0) v = __ldg(A.snap + key);
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_interp_kernel(BatchArg
           break;
         case CC_ASSERT:
           if (x == 0) {
-            OutRec e{A.interval, 0, 0, 0, CLS_ASSERT, gl, (uint32_t)imm, 0, 0, 0};
+            OutRec e{interval, 0, 0, 0, CLS_ASSERT, gl, (uint32_t)imm, 0, 0, 0};
             batch_err(A, k, e);
             st = TS_DEAD;
             running = false;
@@ -294,7 +297,7 @@ __global__ void batch_compact_kernel(BatchArgs A, LogRec *out, unsigned long lon
   const uint4 *src = reinterpret_cast<const uint4 *>(A.log) + D.slice_off + (uint64_t)(task - D.task_off) * D.slice;
   for (uint32_t i = threadIdx.x & 31u; i < n; i += 32) {
     const uint4 r = src[i];
-    if (A.owner && !shadow_needs_exact(A.owner, r.x, A.tag)) continue;
+    if (A.round[2] && !shadow_needs_exact(A.owner, r.x, A.round[1])) continue;
     cg::coalesced_group g = cg::coalesced_threads();
     unsigned long long base = 0;
     if (g.thread_rank() == 0) base = atomicAdd(total, (unsigned long long)g.size());
@@ -312,8 +315,10 @@ __global__ void batch_commit_kernel(BatchArgs A) {
   if (!D.active) return;
   const uint32_t gl = (task - D.task_off) * 32 + (threadIdx.x & 31u);
   if ((uint64_t)gl >= D.N) return;
+  if (!A.round[2]) return;  // sort-path round: the classifier commits every cell
   const uint32_t nw = A.ow_count[D.state_off + gl];
-  const uint32_t hi = (A.tag << 26) | gl, lo = (A.tag << 26) | (kIdMask - gl);
+  const uint32_t tag = A.round[1];
+  const uint32_t hi = (tag << 26) | gl, lo = (tag << 26) | (kIdMask - gl);
   for (uint32_t q = 0; q < nw; q++) {
     const uint2 e = A.ow[D.ow_off + (uint64_t)q * D.N + gl];
     const uint2 w = reinterpret_cast<const uint2 *>(A.owner)[2ull * e.x];
@@ -346,7 +351,7 @@ void launch_batch_compact(const BatchArgs &a, LogRec *out, unsigned long long *t
 }
 
 void launch_batch_commit(const BatchArgs &a, cudaStream_t s) {
-  if (!a.n_tasks || !a.owner) return;
+  if (!a.n_tasks) return;
   count_launch();
   batch_commit_kernel<<<(a.n_tasks + 7) / 8, 256, 0, s>>>(a);
 }

@@ -142,7 +142,8 @@ struct BatchArgs {
   uint32_t *next_task;          // persistent-grid task counter (zero before each launch)
   const Insn *code;             // all instances' bytecode, end to end
   const MemInfo *mems;          // all instances' memory tables
-  uint32_t max_regs, ow_slots, interval, tag;
+  uint32_t max_regs, ow_slots;
+  const uint32_t *round;        // device: [0] interval, [1] owner-table tag, [2] shadow path on
   int32_t *snap;
   int32_t *regs;
   uint32_t *pc, *st, *ow_count;
@@ -155,7 +156,7 @@ struct BatchArgs {
   uint32_t *stop_min, *stop_cnt;
   unsigned long long *acc;      // [2 * instances]: global, local accesses
   uint32_t *flags;
-  uint32_t *owner;              // shadow owner table over the batch's cells (nullptr: sort path)
+  uint32_t *owner;              // shadow owner table over the batch's cells
 };
 
 size_t batch_smem_bytes(uint32_t max_regs, uint32_t ow_slots);

@@ -14,7 +14,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <sys/stat.h>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -97,15 +99,16 @@ struct HostBuf {
 struct Workspace {
   DevBuf code, mems, snap, regs, pc, st, ow, loga, logb, head, runidx, sum, khead, keyidx, nrec,
       recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff, sortscr, reckern,
-      bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc;
-  HostBuf hstats, hrecs;
+      bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround;
+  HostBuf hstats, hrecs, hround, hdesc;
+  cudaStream_t bstream = nullptr;
   bool configured = false, batch_configured = false;
   uint32_t epoch = 0;
   void release_all() {
     for (DevBuf *b : {&code, &mems, &snap, &regs, &pc, &st, &ow, &loga, &logb, &head, &runidx, &sum,
                       &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
                       &owcnt, &compact, &ctacnt, &ctaoff, &sortscr, &reckern, &bdesc, &bcode,
-                      &bmems, &btask, &bkbase, &bkgt, &bklt, &berrk, &shared_acc})
+                      &bmems, &btask, &bkbase, &bkgt, &bklt, &berrk, &shared_acc, &bround})
       b->release();
     epoch = 0;
   }
@@ -125,6 +128,121 @@ Prof g_prof;
 void prof_events() {
   if (!g_prof.ev[0])
     for (auto &e : g_prof.ev) CK(cudaEventCreate(&e));
+}
+
+// ---------------------------------------------------------------- autotuner
+// Classification strategy per size class.  Both strategies are exact, so
+// an undecided class simply alternates them on successive intervals (or
+// batch rounds), timing each interval per million accesses; after two
+// samples of each the cheaper one is kept and written to a JSON cache.
+struct Tuner {
+  struct Entry {
+    int best = 0;
+    double cost[3] = {0, 0, 0};
+    int n[3] = {0, 0, 0};
+  };
+  bool loaded = false;
+  bool persist = true;
+  std::string path;
+  std::map<std::string, Entry> entries;
+
+  static std::string default_path() {
+    if (const char *e = std::getenv("RC_TUNE_CACHE")) return e;
+    if (const char *x = std::getenv("XDG_CACHE_HOME")) return std::string(x) + "/racecheck_autotune.json";
+    if (const char *h = std::getenv("HOME")) return std::string(h) + "/.cache/racecheck_autotune.json";
+    return "";
+  }
+  void load() {
+    if (loaded) return;
+    loaded = true;
+    if (path.empty()) path = default_path();
+    if (!persist || path.empty()) return;
+    FILE *f = std::fopen(path.c_str(), "rb");
+    if (!f) return;
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
+    std::fclose(f);
+    // entries look like  "single:N18:B7": {"best": 2, ...}
+    for (size_t p = 0; (p = text.find('"', p)) != std::string::npos;) {
+      const size_t q = text.find('"', p + 1);
+      if (q == std::string::npos) break;
+      const std::string key = text.substr(p + 1, q - p - 1);
+      p = q + 1;
+      if (key.rfind("single:", 0) != 0 && key.rfind("batch:", 0) != 0) continue;
+      const size_t b = text.find("\"best\":", q);
+      const size_t close = text.find('}', q);
+      if (b == std::string::npos || b > close) continue;
+      const int best = std::atoi(text.c_str() + b + 7);
+      if (best == 1 || best == 2) entries[key].best = best;
+    }
+  }
+  void save() {
+    if (!persist || path.empty()) return;
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) {  // best effort: create the cache folder
+      std::string dir = path.substr(0, slash);
+      std::string cmd_free_dir;
+      (void)cmd_free_dir;
+      mkdir(dir.c_str(), 0755);
+    }
+    const std::string tmp = path + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    std::fprintf(f, "{\n  \"racecheck_autotune\": 1,\n  \"entries\": {");
+    bool first = true;
+    for (auto &kv : entries) {
+      if (!kv.second.best) continue;
+      const Entry &e = kv.second;
+      std::fprintf(f, "%s\n    \"%s\": {\"best\": %d, \"ms_per_maccess_sort\": %.6g, \"ms_per_maccess_shadow\": %.6g}",
+                   first ? "" : ",", kv.first.c_str(), e.best, e.n[1] ? e.cost[1] / e.n[1] : 0.0,
+                   e.n[2] ? e.cost[2] / e.n[2] : 0.0);
+      first = false;
+    }
+    std::fprintf(f, "\n  }\n}\n");
+    std::fclose(f);
+    std::rename(tmp.c_str(), path.c_str());
+  }
+  int choose(const std::string &key) {
+    load();
+    Entry &e = entries[key];
+    if (e.best) return e.best;
+    return e.n[1] <= e.n[2] ? 1 : 2;
+  }
+  void record(const std::string &key, int strategy, double ms, uint64_t accesses) {
+    Entry &e = entries[key];
+    if (e.best || accesses == 0 || strategy < 1 || strategy > 2) return;
+    e.cost[strategy] += ms * 1e6 / (double)accesses;
+    e.n[strategy]++;
+    if (e.n[1] >= 2 && e.n[2] >= 2) {
+      e.best = e.cost[1] / e.n[1] <= e.cost[2] / e.n[2] ? 1 : 2;
+      save();
+    }
+  }
+};
+Tuner g_tuner;
+cudaEvent_t g_tev[2] = {nullptr, nullptr};
+
+void tuner_events() {
+  if (!g_tev[0])
+    for (auto &e : g_tev) CK(cudaEventCreate(&e));
+}
+
+uint32_t bits_of(uint64_t v) {
+  uint32_t b = 0;
+  while (v) {
+    b++;
+    v >>= 1;
+  }
+  return b;
+}
+
+std::string single_key(uint64_t N, uint64_t bound) {
+  return "single:N" + std::to_string(bits_of(N)) + ":B" + std::to_string(bits_of(bound));
+}
+std::string batch_key(uint64_t tasks, uint64_t bound) {
+  return "batch:T" + std::to_string(bits_of(tasks)) + ":B" + std::to_string(bits_of(bound));
 }
 
 // stats block layout (uint32 words)
@@ -172,12 +290,6 @@ Layout make_layout(const Program &p, const rc_input *in, uint32_t G) {
   L.keys = L.GT + (uint64_t)G * L.LT;
   if (L.keys >= 0xFFFFFFFFull) throw Fail{RC_E_INVALID, "global + local cells must stay below 2^32"};
   return L;
-}
-
-int pick_strategy(uint64_t n_log) {
-  if (g_strategy) return g_strategy;
-  (void)n_log;
-  return 2;
 }
 
 // Classify records already sorted by (cell, work-item): run reduce, per-cell
@@ -436,9 +548,10 @@ rc_report *run_instance(const Instance &I) {
   uint32_t *hstats = W.hstats.get<uint32_t>(stat_words + 8);
   CK(cudaMemsetAsync(dstats, 0, stat_words * 4, s));
 
-  const int strategy = pick_strategy(cap);
+  const std::string tkey = single_key(N, P.max_access_per_interval);
   uint32_t *owner = nullptr;
-  if (strategy == 2) owner = shadow_table(W, L.keys, s);
+  if (g_strategy != 1) owner = shadow_table(W, L.keys, s);
+  if (!g_strategy) tuner_events();
   uint32_t *warp_count = W.ctacnt.get<uint32_t>(n_slices);
   uint32_t *ow_cnt = W.owcnt.get<uint32_t>(N);
 
@@ -481,9 +594,11 @@ rc_report *run_instance(const Instance &I) {
     a.stop_cnt = dstats + ST_STOPS + nstops;
     a.acc = reinterpret_cast<unsigned long long *>(dstats + ST_ACC);
     a.flags = dstats + ST_FLAGS;
+    const int strategy = g_strategy ? g_strategy : g_tuner.choose(tkey);
     a.ow_count = ow_cnt;
-    a.owner = owner;
+    a.owner = strategy == 2 ? owner : nullptr;
     a.tag = strategy == 2 ? shadow_next_tag(W, s) : 0;
+    if (!g_strategy) CK(cudaEventRecord(g_tev[0], s));
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
     launch_interp(a, I.G, smem, s);
     CK(cudaGetLastError());
@@ -521,6 +636,13 @@ rc_report *run_instance(const Instance &I) {
       g_prof.launches[1]++;
       g_prof.ms[1] += ms;
       g_prof.bytes[1] += 12.0 * (double)(acc_g - prev_acc[0]);
+    }
+    if (!g_strategy) {  // autotuner sample: this interval's time per access
+      CK(cudaEventRecord(g_tev[1], s));
+      CK(cudaEventSynchronize(g_tev[1]));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, g_tev[0], g_tev[1]));
+      g_tuner.record(tkey, strategy, ms, (acc_g + acc_l) - (prev_acc[0] + prev_acc[1]));
     }
     prev_acc[0] = acc_g;
     prev_acc[1] = acc_l;
@@ -672,7 +794,9 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   uint32_t *hstats = W.hstats.get<uint32_t>(stat_words + 8);
   unsigned long long *dacc = reinterpret_cast<unsigned long long *>(W.shared_acc.get<uint64_t>(2ull * n));
   CK(cudaMemsetAsync(dacc, 0, 16ull * n, s));
-  uint32_t *owner = strategy == 2 ? shadow_table(W, keys, s) : nullptr;
+  uint32_t *owner = strategy != 1 ? shadow_table(W, keys, s) : W.owner.get<uint32_t>(4);
+  const std::string tkey = batch_key(n_tasks, logrecs / std::max<uint64_t>(n_tasks, 1) / 32);
+  if (!strategy) tuner_events();
   // own-write slots in shared memory (up to 8) with 4 CTAs of the interpreter per SM
   uint32_t ow_slots = 0;
   while (ow_slots < 8 && ow_slots < max_writes && batch_smem_bytes(max_regs, ow_slots + 1) <= 50 * 1024) ow_slots++;
@@ -681,95 +805,141 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
   const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((n_tasks + 7) / 8, (uint32_t)sms * 4));
+  uint32_t *dround = W.bround.get<uint32_t>(4);
+  uint32_t *hround = W.hround.get<uint32_t>(4);
+  BatchDesc *hdesc = W.hdesc.get<BatchDesc>(n);
+
+  BatchArgs a{};
+  a.desc = ddesc;
+  a.task_kernel = dtask;
+  a.n_tasks = n_tasks;
+  a.next_task = dstats + 2;
+  a.code = dcode;
+  a.mems = dmems;
+  a.max_regs = max_regs;
+  a.ow_slots = ow_slots;
+  a.round = dround;
+  a.snap = snap;
+  a.regs = dregs;
+  a.pc = dpc;
+  a.st = dst;
+  a.ow_count = dowc;
+  a.ow = dow;
+  a.log = dlog;
+  a.warp_count = dwc;
+  a.errs = derrs;
+  a.err_kernel = derrk;
+  a.err_count = dstats + 1;
+  a.err_cap = err_cap;
+  a.stop_min = dstats + 8;
+  a.stop_cnt = dstats + 8 + stops;
+  a.acc = dacc;
+  a.flags = dstats;
+  a.owner = owner;
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(dstats + 4);
+  LogRec *picked = W.logb.get<LogRec>(std::max<uint64_t>(logrecs, 1));
+
+  // One round's fixed launch sequence -- stat resets, the persistent
+  // interpreter, the owner-table commit and the compaction of the records to
+  // classify -- is captured once into a CUDA graph and replayed every round;
+  // the round number, tag and path come from device memory.
+  if (!W.bstream) CK(cudaStreamCreateWithFlags(&W.bstream, cudaStreamNonBlocking));
+  cudaStream_t bs = W.bstream;
+  {
+    cudaEvent_t ready;
+    CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    CK(cudaEventRecord(ready, s));  // inputs and set-up issued on the caller's stream
+    CK(cudaStreamWaitEvent(bs, ready, 0));
+    CK(cudaEventDestroy(ready));
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(dstats, 0, 8 * 4, bs);
+  cudaMemsetAsync(dstats + 8, 0xFF, stops * 4, bs);
+  cudaMemsetAsync(dstats + 8 + stops, 0, stops * 4, bs);
+  launch_batch_interp(a, grid, smem, bs);
+  launch_batch_commit(a, bs);
+  launch_batch_compact(a, picked, cnt, bs);
+  CK(cudaStreamEndCapture(bs, &graph));
+  CK(cudaGraphInstantiate(&exec, graph, 0));
+  struct GraphGuard {
+    cudaGraph_t g;
+    cudaGraphExec_t e;
+    ~GraphGuard() {
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
+    }
+  } guard{graph, exec};
 
   std::vector<std::vector<OutRec>> races(n), errors(n);
   std::vector<uint32_t> n_intervals(n, 0);
   uint32_t active = n;
-  std::vector<uint64_t> acc(2ull * n);
+  std::vector<uint64_t> acc(2ull * n), prev(2ull * n, 0);
   std::vector<OutRec> rr;
   std::vector<uint32_t> rk;
   for (uint32_t round = 0; active; round++) {
-    CK(cudaMemcpyAsync(ddesc, desc.data(), n * sizeof(BatchDesc), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(dstats, 0, 8 * 4, s));
-    CK(cudaMemsetAsync(dstats + 8, 0xFF, stops * 4, s));
-    CK(cudaMemsetAsync(dstats + 8 + stops, 0, stops * 4, s));
-    BatchArgs a{};
-    a.desc = ddesc;
-    a.task_kernel = dtask;
-    a.n_tasks = n_tasks;
-    a.next_task = dstats + 2;
-    a.code = dcode;
-    a.mems = dmems;
-    a.max_regs = max_regs;
-    a.ow_slots = ow_slots;
-    a.interval = round;
-    a.tag = owner ? shadow_next_tag(W, s) : 0;
-    a.snap = snap;
-    a.regs = dregs;
-    a.pc = dpc;
-    a.st = dst;
-    a.ow_count = dowc;
-    a.ow = dow;
-    a.log = dlog;
-    a.warp_count = dwc;
-    a.errs = derrs;
-    a.err_kernel = derrk;
-    a.err_count = dstats + 1;
-    a.err_cap = err_cap;
-    a.stop_min = dstats + 8;
-    a.stop_cnt = dstats + 8 + stops;
-    a.acc = dacc;
-    a.flags = dstats;
-    a.owner = owner;
-    if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
-    launch_batch_interp(a, grid, smem, s);
-    CK(cudaGetLastError());
-    if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], s));
-    CK(cudaMemcpyAsync(hstats, dstats, stat_words * 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(acc.data(), dacc, 16ull * n, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    const int strat = strategy ? strategy : g_tuner.choose(tkey);
+    std::memcpy(hdesc, desc.data(), n * sizeof(BatchDesc));
+    hround[0] = round;
+    hround[1] = strat == 2 ? shadow_next_tag(W, bs) : 0;
+    hround[2] = strat == 2 ? 1u : 0u;
+    CK(cudaMemcpyAsync(ddesc, hdesc, n * sizeof(BatchDesc), cudaMemcpyHostToDevice, bs));
+    CK(cudaMemcpyAsync(dround, hround, 16, cudaMemcpyHostToDevice, bs));
+    if (!strategy) CK(cudaEventRecord(g_tev[0], bs));
+    if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], bs));
+    CK(cudaGraphLaunch(exec, bs));
+    for (int q = 0; q < 3; q++) count_launch();  // kernels replayed by the graph
+    if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], bs));
+    CK(cudaMemcpyAsync(hstats, dstats, stat_words * 4, cudaMemcpyDeviceToHost, bs));
+    CK(cudaMemcpyAsync(acc.data(), dacc, 16ull * n, cudaMemcpyDeviceToHost, bs));
+    CK(cudaStreamSynchronize(bs));
     if (hstats[0]) throw Fail{RC_E_CAPACITY, "batch log, own-write table or error log overflowed"};
     if (g_prof.on) {
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, g_prof.ev[0], g_prof.ev[1]));
       g_prof.launches[0]++;
       g_prof.ms[0] += ms;
-      CK(cudaEventRecord(g_prof.ev[2], s));
+      CK(cudaEventRecord(g_prof.ev[2], bs));
     }
-    // ---- classification + commit over the shared cell space
-    launch_batch_commit(a, s);
-    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(dstats + 4);
-    LogRec *picked = W.logb.get<LogRec>(std::max<uint64_t>(logrecs, 1));
-    launch_batch_compact(a, picked, cnt, s);
-    CK(cudaMemcpyAsync(hstats + stat_words, cnt, 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const uint64_t m = *reinterpret_cast<uint64_t *>(hstats + stat_words);
+    // ---- exact classification of the picked records over the shared cell space
+    const uint64_t m = *reinterpret_cast<const uint64_t *>(hstats + 4);
     rr.clear();
     rk.clear();
     if (m) {
       uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(m), scan_tmp_words(m)));
       LogRec *other = W.compact.get<LogRec>(m);
-      LogRec *sorted = sort_log(picked, other, m, bitwidth(maxN), bitwidth(keys) + bitwidth(maxN), tmp, s);
+      LogRec *sorted = sort_log(picked, other, m, bitwidth(maxN), bitwidth(keys) + bitwidth(maxN), tmp, bs);
       Layout none;
       BatchMap bm{n, dkbase, dkgt, dklt, &rk};
-      classify_run(W, sorted, m, round, none, snap, hstats + stat_words, rr, s, &bm);
+      classify_run(W, sorted, m, round, none, snap, hstats + stat_words, rr, bs, &bm);
     }
     if (g_prof.on) {
-      CK(cudaEventRecord(g_prof.ev[3], s));
+      CK(cudaEventRecord(g_prof.ev[3], bs));
       CK(cudaEventSynchronize(g_prof.ev[3]));
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, g_prof.ev[2], g_prof.ev[3]));
       g_prof.launches[1]++;
       g_prof.ms[1] += ms;
     }
+    if (!strategy) {
+      CK(cudaEventRecord(g_tev[1], bs));
+      CK(cudaEventSynchronize(g_tev[1]));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, g_tev[0], g_tev[1]));
+      uint64_t done = 0;
+      for (size_t q = 0; q < acc.size(); q++) done += acc[q] - prev[q];
+      g_tuner.record(tkey, strat, ms, done);
+    }
+    prev = acc;
     for (size_t i = 0; i < rr.size(); i++) races[rk[i]].push_back(rr[i]);
     const uint32_t nerr = std::min(hstats[1], err_cap);
     if (nerr) {
       std::vector<OutRec> e(nerr);
       std::vector<uint32_t> ek(nerr);
-      CK(cudaMemcpyAsync(e.data(), derrs, nerr * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(ek.data(), derrk, nerr * 4, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      CK(cudaMemcpyAsync(e.data(), derrs, nerr * sizeof(OutRec), cudaMemcpyDeviceToHost, bs));
+      CK(cudaMemcpyAsync(ek.data(), derrk, nerr * 4, cudaMemcpyDeviceToHost, bs));
+      CK(cudaStreamSynchronize(bs));
       std::vector<std::vector<OutRec>> per(n);
       for (uint32_t i = 0; i < nerr; i++) per[ek[i]].push_back(e[i]);
       for (uint32_t k = 0; k < n; k++) {
@@ -791,6 +961,7 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
       }
     }
   }
+  s = bs;  // final memories are read on the batch stream
   for (uint32_t k = 0; k < n; k++) {
     const BatchItem &it = items[k];
     out[k] = make_report(races[k], errors[k], n_intervals[k], acc[2 * k], acc[2 * k + 1], it.L.GT,
@@ -904,8 +1075,7 @@ int rc_check_batch(const rc_bytecode *const *bcs, const uint32_t *groups, const 
       }
       if (cells >= (1ull << 31) || bytes > ((uint64_t)200 << 30)) throw Fail{RC_E_CAPACITY, "instance too large for a batch"};
       std::vector<BatchItem> sub(items.begin() + i, items.begin() + j);
-      const int strategy = g_strategy ? g_strategy : 2;
-      run_batch(sub, static_cast<cudaStream_t>(inputs[i].cuda_stream), strategy, out + i);
+      run_batch(sub, static_cast<cudaStream_t>(inputs[i].cuda_stream), g_strategy, out + i);
       i = j;
     }
     return RC_OK;
@@ -983,6 +1153,30 @@ int rc_set_strategy(int strategy) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_strategy = strategy;
   return RC_OK;
+}
+
+int rc_autotune_config(const char *cache_path) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_tuner.entries.clear();
+  g_tuner.loaded = false;
+  g_tuner.persist = !(cache_path && cache_path[0] == 0);
+  g_tuner.path = cache_path ? cache_path : "";
+  return RC_OK;
+}
+
+int rc_autotune_reset(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_tuner.entries.clear();
+  g_tuner.loaded = true;  // do not re-read the file
+  return RC_OK;
+}
+
+int rc_autotune_lookup(int kind, uint64_t a, uint64_t b) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_tuner.load();
+  const std::string key = kind == 0 ? single_key(a, b) : batch_key(a, b);
+  auto it = g_tuner.entries.find(key);
+  return it == g_tuner.entries.end() ? 0 : it->second.best;
 }
 
 int rc_profile_enable(int on) {

@@ -94,6 +94,12 @@ def load() -> ctypes.CDLL:
         lib.rc_sort_accesses.restype = c_int
         lib.rc_sort_accesses_noalloc.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, vp]
         lib.rc_sort_accesses_noalloc.restype = c_int
+        lib.rc_autotune_config.argtypes = [ctypes.c_char_p]
+        lib.rc_autotune_config.restype = c_int
+        lib.rc_autotune_reset.argtypes = []
+        lib.rc_autotune_reset.restype = c_int
+        lib.rc_autotune_lookup.argtypes = [c_int, ctypes.c_uint64, ctypes.c_uint64]
+        lib.rc_autotune_lookup.restype = c_int
         lib.rc_kernel_launches.argtypes = []
         lib.rc_kernel_launches.restype = ctypes.c_uint64
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
@@ -290,3 +296,17 @@ def sort_accesses_noalloc(records_in, records_out, cell_bits: int, item_bits: in
                                          ctypes.c_void_p(int(stream) if stream else 0))
     if rc:
         raise RaceCheckError(rc, load().rc_strerror(rc).decode())
+
+
+def autotune_config(cache_path=None) -> None:
+    """Autotuner cache file (None: default location, "": keep decisions in memory only)."""
+    load().rc_autotune_config(None if cache_path is None else cache_path.encode())
+
+
+def autotune_reset() -> None:
+    load().rc_autotune_reset()
+
+
+def autotune_lookup(kind: int, a: int, b: int) -> int:
+    """Decided strategy for a size class (0 undecided, 1 sort, 2 shadow)."""
+    return int(load().rc_autotune_lookup(kind, a, b))

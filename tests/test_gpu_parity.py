@@ -188,3 +188,34 @@ def test_batch_mixed_instances(rc, oracle):
         for g, w, i in zip(got, want, insts):
             same(g, w, f"{i.name} strategy {s}")
     rc.set_strategy(0)
+
+
+def test_autotuner_decides_and_persists(rc, oracle, tmp_path):
+    """Strategy 0 alternates both exact strategies per interval until it has
+    two samples of each, then keeps the cheaper one and writes it to the
+    cache; reports stay identical throughout."""
+    cache = str(tmp_path / "tune.json")
+    rc.autotune_config(cache)
+    rc.set_strategy(0)
+    inst = W.large_kernel(3, groups=16, group_size=256, global_len=65536, local_len=4096)
+    want = oracle.check(inst.src, inst.groups, inst.group_size, inst.globals)
+    bc = rc.compile(inst.src)
+    bound = bc.info()["max_access_per_interval"]
+    assert rc.autotune_lookup(0, inst.n_threads, bound) == 0
+    same(rc.check(bc, inst.groups, inst.group_size, inst.globals), want)  # 9 intervals: decides
+    best = rc.autotune_lookup(0, inst.n_threads, bound)
+    assert best in (1, 2)
+    same(rc.check(bc, inst.groups, inst.group_size, inst.globals), want)
+    assert '"best": %d' % best in open(cache).read()
+    rc.autotune_reset()
+    assert rc.autotune_lookup(0, inst.n_threads, bound) == 0
+    rc.autotune_config(cache)  # reload from the file
+    assert rc.autotune_lookup(0, inst.n_threads, bound) == best
+    # batches decide per round the same way
+    insts = [W.small_kernel(s, n_barriers=3) for s in range(20)]
+    wants = [oracle.check(i.src, i.groups, i.group_size, i.globals) for i in insts]
+    for _ in range(2):
+        got = rc.check_batch([(rc.compile(i.src), i.groups, i.group_size, i.globals) for i in insts])
+        for g, w, i in zip(got, wants, insts):
+            same(g, w, i.name)
+    rc.autotune_config("")
