@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--strategy", type=int, default=0, help="0 auto, 1 sort, 2 shadow")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batch-kernels", type=int, default=10_000,
+                   help="size of the batched-checking measurement (0 skips it)")
     return p.parse_args()
 
 
@@ -143,6 +145,24 @@ def cpu_baseline():
     return {"value": acc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"same program and input, first {SAMPLE_GROUPS} of 1024 groups, "
                       f"{n} run(s) in {dt:.1f} s, single-threaded"}
+
+
+def batch_leg(rc, W, n_kernels):
+    """Batched checking of n uneven kernels in one rc_check_batch call."""
+    insts = W.batch_kernels(0, n_kernels, processes=min(16, os.cpu_count() or 1))
+    items = [(rc.compile(i.src), i.groups, i.group_size, i.globals) for i in insts]
+    rc.check_batch(items[:64], want_final=False)  # warm-up (and autotuner exploration)
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    got = rc.check_batch(items, want_final=False)
+    dt = time.perf_counter() - t0
+    acc = sum(g["n_access"] for g in got)
+    return {"workload": f"{n_kernels} kernels: group size log-uniform 32-1024, 1-64 groups, "
+                        "16-512 statements, 0-8 barriers, global int32 arrays 1K-1M",
+            "kernels_per_s": n_kernels / dt, "accesses_per_s": acc / dt, "seconds": dt,
+            "accesses": acc, "timing": "host wall clock around rc_check_batch (host inputs, "
+                                      "H2D and report D2H included)"}
 
 
 def main():
@@ -260,6 +280,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if args.batch_kernels > 0:
+        out["batch"] = batch_leg(rc, W, args.batch_kernels)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:

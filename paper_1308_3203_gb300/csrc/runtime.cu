@@ -508,8 +508,15 @@ rc_report *run_instance(const Instance &I) {
   const uint64_t cap = (uint64_t)n_slices * slice;     // >= N * bound: the log cannot overflow
   const uint64_t capw = std::max<uint64_t>(P.max_write_per_interval, 1);
   if (cap >= 0xFFFFFFFFull) throw Fail{RC_E_CAPACITY, "interval log bound exceeds 2^32 records"};
-  const uint64_t need = cap * sizeof(LogRec) * 2 + cap * (sizeof(Summary) + 24) + N * capw * 8;
-  if (need > (uint64_t)200 << 30) throw Fail{RC_E_CAPACITY, "instance needs more than 200 GiB of workspace"};
+  // the sort path also needs a summary and index arrays per record; when that
+  // would not fit, every interval takes the shadow path (only the records of
+  // shared written cells are sorted)
+  const uint64_t mem_budget = (uint64_t)200 << 30;
+  const uint64_t base_need = cap * sizeof(LogRec) * 2 + N * (capw * 8 + 4ull * P.n_regs + 12) + L.keys * 20;
+  const bool sort_fits = base_need + cap * (sizeof(Summary) + 24) <= mem_budget;
+  if (base_need > mem_budget) throw Fail{RC_E_CAPACITY, "instance needs more than 200 GiB of workspace"};
+  const int fixed_strategy = g_strategy ? g_strategy : (sort_fits ? 0 : 2);
+  if (fixed_strategy == 1 && !sort_fits) throw Fail{RC_E_CAPACITY, "the sort path does not fit this instance"};
 
   // ---- set-up: program, memory snapshot, work-item state
   Insn *dcode = W.code.get<Insn>(P.code.size());
@@ -550,8 +557,8 @@ rc_report *run_instance(const Instance &I) {
 
   const std::string tkey = single_key(N, P.max_access_per_interval);
   uint32_t *owner = nullptr;
-  if (g_strategy != 1) owner = shadow_table(W, L.keys, s);
-  if (!g_strategy) tuner_events();
+  if (fixed_strategy != 1) owner = shadow_table(W, L.keys, s);
+  if (!fixed_strategy) tuner_events();
   uint32_t *warp_count = W.ctacnt.get<uint32_t>(n_slices);
   uint32_t *ow_cnt = W.owcnt.get<uint32_t>(N);
 
@@ -594,11 +601,11 @@ rc_report *run_instance(const Instance &I) {
     a.stop_cnt = dstats + ST_STOPS + nstops;
     a.acc = reinterpret_cast<unsigned long long *>(dstats + ST_ACC);
     a.flags = dstats + ST_FLAGS;
-    const int strategy = g_strategy ? g_strategy : g_tuner.choose(tkey);
+    const int strategy = fixed_strategy ? fixed_strategy : g_tuner.choose(tkey);
     a.ow_count = ow_cnt;
     a.owner = strategy == 2 ? owner : nullptr;
     a.tag = strategy == 2 ? shadow_next_tag(W, s) : 0;
-    if (!g_strategy) CK(cudaEventRecord(g_tev[0], s));
+    if (!fixed_strategy) CK(cudaEventRecord(g_tev[0], s));
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
     launch_interp(a, I.G, smem, s);
     CK(cudaGetLastError());
@@ -637,7 +644,7 @@ rc_report *run_instance(const Instance &I) {
       g_prof.ms[1] += ms;
       g_prof.bytes[1] += 12.0 * (double)(acc_g - prev_acc[0]);
     }
-    if (!g_strategy) {  // autotuner sample: this interval's time per access
+    if (!fixed_strategy) {  // autotuner sample: this interval's time per access
       CK(cudaEventRecord(g_tev[1], s));
       CK(cudaEventSynchronize(g_tev[1]));
       float ms = 0;

@@ -130,8 +130,7 @@ def small_kernel(seed: int, group_size: int = 64, groups: int = 1, n_stmts: int 
     return Instance(f"small-s{seed}", src, groups, group_size, [A])
 
 
-def batch_kernels(seed: int, n_kernels: int) -> list:
-    """Config-3 batch: uneven shapes, config-1 statement/index distributions."""
+def _batch_params(seed: int, n_kernels: int) -> list:
     rng = np.random.default_rng([3, seed])
     out = []
     for k in range(n_kernels):
@@ -141,11 +140,28 @@ def batch_kernels(seed: int, n_kernels: int) -> list:
         n_stmts = int(rng.integers(16, 513))
         n_bar = int(rng.integers(0, 9))
         L = int(round(math.exp(rng.uniform(math.log(1024), math.log(1 << 20)))))
-        inst = small_kernel(int(rng.integers(1 << 31)), group_size=S, groups=G, n_stmts=n_stmts,
-                            n_barriers=n_bar, L=L)
-        inst.name = f"batch-s{seed}-k{k}"
-        out.append(inst)
+        out.append((f"batch-s{seed}-k{k}", int(rng.integers(1 << 31)), S, G, n_stmts, n_bar, L))
     return out
+
+
+def _batch_one(p):
+    name, kseed, S, G, n_stmts, n_bar, L = p
+    inst = small_kernel(kseed, group_size=S, groups=G, n_stmts=n_stmts, n_barriers=n_bar, L=L)
+    inst.name = name
+    return inst
+
+
+def batch_kernels(seed: int, n_kernels: int, processes: int = 0) -> list:
+    """Config-3 batch: uneven shapes, config-1 statement/index distributions.
+
+    processes > 1 builds the kernels in a spawn-started process pool (the
+    parameters are drawn first, so the result does not depend on it)."""
+    params = _batch_params(seed, n_kernels)
+    if processes > 1 and n_kernels > 64:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            return pool.map(_batch_one, params, chunksize=64)
+    return [_batch_one(p) for p in params]
 
 
 # ----------------------------------------------------------------------------
