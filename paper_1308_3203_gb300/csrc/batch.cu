@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_interp_kernel(BatchArg
           continue;
         }
         const uint32_t key = (mm.z ? lbase : (uint32_t)D.key_base) + mm.y + (uint32_t)idx;
+        if (owner) shadow_claim_warp(owner, logging, key, cls == CC_ST, tag, gl, lane);  // lanes here = logging
         const uint64_t bit = bbloom(key);
         int32_t slot = -1;
         if (bloom & bit) {
@@ -187,7 +188,6 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_interp_kernel(BatchArg
             for (uint32_t q = slots; q < nw; q++)
               if (ow[(uint64_t)q * D.N + gl].x == key) { slot = (int32_t)q; break; }
         }
-        if (owner) shadow_claim(owner, key, cls == CC_ST, tag, gl);
         int32_t v;
         if (cls == CC_LD) {
           if (slot < 0) v = __ldg(A.snap + key);
@@ -261,10 +261,17 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_interp_kernel(BatchArg
       }
     }
     // ---- end of this warp task
-    if (st == TS_BARRIER || (st == TS_EXIT && ran)) {
-      const uint32_t stop = st == TS_BARRIER ? (uint32_t)__ldg(code + pc).y : D.n_barriers;
-      atomicMin(&A.stop_min[D.stop_off + stop], gl);
-      atomicAdd(&A.stop_cnt[D.stop_off + stop], 1u);
+    {  // stop points, one pair of atomics per group of lanes at the same one
+      const bool stopping = st == TS_BARRIER || (st == TS_EXIT && ran);
+      const uint32_t smask = __ballot_sync(lanes, stopping);
+      if (stopping) {
+        const uint32_t stop = st == TS_BARRIER ? (uint32_t)__ldg(code + pc).y : D.n_barriers;
+        const uint32_t g = __match_any_sync(smask, stop);
+        if (lane == (uint32_t)(__ffs(g) - 1)) {
+          atomicMin(&A.stop_min[D.stop_off + stop], gl);
+          atomicAdd(&A.stop_cnt[D.stop_off + stop], (uint32_t)__popc(g));
+        }
+      }
     }
     A.st[D.state_off + gl] = st;
     A.pc[D.state_off + gl] = pc;

@@ -78,11 +78,20 @@ struct InterpArgs {
 // empty; the table is cleared when the tag wraps.  Claims are fire-and-forget
 // reductions: no round trip on the interpreter's critical path.
 constexpr uint32_t kIdMask = (1u << 26) - 1;
-__device__ __forceinline__ void shadow_claim(uint32_t *owner, uint32_t key, bool write, uint32_t tag,
-                                             uint32_t gtid) {
+// Warp-aggregated claim, called by exactly the lanes in `mask` (lane
+// `lane` claiming cell `key` for work-item `id`; ids grow by one per lane
+// within a warp).  Lanes on the same cell form one group whose lowest lane
+// issues the two reductions for the group's largest and smallest id, so a
+// cell that a whole warp touches costs one pair of reductions, not 32:
+// same-address reductions serialise in L2.
+__device__ __forceinline__ void shadow_claim_warp(uint32_t *owner, uint32_t mask, uint32_t key, bool write,
+                                                  uint32_t tag, uint32_t id, uint32_t lane) {
+  const uint32_t g = __match_any_sync(mask, key);
+  if (lane != (uint32_t)(__ffs(g) - 1)) return;
+  const uint32_t hi = 31u - __clz(g);
   uint32_t *w = owner + 4ull * key + (write ? 0 : 2);
-  atomicMax(w, (tag << 26) | gtid);
-  atomicMax(w + 1, (tag << 26) | (kIdMask - gtid));
+  atomicMax(w, (tag << 26) | (id + (hi - lane)));
+  atomicMax(w + 1, (tag << 26) | (kIdMask - id));
 }
 
 // Cells that need the exact (sorted) classification: written by two or more

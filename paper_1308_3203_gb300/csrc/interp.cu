@@ -185,6 +185,8 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
         continue;
       }
       const uint32_t key = (m.space ? lbase : 0u) + m.base + (uint32_t)idx;
+      // the lanes still here are exactly those in `logging`
+      if (A.owner) shadow_claim_warp(A.owner, logging, key, cls == CC_ST, A.tag, gtid, tid & 31u);
       // own-write table: the first `slots` distinct cells in shared memory, the rest in global
       const uint64_t bit = bloom_bit(key);
       int32_t slot = -1;
@@ -196,7 +198,6 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
           for (uint32_t k = slots; k < nw; k++)
             if (A.ow[(uint64_t)k * A.ow_stride + lt].x == key) { slot = (int32_t)k; break; }
       }
-      if (A.owner) shadow_claim(A.owner, key, cls == CC_ST, A.tag, gtid);
       int32_t v;
       if (cls == CC_LD) {
         if (slot < 0) v = __ldg(A.snap + key);
@@ -270,11 +271,70 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
     }
   }
 #undef REG
-  if (st == TS_BARRIER || (st == TS_EXIT && ran)) {
-    // stop point: barrier ordinal, or n_barriers for the exit
-    const uint32_t stop = st == TS_BARRIER ? (uint32_t)(kConst ? c_code[pc].y : __ldg(code + pc).y) : A.n_barriers;
-    atomicMin(&A.stop_min[stop], gtid);
-    atomicAdd(&A.stop_cnt[stop], 1u);
+  // Stop points (barrier ordinal, or n_barriers for the exit), reduced over
+  // the CTA before they reach the kernel-wide table: every work-item of the
+  // kernel reports one, and same-address atomics serialise in L2.  Each
+  // warp folds its lanes by stop point; thread 0 folds the warps' entries.
+  __shared__ uint32_t s_stop[32], s_min[32], s_cnt[32], s_acc[2][32];
+  {
+    // access counters of the warp (global, local)
+    const uint32_t sg = __reduce_add_sync(lanes, seq - nloc), sl = __reduce_add_sync(lanes, nloc);
+    if ((tid & 31u) == 0) {
+      s_acc[0][warp] = sg;
+      s_acc[1][warp] = sl;
+    }
+    const bool stopping = st == TS_BARRIER || (st == TS_EXIT && ran);
+    const uint32_t smask = __ballot_sync(lanes, stopping);
+    const uint32_t lane = tid & 31u;
+    uint32_t stop = kNone, gmin = 0, gcnt = 0;
+    if (stopping) {
+      stop = st == TS_BARRIER ? (uint32_t)(kConst ? c_code[pc].y : __ldg(code + pc).y) : A.n_barriers;
+      const uint32_t g = __match_any_sync(smask, stop);
+      if (g != smask) {  // several stop points in this warp: each group reports its own
+        if (lane == (uint32_t)(__ffs(g) - 1)) {
+          atomicMin(&A.stop_min[stop], gtid);
+          atomicAdd(&A.stop_cnt[stop], (uint32_t)__popc(g));
+        }
+        stop = kNone;
+      }
+      gmin = gtid;  // at the lowest stopping lane: the warp's smallest work-item
+      gcnt = __popc(g);
+    }
+    const uint32_t leader = smask ? (uint32_t)(__ffs(smask) - 1) : 0u;
+    if (lane == leader) {
+      s_stop[warp] = smask ? stop : kNone;
+      s_min[warp] = gmin;
+      s_cnt[warp] = gcnt;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t nwarps = (S + 31u) / 32u;
+    unsigned long long cg = 0, cl = 0;
+    for (uint32_t w = 0; w < nwarps; w++) {
+      cg += s_acc[0][w];
+      cl += s_acc[1][w];
+    }
+    if (cg) atomicAdd(&A.acc[0], cg);
+    if (cl) atomicAdd(&A.acc[1], cl);
+    uint32_t cur = kNone, cmin = 0, ccnt = 0;
+    for (uint32_t w = 0; w < nwarps; w++) {
+      if (s_stop[w] == kNone) continue;
+      if (s_stop[w] != cur) {
+        if (cur != kNone) {
+          atomicMin(&A.stop_min[cur], cmin);
+          atomicAdd(&A.stop_cnt[cur], ccnt);
+        }
+        cur = s_stop[w];
+        cmin = s_min[w];
+        ccnt = 0;
+      }
+      ccnt += s_cnt[w];
+    }
+    if (cur != kNone) {
+      atomicMin(&A.stop_min[cur], cmin);
+      atomicAdd(&A.stop_cnt[cur], ccnt);
+    }
   }
   A.st[gtid] = st;
   A.pc[gtid] = pc;
@@ -286,13 +346,6 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
   }
   if (st == TS_BARRIER) {
     for (uint32_t r = kBuiltinRegs; r < A.n_regs; r++) A.regs[(uint64_t)r * N + gtid] = rf[r * S + tid];
-  }
-  // access counters: one atomic per warp
-  __syncwarp(lanes);
-  const uint32_t sg = __reduce_add_sync(lanes, seq - nloc), sl = __reduce_add_sync(lanes, nloc);
-  if ((tid & 31u) == 0) {
-    if (sg) atomicAdd(&A.acc[0], (unsigned long long)sg);
-    if (sl) atomicAdd(&A.acc[1], (unsigned long long)sl);
   }
   if ((tid & 31u) == 0)
     A.warp_count[(uint64_t)blockIdx.x * A.warps_per_cta + warp] = wfill < A.warp_slice ? wfill : (uint32_t)A.warp_slice;
