@@ -78,27 +78,52 @@ __global__ void run_reduce_kernel(const LogRec *r, uint64_t n, const uint32_t *h
   khead[k] = (i == 0 || r[i - 1].key != f.key) ? 1u : 0u;
 }
 
-struct CellResult {
-  uint32_t n_readers, n_writers, n_acc;
-  uint32_t ww_cls, ww_a, ww_b;  // ww_cls 0 = none
-  uint32_t rw_a, rw_b;          // rw_a kNone = none
-  bool wrote;
-  int32_t commit;
-};
-
 // uniform value of a range, or "mixed"
 struct Uni {
   bool mixed;
   int32_t v;
 };
 __device__ __forceinline__ bool same(const Uni &a, const Uni &b) { return !a.mixed && !b.mixed && a.v == b.v; }
+__device__ __forceinline__ Uni written(const Summary &s) { return Uni{s.wmin != s.wmax, s.wmin}; }
 
+// What decides a cell's witnesses: the first two writers w1, w2 (their
+// written ranges u1, u2, w1's last value l1); tb: first writer after w1
+// whose last value differs from l1; d1, d2: first two writers after w1
+// whose range is not w1's single value; e2: first writer after w2 whose
+// range is not w2's single value.
+struct CellVals {
+  uint32_t w1, w2, tb, d1, d2, e2;
+  Uni u1, u2;
+  int32_t l1;
+};
+
+// The smallest writer j != r whose writes conflict with what reader s
+// observed (kNone if none), from the cell's candidates.
+__device__ __forceinline__ uint32_t reader_conflict(const Summary &s, const CellVals &v) {
+  const uint32_t r = s.gtid;
+  if (s.rmin != s.rmax) return v.w1 != r ? v.w1 : v.w2;  // observed several values
+  const Uni o{false, s.rmin};
+  if (!same(v.u1, o)) {
+    if (v.w1 != r) return v.w1;
+    if (v.w2 == kNone) return kNone;
+    return !same(v.u2, o) ? v.w2 : v.e2;
+  }
+  return v.d1 != r ? v.d1 : v.d2;
+}
+
+__device__ __forceinline__ void set_ww(CellResult &c, const CellVals &v) {
+  if (c.n_writers >= 2) {
+    c.ww_cls = v.tb != kNone ? CLS_WW_RACE : CLS_WW_BENIGN;
+    c.ww_a = v.w1;
+    c.ww_b = v.tb != kNone ? v.tb : v.w2;
+  }
+}
+
+// One thread walks the cell's summaries [b, end) in work-item order.
 __device__ CellResult classify_cell(const Summary *sum, uint64_t b, uint64_t nsum) {
   CellResult c{};
   const uint32_t key = sum[b].key;
-  uint32_t w1 = kNone, w2 = kNone, tb = kNone, d1 = kNone, d2 = kNone, e2 = kNone;
-  Uni u1{true, 0}, u2{true, 0};
-  int32_t l1 = 0;
+  CellVals v{kNone, kNone, kNone, kNone, kNone, kNone, {true, 0}, {true, 0}, 0};
   uint64_t e = b;
   for (; e < nsum && sum[e].key == key; e++) {  // pass 1: counts and writer candidates
     const Summary s = sum[e];
@@ -106,54 +131,36 @@ __device__ CellResult classify_cell(const Summary *sum, uint64_t b, uint64_t nsu
     if (s.meta & kMetaRead) c.n_readers++;
     if (!(s.meta & kMetaWrite)) continue;
     c.n_writers++;
-    const Uni u{s.wmin != s.wmax, s.wmin};
-    if (w1 == kNone) {
-      w1 = s.gtid;
-      u1 = u;
-      l1 = s.wlast;
+    const Uni u = written(s);
+    if (v.w1 == kNone) {
+      v.w1 = s.gtid;
+      v.u1 = u;
+      v.l1 = s.wlast;
     } else {
-      if (w2 == kNone) {
-        w2 = s.gtid;
-        u2 = u;
-      } else if (e2 == kNone && !same(u, u2)) {
-        e2 = s.gtid;
+      if (v.w2 == kNone) {
+        v.w2 = s.gtid;
+        v.u2 = u;
+      } else if (v.e2 == kNone && !same(u, v.u2)) {
+        v.e2 = s.gtid;
       }
-      if (tb == kNone && s.wlast != l1) tb = s.gtid;
-      if (!u1.mixed && !same(u, u1)) {
-        if (d1 == kNone) d1 = s.gtid;
-        else if (d2 == kNone) d2 = s.gtid;
+      if (v.tb == kNone && s.wlast != v.l1) v.tb = s.gtid;
+      if (!v.u1.mixed && !same(u, v.u1)) {
+        if (v.d1 == kNone) v.d1 = s.gtid;
+        else if (v.d2 == kNone) v.d2 = s.gtid;
       }
     }
-    c.wrote = true;
+    c.wrote = 1;
     c.commit = s.wlast;  // ascending order: ends with the highest writer
   }
-  if (c.n_writers >= 2) {
-    c.ww_cls = tb != kNone ? CLS_WW_RACE : CLS_WW_BENIGN;
-    c.ww_a = w1;
-    c.ww_b = tb != kNone ? tb : w2;
-  }
+  set_ww(c, v);
   c.rw_a = kNone;
   if (c.n_writers > 0 && c.n_readers > 0) {
     for (uint64_t k = b; k < e; k++) {  // pass 2: first reader with a conflict
       const Summary s = sum[k];
       if (!(s.meta & kMetaRead)) continue;
-      const uint32_t r = s.gtid;
-      uint32_t j;
-      if (s.rmin != s.rmax) {
-        j = w1 != r ? w1 : w2;
-      } else {
-        const Uni o{false, s.rmin};
-        if (!same(u1, o)) {
-          if (w1 != r) j = w1;
-          else if (w2 == kNone) j = kNone;
-          else if (!same(u2, o)) j = w2;
-          else j = e2;
-        } else {
-          j = d1 != r ? d1 : d2;
-        }
-      }
+      const uint32_t j = reader_conflict(s, v);
       if (j != kNone) {
-        c.rw_a = r;
+        c.rw_a = s.gtid;
         c.rw_b = j;
         break;
       }
@@ -198,10 +205,23 @@ __device__ __forceinline__ OutRec make_rec(const ClassifyArgs &a, uint32_t key, 
   return o;
 }
 
+__device__ __forceinline__ void emit_cell(const ClassifyArgs &a, uint32_t key, const CellResult &c, uint32_t p,
+                                          OutRec *out) {
+  if (c.ww_cls) {
+    out[p] = make_rec(a, key, c.ww_cls, c.ww_a, c.ww_b, c, p);
+    p++;
+  }
+  if (c.rw_a != kNone) out[p] = make_rec(a, key, CLS_RW_RACE, c.rw_a, c.rw_b, c, p);
+}
+
 __global__ void key_classify_kernel(const Summary *sum, uint64_t nsum, const uint32_t *khead,
                                     const uint32_t *keyidx, uint32_t *nrec, ClassifyArgs a) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsum || !khead[i]) return;
+  if (i + kBigCell < nsum && sum[i + kBigCell].key == sum[i].key) {  // a large cell: one CTA's work
+    a.big[atomicAdd(a.nbig, 1u)] = (uint32_t)i;
+    return;
+  }
   const CellResult c = classify_cell(sum, i, nsum);
   if (c.wrote) a.snap[sum[i].key] = c.commit;
   nrec[keyidx[i]] = (c.ww_cls ? 1u : 0u) + (c.rw_a != kNone ? 1u : 0u);
@@ -214,14 +234,185 @@ __global__ void key_emit_kernel(const Summary *sum, uint64_t nsum, const uint32_
   if (i >= nsum || !khead[i]) return;
   const uint32_t k = keyidx[i];
   if (nrec[k] == 0) return;
-  const CellResult c = classify_cell(sum, i, nsum);
-  uint32_t p = recoff[k];
-  const uint32_t key = sum[i].key;
-  if (c.ww_cls) {
-    out[p] = make_rec(a, key, c.ww_cls, c.ww_a, c.ww_b, c, p);
-    p++;
+  if (i + kBigCell < nsum && sum[i + kBigCell].key == sum[i].key) return;  // emitted by big_emit
+  emit_cell(a, sum[i].key, classify_cell(sum, i, nsum), recoff[k], out);
+}
+
+// ---- large cells: one CTA per cell, three sweeps over its summaries.
+// Every candidate is "the first summary (in work-item order) with a
+// property", so each thread keeps the first offsets it meets in its stride
+// and the block takes the minimum: the same witnesses as classify_cell.
+constexpr int kBigThreads = 256;
+
+__device__ __forceinline__ void two_min(uint32_t &a1, uint32_t &a2, uint32_t b1, uint32_t b2) {
+  const uint32_t m1 = min(a1, b1);
+  a2 = min(max(a1, b1), min(a2, b2));  // a1 <= a2 and b1 <= b2
+  a1 = m1;
+}
+
+// block-wide reductions; every thread gets the result (sh: 2 * 32 words)
+__device__ __forceinline__ uint32_t block_sum(uint32_t x, uint32_t *sh) {
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  __syncthreads();
+  if ((threadIdx.x & 31u) == 0) sh[threadIdx.x >> 5] = x;
+  __syncthreads();
+  uint32_t t = 0;
+  for (uint32_t w = 0; w < blockDim.x / 32u; w++) t += sh[w];
+  return t;
+}
+__device__ __forceinline__ uint32_t block_min(uint32_t x, uint32_t *sh) {
+  x = __reduce_min_sync(0xFFFFFFFFu, x);
+  __syncthreads();
+  if ((threadIdx.x & 31u) == 0) sh[threadIdx.x >> 5] = x;
+  __syncthreads();
+  uint32_t t = kNone;
+  for (uint32_t w = 0; w < blockDim.x / 32u; w++) t = min(t, sh[w]);
+  return t;
+}
+__device__ __forceinline__ uint32_t block_max(uint32_t x, uint32_t *sh) {
+  x = __reduce_max_sync(0xFFFFFFFFu, x);
+  __syncthreads();
+  if ((threadIdx.x & 31u) == 0) sh[threadIdx.x >> 5] = x;
+  __syncthreads();
+  uint32_t t = 0;
+  for (uint32_t w = 0; w < blockDim.x / 32u; w++) t = max(t, sh[w]);
+  return t;
+}
+__device__ __forceinline__ void block_two_min(uint32_t &a1, uint32_t &a2, uint32_t *sh) {
+  for (int o = 16; o; o >>= 1) {
+    const uint32_t b1 = __shfl_xor_sync(0xFFFFFFFFu, a1, o), b2 = __shfl_xor_sync(0xFFFFFFFFu, a2, o);
+    two_min(a1, a2, b1, b2);
   }
-  if (c.rw_a != kNone) out[p] = make_rec(a, key, CLS_RW_RACE, c.rw_a, c.rw_b, c, p);
+  __syncthreads();
+  if ((threadIdx.x & 31u) == 0) {
+    sh[threadIdx.x >> 5] = a1;
+    sh[32 + (threadIdx.x >> 5)] = a2;
+  }
+  __syncthreads();
+  a1 = kNone;
+  a2 = kNone;
+  for (uint32_t w = 0; w < blockDim.x / 32u; w++) two_min(a1, a2, sh[w], sh[32 + w]);
+}
+
+__global__ void __launch_bounds__(kBigThreads) big_classify_kernel(const Summary *sum, uint64_t nsum,
+                                                                   const uint32_t *keyidx, uint32_t *nrec,
+                                                                   ClassifyArgs a) {
+  __shared__ uint32_t sh[64];
+  __shared__ CellVals sv;
+  __shared__ int32_t s_commit;
+  const uint32_t t = threadIdx.x, nt = blockDim.x;
+  const uint32_t nbig = *a.nbig;
+  for (uint32_t q = blockIdx.x; q < nbig; q += gridDim.x) {
+    const uint64_t b = a.big[q];
+    const uint32_t key = sum[b].key;
+    // pass 1: extent, counts, first two writers, last writer
+    uint32_t nacc = 0, nr = 0, nw = 0, f1 = kNone, f2 = kNone, lastw = 0, endo = kNone;
+    for (uint64_t base = b;; base += nt) {
+      const uint64_t i = base + t;
+      const bool in = i < nsum && sum[i].key == key;
+      if (in) {
+        const Summary s = sum[i];
+        const uint32_t o = (uint32_t)(i - b);
+        nacc += s.meta & kMetaCount;
+        if (s.meta & kMetaRead) nr++;
+        if (s.meta & kMetaWrite) {
+          nw++;
+          if (f1 == kNone) f1 = o;
+          else if (f2 == kNone) f2 = o;
+          lastw = o + 1;
+        }
+      } else if (endo == kNone) {
+        endo = (uint32_t)(i - b);
+      }
+      if (__syncthreads_or(!in)) break;  // sorted by cell: nothing of it lies further on
+    }
+    const uint32_t end = block_min(endo, sh);
+    nacc = block_sum(nacc, sh);
+    nr = block_sum(nr, sh);
+    nw = block_sum(nw, sh);
+    block_two_min(f1, f2, sh);
+    lastw = block_max(lastw, sh);
+    if (t == 0) {
+      CellVals v{kNone, kNone, kNone, kNone, kNone, kNone, {true, 0}, {true, 0}, 0};
+      if (f1 != kNone) {
+        const Summary s = sum[b + f1];
+        v.w1 = s.gtid;
+        v.u1 = written(s);
+        v.l1 = s.wlast;
+      }
+      if (f2 != kNone) {
+        const Summary s = sum[b + f2];
+        v.w2 = s.gtid;
+        v.u2 = written(s);
+      }
+      sv = v;
+      s_commit = lastw ? sum[b + lastw - 1].wlast : 0;
+    }
+    __syncthreads();
+    const CellVals v0 = sv;
+    // pass 2: writers after w1 (tb, d1, d2) and after w2 (e2)
+    uint32_t tbo = kNone, e2o = kNone, d1o = kNone, d2o = kNone;
+    if (nw >= 2) {
+      for (uint32_t o = t; o < end; o += nt) {
+        const Summary s = sum[b + o];
+        if (!(s.meta & kMetaWrite) || o <= f1) continue;
+        const Uni u = written(s);
+        if (tbo == kNone && s.wlast != v0.l1) tbo = o;
+        if (!v0.u1.mixed && !same(u, v0.u1)) {
+          if (d1o == kNone) d1o = o;
+          else if (d2o == kNone) d2o = o;
+        }
+        if (e2o == kNone && o > f2 && !same(u, v0.u2)) e2o = o;
+      }
+    }
+    tbo = block_min(tbo, sh);
+    e2o = block_min(e2o, sh);
+    block_two_min(d1o, d2o, sh);
+    if (t == 0) {
+      if (tbo != kNone) sv.tb = sum[b + tbo].gtid;
+      if (e2o != kNone) sv.e2 = sum[b + e2o].gtid;
+      if (d1o != kNone) sv.d1 = sum[b + d1o].gtid;
+      if (d2o != kNone) sv.d2 = sum[b + d2o].gtid;
+    }
+    __syncthreads();
+    const CellVals v = sv;
+    // pass 3: first reader with a conflict
+    uint32_t ro = kNone;
+    if (nw > 0 && nr > 0) {
+      for (uint32_t o = t; o < end && ro == kNone; o += nt) {
+        const Summary s = sum[b + o];
+        if ((s.meta & kMetaRead) && reader_conflict(s, v) != kNone) ro = o;
+      }
+    }
+    ro = block_min(ro, sh);
+    if (t == 0) {
+      CellResult c{};
+      c.n_readers = nr;
+      c.n_writers = nw;
+      c.n_acc = nacc;
+      set_ww(c, v);
+      c.rw_a = kNone;
+      if (ro != kNone) {
+        const Summary s = sum[b + ro];
+        c.rw_a = s.gtid;
+        c.rw_b = reader_conflict(s, v);
+      }
+      c.wrote = nw > 0;
+      c.commit = s_commit;
+      if (c.wrote) a.snap[key] = c.commit;
+      nrec[keyidx[b]] = (c.ww_cls ? 1u : 0u) + (c.rw_a != kNone ? 1u : 0u);
+      a.bigres[q] = c;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void big_emit_kernel(const Summary *sum, const uint32_t *keyidx, const uint32_t *nrec,
+                                const uint32_t *recoff, OutRec *out, ClassifyArgs a) {
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= *a.nbig) return;
+  const uint32_t i = a.big[q], k = keyidx[i];
+  if (nrec[k]) emit_cell(a, sum[i].key, a.bigres[q], recoff[k], out);
 }
 
 unsigned blocks_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
@@ -249,6 +440,30 @@ void launch_key_emit(const Summary *sum, uint64_t nsum, const uint32_t *khead,
   if (nsum) count_launch();
   if (nsum)
     key_emit_kernel<<<blocks_for(nsum), kThreads, 0, s>>>(sum, nsum, khead, keyidx, nrec, recoff, out, a);
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+void launch_big_classify(const Summary *sum, uint64_t nsum, const uint32_t *keyidx, uint32_t *nrec,
+                         const ClassifyArgs &a, cudaStream_t s) {
+  if (nsum <= kBigCell) return;  // no cell can be large
+  count_launch();
+  const uint64_t grid = std::min<uint64_t>(big_cells_cap(nsum), (uint64_t)sm_count() * 8);
+  big_classify_kernel<<<(unsigned)grid, kBigThreads, 0, s>>>(sum, nsum, keyidx, nrec, a);
+}
+void launch_big_emit(const Summary *sum, uint64_t nsum, const uint32_t *keyidx, const uint32_t *nrec,
+                     const uint32_t *recoff, OutRec *out, const ClassifyArgs &a, cudaStream_t s) {
+  if (nsum <= kBigCell) return;
+  count_launch();
+  big_emit_kernel<<<blocks_for(big_cells_cap(nsum)), kThreads, 0, s>>>(sum, keyidx, nrec, recoff, out, a);
 }
 
 }  // namespace rc

@@ -189,9 +189,25 @@ void sort_log_into(const LogRec *in, LogRec *out, LogRec *scratch, uint64_t n, u
                    uint32_t *tmp, cudaStream_t s);
 
 // ---- classification (classify.cu)
+// Classification of one cell: counts, WW class and witnesses, RW witnesses,
+// and the value the cell commits.
+struct CellResult {
+  uint32_t n_readers, n_writers, n_acc;
+  uint32_t ww_cls, ww_a, ww_b;  // ww_cls 0 = none
+  uint32_t rw_a, rw_b;          // rw_a kNone = none
+  uint32_t wrote;
+  int32_t commit;
+};
+
+// Cells with more summaries than this are classified by a whole CTA.
+constexpr uint32_t kBigCell = 64;
+
 struct ClassifyArgs {
   uint32_t interval, GT, LT;
   int32_t *snap;  // committed memory, updated in place
+  // cells above kBigCell summaries: head index of each, how many, their results
+  uint32_t *big = nullptr, *nbig = nullptr;
+  CellResult *bigres = nullptr;
   // batches: cells of several instances end to end; records name their instance
   uint32_t n_kernels = 0;
   const uint64_t *kbase = nullptr;  // sorted first cell of each instance
@@ -207,5 +223,12 @@ void launch_key_classify(const Summary *sum, uint64_t nsum, const uint32_t *khea
 void launch_key_emit(const Summary *sum, uint64_t nsum, const uint32_t *khead,
                      const uint32_t *keyidx, const uint32_t *nrec, const uint32_t *recoff,
                      OutRec *out, const ClassifyArgs &a, cudaStream_t s);
+// the large cells key_classify set aside (a.big, a.nbig): results, commit, record counts
+void launch_big_classify(const Summary *sum, uint64_t nsum, const uint32_t *keyidx, uint32_t *nrec,
+                         const ClassifyArgs &a, cudaStream_t s);
+void launch_big_emit(const Summary *sum, uint64_t nsum, const uint32_t *keyidx, const uint32_t *nrec,
+                     const uint32_t *recoff, OutRec *out, const ClassifyArgs &a, cudaStream_t s);
+// capacity of the large-cell list for nsum summaries
+inline uint64_t big_cells_cap(uint64_t nsum) { return nsum / (kBigCell + 1) + 1; }
 
 }  // namespace rc

@@ -99,7 +99,7 @@ struct HostBuf {
 struct Workspace {
   DevBuf code, mems, snap, regs, pc, st, ow, loga, logb, head, runidx, sum, khead, keyidx, nrec,
       recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff, sortscr, reckern,
-      bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround;
+      bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround, big, bigres, nbig;
   HostBuf hstats, hrecs, hround, hdesc;
   cudaStream_t bstream = nullptr;
   bool configured = false, batch_configured = false;
@@ -108,7 +108,8 @@ struct Workspace {
     for (DevBuf *b : {&code, &mems, &snap, &regs, &pc, &st, &ow, &loga, &logb, &head, &runidx, &sum,
                       &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
                       &owcnt, &compact, &ctacnt, &ctaoff, &sortscr, &reckern, &bdesc, &bcode,
-                      &bmems, &btask, &bkbase, &bkgt, &bklt, &berrk, &shared_acc, &bround})
+                      &bmems, &btask, &bkbase, &bkgt, &bklt, &berrk, &shared_acc, &bround, &big,
+                      &bigres, &nbig})
       b->release();
     epoch = 0;
   }
@@ -328,7 +329,12 @@ void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t inter
     ca.kGT = bm->kGT;
     ca.kLT = bm->kLT;
   }
+  ca.big = W.big.get<uint32_t>(big_cells_cap(nsum));
+  ca.bigres = W.bigres.get<CellResult>(big_cells_cap(nsum));
+  ca.nbig = W.nbig.get<uint32_t>(1);
+  CK(cudaMemsetAsync(ca.nbig, 0, 4, s));
   launch_key_classify(sum, nsum, khead, keyidx, nrec, ca, s);
+  launch_big_classify(sum, nsum, keyidx, nrec, ca, s);
   scan_exclusive(nrec, recoff, nkeys, tmp, s);
   CK(cudaMemcpyAsync(hstats, recoff + nkeys - 1, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(hstats + 1, nrec + nkeys - 1, 4, cudaMemcpyDeviceToHost, s));
@@ -338,6 +344,7 @@ void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t inter
   OutRec *out = W.out.get<OutRec>(nrecs);
   if (bm) ca.rec_kernel = W.reckern.get<uint32_t>(nrecs);
   launch_key_emit(sum, nsum, khead, keyidx, nrec, recoff, out, ca, s);
+  launch_big_emit(sum, nsum, keyidx, nrec, recoff, out, ca, s);
   size_t old = races.size();
   races.resize(old + nrecs);
   CK(cudaMemcpyAsync(races.data() + old, out, nrecs * sizeof(OutRec), cudaMemcpyDeviceToHost, s));

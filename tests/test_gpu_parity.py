@@ -105,6 +105,17 @@ def test_batch_shapes(rc, oracle, seed):
     rc.set_strategy(0)
 
 
+@pytest.mark.parametrize("shape", [(1, 65, 8), (1, 66, 32), (3, 97, 16), (2, 200, 8), (1, 300, 64), (5, 129, 4)])
+def test_large_cells(rc, oracle, shape):
+    """Cells touched by more than 64 work-items are classified by a whole
+    CTA (three sweeps with block reductions); small arrays make every cell
+    crowded, with affine and constant values, so witnesses of every kind
+    come from those sweeps."""
+    G, S, L = shape
+    for seed in range(8):
+        run_both(rc, oracle, W.small_kernel(1000 + seed, group_size=S, groups=G, n_stmts=24, n_barriers=2, L=L))
+
+
 EDGE = [
     ("kernel e() { }", 2, 3, []),
     ("kernel e(global int A[]) { A[tid] = tid; }", 1, 1, [np.zeros(1, np.int32)]),
