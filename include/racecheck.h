@@ -231,6 +231,79 @@ int rc_profile_get(int kind, uint64_t *launches, double *ms, double *bytes);
  * (every launch counts, whatever the profiling state). */
 uint64_t rc_kernel_launches(void);
 
+/* ---- learned proposal: which candidate instances to check first
+ *
+ * The method needs, per kernel, a set of candidate instances (launch shape
+ * and input); checking them in a good order finds a race sooner.  These
+ * calls rank candidates with a small network trained on the checker's own
+ * labels.  A ranking never decides a verdict: every race is found and
+ * reported by rc_check; candidates never checked are not claimed race-free. */
+
+#define RC_N_FEATURES 128
+#define RC_MLP_IN 128
+#define RC_MLP_HIDDEN 256
+#define RC_MLP_PARAMS 164865 /* 256*128 + 256 + 2 * (256*256 + 256) + 256 + 1 */
+
+/* Feature vector (RC_N_FEATURES floats) of the candidate instance (bc,
+ * groups, group_size, in): opcode histogram and size counts of the kernel;
+ * per access class (global/local x load/store) how indices depend on tid
+ * and wg, how many work-items reach the accesses, branches on loaded
+ * values, values that vary between work-items, and whether two work-items
+ * of this shape must meet on a cell; collisions among a sample of the
+ * instance's work-items evaluated on its input; the launch shape.  Host
+ * inputs only (in->on_device must be 0).  Errors: RC_E_INVALID. */
+int rc_features(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in, float *out);
+/* rc_features for n candidates into out[n][RC_N_FEATURES], on n_threads host
+ * threads (<= 0: all hardware threads). */
+int rc_features_batch(const rc_bytecode *const *bcs, const uint32_t *groups, const uint32_t *group_size,
+                      const rc_input *inputs, size_t n, float *out, int n_threads);
+
+/* Ranking network: MLP RC_MLP_IN -> 256 -> 256 -> 256 -> 1, ReLU hidden
+ * layers, sigmoid output (probability that the candidate is racy).  FP32
+ * master weights; products on BF16 tensor cores with FP32 accumulation.
+ * Parameter vector layout (FP32, RC_MLP_PARAMS values): W1[256][128] b1[256]
+ * W2[256][256] b2[256] W3[256][256] b3[256] w4[256] b4; layer l computes
+ * h_l = relu(W_l h_{l-1} + b_l), the score is sigmoid(w4 . h3 + b4).
+ * Feature, label and score arrays are device pointers (float, row-major
+ * [n][RC_MLP_IN], [n], [n]); work runs on cuda_stream and is synchronised. */
+typedef struct rc_mlp rc_mlp;
+/* New network with He-uniform weights from `seed`, zero biases; capacity =
+ * rows per device pass (training batch <= capacity). */
+int rc_mlp_create(uint64_t seed, uint32_t capacity, rc_mlp **out);
+void rc_mlp_free(rc_mlp *m);
+int rc_mlp_get_params(const rc_mlp *m, float *host_out);
+int rc_mlp_set_params(rc_mlp *m, const float *host_in);
+/* prob[i] = score of row i of x, for n rows. */
+int rc_mlp_forward(rc_mlp *m, const float *x, uint64_t n, float *prob, void *cuda_stream);
+/* Mean binary cross-entropy of the n <= capacity rows (labels y in {0,1})
+ * and its gradient with respect to every parameter (host_grad: RC_MLP_PARAMS
+ * floats, may be NULL); no update. */
+int rc_mlp_grad(rc_mlp *m, const float *x, const float *y, uint32_t n, float *host_grad, float *host_loss,
+                void *cuda_stream);
+/* Train with Adam (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the mean
+ * binary cross-entropy, `epochs` passes over n rows in minibatches of
+ * `batch`, rows shuffled per epoch from `seed`.  epoch_loss (host, epochs
+ * floats, may be NULL) receives each epoch's mean minibatch loss. */
+int rc_mlp_train(rc_mlp *m, const float *x, const float *y, uint64_t n, uint32_t epochs, uint32_t batch, float lr,
+                 uint64_t seed, float *epoch_loss, void *cuda_stream);
+
+/* Search for a racy candidate: check candidates (as rc_check) in descending
+ * order of scores[i] (host array; ties keep their index order), or in index
+ * order when scores is NULL (plain enumeration), until one report has status
+ * RC_RACY or max_checks candidates (0 = all) were checked.  res->first is
+ * that candidate's index or -1, res->checks the checks made, res->seconds
+ * the host wall time of the checks.  found (may be NULL) receives the racy
+ * candidate's report.  A check error stops the search and is returned. */
+typedef struct {
+  int64_t first;
+  uint32_t checks;
+  uint32_t reserved;
+  double seconds;
+} rc_search_result;
+int rc_search(const rc_bytecode *const *bcs, const uint32_t *groups, const uint32_t *group_size,
+              const rc_input *inputs, size_t n, const float *scores, uint32_t max_checks, rc_search_result *res,
+              rc_report **found);
+
 #ifdef __cplusplus
 }
 #endif

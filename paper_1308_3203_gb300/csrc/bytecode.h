@@ -130,6 +130,9 @@ enum Cls : uint32_t {
   CLS_OOB = 16, CLS_ASSERT = 17, CLS_DIVERGENCE = 18
 };
 
+// Message for rc_last_error() on the calling thread.
+void set_last_error(const std::string &msg);
+
 // Compile kernel source; throws CompileError.
 struct CompileError {
   std::string msg;
@@ -139,3 +142,9 @@ Program compile_program(const std::string &src);
 std::string validate_program(const Program &p);
 
 }  // namespace rc
+
+// The object behind the opaque rc_bytecode handle.
+struct rc_bytecode {
+  rc::Program prog;
+};
+

@@ -1,0 +1,592 @@
+// Learned proposal network: MLP 128 -> 256 -> 256 -> 256 -> 1 (ReLU, sigmoid
+// score) over candidate features, trained on the exact checker's race / no
+// race labels with binary cross-entropy and Adam.
+//
+// Numerics: FP32 master weights; the forward and backward products run on
+// BF16 tensor cores (mma.sync m16n8k16, FP32 accumulation) with BF16
+// operands: the input features, the weight copies, the hidden activations
+// h = relu(z) and the pre-activation gradients dz are rounded to BF16 where
+// they are stored; biases, the output layer's dot product, the loss and all
+// gradient sums stay in FP32.  Weight gradients reduce over the batch in a
+// fixed order (split-K partials summed per element in split order), so a
+// training run is deterministic.
+//
+// Parameter vector (FP32, also the layout of gradients and Adam moments):
+//   W1[256][128] b1[256] W2[256][256] b2[256] W3[256][256] b3[256] w4[256] b4
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "racecheck.h"
+#include "device.cuh"
+
+namespace rc {
+namespace {
+
+constexpr int kIn = RC_MLP_IN, kHid = RC_MLP_HIDDEN;
+constexpr size_t oW1 = 0, ob1 = oW1 + (size_t)kHid * kIn, oW2 = ob1 + kHid, ob2 = oW2 + (size_t)kHid * kHid,
+                 oW3 = ob2 + kHid, ob3 = oW3 + (size_t)kHid * kHid, ow4 = ob3 + kHid, ob4 = ow4 + kHid,
+                 kParams = ob4 + 1;
+static_assert(kParams == RC_MLP_PARAMS, "parameter layout");
+
+typedef __nv_bfloat16 bf16;
+
+// ---------------------------------------------------------------- GEMM
+// C[M][N] = A[M][K] * B[K][N] on a 64 x 64 tile per CTA (4 warps, 32 x 32
+// each), K in steps of 32.  Both operands are staged in shared memory with K
+// contiguous ([row][k], rows padded to 40 elements so the fragment loads of
+// a warp hit 32 distinct banks); modes differ in where the tiles come from:
+//   FWD   A = act[M][K],           B[k][n] = W[n][k]      (W is [N][K])
+//         out = relu(C + bias) as BF16 [M][N]
+//   DGRAD A = dz[M][K],            B[k][n] = W[k][n]      (W is [K][N])
+//         out = C where h[m][n] > 0, else 0, as BF16 [M][N]
+//   WGRAD A[m][k] = dz[k][m],      B[k][n] = h[k][n]      (dz [rows][M], h [rows][N])
+//         K = batch rows [z*kchunk, ...); out = FP32 partial z of C
+constexpr int BM = 64, BN = 64, BK = 32, BKP = BK + 8, kGemmThreads = 128;
+enum GemmMode { FWD = 0, DGRAD = 1, WGRAD = 2 };
+
+struct GemmArgs {
+  const bf16 *A;      // FWD/DGRAD: [M][K]; WGRAD: dz [rows][M]
+  const bf16 *B;      // FWD: W [N][K]; DGRAD: W [K][N]; WGRAD: h [rows][N]
+  const float *bias;  // FWD
+  const bf16 *mask;   // DGRAD: h [M][N]
+  bf16 *out;          // FWD/DGRAD: [M][N]
+  float *part;        // WGRAD: [splits][M][N]
+  int M, N, K;        // WGRAD: M = dz columns, N = h columns, K = rows
+  int kchunk;         // WGRAD: rows per split
+};
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// stage a 64 x 32 tile whose source rows are K-contiguous: tile[r][k] = src[(r0 + r) * ld + k0 + k]
+__device__ __forceinline__ void stage_rows(bf16 (*tile)[BKP], const bf16 *src, int ld, int r0, int rmax, int k0) {
+  const int t = threadIdx.x, r = t >> 1, h = (t & 1) * 16;
+  uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
+  if (r0 + r < rmax) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(src + (size_t)(r0 + r) * ld + k0 + h);
+    v0 = p[0];
+    v1 = p[1];
+  }
+  uint4 *q = reinterpret_cast<uint4 *>(&tile[r][h]);  // 80-byte rows: 16-byte aligned at h = 0, 16
+  q[0] = v0;
+  q[1] = v1;
+}
+
+// stage a 64 x 32 tile from a source whose rows run along the tile's rows:
+// tile[r][k] = src[(k0 + k) * ld + r0 + r], source rows k0 + k < kmax
+__device__ __forceinline__ void stage_cols(bf16 (*tile)[BKP], const bf16 *src, int ld, int r0, int k0, int kmax) {
+  const int t = threadIdx.x, k = t >> 2, c = (t & 3) * 16;
+  uint4 v[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+  if (k0 + k < kmax) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(src + (size_t)(k0 + k) * ld + r0 + c);
+    v[0] = p[0];
+    v[1] = p[1];
+  }
+  const bf16 *e = reinterpret_cast<const bf16 *>(v);
+#pragma unroll
+  for (int j = 0; j < 16; j++) tile[c + j][k] = e[j];
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kGemmThreads) gemm_kernel(GemmArgs g) {
+  __shared__ __align__(16) bf16 As[BM][BKP];
+  __shared__ __align__(16) bf16 Bs[BN][BKP];
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  int kbeg = 0, kend = g.K;
+  if (MODE == WGRAD) {
+    kbeg = blockIdx.z * g.kchunk;
+    kend = min(g.K, kbeg + g.kchunk);
+  }
+  float acc[2][4][4] = {};
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    if (MODE == FWD) {
+      stage_rows(As, g.A, g.K, m0, g.M, k0);
+      stage_rows(Bs, g.B, g.K, n0, g.N, k0);
+    } else if (MODE == DGRAD) {
+      stage_rows(As, g.A, g.K, m0, g.M, k0);
+      stage_cols(Bs, g.B, g.N, n0, k0, g.K);
+    } else {
+      stage_cols(As, g.A, g.M, m0, k0, kend);
+      stage_cols(Bs, g.B, g.N, n0, k0, kend);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int mi = 0; mi < 2; mi++) {
+        const int r = wm + mi * 16 + grp;
+        a[mi][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + tig * 2]);
+        a[mi][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + tig * 2]);
+        a[mi][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + tig * 2 + 8]);
+        a[mi][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + tig * 2 + 8]);
+      }
+#pragma unroll
+      for (int ni = 0; ni < 4; ni++) {
+        const int c = wn + ni * 8 + grp;
+        b[ni][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + tig * 2]);
+        b[ni][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + tig * 2 + 8]);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; mi++)
+#pragma unroll
+        for (int ni = 0; ni < 4; ni++) mma_bf16(acc[mi][ni], a[mi], b[ni]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mi = 0; mi < 2; mi++)
+#pragma unroll
+    for (int ni = 0; ni < 4; ni++)
+#pragma unroll
+      for (int h = 0; h < 2; h++) {  // h = 0: row grp, h = 1: row grp + 8
+        const int r = m0 + wm + mi * 16 + grp + h * 8, c = n0 + wn + ni * 8 + tig * 2;
+        if (r >= g.M) continue;
+        const float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
+        if (MODE == FWD) {
+          const float z0 = v0 + g.bias[c], z1 = v1 + g.bias[c + 1];
+          *reinterpret_cast<__nv_bfloat162 *>(g.out + (size_t)r * g.N + c) =
+              __floats2bfloat162_rn(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
+        } else if (MODE == DGRAD) {
+          const __nv_bfloat162 hm = *reinterpret_cast<const __nv_bfloat162 *>(g.mask + (size_t)r * g.N + c);
+          const float d0 = __bfloat162float(hm.x) > 0.0f ? v0 : 0.0f;
+          const float d1 = __bfloat162float(hm.y) > 0.0f ? v1 : 0.0f;
+          *reinterpret_cast<__nv_bfloat162 *>(g.out + (size_t)r * g.N + c) = __floats2bfloat162_rn(d0, d1);
+        } else {
+          float *p = g.part + ((size_t)blockIdx.z * g.M + r) * g.N + c;
+          p[0] = v0;
+          p[1] = v1;
+        }
+      }
+}
+
+// ---------------------------------------------------------------- small kernels
+// rows of the (shuffled) batch: features to BF16, labels to FP32
+__global__ void gather_kernel(const float *X, const float *Y, const uint32_t *idx, int n, bf16 *Xb, float *Yb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * kIn) return;
+  const int r = i / kIn, c = i % kIn;
+  const uint32_t s = idx ? idx[r] : (uint32_t)r;
+  Xb[i] = __float2bfloat16_rn(X[(size_t)s * kIn + c]);
+  if (c == 0 && Yb) Yb[r] = Y[s];
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  return x;
+}
+
+// output layer, one warp per row: logit = h3 . w4 + b4 (BF16 operands, FP32 sum)
+__device__ __forceinline__ float head_logit(const bf16 *h3, const bf16 *w4b, float b4, int lane) {
+  const uint4 hv = reinterpret_cast<const uint4 *>(h3)[lane];
+  const uint4 wv = reinterpret_cast<const uint4 *>(w4b)[lane];
+  const bf16 *he = reinterpret_cast<const bf16 *>(&hv), *we = reinterpret_cast<const bf16 *>(&wv);
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; j++) s += __bfloat162float(he[j]) * __bfloat162float(we[j]);
+  return warp_sum(s) + b4;
+}
+
+__global__ void head_fwd_kernel(const bf16 *H3, const bf16 *w4b, const float *P, int n, float *prob) {
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const float z = head_logit(H3 + (size_t)r * kHid, w4b, P[ob4], lane);
+  if (lane == 0) prob[r] = 1.0f / (1.0f + expf(-z));
+}
+
+// loss and the output layer's gradients: dl = (sigmoid(z) - y) / n,
+// loss_r = log(1 + e^z) - y z, dz3 = dl * w4 where h3 > 0
+__global__ void head_bwd_kernel(const bf16 *H3, const bf16 *w4b, const float *P, const float *Yb, int n,
+                                float inv_n, float *dl, float *loss, bf16 *dZ3) {
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const bf16 *h = H3 + (size_t)r * kHid;
+  const float z = head_logit(h, w4b, P[ob4], lane);
+  const float y = Yb[r];
+  const float p = 1.0f / (1.0f + expf(-z));
+  const float d = (p - y) * inv_n;
+  if (lane == 0) {
+    dl[r] = d;
+    loss[r] = fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))) - y * z;
+  }
+  const uint4 hv = reinterpret_cast<const uint4 *>(h)[lane];
+  const uint4 wv = reinterpret_cast<const uint4 *>(w4b)[lane];
+  const bf16 *he = reinterpret_cast<const bf16 *>(&hv), *we = reinterpret_cast<const bf16 *>(&wv);
+  __align__(16) bf16 o[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++)
+    o[j] = __float2bfloat16_rn(__bfloat162float(he[j]) > 0.0f ? d * __bfloat162float(we[j]) : 0.0f);
+  reinterpret_cast<uint4 *>(dZ3 + (size_t)r * kHid)[lane] = *reinterpret_cast<const uint4 *>(o);
+}
+
+// column sums over a row chunk: part[chunk][c] = sum_r w[r] * A[r][c] (w = 1 if null)
+constexpr int kColRows = 256;
+__global__ void colsum_kernel(const bf16 *A, const float *w, int n, float *part) {
+  const int c = threadIdx.x;  // blockDim = kHid
+  const int r0 = blockIdx.x * kColRows, r1 = min(n, r0 + kColRows);
+  float s = 0.0f;
+  for (int r = r0; r < r1; r++) s += (w ? w[r] : 1.0f) * __bfloat162float(A[(size_t)r * kHid + c]);
+  part[(size_t)blockIdx.x * kHid + c] = s;
+}
+// sum of dl over a row chunk (output bias)
+__global__ void vecsum_kernel(const float *v, int n, float *part) {
+  __shared__ float sh[32];
+  const int r0 = blockIdx.x * kColRows;
+  const int r = r0 + threadIdx.x;
+  float s = (r < n && threadIdx.x < kColRows) ? v[r] : 0.0f;
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[k];
+    part[blockIdx.x] = t;
+  }
+}
+// out[i] = sum over z of part[z][i], in split order
+__global__ void reduce_parts_kernel(const float *part, int splits, int count, float *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float s = 0.0f;
+  for (int z = 0; z < splits; z++) s += part[(size_t)z * count + i];
+  out[i] = s;
+}
+
+__global__ void adam_kernel(float *P, const float *G, float *Mm, float *Vv, bf16 *Pb, size_t n, float lr, float b1,
+                            float b2, float c1, float c2, float eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = G[i];
+  const float m = b1 * Mm[i] + (1.0f - b1) * g;
+  const float v = b2 * Vv[i] + (1.0f - b2) * g * g;
+  Mm[i] = m;
+  Vv[i] = v;
+  const float p = P[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+  P[i] = p;
+  Pb[i] = __float2bfloat16_rn(p);
+}
+
+__global__ void to_bf16_kernel(const float *P, bf16 *Pb, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Pb[i] = __float2bfloat16_rn(P[i]);
+}
+
+unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+}  // namespace rc
+
+// ---------------------------------------------------------------- the network object
+struct rc_mlp {
+  uint32_t cap = 0;  // rows per pass
+  float *P = nullptr, *G = nullptr, *Mm = nullptr, *Vv = nullptr;
+  rc::bf16 *Pb = nullptr;
+  rc::bf16 *Xb = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *D1 = nullptr, *D2 = nullptr;
+  float *Yb = nullptr, *dl = nullptr, *loss = nullptr, *part = nullptr, *scal = nullptr;
+  uint32_t *idx = nullptr;
+  size_t part_floats = 0;
+  uint64_t step = 0;
+};
+
+namespace rc {
+namespace {
+
+struct MlpFail {
+  int code;
+  const char *msg;
+};
+#define MK(x)                                                   \
+  do {                                                          \
+    cudaError_t e_ = (x);                                       \
+    if (e_ != cudaSuccess) throw MlpFail{RC_E_CUDA, cudaGetErrorString(e_)}; \
+  } while (0)
+
+int wgrad_splits(int rows) { return std::max(1, std::min(64, (rows + 511) / 512)); }
+
+// forward pass of rows [0, n) of the staged batch m->Xb (n <= cap)
+void forward(rc_mlp *m, int n, cudaStream_t s) {
+  const bf16 *Wb = m->Pb;
+  GemmArgs g{};
+  g.M = n;
+  g.N = kHid;
+  dim3 grid(nblk(n, BM), kHid / BN);
+  g.A = m->Xb, g.B = Wb + oW1, g.bias = m->P + ob1, g.out = m->H1, g.K = kIn;
+  count_launch();
+  gemm_kernel<FWD><<<grid, kGemmThreads, 0, s>>>(g);
+  g.A = m->H1, g.B = Wb + oW2, g.bias = m->P + ob2, g.out = m->H2, g.K = kHid;
+  count_launch();
+  gemm_kernel<FWD><<<grid, kGemmThreads, 0, s>>>(g);
+  g.A = m->H2, g.B = Wb + oW3, g.bias = m->P + ob3, g.out = m->H3, g.K = kHid;
+  count_launch();
+  gemm_kernel<FWD><<<grid, kGemmThreads, 0, s>>>(g);
+}
+
+// dW = dz^T h (+ split-K partials), db = column sums of dz
+void weight_grads(rc_mlp *m, const bf16 *dz, const bf16 *h, int kin, int n, size_t oW, size_t ob, cudaStream_t s) {
+  const int splits = wgrad_splits(n);
+  GemmArgs g{};
+  g.A = dz;
+  g.B = h;
+  g.part = m->part;
+  g.M = kHid;
+  g.N = kin;
+  g.K = n;
+  g.kchunk = (((n + splits - 1) / splits) + BK - 1) / BK * BK;
+  const int zs = (n + g.kchunk - 1) / g.kchunk;
+  count_launch();
+  gemm_kernel<WGRAD><<<dim3(kHid / BM, kin / BN, zs), kGemmThreads, 0, s>>>(g);
+  count_launch();
+  reduce_parts_kernel<<<nblk((size_t)kHid * kin, 256), 256, 0, s>>>(m->part, zs, kHid * kin, m->G + oW);
+  const int chunks = (n + kColRows - 1) / kColRows;
+  count_launch();
+  colsum_kernel<<<chunks, kHid, 0, s>>>(dz, nullptr, n, m->part);
+  count_launch();
+  reduce_parts_kernel<<<1, kHid, 0, s>>>(m->part, chunks, kHid, m->G + ob);
+}
+
+// forward + backward of the staged batch; gradients into m->G, per-row losses into m->loss
+void backward(rc_mlp *m, int n, cudaStream_t s) {
+  forward(m, n, s);
+  count_launch();
+  head_bwd_kernel<<<nblk((size_t)n * 32, 256), 256, 0, s>>>(m->H3, m->Pb + ow4, m->P, m->Yb, n, 1.0f / n, m->dl,
+                                                            m->loss, m->D2);
+  // output layer: gw4 = sum_r dl_r h3_r, gb4 = sum_r dl_r
+  const int chunks = (n + kColRows - 1) / kColRows;
+  count_launch();
+  colsum_kernel<<<chunks, kHid, 0, s>>>(m->H3, m->dl, n, m->part);
+  count_launch();
+  reduce_parts_kernel<<<1, kHid, 0, s>>>(m->part, chunks, kHid, m->G + ow4);
+  count_launch();
+  vecsum_kernel<<<chunks, kColRows, 0, s>>>(m->dl, n, m->part);
+  count_launch();
+  reduce_parts_kernel<<<1, 1, 0, s>>>(m->part, chunks, 1, m->G + ob4);
+  // layer 3 (dz3 in D2), then dz2 = (dz3 W3) * [h2 > 0] into D1
+  weight_grads(m, m->D2, m->H2, kHid, n, oW3, ob3, s);
+  GemmArgs g{};
+  g.M = n;
+  g.N = kHid;
+  g.K = kHid;
+  g.A = m->D2, g.B = m->Pb + oW3, g.mask = m->H2, g.out = m->D1;
+  count_launch();
+  gemm_kernel<DGRAD><<<dim3(nblk(n, BM), kHid / BN), kGemmThreads, 0, s>>>(g);
+  weight_grads(m, m->D1, m->H1, kHid, n, oW2, ob2, s);
+  g.A = m->D1, g.B = m->Pb + oW2, g.mask = m->H1, g.out = m->D2;  // dz1 into D2
+  count_launch();
+  gemm_kernel<DGRAD><<<dim3(nblk(n, BM), kHid / BN), kGemmThreads, 0, s>>>(g);
+  weight_grads(m, m->D2, m->Xb, kIn, n, oW1, ob1, s);
+}
+
+void stage(rc_mlp *m, const float *X, const float *Y, const uint32_t *idx, int n, cudaStream_t s) {
+  count_launch();
+  gather_kernel<<<nblk((size_t)n * kIn, 256), 256, 0, s>>>(X, Y, idx, n, m->Xb, Y ? m->Yb : nullptr);
+}
+
+// mean of the per-row losses into m->scal[slot]
+void mean_loss(rc_mlp *m, int n, int slot, cudaStream_t s) {
+  const int chunks = (n + kColRows - 1) / kColRows;
+  count_launch();
+  vecsum_kernel<<<chunks, kColRows, 0, s>>>(m->loss, n, m->part);
+  count_launch();
+  reduce_parts_kernel<<<1, 1, 0, s>>>(m->part, chunks, 1, m->scal + slot);
+}
+
+void adam(rc_mlp *m, float lr, cudaStream_t s) {
+  m->step++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - (float)std::pow(b1, (double)m->step), c2 = 1.0f - (float)std::pow(b2, (double)m->step);
+  count_launch();
+  adam_kernel<<<nblk(kParams, 256), 256, 0, s>>>(m->P, m->G, m->Mm, m->Vv, m->Pb, kParams, lr, b1, b2, c1, c2, 1e-8f);
+}
+
+uint64_t splitmix(uint64_t &x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <class F>
+int guarded(F f) {
+  try {
+    f();
+    return RC_OK;
+  } catch (const MlpFail &e) {
+    set_last_error(e.msg);
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    set_last_error("out of host memory");
+    return RC_E_NOMEM;
+  }
+}
+
+}  // namespace
+}  // namespace rc
+
+using namespace rc;
+
+extern "C" {
+
+int rc_mlp_create(uint64_t seed, uint32_t capacity, rc_mlp **out) {
+  if (!out || capacity == 0 || capacity > (1u << 24)) {
+    set_last_error("bad arguments");
+    return RC_E_INVALID;
+  }
+  rc_mlp *m = new (std::nothrow) rc_mlp();
+  if (!m) return RC_E_NOMEM;
+  const int rc = guarded([&] {
+    m->cap = capacity;
+    const size_t cap = capacity;
+    const int max_splits = wgrad_splits((int)std::min<size_t>(cap, 1u << 30));
+    m->part_floats = std::max<size_t>((size_t)max_splits * kHid * kHid, ((cap + kColRows - 1) / kColRows) * kHid);
+    MK(cudaMalloc(&m->P, kParams * 4));
+    MK(cudaMalloc(&m->G, kParams * 4));
+    MK(cudaMalloc(&m->Mm, kParams * 4));
+    MK(cudaMalloc(&m->Vv, kParams * 4));
+    MK(cudaMalloc(&m->Pb, kParams * 2));
+    MK(cudaMalloc(&m->Xb, cap * kIn * 2));
+    MK(cudaMalloc(&m->H1, cap * kHid * 2));
+    MK(cudaMalloc(&m->H2, cap * kHid * 2));
+    MK(cudaMalloc(&m->H3, cap * kHid * 2));
+    MK(cudaMalloc(&m->D1, cap * kHid * 2));
+    MK(cudaMalloc(&m->D2, cap * kHid * 2));
+    MK(cudaMalloc(&m->Yb, cap * 4));
+    MK(cudaMalloc(&m->dl, cap * 4));
+    MK(cudaMalloc(&m->loss, cap * 4));
+    MK(cudaMalloc(&m->idx, cap * 4));
+    MK(cudaMalloc(&m->part, m->part_floats * 4));
+    MK(cudaMalloc(&m->scal, 4096 * 4));
+    // He-uniform weights for the ReLU layers, zero biases
+    std::vector<float> p(kParams, 0.0f);
+    uint64_t st = seed;
+    auto uni = [&](float a) { return (float)((splitmix(st) >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0) * a; };
+    const float a1 = std::sqrt(6.0f / kIn), a2 = std::sqrt(6.0f / kHid), a4 = std::sqrt(3.0f / kHid);
+    for (size_t i = 0; i < (size_t)kHid * kIn; i++) p[oW1 + i] = uni(a1);
+    for (size_t i = 0; i < (size_t)kHid * kHid; i++) p[oW2 + i] = uni(a2);
+    for (size_t i = 0; i < (size_t)kHid * kHid; i++) p[oW3 + i] = uni(a2);
+    for (size_t i = 0; i < (size_t)kHid; i++) p[ow4 + i] = uni(a4);
+    MK(cudaMemcpy(m->P, p.data(), kParams * 4, cudaMemcpyHostToDevice));
+    MK(cudaMemset(m->Mm, 0, kParams * 4));
+    MK(cudaMemset(m->Vv, 0, kParams * 4));
+    MK(cudaMemset(m->G, 0, kParams * 4));
+    count_launch();
+    to_bf16_kernel<<<nblk(kParams, 256), 256>>>(m->P, m->Pb, kParams);
+    MK(cudaGetLastError());
+    MK(cudaDeviceSynchronize());
+  });
+  if (rc) {
+    rc_mlp_free(m);
+    return rc;
+  }
+  *out = m;
+  return RC_OK;
+}
+
+void rc_mlp_free(rc_mlp *m) {
+  if (!m) return;
+  for (void *p : {(void *)m->P, (void *)m->G, (void *)m->Mm, (void *)m->Vv, (void *)m->Pb, (void *)m->Xb,
+                  (void *)m->H1, (void *)m->H2, (void *)m->H3, (void *)m->D1, (void *)m->D2, (void *)m->Yb,
+                  (void *)m->dl, (void *)m->loss, (void *)m->idx, (void *)m->part, (void *)m->scal})
+    if (p) cudaFree(p);
+  delete m;
+}
+
+int rc_mlp_get_params(const rc_mlp *m, float *out) {
+  if (!m || !out) return RC_E_INVALID;
+  return guarded([&] { MK(cudaMemcpy(out, m->P, kParams * 4, cudaMemcpyDeviceToHost)); });
+}
+
+int rc_mlp_set_params(rc_mlp *m, const float *in) {
+  if (!m || !in) return RC_E_INVALID;
+  return guarded([&] {
+    MK(cudaMemcpy(m->P, in, kParams * 4, cudaMemcpyHostToDevice));
+    count_launch();
+    to_bf16_kernel<<<nblk(kParams, 256), 256>>>(m->P, m->Pb, kParams);
+    MK(cudaGetLastError());
+    MK(cudaDeviceSynchronize());
+  });
+}
+
+int rc_mlp_forward(rc_mlp *m, const float *x, uint64_t n, float *prob, void *cuda_stream) {
+  if (!m || (n && (!x || !prob))) return RC_E_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  return guarded([&] {
+    for (uint64_t r0 = 0; r0 < n; r0 += m->cap) {
+      const int k = (int)std::min<uint64_t>(m->cap, n - r0);
+      stage(m, x + r0 * kIn, nullptr, nullptr, k, s);
+      forward(m, k, s);
+      count_launch();
+      head_fwd_kernel<<<nblk((size_t)k * 32, 256), 256, 0, s>>>(m->H3, m->Pb + ow4, m->P, k, prob + r0);
+    }
+    MK(cudaGetLastError());
+    MK(cudaStreamSynchronize(s));
+  });
+}
+
+int rc_mlp_grad(rc_mlp *m, const float *x, const float *y, uint32_t n, float *grad, float *loss, void *cuda_stream) {
+  if (!m || n == 0 || n > m->cap || !x || !y) return RC_E_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  return guarded([&] {
+    stage(m, x, y, nullptr, (int)n, s);
+    backward(m, (int)n, s);
+    mean_loss(m, (int)n, 0, s);
+    if (grad) MK(cudaMemcpyAsync(grad, m->G, kParams * 4, cudaMemcpyDeviceToHost, s));
+    float l = 0;
+    MK(cudaMemcpyAsync(&l, m->scal, 4, cudaMemcpyDeviceToHost, s));
+    MK(cudaGetLastError());
+    MK(cudaStreamSynchronize(s));
+    if (loss) *loss = l;
+  });
+}
+
+int rc_mlp_train(rc_mlp *m, const float *x, const float *y, uint64_t n, uint32_t epochs, uint32_t batch, float lr,
+                 uint64_t seed, float *epoch_loss, void *cuda_stream) {
+  if (!m || n == 0 || !x || !y || batch == 0 || batch > m->cap || n > 0xFFFFFFFFull || epochs > 4096)
+    return RC_E_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  return guarded([&] {
+    std::vector<uint32_t> perm(n);
+    uint32_t *didx = nullptr;
+    MK(cudaMalloc(&didx, n * 4));
+    struct Free {
+      uint32_t *p;
+      ~Free() { cudaFree(p); }
+    } fr{didx};
+    uint64_t st = seed;
+    std::vector<float> sums(epochs, 0.0f);
+    for (uint32_t e = 0; e < epochs; e++) {
+      for (uint64_t i = 0; i < n; i++) perm[i] = (uint32_t)i;
+      for (uint64_t i = n - 1; i > 0; i--) std::swap(perm[i], perm[splitmix(st) % (i + 1)]);
+      MK(cudaMemcpyAsync(didx, perm.data(), n * 4, cudaMemcpyHostToDevice, s));
+      uint32_t nb = 0;
+      for (uint64_t r0 = 0; r0 < n; r0 += batch, nb++) {
+        const int k = (int)std::min<uint64_t>(batch, n - r0);
+        stage(m, x, y, didx + r0, k, s);
+        backward(m, k, s);
+        mean_loss(m, k, (int)std::min<uint32_t>(nb, 4095), s);
+        adam(m, lr, s);
+      }
+      std::vector<float> ls(std::min<uint32_t>(nb, 4096));
+      MK(cudaMemcpyAsync(ls.data(), m->scal, ls.size() * 4, cudaMemcpyDeviceToHost, s));
+      MK(cudaStreamSynchronize(s));
+      double t = 0;
+      for (float v : ls) t += v;
+      sums[e] = (float)(t / std::max<size_t>(ls.size(), 1));
+    }
+    MK(cudaGetLastError());
+    if (epoch_loss) std::memcpy(epoch_loss, sums.data(), epochs * 4);
+  });
+}
+
+}  // extern "C"

@@ -17,6 +17,7 @@
 #include <map>
 #include <mutex>
 #include <sys/stat.h>
+#include <chrono>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -24,10 +25,6 @@
 
 #include "racecheck.h"
 #include "device.cuh"
-
-struct rc_bytecode {
-  rc::Program prog;
-};
 
 namespace rc {
 namespace {
@@ -999,6 +996,7 @@ int fail_code(const Fail &f) {
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void set_last_error(const std::string &msg) { g_last_error = msg; }
 
 }  // namespace rc
 
@@ -1053,6 +1051,49 @@ int rc_check(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const 
     Instance I{&bc->prog, groups, group_size, (uint64_t)groups * group_size, in,
                static_cast<cudaStream_t>(in->cuda_stream)};
     *out = run_instance(I);
+    return RC_OK;
+  } catch (const Fail &f) {
+    return fail_code(f);
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return RC_E_NOMEM;
+  }
+}
+
+int rc_search(const rc_bytecode *const *bcs, const uint32_t *groups, const uint32_t *group_size,
+              const rc_input *inputs, size_t n, const float *scores, uint32_t max_checks, rc_search_result *res,
+              rc_report **found) {
+  if (!res || (n && (!bcs || !groups || !group_size || !inputs))) return RC_E_INVALID;
+  res->first = -1;
+  res->checks = 0;
+  res->seconds = 0;
+  if (found) *found = nullptr;
+  // candidates in descending score (ties keep their order), or as given
+  std::vector<size_t> order(n);
+  for (size_t i = 0; i < n; i++) order[i] = i;
+  if (scores)
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return scores[a] > scores[b]; });
+  const size_t limit = max_checks ? std::min<size_t>(n, max_checks) : n;
+  std::lock_guard<std::mutex> lk(g_mu);
+  try {
+    if (g_prof.on) prof_events();
+    const auto t0 = std::chrono::steady_clock::now();
+    for (size_t k = 0; k < limit; k++) {
+      const size_t i = order[k];
+      check_args(bcs[i], groups[i], group_size[i], &inputs[i]);
+      Instance I{&bcs[i]->prog, groups[i], group_size[i], (uint64_t)groups[i] * group_size[i], &inputs[i],
+                 static_cast<cudaStream_t>(inputs[i].cuda_stream)};
+      rc_report *r = run_instance(I);
+      res->checks++;
+      if (r->status == RC_RACY) {
+        res->first = (int64_t)i;
+        if (found) *found = r;
+        else rc_report_free(r);
+        break;
+      }
+      rc_report_free(r);
+    }
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return RC_OK;
   } catch (const Fail &f) {
     return fail_code(f);

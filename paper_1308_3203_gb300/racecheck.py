@@ -55,6 +55,14 @@ class _Info(ctypes.Structure):
                                     ("max_write_per_interval", ctypes.c_uint64)]
 
 
+class _SearchResult(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_int64), ("checks", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("seconds", ctypes.c_double)]
+
+
+N_FEATURES = 128
+MLP_PARAMS = 164865
+
 _lock = threading.Lock()
 _lib = None
 
@@ -102,6 +110,26 @@ def load() -> ctypes.CDLL:
         lib.rc_autotune_lookup.restype = c_int
         lib.rc_kernel_launches.argtypes = []
         lib.rc_kernel_launches.restype = ctypes.c_uint64
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.rc_features_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint32),
+                                          ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_Input),
+                                          ctypes.c_size_t, fp, c_int]
+        lib.rc_mlp_create.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(vp)]
+        lib.rc_mlp_free.argtypes = [vp]
+        lib.rc_mlp_free.restype = None
+        lib.rc_mlp_get_params.argtypes = [vp, fp]
+        lib.rc_mlp_set_params.argtypes = [vp, fp]
+        lib.rc_mlp_forward.argtypes = [vp, vp, ctypes.c_uint64, vp, vp]
+        lib.rc_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_uint32, fp, fp, vp]
+        lib.rc_mlp_train.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                     ctypes.c_float, ctypes.c_uint64, fp, vp]
+        lib.rc_search.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint32),
+                                  ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_Input), ctypes.c_size_t,
+                                  fp, ctypes.c_uint32, ctypes.POINTER(_SearchResult),
+                                  ctypes.POINTER(ctypes.POINTER(_Report))]
+        for f in ("rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
+                  "rc_mlp_forward", "rc_mlp_grad", "rc_mlp_train", "rc_search"):
+            getattr(lib, f).restype = c_int
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
                   "rc_set_strategy", "rc_profile_enable", "rc_profile_reset", "rc_profile_get",
                   "rc_release_workspace"):
@@ -310,3 +338,128 @@ def autotune_reset() -> None:
 def autotune_lookup(kind: int, a: int, b: int) -> int:
     """Decided strategy for a size class (0 undecided, 1 sort, 2 shadow)."""
     return int(load().rc_autotune_lookup(kind, a, b))
+
+
+# ---------------------------------------------------------------- learned proposal
+
+
+def _items_arrays(items, want_final=False):
+    n = len(items)
+    hs = (ctypes.c_void_p * max(n, 1))(*[it[0].handle.value for it in items])
+    gs = (ctypes.c_uint32 * max(n, 1))(*[it[1] for it in items])
+    ss = (ctypes.c_uint32 * max(n, 1))(*[it[2] for it in items])
+    inputs = (_Input * max(n, 1))()
+    keep = []
+    for i, it in enumerate(items):
+        inp, k = _marshal(it[3], None, want_final)
+        inputs[i] = inp
+        keep.append(k)
+    return hs, gs, ss, inputs, keep
+
+
+def features(items, n_threads: int = 0) -> np.ndarray:
+    """Feature vectors [n, 128] of candidate instances items = [(bytecode,
+    groups, group_size, host globals)]."""
+    n = len(items)
+    out = np.zeros((max(n, 1), N_FEATURES), dtype=np.float32)
+    hs, gs, ss, inputs, keep = _items_arrays(items)
+    rc = load().rc_features_batch(hs, gs, ss, inputs, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                  n_threads)
+    del keep
+    if rc:
+        _raise(rc)
+    return out[:n]
+
+
+def search(items, scores=None, max_checks: int = 0) -> dict:
+    """Check candidates in descending score order (or as given when scores is
+    None) until one is racy; returns first (index or -1), checks, seconds and
+    the racy candidate's report."""
+    n = len(items)
+    hs, gs, ss, inputs, keep = _items_arrays(items)
+    sc = None
+    if scores is not None:
+        sc = np.ascontiguousarray(np.asarray(scores, dtype=np.float32))
+        if sc.shape != (n,):
+            raise ValueError("one score per candidate")
+    res = _SearchResult()
+    found = ctypes.POINTER(_Report)()
+    rc = load().rc_search(hs, gs, ss, inputs, n,
+                          sc.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if sc is not None else None,
+                          max_checks, ctypes.byref(res), ctypes.byref(found))
+    del keep
+    if rc:
+        _raise(rc)
+    return dict(first=int(res.first), checks=int(res.checks), seconds=float(res.seconds),
+                report=_report(found) if found else None)
+
+
+class MLP:
+    """Ranking network (128 -> 256 -> 256 -> 256 -> 1) on the GPU.  Inputs
+    are CUDA float32 tensors: features [n, 128], labels [n]."""
+
+    def __init__(self, seed: int = 0, capacity: int = 65536):
+        self._h = ctypes.c_void_p()
+        rc = load().rc_mlp_create(seed, capacity, ctypes.byref(self._h))
+        if rc:
+            _raise(rc)
+        self.capacity = capacity
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.rc_mlp_free(self._h)
+            self._h = None
+
+    @staticmethod
+    def _dev(t, cols=None):
+        if not (_is_torch_cuda(t) and str(t.dtype) == "torch.float32" and t.is_contiguous()):
+            raise ValueError("expected a contiguous float32 CUDA tensor")
+        if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+            raise ValueError(f"expected shape [n, {cols}]")
+        return ctypes.c_void_p(t.data_ptr())
+
+    @staticmethod
+    def _stream():
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def params(self) -> np.ndarray:
+        p = np.zeros(MLP_PARAMS, dtype=np.float32)
+        rc = load().rc_mlp_get_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if rc:
+            _raise(rc)
+        return p
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        if p.shape != (MLP_PARAMS,):
+            raise ValueError("parameter vector of the wrong size")
+        rc = load().rc_mlp_set_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if rc:
+            _raise(rc)
+
+    def forward(self, x):
+        import torch
+        out = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        rc = load().rc_mlp_forward(self._h, self._dev(x, N_FEATURES), x.shape[0], ctypes.c_void_p(out.data_ptr()),
+                                   self._stream())
+        if rc:
+            _raise(rc)
+        return out
+
+    def grad(self, x, y):
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        rc = load().rc_mlp_grad(self._h, self._dev(x, N_FEATURES), self._dev(y), x.shape[0],
+                                g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss), self._stream())
+        if rc:
+            _raise(rc)
+        return g, float(loss.value)
+
+    def train(self, x, y, epochs: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0) -> np.ndarray:
+        losses = np.zeros(max(epochs, 1), dtype=np.float32)
+        rc = load().rc_mlp_train(self._h, self._dev(x, N_FEATURES), self._dev(y), x.shape[0], epochs, batch, lr,
+                                 seed, losses.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self._stream())
+        if rc:
+            _raise(rc)
+        return losses[:epochs]

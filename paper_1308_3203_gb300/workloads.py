@@ -439,3 +439,99 @@ def tiny_kernel(seed: int) -> Instance:
     src = f"kernel tiny({decl}) {{\n" + "\n".join("  " + x for x in lines) + "\n}\n"
     A = rng.integers(0, 4, size=L, dtype=np.int32)
     return Instance(f"tiny-s{seed}", src, G, S, [A])
+
+
+# ----------------------------------------------------------------------------
+# proposal kernels: races that appear only for some candidate instances
+
+
+@dataclasses.dataclass
+class ProposalKernel:
+    name: str
+    src: str
+    L: int        # global A[] length
+    LI: int       # global In[] length
+    V: int        # In[] values are uniform in [0, V)
+    seed: int
+
+    def instance(self, groups: int, group_size: int, input_seed: int) -> Instance:
+        rng = np.random.default_rng([11, self.seed, input_seed])
+        A = rng.integers(0, 16, size=self.L, dtype=np.int32)
+        In = rng.integers(0, self.V, size=self.LI, dtype=np.int32)
+        return Instance(f"{self.name}-G{groups}-S{group_size}-i{input_seed}", self.src, groups, group_size, [A, In])
+
+
+def proposal_kernel(seed: int) -> ProposalKernel:
+    """A kernel whose races depend on the launch shape and the input, each
+    racy statement on roughly one candidate in eight: stores gated on
+    ``tid >= K`` (K in [700, 1024)) or ``wg >= K`` (K in [24, 64)),
+    indices ``(a*gtid + B) % L`` that collide only past L/gcd(a, L)
+    work-items (L log-uniform in [8K, 256K]), a local array indexed
+    ``tid % m`` (m in [700, 1024): racy for larger groups), a store under a
+    branch on an input value that few positions hold, and read-then-write
+    neighbours under ``tid >= K``.  One to four such statements among
+    private arithmetic and plain loads, up to two barriers."""
+    rng = np.random.default_rng([10, seed])
+    L = int(round(math.exp(rng.uniform(math.log(8192), math.log(262144)))))
+    LI = int(round(math.exp(rng.uniform(math.log(256), math.log(4096)))))
+    V = LI * int(rng.integers(2, 17))
+    lines = []
+
+    def filler():
+        k = rng.random()
+        v = f"v{int(rng.integers(4))}"
+        if k < 0.5:
+            return [f"{v} = {int(rng.integers(-3, 4))} * tid + {int(rng.integers(16))};"]
+        if k < 0.8:
+            return [f"{v} = A[(tid + {int(rng.integers(L))}) % {L}];"]
+        return [f"{v} = {v} * {int(rng.integers(1, 4))} + wg;"]
+
+    def gated():
+        k = int(rng.integers(6))
+        B = int(rng.integers(L))
+        d = int(rng.integers(16))
+        if k == 0:
+            K = int(rng.integers(700, 1024))
+            return [f"if (tid >= {K}) {{", f"  A[{B}] = {int(rng.choice([-2, -1, 1, 2, 3]))} * tid + {d};", "}"]
+        if k == 1:
+            K = int(rng.integers(24, 64))
+            return [f"if (wg >= {K}) {{", f"  A[(wg + {B}) % {L}] = tid + {d};", "}"]
+        if k == 2:
+            a = int(rng.integers(1, 4))
+            return [f"A[({a} * gtid + {B}) % {L}] = gtid + {d};"]
+        if k == 3:
+            m = int(rng.integers(700, 1024))
+            return [f"Lc[tid % {m}] = tid + {d};"]
+        if k == 4:
+            t = int(rng.integers(V))
+            return [f"x = In[gtid % {LI}];", f"if (x == {t}) {{", f"  A[{B}] = gtid;", "}"]
+        K = int(rng.integers(700, 1024))
+        return [f"y = A[(tid + {B}) % {L}];", f"if (tid >= {K}) {{", f"  A[(tid + {B + 1}) % {L}] = y + 1;", "}"]
+
+    n_gated = int(rng.integers(1, 5))
+    n_fill = int(rng.integers(2, 9))
+    kinds = ["g"] * n_gated + ["f"] * n_fill
+    rng.shuffle(kinds)
+    for kd in kinds:
+        lines += gated() if kd == "g" else filler()
+    tops = [i for i, x in enumerate(lines) if not x.startswith(" ") and not x.startswith("}")]
+    n_bar = int(rng.integers(0, 3))
+    pos = sorted(rng.choice(len(tops), size=min(n_bar, len(tops)), replace=False).tolist())
+    for p in reversed(pos):
+        lines.insert(tops[p], "barrier;")
+    src = ("kernel proposal(global int A[], global int In[], local int Lc[1024]) {\n"
+           + "\n".join("  " + x for x in lines) + "\n}\n")
+    return ProposalKernel(f"prop-s{seed}", src, L, LI, V, seed)
+
+
+def proposal_candidates(seed: int, n: int = 64) -> list:
+    """The candidate instances of a proposal kernel, in enumeration order:
+    (groups, group_size, input_seed) with group size a multiple of 32 in
+    [32, 1024], group count log-uniform in [1, 64]."""
+    rng = np.random.default_rng([12, seed])
+    out = []
+    for _ in range(n):
+        S = 32 * int(rng.integers(1, 33))
+        G = int(round(math.exp(rng.uniform(0.0, math.log(64)))))
+        out.append((max(1, min(64, G)), S, int(rng.integers(1 << 31))))
+    return out

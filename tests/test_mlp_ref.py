@@ -1,0 +1,91 @@
+"""Pins of the CPU reference of the ranking network (no GPU): its gradient
+against central finite differences of its own loss in float64, its bfloat16
+rounding against torch's conversion, and closed forms of a degenerate
+network."""
+import numpy as np
+import pytest
+
+from oracle import mlp_ref as M
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(size=4000).astype(np.float32) * 10.0 ** rng.integers(-8, 8, size=4000),
+                        # exact ties between two bfloat16 values: low 16 bits 0x8000
+                        (np.arange(1, 2001, dtype=np.uint32) << 16 | 0x8000).view(np.float32),
+                        np.array([0.0, -0.0, 1.0, -1.0, 3.0e38], dtype=np.float32)])
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(M.bf16(x), want)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_gradient_matches_finite_differences(seed):
+    rng = np.random.default_rng(seed)
+    p = M.init_params(seed)
+    X = rng.normal(size=(6, M.IN))
+    y = rng.integers(0, 2, size=6).astype(np.float64)
+    _, g = M.loss_and_grad(p, X, y, bf16_points=False, dtype=np.float64)
+    off = M.offsets()
+    idx = []
+    for name, (a, b, _) in off.items():  # parameters of every block
+        idx += list(rng.choice(np.arange(a, b), size=min(12, b - a), replace=False))
+    eps = 1e-6
+    for i in idx:
+        q = p.copy()
+        q[i] += eps
+        lp, _ = M.loss_and_grad(q, X, y, bf16_points=False, dtype=np.float64)
+        q[i] -= 2 * eps
+        lm, _ = M.loss_and_grad(q, X, y, bf16_points=False, dtype=np.float64)
+        fd = (lp - lm) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
+
+
+def test_zero_network_closed_form():
+    """All weights and hidden biases zero, b4 = c: every score is
+    sigmoid(c), the loss is mean(log(1 + e^c) - y c), dL/db4 = mean(p - y)
+    and every other gradient is zero (the hidden units are all 0)."""
+    c = 0.7
+    p = np.zeros(M.N_PARAMS)
+    p[-1] = c
+    X = np.random.default_rng(1).normal(size=(5, M.IN))
+    y = np.array([1, 0, 1, 1, 0], dtype=np.float64)
+    prob, _ = M.forward(p, X, bf16_points=False, dtype=np.float64)
+    s = 1 / (1 + np.exp(-c))
+    np.testing.assert_allclose(prob, s, rtol=1e-15)
+    loss, g = M.loss_and_grad(p, X, y, bf16_points=False, dtype=np.float64)
+    assert loss == pytest.approx(np.mean(np.log1p(np.exp(c)) - y * c), rel=1e-14)
+    assert g[-1] == pytest.approx(np.mean(s - y), rel=1e-13)
+    assert np.all(g[:-1] == 0)
+
+
+def test_one_unit_path_closed_form():
+    """Only unit 0 of each layer is live: W1[0] = e_0, W2[0][0] = W3[0][0] = 1,
+    w4[0] = 1.  For x_0 > 0 the score is sigmoid(x_0 + b4) and
+    dL/dW1[0][0] = (p - y) x_0 / n, for x_0 < 0 it is sigmoid(b4) with a
+    zero W1 gradient (the ReLU is closed)."""
+    d = {k: np.zeros(s) for k, s in M.SIZES}
+    d["W1"][0, 0] = 1
+    d["W2"][0, 0] = 1
+    d["W3"][0, 0] = 1
+    d["w4"][0] = 1
+    d["b4"][0] = -0.25
+    p = M.pack(d)
+    X = np.zeros((2, M.IN))
+    X[0, 0], X[1, 0] = 1.5, -2.0
+    y = np.array([0.0, 1.0])
+    prob, _ = M.forward(p, X, bf16_points=False, dtype=np.float64)
+    np.testing.assert_allclose(prob, 1 / (1 + np.exp(-np.array([1.25, -0.25]))), rtol=1e-14)
+    _, g = M.loss_and_grad(p, X, y, bf16_points=False, dtype=np.float64)
+    G = M.unpack(g)
+    assert G["W1"][0, 0] == pytest.approx((prob[0] - 0.0) * 1.5 / 2, rel=1e-13)
+    assert G["b4"][0] == pytest.approx(((prob[0] - 0) + (prob[1] - 1)) / 2, rel=1e-13)
+
+
+def test_bf16_points_stay_close_to_exact():
+    """Rounding at the BF16 points changes scores by far less than they vary."""
+    p = M.init_params(4)
+    X = np.random.default_rng(4).normal(size=(64, M.IN))
+    a, _ = M.forward(p, X, bf16_points=True)
+    b, _ = M.forward(p, X, bf16_points=False, dtype=np.float64)
+    assert np.max(np.abs(a - b)) < 0.02
