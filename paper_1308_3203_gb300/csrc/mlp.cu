@@ -255,13 +255,13 @@ __global__ void vecsum_kernel(const float *v, int n, float *part) {
     part[blockIdx.x] = t;
   }
 }
-// out[i] = sum over z of part[z][i], in split order
-__global__ void reduce_parts_kernel(const float *part, int splits, int count, float *out) {
+// out[i] = scale * (sum over z of part[z][i]), summed in split order
+__global__ void reduce_parts_kernel(const float *part, int splits, int count, float *out, float scale = 1.0f) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   float s = 0.0f;
   for (int z = 0; z < splits; z++) s += part[(size_t)z * count + i];
-  out[i] = s;
+  out[i] = s * scale;
 }
 
 __global__ void adam_kernel(float *P, const float *G, float *Mm, float *Vv, bf16 *Pb, size_t n, float lr, float b1,
@@ -399,7 +399,7 @@ void mean_loss(rc_mlp *m, int n, int slot, cudaStream_t s) {
   count_launch();
   vecsum_kernel<<<chunks, kColRows, 0, s>>>(m->loss, n, m->part);
   count_launch();
-  reduce_parts_kernel<<<1, 1, 0, s>>>(m->part, chunks, 1, m->scal + slot);
+  reduce_parts_kernel<<<1, 1, 0, s>>>(m->part, chunks, 1, m->scal + slot, 1.0f / n);
 }
 
 void adam(rc_mlp *m, float lr, cudaStream_t s) {

@@ -36,7 +36,7 @@ def feature_rows(rc, n, seed):
         _, items = proposal.kernel_candidates(1000 + seed * 100 + s)
         rows.append(rc.features(items))
         s += 1
-    X = np.concatenate(rows)[: n // 2]
+    X = np.concatenate(rows)[: n // 2] if rows else np.zeros((0, M.IN), np.float32)
     rng = np.random.default_rng(seed)
     return np.concatenate([X, rng.uniform(0, 1, size=(n - len(X), M.IN)).astype(np.float32)])
 
