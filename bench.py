@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch-kernels", type=int, default=10_000,
                    help="size of the batched-checking measurement (0 skips it)")
+    p.add_argument("--proposal-kernels", type=int, default=2000,
+                   help="training kernels of the learned-proposal measurement (0 skips it)")
     return p.parse_args()
 
 
@@ -163,6 +165,46 @@ def batch_leg(rc, W, n_kernels):
             "kernels_per_s": n_kernels / dt, "accesses_per_s": acc / dt, "seconds": dt,
             "accesses": acc, "timing": "host wall clock around rc_check_batch (host inputs, "
                                       "H2D and report D2H included)"}
+
+
+def proposal_leg(rc, n_train, n_eval=200, epochs=20):
+    """Learned proposal: label every candidate of n_train kernels with the
+    checker, train the ranking network on the GPU, then compare ranked search
+    with plain enumeration on n_eval held-out kernels."""
+    import torch
+    from paper_1308_3203_gb300 import proposal
+    t0 = time.perf_counter()
+    X, y, _ = proposal.dataset(range(n_train))
+    t_data = time.perf_counter() - t0
+    m = rc.MLP(seed=0, capacity=8192)
+    xt = torch.from_numpy(X).cuda()
+    yt = torch.from_numpy(y).cuda()
+    batch = 2048
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = m.train(xt, yt, epochs=epochs, batch=batch, lr=2e-3, seed=1)
+    t_train = time.perf_counter() - t0
+    # multiply-adds x 2 per example: forward 3 GEMM layers + head; backward
+    # weight gradients of 3 layers + head, data gradients of layers 2 and 3
+    fwd = 2 * (128 * 256 + 2 * 256 * 256 + 256)
+    flops = 3 * fwd - 2 * 128 * 256
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        m.forward(xt)
+    torch.cuda.synchronize()
+    t_inf = (time.perf_counter() - t0) / 5
+    res = proposal.compare_search(m, range(10**6, 10**6 + n_eval))
+    res.pop("rows")
+    return {"workload": f"{n_train} training kernels x 64 candidates (group size 32..1024 step 32, "
+                        f"1..64 groups, input seed), {n_eval} held-out kernels",
+            "train_examples": int(len(y)), "racy_fraction": float(y.mean()),
+            "label_and_feature_seconds": t_data, "epochs": epochs, "batch": batch,
+            "train_seconds": t_train, "train_examples_per_s": epochs * len(y) / t_train,
+            "train_tflops": epochs * len(y) * flops / t_train / 1e12,
+            "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1]),
+            "inference_examples_per_s": len(y) / t_inf,
+            "search": res}
 
 
 def main():
@@ -286,6 +328,8 @@ def main():
     }
     if args.batch_kernels > 0:
         out["batch"] = batch_leg(rc, W, args.batch_kernels)
+    if args.proposal_kernels > 0:
+        out["proposal"] = proposal_leg(rc, args.proposal_kernels)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:
