@@ -4,6 +4,9 @@
 // Step 1 (run reduce): every run of records of one (cell, work-item) becomes
 // a Summary: the range of values the work-item observed, the range it wrote,
 // the value of its last write (highest sequence number) and its access count.
+// The kernel of the last run also stores the number of summaries in device
+// memory, so the later steps run over an upper bound (the record count)
+// without the host reading the exact counts in between.
 //
 // Step 2 (per cell, over the summaries of that cell in work-item order):
 //  * WW (Sec. 1 and the race rule of Sec. 4: differing values at a barrier
@@ -40,7 +43,7 @@ __global__ void run_heads_kernel(const LogRec *r, uint64_t n, uint32_t *head) {
 }
 
 __global__ void run_reduce_kernel(const LogRec *r, uint64_t n, const uint32_t *head,
-                                  const uint32_t *runidx, Summary *sum, uint32_t *khead) {
+                                  const uint32_t *runidx, Summary *sum, uint32_t *khead, uint32_t *nsum) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || !head[i]) return;
   const LogRec f = r[i];
@@ -54,7 +57,8 @@ __global__ void run_reduce_kernel(const LogRec *r, uint64_t n, const uint32_t *h
   s.wmax = INT32_MIN;
   s.wlast = 0;
   uint32_t cnt = 0, flags = 0, lastseq = 0;
-  for (uint64_t j = i; j < n; j++) {
+  uint64_t j = i;
+  for (; j < n; j++) {
     const LogRec x = r[j];
     if (x.key != f.key || (x.tw & 0x7FFFFFFFu) != g) break;
     cnt++;
@@ -76,6 +80,7 @@ __global__ void run_reduce_kernel(const LogRec *r, uint64_t n, const uint32_t *h
   const uint32_t k = runidx[i];
   sum[k] = s;
   khead[k] = (i == 0 || r[i - 1].key != f.key) ? 1u : 0u;
+  if (j == n) *nsum = k + 1;  // the last run
 }
 
 // uniform value of a range, or "mixed"
@@ -217,6 +222,7 @@ __device__ __forceinline__ void emit_cell(const ClassifyArgs &a, uint32_t key, c
 __global__ void key_classify_kernel(const Summary *sum, uint64_t nsum, const uint32_t *khead,
                                     const uint32_t *keyidx, uint32_t *nrec, ClassifyArgs a) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  nsum = *a.nsum;  // the launch covers an upper bound
   if (i >= nsum || !khead[i]) return;
   if (i + kBigCell < nsum && sum[i + kBigCell].key == sum[i].key) {  // a large cell: one CTA's work
     a.big[atomicAdd(a.nbig, 1u)] = (uint32_t)i;
@@ -231,6 +237,7 @@ __global__ void key_emit_kernel(const Summary *sum, uint64_t nsum, const uint32_
                                 const uint32_t *keyidx, const uint32_t *nrec, const uint32_t *recoff,
                                 OutRec *out, ClassifyArgs a) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  nsum = *a.nsum;
   if (i >= nsum || !khead[i]) return;
   const uint32_t k = keyidx[i];
   if (nrec[k] == 0) return;
@@ -302,6 +309,7 @@ __global__ void __launch_bounds__(kBigThreads) big_classify_kernel(const Summary
   __shared__ int32_t s_commit;
   const uint32_t t = threadIdx.x, nt = blockDim.x;
   const uint32_t nbig = *a.nbig;
+  nsum = *a.nsum;
   for (uint32_t q = blockIdx.x; q < nbig; q += gridDim.x) {
     const uint64_t b = a.big[q];
     const uint32_t key = sum[b].key;
@@ -424,9 +432,9 @@ void launch_run_heads(const LogRec *r, uint64_t n, uint32_t *head, cudaStream_t 
   if (n) run_heads_kernel<<<blocks_for(n), kThreads, 0, s>>>(r, n, head);
 }
 void launch_run_reduce(const LogRec *r, uint64_t n, const uint32_t *head, const uint32_t *runidx,
-                       Summary *sum, uint32_t *khead, cudaStream_t s) {
+                       Summary *sum, uint32_t *khead, uint32_t *nsum, cudaStream_t s) {
   if (n) count_launch();
-  if (n) run_reduce_kernel<<<blocks_for(n), kThreads, 0, s>>>(r, n, head, runidx, sum, khead);
+  if (n) run_reduce_kernel<<<blocks_for(n), kThreads, 0, s>>>(r, n, head, runidx, sum, khead, nsum);
 }
 void launch_key_classify(const Summary *sum, uint64_t nsum, const uint32_t *khead,
                          const uint32_t *keyidx, uint32_t *nrec, const ClassifyArgs &a,

@@ -208,6 +208,7 @@ struct ClassifyArgs {
   // cells above kBigCell summaries: head index of each, how many, their results
   uint32_t *big = nullptr, *nbig = nullptr;
   CellResult *bigres = nullptr;
+  const uint32_t *nsum = nullptr;  // device: number of summaries (launches cover an upper bound)
   // batches: cells of several instances end to end; records name their instance
   uint32_t n_kernels = 0;
   const uint64_t *kbase = nullptr;  // sorted first cell of each instance
@@ -215,8 +216,9 @@ struct ClassifyArgs {
   uint32_t *rec_kernel = nullptr;   // instance of each emitted record
 };
 void launch_run_heads(const LogRec *r, uint64_t n, uint32_t *head, cudaStream_t s);
+// also stores the number of summaries in *nsum (device)
 void launch_run_reduce(const LogRec *r, uint64_t n, const uint32_t *head, const uint32_t *runidx,
-                       Summary *sum, uint32_t *khead, cudaStream_t s);
+                       Summary *sum, uint32_t *khead, uint32_t *nsum, cudaStream_t s);
 void launch_key_classify(const Summary *sum, uint64_t nsum, const uint32_t *khead,
                          const uint32_t *keyidx, uint32_t *nrec, const ClassifyArgs &a,
                          cudaStream_t s);

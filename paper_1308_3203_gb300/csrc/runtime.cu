@@ -70,6 +70,10 @@ struct DevBuf {
     }
     return static_cast<T *>(p);
   }
+  template <class T>
+  T *as() {
+    return static_cast<T *>(p);
+  }
   void release() {
     if (p) cudaFree(p);
     p = nullptr;
@@ -208,6 +212,10 @@ struct Tuner {
     if (e.best) return e.best;
     return e.n[1] <= e.n[2] ? 1 : 2;
   }
+  bool decided(const std::string &key) {
+    load();
+    return entries[key].best != 0;
+  }
   void record(const std::string &key, int strategy, double ms, uint64_t accesses) {
     Entry &e = entries[key];
     if (e.best || accesses == 0 || strategy < 1 || strategy > 2) return;
@@ -302,23 +310,23 @@ struct BatchMap {  // cell space of a batch: instance first cells and sizes (dev
 void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t interval, const Layout &L,
                   int32_t *snap, uint32_t *hstats, std::vector<OutRec> &races, cudaStream_t s,
                   const BatchMap *bm = nullptr) {
+  // Summaries, cells and records number at most n, so every step runs over n
+  // entries: key heads and record counts past the real ends are zero (set
+  // here), and the kernels that read summaries take their exact number from
+  // device memory; the host reads one count, the number of records to emit.
   uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(n), scan_tmp_words(n)));
   uint32_t *head = W.head.get<uint32_t>(n), *runidx = W.runidx.get<uint32_t>(n);
   launch_run_heads(sorted, n, head, s);
   scan_exclusive(head, runidx, n, tmp, s);
   Summary *sum = W.sum.get<Summary>(n);
   uint32_t *khead = W.khead.get<uint32_t>(n), *keyidx = W.keyidx.get<uint32_t>(n);
-  launch_run_reduce(sorted, n, head, runidx, sum, khead, s);
-  CK(cudaMemcpyAsync(hstats, runidx + n - 1, 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hstats + 1, head + n - 1, 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  const uint64_t nsum = (uint64_t)hstats[0] + hstats[1];
-  scan_exclusive(khead, keyidx, nsum, tmp, s);
-  CK(cudaMemcpyAsync(hstats, keyidx + nsum - 1, 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hstats + 1, khead + nsum - 1, 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  const uint64_t nkeys = (uint64_t)hstats[0] + hstats[1];
-  uint32_t *nrec = W.nrec.get<uint32_t>(nkeys), *recoff = W.recoff.get<uint32_t>(nkeys);
+  uint32_t *counts = W.nbig.get<uint32_t>(2);  // [0] large cells, [1] summaries
+  CK(cudaMemsetAsync(khead, 0, n * 4, s));
+  CK(cudaMemsetAsync(counts, 0, 8, s));
+  launch_run_reduce(sorted, n, head, runidx, sum, khead, counts + 1, s);
+  scan_exclusive(khead, keyidx, n, tmp, s);
+  uint32_t *nrec = W.nrec.get<uint32_t>(n), *recoff = W.recoff.get<uint32_t>(n);
+  CK(cudaMemsetAsync(nrec, 0, n * 4, s));
   ClassifyArgs ca{interval, (uint32_t)L.GT, (uint32_t)std::max<uint64_t>(L.LT, 1), snap};
   if (bm) {
     ca.n_kernels = bm->n;
@@ -326,22 +334,22 @@ void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t inter
     ca.kGT = bm->kGT;
     ca.kLT = bm->kLT;
   }
-  ca.big = W.big.get<uint32_t>(big_cells_cap(nsum));
-  ca.bigres = W.bigres.get<CellResult>(big_cells_cap(nsum));
-  ca.nbig = W.nbig.get<uint32_t>(1);
-  CK(cudaMemsetAsync(ca.nbig, 0, 4, s));
-  launch_key_classify(sum, nsum, khead, keyidx, nrec, ca, s);
-  launch_big_classify(sum, nsum, keyidx, nrec, ca, s);
-  scan_exclusive(nrec, recoff, nkeys, tmp, s);
-  CK(cudaMemcpyAsync(hstats, recoff + nkeys - 1, 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hstats + 1, nrec + nkeys - 1, 4, cudaMemcpyDeviceToHost, s));
+  ca.big = W.big.get<uint32_t>(big_cells_cap(n));
+  ca.bigres = W.bigres.get<CellResult>(big_cells_cap(n));
+  ca.nbig = counts;
+  ca.nsum = counts + 1;
+  launch_key_classify(sum, n, khead, keyidx, nrec, ca, s);
+  launch_big_classify(sum, n, keyidx, nrec, ca, s);
+  scan_exclusive(nrec, recoff, n, tmp, s);
+  CK(cudaMemcpyAsync(hstats, recoff + n - 1, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hstats + 1, nrec + n - 1, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const uint64_t nrecs = (uint64_t)hstats[0] + hstats[1];
   if (nrecs == 0) return;
   OutRec *out = W.out.get<OutRec>(nrecs);
   if (bm) ca.rec_kernel = W.reckern.get<uint32_t>(nrecs);
-  launch_key_emit(sum, nsum, khead, keyidx, nrec, recoff, out, ca, s);
-  launch_big_emit(sum, nsum, keyidx, nrec, recoff, out, ca, s);
+  launch_key_emit(sum, n, khead, keyidx, nrec, recoff, out, ca, s);
+  launch_big_emit(sum, n, keyidx, nrec, recoff, out, ca, s);
   size_t old = races.size();
   races.resize(old + nrecs);
   CK(cudaMemcpyAsync(races.data() + old, out, nrecs * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
@@ -394,20 +402,24 @@ uint32_t shadow_next_tag(Workspace &W, cudaStream_t s) {
 
 // Shadow path: commit single-writer cells from the own-write tables, send
 // the log records of shared written cells through the exact sort path.
-void classify_shadow(Workspace &W, const LogRec *log, uint32_t n_slices, uint64_t slice,
-                     const uint32_t *count, uint64_t keys, uint64_t N, uint32_t interval,
-                     const Layout &L, int32_t *snap, const uint32_t *owner, uint32_t tag, const uint2 *ow,
-                     const uint32_t *ow_count, uint32_t *dcount, uint32_t *hstats,
-                     std::vector<OutRec> &races, cudaStream_t s) {
+// Shadow path, device half: commit the single-writer cells from the
+// own-write tables and compact the records of every other written cell into
+// W.logb; the number of compacted records lands in *dcount (64-bit).
+void shadow_launch(Workspace &W, const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
+                   uint64_t N, int32_t *snap, const uint32_t *owner, uint32_t tag, const uint2 *ow,
+                   const uint32_t *ow_count, uint32_t *dcount, cudaStream_t s) {
   launch_shadow_commit(ow, ow_count, N, (uint32_t)N, owner, tag, snap, s);
   unsigned long long *cnt = reinterpret_cast<unsigned long long *>(dcount);
   CK(cudaMemsetAsync(cnt, 0, 8, s));
   LogRec *shared = W.logb.get<LogRec>((uint64_t)n_slices * slice);
   launch_shadow_compact(log, n_slices, slice, count, owner, tag, shared, cnt, s);
-  CK(cudaMemcpyAsync(hstats, cnt, 8, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  const uint64_t m = *reinterpret_cast<uint64_t *>(hstats);
+}
+
+// Shadow path, host half: the m compacted records are sorted and classified.
+void shadow_finish(Workspace &W, uint64_t m, uint64_t keys, uint64_t N, uint32_t interval, const Layout &L,
+                   int32_t *snap, uint32_t *hstats, std::vector<OutRec> &races, cudaStream_t s) {
   if (m == 0) return;
+  LogRec *shared = W.logb.as<LogRec>();
   uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(m), scan_tmp_words(m)));
   LogRec *other = W.compact.get<LogRec>(m);
   LogRec *sorted = sort_log(shared, other, m, bitwidth(N), bitwidth(keys) + bitwidth(N), tmp, s);
@@ -609,11 +621,19 @@ rc_report *run_instance(const Instance &I) {
     a.ow_count = ow_cnt;
     a.owner = strategy == 2 ? owner : nullptr;
     a.tag = strategy == 2 ? shadow_next_tag(W, s) : 0;
-    if (!fixed_strategy) CK(cudaEventRecord(g_tev[0], s));
+    const bool tuning = !fixed_strategy && !g_tuner.decided(tkey);
+    if (tuning) CK(cudaEventRecord(g_tev[0], s));
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
     launch_interp(a, I.G, smem, s);
     CK(cudaGetLastError());
-    if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], s));
+    if (g_prof.on) {
+      CK(cudaEventRecord(g_prof.ev[1], s));
+      CK(cudaEventRecord(g_prof.ev[2], s));
+    }
+    // the shadow path's commit and compaction need nothing from the host:
+    // they are queued before the one synchronisation that reads the stats
+    if (strategy == 2)
+      shadow_launch(W, log, n_slices, slice, warp_count, N, snap, owner, a.tag, ow, ow_cnt, dstats + ST_SCRATCH, s);
     CK(cudaMemcpyAsync(hstats, dstats, stat_words * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const uint32_t flags = hstats[ST_FLAGS];
@@ -629,12 +649,11 @@ rc_report *run_instance(const Instance &I) {
       g_prof.launches[0]++;
       g_prof.ms[0] += ms;
       g_prof.bytes[0] += 12.0 * (double)(acc_g - prev_acc[0]);
-      CK(cudaEventRecord(g_prof.ev[2], s));
     }
     // ---- classification + commit
     if (strategy == 2) {
-      classify_shadow(W, log, n_slices, slice, warp_count, L.keys, N, interval, L, snap, owner, a.tag, ow,
-                      ow_cnt, dstats + ST_SCRATCH, hstats + stat_words, races, s);
+      const uint64_t m = *reinterpret_cast<const uint64_t *>(hstats + ST_SCRATCH);
+      shadow_finish(W, m, L.keys, N, interval, L, snap, hstats + stat_words, races, s);
     } else {
       classify_sorted(W, log, n_slices, slice, warp_count, L.keys, N, interval, L, snap, hstats + stat_words,
                       races, s);
@@ -648,7 +667,7 @@ rc_report *run_instance(const Instance &I) {
       g_prof.ms[1] += ms;
       g_prof.bytes[1] += 12.0 * (double)(acc_g - prev_acc[0]);
     }
-    if (!fixed_strategy) {  // autotuner sample: this interval's time per access
+    if (tuning) {  // autotuner sample: this interval's time per access
       CK(cudaEventRecord(g_tev[1], s));
       CK(cudaEventSynchronize(g_tev[1]));
       float ms = 0;
@@ -891,13 +910,14 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   std::vector<uint32_t> rk;
   for (uint32_t round = 0; active; round++) {
     const int strat = strategy ? strategy : g_tuner.choose(tkey);
+    const bool tuning = !strategy && !g_tuner.decided(tkey);
     std::memcpy(hdesc, desc.data(), n * sizeof(BatchDesc));
     hround[0] = round;
     hround[1] = strat == 2 ? shadow_next_tag(W, bs) : 0;
     hround[2] = strat == 2 ? 1u : 0u;
     CK(cudaMemcpyAsync(ddesc, hdesc, n * sizeof(BatchDesc), cudaMemcpyHostToDevice, bs));
     CK(cudaMemcpyAsync(dround, hround, 16, cudaMemcpyHostToDevice, bs));
-    if (!strategy) CK(cudaEventRecord(g_tev[0], bs));
+    if (tuning) CK(cudaEventRecord(g_tev[0], bs));
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], bs));
     CK(cudaGraphLaunch(exec, bs));
     for (int q = 0; q < 3; q++) count_launch();  // kernels replayed by the graph
@@ -933,7 +953,7 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
       g_prof.launches[1]++;
       g_prof.ms[1] += ms;
     }
-    if (!strategy) {
+    if (tuning) {
       CK(cudaEventRecord(g_tev[1], bs));
       CK(cudaEventSynchronize(g_tev[1]));
       float ms = 0;
