@@ -38,6 +38,27 @@ WORKLOAD = ("large instance: 1024 groups x 256 work-items, 8 barriers, 200 state
 SAMPLE_GROUPS = 96
 
 
+# DRAM traffic of interp_kernel per launch: dram__bytes_read.sum +
+# dram__bytes_write.sum, mean over the 9 launches of one check, from
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
+#       -k regex:interp_kernel -s 27 -c 9 python bench.py --steps 3 --warmup 3 \
+#       --no-cpu-baseline --batch-kernels 0 --proposal-kernels 0
+# (profiles/interp_kernel_large_instance.md).  It holds only for the kernel
+# sources it was taken on; any change to them reports null.
+INTERP_TRAFFIC = {"sources_sha256": "5893b564e63b51cf305821cf5100dd7c97eacfcc4b89120ff03fbe8c77434827",
+                  "bytes_per_launch": 148880441}
+INTERP_SOURCES = ("paper_1308_3203_gb300/csrc/interp.cu", "paper_1308_3203_gb300/csrc/device.cuh")
+
+
+def interp_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in INTERP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -74,8 +95,9 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(1.0)  # nvidia-smi takes a moment before its first sample
         except OSError:
             self.p = None
 
@@ -149,22 +171,53 @@ def cpu_baseline():
                       f"{n} run(s) in {dt:.1f} s, single-threaded"}
 
 
-def batch_leg(rc, W, n_kernels):
-    """Batched checking of n uneven kernels in one rc_check_batch call."""
-    insts = W.batch_kernels(0, n_kernels, processes=min(16, os.cpu_count() or 1))
+def shard(n: int, rank: int, world: int) -> range:
+    """The units rank `rank` of `world` takes: every world-th, from rank."""
+    return range(rank, n, world)
+
+
+def combine(values, dist, op: str):
+    """Reduce a list of floats over the ranks ("max" or "sum"); identity
+    without a process group."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    backend = dist.get_backend()
+    dev = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(x) for x in t.cpu()]
+
+
+def batch_leg(rc, W, n_kernels, rank=0, world=1, dist=None):
+    """Batched checking of n uneven kernels: each rank checks its shard in
+    one rc_check_batch call (independent problems: no exchange); kernels/s
+    = all kernels / the slowest rank's time."""
+    params = W._batch_params(0, n_kernels)
+    mine = [params[i] for i in shard(n_kernels, rank, world)]
+    if len(mine) > 64 and (os.cpu_count() or 1) > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count())) as pool:
+            insts = pool.map(W._batch_one, mine, chunksize=64)
+    else:
+        insts = [W._batch_one(p) for p in mine]
     items = [(rc.compile(i.src), i.groups, i.group_size, i.globals) for i in insts]
     rc.check_batch(items[:64], want_final=False)  # warm-up (and autotuner exploration)
     import torch
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     got = rc.check_batch(items, want_final=False)
     dt = time.perf_counter() - t0
     acc = sum(g["n_access"] for g in got)
+    dt_max, = combine([dt], dist, "max")
+    acc_all, n_all = combine([acc, len(items)], dist, "sum")
     return {"workload": f"{n_kernels} kernels: group size log-uniform 32-1024, 1-64 groups, "
                         "16-512 statements, 0-8 barriers, global int32 arrays 1K-1M",
-            "kernels_per_s": n_kernels / dt, "accesses_per_s": acc / dt, "seconds": dt,
-            "accesses": acc, "timing": "host wall clock around rc_check_batch (host inputs, "
-                                      "H2D and report D2H included)"}
+            "kernels_per_s": n_all / dt_max, "accesses_per_s": acc_all / dt_max, "seconds": dt_max,
+            "accesses": int(acc_all), "timing": "host wall clock around rc_check_batch (host inputs, "
+                                                "H2D and report D2H included), slowest rank"}
 
 
 def proposal_leg(rc, n_train, n_eval=200, epochs=20):
@@ -282,16 +335,8 @@ def main():
     clk = clocks.stop()
 
     acc_step = rep["n_access"]
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms, ms_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max, ms_e2e = float(t[0]), float(t[1])
-        a = torch.tensor([acc_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(a)
-        acc_all = float(a[0])
-    else:
-        acc_all = float(acc_step)
+    t_max, ms_e2e = combine([ms, ms_e2e], dist, "max")
+    acc_all, = combine([acc_step], dist, "sum")
     value = acc_all * args.steps / (t_max / 1e3)
     e2e = acc_all * args.steps / (ms_e2e / 1e3)
 
@@ -303,8 +348,11 @@ def main():
     p0 = prof[0]
     interp_ms = p0["ms"] / max(p0["launches"], 1)
     achieved = (p0["bytes"] / max(p0["launches"], 1)) / (interp_ms / 1e3) / 1e9 if interp_ms else 0.0
+    traffic = INTERP_TRAFFIC["bytes_per_launch"] \
+        if INTERP_TRAFFIC["sources_sha256"] == interp_sources_sha256() else None
     roof = {"kernel": "interp_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+            "algorithmic_bytes_per_launch": p0["bytes"] / max(p0["launches"], 1),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s",
             "avg_launch_ms": interp_ms,
             "classify_ms_per_interval": prof[1]["ms"] / max(prof[1]["launches"], 1),
@@ -327,7 +375,7 @@ def main():
         "clocks": clk,
     }
     if args.batch_kernels > 0:
-        out["batch"] = batch_leg(rc, W, args.batch_kernels)
+        out["batch"] = batch_leg(rc, W, args.batch_kernels, rank, world, dist)
     if args.proposal_kernels > 0:
         out["proposal"] = proposal_leg(rc, args.proposal_kernels)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -80,17 +80,22 @@ struct InterpArgs {
 constexpr uint32_t kIdMask = (1u << 26) - 1;
 // Warp-aggregated claim, called by exactly the lanes in `mask` (lane
 // `lane` claiming cell `key` for work-item `id`; ids grow by one per lane
-// within a warp).  Lanes on the same cell form one group whose lowest lane
-// issues the two reductions for the group's largest and smallest id, so a
-// cell that a whole warp touches costs one pair of reductions, not 32:
-// same-address reductions serialise in L2.
+// within a warp).  When every lane is on one cell (an index that does not
+// depend on the work-item), the lowest lane issues the two reductions for
+// the largest and smallest id: same-address reductions serialise in L2, and
+// a cell that a whole warp touches would otherwise take 32 pairs.  Lanes on
+// different cells claim their own.
 __device__ __forceinline__ void shadow_claim_warp(uint32_t *owner, uint32_t mask, uint32_t key, bool write,
                                                   uint32_t tag, uint32_t id, uint32_t lane) {
-  const uint32_t g = __match_any_sync(mask, key);
-  if (lane != (uint32_t)(__ffs(g) - 1)) return;
-  const uint32_t hi = 31u - __clz(g);
   uint32_t *w = owner + 4ull * key + (write ? 0 : 2);
-  atomicMax(w, (tag << 26) | (id + (hi - lane)));
+  if (__reduce_min_sync(mask, key) == __reduce_max_sync(mask, key)) {
+    if (lane != (uint32_t)(__ffs(mask) - 1)) return;
+    const uint32_t hi = 31u - __clz(mask);
+    atomicMax(w, (tag << 26) | (id + (hi - lane)));
+    atomicMax(w + 1, (tag << 26) | (kIdMask - id));
+    return;
+  }
+  atomicMax(w, (tag << 26) | id);
   atomicMax(w + 1, (tag << 26) | (kIdMask - id));
 }
 
