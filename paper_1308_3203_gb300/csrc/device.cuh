@@ -67,6 +67,7 @@ struct InterpArgs {
   uint32_t *ow_count;             // [N] own-write entries per work-item
   uint32_t *owner;                // shadow owner table (nullptr: not used)
   uint32_t tag;
+  const uint32_t *proceed;        // non-null: the launch does nothing unless *proceed != 0
 };
 
 // ---- shadow owner table (shadow.cu)
@@ -127,6 +128,11 @@ void count_launch();
 enum Flag : uint32_t { FLAG_LOG_FULL = 1, FLAG_OW_FULL = 2, FLAG_ERR_FULL = 4 };
 
 void launch_interp(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStream_t s);
+// Gate of a speculatively queued interval: *proceed = 1 iff the previous
+// interval overflowed nothing, compacted no record for the exact sort, and
+// its work-items all stopped at one barrier (the run goes on unchanged).
+void launch_interval_gate(const uint32_t *flags, const unsigned long long *compacted, const uint32_t *stop_cnt,
+                          uint32_t n_barriers, uint32_t *proceed, cudaStream_t s);
 size_t interp_smem_bytes(uint32_t n_mems, uint32_t n_regs, uint32_t S, uint32_t ow_slots);
 cudaError_t interp_configure();
 constexpr uint32_t kConstCodeInsns = 4000;  // programs up to this size run from constant memory

@@ -52,6 +52,7 @@ __constant__ uint4 c_code[kConstCodeInsns];
 
 template <bool kConst>
 __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
+  if (A.proceed && *A.proceed == 0) return;  // a closed gate: the host runs this interval later
   extern __shared__ __align__(16) unsigned char smem[];
   const uint4 *__restrict__ code = reinterpret_cast<const uint4 *>(A.code);
   MemInfo *mems = reinterpret_cast<MemInfo *>(smem);
@@ -351,7 +352,25 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
     A.warp_count[(uint64_t)blockIdx.x * A.warps_per_cta + warp] = wfill < A.warp_slice ? wfill : (uint32_t)A.warp_slice;
 }
 
+__global__ void interval_gate_kernel(const uint32_t *flags, const unsigned long long *compacted,
+                                     const uint32_t *stop_cnt, uint32_t n_barriers, uint32_t *proceed) {
+  uint32_t n_points = 0;
+  bool any_barrier = false;
+  for (uint32_t k = 0; k <= n_barriers; k++) {
+    if (!stop_cnt[k]) continue;
+    n_points++;
+    if (k < n_barriers) any_barrier = true;
+  }
+  *proceed = (*flags == 0 && *compacted == 0 && n_points == 1 && any_barrier) ? 1u : 0u;
+}
+
 }  // namespace
+
+void launch_interval_gate(const uint32_t *flags, const unsigned long long *compacted, const uint32_t *stop_cnt,
+                          uint32_t n_barriers, uint32_t *proceed, cudaStream_t s) {
+  count_launch();
+  interval_gate_kernel<<<1, 1, 0, s>>>(flags, compacted, stop_cnt, n_barriers, proceed);
+}
 
 size_t interp_smem_bytes(uint32_t n_mems, uint32_t n_regs, uint32_t S, uint32_t ow_slots) {
   return (size_t)n_mems * sizeof(MemInfo) + (size_t)n_regs * S * 4 + (size_t)ow_slots * S * 8;

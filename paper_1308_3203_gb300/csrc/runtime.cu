@@ -103,6 +103,7 @@ struct Workspace {
       bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround, big, bigres, nbig;
   HostBuf hstats, hrecs, hround, hdesc;
   cudaStream_t bstream = nullptr;
+  cudaEvent_t sev[2] = {nullptr, nullptr};  // stats of an interval (by parity) reached the host
   bool configured = false, batch_configured = false;
   uint32_t epoch = 0;
   void release_all() {
@@ -564,12 +565,17 @@ rc_report *run_instance(const Instance &I) {
   uint2 *ow = W.ow.get<uint2>(N * capw);
   LogRec *log = W.loga.get<LogRec>(cap);
   const uint32_t err_cap = (uint32_t)std::min<uint64_t>(N, 1u << 24);
-  OutRec *errs = W.errs.get<OutRec>(err_cap);
+  // two of everything an interval reports (by interval parity), so the next
+  // interval can be queued while the host reads this one's
+  OutRec *errs2 = W.errs.get<OutRec>(2ull * err_cap);
   const uint32_t nstops = P.n_barriers + 1;
   const size_t stat_words = ST_STOPS + 2 * nstops;
-  uint32_t *dstats = W.stats.get<uint32_t>(stat_words);
-  uint32_t *hstats = W.hstats.get<uint32_t>(stat_words + 8);
-  CK(cudaMemsetAsync(dstats, 0, stat_words * 4, s));
+  uint32_t *dstats2 = W.stats.get<uint32_t>(2 * stat_words + 2);
+  uint32_t *gate = dstats2 + 2 * stat_words;  // gate[parity]: the speculatively queued interval may run
+  uint32_t *hstats2 = W.hstats.get<uint32_t>(2 * stat_words + 8);
+  uint32_t *hscratch = hstats2 + 2 * stat_words;
+  if (!W.sev[0])
+    for (auto &e : W.sev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
   const std::string tkey = single_key(N, P.max_access_per_interval);
   uint32_t *owner = nullptr;
@@ -578,51 +584,52 @@ rc_report *run_instance(const Instance &I) {
   uint32_t *warp_count = W.ctacnt.get<uint32_t>(n_slices);
   uint32_t *ow_cnt = W.owcnt.get<uint32_t>(N);
 
-  std::vector<OutRec> races, errors;
-  uint32_t interval = 0;
-  uint64_t prev_acc[2] = {0, 0};
-  for (;; interval++) {
-    CK(cudaMemsetAsync(dstats + ST_FLAGS, 0, 8, s));
-    CK(cudaMemsetAsync(dstats + ST_STOPS, 0xFF, nstops * 4, s));
-    CK(cudaMemsetAsync(dstats + ST_STOPS + nstops, 0, nstops * 4, s));
-    InterpArgs a{};
-    a.code = dcode;
-    a.mems = dmems;
-    a.n_insn = (uint32_t)P.code.size();
-    a.n_regs = P.n_regs;
-    a.n_mems = (uint32_t)P.mems.size();
-    a.n_barriers = P.n_barriers;
-    a.S = I.S;
-    a.G = I.G;
-    a.group0 = 0;
-    a.GT = (uint32_t)L.GT;
-    a.LT = (uint32_t)L.LT;
-    a.interval = interval;
-    a.snap = snap;
-    a.regs = regs;
-    a.pc = pc;
-    a.st = st;
-    a.ow = ow;
-    a.capw = (uint32_t)std::min<uint64_t>(capw, 0xFFFFFFFFu);
-    a.ow_stride = (uint32_t)N;
-    a.ow_slots = ow_slots;
-    a.log = log;
-    a.warp_count = warp_count;
-    a.warps_per_cta = wpc;
-    a.warp_slice = slice;
-    a.errs = errs;
-    a.err_count = dstats + ST_ERRCNT;
-    a.err_cap = err_cap;
-    a.stop_min = dstats + ST_STOPS;
-    a.stop_cnt = dstats + ST_STOPS + nstops;
-    a.acc = reinterpret_cast<unsigned long long *>(dstats + ST_ACC);
-    a.flags = dstats + ST_FLAGS;
-    const int strategy = fixed_strategy ? fixed_strategy : g_tuner.choose(tkey);
-    a.ow_count = ow_cnt;
+  InterpArgs base{};
+  base.code = dcode;
+  base.mems = dmems;
+  base.n_insn = (uint32_t)P.code.size();
+  base.n_regs = P.n_regs;
+  base.n_mems = (uint32_t)P.mems.size();
+  base.n_barriers = P.n_barriers;
+  base.S = I.S;
+  base.G = I.G;
+  base.group0 = 0;
+  base.GT = (uint32_t)L.GT;
+  base.LT = (uint32_t)L.LT;
+  base.snap = snap;
+  base.regs = regs;
+  base.pc = pc;
+  base.st = st;
+  base.ow = ow;
+  base.capw = (uint32_t)std::min<uint64_t>(capw, 0xFFFFFFFFu);
+  base.ow_stride = (uint32_t)N;
+  base.ow_slots = ow_slots;
+  base.log = log;
+  base.warp_count = warp_count;
+  base.warps_per_cta = wpc;
+  base.warp_slice = slice;
+  base.err_cap = err_cap;
+  base.ow_count = ow_cnt;
+  auto dbuf = [&](uint32_t k) { return dstats2 + (k & 1) * stat_words; };
+  auto hbuf = [&](uint32_t k) { return hstats2 + (k & 1) * stat_words; };
+  // one interval's interpreter launch (gated: runs only if gate[k & 1] is set on the device)
+  auto enqueue_interp = [&](uint32_t k, int strategy, uint32_t tag, bool gated, bool timed) {
+    uint32_t *d = dbuf(k);
+    CK(cudaMemsetAsync(d, 0, ST_STOPS * 4, s));  // counters, flags, error count, scratch
+    CK(cudaMemsetAsync(d + ST_STOPS, 0xFF, nstops * 4, s));
+    CK(cudaMemsetAsync(d + ST_STOPS + nstops, 0, nstops * 4, s));
+    InterpArgs a = base;
+    a.interval = k;
+    a.errs = errs2 + (uint64_t)(k & 1) * err_cap;
+    a.err_count = d + ST_ERRCNT;
+    a.stop_min = d + ST_STOPS;
+    a.stop_cnt = d + ST_STOPS + nstops;
+    a.acc = reinterpret_cast<unsigned long long *>(d + ST_ACC);
+    a.flags = d + ST_FLAGS;
     a.owner = strategy == 2 ? owner : nullptr;
-    a.tag = strategy == 2 ? shadow_next_tag(W, s) : 0;
-    const bool tuning = !fixed_strategy && !g_tuner.decided(tkey);
-    if (tuning) CK(cudaEventRecord(g_tev[0], s));
+    a.tag = tag;
+    a.proceed = gated ? gate + (k & 1) : nullptr;
+    if (timed) CK(cudaEventRecord(g_tev[0], s));
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
     launch_interp(a, I.G, smem, s);
     CK(cudaGetLastError());
@@ -630,33 +637,66 @@ rc_report *run_instance(const Instance &I) {
       CK(cudaEventRecord(g_prof.ev[1], s));
       CK(cudaEventRecord(g_prof.ev[2], s));
     }
-    // the shadow path's commit and compaction need nothing from the host:
-    // they are queued before the one synchronisation that reads the stats
+  };
+  // the work after the interpreter that needs nothing from the host, then the stats read
+  auto enqueue_post = [&](uint32_t k, int strategy, uint32_t tag) {
     if (strategy == 2)
-      shadow_launch(W, log, n_slices, slice, warp_count, N, snap, owner, a.tag, ow, ow_cnt, dstats + ST_SCRATCH, s);
-    CK(cudaMemcpyAsync(hstats, dstats, stat_words * 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const uint32_t flags = hstats[ST_FLAGS];
+      shadow_launch(W, log, n_slices, slice, warp_count, N, snap, owner, tag, ow, ow_cnt, dbuf(k) + ST_SCRATCH, s);
+    CK(cudaMemcpyAsync(hbuf(k), dbuf(k), stat_words * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(W.sev[k & 1], s));
+  };
+
+  std::vector<OutRec> races, errors;
+  uint64_t tot_g = 0, tot_l = 0;
+  uint32_t interval = 0;
+  int strategy = fixed_strategy ? fixed_strategy : g_tuner.choose(tkey);
+  bool timed = !fixed_strategy && !g_tuner.decided(tkey);  // autotuner sample of this interval
+  uint32_t tag = strategy == 2 ? shadow_next_tag(W, s) : 0;
+  enqueue_interp(0, strategy, tag, false, timed);
+  enqueue_post(0, strategy, tag);
+  for (;; interval++) {
+    // Speculation: when this interval and the next take the shadow path and
+    // nothing is being timed, the next interval's interpreter is queued now,
+    // behind a gate the device sets only if this interval compacted no
+    // record, overflowed nothing and its barrier agreement lets the run go
+    // on -- exactly the case in which the host would launch it unchanged.
+    bool next_queued = false;
+    uint32_t next_tag = 0;
+    if (strategy == 2 && !timed && !g_prof.on) {
+      const int ns = fixed_strategy ? fixed_strategy : g_tuner.choose(tkey);
+      if (ns == 2 && (fixed_strategy || g_tuner.decided(tkey))) {
+        next_tag = shadow_next_tag(W, s);
+        uint32_t *d = dbuf(interval);
+        launch_interval_gate(d + ST_FLAGS, reinterpret_cast<const unsigned long long *>(d + ST_SCRATCH),
+                             d + ST_STOPS + nstops, P.n_barriers, gate + ((interval + 1) & 1), s);
+        enqueue_interp(interval + 1, 2, next_tag, true, false);
+        next_queued = true;
+      }
+    }
+    CK(cudaEventSynchronize(W.sev[interval & 1]));
+    const uint32_t *h = hbuf(interval);
+    const uint32_t flags = h[ST_FLAGS];
     if (flags) throw Fail{RC_E_CAPACITY, "interval log, own-write table or error log overflowed"};
-    const uint64_t acc_g = *reinterpret_cast<uint64_t *>(hstats + ST_ACC);
-    const uint64_t acc_l = *reinterpret_cast<uint64_t *>(hstats + ST_ACC + 2);
-    std::vector<uint32_t> stop_min(hstats + ST_STOPS, hstats + ST_STOPS + nstops);
-    std::vector<uint32_t> stop_cnt(hstats + ST_STOPS + nstops, hstats + ST_STOPS + 2 * nstops);
-    const uint32_t nerr = std::min(hstats[ST_ERRCNT], err_cap);
+    const uint64_t acc_g = *reinterpret_cast<const uint64_t *>(h + ST_ACC);
+    const uint64_t acc_l = *reinterpret_cast<const uint64_t *>(h + ST_ACC + 2);
+    const uint64_t m = *reinterpret_cast<const uint64_t *>(h + ST_SCRATCH);
+    std::vector<uint32_t> stop_min(h + ST_STOPS, h + ST_STOPS + nstops);
+    std::vector<uint32_t> stop_cnt(h + ST_STOPS + nstops, h + ST_STOPS + 2 * nstops);
+    const uint32_t nerr = std::min(h[ST_ERRCNT], err_cap);
+    tot_g += acc_g;
+    tot_l += acc_l;
     if (g_prof.on) {
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, g_prof.ev[0], g_prof.ev[1]));
       g_prof.launches[0]++;
       g_prof.ms[0] += ms;
-      g_prof.bytes[0] += 12.0 * (double)(acc_g - prev_acc[0]);
+      g_prof.bytes[0] += 12.0 * (double)acc_g;
     }
     // ---- classification + commit
     if (strategy == 2) {
-      const uint64_t m = *reinterpret_cast<const uint64_t *>(hstats + ST_SCRATCH);
-      shadow_finish(W, m, L.keys, N, interval, L, snap, hstats + stat_words, races, s);
+      shadow_finish(W, m, L.keys, N, interval, L, snap, hscratch, races, s);
     } else {
-      classify_sorted(W, log, n_slices, slice, warp_count, L.keys, N, interval, L, snap, hstats + stat_words,
-                      races, s);
+      classify_sorted(W, log, n_slices, slice, warp_count, L.keys, N, interval, L, snap, hscratch, races, s);
     }
     if (g_prof.on) {
       CK(cudaEventRecord(g_prof.ev[3], s));
@@ -665,21 +705,20 @@ rc_report *run_instance(const Instance &I) {
       CK(cudaEventElapsedTime(&ms, g_prof.ev[2], g_prof.ev[3]));
       g_prof.launches[1]++;
       g_prof.ms[1] += ms;
-      g_prof.bytes[1] += 12.0 * (double)(acc_g - prev_acc[0]);
+      g_prof.bytes[1] += 12.0 * (double)acc_g;
     }
-    if (tuning) {  // autotuner sample: this interval's time per access
+    if (timed) {  // autotuner sample: this interval's time per access
       CK(cudaEventRecord(g_tev[1], s));
       CK(cudaEventSynchronize(g_tev[1]));
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, g_tev[0], g_tev[1]));
-      g_tuner.record(tkey, strategy, ms, (acc_g + acc_l) - (prev_acc[0] + prev_acc[1]));
+      g_tuner.record(tkey, strategy, ms, acc_g + acc_l);
     }
-    prev_acc[0] = acc_g;
-    prev_acc[1] = acc_l;
     // ---- error records of this interval
     if (nerr) {
       std::vector<OutRec> e(nerr);
-      CK(cudaMemcpyAsync(e.data(), errs, nerr * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(e.data(), errs2 + (uint64_t)(interval & 1) * err_cap, nerr * sizeof(OutRec),
+                         cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       std::sort(e.begin(), e.end(), [](const OutRec &x, const OutRec &y) {
         return x.cls != y.cls ? x.cls < y.cls : x.t_a < y.t_a;
@@ -688,9 +727,21 @@ rc_report *run_instance(const Instance &I) {
     }
     // ---- barrier agreement (barrier-release rule of Sec. 4)
     if (!barrier_agreement(interval, P.n_barriers, stop_min.data(), stop_cnt.data(), errors)) break;
+    if (next_queued && m == 0) {  // the gate opened: the next interval is already running
+      tag = next_tag;
+      enqueue_post(interval + 1, 2, tag);
+      continue;
+    }
+    // the next interval starts after this one's classification
+    strategy = fixed_strategy ? fixed_strategy : g_tuner.choose(tkey);
+    timed = !fixed_strategy && !g_tuner.decided(tkey);
+    if (strategy == 2) tag = next_queued ? next_tag : shadow_next_tag(W, s);  // a closed gate used no claims
+    else tag = 0;
+    enqueue_interp(interval + 1, strategy, tag, false, timed);
+    enqueue_post(interval + 1, strategy, tag);
   }
 
-  return make_report(races, errors, interval + 1, prev_acc[0], prev_acc[1], L.GT,
+  return make_report(races, errors, interval + 1, tot_g, tot_l, L.GT,
                      (I.in->flags & RC_WANT_FINAL_MEMORY) ? snap : nullptr, s);
 }
 
