@@ -11,11 +11,7 @@
 // end to end.  The interpreter step is the single-instance one (min-PC
 // reconvergence, indexed LD/ST, ballot-ranked log appends, owner claims);
 // see interp.cu for the semantics it implements.
-#include <cooperative_groups.h>
-
 #include "device.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace rc {
 namespace {
@@ -300,17 +296,9 @@ __global__ void batch_compact_kernel(BatchArgs A, LogRec *out, unsigned long lon
   const uint32_t k = A.task_kernel[task];
   if (!A.desc[k].active) return;
   const BatchDesc &D = A.desc[k];
-  const uint32_t n = A.warp_count[task];
-  const uint4 *src = reinterpret_cast<const uint4 *>(A.log) + D.slice_off + (uint64_t)(task - D.task_off) * D.slice;
-  for (uint32_t i = threadIdx.x & 31u; i < n; i += 32) {
-    const uint4 r = src[i];
-    if (A.round[2] && !shadow_needs_exact(A.owner, r.x, A.round[1])) continue;
-    cg::coalesced_group g = cg::coalesced_threads();
-    unsigned long long base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(total, (unsigned long long)g.size());
-    base = g.shfl(base, 0);
-    reinterpret_cast<uint4 *>(out)[base + g.thread_rank()] = r;
-  }
+  compact_slice(reinterpret_cast<const uint4 *>(A.log) + D.slice_off + (uint64_t)(task - D.task_off) * D.slice,
+                A.warp_count[task], A.round[2] ? A.owner : nullptr, A.round[1], reinterpret_cast<uint4 *>(out),
+                total, threadIdx.x & 31u);
 }
 
 // One thread per work-item of every active instance (task-major).

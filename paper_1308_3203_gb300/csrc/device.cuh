@@ -112,6 +112,44 @@ __device__ __forceinline__ bool shadow_needs_exact(const uint32_t *owner, uint32
   return rmax != wmax || rmin != wmax;
 }
 
+// One warp appends the records of its log slice src[0, n) that need the
+// exact classification (all of them when owner is null) to out, at
+// positions taken from *total.  Each lane holds four records in flight, so
+// the owner-table lookups overlap, and the warp takes its positions with one
+// atomic per 128 records; a work-item's records keep their slice order.
+// Called by all 32 lanes of a warp.
+__device__ __forceinline__ void compact_slice(const uint4 *src, uint32_t n, const uint32_t *owner, uint32_t tag,
+                                              uint4 *out, unsigned long long *total, uint32_t lane) {
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t base = 0; base < n; base += 128) {
+    uint4 r[4];
+    bool need[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const uint32_t i = base + q * 32 + lane;
+      r[q] = i < n ? src[i] : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      need[q] = base + q * 32 + lane < n && (!owner || shadow_needs_exact(owner, r[q].x, tag));
+    uint32_t bal[4], tot = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      bal[q] = __ballot_sync(0xFFFFFFFFu, need[q]);
+      tot += __popc(bal[q]);
+    }
+    if (tot == 0) continue;
+    unsigned long long pos = 0;
+    if (lane == 0) pos = atomicAdd(total, (unsigned long long)tot);
+    pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (need[q]) out[pos + __popc(bal[q] & lt)] = r[q];
+      pos += __popc(bal[q]);
+    }
+  }
+}
+
 // log: n_slices warp slices of `slice` records, count[i] valid in slice i
 void launch_shadow_compact(const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
                            const uint32_t *owner, uint32_t tag, LogRec *out, unsigned long long *total,

@@ -12,11 +12,7 @@
 // (delayed visibility); shared writes go to the work-item's own-write table.
 // Every access is appended to the interval's log with one warp-aggregated
 // atomic per instruction and one 16-byte store per work-item.
-#include <cooperative_groups.h>
-
 #include "device.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace rc {
 namespace {

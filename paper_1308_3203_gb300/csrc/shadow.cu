@@ -8,11 +8,7 @@
 //  * the log records of every other written cell are compacted (one warp-
 //    aggregated atomic per warp and instruction) and classified exactly by
 //    the sort path.
-#include <cooperative_groups.h>
-
 #include "device.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace rc {
 namespace {
@@ -23,17 +19,8 @@ __global__ void shadow_compact_kernel(const LogRec *log, uint32_t n_slices, uint
                                       unsigned long long *total) {
   const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= n_slices) return;
-  const uint32_t n = count[w];
-  const uint4 *src = reinterpret_cast<const uint4 *>(log) + (uint64_t)w * slice;
-  for (uint32_t i = threadIdx.x & 31u; i < n; i += 32) {
-    const uint4 r = src[i];
-    if (!shadow_needs_exact(owner, r.x, tag)) continue;
-    cg::coalesced_group g = cg::coalesced_threads();
-    unsigned long long base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(total, (unsigned long long)g.size());
-    base = g.shfl(base, 0);
-    reinterpret_cast<uint4 *>(out)[base + g.thread_rank()] = r;
-  }
+  compact_slice(reinterpret_cast<const uint4 *>(log) + (uint64_t)w * slice, count[w], owner, tag,
+                reinterpret_cast<uint4 *>(out), total, threadIdx.x & 31u);
 }
 
 __global__ void shadow_commit_kernel(const uint2 *ow, const uint32_t *ow_count, uint64_t N, uint32_t ow_stride,
