@@ -231,6 +231,32 @@ int rc_profile_get(int kind, uint64_t *launches, double *ms, double *bytes);
  * (every launch counts, whatever the profiling state). */
 uint64_t rc_kernel_launches(void);
 
+/* ---- exhaustive interleavings of small instances
+ *
+ * The checker runs one canonical schedule per barrier interval and flags
+ * conflicts conservatively.  Sec. 4 defines a race over ALL schedules: two
+ * schedules reaching different shared states at a barrier.  rc_explore runs
+ * the instance like rc_check and, before each of its first max_intervals
+ * intervals, runs every schedule of that interval with one truly shared
+ * memory from the checker's state at the interval's start: a flagged
+ * interval is confirmed when several shared states are reachable at its
+ * closing barrier or a read depends on the schedule. */
+typedef struct {
+  uint32_t interval;
+  uint32_t n_end_states; /* distinct shared memories (global + local) at the closing barrier */
+  uint32_t deviated;     /* 1: in some schedule some read differs from its work-item's solo run */
+  uint32_t complete;     /* 1: every schedule explored within max_states */
+  uint64_t n_states;     /* distinct states visited */
+} rc_explore_interval;
+/* Explore every schedule of the first max_intervals intervals of a small
+ * instance (groups * group_size <= 16 work-items, <= 4096 cells, <= 64
+ * registers).  out holds max_intervals entries; *n_out receives the number
+ * filled (the run's intervals, at most max_intervals).  max_states bounds
+ * the distinct states per interval (0: 1,000,000); beyond it an interval is
+ * reported incomplete.  Errors: RC_E_INVALID, RC_E_CAPACITY, RC_E_CUDA. */
+int rc_explore(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in, uint64_t max_states,
+               rc_explore_interval *out, uint32_t max_intervals, uint32_t *n_out);
+
 /* ---- learned proposal: which candidate instances to check first
  *
  * The method needs, per kernel, a set of candidate instances (launch shape

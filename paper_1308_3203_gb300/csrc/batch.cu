@@ -12,24 +12,11 @@
 // reconvergence, indexed LD/ST, ballot-ranked log appends, owner claims);
 // see interp.cu for the semantics it implements.
 #include "device.cuh"
+#include "semantics.cuh"
 
 namespace rc {
 namespace {
 
-__device__ __forceinline__ int32_t bidiv(int32_t a, int32_t b) {
-  if (b == 0) return 0;
-  if (a == INT32_MIN && b == -1) return INT32_MIN;
-  return a / b;
-}
-__device__ __forceinline__ int32_t bimod(int32_t a, int32_t b) {
-  if (b == 0) return 0;
-  const uint32_t m = b < 0 ? 0u - (uint32_t)b : (uint32_t)b;
-  if ((int32_t)m > 0) {
-    const int32_t r = a % (int32_t)m;
-    return r < 0 ? r + (int32_t)m : r;
-  }
-  return a & 0x7FFFFFFF;
-}
 __device__ __forceinline__ uint64_t bbloom(uint32_t key) { return 1ull << ((key * 2654435761u) >> 26); }
 
 __device__ __forceinline__ void batch_err(const BatchArgs &A, uint32_t k, const OutRec &r) {
@@ -109,56 +96,16 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_interp_kernel(BatchArg
       const int32_t x = REG(ra);
       const int32_t yr = REG(rb);
       if (cls == CC_ALU) {
-        const uint32_t ux = (uint32_t)x, uy = (uint32_t)yr, ui = (uint32_t)imm;
-        int32_t r;
-        switch (raw.x & 0xFFu) {
-          case OP_MOVI: r = imm; break;
-          case OP_MOV: r = x; break;
-          case OP_ADD: r = (int32_t)(ux + uy); break;
-          case OP_SUB: r = (int32_t)(ux - uy); break;
-          case OP_MUL: r = (int32_t)(ux * uy); break;
-          case OP_ADDI: r = (int32_t)(ux + ui); break;
-          case OP_MULI: r = (int32_t)(ux * ui); break;
-          case OP_ANDI: r = x & imm; break;
-          case OP_RSUBI: r = (int32_t)(ui - ux); break;
-          case OP_MADI: r = (int32_t)(ux * ui + uy); break;
-          case OP_NEG: r = (int32_t)(0u - ux); break;
-          case OP_NOT: r = x == 0; break;
-          case OP_LT: r = x < yr; break;
-          case OP_LE: r = x <= yr; break;
-          case OP_GT: r = x > yr; break;
-          case OP_GE: r = x >= yr; break;
-          case OP_EQ: r = x == yr; break;
-          case OP_NE: r = x != yr; break;
-          case OP_LTI: r = x < imm; break;
-          case OP_LEI: r = x <= imm; break;
-          case OP_GTI: r = x > imm; break;
-          case OP_GEI: r = x >= imm; break;
-          case OP_EQI: r = x == imm; break;
-          case OP_NEI: r = x != imm; break;
-          case OP_BZ: r = x == 0; break;
-          case OP_BFLTI: r = !(x < imm); break;
-          case OP_BFLEI: r = !(x <= imm); break;
-          case OP_BFGTI: r = !(x > imm); break;
-          case OP_BFGEI: r = !(x >= imm); break;
-          case OP_BFEQI: r = x != imm; break;
-          case OP_BFNEI: r = x == imm; break;
-          case OP_LOOP: r = (int32_t)(ux + 1u); break;
-          default: r = 1; break;
-        }
+        const int32_t r = sem_alu(raw.x & 0xFFu, x, yr, imm);
         if (act) {
           if (ctl & AL_WRITE) REG(d) = r;
-          const uint32_t mode = (ctl >> AL_MODE_SHIFT) & 3u;
-          const bool take = mode == 2u || (mode == 1u && ((ctl & AL_LOOPCOND) ? r < imm : r != 0));
-          pc = take ? tgt : pc + 1;
+          pc = sem_branch(ctl, r, imm) ? tgt : pc + 1;
         }
         continue;
       }
       if (cls == CC_LD || cls == CC_ST) {
         const uint4 mm = __ldg(mems + (ctl >> CTL_MEM_SHIFT));  // MemInfo: len, base, space
-        uint32_t ui = (uint32_t)x + (uint32_t)imm;
-        if (ctl & CTL_AM) ui &= ((2u << ((ctl >> CTL_K_SHIFT) & 0x1Fu)) - 1u) >> 1;
-        const int32_t idx = (int32_t)(ui + tgt);
+        const int32_t idx = sem_index(x, imm, (int32_t)tgt, ctl);
         const bool inb = (uint32_t)idx < mm.x;
         const uint32_t logging = __ballot_sync(lanes, act && inb);
         const uint32_t slot_pos = wfill + __popc(logging & lane_lt);
@@ -219,13 +166,11 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_interp_kernel(BatchArg
       if (!act) continue;
       pc++;
       switch (cls) {
-        case CC_DIVMOD: {
-          const int32_t y = (ctl & DM_YIMM) ? imm : yr;
-          REG(d) = (ctl & DM_MOD) ? bimod(x, y) : bidiv(x, y);
+        case CC_DIVMOD:
+          REG(d) = sem_divmod(ctl, x, yr, imm);
           break;
-        }
         case CC_LOGIC:
-          REG(d) = (ctl & 1u) ? ((x != 0) || (yr != 0)) : ((x != 0) && (yr != 0));
+          REG(d) = sem_logic(ctl, x, yr);
           break;
         case CC_SIZE:
           REG(d) = (int32_t)__ldg(mems + (ctl >> CTL_MEM_SHIFT)).x;

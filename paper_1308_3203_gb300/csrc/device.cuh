@@ -224,6 +224,27 @@ void launch_batch_interp(const BatchArgs &a, uint32_t grid, size_t smem, cudaStr
 void launch_batch_compact(const BatchArgs &a, LogRec *out, unsigned long long *total, cudaStream_t s);
 void launch_batch_commit(const BatchArgs &a, cudaStream_t s);
 
+// ---- interleaving explorer (explore.cu)
+// The checker's state at the start of one interval of a small instance.
+struct ExploreInput {
+  const Insn *code;
+  const MemInfo *mems;  // device
+  uint32_t n_insn, N, S, n_regs, cells, GT, LT, interval, max_access;
+  const int32_t *snap, *regs;  // cells; registers [n_regs][N]
+  const uint32_t *pc, *st;     // [N]
+};
+struct ExploreResult {
+  uint32_t n_end_states;  // distinct shared memories at the interval's closing barrier
+  uint32_t deviated;      // a read of some schedule differs from the work-item's solo run
+  uint32_t complete;      // every schedule was explored within the budget
+  uint64_t n_states;      // distinct states visited
+};
+struct ExploreError {
+  const char *msg;
+};
+// Every schedule of the interval from that state (throws ExploreError on a CUDA failure).
+ExploreResult explore_interval(const ExploreInput &in, uint64_t max_states, cudaStream_t s);
+
 // ---- scan / sort (sort.cu)
 // exclusive prefix sum of n uint32 values; tmp must hold scan_tmp_words(n)
 size_t scan_tmp_words(uint64_t n);

@@ -13,24 +13,11 @@
 // Every access is appended to the interval's log with one warp-aggregated
 // atomic per instruction and one 16-byte store per work-item.
 #include "device.cuh"
+#include "semantics.cuh"
 
 namespace rc {
 namespace {
 
-__device__ __forceinline__ int32_t idiv(int32_t a, int32_t b) {  // truncating; x / 0 = 0
-  if (b == 0) return 0;
-  if (a == INT32_MIN && b == -1) return INT32_MIN;  // 2^31 wraps
-  return a / b;
-}
-__device__ __forceinline__ int32_t imod(int32_t a, int32_t b) {  // Euclidean, in [0, |b|); x % 0 = 0
-  if (b == 0) return 0;
-  const uint32_t m = b < 0 ? 0u - (uint32_t)b : (uint32_t)b;
-  if ((int32_t)m > 0) {
-    const int32_t r = a % (int32_t)m;
-    return r < 0 ? r + (int32_t)m : r;
-  }
-  return a & 0x7FFFFFFF;  // |b| = 2^31
-}
 __device__ __forceinline__ uint64_t bloom_bit(uint32_t key) {
   return 1ull << ((key * 2654435761u) >> 26);
 }
@@ -117,56 +104,17 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
     const int32_t x = REG(ra);
     const int32_t yr = REG(rb);
     if (cls == CC_ALU) {  // arithmetic, moves, comparisons, branches
-      const uint32_t ux = (uint32_t)x, uy = (uint32_t)yr, ui = (uint32_t)imm;
-      int32_t r;
-      switch (raw.x & 0xFFu) {  // warp-uniform; branch forms leave r != 0 when taken
-        case OP_MOVI: r = imm; break;
-        case OP_MOV: r = x; break;
-        case OP_ADD: r = (int32_t)(ux + uy); break;
-        case OP_SUB: r = (int32_t)(ux - uy); break;
-        case OP_MUL: r = (int32_t)(ux * uy); break;
-        case OP_ADDI: r = (int32_t)(ux + ui); break;
-        case OP_MULI: r = (int32_t)(ux * ui); break;
-        case OP_ANDI: r = x & imm; break;
-        case OP_RSUBI: r = (int32_t)(ui - ux); break;
-        case OP_MADI: r = (int32_t)(ux * ui + uy); break;
-        case OP_NEG: r = (int32_t)(0u - ux); break;
-        case OP_NOT: r = x == 0; break;
-        case OP_LT: r = x < yr; break;
-        case OP_LE: r = x <= yr; break;
-        case OP_GT: r = x > yr; break;
-        case OP_GE: r = x >= yr; break;
-        case OP_EQ: r = x == yr; break;
-        case OP_NE: r = x != yr; break;
-        case OP_LTI: r = x < imm; break;
-        case OP_LEI: r = x <= imm; break;
-        case OP_GTI: r = x > imm; break;
-        case OP_GEI: r = x >= imm; break;
-        case OP_EQI: r = x == imm; break;
-        case OP_NEI: r = x != imm; break;
-        case OP_BZ: r = x == 0; break;
-        case OP_BFLTI: r = !(x < imm); break;
-        case OP_BFLEI: r = !(x <= imm); break;
-        case OP_BFGTI: r = !(x > imm); break;
-        case OP_BFGEI: r = !(x >= imm); break;
-        case OP_BFEQI: r = x != imm; break;
-        case OP_BFNEI: r = x == imm; break;
-        case OP_LOOP: r = (int32_t)(ux + 1u); break;
-        default: r = 1; break;  // OP_JMP, OP_NOP
-      }
+      // warp-uniform opcode; branch forms leave r != 0 when taken
+      const int32_t r = sem_alu(raw.x & 0xFFu, x, yr, imm);
       if (act) {
         if (ctl & AL_WRITE) REG(d) = r;
-        const uint32_t mode = (ctl >> AL_MODE_SHIFT) & 3u;
-        const bool take = mode == 2u || (mode == 1u && ((ctl & AL_LOOPCOND) ? r < imm : r != 0));
-        pc = take ? tgt : pc + 1;
+        pc = sem_branch(ctl, r, imm) ? tgt : pc + 1;
       }
       continue;
     }
     if (cls == CC_LD || cls == CC_ST) {
       const MemInfo m = mems[ctl >> CTL_MEM_SHIFT];  // (LD/ST class: operand bits)
-      uint32_t ui = (uint32_t)x + (uint32_t)imm;
-      if (ctl & CTL_AM) ui &= ((2u << ((ctl >> CTL_K_SHIFT) & 0x1Fu)) - 1u) >> 1;  // 2^k - 1
-      const int32_t idx = (int32_t)(ui + (uint32_t)tgt);
+      const int32_t idx = sem_index(x, imm, (int32_t)tgt, ctl);
       const bool inb = (uint32_t)idx < m.len;
       const uint32_t logging = __ballot_sync(lanes, act && inb);
       const uint32_t slot_pos = wfill + __popc(logging & lane_lt);
@@ -230,13 +178,11 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
     if (!act) continue;
     pc++;
     switch (cls) {
-      case CC_DIVMOD: {
-        const int32_t y = (ctl & DM_YIMM) ? imm : yr;
-        REG(d) = (ctl & DM_MOD) ? imod(x, y) : idiv(x, y);
+      case CC_DIVMOD:
+        REG(d) = sem_divmod(ctl, x, yr, imm);
         break;
-      }
       case CC_LOGIC:  // (x != 0) and / or (yr != 0)
-        REG(d) = (ctl & 1u) ? ((x != 0) || (yr != 0)) : ((x != 0) && (yr != 0));
+        REG(d) = sem_logic(ctl, x, yr);
         break;
       case CC_SIZE:
         REG(d) = (int32_t)mems[ctl >> CTL_MEM_SHIFT].len;

@@ -261,12 +261,21 @@ uint32_t bitwidth(uint64_t v) {  // bits needed to represent values < v (v >= 1)
   return std::max<uint32_t>(b, 1);
 }
 
+// Exhaustive exploration of each interval before the canonical run takes it
+// (rc_explore): results by interval.
+struct ExploreRun {
+  uint64_t max_states;
+  uint32_t max_intervals;
+  std::vector<ExploreResult> results;
+};
+
 struct Instance {
   const Program *p;
   uint32_t G, S;
   uint64_t N;
   const rc_input *in;
   cudaStream_t s;
+  ExploreRun *explore = nullptr;
 };
 
 struct Layout {
@@ -614,6 +623,30 @@ rc_report *run_instance(const Instance &I) {
   auto hbuf = [&](uint32_t k) { return hstats2 + (k & 1) * stat_words; };
   // one interval's interpreter launch (gated: runs only if gate[k & 1] is set on the device)
   auto enqueue_interp = [&](uint32_t k, int strategy, uint32_t tag, bool gated, bool timed) {
+    if (I.explore && k < I.explore->max_intervals) {  // every schedule of interval k, from this state
+      CK(cudaStreamSynchronize(s));
+      ExploreInput e{};
+      e.code = dcode;
+      e.mems = dmems;
+      e.n_insn = (uint32_t)P.code.size();
+      e.N = (uint32_t)N;
+      e.S = I.S;
+      e.n_regs = P.n_regs;
+      e.cells = (uint32_t)L.keys;
+      e.GT = (uint32_t)L.GT;
+      e.LT = (uint32_t)L.LT;
+      e.interval = k;
+      e.max_access = (uint32_t)std::min<uint64_t>(P.max_access_per_interval, 1u << 20);
+      e.snap = snap;
+      e.regs = regs;
+      e.pc = pc;
+      e.st = st;
+      try {
+        I.explore->results.push_back(explore_interval(e, I.explore->max_states, s));
+      } catch (const ExploreError &x) {
+        throw Fail{RC_E_CUDA, x.msg};
+      }
+    }
     uint32_t *d = dbuf(k);
     CK(cudaMemsetAsync(d, 0, ST_STOPS * 4, s));  // counters, flags, error count, scratch
     CK(cudaMemsetAsync(d + ST_STOPS, 0xFF, nstops * 4, s));
@@ -662,7 +695,7 @@ rc_report *run_instance(const Instance &I) {
     // on -- exactly the case in which the host would launch it unchanged.
     bool next_queued = false;
     uint32_t next_tag = 0;
-    if (strategy == 2 && !timed && !g_prof.on) {
+    if (strategy == 2 && !timed && !g_prof.on && !I.explore) {
       const int ns = fixed_strategy ? fixed_strategy : g_tuner.choose(tkey);
       if (ns == 2 && (fixed_strategy || g_tuner.decided(tkey))) {
         next_tag = shadow_next_tag(W, s);
@@ -1122,6 +1155,39 @@ int rc_check(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const 
     Instance I{&bc->prog, groups, group_size, (uint64_t)groups * group_size, in,
                static_cast<cudaStream_t>(in->cuda_stream)};
     *out = run_instance(I);
+    return RC_OK;
+  } catch (const Fail &f) {
+    return fail_code(f);
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return RC_E_NOMEM;
+  }
+}
+
+int rc_explore(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in, uint64_t max_states,
+               rc_explore_interval *out, uint32_t max_intervals, uint32_t *n_out) {
+  if (!out || !n_out) return RC_E_INVALID;
+  *n_out = 0;
+  std::lock_guard<std::mutex> lk(g_mu);
+  try {
+    check_args(bc, groups, group_size, in);
+    if ((uint64_t)groups * group_size > 16) throw Fail{RC_E_INVALID, "the explorer takes at most 16 work-items"};
+    Layout L = make_layout(bc->prog, in, groups);
+    if (L.keys > 4096) throw Fail{RC_E_INVALID, "the explorer takes at most 4096 cells"};
+    if (bc->prog.n_regs > 64) throw Fail{RC_E_INVALID, "the explorer takes at most 64 registers"};
+    ExploreRun ex{max_states ? max_states : 1000000, max_intervals, {}};
+    Instance I{&bc->prog, groups, group_size, (uint64_t)groups * group_size, in,
+               static_cast<cudaStream_t>(in->cuda_stream), &ex};
+    rc_report *r = run_instance(I);
+    rc_report_free(r);
+    for (size_t k = 0; k < ex.results.size(); k++) {
+      out[k].interval = (uint32_t)k;
+      out[k].n_end_states = ex.results[k].n_end_states;
+      out[k].deviated = ex.results[k].deviated;
+      out[k].complete = ex.results[k].complete;
+      out[k].n_states = ex.results[k].n_states;
+    }
+    *n_out = (uint32_t)ex.results.size();
     return RC_OK;
   } catch (const Fail &f) {
     return fail_code(f);

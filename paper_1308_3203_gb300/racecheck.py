@@ -55,6 +55,11 @@ class _Info(ctypes.Structure):
                                     ("max_write_per_interval", ctypes.c_uint64)]
 
 
+class _ExploreInterval(ctypes.Structure):
+    _fields_ = [("interval", ctypes.c_uint32), ("n_end_states", ctypes.c_uint32), ("deviated", ctypes.c_uint32),
+                ("complete", ctypes.c_uint32), ("n_states", ctypes.c_uint64)]
+
+
 class _SearchResult(ctypes.Structure):
     _fields_ = [("first", ctypes.c_int64), ("checks", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("seconds", ctypes.c_double)]
@@ -127,7 +132,9 @@ def load() -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_Input), ctypes.c_size_t,
                                   fp, ctypes.c_uint32, ctypes.POINTER(_SearchResult),
                                   ctypes.POINTER(ctypes.POINTER(_Report))]
-        for f in ("rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
+        lib.rc_explore.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input), ctypes.c_uint64,
+                                   ctypes.POINTER(_ExploreInterval), ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
+        for f in ("rc_explore", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
                   "rc_mlp_forward", "rc_mlp_grad", "rc_mlp_train", "rc_search"):
             getattr(lib, f).restype = c_int
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
@@ -338,6 +345,24 @@ def autotune_reset() -> None:
 def autotune_lookup(kind: int, a: int, b: int) -> int:
     """Decided strategy for a size class (0 undecided, 1 sort, 2 shadow)."""
     return int(load().rc_autotune_lookup(kind, a, b))
+
+
+def explore(bc: Bytecode, groups: int, group_size: int, globals_, max_states: int = 0,
+            max_intervals: int = 64) -> list:
+    """Every schedule of each interval of a small instance (<= 16 work-items),
+    from the checker's state at the interval's start: per interval
+    n_end_states (distinct shared memories at its closing barrier), deviated
+    (some read depends on the schedule), complete, n_states."""
+    inp, keep = _marshal(globals_, None, False)
+    out = (_ExploreInterval * max(max_intervals, 1))()
+    n = ctypes.c_uint32()
+    rc = load().rc_explore(bc.handle, groups, group_size, ctypes.byref(inp), max_states, out, max_intervals,
+                           ctypes.byref(n))
+    del keep
+    if rc:
+        _raise(rc)
+    return [dict(interval=o.interval, n_end_states=o.n_end_states, deviated=bool(o.deviated),
+                 complete=bool(o.complete), n_states=int(o.n_states)) for o in out[:n.value]]
 
 
 # ---------------------------------------------------------------- learned proposal
