@@ -257,6 +257,30 @@ typedef struct {
 int rc_explore(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in, uint64_t max_states,
                rc_explore_interval *out, uint32_t max_intervals, uint32_t *n_out);
 
+/* The interleaving product of two work-items (the fix proposed at the end of
+ * Sec. 6 for a symbolic execution that misses branches on array values):
+ * for every pair i < j of the instance's work-items, every schedule of the
+ * two alone (all other work-items do not run) from the checker's state at
+ * the start of each of the first max_intervals intervals.  It scales to
+ * more work-items than rc_explore, at the price of missing races that need
+ * three or more work-items to show. */
+typedef struct {
+  uint32_t interval;
+  uint32_t n_pairs;          /* pairs (i < j): N (N - 1) / 2                          */
+  uint32_t n_racy;           /* pairs reaching two or more shared memories            */
+  uint32_t n_deviated;       /* pairs with a read that depends on the schedule        */
+  uint32_t first_i, first_j; /* smallest racy pair in (i, j) order, 0xFFFFFFFF if none */
+  uint32_t complete;         /* 1: every schedule explored within max_states          */
+  uint32_t reserved;
+  uint64_t n_states;         /* distinct (pair, state) items visited                  */
+} rc_pair_interval;
+/* groups * group_size <= 256 work-items, <= 4096 cells, <= 64 registers.
+ * pair_detail (may be NULL) receives max_intervals x n_pairs values, pairs in
+ * (i, j) order: distinct shared memories | (schedule-dependent read) << 31. */
+int rc_explore_pairs(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in,
+                     uint64_t max_states, rc_pair_interval *out, uint32_t max_intervals, uint32_t *n_out,
+                     uint32_t *pair_detail);
+
 /* ---- learned proposal: which candidate instances to check first
  *
  * The method needs, per kernel, a set of candidate instances (launch shape

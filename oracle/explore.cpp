@@ -182,6 +182,11 @@ using namespace orc;
 using namespace orc::ex;
 
 struct ExploreResult {
+  // pair mode: per interval, per pair (i < j) in (i, j) order, the distinct
+  // shared states reached when only i and j run from the interval's start
+  // (all other work-items frozen) | (a read of i or j depends on the
+  // schedule) << 31; empty for an interval that starts from several states
+  std::vector<std::vector<uint32_t>> pairs;
   std::vector<uint32_t> n_end_states;  // per interval: distinct shared states at its barrier
   std::vector<uint8_t> deviated;       // per interval: some read depends on the schedule
   std::vector<uint32_t> n_final;       // distinct final global memories (over all schedules)
@@ -195,9 +200,9 @@ extern "C" {
 // Explore every schedule of a tiny instance.  Returns 0 on success, 1 parse
 // error, 2 bad input.  max_states bounds the total work; on overflow the
 // result has overflow = 1 and must not be used.
-int explore_check(const char *src, uint32_t groups, uint32_t group_size, uint32_t n_global,
-                  const uint64_t *global_len, const int32_t *const *global_init,
-                  uint64_t max_states, void **out, char *err, size_t err_len) {
+static int explore_impl(const char *src, uint32_t groups, uint32_t group_size, uint32_t n_global,
+                        const uint64_t *global_len, const int32_t *const *global_init, uint64_t max_states,
+                        bool pairs, void **out, char *err, size_t err_len) {
   *out = nullptr;
   try {
     Explorer ex;
@@ -238,6 +243,25 @@ int explore_check(const char *src, uint32_t groups, uint32_t group_size, uint32_
     std::set<GState> frontier{init};
     std::set<std::vector<int32_t>> finals;
     while (!frontier.empty() && !ex.overflow) {
+      if (pairs) {  // the interleaving product of every two work-items, from a unique start
+        std::vector<uint32_t> pv;
+        if (frontier.size() == 1) {
+          const GState &s0 = *frontier.begin();
+          for (uint32_t i = 0; i < ex.N; i++)
+            for (uint32_t j = i + 1; j < ex.N; j++) {
+              GState s = s0;
+              for (uint32_t g = 0; g < ex.N; g++)
+                if (g != i && g != j) s.th[g].st = DED;
+              std::set<GState> pe;
+              bool pd = false;
+              ex.explore_interval(s, pe, pd);
+              std::set<std::pair<std::vector<int32_t>, std::vector<int32_t>>> mem;
+              for (const GState &e : pe) mem.insert({e.gmem, e.lmem});
+              pv.push_back((uint32_t)mem.size() | (pd ? 0x80000000u : 0u));
+            }
+        }
+        res->pairs.push_back(pv);
+      }
       std::set<GState> ends;
       bool dev = false;
       for (const GState &s : frontier) ex.explore_interval(s, ends, dev);
@@ -289,6 +313,25 @@ int explore_check(const char *src, uint32_t groups, uint32_t group_size, uint32_
     return 2;
   }
 }
+
+int explore_check(const char *src, uint32_t groups, uint32_t group_size, uint32_t n_global,
+                  const uint64_t *global_len, const int32_t *const *global_init,
+                  uint64_t max_states, void **out, char *err, size_t err_len) {
+  return explore_impl(src, groups, group_size, n_global, global_len, global_init, max_states, false, out, err,
+                      err_len);
+}
+
+// explore_check plus, for every interval that starts from one state, the
+// interleaving product of every pair of work-items (see ExploreResult::pairs)
+int explore_pairs_check(const char *src, uint32_t groups, uint32_t group_size, uint32_t n_global,
+                        const uint64_t *global_len, const int32_t *const *global_init,
+                        uint64_t max_states, void **out, char *err, size_t err_len) {
+  return explore_impl(src, groups, group_size, n_global, global_len, global_init, max_states, true, out, err,
+                      err_len);
+}
+
+uint32_t explore_n_pairs(void *h, uint32_t k) { return (uint32_t)((ExploreResult *)h)->pairs[k].size(); }
+const uint32_t *explore_pairs(void *h, uint32_t k) { return ((ExploreResult *)h)->pairs[k].data(); }
 
 uint32_t explore_n_intervals(void *h) { return (uint32_t)((ExploreResult *)h)->n_end_states.size(); }
 uint32_t explore_end_states(void *h, uint32_t k) { return ((ExploreResult *)h)->n_end_states[k]; }

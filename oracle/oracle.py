@@ -80,6 +80,12 @@ def _load():
                                 ("explore_overflow", ctypes.c_int, [])]:
             getattr(lib, name).restype = rt
             getattr(lib, name).argtypes = [vp] + extra
+        lib.explore_pairs_check.restype = ctypes.c_int
+        lib.explore_pairs_check.argtypes = lib.explore_check.argtypes
+        lib.explore_n_pairs.restype = u32
+        lib.explore_n_pairs.argtypes = [vp, u32]
+        lib.explore_pairs.restype = vp
+        lib.explore_pairs.argtypes = [vp, u32]
         lib.explore_free.argtypes = [vp]
         lib.explore_free.restype = None
         _lib = lib
@@ -156,5 +162,35 @@ def explore(src: str, groups: int, group_size: int, globals_, max_states: int = 
         finals = [fin[i * tot:(i + 1) * tot] for i in range(nf)]
         return dict(end_states=ends, deviated=dev, finals=finals,
                     diverged=bool(lib.explore_diverged(h)), overflow=bool(lib.explore_overflow(h)))
+    finally:
+        lib.explore_free(h)
+
+
+def explore_pairs(src: str, groups: int, group_size: int, globals_, max_states: int = 2_000_000) -> list:
+    """The interleaving product of every two work-items i < j (all others
+    frozen), per interval that starts from a single state: a list per
+    interval, None where the interval starts from several states, else one
+    (end_states, deviated) tuple per pair in (i, j) order."""
+    lib = _load()
+    arrs, n, lens, ptrs = _marshal(globals_)
+    h = ctypes.c_void_p()
+    err = ctypes.create_string_buffer(512)
+    rc = lib.explore_pairs_check(src.encode(), groups, group_size, n, lens, ptrs, max_states,
+                                 ctypes.byref(h), err, 512)
+    if rc != 0:
+        raise OracleError(f"explorer rc={rc}: {err.value.decode()}")
+    try:
+        if lib.explore_overflow(h):
+            raise OracleError("explorer state budget exceeded")
+        out = []
+        for k in range(lib.explore_n_intervals(h)):
+            m = lib.explore_n_pairs(h, k)
+            if m == 0:
+                out.append(None)
+                continue
+            v = np.zeros(m, dtype=np.uint32)
+            ctypes.memmove(v.ctypes.data, lib.explore_pairs(h, k), m * 4)
+            out.append([(int(x & 0x7FFFFFFF), bool(x >> 31)) for x in v])
+        return out
     finally:
         lib.explore_free(h)

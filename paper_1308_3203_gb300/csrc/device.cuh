@@ -1,6 +1,7 @@
 // Device-side data layouts shared by the kernels of the checker.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "bytecode.h"
@@ -242,8 +243,13 @@ struct ExploreResult {
 struct ExploreError {
   const char *msg;
 };
-// Every schedule of the interval from that state (throws ExploreError on a CUDA failure).
-ExploreResult explore_interval(const ExploreInput &in, uint64_t max_states, cudaStream_t s);
+// Every schedule of the interval from that state (throws ExploreError on a
+// CUDA failure).  With pair_out, the search covers every pair of work-items
+// (i < j) alone instead (the others do not run), and pair_out receives per
+// pair, in (i, j) order, its distinct end memories | (schedule-dependent
+// read) << 31; n_end_states then counts distinct (pair, memory) items.
+ExploreResult explore_interval(const ExploreInput &in, uint64_t max_states, cudaStream_t s,
+                               std::vector<uint32_t> *pair_out = nullptr);
 
 // ---- scan / sort (sort.cu)
 // exclusive prefix sum of n uint32 values; tmp must hold scan_tmp_words(n)

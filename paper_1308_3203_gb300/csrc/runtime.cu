@@ -266,7 +266,9 @@ uint32_t bitwidth(uint64_t v) {  // bits needed to represent values < v (v >= 1)
 struct ExploreRun {
   uint64_t max_states;
   uint32_t max_intervals;
+  bool pairs;  // the interleaving product of every two work-items instead of all of them
   std::vector<ExploreResult> results;
+  std::vector<std::vector<uint32_t>> pair_results;
 };
 
 struct Instance {
@@ -642,7 +644,13 @@ rc_report *run_instance(const Instance &I) {
       e.pc = pc;
       e.st = st;
       try {
-        I.explore->results.push_back(explore_interval(e, I.explore->max_states, s));
+        if (I.explore->pairs) {
+          std::vector<uint32_t> pv;
+          I.explore->results.push_back(explore_interval(e, I.explore->max_states, s, &pv));
+          I.explore->pair_results.push_back(std::move(pv));
+        } else {
+          I.explore->results.push_back(explore_interval(e, I.explore->max_states, s));
+        }
       } catch (const ExploreError &x) {
         throw Fail{RC_E_CUDA, x.msg};
       }
@@ -1175,7 +1183,7 @@ int rc_explore(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, cons
     Layout L = make_layout(bc->prog, in, groups);
     if (L.keys > 4096) throw Fail{RC_E_INVALID, "the explorer takes at most 4096 cells"};
     if (bc->prog.n_regs > 64) throw Fail{RC_E_INVALID, "the explorer takes at most 64 registers"};
-    ExploreRun ex{max_states ? max_states : 1000000, max_intervals, {}};
+    ExploreRun ex{max_states ? max_states : 1000000, max_intervals, false, {}, {}};
     Instance I{&bc->prog, groups, group_size, (uint64_t)groups * group_size, in,
                static_cast<cudaStream_t>(in->cuda_stream), &ex};
     rc_report *r = run_instance(I);
@@ -1186,6 +1194,59 @@ int rc_explore(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, cons
       out[k].deviated = ex.results[k].deviated;
       out[k].complete = ex.results[k].complete;
       out[k].n_states = ex.results[k].n_states;
+    }
+    *n_out = (uint32_t)ex.results.size();
+    return RC_OK;
+  } catch (const Fail &f) {
+    return fail_code(f);
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return RC_E_NOMEM;
+  }
+}
+
+int rc_explore_pairs(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in,
+                     uint64_t max_states, rc_pair_interval *out, uint32_t max_intervals, uint32_t *n_out,
+                     uint32_t *pair_detail) {
+  if (!out || !n_out) return RC_E_INVALID;
+  *n_out = 0;
+  std::lock_guard<std::mutex> lk(g_mu);
+  try {
+    check_args(bc, groups, group_size, in);
+    const uint64_t N = (uint64_t)groups * group_size;
+    if (N > 256) throw Fail{RC_E_INVALID, "the pair explorer takes at most 256 work-items"};
+    Layout L = make_layout(bc->prog, in, groups);
+    if (L.keys > 4096) throw Fail{RC_E_INVALID, "the explorer takes at most 4096 cells"};
+    if (bc->prog.n_regs > 64) throw Fail{RC_E_INVALID, "the explorer takes at most 64 registers"};
+    ExploreRun ex{max_states ? max_states : 1000000, max_intervals, true, {}, {}};
+    Instance I{&bc->prog, groups, group_size, N, in, static_cast<cudaStream_t>(in->cuda_stream), &ex};
+    rc_report *r = run_instance(I);
+    rc_report_free(r);
+    const uint32_t P = (uint32_t)(N * (N - 1) / 2);
+    for (size_t k = 0; k < ex.results.size(); k++) {
+      const std::vector<uint32_t> &pv = ex.pair_results[k];
+      rc_pair_interval &o = out[k];
+      o.interval = (uint32_t)k;
+      o.n_pairs = P;
+      o.n_racy = o.n_deviated = 0;
+      o.first_i = o.first_j = 0xFFFFFFFFu;
+      o.complete = ex.results[k].complete;
+      o.reserved = 0;
+      o.n_states = ex.results[k].n_states;
+      uint32_t p = 0;
+      for (uint32_t i = 0; i < N; i++)
+        for (uint32_t j = i + 1; j < N; j++, p++) {
+          const uint32_t v = p < pv.size() ? pv[p] : 0;
+          if ((v & 0x7FFFFFFFu) >= 2) {
+            if (!o.n_racy) {
+              o.first_i = i;
+              o.first_j = j;
+            }
+            o.n_racy++;
+          }
+          if (v >> 31) o.n_deviated++;
+          if (pair_detail) pair_detail[k * P + p] = v;
+        }
     }
     *n_out = (uint32_t)ex.results.size();
     return RC_OK;

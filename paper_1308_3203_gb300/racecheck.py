@@ -60,6 +60,11 @@ class _ExploreInterval(ctypes.Structure):
                 ("complete", ctypes.c_uint32), ("n_states", ctypes.c_uint64)]
 
 
+class _PairInterval(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("interval", "n_pairs", "n_racy", "n_deviated", "first_i",
+                                               "first_j", "complete", "reserved")] + [("n_states", ctypes.c_uint64)]
+
+
 class _SearchResult(ctypes.Structure):
     _fields_ = [("first", ctypes.c_int64), ("checks", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("seconds", ctypes.c_double)]
@@ -134,7 +139,10 @@ def load() -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.POINTER(_Report))]
         lib.rc_explore.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input), ctypes.c_uint64,
                                    ctypes.POINTER(_ExploreInterval), ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
-        for f in ("rc_explore", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
+        lib.rc_explore_pairs.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input),
+                                         ctypes.c_uint64, ctypes.POINTER(_PairInterval), ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]
+        for f in ("rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
                   "rc_mlp_forward", "rc_mlp_grad", "rc_mlp_train", "rc_search"):
             getattr(lib, f).restype = c_int
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
@@ -363,6 +371,35 @@ def explore(bc: Bytecode, groups: int, group_size: int, globals_, max_states: in
         _raise(rc)
     return [dict(interval=o.interval, n_end_states=o.n_end_states, deviated=bool(o.deviated),
                  complete=bool(o.complete), n_states=int(o.n_states)) for o in out[:n.value]]
+
+
+def explore_pairs(bc: Bytecode, groups: int, group_size: int, globals_, max_states: int = 0,
+                  max_intervals: int = 64, detail: bool = False) -> list:
+    """The interleaving product of every pair of work-items i < j (the others
+    do not run), per interval from the checker's state at its start: n_pairs,
+    n_racy (pairs reaching >= 2 shared memories), n_deviated, first racy pair,
+    complete, n_states; with detail, per pair (end memories, deviated)."""
+    inp, keep = _marshal(globals_, None, False)
+    out = (_PairInterval * max(max_intervals, 1))()
+    n = ctypes.c_uint32()
+    N = groups * group_size
+    P = N * (N - 1) // 2
+    det = np.zeros(max(max_intervals * P, 1), dtype=np.uint32) if detail else None
+    rc = load().rc_explore_pairs(bc.handle, groups, group_size, ctypes.byref(inp), max_states, out, max_intervals,
+                                 ctypes.byref(n),
+                                 det.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)) if detail else None)
+    del keep
+    if rc:
+        _raise(rc)
+    res = []
+    for k, o in enumerate(out[:n.value]):
+        d = dict(interval=o.interval, n_pairs=o.n_pairs, n_racy=o.n_racy, n_deviated=o.n_deviated,
+                 first=(o.first_i, o.first_j) if o.n_racy else None, complete=bool(o.complete),
+                 n_states=int(o.n_states))
+        if detail:
+            d["pairs"] = [(int(x & 0x7FFFFFFF), bool(x >> 31)) for x in det[k * P:(k + 1) * P]]
+        res.append(d)
+    return res
 
 
 # ---------------------------------------------------------------- learned proposal
