@@ -219,10 +219,15 @@ int rc_autotune_reset(void);
  * returns 1 (sort), 2 (shadow) or 0 if undecided. */
 int rc_autotune_lookup(int kind, uint64_t a, uint64_t b);
 
-/* Kernel timing: when enabled, the library brackets its kernels with CUDA
- * events on the caller's stream and accumulates, per kernel kind, launches,
- * device milliseconds and algorithmic bytes.  kind: 0 interpreter, 1 log
- * classification (sort or shadow path), 2 commit.  Reset clears the sums. */
+/* Kernel timing: when enabled, the library brackets its work with CUDA
+ * events on the caller's stream and accumulates, per kind, the number of
+ * intervals (or batch rounds), device milliseconds and algorithmic bytes
+ * (12 per logged global access).  kind 0: the interpreter launch; kind 1:
+ * everything after it until the interval's classification is done (owner-
+ * table commit, compaction, sort and classification, and any wait for the
+ * host in between); kind 2: reserved (zero).  Timing an interval
+ * synchronises it, so the speculative launch of the next interval is off
+ * while enabled.  Reset clears the sums. */
 int rc_profile_enable(int on);
 int rc_profile_reset(void);
 int rc_profile_get(int kind, uint64_t *launches, double *ms, double *bytes);
@@ -322,6 +327,12 @@ typedef struct rc_mlp rc_mlp;
 int rc_mlp_create(uint64_t seed, uint32_t capacity, rc_mlp **out);
 void rc_mlp_free(rc_mlp *m);
 int rc_mlp_get_params(const rc_mlp *m, float *host_out);
+/* Forward products on the mma.sync tensor-core kernels (backend 0) or on the
+ * tcgen05 kernels with TMEM accumulators (backend 1); backward products use
+ * mma.sync either way.  rc_mlp_backend_error sets *flag nonzero if a tcgen05
+ * launch gave up waiting for its MMAs (its outputs are then not valid). */
+int rc_mlp_set_backend(rc_mlp *m, int backend);
+int rc_mlp_backend_error(rc_mlp *m, uint32_t *flag);
 int rc_mlp_set_params(rc_mlp *m, const float *host_in);
 /* prob[i] = score of row i of x, for n rows. */
 int rc_mlp_forward(rc_mlp *m, const float *x, uint64_t n, float *prob, void *cuda_stream);

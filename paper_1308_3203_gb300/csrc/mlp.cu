@@ -2,8 +2,9 @@
 // score) over candidate features, trained on the exact checker's race / no
 // race labels with binary cross-entropy and Adam.
 //
-// Numerics: FP32 master weights; the forward and backward products run on
-// BF16 tensor cores (mma.sync m16n8k16, FP32 accumulation) with BF16
+// Numerics: FP32 master weights; the forward products run on the tcgen05
+// tensor cores (FP32 accumulators in TMEM; mma.sync selectable) and the
+// backward products on mma.sync m16n8k16 (FP32 accumulation), with BF16
 // operands: the input features, the weight copies, the hidden activations
 // h = relu(z) and the pre-activation gradients dz are rounded to BF16 where
 // they are stored; biases, the output layer's dot product, the loss and all
@@ -172,6 +173,131 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(GemmArgs g) {
       }
 }
 
+// ---------------------------------------------------------------- tcgen05 forward layer
+// out[M][256] = relu(act[M][K] * W[256][K]^T + bias) on the 5th-generation
+// tensor cores: one CTA (4 warps) per 128 rows.  Both operands are staged in
+// shared memory in the canonical K-major layout without swizzle: 8-row x
+// 16-byte core matrices, 128 bytes each, core matrices along K adjacent
+// (leading byte offset 128) and 8-row groups K/8 core matrices apart (stride
+// byte offset K*16).  One thread issues K/16 MMAs of 128 x 256 x 16
+// (kind::f16, BF16 operands, FP32 accumulator in 256 TMEM columns) and
+// commits them to an mbarrier; after it fires, each warp reads its 32 rows
+// of the accumulator (lanes 32w..32w+31), adds the bias, applies the ReLU
+// and stores BF16.
+constexpr int kTcRows = 128, kTcThreads = 128;
+constexpr uint32_t kTcWaitLimit = 1u << 26;  // mbarrier polls before the CTA gives up
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start, leading and stride byte offsets
+// (all >> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = 256, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+template <int K>
+__global__ void __launch_bounds__(kTcThreads) tc_fwd_kernel(const bf16 *__restrict__ act, const bf16 *__restrict__ W,
+                                                            const float *__restrict__ bias, bf16 *__restrict__ out,
+                                                            int M, uint32_t *err) {
+  constexpr int KC = K / 8;                       // core matrices along K
+  constexpr uint32_t A_BYTES = kTcRows * K * 2, B_BYTES = kHid * K * 2;
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char *As = tsm, *Bs = tsm + A_BYTES;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(tsm + A_BYTES + B_BYTES);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int m0 = blockIdx.x * kTcRows;
+  // stage both operands, 16 bytes (8 elements along K) per copy
+  for (int i = t; i < kTcRows * KC; i += kTcThreads) {
+    const int r = i / KC, c = i % KC;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (m0 + r < M) v = *reinterpret_cast<const uint4 *>(act + (size_t)(m0 + r) * K + c * 8);
+    *reinterpret_cast<uint4 *>(As + ((r >> 3) * KC + c) * 128 + (r & 7) * 16) = v;
+  }
+  for (int i = t; i < kHid * KC; i += kTcThreads) {
+    const int n = i / KC, c = i % KC;
+    *reinterpret_cast<uint4 *>(Bs + ((n >> 3) * KC + c) * 128 + (n & 7) * 16) =
+        *reinterpret_cast<const uint4 *>(W + (size_t)n * K + c * 8);
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor cores
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  if (t == 0) {
+    const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+#pragma unroll 1
+    for (int k = 0; k < K / 16; k++) {  // two core matrices along K per MMA
+      const uint64_t ad = tc_desc(a0 + k * 256, 128, KC * 128), bd = tc_desc(b0 + k * 256, 128, KC * 128);
+      const uint32_t acc = k > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_addr(mbar)));
+  }
+  // wait (bounded) for the MMAs to complete
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kTcWaitLimit && !done; it++)
+    asm volatile(
+        "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], 0;\n selp.b32 %0, 1, 0, P1;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(mbar)));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!done) {
+    if (t == 0) atomicOr(err, 1u);
+  } else {
+    const int r = warp * 32 + lane;  // accumulator row = TMEM lane
+#pragma unroll 1
+    for (int j = 0; j < kHid / 32; j++) {
+      uint32_t v[32];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+            "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+            "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+            "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m0 + r < M) {
+        __align__(16) bf16 o[32];
+#pragma unroll
+        for (int q = 0; q < 32; q++) o[q] = __float2bfloat16_rn(fmaxf(__uint_as_float(v[q]) + bias[j * 32 + q], 0.0f));
+        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)(m0 + r) * kHid + j * 32);
+#pragma unroll
+        for (int q = 0; q < 4; q++) dst[q] = reinterpret_cast<const uint4 *>(o)[q];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+}
+
+template <int K>
+constexpr size_t tc_smem() {
+  return (size_t)kTcRows * K * 2 + (size_t)kHid * K * 2 + 16;
+}
+
 // ---------------------------------------------------------------- small kernels
 // rows of the (shuffled) batch: features to BF16, labels to FP32
 __global__ void gather_kernel(const float *X, const float *Y, const uint32_t *idx, int n, bf16 *Xb, float *Yb) {
@@ -291,6 +417,8 @@ unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // ---------------------------------------------------------------- the network object
 struct rc_mlp {
   uint32_t cap = 0;  // rows per pass
+  int backend = 1;   // forward products: 0 mma.sync, 1 tcgen05
+  uint32_t *tc_err = nullptr;  // device flag: a tcgen05 CTA gave up waiting for its MMAs
   float *P = nullptr, *G = nullptr, *Mm = nullptr, *Vv = nullptr;
   rc::bf16 *Pb = nullptr;
   rc::bf16 *Xb = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *D1 = nullptr, *D2 = nullptr;
@@ -318,6 +446,16 @@ int wgrad_splits(int rows) { return std::max(1, std::min(64, (rows + 511) / 512)
 // forward pass of rows [0, n) of the staged batch m->Xb (n <= cap)
 void forward(rc_mlp *m, int n, cudaStream_t s) {
   const bf16 *Wb = m->Pb;
+  if (m->backend == 1) {
+    const unsigned grid = (unsigned)((n + kTcRows - 1) / kTcRows);
+    count_launch();
+    tc_fwd_kernel<kIn><<<grid, kTcThreads, tc_smem<kIn>(), s>>>(m->Xb, Wb + oW1, m->P + ob1, m->H1, n, m->tc_err);
+    count_launch();
+    tc_fwd_kernel<kHid><<<grid, kTcThreads, tc_smem<kHid>(), s>>>(m->H1, Wb + oW2, m->P + ob2, m->H2, n, m->tc_err);
+    count_launch();
+    tc_fwd_kernel<kHid><<<grid, kTcThreads, tc_smem<kHid>(), s>>>(m->H2, Wb + oW3, m->P + ob3, m->H3, n, m->tc_err);
+    return;
+  }
   GemmArgs g{};
   g.M = n;
   g.N = kHid;
@@ -467,6 +605,10 @@ int rc_mlp_create(uint64_t seed, uint32_t capacity, rc_mlp **out) {
     MK(cudaMalloc(&m->idx, cap * 4));
     MK(cudaMalloc(&m->part, m->part_floats * 4));
     MK(cudaMalloc(&m->scal, 4096 * 4));
+    MK(cudaMalloc(&m->tc_err, 4));
+    MK(cudaMemset(m->tc_err, 0, 4));
+    MK(cudaFuncSetAttribute(tc_fwd_kernel<kIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<kIn>()));
+    MK(cudaFuncSetAttribute(tc_fwd_kernel<kHid>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<kHid>()));
     // He-uniform weights for the ReLU layers, zero biases
     std::vector<float> p(kParams, 0.0f);
     uint64_t st = seed;
@@ -497,9 +639,21 @@ void rc_mlp_free(rc_mlp *m) {
   if (!m) return;
   for (void *p : {(void *)m->P, (void *)m->G, (void *)m->Mm, (void *)m->Vv, (void *)m->Pb, (void *)m->Xb,
                   (void *)m->H1, (void *)m->H2, (void *)m->H3, (void *)m->D1, (void *)m->D2, (void *)m->Yb,
-                  (void *)m->dl, (void *)m->loss, (void *)m->idx, (void *)m->part, (void *)m->scal})
+                  (void *)m->dl, (void *)m->loss, (void *)m->idx, (void *)m->part, (void *)m->scal,
+                  (void *)m->tc_err})
     if (p) cudaFree(p);
   delete m;
+}
+
+int rc_mlp_set_backend(rc_mlp *m, int backend) {
+  if (!m || backend < 0 || backend > 1) return RC_E_INVALID;
+  m->backend = backend;
+  return RC_OK;
+}
+
+int rc_mlp_backend_error(rc_mlp *m, uint32_t *flag) {
+  if (!m || !flag) return RC_E_INVALID;
+  return guarded([&] { MK(cudaMemcpy(flag, m->tc_err, 4, cudaMemcpyDeviceToHost)); });
 }
 
 int rc_mlp_get_params(const rc_mlp *m, float *out) {

@@ -142,7 +142,9 @@ def load() -> ctypes.CDLL:
         lib.rc_explore_pairs.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input),
                                          ctypes.c_uint64, ctypes.POINTER(_PairInterval), ctypes.c_uint32,
                                          ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]
-        for f in ("rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
+        lib.rc_mlp_set_backend.argtypes = [vp, c_int]
+        lib.rc_mlp_backend_error.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+        for f in ("rc_mlp_set_backend", "rc_mlp_backend_error", "rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
                   "rc_mlp_forward", "rc_mlp_grad", "rc_mlp_train", "rc_search"):
             getattr(lib, f).restype = c_int
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
@@ -484,6 +486,20 @@ class MLP:
     def _stream():
         import torch
         return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def set_backend(self, backend: int) -> None:
+        """Forward products on mma.sync (0) or tcgen05 with TMEM accumulators (1, the default)."""
+        rc = load().rc_mlp_set_backend(self._h, backend)
+        if rc:
+            _raise(rc)
+
+    def backend_error(self) -> int:
+        """Nonzero if a tcgen05 launch gave up waiting for its MMAs."""
+        v = ctypes.c_uint32()
+        rc = load().rc_mlp_backend_error(self._h, ctypes.byref(v))
+        if rc:
+            _raise(rc)
+        return int(v.value)
 
     def params(self) -> np.ndarray:
         p = np.zeros(MLP_PARAMS, dtype=np.float32)

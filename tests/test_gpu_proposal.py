@@ -65,6 +65,25 @@ def test_forward_matches_reference(rc, n):
     np.testing.assert_allclose(got, exact, atol=3e-2, rtol=0)
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 1000, 4097])
+def test_tcgen05_forward_matches(rc, n):
+    """The tcgen05 forward (TMEM accumulators) against the mma.sync forward
+    and the CPU reference on the same parameters and rows (ragged 128-row
+    tiles, several passes over the capacity)."""
+    m = rc.MLP(seed=1, capacity=2048)
+    p = M.init_params(5).astype(np.float32)
+    m.set_params(p)
+    X = feature_rows(rc, n, 50 + n)
+    m.set_backend(0)
+    a = m.forward(cuda(X)).cpu().numpy()
+    m.set_backend(1)
+    b = m.forward(cuda(X)).cpu().numpy()
+    assert m.backend_error() == 0
+    want, _ = M.forward(p, X, bf16_points=True)
+    np.testing.assert_allclose(b, a, atol=4e-3, rtol=0)
+    np.testing.assert_allclose(b, want, atol=4e-3, rtol=0)
+
+
 @pytest.mark.parametrize("n", [7, 777, 2500])
 def test_gradient_matches_reference(rc, n):
     m = rc.MLP(seed=2, capacity=4096)
