@@ -327,10 +327,11 @@ typedef struct rc_mlp rc_mlp;
 int rc_mlp_create(uint64_t seed, uint32_t capacity, rc_mlp **out);
 void rc_mlp_free(rc_mlp *m);
 int rc_mlp_get_params(const rc_mlp *m, float *host_out);
-/* Forward products on the mma.sync tensor-core kernels (backend 0) or on the
- * tcgen05 kernels with TMEM accumulators (backend 1); backward products use
- * mma.sync either way.  rc_mlp_backend_error sets *flag nonzero if a tcgen05
- * launch gave up waiting for its MMAs (its outputs are then not valid). */
+/* Every product (forward, data and weight gradients) on the tcgen05 kernels
+ * with TMEM accumulators (backend 1, the default) or on the mma.sync
+ * m16n8k16 kernels (backend 0).  rc_mlp_backend_error sets *flag nonzero if
+ * a tcgen05 launch gave up waiting for its MMAs (its outputs are then not
+ * valid). */
 int rc_mlp_set_backend(rc_mlp *m, int backend);
 int rc_mlp_backend_error(rc_mlp *m, uint32_t *flag);
 int rc_mlp_set_params(rc_mlp *m, const float *host_in);

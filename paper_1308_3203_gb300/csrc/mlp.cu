@@ -2,10 +2,9 @@
 // score) over candidate features, trained on the exact checker's race / no
 // race labels with binary cross-entropy and Adam.
 //
-// Numerics: FP32 master weights; the forward products run on the tcgen05
-// tensor cores (FP32 accumulators in TMEM; mma.sync selectable) and the
-// backward products on mma.sync m16n8k16 (FP32 accumulation), with BF16
-// operands: the input features, the weight copies, the hidden activations
+// Numerics: FP32 master weights; the forward and backward products run on
+// the tcgen05 tensor cores with FP32 accumulators in TMEM (mma.sync m16n8k16
+// kernels selectable), with BF16 operands: the input features, the weight copies, the hidden activations
 // h = relu(z) and the pre-activation gradients dz are rounded to BF16 where
 // they are stored; biases, the output layer's dot product, the loss and all
 // gradient sums stay in FP32.  Weight gradients reduce over the batch in a
@@ -298,6 +297,179 @@ constexpr size_t tc_smem() {
   return (size_t)kTcRows * K * 2 + (size_t)kHid * K * 2 + 16;
 }
 
+// ---- tcgen05 backward products.  The same tile layout and MMA sequence;
+// operands whose source runs along M (or N) instead of K are transposed
+// while staging, one 16-byte source row (8 M/N values at one K) at a time.
+constexpr int kTcK = 256;  // K per staged sub-tile
+
+// tile[mn][k] (K-major core matrices, KC = kTcK / 8) = src[(k0 + k) * ld + mn0 + mn]
+// for k < kn (else 0), mn < rows
+__device__ __forceinline__ void tc_stage_mn(unsigned char *tile, const bf16 *src, int ld, int mn0, int rows, int k0,
+                                            int kn) {
+  constexpr int KC = kTcK / 8;
+  for (int i = threadIdx.x; i < kTcK * (rows / 8); i += kTcThreads) {
+    const int k = i / (rows / 8), g = i % (rows / 8);  // one source row of 8 M/N values
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (k < kn) v = *reinterpret_cast<const uint4 *>(src + (size_t)(k0 + k) * ld + mn0 + g * 8);
+    const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+      *reinterpret_cast<bf16 *>(tile + (g * KC + (k >> 3)) * 128 + q * 16 + (k & 7) * 2) = e[q];
+  }
+}
+
+// the MMAs of one staged sub-tile (K = kTcK) into TMEM, committed to mbar;
+// returns false if the bounded wait ran out
+__device__ __forceinline__ bool tc_mma_tile(const unsigned char *As, const unsigned char *Bs, uint32_t tmem,
+                                            uint32_t idesc, bool accumulate, uint64_t *mbar, uint32_t phase) {
+  constexpr int KC = kTcK / 8;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (threadIdx.x == 0) {
+    const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+#pragma unroll 1
+    for (int k = 0; k < kTcK / 16; k++) {
+      const uint64_t ad = tc_desc(a0 + k * 256, 128, KC * 128), bd = tc_desc(b0 + k * 256, 128, KC * 128);
+      const uint32_t acc = (accumulate || k > 0) ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_addr(mbar)));
+  }
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kTcWaitLimit && !done; it++)
+    asm volatile(
+        "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(mbar)), "r"(phase));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return __syncthreads_and(done) != 0;
+}
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t v[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+        "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+        "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t tc_begin(uint64_t *mbar, uint32_t *tslot) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return *tslot;
+}
+
+__device__ __forceinline__ void tc_end(uint32_t tmem) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+}
+
+__host__ __device__ constexpr uint32_t tc_idesc(uint32_t n) { return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24); }
+constexpr size_t kTcBwdSmem = (size_t)kTcRows * kTcK * 2 + (size_t)kHid * kTcK * 2 + 16;
+
+// dz_prev[M][256] = (dz[M][256] * W[256][256]) where h[M][256] > 0, as BF16
+__global__ void __launch_bounds__(kTcThreads) tc_dgrad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ W,
+                                                              const bf16 *__restrict__ h, bf16 *__restrict__ out,
+                                                              int M, uint32_t *err) {
+  constexpr int KC = kTcK / 8;
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char *As = tsm, *Bs = tsm + kTcRows * kTcK * 2;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(tsm + kTcBwdSmem - 16);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, m0 = blockIdx.x * kTcRows;
+  for (int i = t; i < kTcRows * KC; i += kTcThreads) {  // A = dz rows, K contiguous
+    const int r = i / KC, c = i % KC;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (m0 + r < M) v = *reinterpret_cast<const uint4 *>(dz + (size_t)(m0 + r) * kHid + c * 8);
+    *reinterpret_cast<uint4 *>(As + ((r >> 3) * KC + c) * 128 + (r & 7) * 16) = v;
+  }
+  tc_stage_mn(Bs, W, kHid, 0, kHid, 0, kTcK);  // B[n][k] = W[k][n]
+  const uint32_t tmem = tc_begin(mbar, tslot);
+  if (!tc_mma_tile(As, Bs, tmem, tc_idesc(256), false, mbar, 0)) {
+    if (t == 0) atomicOr(err, 1u);
+  } else {
+    const int r = warp * 32 + lane;
+#pragma unroll 1
+    for (int j = 0; j < kHid / 32; j++) {
+      uint32_t v[32];
+      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32), v);
+      if (m0 + r < M) {
+        const bf16 *hm = h + (size_t)(m0 + r) * kHid + j * 32;
+        __align__(16) bf16 o[32];
+#pragma unroll
+        for (int q = 0; q < 32; q++)
+          o[q] = __float2bfloat16_rn(__bfloat162float(hm[q]) > 0.0f ? __uint_as_float(v[q]) : 0.0f);
+        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)(m0 + r) * kHid + j * 32);
+#pragma unroll
+        for (int q = 0; q < 4; q++) dst[q] = reinterpret_cast<const uint4 *>(o)[q];
+      }
+    }
+  }
+  tc_end(tmem);
+}
+
+// partial z of dW[256][N] = dz^T h over rows [z*kchunk, ...): the CTA at
+// blockIdx.x = half takes output rows j = 128*half .. +127, K = batch rows
+// in sub-tiles of kTcK accumulated in TMEM
+__global__ void __launch_bounds__(kTcThreads) tc_wgrad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ h,
+                                                              int N, int rows, int kchunk, float *__restrict__ part,
+                                                              uint32_t *err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char *As = tsm, *Bs = tsm + kTcRows * kTcK * 2;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(tsm + kTcBwdSmem - 16);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int j0 = blockIdx.x * kTcRows, z = blockIdx.y;
+  const int kbeg = z * kchunk, kend = min(rows, kbeg + kchunk);
+  const uint32_t tmem = tc_begin(mbar, tslot);
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int k0 = kbeg; k0 < kend && ok; k0 += kTcK, phase ^= 1u) {
+    const int kn = min(kTcK, kend - k0);
+    tc_stage_mn(As, dz, kHid, j0, kTcRows, k0, kn);  // A[j][r] = dz[r][j0 + j]
+    tc_stage_mn(Bs, h, N, 0, N, k0, kn);             // B[i][r] = h[r][i]
+    ok = tc_mma_tile(As, Bs, tmem, tc_idesc((uint32_t)N), k0 > kbeg, mbar, phase);
+  }
+  if (!ok) {
+    if (t == 0) atomicOr(err, 1u);
+  } else {
+    const int r = warp * 32 + lane;  // output row j0 + r
+    float *dst = part + ((size_t)z * kHid + j0 + r) * N;
+#pragma unroll 1
+    for (int j = 0; j < N / 32; j++) {
+      uint32_t v[32];
+      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32), v);
+#pragma unroll
+      for (int q = 0; q < 32; q += 4)
+        *reinterpret_cast<float4 *>(dst + j * 32 + q) =
+            make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]), __uint_as_float(v[q + 2]),
+                        __uint_as_float(v[q + 3]));
+    }
+  }
+  tc_end(tmem);
+}
+
 // ---------------------------------------------------------------- small kernels
 // rows of the (shuffled) batch: features to BF16, labels to FP32
 __global__ void gather_kernel(const float *X, const float *Y, const uint32_t *idx, int n, bf16 *Xb, float *Yb) {
@@ -474,6 +646,21 @@ void forward(rc_mlp *m, int n, cudaStream_t s) {
 // dW = dz^T h (+ split-K partials), db = column sums of dz
 void weight_grads(rc_mlp *m, const bf16 *dz, const bf16 *h, int kin, int n, size_t oW, size_t ob, cudaStream_t s) {
   const int splits = wgrad_splits(n);
+  if (m->backend == 1) {
+    const int kchunk = (((n + splits - 1) / splits) + 15) / 16 * 16;
+    const int zs = (n + kchunk - 1) / kchunk;
+    count_launch();
+    tc_wgrad_kernel<<<dim3(kHid / kTcRows, zs), kTcThreads, kTcBwdSmem, s>>>(dz, h, kin, n, kchunk, m->part,
+                                                                           m->tc_err);
+    count_launch();
+    reduce_parts_kernel<<<nblk((size_t)kHid * kin, 256), 256, 0, s>>>(m->part, zs, kHid * kin, m->G + oW);
+    const int chunks = (n + kColRows - 1) / kColRows;
+    count_launch();
+    colsum_kernel<<<chunks, kHid, 0, s>>>(dz, nullptr, n, m->part);
+    count_launch();
+    reduce_parts_kernel<<<1, kHid, 0, s>>>(m->part, chunks, kHid, m->G + ob);
+    return;
+  }
   GemmArgs g{};
   g.A = dz;
   g.B = h;
@@ -517,12 +704,19 @@ void backward(rc_mlp *m, int n, cudaStream_t s) {
   g.N = kHid;
   g.K = kHid;
   g.A = m->D2, g.B = m->Pb + oW3, g.mask = m->H2, g.out = m->D1;
+  const unsigned tgrid = (unsigned)((n + kTcRows - 1) / kTcRows);
   count_launch();
-  gemm_kernel<DGRAD><<<dim3(nblk(n, BM), kHid / BN), kGemmThreads, 0, s>>>(g);
+  if (m->backend == 1)
+    tc_dgrad_kernel<<<tgrid, kTcThreads, kTcBwdSmem, s>>>(m->D2, m->Pb + oW3, m->H2, m->D1, n, m->tc_err);
+  else
+    gemm_kernel<DGRAD><<<dim3(nblk(n, BM), kHid / BN), kGemmThreads, 0, s>>>(g);
   weight_grads(m, m->D1, m->H1, kHid, n, oW2, ob2, s);
   g.A = m->D1, g.B = m->Pb + oW2, g.mask = m->H1, g.out = m->D2;  // dz1 into D2
   count_launch();
-  gemm_kernel<DGRAD><<<dim3(nblk(n, BM), kHid / BN), kGemmThreads, 0, s>>>(g);
+  if (m->backend == 1)
+    tc_dgrad_kernel<<<tgrid, kTcThreads, kTcBwdSmem, s>>>(m->D1, m->Pb + oW2, m->H1, m->D2, n, m->tc_err);
+  else
+    gemm_kernel<DGRAD><<<dim3(nblk(n, BM), kHid / BN), kGemmThreads, 0, s>>>(g);
   weight_grads(m, m->D2, m->Xb, kIn, n, oW1, ob1, s);
 }
 
@@ -609,6 +803,8 @@ int rc_mlp_create(uint64_t seed, uint32_t capacity, rc_mlp **out) {
     MK(cudaMemset(m->tc_err, 0, 4));
     MK(cudaFuncSetAttribute(tc_fwd_kernel<kIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<kIn>()));
     MK(cudaFuncSetAttribute(tc_fwd_kernel<kHid>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<kHid>()));
+    MK(cudaFuncSetAttribute(tc_dgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcBwdSmem));
+    MK(cudaFuncSetAttribute(tc_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcBwdSmem));
     // He-uniform weights for the ReLU layers, zero biases
     std::vector<float> p(kParams, 0.0f);
     uint64_t st = seed;

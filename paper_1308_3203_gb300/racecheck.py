@@ -488,7 +488,7 @@ class MLP:
         return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
     def set_backend(self, backend: int) -> None:
-        """Forward products on mma.sync (0) or tcgen05 with TMEM accumulators (1, the default)."""
+        """Every product on tcgen05 with TMEM accumulators (1, the default) or on mma.sync (0)."""
         rc = load().rc_mlp_set_backend(self._h, backend)
         if rc:
             _raise(rc)

@@ -84,9 +84,12 @@ def test_tcgen05_forward_matches(rc, n):
     np.testing.assert_allclose(b, want, atol=4e-3, rtol=0)
 
 
+@pytest.mark.parametrize("backend", [0, 1])
 @pytest.mark.parametrize("n", [7, 777, 2500])
-def test_gradient_matches_reference(rc, n):
+def test_gradient_matches_reference(rc, n, backend):
+    """Both backends: mma.sync (0) and tcgen05 (1) for every product."""
     m = rc.MLP(seed=2, capacity=4096)
+    m.set_backend(backend)
     p = M.init_params(11).astype(np.float32)
     m.set_params(p)
     X = feature_rows(rc, n, 7 + n)
@@ -100,6 +103,7 @@ def test_gradient_matches_reference(rc, n):
         assert d < 2e-2 and cos > 0.9995, (name, d, cos)
     # the parameters did not move
     np.testing.assert_array_equal(m.params(), p)
+    assert m.backend_error() == 0
 
 
 def test_training_ranks_racy_candidates_first(rc):
