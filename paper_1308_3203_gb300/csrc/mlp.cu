@@ -174,16 +174,17 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(GemmArgs g) {
 
 // ---------------------------------------------------------------- tcgen05 forward layer
 // out[M][256] = relu(act[M][K] * W[256][K]^T + bias) on the 5th-generation
-// tensor cores: one CTA (4 warps) per 128 rows.  Both operands are staged in
+// tensor cores: one CTA (4 warps) per 128 rows x 64 output columns.  Both operands are staged in
 // shared memory in the canonical K-major layout without swizzle: 8-row x
 // 16-byte core matrices, 128 bytes each, core matrices along K adjacent
 // (leading byte offset 128) and 8-row groups K/8 core matrices apart (stride
-// byte offset K*16).  One thread issues K/16 MMAs of 128 x 256 x 16
-// (kind::f16, BF16 operands, FP32 accumulator in 256 TMEM columns) and
+// byte offset K*16).  One thread issues K/16 MMAs of 128 x 64 x 16
+// (kind::f16, BF16 operands, FP32 accumulator in 64 TMEM columns) and
 // commits them to an mbarrier; after it fires, each warp reads its 32 rows
 // of the accumulator (lanes 32w..32w+31), adds the bias, applies the ReLU
 // and stores BF16.
 constexpr int kTcRows = 128, kTcThreads = 128;
+constexpr int kTcN = 64;  // output columns per CTA: the grid's second dimension covers the rest
 constexpr uint32_t kTcWaitLimit = 1u << 26;  // mbarrier polls before the CTA gives up
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -198,21 +199,23 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 }
 
 // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = 256, M = 128
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+// K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t tc_idesc(uint32_t n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
 
 template <int K>
 __global__ void __launch_bounds__(kTcThreads) tc_fwd_kernel(const bf16 *__restrict__ act, const bf16 *__restrict__ W,
                                                             const float *__restrict__ bias, bf16 *__restrict__ out,
                                                             int M, uint32_t *err) {
   constexpr int KC = K / 8;                       // core matrices along K
-  constexpr uint32_t A_BYTES = kTcRows * K * 2, B_BYTES = kHid * K * 2;
+  constexpr uint32_t A_BYTES = kTcRows * K * 2, B_BYTES = kTcN * K * 2;
   extern __shared__ __align__(1024) unsigned char tsm[];
   unsigned char *As = tsm, *Bs = tsm + A_BYTES;
   uint64_t *mbar = reinterpret_cast<uint64_t *>(tsm + A_BYTES + B_BYTES);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int m0 = blockIdx.x * kTcRows;
+  const int m0 = blockIdx.x * kTcRows, n0 = blockIdx.y * kTcN;
   // stage both operands, 16 bytes (8 elements along K) per copy
   for (int i = t; i < kTcRows * KC; i += kTcThreads) {
     const int r = i / KC, c = i % KC;
@@ -220,10 +223,10 @@ __global__ void __launch_bounds__(kTcThreads) tc_fwd_kernel(const bf16 *__restri
     if (m0 + r < M) v = *reinterpret_cast<const uint4 *>(act + (size_t)(m0 + r) * K + c * 8);
     *reinterpret_cast<uint4 *>(As + ((r >> 3) * KC + c) * 128 + (r & 7) * 16) = v;
   }
-  for (int i = t; i < kHid * KC; i += kTcThreads) {
+  for (int i = t; i < kTcN * KC; i += kTcThreads) {
     const int n = i / KC, c = i % KC;
     *reinterpret_cast<uint4 *>(Bs + ((n >> 3) * KC + c) * 128 + (n & 7) * 16) =
-        *reinterpret_cast<const uint4 *>(W + (size_t)n * K + c * 8);
+        *reinterpret_cast<const uint4 *>(W + (size_t)(n0 + n) * K + c * 8);
   }
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
@@ -231,7 +234,8 @@ __global__ void __launch_bounds__(kTcThreads) tc_fwd_kernel(const bf16 *__restri
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor cores
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "n"(kTcN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -247,7 +251,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_fwd_kernel(const bf16 *__restri
       asm volatile(
           "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
           " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-          "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
+          "l"(ad), "l"(bd), "r"(tc_idesc(kTcN)), "r"(acc));
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
         smem_addr(mbar)));
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_fwd_kernel(const bf16 *__restri
   } else {
     const int r = warp * 32 + lane;  // accumulator row = TMEM lane
 #pragma unroll 1
-    for (int j = 0; j < kHid / 32; j++) {
+    for (int j = 0; j < kTcN / 32; j++) {
       uint32_t v[32];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -280,8 +284,9 @@ __global__ void __launch_bounds__(kTcThreads) tc_fwd_kernel(const bf16 *__restri
       if (m0 + r < M) {
         __align__(16) bf16 o[32];
 #pragma unroll
-        for (int q = 0; q < 32; q++) o[q] = __float2bfloat16_rn(fmaxf(__uint_as_float(v[q]) + bias[j * 32 + q], 0.0f));
-        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)(m0 + r) * kHid + j * 32);
+        for (int q = 0; q < 32; q++)
+          o[q] = __float2bfloat16_rn(fmaxf(__uint_as_float(v[q]) + bias[n0 + j * 32 + q], 0.0f));
+        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)(m0 + r) * kHid + n0 + j * 32);
 #pragma unroll
         for (int q = 0; q < 4; q++) dst[q] = reinterpret_cast<const uint4 *>(o)[q];
       }
@@ -289,32 +294,44 @@ __global__ void __launch_bounds__(kTcThreads) tc_fwd_kernel(const bf16 *__restri
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTcN));
 }
 
 template <int K>
 constexpr size_t tc_smem() {
-  return (size_t)kTcRows * K * 2 + (size_t)kHid * K * 2 + 16;
+  return (size_t)kTcRows * K * 2 + (size_t)kTcN * K * 2 + 16;
 }
 
 // ---- tcgen05 backward products.  The same tile layout and MMA sequence;
 // operands whose source runs along M (or N) instead of K are transposed
-// while staging, one 16-byte source row (8 M/N values at one K) at a time.
+// while staging, 8 x 8 blocks at a time.
 constexpr int kTcK = 256;  // K per staged sub-tile
 
 // tile[mn][k] (K-major core matrices, KC = kTcK / 8) = src[(k0 + k) * ld + mn0 + mn]
-// for k < kn (else 0), mn < rows
+// for k < kn (else 0), mn < rows.  Each thread moves one 8 x 8 block: eight
+// 16-byte source rows (8 M/N values at 8 consecutive K) are transposed in
+// registers into eight 16-byte core-matrix rows (8 K values at one M/N).
 __device__ __forceinline__ void tc_stage_mn(unsigned char *tile, const bf16 *src, int ld, int mn0, int rows, int k0,
                                             int kn) {
   constexpr int KC = kTcK / 8;
-  for (int i = threadIdx.x; i < kTcK * (rows / 8); i += kTcThreads) {
-    const int k = i / (rows / 8), g = i % (rows / 8);  // one source row of 8 M/N values
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (k < kn) v = *reinterpret_cast<const uint4 *>(src + (size_t)(k0 + k) * ld + mn0 + g * 8);
-    const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+  const int G = rows / 8;
+  for (int i = threadIdx.x; i < KC * G; i += kTcThreads) {
+    const int c = i / G, g = i % G;  // K chunk, M/N group
+    __align__(16) bf16 v[8][8];
 #pragma unroll
-    for (int q = 0; q < 8; q++)
-      *reinterpret_cast<bf16 *>(tile + (g * KC + (k >> 3)) * 128 + q * 16 + (k & 7) * 2) = e[q];
+    for (int e = 0; e < 8; e++) {
+      const int k = c * 8 + e;
+      uint4 x = make_uint4(0, 0, 0, 0);
+      if (k < kn) x = *reinterpret_cast<const uint4 *>(src + (size_t)(k0 + k) * ld + mn0 + g * 8);
+      *reinterpret_cast<uint4 *>(v[e]) = x;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      __align__(16) bf16 w[8];
+#pragma unroll
+      for (int e = 0; e < 8; e++) w[e] = v[e][q];
+      *reinterpret_cast<uint4 *>(tile + (g * KC + c) * 128 + q * 16) = *reinterpret_cast<const uint4 *>(w);
+    }
   }
 }
 
@@ -370,7 +387,8 @@ __device__ __forceinline__ uint32_t tc_begin(uint64_t *mbar, uint32_t *tslot) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (threadIdx.x < 32) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "n"(kTcN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -382,11 +400,10 @@ __device__ __forceinline__ uint32_t tc_begin(uint64_t *mbar, uint32_t *tslot) {
 __device__ __forceinline__ void tc_end(uint32_t tmem) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTcN));
 }
 
-__host__ __device__ constexpr uint32_t tc_idesc(uint32_t n) { return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24); }
-constexpr size_t kTcBwdSmem = (size_t)kTcRows * kTcK * 2 + (size_t)kHid * kTcK * 2 + 16;
+constexpr size_t kTcBwdSmem = (size_t)kTcRows * kTcK * 2 + (size_t)kTcN * kTcK * 2 + 16;
 
 // dz_prev[M][256] = (dz[M][256] * W[256][256]) where h[M][256] > 0, as BF16
 __global__ void __launch_bounds__(kTcThreads) tc_dgrad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ W,
@@ -397,30 +414,30 @@ __global__ void __launch_bounds__(kTcThreads) tc_dgrad_kernel(const bf16 *__rest
   unsigned char *As = tsm, *Bs = tsm + kTcRows * kTcK * 2;
   uint64_t *mbar = reinterpret_cast<uint64_t *>(tsm + kTcBwdSmem - 16);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, m0 = blockIdx.x * kTcRows;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, m0 = blockIdx.x * kTcRows, n0 = blockIdx.y * kTcN;
   for (int i = t; i < kTcRows * KC; i += kTcThreads) {  // A = dz rows, K contiguous
     const int r = i / KC, c = i % KC;
     uint4 v = make_uint4(0, 0, 0, 0);
     if (m0 + r < M) v = *reinterpret_cast<const uint4 *>(dz + (size_t)(m0 + r) * kHid + c * 8);
     *reinterpret_cast<uint4 *>(As + ((r >> 3) * KC + c) * 128 + (r & 7) * 16) = v;
   }
-  tc_stage_mn(Bs, W, kHid, 0, kHid, 0, kTcK);  // B[n][k] = W[k][n]
+  tc_stage_mn(Bs, W, kHid, n0, kTcN, 0, kTcK);  // B[n][k] = W[k][n0 + n]
   const uint32_t tmem = tc_begin(mbar, tslot);
-  if (!tc_mma_tile(As, Bs, tmem, tc_idesc(256), false, mbar, 0)) {
+  if (!tc_mma_tile(As, Bs, tmem, tc_idesc(kTcN), false, mbar, 0)) {
     if (t == 0) atomicOr(err, 1u);
   } else {
     const int r = warp * 32 + lane;
 #pragma unroll 1
-    for (int j = 0; j < kHid / 32; j++) {
+    for (int j = 0; j < kTcN / 32; j++) {
       uint32_t v[32];
       tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32), v);
       if (m0 + r < M) {
-        const bf16 *hm = h + (size_t)(m0 + r) * kHid + j * 32;
+        const bf16 *hm = h + (size_t)(m0 + r) * kHid + n0 + j * 32;
         __align__(16) bf16 o[32];
 #pragma unroll
         for (int q = 0; q < 32; q++)
           o[q] = __float2bfloat16_rn(__bfloat162float(hm[q]) > 0.0f ? __uint_as_float(v[q]) : 0.0f);
-        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)(m0 + r) * kHid + j * 32);
+        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)(m0 + r) * kHid + n0 + j * 32);
 #pragma unroll
         for (int q = 0; q < 4; q++) dst[q] = reinterpret_cast<const uint4 *>(o)[q];
       }
@@ -430,8 +447,8 @@ __global__ void __launch_bounds__(kTcThreads) tc_dgrad_kernel(const bf16 *__rest
 }
 
 // partial z of dW[256][N] = dz^T h over rows [z*kchunk, ...): the CTA at
-// blockIdx.x = half takes output rows j = 128*half .. +127, K = batch rows
-// in sub-tiles of kTcK accumulated in TMEM
+// (blockIdx.x, blockIdx.y) takes output rows j = 128*x .. +127 and columns
+// 64*y .. +63, K = batch rows in sub-tiles of kTcK accumulated in TMEM
 __global__ void __launch_bounds__(kTcThreads) tc_wgrad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ h,
                                                               int N, int rows, int kchunk, float *__restrict__ part,
                                                               uint32_t *err) {
@@ -440,7 +457,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_wgrad_kernel(const bf16 *__rest
   uint64_t *mbar = reinterpret_cast<uint64_t *>(tsm + kTcBwdSmem - 16);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int j0 = blockIdx.x * kTcRows, z = blockIdx.y;
+  const int j0 = blockIdx.x * kTcRows, n0 = blockIdx.y * kTcN, z = blockIdx.z;
   const int kbeg = z * kchunk, kend = min(rows, kbeg + kchunk);
   const uint32_t tmem = tc_begin(mbar, tslot);
   bool ok = true;
@@ -448,16 +465,16 @@ __global__ void __launch_bounds__(kTcThreads) tc_wgrad_kernel(const bf16 *__rest
   for (int k0 = kbeg; k0 < kend && ok; k0 += kTcK, phase ^= 1u) {
     const int kn = min(kTcK, kend - k0);
     tc_stage_mn(As, dz, kHid, j0, kTcRows, k0, kn);  // A[j][r] = dz[r][j0 + j]
-    tc_stage_mn(Bs, h, N, 0, N, k0, kn);             // B[i][r] = h[r][i]
-    ok = tc_mma_tile(As, Bs, tmem, tc_idesc((uint32_t)N), k0 > kbeg, mbar, phase);
+    tc_stage_mn(Bs, h, N, n0, kTcN, k0, kn);         // B[i][r] = h[r][n0 + i]
+    ok = tc_mma_tile(As, Bs, tmem, tc_idesc(kTcN), k0 > kbeg, mbar, phase);
   }
   if (!ok) {
     if (t == 0) atomicOr(err, 1u);
   } else {
     const int r = warp * 32 + lane;  // output row j0 + r
-    float *dst = part + ((size_t)z * kHid + j0 + r) * N;
+    float *dst = part + ((size_t)z * kHid + j0 + r) * N + n0;
 #pragma unroll 1
-    for (int j = 0; j < N / 32; j++) {
+    for (int j = 0; j < kTcN / 32; j++) {
       uint32_t v[32];
       tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32), v);
 #pragma unroll
@@ -619,7 +636,7 @@ int wgrad_splits(int rows) { return std::max(1, std::min(64, (rows + 511) / 512)
 void forward(rc_mlp *m, int n, cudaStream_t s) {
   const bf16 *Wb = m->Pb;
   if (m->backend == 1) {
-    const unsigned grid = (unsigned)((n + kTcRows - 1) / kTcRows);
+    const dim3 grid((unsigned)((n + kTcRows - 1) / kTcRows), kHid / kTcN);
     count_launch();
     tc_fwd_kernel<kIn><<<grid, kTcThreads, tc_smem<kIn>(), s>>>(m->Xb, Wb + oW1, m->P + ob1, m->H1, n, m->tc_err);
     count_launch();
@@ -650,8 +667,8 @@ void weight_grads(rc_mlp *m, const bf16 *dz, const bf16 *h, int kin, int n, size
     const int kchunk = (((n + splits - 1) / splits) + 15) / 16 * 16;
     const int zs = (n + kchunk - 1) / kchunk;
     count_launch();
-    tc_wgrad_kernel<<<dim3(kHid / kTcRows, zs), kTcThreads, kTcBwdSmem, s>>>(dz, h, kin, n, kchunk, m->part,
-                                                                           m->tc_err);
+    tc_wgrad_kernel<<<dim3(kHid / kTcRows, kin / kTcN, zs), kTcThreads, kTcBwdSmem, s>>>(dz, h, kin, n, kchunk,
+                                                                                        m->part, m->tc_err);
     count_launch();
     reduce_parts_kernel<<<nblk((size_t)kHid * kin, 256), 256, 0, s>>>(m->part, zs, kHid * kin, m->G + oW);
     const int chunks = (n + kColRows - 1) / kColRows;
@@ -704,7 +721,7 @@ void backward(rc_mlp *m, int n, cudaStream_t s) {
   g.N = kHid;
   g.K = kHid;
   g.A = m->D2, g.B = m->Pb + oW3, g.mask = m->H2, g.out = m->D1;
-  const unsigned tgrid = (unsigned)((n + kTcRows - 1) / kTcRows);
+  const dim3 tgrid((unsigned)((n + kTcRows - 1) / kTcRows), kHid / kTcN);
   count_launch();
   if (m->backend == 1)
     tc_dgrad_kernel<<<tgrid, kTcThreads, kTcBwdSmem, s>>>(m->D2, m->Pb + oW3, m->H2, m->D1, n, m->tc_err);
