@@ -39,14 +39,16 @@ SAMPLE_GROUPS = 96
 
 
 # DRAM traffic of interp_kernel per launch: dram__bytes_read.sum +
-# dram__bytes_write.sum, mean over the 9 launches of one check, from
-#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
-#       -k regex:interp_kernel -s 27 -c 9 python bench.py --steps 3 --warmup 3 \
-#       --no-cpu-baseline --batch-kernels 0 --proposal-kernels 0
+# dram__bytes_write.sum, mean over the 108 interval launches of the command
+# below (the 18 speculative launches whose gate stayed closed, under 10 us
+# each, are left out: the bench's own timing runs with the gate off), from
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
+#       --clock-control none -k regex:interp_kernel --csv \
+#       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --batch-kernels 0 --proposal-kernels 0
 # (profiles/interp_kernel_large_instance.md).  It holds only for the kernel
 # sources it was taken on; any change to them reports null.
-INTERP_TRAFFIC = {"sources_sha256": "5893b564e63b51cf305821cf5100dd7c97eacfcc4b89120ff03fbe8c77434827",
-                  "bytes_per_launch": 148880441}
+INTERP_TRAFFIC = {"sources_sha256": "eccde2675963590d6cbbb7ada022c1f3076cfd5b32dd827a06ce209a2c3975e4",
+                  "bytes_per_launch": 148552201}
 INTERP_SOURCES = ("paper_1308_3203_gb300/csrc/interp.cu", "paper_1308_3203_gb300/csrc/device.cuh")
 
 
