@@ -286,6 +286,31 @@ int rc_explore_pairs(const rc_bytecode *bc, uint32_t groups, uint32_t group_size
                      uint64_t max_states, rc_pair_interval *out, uint32_t max_intervals, uint32_t *n_out,
                      uint32_t *pair_detail);
 
+/* ---- two-work-item NoRace pre-filter (no GPU work)
+ *
+ * A restricted, sound form of the paper's symbolic method (Sec. 5-6: two
+ * renamed work-items i != j; Table 1's bounds premise).  Every register is
+ * tracked as an affine form in tid and wg (optionally reduced modulo a
+ * constant) by a fixpoint over the bytecode's control flow; branch
+ * conditions are ignored, so every access counts as made by every
+ * work-item.  For the launch shape groups x group_size and the input
+ * lengths (global_init is not read), race_free = 1 means no two work-items
+ * can make a conflicting pair of accesses in one barrier interval under any
+ * schedule: every pair of accesses to one array (one a store) in a common
+ * barrier region has disjoint index ranges, or the same index form that is
+ * one-to-one on the work-items (one group's, for local arrays), or both
+ * store one constant.  race_free = 0 decides nothing (the checker does);
+ * first_pc_a/b name the first pair left open.  in_bounds = 1 means every
+ * index is provably within its array. */
+typedef struct {
+  int32_t race_free;
+  int32_t in_bounds;
+  uint32_t first_pc_a, first_pc_b; /* bytecode positions, 0xFFFFFFFF if none */
+  uint32_t n_pairs;                /* access pairs that may meet in one interval */
+  uint32_t n_unresolved;           /* pairs the pre-filter could not clear      */
+} rc_prove_result;
+int rc_prove(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in, rc_prove_result *out);
+
 /* ---- learned proposal: which candidate instances to check first
  *
  * The method needs, per kernel, a set of candidate instances (launch shape

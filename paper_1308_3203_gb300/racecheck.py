@@ -65,6 +65,11 @@ class _PairInterval(ctypes.Structure):
                                                "first_j", "complete", "reserved")] + [("n_states", ctypes.c_uint64)]
 
 
+class _ProveResult(ctypes.Structure):
+    _fields_ = [("race_free", ctypes.c_int32), ("in_bounds", ctypes.c_int32), ("first_pc_a", ctypes.c_uint32),
+                ("first_pc_b", ctypes.c_uint32), ("n_pairs", ctypes.c_uint32), ("n_unresolved", ctypes.c_uint32)]
+
+
 class _SearchResult(ctypes.Structure):
     _fields_ = [("first", ctypes.c_int64), ("checks", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("seconds", ctypes.c_double)]
@@ -144,7 +149,9 @@ def load() -> ctypes.CDLL:
                                          ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]
         lib.rc_mlp_set_backend.argtypes = [vp, c_int]
         lib.rc_mlp_backend_error.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
-        for f in ("rc_mlp_set_backend", "rc_mlp_backend_error", "rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
+        lib.rc_prove.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input),
+                                 ctypes.POINTER(_ProveResult)]
+        for f in ("rc_prove", "rc_mlp_set_backend", "rc_mlp_backend_error", "rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
                   "rc_mlp_forward", "rc_mlp_grad", "rc_mlp_train", "rc_search"):
             getattr(lib, f).restype = c_int
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
@@ -355,6 +362,20 @@ def autotune_reset() -> None:
 def autotune_lookup(kind: int, a: int, b: int) -> int:
     """Decided strategy for a size class (0 undecided, 1 sort, 2 shadow)."""
     return int(load().rc_autotune_lookup(kind, a, b))
+
+
+def prove(bc: Bytecode, groups: int, group_size: int, globals_) -> dict:
+    """Two-work-item NoRace pre-filter for this launch shape (host only):
+    race_free / in_bounds are proofs when True and say nothing when False."""
+    inp, keep = _marshal(globals_, None, False)
+    res = _ProveResult()
+    rc = load().rc_prove(bc.handle, groups, group_size, ctypes.byref(inp), ctypes.byref(res))
+    del keep
+    if rc:
+        _raise(rc)
+    return dict(race_free=bool(res.race_free), in_bounds=bool(res.in_bounds),
+                first=(res.first_pc_a, res.first_pc_b) if not res.race_free else None,
+                n_pairs=res.n_pairs, n_unresolved=res.n_unresolved)
 
 
 def explore(bc: Bytecode, groups: int, group_size: int, globals_, max_states: int = 0,

@@ -1,0 +1,178 @@
+"""Two-work-item NoRace pre-filter (host code of the library, no GPU).
+
+The pre-filter's "race-free" and "in bounds" are proofs: whenever it says
+so, the oracle's canonical run has no WW_RACE / RW_RACE record (resp. no
+OOB record) and every schedule the interleaving explorer enumerates reaches
+one shared state.  When it says nothing, the checker decides.
+"""
+import numpy as np
+import pytest
+
+from paper_1308_3203_gb300 import workloads as W
+
+WW_RACE, RW_RACE, OOB = 1, 3, 16
+
+
+@pytest.fixture(scope="module")
+def rc():
+    from paper_1308_3203_gb300 import build as gpu_build
+    gpu_build.build()
+    from paper_1308_3203_gb300 import racecheck
+    racecheck.load()
+    return racecheck
+
+
+def classes(rep):
+    return set(int(c) for c in rep["records"][:, 4]) if len(rep["records"]) else set()
+
+
+def zeros(*ns):
+    return [np.zeros(n, np.int32) for n in ns]
+
+
+# (source, groups, group size, array lengths, race_free, in_bounds) -- the
+# expected verdicts are what a sound two-work-item argument can show
+HAND = [
+    # one cell per work-item (Sec. 5's canonical NoRace case)
+    ("kernel k(global int A[]) { A[tid + wg * 32] = tid; }", 4, 32, (128,), True, True),
+    ("kernel k(global int A[]) { A[gtid] = A[gtid] + 1; }", 4, 32, (128,), True, True),
+    # every work-item writes cell 0 with its own value: a race
+    ("kernel k(global int A[]) { A[0] = tid; }", 1, 32, (4,), False, True),
+    # ... with one value: benign
+    ("kernel k(global int A[]) { A[0] = 7; }", 2, 32, (4,), True, True),
+    # barrier separates the write of L[tid] from the read of a neighbour's cell
+    ("kernel k(global int A[], local int L[32]) {\n L[tid] = tid;\n barrier;\n"
+     " A[gtid] = L[(tid + 1) % 32];\n}", 2, 32, (64,), True, True),
+    # the same without the barrier: the read meets the neighbour's write
+    ("kernel k(global int A[], local int L[32]) {\n L[tid] = tid;\n"
+     " A[gtid] = L[(tid + 1) % 32];\n}", 2, 32, (64,), False, True),
+    # disjoint ranges: writes to [0, 32), reads from [32, 64)
+    ("kernel k(global int A[]) { A[tid] = A[tid + 32]; }", 1, 32, (64,), True, True),
+    # too short an array: race-free but not in bounds
+    ("kernel k(global int A[]) { A[tid] = 1; }", 1, 32, (16,), True, False),
+    # a guard narrows who writes: only work-item 0 of one group
+    ("kernel k(global int g) { if (tid == 0) { g = 5 + tid; } }", 1, 32, (1,), True, True),
+    ("kernel k(global int g) { g = 5 + tid; }", 1, 32, (1,), False, True),
+    # ... but tid 0 of every group writes its own wg: a race
+    ("kernel k(global int g) { if (tid == 0) { g = wg; } }", 4, 32, (1,), False, True),
+    # a guard keeps the index in bounds
+    ("kernel k(global int A[]) { if (tid < 8) { A[tid] = 1; } }", 1, 32, (8,), True, True),
+    ("kernel k(global int A[]) { if (tid >= 24) { A[tid - 24] = 1; } }", 1, 32, (8,), True, True),
+    # two guarded halves writing disjoint ranges
+    ("kernel k(global int A[]) {\n if (tid < 8) { A[tid] = 1; }\n"
+     " if (tid >= 8) { A[tid + 8] = 2; }\n}", 1, 16, (24,), True, True),
+    # two guarded halves that overlap at cells 0..7 with different values
+    ("kernel k(global int A[]) {\n if (tid < 8) { A[tid] = 1; }\n"
+     " if (tid >= 8) { A[tid - 8] = 2; }\n}", 1, 16, (8,), False, True),
+    # an else branch is not narrowed (it is entered by the jump): its cells
+    # [12, 20) seem to reach down to 4 and meet the then-branch's [0, 8)
+    ("kernel k(global int A[]) { if (tid < 8) { A[tid] = 1; } else { A[tid + 4] = 2; } }",
+     1, 16, (20,), False, True),
+    # ... where the full range is disjoint anyway, the claim stands
+    ("kernel k(global int A[]) { if (tid < 8) { A[tid] = 1; } else { A[tid + 8] = 2; } }",
+     1, 16, (24,), True, True),
+    # a loop counter is a bounded variable of its own: each work-item owns 4 cells
+    ("kernel k(global int A[]) { for i in 0 .. 4 { A[gtid * 4 + i] = i; } }", 2, 8, (64,), True, True),
+    # ... nested, with a stride that keeps the cells apart
+    ("kernel k(global int A[]) { for i in 0 .. 4 { for j in 0 .. 2 { A[gtid * 8 + i * 2 + j] = j; } } }",
+     2, 8, (128,), True, True),
+    # ... but 4 cells at a stride of 2 overlap the next work-item's: a race
+    ("kernel k(global int A[]) { for i in 0 .. 4 { A[gtid * 2 + i] = i; } }", 2, 8, (64,), False, True),
+    # a loaded index says nothing
+    ("kernel k(global int A[], global int B[]) { A[B[gtid]] = 1; }", 1, 8, (8, 8), True, False),
+    ("kernel k(global int A[], global int B[]) { A[B[gtid]] = tid; }", 1, 8, (8, 8), False, False),
+]
+
+
+@pytest.mark.parametrize("case", range(len(HAND)))
+def test_hand_examples(rc, oracle, case):
+    src, G, S, lens, want_free, want_bounds = HAND[case]
+    g = zeros(*lens)
+    p = rc.prove(rc.compile(src), G, S, g)
+    assert (p["race_free"], p["in_bounds"]) == (want_free, want_bounds), (src, p)
+    rep = oracle.check(src, G, S, g)
+    cls = classes(rep)
+    if p["race_free"]:
+        assert not cls & {WW_RACE, RW_RACE}
+    if p["in_bounds"]:
+        assert OOB not in cls
+    # the racy examples are racy: the claims withheld above are not just imprecision
+    if src.startswith("kernel k(global int A[]) { A[0] = tid") or "g = wg" in src or "tid - 8" in src \
+            or "gtid * 2 + i" in src:
+        assert cls & {WW_RACE, RW_RACE}
+
+
+def test_first_pair_and_counts(rc):
+    p = rc.prove(rc.compile("kernel k(global int A[]) {\n A[tid] = 1;\n A[0] = tid;\n}"), 1, 8, zeros(8))
+    assert not p["race_free"] and p["n_unresolved"] >= 1 and p["n_pairs"] >= p["n_unresolved"]
+    assert p["first"][0] <= p["first"][1]
+    q = rc.prove(rc.compile("kernel k(global int A[]) { A[tid] = 1; }"), 1, 8, zeros(8))
+    assert q["race_free"] and q["first"] is None and q["n_unresolved"] == 0 and q["n_pairs"] == 1
+
+
+def test_single_work_item_is_race_free(rc):
+    p = rc.prove(rc.compile("kernel k(global int A[]) { A[0] = tid; A[1] = A[0]; }"), 1, 1, zeros(2))
+    assert p["race_free"] and p["in_bounds"]
+
+
+def test_rejects_bad_arguments(rc):
+    bc = rc.compile("kernel k(global int A[]) { A[tid] = 1; }")
+    with pytest.raises(Exception):
+        rc.prove(bc, 1, 8, [])          # one global array declared
+    with pytest.raises(Exception):
+        rc.prove(bc, 0, 8, zeros(8))    # empty launch
+
+
+def families():
+    out = []
+    out += [("tiny", W.tiny_kernel(s)) for s in range(150)]
+    out += [("small", W.small_kernel(s, group_size=8, n_stmts=12)) for s in range(150)]
+    out += [("small64", W.small_kernel(s)) for s in range(40)]
+    for s in range(10):
+        pk = W.proposal_kernel(s)
+        for (G, S, i) in W.proposal_candidates(s, 8):
+            if G * S <= 4096:
+                out.append(("proposal", pk.instance(G, S, i)))
+    out += [("large", W.large_kernel(s, groups=2, group_size=32, global_len=4096, local_len=64,
+                                     n_stmts=40, n_barriers=3)) for s in range(12)]
+    out += [("stress", W.stress_kernel(s, groups=4, group_size=64)) for s in range(12)]
+    return out
+
+
+def test_sound_against_the_oracle(rc, oracle):
+    """No generated instance on which the pre-filter proves race freedom (or
+    bounds) has a race (or OOB) record in the oracle's report; and the proof
+    fires on a real share of the families where it can."""
+    proved = {}
+    for fam, inst in families():
+        p = rc.prove(rc.compile(inst.src), inst.groups, inst.group_size, inst.globals)
+        rep = oracle.check(inst.src, inst.groups, inst.group_size, inst.globals)
+        cls = classes(rep)
+        if p["race_free"]:
+            assert not cls & {WW_RACE, RW_RACE}, (inst.name, p)
+        if p["in_bounds"]:
+            assert OOB not in cls, (inst.name, p)
+        n, k = proved.get(fam, (0, 0))
+        proved[fam] = (n + 1, k + int(p["race_free"]))
+    assert proved["tiny"][1] >= 20, proved
+    assert proved["small"][1] >= 20, proved
+    assert proved["large"][1] >= 8 and proved["stress"][1] >= 2, proved
+
+
+def test_race_free_tiny_kernels_are_schedule_independent(rc, oracle):
+    """Ground truth beyond the canonical run: on every tiny instance the
+    pre-filter proves race-free, every interval of every schedule reaches a
+    single shared state and no read depends on the schedule."""
+    n = 0
+    for s in range(200):
+        inst = W.tiny_kernel(s)
+        p = rc.prove(rc.compile(inst.src), inst.groups, inst.group_size, inst.globals)
+        if not p["race_free"]:
+            continue
+        ex = oracle.explore(inst.src, inst.groups, inst.group_size, inst.globals)
+        assert not ex["overflow"]
+        assert all(e == 1 for e in ex["end_states"]), (inst.name, ex["end_states"])
+        assert not any(ex["deviated"]), inst.name
+        assert len(ex["finals"]) == 1
+        n += 1
+    assert n >= 10
