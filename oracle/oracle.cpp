@@ -21,6 +21,15 @@
 // schedule, per-thread last writes, read/write conflicts, witnesses, commit
 // order, arithmetic) are the ones listed in the project's design notes; each
 // is restated next to the code that implements it below.
+//
+// Work-group-scoped barriers (OpenCL's barrier, against the paper's
+// kernel-wide one of Sec. 2 / Sec. 4): the same lock-step run (round k runs
+// every group's k-th interval, which is one legal schedule when a barrier
+// only waits for its own group), but the barrier-release rule is applied to
+// each work-group on its own -- groups may stop at different barriers, and
+// a group whose work-items all exited is finished while others go on -- and,
+// since no barrier orders work-items of different groups, every global cell
+// is also classified over the whole run between groups (run_cross_group).
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>
@@ -37,6 +46,7 @@ namespace orc {
 
 enum Cls : uint32_t {
   C_WW_RACE = 1, C_WW_BENIGN = 2, C_RW_RACE = 3,
+  C_XG_WW_RACE = 4, C_XG_WW_BENIGN = 5, C_XG_RW_RACE = 6,
   C_OOB = 16, C_ASSERT = 17, C_DIVERGENCE = 18
 };
 enum Status : int32_t {
@@ -83,6 +93,9 @@ struct Checker {
   std::vector<int32_t> local_snap;   // committed local memory, G x local_total
   std::vector<Thread> th;
   Report rep;
+  bool group_scope = false;
+  std::map<uint32_t, std::vector<Access>> whole_run;  // group scope: every access to each global cell
+  std::vector<int32_t> initial_global;                // global memory before the run
 
   // per interval
   std::map<Cell, std::vector<Access>> log;
@@ -244,9 +257,99 @@ struct Checker {
     }
   }
 
+  // Group scope: classify each global cell over the whole run between
+  // work-items of different groups (no barrier orders them).
+  //  * XG WW: writers in two or more groups.  XG_WW_BENIGN when every write
+  //    to the cell stored one value, else XG_WW_RACE; witness (smallest
+  //    writer, largest writer).
+  //  * XG RW: a reader and a writer in different groups, unless the cell
+  //    held one value all along: its value before the run, every value
+  //    written and every value the reads observed are one and the same (a
+  //    read by another group may come before or after any write).
+  //    Witness, from the smallest/largest reader r0/r1 and writer w0/w1:
+  //    (r0, w0) if their groups differ, else (r0, w1) if those differ, else
+  //    (r1, w0).
+  //  Counts: n_readers = reads, n_writers = writes, n_accesses = both.
+  void run_cross_group() {
+    for (auto &kv : whole_run) {
+      std::set<uint32_t> wgw, wgr;
+      std::set<int32_t> written, seen;
+      uint32_t w0 = 0, w1 = 0, r0 = 0, r1 = 0, nrd = 0, nwr = 0;
+      for (const Access &a : kv.second) {
+        if (a.write) {
+          if (!nwr || a.gtid < w0) w0 = a.gtid;
+          if (!nwr || a.gtid > w1) w1 = a.gtid;
+          nwr++;
+          wgw.insert(a.gtid / S);
+          written.insert(a.value);
+        } else {
+          if (!nrd || a.gtid < r0) r0 = a.gtid;
+          if (!nrd || a.gtid > r1) r1 = a.gtid;
+          nrd++;
+          wgr.insert(a.gtid / S);
+          seen.insert(a.value);
+        }
+      }
+      Record base{0xFFFFFFFFu, 0, 0, kv.first, 0, 0, 0, nrd, nwr, nrd + nwr};
+      if (wgw.size() >= 2) {
+        Record r = base;
+        r.cls = written.size() == 1 ? C_XG_WW_BENIGN : C_XG_WW_RACE;
+        r.t_a = w0;
+        r.t_b = w1;
+        rep.records.push_back(r);
+      }
+      const bool cross = !wgw.empty() && !wgr.empty() &&
+                         !(wgw.size() == 1 && wgr.size() == 1 && *wgw.begin() == *wgr.begin());
+      std::set<int32_t> all = written;
+      all.insert(seen.begin(), seen.end());
+      all.insert(initial_global[kv.first]);
+      if (cross && all.size() >= 2) {
+        Record r = base;
+        r.cls = C_XG_RW_RACE;
+        if (r0 / S != w0 / S) { r.t_a = r0; r.t_b = w0; }
+        else if (r0 / S != w1 / S) { r.t_a = r0; r.t_b = w1; }
+        else { r.t_a = r1; r.t_b = w0; }
+        rep.records.push_back(r);
+      }
+    }
+  }
+
+  // Group scope: the barrier-release rule per work-group.  Returns whether
+  // some group waits at a barrier (the run goes on); adds DIVERGENCE records
+  // (wg = the group) for every group whose live work-items stopped at two
+  // or more points, and sets diverged.
+  bool group_agreement(uint32_t interval, std::vector<char> &done, bool &diverged) {
+    bool any_barrier = false;
+    for (uint32_t wg = 0; wg < G; wg++) {
+      if (done[wg]) continue;
+      std::map<uint32_t, std::pair<uint32_t, uint32_t>> stops;  // stop id -> (min gtid, count)
+      bool waits = false;
+      for (uint32_t t = 0; t < S; t++) {
+        const uint32_t g = wg * S + t;
+        uint32_t id;
+        if (th[g].st == AT_BARRIER) { id = (uint32_t)cfg.nodes[th[g].node].id; waits = true; }
+        else if (th[g].st == EXITED) id = 0xFFFFFFFFu;  // exited in this round: the group was not done
+        else continue;
+        auto it = stops.find(id);
+        if (it == stops.end()) stops[id] = {g, 1};
+        else it->second.second++;
+      }
+      if (stops.size() >= 2) {
+        diverged = true;
+        for (auto &s2 : stops)
+          errors.push_back({interval, 0, wg, 0, C_DIVERGENCE, s2.second.first, s2.first, 0, 0, s2.second.second});
+      }
+      if (!waits) done[wg] = 1;  // every live work-item exited: the group is finished
+      any_barrier |= waits;
+    }
+    return any_barrier;
+  }
+
   void run(bool reverse) {
     const uint32_t N = G * S;
     th.assign(N, Thread{cfg.start, RUNNING, std::vector<int32_t>(cfg.n_vars, 0)});
+    std::vector<char> done(G, 0);  // group scope: groups whose work-items all exited
+    initial_global = global_snap;
     for (uint32_t interval = 0;; interval++) {
       log.clear();
       errors.clear();
@@ -257,11 +360,19 @@ struct Checker {
       rep.n_intervals = interval + 1;
       // classify every touched cell, in (space, wg, addr) order
       for (auto &kv : log) classify_cell(interval, kv.first, kv.second);
+      if (group_scope)
+        for (auto &kv : log)
+          if (std::get<0>(kv.first) == 0) {
+            auto &v = whole_run[std::get<2>(kv.first)];
+            v.insert(v.end(), kv.second.begin(), kv.second.end());
+          }
       // barrier agreement (Sec. 4 barrier-release rule): every thread that
-      // is still alive must stop at the same barrier, or all must exit.
+      // is still alive must stop at the same barrier, or all must exit
+      // (group scope: within each work-group).
       std::map<uint32_t, std::pair<uint32_t, uint32_t>> stops;  // stop id -> (min gtid, count)
-      bool any_barrier = false;
-      for (uint32_t g = 0; g < N; g++) {
+      bool any_barrier = false, group_div = false;
+      if (group_scope) any_barrier = group_agreement(interval, done, group_div);
+      for (uint32_t g = 0; g < N && !group_scope; g++) {
         uint32_t id;
         // a thread that reached exit stops at the implicit final barrier;
         // once one has, the run ends, so no earlier exits are still around
@@ -272,8 +383,8 @@ struct Checker {
         if (it == stops.end()) stops[id] = {g, 1};
         else it->second.second++;
       }
-      bool diverged = stops.size() >= 2;
-      if (diverged) {
+      bool diverged = stops.size() >= 2 || group_div;
+      if (stops.size() >= 2) {
         for (auto &s : stops)
           errors.push_back({interval, 0, 0, 0, C_DIVERGENCE, s.second.first, s.first, 0, 0, s.second.second});
       }
@@ -297,9 +408,13 @@ struct Checker {
       if (diverged || !any_barrier) break;
     }
     // report: race records already sorted by (interval, space, wg, addr, cls);
-    // error records follow, sorted by (interval, kind, gtid).
+    // group scope: the cross-group records of the whole run (interval
+    // 0xFFFFFFFF) by (addr, cls); error records follow, sorted by
+    // (interval, kind, gtid).
+    if (group_scope) run_cross_group();
     bool racy = false, div = false, as = false, oob = false;
-    for (auto &r : rep.records) racy |= (r.cls == C_WW_RACE || r.cls == C_RW_RACE);
+    for (auto &r : rep.records)
+      racy |= (r.cls == C_WW_RACE || r.cls == C_RW_RACE || r.cls == C_XG_WW_RACE || r.cls == C_XG_RW_RACE);
     for (auto &e : interval_errors) {
       div |= e.cls == C_DIVERGENCE;
       as |= e.cls == C_ASSERT;
@@ -325,12 +440,13 @@ struct OracleHandle {
 extern "C" {
 
 // Run the checker.  global_len/global_init give one int32 array per `global`
-// declaration, in declaration order.  reverse != 0 runs the threads of every
-// interval in descending gtid order (the report must not change).
+// declaration, in declaration order.  mode bit 0 runs the threads of every
+// interval in descending gtid order (the report must not change); bit 1
+// takes barriers as work-group scoped.
 // Returns 0 on success, 1 on a parse error (message in err), 2 on a bad
 // launch shape or input.
 int oracle_check(const char *src, uint32_t groups, uint32_t group_size, uint32_t n_global,
-                 const uint64_t *global_len, const int32_t *const *global_init, int reverse,
+                 const uint64_t *global_len, const int32_t *const *global_init, int mode,
                  void **out, char *err, size_t err_len) {
   *out = nullptr;
   try {
@@ -366,7 +482,8 @@ int oracle_check(const char *src, uint32_t groups, uint32_t group_size, uint32_t
       gi++;
     }
     ck.local_snap.assign((uint64_t)groups * ck.local_total, 0);
-    ck.run(reverse != 0);
+    ck.group_scope = (mode & 2) != 0;
+    ck.run((mode & 1) != 0);
     auto *h = new OracleHandle{std::move(ck.rep)};
     *out = h;
     return 0;

@@ -104,10 +104,13 @@ def _marshal(globals_):
     return arrs, n, lens, ptrs
 
 
-def check(src: str, groups: int, group_size: int, globals_, reverse: bool = False) -> dict:
+def check(src: str, groups: int, group_size: int, globals_, reverse: bool = False,
+          group_barriers: bool = False) -> dict:
     """Run the reference checker on one instance.
 
     ``globals_`` is one int32 array per ``global`` declaration, in order.
+    ``group_barriers`` takes barriers as work-group scoped (per-group barrier
+    agreement, cross-group records of the whole run).
     Returns dict(status, n_intervals, n_access, n_global, n_local,
     records (uint32 [n, 10]), final (int32, all global arrays concatenated)).
     """
@@ -115,7 +118,8 @@ def check(src: str, groups: int, group_size: int, globals_, reverse: bool = Fals
     arrs, n, lens, ptrs = _marshal(globals_)
     h = ctypes.c_void_p()
     err = ctypes.create_string_buffer(512)
-    rc = lib.oracle_check(src.encode(), groups, group_size, n, lens, ptrs, 1 if reverse else 0,
+    rc = lib.oracle_check(src.encode(), groups, group_size, n, lens, ptrs,
+                          (1 if reverse else 0) | (2 if group_barriers else 0),
                           ctypes.byref(h), err, 512)
     if rc != 0:
         raise OracleError(f"oracle rc={rc}: {err.value.decode()}")

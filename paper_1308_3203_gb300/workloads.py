@@ -535,3 +535,59 @@ def proposal_candidates(seed: int, n: int = 64) -> list:
         G = int(round(math.exp(rng.uniform(0.0, math.log(64)))))
         out.append((max(1, min(64, G)), S, int(rng.integers(1 << 31))))
     return out
+
+
+# ----------------------------------------------------------------------------
+# work-group-scoped barrier kernels
+
+
+def group_kernel(seed: int, groups: int = 4, group_size: int = 32, n_stmts: int = 24) -> Instance:
+    """Kernels for work-group-scoped barriers: each group has a slab of its
+    own in A (accesses there can race only inside the group), a shared tail
+    of 16 cells that every group reads and writes, a local array, barriers
+    every work-item takes, and barriers only some groups take (under a
+    condition on wg, so a whole group agrees)."""
+    rng = np.random.default_rng([13, seed])
+    G, S = groups, group_size
+    L = G * S + 16
+    lines = []
+
+    def own():
+        return f"A[wg * {S} + ({int(rng.integers(1, 3))} * tid + {int(rng.integers(S))}) % {S}]"
+
+    def shared():
+        return f"A[{G * S} + (tid + {int(rng.integers(16))}) % {int(rng.choice([1, 4, 16]))}]"
+
+    def val():
+        k = rng.random()
+        if k < 0.3:
+            return str(int(rng.integers(4)))
+        if k < 0.6:
+            return f"(wg + {int(rng.integers(3))}) % 3"
+        return f"x + {int(rng.integers(3))}"
+
+    def stmt(depth):
+        k = rng.random()
+        if k < 0.25:
+            return [f"x = {own()};"]
+        if k < 0.45:
+            return [f"{own()} = {val()};"]
+        if k < 0.55:
+            return [f"x = {shared()};"]
+        if k < 0.63:
+            return [f"{shared()} = {val()};"]
+        if k < 0.72:
+            return [f"Lc[(tid + {int(rng.integers(8))}) % 8] = {val()};"] if rng.random() < 0.5 else \
+                   [f"x = Lc[tid % 8];"]
+        if k < 0.8 or depth > 0:
+            return ["barrier;"] if depth == 0 else [f"x = x + {int(rng.integers(3))};"]
+        m = int(rng.integers(2, 4))
+        body = [f"if (wg % {m} == {int(rng.integers(m))}) {{", "  barrier;"]
+        body += ["  " + x for x in stmt(1)]
+        return body + ["}"]
+
+    for _ in range(n_stmts):
+        lines += stmt(0)
+    src = "kernel grp(global int A[], local int Lc[8]) {\n" + "\n".join("  " + x for x in lines) + "\n}\n"
+    A = rng.integers(0, 4, size=L, dtype=np.int32)
+    return Instance(f"group-s{seed}-{G}x{S}", src, G, S, [A])

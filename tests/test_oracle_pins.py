@@ -334,3 +334,151 @@ def test_bruteforce_schedules(oracle, chunk):
             seen["ww"] += 1
             assert e["end_states"][k] >= 2, (seed, i.src)
     assert seen["free"] and seen["rw"], seen
+
+
+# ---------------------------------------------------------------- work-group-scoped barriers
+# Closed forms for the cross-group classification of the whole run and the
+# per-group barrier-release rule (OpenCL barriers wait for their own group
+# only), and two reductions to the kernel-wide checker.
+
+XG = 2**32 - 1  # interval field of the cross-group records
+
+
+def _grp(oracle, body, G, S, A, gb=True, decl="global int A[]"):
+    src = f"kernel t({decl}) {{\n{body}\n}}\n"
+    return oracle.check(src, G, S, [np.array(A, np.int32)], group_barriers=gb)
+
+
+def _xg(r):
+    return [list(map(int, x)) for x in r["records"] if x[0] == XG]
+
+
+@pytest.mark.parametrize("G,S,m", [(2, 4, 4), (3, 8, 3), (4, 32, 5)])
+@pytest.mark.parametrize("same", [False, True])
+def test_group_scope_cross_group_writes(oracle, G, S, m, same):
+    # every group writes cells 0..m-1 (work-items tid = c mod m): writers in
+    # all G groups; values wg + 7 differ between groups, 7 does not
+    r = _grp(oracle, f"A[tid % {m}] = {'7' if same else 'wg + 7'};", G, S, [0] * m)
+    want = []
+    for c in range(m):
+        tids = [t for t in range(S) if t % m == c]
+        nw = G * len(tids)
+        want.append(rec(XG, c, 5 if same else 4, tids[0], (G - 1) * S + tids[-1], 0, nw, nw))
+    assert _xg(r) == want
+    assert r["status"] == (0 if same else 1)
+
+
+@pytest.mark.parametrize("G,S,k", [(2, 4, 1), (3, 4, 5), (4, 8, 3), (2, 16, 16)])
+def test_group_scope_neighbour_read_after_barrier(oracle, G, S, k):
+    # A[gtid] = 1 | barrier | read A[(gtid + k) % N]: the barrier orders the
+    # pair only inside a group; cell c (written by c, read by (c - k) mod N)
+    # races across groups: value 0 before, 1 after the write
+    N = G * S
+    body = f"A[gtid] = 1;\nbarrier;\nx = A[(gtid + {k}) % {N}];"
+    want = [rec(XG, c, 6, (c - k) % N, c, 1, 1, 2) for c in range(N) if ((c - k) % N) // S != c // S]
+    r = _grp(oracle, body, G, S, [0] * N)
+    assert _xg(r) == want and r["status"] == (1 if want else 0)
+    r = _grp(oracle, body, G, S, [0] * N, gb=False)
+    assert len(r["records"]) == 0 and r["status"] == 0
+
+
+def test_group_scope_read_of_a_value_held_all_along(oracle):
+    # group 0 writes 5, everyone reads after the barrier: a race unless the
+    # cell held 5 before the run; witness: all readers r0 = 0, r1 = 7 and all
+    # writers (0..3) -> (r1, w0) = (7, 0)
+    body = "if (wg == 0) { A[0] = 5; }\nbarrier;\nx = A[0];"
+    r = _grp(oracle, body, 2, 4, [0])
+    assert _xg(r) == [rec(XG, 0, 6, 7, 0, 8, 4, 12)] and r["status"] == 1
+    r = _grp(oracle, body, 2, 4, [5])
+    assert _xg(r) == [] and r["status"] == 0
+    # the same with the writer in group 1: (r0, w0) = (0, 4)
+    r = _grp(oracle, body.replace("wg == 0", "wg == 1"), 2, 4, [0])
+    assert _xg(r) == [rec(XG, 0, 6, 0, 4, 8, 4, 12)]
+    # writers 0..3 and 4..7 both: (r0, w1) = (0, 7), and a cross-group WW
+    r = _grp(oracle, "A[0] = wg;\nbarrier;\nif (wg == 0) { x = A[0]; }", 2, 4, [0])
+    assert _xg(r) == [rec(XG, 0, 4, 0, 7, 4, 8, 12), rec(XG, 0, 6, 0, 7, 4, 8, 12)]
+
+
+def test_group_scope_cross_round_writes(oracle):
+    # group 0 writes in round 0, group 1 in round 1: no race with a kernel-wide
+    # barrier, a cross-group race with a group-scoped one
+    body = "if (wg == 0) { A[0] = 1; }\nbarrier;\nif (wg == 1) { A[0] = 2; }"
+    r = _grp(oracle, body, 2, 4, [0], gb=False)
+    assert r["status"] == 0 and all(x[4] == 2 for x in r["records"])
+    r = _grp(oracle, body, 2, 4, [0])
+    assert _xg(r) == [rec(XG, 0, 4, 0, 7, 0, 8, 8)] and r["status"] == 1
+    np.testing.assert_array_equal(r["final"], [2])
+
+
+def test_group_scope_barrier_agreement_per_group(oracle):
+    # a barrier only group 0 takes: divergence kernel-wide, fine per group
+    r = _grp(oracle, "if (wg == 0) { barrier; A[0] = 3; }", 2, 4, [0], gb=False)
+    assert r["status"] == 4
+    r = _grp(oracle, "if (wg == 0) { barrier; A[0] = 3; }", 2, 4, [0])
+    assert r["status"] == 0 and r["n_intervals"] == 2
+    np.testing.assert_array_equal(r["final"], [3])
+    # groups at different barriers in one round
+    r = _grp(oracle, "if (wg == 0) { barrier; } else { barrier; }\nA[gtid] = 1;", 2, 4, [0] * 8)
+    assert r["status"] == 0 and r["n_intervals"] == 2 and len(r["records"]) == 0
+    # divergence inside each group: one record per stop point, wg = the group
+    r = _grp(oracle, "if (tid == 0) { barrier; }", 2, 4, [0])
+    np.testing.assert_array_equal(r["records"], [rec(0, 0, 18, 0, 0, 0, 0, 1, wg=0),
+                                                 rec(0, 0, 18, 1, XG, 0, 0, 3, wg=0),
+                                                 rec(0, 0, 18, 4, 0, 0, 0, 1, wg=1),
+                                                 rec(0, 0, 18, 5, XG, 0, 0, 3, wg=1)])
+    assert r["status"] == 4 and r["n_intervals"] == 1
+    # only group 1 diverges
+    r = _grp(oracle, "if (wg == 1) { if (tid < 2) { barrier; } }", 2, 4, [0])
+    np.testing.assert_array_equal(r["records"], [rec(0, 0, 18, 4, 0, 0, 0, 2, wg=1),
+                                                 rec(0, 0, 18, 6, XG, 0, 0, 2, wg=1)])
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_group_scope_with_one_group_is_kernel_scope(oracle, seed):
+    inst = W.tiny_kernel(seed) if seed % 2 else W.small_kernel(seed, group_size=16, n_stmts=12, n_barriers=2)
+    a = oracle.check(inst.src, 1, inst.group_size, inst.globals)
+    b = oracle.check(inst.src, 1, inst.group_size, inst.globals, group_barriers=True)
+    for k in ("status", "n_intervals", "n_access"):
+        assert a[k] == b[k]
+    np.testing.assert_array_equal(a["records"], b["records"])
+    np.testing.assert_array_equal(a["final"], b["final"])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_group_scope_private_slabs_are_kernel_scope(oracle, seed):
+    # each group touches only its own slab of A and takes the same barriers:
+    # no cross-group pair, so the report is the kernel-wide one
+    G, S = 3, 8
+    rng = np.random.default_rng([12, seed])
+    lines = []
+    for _ in range(10):
+        c = int(rng.integers(S))
+        if rng.random() < 0.2:
+            lines.append("barrier;")
+        elif rng.random() < 0.5:
+            lines.append(f"A[wg * {S} + (tid + {c}) % {S}] = tid + {int(rng.integers(3))};")
+        else:
+            lines.append(f"x = A[wg * {S} + (tid * 2 + {c}) % {S}];")
+    src = "kernel t(global int A[]) {\n" + "\n".join(lines) + "\n}\n"
+    A = rng.integers(0, 4, size=G * S).astype(np.int32)
+    a = oracle.check(src, G, S, [A])
+    b = oracle.check(src, G, S, [A], group_barriers=True)
+    np.testing.assert_array_equal(a["records"], b["records"])
+    np.testing.assert_array_equal(a["final"], b["final"])
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_group_scope_thread_order_does_not_matter(oracle, seed):
+    inst = W.group_kernel(seed)
+    a = oracle.check(inst.src, inst.groups, inst.group_size, inst.globals, group_barriers=True)
+    b = oracle.check(inst.src, inst.groups, inst.group_size, inst.globals, reverse=True, group_barriers=True)
+    np.testing.assert_array_equal(a["records"], b["records"])
+    np.testing.assert_array_equal(a["final"], b["final"])
+
+
+def test_group_scope_local_cells_stay_in_their_group(oracle):
+    # every group writes its own L[0] with its own value: no cross-group record
+    src = "kernel t(global int A[], local int L[1]) {\n L[0] = wg;\n barrier;\n A[gtid] = L[0];\n}\n"
+    r = oracle.check(src, 3, 4, [np.zeros(12, np.int32)], group_barriers=True)
+    assert _xg(r) == [] and r["status"] == 0
+    np.testing.assert_array_equal(r["final"], np.repeat(np.arange(3), 4))
