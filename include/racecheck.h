@@ -47,7 +47,7 @@ extern "C" {
 
 /* ---- report status (rc_report.status) */
 #define RC_RACE_FREE 0        /* no race, no error                                  */
-#define RC_RACY 1             /* at least one WW_RACE or RW_RACE record             */
+#define RC_RACY 1             /* at least one WW_RACE, RW_RACE, XG_WW_RACE or XG_RW_RACE record */
 #define RC_ERROR_OOB 2        /* out-of-bounds access (Sec. 5 Table 1 premise), no race */
 #define RC_ERROR_ASSERT 3     /* failed assert (Sec. 4 assert rule), no race        */
 #define RC_ERROR_DIVERGENCE 4 /* work-items stopped at different barriers, no race  */
@@ -56,12 +56,27 @@ extern "C" {
 #define RC_WW_RACE 1    /* two writers' last values in the interval differ       */
 #define RC_WW_BENIGN 2  /* >= 2 writers, all last values equal (benign, Sec. 1)  */
 #define RC_RW_RACE 3    /* a read observed o, another work-item wrote v != o     */
+/* cross-group classes (RC_GROUP_BARRIERS only): one global cell over the whole run */
+#define RC_XG_WW_RACE 4   /* writers in >= 2 work-groups, written values differ     */
+#define RC_XG_WW_BENIGN 5 /* writers in >= 2 work-groups, one value written         */
+#define RC_XG_RW_RACE 6   /* reader and writer in different work-groups, and the cell
+                             did not hold one value all along                        */
 #define RC_OOB 16       /* error: access outside 0 <= index < size(array)        */
 #define RC_ASSERT_FAIL 17
 #define RC_DIVERGENCE 18
 
 /* Options for rc_input.flags */
 #define RC_WANT_FINAL_MEMORY 1u /* fill rc_report.final_global            */
+/* Work-group-scoped barriers (OpenCL's barrier; the paper's is kernel-wide,
+ * Sec. 2 and the barrier-release rule of Sec. 4).  The run is the same
+ * lock-step schedule (round k runs every group's k-th interval), but barrier
+ * agreement holds per work-group: groups may wait at different barriers, and
+ * a group whose work-items all exited is finished while others go on.  As no
+ * barrier orders work-items of different groups, every global cell is also
+ * classified over the whole run between groups (RC_XG_* records).  Only
+ * rc_check and rc_search take it; rc_check_batch, rc_explore and
+ * rc_explore_pairs return RC_E_INVALID. */
+#define RC_GROUP_BARRIERS 2u
 
 typedef struct rc_bytecode rc_bytecode; /* opaque, library-owned */
 
@@ -104,9 +119,17 @@ typedef struct {
  *  ASSERT_FAIL: t_a = the work-item, t_b = assert ordinal (source order);
  *  DIVERGENCE: one record per stop point, t_a = smallest work-item stopped
  *    there, t_b = barrier ordinal (0xFFFFFFFF = exit), n_accesses = how many
- *    work-items stopped there.
- * Race records come first, sorted by (interval, space, wg, addr, cls);
- * error records follow, sorted by (interval, cls, t_a). */
+ *    work-items stopped there (RC_GROUP_BARRIERS: per diverging work-group,
+ *    wg = the group);
+ *  XG records (RC_GROUP_BARRIERS): interval = 0xFFFFFFFF (the whole run),
+ *    space 0, wg 0, addr = the global cell; XG_WW_*: (t_a, t_b) = smallest
+ *    and largest writer; XG_RW_RACE: from the smallest/largest reader r0/r1
+ *    and writer w0/w1, (r0, w0) if their groups differ, else (r0, w1) if
+ *    those differ, else (r1, w0); n_readers / n_writers = reads / writes of
+ *    the cell in the run, n_accesses = both.
+ * Race records come first, sorted by (interval, space, wg, addr, cls), then
+ * the XG records by (addr, cls); error records follow, sorted by (interval,
+ * cls, t_a). */
 typedef struct {
   uint32_t interval, space, wg, addr, cls, t_a, t_b, n_readers, n_writers, n_accesses;
 } rc_record;

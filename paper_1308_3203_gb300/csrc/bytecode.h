@@ -127,6 +127,7 @@ enum TStatus : uint32_t { TS_RUN = 0, TS_BARRIER = 1, TS_EXIT = 2, TS_DEAD = 3 }
 // Record classes (values shared with the public header).
 enum Cls : uint32_t {
   CLS_WW_RACE = 1, CLS_WW_BENIGN = 2, CLS_RW_RACE = 3,
+  CLS_XG_WW_RACE = 4, CLS_XG_WW_BENIGN = 5, CLS_XG_RW_RACE = 6,
   CLS_OOB = 16, CLS_ASSERT = 17, CLS_DIVERGENCE = 18
 };
 

@@ -69,6 +69,9 @@ struct InterpArgs {
   uint32_t *owner;                // shadow owner table (nullptr: not used)
   uint32_t tag;
   const uint32_t *proceed;        // non-null: the launch does nothing unless *proceed != 0
+  uint32_t *group_div;            // non-null: work-group-scoped barriers; counts diverging groups,
+                                  // whose DIVERGENCE records go to errs (needs 8 * (n_barriers + 1)
+                                  // bytes of dynamic shared memory after the own-write slots)
 };
 
 // ---- shadow owner table (shadow.cu)
@@ -179,6 +182,23 @@ constexpr uint32_t kConstCodeInsns = 4000;  // programs up to this size run from
 cudaError_t interp_upload_code(const Insn *host_code, uint32_t n_insn, cudaStream_t s);
 constexpr size_t kMaxSmemPerBlock = 227 * 1024;  // opt-in shared memory per CTA on sm_103
 size_t interp_max_dynamic_smem();  // valid after interp_configure()
+
+// ---- work-group-scoped barriers: cross-group classification (xgroup.cu)
+// One global cell over the whole run: smallest/largest writer and reader,
+// smallest/largest value written, smallest/largest value observed (seeded
+// with the cell's value before the run).  Counts (reads, writes) live apart.
+struct __align__(16) XgCell {
+  uint32_t wmin, wmax, rmin, rmax;
+  int32_t vmin, vmax, omin, omax;
+};
+void launch_xg_init(XgCell *xg, uint2 *cnt, const int32_t *snap, uint64_t GT, cudaStream_t s);
+// fold one interval's log (its warp slices) into the table
+void launch_xg_update(const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count, uint64_t GT,
+                      XgCell *xg, uint2 *cnt, cudaStream_t s);
+// records per cell (0-2), then the records at offs (exclusive scan of nrec)
+void launch_xg_count(const XgCell *xg, uint64_t GT, uint32_t S, uint32_t *nrec, cudaStream_t s);
+void launch_xg_emit(const XgCell *xg, const uint2 *cnt, uint64_t GT, uint32_t S, const uint32_t *nrec,
+                    const uint32_t *offs, OutRec *out, cudaStream_t s);
 
 // ---- batched checking (batch.cu)
 struct BatchDesc {  // one instance of a batch

@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
   // kernel reports one, and same-address atomics serialise in L2.  Each
   // warp folds its lanes by stop point; thread 0 folds the warps' entries.
   __shared__ uint32_t s_stop[32], s_min[32], s_cnt[32], s_acc[2][32];
+  const bool stopping = st == TS_BARRIER || (st == TS_EXIT && ran);
   {
     // access counters of the warp (global, local)
     const uint32_t sg = __reduce_add_sync(lanes, seq - nloc), sl = __reduce_add_sync(lanes, nloc);
@@ -226,7 +227,6 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
       s_acc[0][warp] = sg;
       s_acc[1][warp] = sl;
     }
-    const bool stopping = st == TS_BARRIER || (st == TS_EXIT && ran);
     const uint32_t smask = __ballot_sync(lanes, stopping);
     const uint32_t lane = tid & 31u;
     uint32_t stop = kNone, gmin = 0, gcnt = 0;
@@ -292,6 +292,35 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
   }
   if ((tid & 31u) == 0)
     A.warp_count[(uint64_t)blockIdx.x * A.warps_per_cta + warp] = wfill < A.warp_slice ? wfill : (uint32_t)A.warp_slice;
+  // Work-group-scoped barriers: the barrier-release rule within this group,
+  // from its own stop points (smallest work-item, count) gathered in the
+  // dynamic shared memory after the own-write slots (8 * (n_barriers + 1)
+  // bytes the host adds in this mode).
+  if (A.group_div) {  // uniform over the grid
+    uint32_t *grp_min = reinterpret_cast<uint32_t *>(owv + slots * S), *grp_cnt = grp_min + (A.n_barriers + 1);
+    for (uint32_t k = tid; k <= A.n_barriers; k += blockDim.x) {
+      grp_min[k] = kNone;
+      grp_cnt[k] = 0;
+    }
+    __syncthreads();
+    if (stopping) {
+      const uint32_t stop = st == TS_BARRIER ? (uint32_t)(kConst ? c_code[pc].y : __ldg(code + pc).y) : A.n_barriers;
+      atomicMin(&grp_min[stop], gtid);
+      atomicAdd(&grp_cnt[stop], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t points = 0;
+      for (uint32_t k = 0; k <= A.n_barriers; k++) points += grp_cnt[k] != 0;
+      if (points >= 2) {
+        for (uint32_t k = 0; k <= A.n_barriers; k++)
+          if (grp_cnt[k])
+            append_err(A, OutRec{A.interval, 0, wg, 0, CLS_DIVERGENCE, grp_min[k], k < A.n_barriers ? k : kNone, 0,
+                                 0, grp_cnt[k]});
+        atomicAdd(A.group_div, 1u);
+      }
+    }
+  }
 }
 
 __global__ void interval_gate_kernel(const uint32_t *flags, const unsigned long long *compacted,

@@ -100,7 +100,8 @@ struct HostBuf {
 struct Workspace {
   DevBuf code, mems, snap, regs, pc, st, ow, loga, logb, head, runidx, sum, khead, keyidx, nrec,
       recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff, sortscr, reckern,
-      bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround, big, bigres, nbig;
+      bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround, big, bigres, nbig, xg, xgcnt,
+      xgn, xgoff, xgtmp, xgout;
   HostBuf hstats, hrecs, hround, hdesc;
   cudaStream_t bstream = nullptr;
   cudaEvent_t sev[2] = {nullptr, nullptr};  // stats of an interval (by parity) reached the host
@@ -111,7 +112,7 @@ struct Workspace {
                       &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
                       &owcnt, &compact, &ctacnt, &ctaoff, &sortscr, &reckern, &bdesc, &bcode,
                       &bmems, &btask, &bkbase, &bkgt, &bklt, &berrk, &shared_acc, &bround, &big,
-                      &bigres, &nbig})
+                      &bigres, &nbig, &xg, &xgcnt, &xgn, &xgoff, &xgtmp, &xgout})
       b->release();
     epoch = 0;
   }
@@ -253,7 +254,7 @@ std::string batch_key(uint64_t tasks, uint64_t bound) {
 }
 
 // stats block layout (uint32 words)
-enum : uint32_t { ST_LOGCNT = 0, ST_ACC = 2, ST_FLAGS = 6, ST_ERRCNT = 7, ST_SCRATCH = 8, ST_STOPS = 10 };
+enum : uint32_t { ST_LOGCNT = 0, ST_ACC = 2, ST_FLAGS = 6, ST_ERRCNT = 7, ST_SCRATCH = 8, ST_GDIV = 10, ST_STOPS = 11 };
 
 uint32_t bitwidth(uint64_t v) {  // bits needed to represent values < v (v >= 1)
   uint32_t b = 0;
@@ -450,7 +451,8 @@ rc_report *make_report(const std::vector<OutRec> &races, const std::vector<OutRe
   rep->n_local = acc_l;
   rep->n_access = acc_g + acc_l;
   bool racy = false, div = false, as = false, oob = false;
-  for (const OutRec &x : races) racy |= x.cls == CLS_WW_RACE || x.cls == CLS_RW_RACE;
+  for (const OutRec &x : races)
+    racy |= x.cls == CLS_WW_RACE || x.cls == CLS_RW_RACE || x.cls == CLS_XG_WW_RACE || x.cls == CLS_XG_RW_RACE;
   for (const OutRec &x : errors) {
     div |= x.cls == CLS_DIVERGENCE;
     as |= x.cls == CLS_ASSERT;
@@ -518,9 +520,14 @@ rc_report *run_instance(const Instance &I) {
   }
   Layout L = make_layout(P, I.in, I.G);
   const uint64_t N = I.N;
+  // work-group-scoped barriers: per-group stop points in shared memory, a
+  // cross-group table over the global cells
+  const bool group = (I.in->flags & RC_GROUP_BARRIERS) != 0;
+  if (group && 2 * L.GT >= 0xFFFFFFFFull) throw Fail{RC_E_CAPACITY, "too many global cells for group scope"};
   // own-write slots in shared memory: as many as fit (up to 8) while keeping
   // at least two CTAs, or 2048 threads, per SM
-  const size_t base_smem = interp_smem_bytes((uint32_t)P.mems.size(), P.n_regs, I.S, 0);
+  const size_t base_smem = interp_smem_bytes((uint32_t)P.mems.size(), P.n_regs, I.S, 0) +
+                           (group ? 8ull * (P.n_barriers + 1) : 0);
   if (base_smem > interp_max_dynamic_smem())
     throw Fail{RC_E_INVALID, "kernel too large for shared memory at this group size"};
   const uint32_t ctas_per_sm = std::max<uint32_t>(2, 2048 / I.S);
@@ -594,6 +601,15 @@ rc_report *run_instance(const Instance &I) {
   if (!fixed_strategy) tuner_events();
   uint32_t *warp_count = W.ctacnt.get<uint32_t>(n_slices);
   uint32_t *ow_cnt = W.owcnt.get<uint32_t>(N);
+
+  XgCell *xg = nullptr;
+  uint2 *xgcnt = nullptr;
+  if (group) {
+    xg = W.xg.get<XgCell>(std::max<uint64_t>(L.GT, 1));
+    xgcnt = W.xgcnt.get<uint2>(std::max<uint64_t>(L.GT, 1));
+    launch_xg_init(xg, xgcnt, snap, L.GT, s);
+    CK(cudaGetLastError());
+  }
 
   InterpArgs base{};
   base.code = dcode;
@@ -670,6 +686,7 @@ rc_report *run_instance(const Instance &I) {
     a.owner = strategy == 2 ? owner : nullptr;
     a.tag = tag;
     a.proceed = gated ? gate + (k & 1) : nullptr;
+    a.group_div = group ? d + ST_GDIV : nullptr;
     if (timed) CK(cudaEventRecord(g_tev[0], s));
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
     launch_interp(a, I.G, smem, s);
@@ -681,6 +698,10 @@ rc_report *run_instance(const Instance &I) {
   };
   // the work after the interpreter that needs nothing from the host, then the stats read
   auto enqueue_post = [&](uint32_t k, int strategy, uint32_t tag) {
+    if (group) {
+      launch_xg_update(log, n_slices, slice, warp_count, L.GT, xg, xgcnt, s);
+      CK(cudaGetLastError());
+    }
     if (strategy == 2)
       shadow_launch(W, log, n_slices, slice, warp_count, N, snap, owner, tag, ow, ow_cnt, dbuf(k) + ST_SCRATCH, s);
     CK(cudaMemcpyAsync(hbuf(k), dbuf(k), stat_words * 4, cudaMemcpyDeviceToHost, s));
@@ -703,7 +724,7 @@ rc_report *run_instance(const Instance &I) {
     // on -- exactly the case in which the host would launch it unchanged.
     bool next_queued = false;
     uint32_t next_tag = 0;
-    if (strategy == 2 && !timed && !g_prof.on && !I.explore) {
+    if (strategy == 2 && !timed && !g_prof.on && !I.explore && !group) {
       const int ns = fixed_strategy ? fixed_strategy : g_tuner.choose(tkey);
       if (ns == 2 && (fixed_strategy || g_tuner.decided(tkey))) {
         next_tag = shadow_next_tag(W, s);
@@ -766,8 +787,15 @@ rc_report *run_instance(const Instance &I) {
       });
       errors.insert(errors.end(), e.begin(), e.end());
     }
-    // ---- barrier agreement (barrier-release rule of Sec. 4)
-    if (!barrier_agreement(interval, P.n_barriers, stop_min.data(), stop_cnt.data(), errors)) break;
+    // ---- barrier agreement (barrier-release rule of Sec. 4; group scope:
+    // each group checked it on the device and wrote its DIVERGENCE records)
+    if (group) {
+      bool any_barrier = false;
+      for (uint32_t k = 0; k < P.n_barriers; k++) any_barrier |= stop_cnt[k] != 0;
+      if (h[ST_GDIV] || !any_barrier) break;
+    } else if (!barrier_agreement(interval, P.n_barriers, stop_min.data(), stop_cnt.data(), errors)) {
+      break;
+    }
     if (next_queued && m == 0) {  // the gate opened: the next interval is already running
       tag = next_tag;
       enqueue_post(interval + 1, 2, tag);
@@ -782,6 +810,27 @@ rc_report *run_instance(const Instance &I) {
     enqueue_post(interval + 1, strategy, tag);
   }
 
+  if (group && L.GT) {  // cross-group records of the whole run, in cell order
+    uint32_t *nrec = W.xgn.get<uint32_t>(L.GT), *offs = W.xgoff.get<uint32_t>(L.GT);
+    uint32_t *tmp = W.xgtmp.get<uint32_t>(scan_tmp_words(L.GT));
+    launch_xg_count(xg, L.GT, I.S, nrec, s);
+    scan_exclusive(nrec, offs, L.GT, tmp, s);
+    CK(cudaGetLastError());
+    uint32_t tail[2] = {0, 0};
+    CK(cudaMemcpyAsync(&tail[0], offs + L.GT - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&tail[1], nrec + L.GT - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t total = (uint64_t)tail[0] + tail[1];
+    if (total) {
+      OutRec *out = W.xgout.get<OutRec>(total);
+      launch_xg_emit(xg, xgcnt, L.GT, I.S, nrec, offs, out, s);
+      CK(cudaGetLastError());
+      const size_t at = races.size();
+      races.resize(at + total);
+      CK(cudaMemcpyAsync(races.data() + at, out, total * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+  }
   return make_report(races, errors, interval + 1, tot_g, tot_l, L.GT,
                      (I.in->flags & RC_WANT_FINAL_MEMORY) ? snap : nullptr, s);
 }
@@ -1179,6 +1228,7 @@ int rc_explore(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, cons
   std::lock_guard<std::mutex> lk(g_mu);
   try {
     check_args(bc, groups, group_size, in);
+    if (in->flags & RC_GROUP_BARRIERS) throw Fail{RC_E_INVALID, "the explorer takes kernel-wide barriers only"};
     if ((uint64_t)groups * group_size > 16) throw Fail{RC_E_INVALID, "the explorer takes at most 16 work-items"};
     Layout L = make_layout(bc->prog, in, groups);
     if (L.keys > 4096) throw Fail{RC_E_INVALID, "the explorer takes at most 4096 cells"};
@@ -1213,6 +1263,7 @@ int rc_explore_pairs(const rc_bytecode *bc, uint32_t groups, uint32_t group_size
   std::lock_guard<std::mutex> lk(g_mu);
   try {
     check_args(bc, groups, group_size, in);
+    if (in->flags & RC_GROUP_BARRIERS) throw Fail{RC_E_INVALID, "the explorer takes kernel-wide barriers only"};
     const uint64_t N = (uint64_t)groups * group_size;
     if (N > 256) throw Fail{RC_E_INVALID, "the pair explorer takes at most 256 work-items"};
     Layout L = make_layout(bc->prog, in, groups);
@@ -1311,6 +1362,8 @@ int rc_check_batch(const rc_bytecode *const *bcs, const uint32_t *groups, const 
     items.reserve(n);
     for (size_t i = 0; i < n; i++) {
       check_args(bcs[i], groups[i], group_size[i], &inputs[i]);
+      if (inputs[i].flags & RC_GROUP_BARRIERS)
+        throw Fail{RC_E_INVALID, "batched checking takes kernel-wide barriers only"};
       items.push_back(plan_item(bcs[i], groups[i], group_size[i], &inputs[i]));
     }
     if (g_prof.on) prof_events();

@@ -19,10 +19,12 @@ LIB_PATH = os.path.join(_PKG, "libracecheck.so")
 RECORD_FIELDS = ("interval", "space", "wg", "addr", "cls", "t_a", "t_b",
                  "n_readers", "n_writers", "n_accesses")
 WW_RACE, WW_BENIGN, RW_RACE = 1, 2, 3
+XG_WW_RACE, XG_WW_BENIGN, XG_RW_RACE = 4, 5, 6
 OOB, ASSERT_FAIL, DIVERGENCE = 16, 17, 18
 RACE_FREE, RACY, ERROR_OOB, ERROR_ASSERT, ERROR_DIVERGENCE = 0, 1, 2, 3, 4
 STRATEGY_AUTO, STRATEGY_SORT, STRATEGY_SHADOW = 0, 1, 2
 RC_WANT_FINAL_MEMORY = 1
+RC_GROUP_BARRIERS = 2
 
 
 class RaceCheckError(RuntimeError):
@@ -251,11 +253,14 @@ def _report(p) -> dict:
 
 
 def check(bc: Bytecode, groups: int, group_size: int, globals_, stream=None,
-          want_final: bool = True) -> dict:
+          want_final: bool = True, group_barriers: bool = False) -> dict:
     """Check one instance.  ``globals_``: one int32 array per ``global``
-    declaration (numpy / host tensors, or contiguous int32 CUDA tensors)."""
+    declaration (numpy / host tensors, or contiguous int32 CUDA tensors).
+    ``group_barriers``: barriers are work-group scoped (RC_GROUP_BARRIERS)."""
     lib = load()
     inp, keep = _marshal(globals_, stream, want_final)
+    if group_barriers:
+        inp.flags |= RC_GROUP_BARRIERS
     out = ctypes.POINTER(_Report)()
     rc = lib.rc_check(bc.handle, groups, group_size, ctypes.byref(inp), ctypes.byref(out))
     del keep
