@@ -254,7 +254,11 @@ std::string batch_key(uint64_t tasks, uint64_t bound) {
 }
 
 // stats block layout (uint32 words)
-enum : uint32_t { ST_LOGCNT = 0, ST_ACC = 2, ST_FLAGS = 6, ST_ERRCNT = 7, ST_SCRATCH = 8, ST_GDIV = 10, ST_STOPS = 11 };
+enum : uint32_t { ST_LOGCNT = 0, ST_ACC = 2, ST_FLAGS = 6, ST_ERRCNT = 7, ST_SCRATCH = 8, ST_GDIV = 10, ST_STOPS = 12 };
+// The two stats buffers (by interval parity) sit stat_words = ST_STOPS +
+// 2 * (n_barriers + 1) words apart, and each holds 64-bit counters at ST_ACC
+// and ST_SCRATCH: ST_STOPS must be even so both buffers keep them 8-byte aligned.
+static_assert(ST_STOPS % 2 == 0 && ST_ACC % 2 == 0 && ST_SCRATCH % 2 == 0, "64-bit stats words need 8-byte alignment");
 
 uint32_t bitwidth(uint64_t v) {  // bits needed to represent values < v (v >= 1)
   uint32_t b = 0;
