@@ -221,9 +221,15 @@ int rc_sort_accesses_noalloc(const rc_access *in, rc_access *out, uint64_t n, ui
 /* Release every device workspace the library holds. */
 int rc_release_workspace(void);
 
-/* Classification strategy for later calls: 0 = automatic (size-based),
- * 1 = radix sort of the whole log + segmented scan, 2 = shadow-cell owner
- * table + sort of shared cells only.  Returns RC_E_INVALID for other values. */
+/* Classification strategy for later calls: 0 = automatic (resident when
+ * possible, else size-based), 1 = radix sort of the whole log + segmented
+ * scan, 2 = shadow-cell owner table + sort of shared cells only, both one
+ * launch sequence per barrier interval; 3 = resident: when every work-group
+ * fits on the GPU at once (and the group size is a multiple of 32, barriers
+ * are kernel-wide), one cooperative launch runs every interval with the
+ * owner table, committing in-kernel between grid-wide barriers, and the
+ * shared cells' records are sorted after the run; otherwise as 0.  Batches
+ * take 3 as 0.  Returns RC_E_INVALID for other values. */
 int rc_set_strategy(int strategy);
 
 /* Autotuner of the classification strategy (strategy 0 above).  Per size

@@ -229,7 +229,7 @@ __global__ void key_classify_kernel(const Summary *sum, uint64_t nsum, const uin
     return;
   }
   const CellResult c = classify_cell(sum, i, nsum);
-  if (c.wrote) a.snap[sum[i].key] = c.commit;
+  if (c.wrote && a.snap) a.snap[sum[i].key] = c.commit;  // no snapshot: commits were made already
   nrec[keyidx[i]] = (c.ww_cls ? 1u : 0u) + (c.rw_a != kNone ? 1u : 0u);
 }
 
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kBigThreads) big_classify_kernel(const Summary
       }
       c.wrote = nw > 0;
       c.commit = s_commit;
-      if (c.wrote) a.snap[key] = c.commit;
+      if (c.wrote && a.snap) a.snap[key] = c.commit;
       nrec[keyidx[b]] = (c.ww_cls ? 1u : 0u) + (c.rw_a != kNone ? 1u : 0u);
       a.bigres[q] = c;
     }

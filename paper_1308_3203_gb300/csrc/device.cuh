@@ -38,6 +38,8 @@ struct OutRec {  // report record, field order of rc_record
 };
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+// device-side overflow / error flags of a run (InterpArgs::flags)
+enum Flag : uint32_t { FLAG_LOG_FULL = 1, FLAG_OW_FULL = 2, FLAG_ERR_FULL = 4, FLAG_ACC_FULL = 16 };
 constexpr uint32_t kMetaRead = 1u << 30, kMetaWrite = 1u << 31, kMetaCount = (1u << 30) - 1;
 
 // Interpreter launch arguments (one launch runs one barrier interval for a
@@ -65,6 +67,7 @@ struct InterpArgs {
   uint32_t *stop_min, *stop_cnt;  // [n_barriers + 1], last slot = exit
   unsigned long long *acc;        // [0] global accesses, [1] local accesses
   uint32_t *flags;                // bit 0 log full, bit 1 own-write table full, bit 2 error log full
+                                  // (resident runs: two words, by interval parity)
   uint32_t *ow_count;             // [N] own-write entries per work-item
   uint32_t *owner;                // shadow owner table (nullptr: not used)
   uint32_t tag;
@@ -72,6 +75,16 @@ struct InterpArgs {
   uint32_t *group_div;            // non-null: work-group-scoped barriers; counts diverging groups,
                                   // whose DIVERGENCE records go to errs (needs 8 * (n_barriers + 1)
                                   // bytes of dynamic shared memory after the own-write slots)
+  // Resident runs (one cooperative launch runs every interval):
+  int32_t *commit;                // the snapshot the kernel commits to (== snap)
+  unsigned *grid_bar;             // [0] arrivals, [1] generation, [2] timed out (zero before the launch)
+  LogRec *acc_out;                // records of cells that need the exact sort, all intervals
+  unsigned long long *acc_total;  // records in acc_out
+  unsigned long long acc_cap;
+  unsigned long long *iv_off;     // [max_intervals + 1]: first record of each interval in acc_out
+  uint32_t max_intervals;
+  uint32_t *run_info;             // [0] intervals run, [1] owner-table tag of the last one
+  unsigned long long owner_words; // size of the owner table (cleared in-kernel when the tag wraps)
 };
 
 // ---- shadow owner table (shadow.cu)
@@ -107,7 +120,7 @@ __device__ __forceinline__ void shadow_claim_warp(uint32_t *owner, uint32_t mask
 // Cells that need the exact (sorted) classification: written by two or more
 // work-items, or written by one and read by another.
 __device__ __forceinline__ bool shadow_needs_exact(const uint32_t *owner, uint32_t key, uint32_t tag) {
-  const uint4 o = reinterpret_cast<const uint4 *>(owner)[key];
+  const uint4 o = __ldcg(reinterpret_cast<const uint4 *>(owner) + key);  // L2: written by other SMs' atomics
   if ((o.x >> 26) != tag) return false;  // nobody wrote the cell
   const uint32_t wmax = o.x & kIdMask, wmin = kIdMask - (o.y & kIdMask);
   if (wmax != wmin) return true;
@@ -121,9 +134,11 @@ __device__ __forceinline__ bool shadow_needs_exact(const uint32_t *owner, uint32
 // positions taken from *total.  Each lane holds four records in flight, so
 // the owner-table lookups overlap, and the warp takes its positions with one
 // atomic per 128 records; a work-item's records keep their slice order.
-// Called by all 32 lanes of a warp.
+// Positions at or past cap are not written and raise FLAG_ACC_FULL in
+// *flags.  Called by all 32 lanes of a warp.
 __device__ __forceinline__ void compact_slice(const uint4 *src, uint32_t n, const uint32_t *owner, uint32_t tag,
-                                              uint4 *out, unsigned long long *total, uint32_t lane) {
+                                              uint4 *out, unsigned long long *total, uint32_t lane,
+                                              unsigned long long cap = ~0ull, uint32_t *flags = nullptr) {
   const uint32_t lt = (1u << lane) - 1u;
   for (uint32_t base = 0; base < n; base += 128) {
     uint4 r[4];
@@ -148,7 +163,11 @@ __device__ __forceinline__ void compact_slice(const uint4 *src, uint32_t n, cons
     pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-      if (need[q]) out[pos + __popc(bal[q] & lt)] = r[q];
+      if (need[q]) {
+        const unsigned long long p = pos + __popc(bal[q] & lt);
+        if (p < cap) out[p] = r[q];
+        else atomicOr(flags, FLAG_ACC_FULL);
+      }
       pos += __popc(bal[q]);
     }
   }
@@ -166,10 +185,15 @@ void launch_densify(const LogRec *log, uint32_t n_slices, uint64_t slice, const 
 
 // Kernels launched by the library since load (every launch site adds one).
 void count_launch();
-
-enum Flag : uint32_t { FLAG_LOG_FULL = 1, FLAG_OW_FULL = 2, FLAG_ERR_FULL = 4 };
+// streaming multiprocessors of the current device
+int sm_count();
 
 void launch_interp(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStream_t s);
+// Resident run: every interval in one cooperative launch of n_groups CTAs
+// (all resident at once; see interp.cu).  blocks_per_sm: how many CTAs of
+// this shape fit on one SM.
+cudaError_t launch_interp_resident(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStream_t s);
+int interp_resident_blocks_per_sm(uint32_t n_insn, uint32_t S, size_t smem);
 // Gate of a speculatively queued interval: *proceed = 1 iff the previous
 // interval overflowed nothing, compacted no record for the exact sort, and
 // its work-items all stopped at one barrier (the run goes on unchanged).

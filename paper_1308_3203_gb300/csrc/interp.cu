@@ -12,6 +12,17 @@
 // (delayed visibility); shared writes go to the work-item's own-write table.
 // Every access is appended to the interval's log with one warp-aggregated
 // atomic per instruction and one 16-byte store per work-item.
+//
+// Resident runs: when every work-group of the instance fits on the GPU at
+// once, one cooperative launch runs all intervals.  Registers stay in shared
+// memory from one interval to the next; at each interval's end a bounded
+// grid-wide barrier separates the interpretation from the commit (each
+// work-item stores its last write to every cell whose highest writer it is,
+// per the owner table: the value the sort path commits) and the compaction
+// of the records that need the exact sort (appended for classification after
+// the run), and a second barrier separates those from the next interval.
+// Every CTA then reads the interval's stop points and flags and takes the
+// same decision to go on or stop.
 #include "device.cuh"
 #include "semantics.cuh"
 
@@ -22,10 +33,48 @@ __device__ __forceinline__ uint64_t bloom_bit(uint32_t key) {
   return 1ull << ((key * 2654435761u) >> 26);
 }
 
-__device__ __forceinline__ void append_err(const InterpArgs &A, const OutRec &r) {
+__device__ __forceinline__ void append_err(const InterpArgs &A, const OutRec &r, uint32_t *flags) {
   uint32_t pos = atomicAdd(A.err_count, 1u);
   if (pos < A.err_cap) A.errs[pos] = r;
-  else atomicOr(A.flags, FLAG_ERR_FULL);
+  else atomicOr(flags, FLAG_ERR_FULL);
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident, so the
+// wait ends unless a CTA left early).  Each thread fences its own writes,
+// thread 0 arrives and waits for the generation to move, bounded by about
+// twenty seconds of SM clock (an interval's work is bounded by the host's
+// choice of resident runs, see run_resident); a CTA that
+// gives up (or sees another give up) sets bar[2] and the call returns
+// false, and the kernel then ends.  bar: [0] arrivals, [1] generation,
+// [2] timed out.
+__device__ __noinline__ bool grid_sync(unsigned *bar, unsigned nblocks) {
+  __shared__ uint32_t s_ok;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = bar + 1;
+    const unsigned g = *gen;
+    uint32_t ok = 1;
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (*(volatile unsigned *)(bar + 2) || clock64() - t0 > 40000000000ll) {
+          atomicExch(bar + 2, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 // Bytecode of the instance being checked when it fits (the warp fetches
@@ -33,9 +82,9 @@ __device__ __forceinline__ void append_err(const InterpArgs &A, const OutRec &r)
 // broadcast case).  Larger programs are read from global memory.
 __constant__ uint4 c_code[kConstCodeInsns];
 
-template <bool kConst>
+template <bool kConst, bool kResident>
 __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
-  if (A.proceed && *A.proceed == 0) return;  // a closed gate: the host runs this interval later
+  if (!kResident && A.proceed && *A.proceed == 0) return;  // a closed gate: the host runs this interval later
   extern __shared__ __align__(16) unsigned char smem[];
   const uint4 *__restrict__ code = reinterpret_cast<const uint4 *>(A.code);
   MemInfo *mems = reinterpret_cast<MemInfo *>(smem);
@@ -66,16 +115,30 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
     rf[REG_GSIZE * S + tid] = (int32_t)S;
     rf[REG_NGROUPS * S + tid] = (int32_t)A.G;
   }
+  // resident: the current interval and owner-table tag live in shared
+  // memory (CTA-uniform), which keeps the interpreter's registers free
+  __shared__ uint32_t s_iv[2];
+  if (kResident && tid == 0) {
+    s_iv[0] = A.interval;
+    s_iv[1] = A.tag;
+  }
   __syncthreads();
 
 #define REG(i) rf[(uint32_t)(i) * S + tid]
-  uint32_t nloc = 0, seq = 0, nw = 0;  // global accesses = seq - nloc
-  uint64_t bloom = 0;
+#define INTERVAL (kResident ? s_iv[0] : A.interval)
+#define TAG (kResident ? s_iv[1] : A.tag)
   const uint32_t lbase = A.GT + wg * A.LT;
-  const bool ran = st == TS_RUN;
-  bool running = ran;
   const uint32_t wbase = tid & ~31u;
   const uint32_t lanes = S - wbase >= 32 ? 0xFFFFFFFFu : ((1u << (S - wbase)) - 1u);
+  const uint32_t nstops = A.n_barriers + 1;
+  for (;;) {  // resident: one pass per barrier interval; otherwise a single pass
+  // resident runs raise an interval's flags in the word of its parity, so a
+  // CTA still deciding on interval k never sees a flag of interval k + 1
+  uint32_t *const flags = A.flags + (kResident ? (INTERVAL & 1u) : 0u);
+  uint32_t nloc = 0, seq = 0, nw = 0;  // global accesses = seq - nloc
+  uint64_t bloom = 0;
+  const bool ran = st == TS_RUN;
+  bool running = ran;
 
   // Min-PC reconvergence: every iteration the warp executes the instruction
   // at the smallest bytecode pc among its running lanes; lanes that are
@@ -122,16 +185,16 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
       if (!act) continue;
       pc++;
       if (!inb) {  // ⊥: out of bounds, the work-item stops
-        OutRec e{A.interval, m.space, m.space ? wg : 0u, (uint32_t)idx, CLS_OOB, gtid,
+        OutRec e{INTERVAL, m.space, m.space ? wg : 0u, (uint32_t)idx, CLS_OOB, gtid,
                  ctl >> CTL_MEM_SHIFT, 0, 0, 0};
-        append_err(A, e);
+        append_err(A, e, flags);
         st = TS_DEAD;
         running = false;
         continue;
       }
       const uint32_t key = (m.space ? lbase : 0u) + m.base + (uint32_t)idx;
       // the lanes still here are exactly those in `logging`
-      if (A.owner) shadow_claim_warp(A.owner, logging, key, cls == CC_ST, A.tag, gtid, tid & 31u);
+      if (A.owner) shadow_claim_warp(A.owner, logging, key, cls == CC_ST, TAG, gtid, tid & 31u);
       // own-write table: the first `slots` distinct cells in shared memory, the rest in global
       const uint64_t bit = bloom_bit(key);
       int32_t slot = -1;
@@ -145,7 +208,7 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
       }
       int32_t v;
       if (cls == CC_LD) {
-        if (slot < 0) v = __ldg(A.snap + key);
+        if (slot < 0) v = kResident ? __ldcg(A.snap + key) : __ldg(A.snap + key);  // resident: committed in-kernel
         else if ((uint32_t)slot < slots) v = owv[slot * S + tid];
         else v = (int32_t)A.ow[(uint64_t)slot * A.ow_stride + lt].y;
         REG(d) = v;
@@ -164,13 +227,13 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
           nw++;
           bloom |= bit;
         } else {
-          atomicOr(A.flags, FLAG_OW_FULL);
+          atomicOr(flags, FLAG_OW_FULL);
         }
       }
       if (slot_pos < A.warp_slice)  // always true: the slice holds the static per-interval bound
         wlog[slot_pos] = make_uint4(key, gtid | (cls == CC_ST ? 0x80000000u : 0u), (uint32_t)v, seq);
       else
-        atomicOr(A.flags, FLAG_LOG_FULL);
+        atomicOr(flags, FLAG_LOG_FULL);
       seq++;
       nloc += m.space;
       continue;
@@ -195,8 +258,8 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
         break;
       case CC_ASSERT:
         if (x == 0) {  // ⊥
-          OutRec e{A.interval, 0, 0, 0, CLS_ASSERT, gtid, (uint32_t)imm, 0, 0, 0};
-          append_err(A, e);
+          OutRec e{INTERVAL, 0, 0, 0, CLS_ASSERT, gtid, (uint32_t)imm, 0, 0, 0};
+          append_err(A, e, flags);
           st = TS_DEAD;
           running = false;
         }
@@ -220,6 +283,9 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
   // warp folds its lanes by stop point; thread 0 folds the warps' entries.
   __shared__ uint32_t s_stop[32], s_min[32], s_cnt[32], s_acc[2][32];
   const bool stopping = st == TS_BARRIER || (st == TS_EXIT && ran);
+  // resident runs alternate two stop tables by interval parity
+  uint32_t *const stop_min = A.stop_min + (kResident ? (INTERVAL & 1u) * nstops : 0u);
+  uint32_t *const stop_cnt = A.stop_cnt + (kResident ? (INTERVAL & 1u) * nstops : 0u);
   {
     // access counters of the warp (global, local)
     const uint32_t sg = __reduce_add_sync(lanes, seq - nloc), sl = __reduce_add_sync(lanes, nloc);
@@ -235,8 +301,8 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
       const uint32_t g = __match_any_sync(smask, stop);
       if (g != smask) {  // several stop points in this warp: each group reports its own
         if (lane == (uint32_t)(__ffs(g) - 1)) {
-          atomicMin(&A.stop_min[stop], gtid);
-          atomicAdd(&A.stop_cnt[stop], (uint32_t)__popc(g));
+          atomicMin(&stop_min[stop], gtid);
+          atomicAdd(&stop_cnt[stop], (uint32_t)__popc(g));
         }
         stop = kNone;
       }
@@ -265,8 +331,8 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
       if (s_stop[w] == kNone) continue;
       if (s_stop[w] != cur) {
         if (cur != kNone) {
-          atomicMin(&A.stop_min[cur], cmin);
-          atomicAdd(&A.stop_cnt[cur], ccnt);
+          atomicMin(&stop_min[cur], cmin);
+          atomicAdd(&stop_cnt[cur], ccnt);
         }
         cur = s_stop[w];
         cmin = s_min[w];
@@ -275,9 +341,73 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
       ccnt += s_cnt[w];
     }
     if (cur != kNone) {
-      atomicMin(&A.stop_min[cur], cmin);
-      atomicAdd(&A.stop_cnt[cur], ccnt);
+      atomicMin(&stop_min[cur], cmin);
+      atomicAdd(&stop_cnt[cur], ccnt);
     }
+  }
+  if constexpr (kResident) {
+    // ---- the interval's end: commit and compaction between two grid barriers
+    if (!grid_sync(A.grid_bar, gridDim.x)) return;
+    const uint32_t interval = s_iv[0], tag = s_iv[1];
+    {
+      const uint32_t hi = (tag << 26) | gtid;  // owner word of the cell's highest writer
+      const uint32_t ns = nw < slots ? nw : slots;
+      for (uint32_t k = 0; k < nw; k++) {
+        uint32_t key;
+        int32_t v;
+        if (k < ns) {
+          key = owk[k * S + tid];
+          v = owv[k * S + tid];
+        } else {
+          const uint2 e = A.ow[(uint64_t)k * A.ow_stride + lt];
+          key = e.x;
+          v = (int32_t)e.y;
+        }
+        if (__ldcg(A.owner + 4ull * key) == hi) A.commit[key] = v;
+      }
+      compact_slice(wlog, wfill < A.warp_slice ? wfill : (uint32_t)A.warp_slice, A.owner, tag,
+                    reinterpret_cast<uint4 *>(A.acc_out), A.acc_total, tid & 31u, A.acc_cap, flags);
+      if (blockIdx.x == 0)  // the next interval's stop table starts empty
+        for (uint32_t k = tid; k < nstops; k += blockDim.x) {
+          A.stop_min[((interval + 1u) & 1u) * nstops + k] = kNone;
+          A.stop_cnt[((interval + 1u) & 1u) * nstops + k] = 0;
+        }
+    }
+    if (!grid_sync(A.grid_bar, gridDim.x)) return;
+    __shared__ uint32_t s_go;
+    if (tid == 0) {  // every CTA reads the same final values: one decision for the grid
+      uint32_t points = 0;
+      bool any_barrier = false;
+      for (uint32_t k = 0; k < nstops; k++)
+        if (__ldcg(stop_cnt + k)) {
+          points++;
+          any_barrier |= k < A.n_barriers;
+        }
+      const uint32_t fl = __ldcg(flags);
+      if (blockIdx.x == 0) {
+        A.iv_off[interval + 1] = __ldcg(A.acc_total);
+        A.run_info[0] = interval + 1;
+        A.run_info[1] = tag;
+      }
+      s_go = fl == 0 && points == 1 && any_barrier && interval + 1 < A.max_intervals;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    if (tag == 63) {  // the 6-bit tag wraps: clear the owner table first
+      const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+      for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid; i < A.owner_words; i += stride) A.owner[i] = 0;
+      if (!grid_sync(A.grid_bar, gridDim.x)) return;
+    }
+    if (tid == 0) {  // every thread read s_iv before the last __syncthreads
+      s_iv[0] = interval + 1;
+      s_iv[1] = tag == 63 ? 1u : tag + 1u;
+    }
+    __syncthreads();
+    if (st == TS_BARRIER) {  // resume after the barrier it waited at
+      st = TS_RUN;
+      pc += 1;
+    }
+    continue;
   }
   A.st[gtid] = st;
   A.pc[gtid] = pc;
@@ -316,12 +446,16 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
         for (uint32_t k = 0; k <= A.n_barriers; k++)
           if (grp_cnt[k])
             append_err(A, OutRec{A.interval, 0, wg, 0, CLS_DIVERGENCE, grp_min[k], k < A.n_barriers ? k : kNone, 0,
-                                 0, grp_cnt[k]});
+                                 0, grp_cnt[k]}, A.flags);
         atomicAdd(A.group_div, 1u);
       }
     }
   }
+  return;
+  }  // the interval loop
 }
+#undef INTERVAL
+#undef TAG
 
 __global__ void interval_gate_kernel(const uint32_t *flags, const unsigned long long *compacted,
                                      const uint32_t *stop_cnt, uint32_t n_barriers, uint32_t *proceed) {
@@ -350,15 +484,42 @@ size_t interp_smem_bytes(uint32_t n_mems, uint32_t n_regs, uint32_t S, uint32_t 
 size_t g_interp_static_smem = 0;
 
 cudaError_t interp_configure() {
-  cudaFuncAttributes fa, fb;
-  cudaError_t e = cudaFuncGetAttributes(&fa, interp_kernel<true>);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fb, interp_kernel<false>);
-  if (e != cudaSuccess) return e;
-  g_interp_static_smem = fa.sharedSizeBytes > fb.sharedSizeBytes ? fa.sharedSizeBytes : fb.sharedSizeBytes;
+  const void *fns[4] = {(const void *)interp_kernel<true, false>, (const void *)interp_kernel<false, false>,
+                        (const void *)interp_kernel<true, true>, (const void *)interp_kernel<false, true>};
+  size_t st = 0;
+  for (const void *f : fns) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    st = fa.sharedSizeBytes > st ? fa.sharedSizeBytes : st;
+  }
+  g_interp_static_smem = st;
   const int dyn = (int)(kMaxSmemPerBlock - g_interp_static_smem);
-  e = cudaFuncSetAttribute(interp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(interp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-  return e;
+  for (const void *f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int interp_resident_blocks_per_sm(uint32_t n_insn, uint32_t S, size_t smem) {
+  int nb = 0;
+  const void *f = n_insn <= kConstCodeInsns ? (const void *)interp_kernel<true, true>
+                                             : (const void *)interp_kernel<false, true>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, (int)S, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+cudaError_t launch_interp_resident(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStream_t s) {
+  count_launch();
+  InterpArgs arg = a;
+  void *params[] = {&arg};
+  const void *f = a.n_insn <= kConstCodeInsns ? (const void *)interp_kernel<true, true>
+                                               : (const void *)interp_kernel<false, true>;
+  return cudaLaunchCooperativeKernel(f, dim3(n_groups), dim3(a.S), params, smem, s);
 }
 
 size_t interp_max_dynamic_smem() { return kMaxSmemPerBlock - g_interp_static_smem; }
@@ -370,8 +531,8 @@ cudaError_t interp_upload_code(const Insn *host_code, uint32_t n_insn, cudaStrea
 
 void launch_interp(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStream_t s) {
   count_launch();
-  if (a.n_insn <= kConstCodeInsns) interp_kernel<true><<<n_groups, a.S, smem, s>>>(a);
-  else interp_kernel<false><<<n_groups, a.S, smem, s>>>(a);
+  if (a.n_insn <= kConstCodeInsns) interp_kernel<true, false><<<n_groups, a.S, smem, s>>>(a);
+  else interp_kernel<false, false><<<n_groups, a.S, smem, s>>>(a);
 }
 
 }  // namespace rc

@@ -101,7 +101,7 @@ struct Workspace {
   DevBuf code, mems, snap, regs, pc, st, ow, loga, logb, head, runidx, sum, khead, keyidx, nrec,
       recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff, sortscr, reckern,
       bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround, big, bigres, nbig, xg, xgcnt,
-      xgn, xgoff, xgtmp, xgout;
+      xgn, xgoff, xgtmp, xgout, rstat, rivoff;
   HostBuf hstats, hrecs, hround, hdesc;
   cudaStream_t bstream = nullptr;
   cudaEvent_t sev[2] = {nullptr, nullptr};  // stats of an interval (by parity) reached the host
@@ -112,7 +112,7 @@ struct Workspace {
                       &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
                       &owcnt, &compact, &ctacnt, &ctaoff, &sortscr, &reckern, &bdesc, &bcode,
                       &bmems, &btask, &bkbase, &bkgt, &bklt, &berrk, &shared_acc, &bround, &big,
-                      &bigres, &nbig, &xg, &xgcnt, &xgn, &xgoff, &xgtmp, &xgout})
+                      &bigres, &nbig, &xg, &xgcnt, &xgn, &xgoff, &xgtmp, &xgout, &rstat, &rivoff})
       b->release();
     epoch = 0;
   }
@@ -514,6 +514,144 @@ bool barrier_agreement(uint32_t interval, uint32_t n_barriers, const uint32_t *s
   return any_barrier;
 }
 
+// Resident run of one instance (see interp.cu): every interval in one
+// cooperative launch, then the exact classification of the compacted records
+// interval by interval (their commits were made in-kernel).  Returns null
+// when the instance cannot be resident or the run had to stop early (the
+// record buffer or the interval table filled up); the caller then checks it
+// interval by interval from the initial state.
+constexpr uint32_t kResidentMaxIntervals = 4096;
+
+rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const InterpArgs &base, size_t base_smem,
+                        uint32_t *owner, int32_t *snap, OutRec *errs, uint32_t *hscratch, cudaStream_t s) {
+  const Program &P = *I.p;
+  static int coop = -1;
+  if (coop < 0) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  }
+  if (!coop) return nullptr;
+  // intervals of bounded work only (the grid barrier's wait is bounded too)
+  if (P.max_access_per_interval > 4096) return nullptr;
+  // the most own-write slots that still let every work-group be resident
+  const int nsm = sm_count();
+  int slots = -1;
+  size_t smem = 0;
+  for (int sl = (int)std::min<uint64_t>(8, P.max_write_per_interval); sl >= 0; sl--) {
+    const size_t sm = base_smem + (size_t)sl * I.S * 8;
+    if (sm > interp_max_dynamic_smem()) continue;
+    if ((uint64_t)interp_resident_blocks_per_sm((uint32_t)P.code.size(), I.S, sm) * nsm >= I.G) {
+      slots = sl;
+      smem = sm;
+      break;
+    }
+  }
+  if (slots < 0) return nullptr;
+  const uint32_t nstops = P.n_barriers + 1;
+  // device words: [0..2] grid barrier (arrivals, generation, timed out), [3] error count,
+  // [4,5] intervals run / last tag, [6,7] flags by interval parity, [8,9] compacted records
+  // (u64), [10..13] access counters (2 x u64), then two stop tables (smallest work-item, count)
+  // by interval parity
+  enum : uint32_t { R_BAR = 0, R_ERRS = 3, R_INFO = 4, R_FLAGS = 6, R_TOTAL = 8, R_ACC = 10, R_STOPS = 14 };
+  const size_t words = R_STOPS + 4 * nstops;
+  uint32_t *d = W.rstat.get<uint32_t>(words);
+  CK(cudaMemsetAsync(d, 0, words * 4, s));
+  CK(cudaMemsetAsync(d + R_STOPS, 0xFF, 2 * nstops * 4, s));
+  unsigned long long *ivoff = W.rivoff.get<unsigned long long>(kResidentMaxIntervals + 1);
+  CK(cudaMemsetAsync(ivoff, 0, 8, s));
+  const uint64_t acc_cap = std::max<uint64_t>((uint64_t)base.warps_per_cta * I.G * base.warp_slice, 1u << 16);
+  LogRec *acc = W.logb.get<LogRec>(acc_cap);
+
+  InterpArgs a = base;
+  a.interval = 0;
+  a.tag = shadow_next_tag(W, s);
+  a.owner = owner;
+  a.ow_slots = (uint32_t)slots;
+  a.errs = errs;
+  a.err_count = d + R_ERRS;
+  a.stop_min = d + R_STOPS;
+  a.stop_cnt = d + R_STOPS + 2 * nstops;
+  a.acc = reinterpret_cast<unsigned long long *>(d + R_ACC);
+  a.flags = d + R_FLAGS;
+  a.proceed = nullptr;
+  a.group_div = nullptr;
+  a.commit = snap;
+  a.grid_bar = d + R_BAR;
+  a.acc_out = acc;
+  a.acc_total = reinterpret_cast<unsigned long long *>(d + R_TOTAL);
+  a.acc_cap = acc_cap;
+  a.iv_off = ivoff;
+  a.max_intervals = kResidentMaxIntervals;
+  a.run_info = d + R_INFO;
+  a.owner_words = 4ull * L.keys;
+  if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
+  const cudaError_t e = launch_interp_resident(a, I.G, smem, s);
+  if (e == cudaErrorCooperativeLaunchTooLarge) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  CK(e);
+  if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], s));
+  std::vector<uint32_t> h(words);
+  CK(cudaMemcpyAsync(h.data(), d, words * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  W.epoch = h[R_INFO + 1];  // the owner-table tag of the last interval
+  const uint32_t flags = h[R_FLAGS] | h[R_FLAGS + 1];
+  if (h[R_BAR + 2]) throw Fail{RC_E_TIMEOUT, "a grid barrier of the resident run timed out"};
+  if (flags & (FLAG_LOG_FULL | FLAG_OW_FULL | FLAG_ERR_FULL))
+    throw Fail{RC_E_CAPACITY, "interval log, own-write table or error log overflowed"};
+  if (flags & FLAG_ACC_FULL) return nullptr;
+  const uint32_t n_run = h[R_INFO];
+  if (n_run == 0) throw Fail{RC_E_CUDA, "the resident run reported no interval"};
+  const uint32_t last = n_run - 1;
+  const uint64_t acc_g = *reinterpret_cast<const uint64_t *>(&h[R_ACC]);
+  const uint64_t acc_l = *reinterpret_cast<const uint64_t *>(&h[R_ACC + 2]);
+  if (g_prof.on) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, g_prof.ev[0], g_prof.ev[1]));
+    g_prof.launches[0]++;
+    g_prof.ms[0] += ms;
+    g_prof.bytes[0] += 12.0 * (double)acc_g;
+  }
+  // error records by (interval, class, work-item); the divergence records of
+  // the last interval's barrier agreement follow
+  std::vector<OutRec> races, errors(std::min<uint32_t>(h[R_ERRS], base.err_cap));
+  if (!errors.empty()) {
+    CK(cudaMemcpyAsync(errors.data(), errs, errors.size() * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::sort(errors.begin(), errors.end(), [](const OutRec &x, const OutRec &y) {
+      return x.interval != y.interval ? x.interval < y.interval : x.cls != y.cls ? x.cls < y.cls : x.t_a < y.t_a;
+    });
+  }
+  const uint32_t *smin = &h[R_STOPS + (last & 1u) * nstops], *scnt = &h[R_STOPS + 2 * nstops + (last & 1u) * nstops];
+  if (barrier_agreement(last, P.n_barriers, smin, scnt, errors)) return nullptr;  // stopped at the interval cap
+  // the compacted records, classified interval by interval without commits
+  std::vector<unsigned long long> off(n_run + 1);
+  CK(cudaMemcpyAsync(off.data(), ivoff, (n_run + 1) * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (g_prof.on) CK(cudaEventRecord(g_prof.ev[2], s));
+  for (uint32_t k = 0; k < n_run; k++) {
+    const uint64_t m = off[k + 1] - off[k];
+    if (!m) continue;
+    uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(m), scan_tmp_words(m)));
+    LogRec *other = W.compact.get<LogRec>(m);
+    LogRec *sorted = sort_log(acc + off[k], other, m, bitwidth(I.N), bitwidth(L.keys) + bitwidth(I.N), tmp, s);
+    classify_run(W, sorted, m, k, L, nullptr, hscratch, races, s);
+  }
+  if (g_prof.on) {
+    CK(cudaEventRecord(g_prof.ev[3], s));
+    CK(cudaEventSynchronize(g_prof.ev[3]));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, g_prof.ev[2], g_prof.ev[3]));
+    g_prof.launches[1]++;
+    g_prof.ms[1] += ms;
+    g_prof.bytes[1] += 12.0 * (double)acc_g;
+  }
+  return make_report(races, errors, n_run, acc_g, acc_l, L.GT, (I.in->flags & RC_WANT_FINAL_MEMORY) ? snap : nullptr,
+                     s);
+}
+
 rc_report *run_instance(const Instance &I) {
   Workspace &W = g_ws;
   const Program &P = *I.p;
@@ -554,7 +692,9 @@ rc_report *run_instance(const Instance &I) {
   const uint64_t base_need = cap * sizeof(LogRec) * 2 + N * (capw * 8 + 4ull * P.n_regs + 12) + L.keys * 20;
   const bool sort_fits = base_need + cap * (sizeof(Summary) + 24) <= mem_budget;
   if (base_need > mem_budget) throw Fail{RC_E_CAPACITY, "instance needs more than 200 GiB of workspace"};
-  const int fixed_strategy = g_strategy ? g_strategy : (sort_fits ? 0 : 2);
+  // strategy 3 (resident) runs like 0 when the instance cannot be resident
+  const int asked = g_strategy == 3 ? 0 : g_strategy;
+  const int fixed_strategy = asked ? asked : (sort_fits ? 0 : 2);
   if (fixed_strategy == 1 && !sort_fits) throw Fail{RC_E_CAPACITY, "the sort path does not fit this instance"};
 
   // ---- set-up: program, memory snapshot, work-item state
@@ -565,7 +705,7 @@ rc_report *run_instance(const Instance &I) {
   if (!L.mems.empty())
     CK(cudaMemcpyAsync(dmems, L.mems.data(), L.mems.size() * sizeof(MemInfo), cudaMemcpyHostToDevice, s));
   int32_t *snap = W.snap.get<int32_t>(std::max<uint64_t>(L.keys, 1));
-  {
+  auto load_snapshot = [&]() {
     uint32_t gi = 0;
     for (size_t m = 0; m < P.mems.size(); m++) {
       if (P.mems[m].space != 0) continue;
@@ -578,7 +718,8 @@ rc_report *run_instance(const Instance &I) {
       gi++;
     }
     if (L.keys > L.GT) CK(cudaMemsetAsync(snap + L.GT, 0, (L.keys - L.GT) * 4, s));
-  }
+  };
+  load_snapshot();
   int32_t *regs = W.regs.get<int32_t>(N * P.n_regs);
   uint32_t *pc = W.pc.get<uint32_t>(N), *st = W.st.get<uint32_t>(N);
   CK(cudaMemsetAsync(regs, 0, N * P.n_regs * 4, s));
@@ -600,8 +741,11 @@ rc_report *run_instance(const Instance &I) {
     for (auto &e : W.sev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
   const std::string tkey = single_key(N, P.max_access_per_interval);
+  // resident run: every work-group on the GPU at once (one cooperative
+  // launch runs all intervals), shadow owner table, full warps
+  const bool resident_wanted = (g_strategy == 0 || g_strategy == 3) && !group && !I.explore && I.S % 32 == 0;
   uint32_t *owner = nullptr;
-  if (fixed_strategy != 1) owner = shadow_table(W, L.keys, s);
+  if (fixed_strategy != 1 || resident_wanted) owner = shadow_table(W, L.keys, s);
   if (!fixed_strategy) tuner_events();
   uint32_t *warp_count = W.ctacnt.get<uint32_t>(n_slices);
   uint32_t *ow_cnt = W.owcnt.get<uint32_t>(N);
@@ -641,6 +785,11 @@ rc_report *run_instance(const Instance &I) {
   base.warp_slice = slice;
   base.err_cap = err_cap;
   base.ow_count = ow_cnt;
+  if (resident_wanted) {
+    rc_report *r = run_resident(W, I, L, base, base_smem, owner, snap, errs2, hscratch, s);
+    if (r) return r;
+    load_snapshot();  // the resident run stopped early: start over interval by interval
+  }
   auto dbuf = [&](uint32_t k) { return dstats2 + (k & 1) * stat_words; };
   auto hbuf = [&](uint32_t k) { return hstats2 + (k & 1) * stat_words; };
   // one interval's interpreter launch (gated: runs only if gate[k & 1] is set on the device)
@@ -1385,7 +1534,7 @@ int rc_check_batch(const rc_bytecode *const *bcs, const uint32_t *groups, const 
       }
       if (cells >= (1ull << 31) || bytes > ((uint64_t)200 << 30)) throw Fail{RC_E_CAPACITY, "instance too large for a batch"};
       std::vector<BatchItem> sub(items.begin() + i, items.begin() + j);
-      run_batch(sub, static_cast<cudaStream_t>(inputs[i].cuda_stream), g_strategy, out + i);
+      run_batch(sub, static_cast<cudaStream_t>(inputs[i].cuda_stream), g_strategy == 3 ? 0 : g_strategy, out + i);
       i = j;
     }
     return RC_OK;
@@ -1459,7 +1608,7 @@ int rc_release_workspace(void) {
 }
 
 int rc_set_strategy(int strategy) {
-  if (strategy < 0 || strategy > 2) return RC_E_INVALID;
+  if (strategy < 0 || strategy > 3) return RC_E_INVALID;
   std::lock_guard<std::mutex> lk(g_mu);
   g_strategy = strategy;
   return RC_OK;

@@ -22,7 +22,7 @@ WW_RACE, WW_BENIGN, RW_RACE = 1, 2, 3
 XG_WW_RACE, XG_WW_BENIGN, XG_RW_RACE = 4, 5, 6
 OOB, ASSERT_FAIL, DIVERGENCE = 16, 17, 18
 RACE_FREE, RACY, ERROR_OOB, ERROR_ASSERT, ERROR_DIVERGENCE = 0, 1, 2, 3, 4
-STRATEGY_AUTO, STRATEGY_SORT, STRATEGY_SHADOW = 0, 1, 2
+STRATEGY_AUTO, STRATEGY_SORT, STRATEGY_SHADOW, STRATEGY_RESIDENT = 0, 1, 2, 3
 RC_WANT_FINAL_MEMORY = 1
 RC_GROUP_BARRIERS = 2
 

@@ -3,7 +3,8 @@
 Race reports are integer results, so the bar is bit-exact equality of every
 record (interval, cell, class, witness pair, counts), the status, the access
 counters and the final global memory.  Each case runs under both
-classification strategies (full sort, shadow owner table).
+classification strategies (full sort, shadow owner table) and the resident
+run (one cooperative launch for every interval) where the shape allows it.
 """
 import numpy as np
 import pytest
@@ -13,7 +14,7 @@ from tests.golden import golden
 
 pytestmark = pytest.mark.gpu
 
-STRATEGIES = (1, 2)
+STRATEGIES = (1, 2, 3)
 
 
 @pytest.fixture(scope="module")
