@@ -584,7 +584,9 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   a.iv_off = ivoff;
   a.max_intervals = kResidentMaxIntervals;
   a.run_info = d + R_INFO;
-  a.owner_words = 4ull * L.keys;
+  // all of it, as the host's wrap does: words past this instance's cells may hold
+  // tags of an earlier, larger instance that later calls would otherwise meet again
+  a.owner_words = W.owner.cap / 4;
   if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
   const cudaError_t e = launch_interp_resident(a, I.G, smem, s);
   if (e == cudaErrorCooperativeLaunchTooLarge) {

@@ -117,3 +117,19 @@ def test_interval_cap_falls_back(rc, oracle):
     src = "kernel t(global int A[]) {\n for i in 0 .. 4100 {\n  A[gtid] = i;\n  barrier;\n }\n}\n"
     want = check(rc, oracle, src, 1, 32, [np.zeros(32, np.int32)], "cap")
     assert want["n_intervals"] == 4101
+
+
+def test_owner_table_reuse_across_instances(rc, oracle):
+    """A small instance whose in-kernel tag wrap must also clear the owner-table
+    words of a larger instance checked before and after it."""
+    big = W.large_kernel(2, groups=8, group_size=64, global_len=8192, local_len=256)
+    wrap = ("kernel t(global int A[]) {\n for i in 0 .. 70 {\n  A[(gtid + i) % 64] = i;\n"
+            "  x = A[(gtid + i + 1) % 64];\n  barrier;\n }\n}\n")
+    wb = oracle.check(big.src, big.groups, big.group_size, big.globals)
+    ww = oracle.check(wrap, 2, 32, [np.zeros(64, np.int32)])
+    bb, bw = rc.compile(big.src), rc.compile(wrap)
+    rc.set_strategy(3)
+    for _ in range(4):
+        same(rc.check(bb, big.groups, big.group_size, big.globals), wb, "big")
+        same(rc.check(bw, 2, 32, [np.zeros(64, np.int32)]), ww, "wrap")
+    rc.set_strategy(0)
