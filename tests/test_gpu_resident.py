@@ -71,10 +71,9 @@ def test_large_kernels_reduced(rc, oracle, shape):
 
 
 def test_large_instance_full_size(rc, oracle):
-    """The bench workload (1024 x 256), sampled against the oracle's first 64
-    groups' records is not possible (global cells are shared), so the full
-    report is compared with the interval-by-interval GPU path instead, and
-    the reduced instance above carries the oracle comparison."""
+    """The bench workload (1024 x 256): the resident report equals the
+    interval-by-interval shadow path's, which test_gpu_parity compares with
+    the oracle at this size."""
     inst = W.large_kernel(0)
     bc = rc.compile(inst.src)
     rc.set_strategy(2)
