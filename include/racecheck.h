@@ -319,11 +319,12 @@ int rc_explore_pairs(const rc_bytecode *bc, uint32_t groups, uint32_t group_size
  *
  * A restricted, sound form of the paper's symbolic method (Sec. 5-6: two
  * renamed work-items i != j; Table 1's bounds premise).  Every register is
- * tracked as an affine form in tid and wg (optionally reduced modulo a
- * constant) by a fixpoint over the bytecode's control flow; branch
- * conditions are ignored, so every access counts as made by every
- * work-item.  For the launch shape groups x group_size and the input
- * lengths (global_init is not read), race_free = 1 means no two work-items
+ * tracked as an affine form in tid, wg and the counters of constant-trip
+ * loops (optionally reduced modulo a constant) by a fixpoint over the
+ * bytecode's control flow; a compare-and-branch on an affine function of
+ * tid (or wg) narrows the work-items that reach its then-region.  For the
+ * launch shape groups x group_size and the input lengths (global_init is
+ * not read), race_free = 1 means no two work-items
  * can make a conflicting pair of accesses in one barrier interval under any
  * schedule: every pair of accesses to one array (one a store) in a common
  * barrier region has disjoint index ranges, or the same index form that is
@@ -339,6 +340,17 @@ typedef struct {
   uint32_t n_unresolved;           /* pairs the pre-filter could not clear      */
 } rc_prove_result;
 int rc_prove(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in, rc_prove_result *out);
+
+/* Private accesses of the same analysis: flags[pc] = 1 (n_flags >= the
+ * bytecode's instruction count) for a load or store none of whose pairs with
+ * another work-item's access in a common barrier interval (one of the two a
+ * store, same array) can share a cell -- cleared by disjoint index ranges or
+ * a one-to-one index, not by equal values.  No other work-item touches the
+ * cells such an access touches in its interval, so it is never part of a
+ * race or benign record; the checker (owner-table and resident runs) skips
+ * logging them and claims only their stores.  *n_private = the count. */
+int rc_prove_private(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in,
+                     uint8_t *flags, uint32_t n_flags, uint32_t *n_private);
 
 /* ---- learned proposal: which candidate instances to check first
  *

@@ -86,6 +86,8 @@ enum : uint32_t {
   CTL_AM = 1u << 0,         // index = ((REG(a) + imm) & (2^k - 1)) + imm2
   CTL_K_SHIFT = 1,          // 5 bits: k
   CTL_MEM_SHIFT = 24,       // 8 bits: memory object of LD/ST/SIZE
+  CTL_PRIV = 1u << 6,       // LD/ST proven private for this launch shape (set per check, never compiled in):
+                            // no other work-item touches its cells in its interval -- not logged, loads claim nothing
   // DIVMOD bits
   DM_MOD = 1u << 0,
   DM_YIMM = 1u << 1,
@@ -119,6 +121,15 @@ struct Program {
   // loops make these finite); used to size logs so they cannot overflow
   uint64_t max_access_per_interval = 0;
   uint64_t max_write_per_interval = 0;
+  // the bytecode with CTL_PRIV set on the private accesses of the last launch
+  // shape and input lengths it was checked with (filled by the checker)
+  struct PrivateCode {
+    bool valid = false;
+    uint32_t G = 0, S = 0, n_private = 0;
+    std::vector<uint32_t> lens;
+    std::vector<Insn> code;
+  };
+  mutable PrivateCode priv;
 };
 
 // Thread status codes kept in device state.

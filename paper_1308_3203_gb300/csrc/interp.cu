@@ -179,7 +179,11 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
       const MemInfo m = mems[ctl >> CTL_MEM_SHIFT];  // (LD/ST class: operand bits)
       const int32_t idx = sem_index(x, imm, (int32_t)tgt, ctl);
       const bool inb = (uint32_t)idx < m.len;
-      const uint32_t logging = __ballot_sync(lanes, act && inb);
+      // a private access (warp-uniform: one instruction) is counted but not
+      // logged, and only its stores claim their cells (for the commit)
+      const bool priv = (ctl & CTL_PRIV) != 0;
+      const uint32_t performing = __ballot_sync(lanes, act && inb);
+      const uint32_t logging = priv ? 0u : performing;
       const uint32_t slot_pos = wfill + __popc(logging & lane_lt);
       wfill += __popc(logging);
       if (!act) continue;
@@ -193,8 +197,8 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
         continue;
       }
       const uint32_t key = (m.space ? lbase : 0u) + m.base + (uint32_t)idx;
-      // the lanes still here are exactly those in `logging`
-      if (A.owner) shadow_claim_warp(A.owner, logging, key, cls == CC_ST, TAG, gtid, tid & 31u);
+      // the lanes still here are exactly those in `performing`
+      if (A.owner && !(priv && cls == CC_LD)) shadow_claim_warp(A.owner, performing, key, cls == CC_ST, TAG, gtid, tid & 31u);
       // own-write table: the first `slots` distinct cells in shared memory, the rest in global
       const uint64_t bit = bloom_bit(key);
       int32_t slot = -1;
@@ -230,10 +234,12 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
           atomicOr(flags, FLAG_OW_FULL);
         }
       }
-      if (slot_pos < A.warp_slice)  // always true: the slice holds the static per-interval bound
-        wlog[slot_pos] = make_uint4(key, gtid | (cls == CC_ST ? 0x80000000u : 0u), (uint32_t)v, seq);
-      else
-        atomicOr(flags, FLAG_LOG_FULL);
+      if (!priv) {
+        if (slot_pos < A.warp_slice)  // always true: the slice holds the static per-interval bound
+          wlog[slot_pos] = make_uint4(key, gtid | (cls == CC_ST ? 0x80000000u : 0u), (uint32_t)v, seq);
+        else
+          atomicOr(flags, FLAG_LOG_FULL);
+      }
       seq++;
       nloc += m.space;
       continue;

@@ -528,23 +528,17 @@ struct Prover {
 }  // namespace
 }  // namespace rc
 
-extern "C" int rc_prove(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in,
-                        rc_prove_result *out) {
-  using namespace rc;
-  if (!bc || !in || !out || !groups || !group_size) {
-    set_last_error("null argument or empty launch");
-    return RC_E_INVALID;
-  }
-  const Program &p = bc->prog;
-  if (in->n_global != p.n_global || (in->n_global && !in->global_len)) {
-    set_last_error("input count differs from the kernel's global declarations");
-    return RC_E_INVALID;
-  }
-  std::vector<uint32_t> lens;
-  uint32_t gi = 0;
-  for (const MemDecl &m : p.mems)
-    lens.push_back(m.space == 0 ? (uint32_t)std::min<uint64_t>(in->global_len[gi++], 0x7FFFFFFFu)
-                                : (uint32_t)m.decl_len);
+namespace rc {
+
+// The pre-filter over one launch shape.  out: the verdicts (see rc_prove);
+// priv (if not null, one byte per instruction): 1 for a load or store every
+// pair of which, with any access by another work-item that may meet it in a
+// barrier interval (one of the two a store, same array), is cleared by
+// disjoint cells or a one-to-one index (or cannot happen): no other
+// work-item touches the cells it touches in its interval, so it can never
+// be part of a race or benign record.
+void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const std::vector<uint32_t> &lens,
+                   rc_prove_result *out, std::vector<uint8_t> *priv) {
   Prover pr(p, Shape(group_size, groups), lens);
   pr.dataflow();
   pr.regions();
@@ -573,6 +567,10 @@ extern "C" int rc_prove(const rc_bytecode *bc, uint32_t groups, uint32_t group_s
   out->race_free = 1;
   out->in_bounds = 1;
   out->first_pc_a = out->first_pc_b = 0xFFFFFFFFu;
+  if (priv) {
+    priv->assign(p.code.size(), 0);
+    for (const Acc &a : acc) (*priv)[a.pc] = 1;
+  }
   for (const Acc &a : acc) {  // Table 1 bounds premise
     if (a.box.empty()) continue;  // no work-item gets there
     const Range r = range_of(a.idx, a.box);
@@ -592,6 +590,7 @@ extern "C" int rc_prove(const rc_bytecode *bc, uint32_t groups, uint32_t group_s
         ok = ra.hi < rb.lo || rb.hi < ra.lo;                            // disjoint cells
         ok = ok || (a.idx == b.idx && injective(a.idx, h, a.local));  // only with itself
       }
+      if (!ok && priv) (*priv)[a.pc] = (*priv)[b.pc] = 0;  // the two may share a cell
       if (!ok && a.store && b.store && a.val.kind == AF::AFF && b.val.kind == AF::AFF) {
         const Range va = range_of(a.val, a.box), vb = range_of(b.val, b.box);
         ok = va.lo == va.hi && vb.lo == vb.hi && va.lo == vb.lo;  // every writer stores one value: benign
@@ -605,5 +604,57 @@ extern "C" int rc_prove(const rc_bytecode *bc, uint32_t groups, uint32_t group_s
         out->n_unresolved++;
       }
     }
+}
+
+// per memory object: the input's length (global) or the declared one (local)
+bool prove_lengths(const Program &p, const rc_input *in, std::vector<uint32_t> &lens) {
+  if (in->n_global != p.n_global || (in->n_global && !in->global_len)) return false;
+  lens.clear();
+  uint32_t gi = 0;
+  for (const MemDecl &m : p.mems)
+    lens.push_back(m.space == 0 ? (uint32_t)std::min<uint64_t>(in->global_len[gi++], 0x7FFFFFFFu)
+                                : (uint32_t)m.decl_len);
+  return true;
+}
+
+}  // namespace rc
+
+extern "C" int rc_prove(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in,
+                        rc_prove_result *out) {
+  using namespace rc;
+  if (!bc || !in || !out || !groups || !group_size) {
+    set_last_error("null argument or empty launch");
+    return RC_E_INVALID;
+  }
+  std::vector<uint32_t> lens;
+  if (!prove_lengths(bc->prog, in, lens)) {
+    set_last_error("input count differs from the kernel's global declarations");
+    return RC_E_INVALID;
+  }
+  prove_analyze(bc->prog, groups, group_size, lens, out, nullptr);
+  return RC_OK;
+}
+
+extern "C" int rc_prove_private(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in,
+                                uint8_t *flags, uint32_t n_flags, uint32_t *n_private) {
+  using namespace rc;
+  if (!bc || !in || !flags || !n_private || !groups || !group_size || n_flags < bc->prog.code.size()) {
+    set_last_error("null argument, empty launch or flag array shorter than the bytecode");
+    return RC_E_INVALID;
+  }
+  std::vector<uint32_t> lens;
+  if (!prove_lengths(bc->prog, in, lens)) {
+    set_last_error("input count differs from the kernel's global declarations");
+    return RC_E_INVALID;
+  }
+  rc_prove_result r;
+  std::vector<uint8_t> priv;
+  prove_analyze(bc->prog, groups, group_size, lens, &r, &priv);
+  uint32_t n = 0;
+  for (size_t k = 0; k < priv.size(); k++) {
+    flags[k] = priv[k];
+    n += priv[k];
+  }
+  *n_private = n;
   return RC_OK;
 }

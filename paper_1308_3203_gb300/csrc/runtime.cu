@@ -27,6 +27,11 @@
 #include "device.cuh"
 
 namespace rc {
+// The two-work-item pre-filter (prove.cpp).
+void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const std::vector<uint32_t> &lens,
+                   rc_prove_result *out, std::vector<uint8_t> *priv);
+bool prove_lengths(const Program &p, const rc_input *in, std::vector<uint32_t> &lens);
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -522,6 +527,31 @@ bool barrier_agreement(uint32_t interval, uint32_t n_barriers, const uint32_t *s
 // interval by interval from the initial state.
 constexpr uint32_t kResidentMaxIntervals = 4096;
 
+// The bytecode with CTL_PRIV on every access the pre-filter proves private
+// for this launch shape and these input lengths (cached on the program).
+const std::vector<Insn> &private_code(const Program &P, uint32_t G, uint32_t S, const rc_input *in) {
+  std::vector<uint32_t> lens;
+  if (!prove_lengths(P, in, lens)) throw Fail{RC_E_INVALID, "input count differs from the kernel's global declarations"};
+  Program::PrivateCode &c = P.priv;
+  if (!(c.valid && c.G == G && c.S == S && c.lens == lens)) {
+    rc_prove_result r;
+    std::vector<uint8_t> flags;
+    prove_analyze(P, G, S, lens, &r, &flags);
+    c.code = P.code;
+    c.n_private = 0;
+    for (size_t k = 0; k < flags.size(); k++)
+      if (flags[k]) {
+        c.code[k].ctl |= CTL_PRIV;
+        c.n_private++;
+      }
+    c.G = G;
+    c.S = S;
+    c.lens = lens;
+    c.valid = true;
+  }
+  return c.code;
+}
+
 rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const InterpArgs &base, size_t base_smem,
                         uint32_t *owner, int32_t *snap, OutRec *errs, uint32_t *hscratch, cudaStream_t s) {
   const Program &P = *I.p;
@@ -702,8 +732,21 @@ rc_report *run_instance(const Instance &I) {
   // ---- set-up: program, memory snapshot, work-item state
   Insn *dcode = W.code.get<Insn>(P.code.size());
   MemInfo *dmems = W.mems.get<MemInfo>(std::max<size_t>(L.mems.size(), 1));
-  CK(cudaMemcpyAsync(dcode, P.code.data(), P.code.size() * sizeof(Insn), cudaMemcpyHostToDevice, s));
-  CK(interp_upload_code(P.code.data(), (uint32_t)P.code.size(), s));
+  auto upload_code = [&](const std::vector<Insn> &c) {
+    CK(cudaMemcpyAsync(dcode, c.data(), c.size() * sizeof(Insn), cudaMemcpyHostToDevice, s));
+    CK(interp_upload_code(c.data(), (uint32_t)c.size(), s));
+  };
+  // resident run: every work-group on the GPU at once (one cooperative
+  // launch runs all intervals), shadow owner table, full warps
+  const bool resident_wanted = (g_strategy == 0 || g_strategy == 3) && !group && !I.explore && I.S % 32 == 0;
+  // accesses the pre-filter proves private skip the log wherever commits come
+  // from the owner table (resident runs, the shadow strategy throughout);
+  // the full sort commits from the log, the cross-group table and the
+  // explorer read it
+  const std::vector<Insn> *pcode =
+      !group && !I.explore && (resident_wanted || fixed_strategy == 2) ? &private_code(P, I.G, I.S, I.in) : nullptr;
+  const std::vector<Insn> &interval_code = pcode && fixed_strategy == 2 ? *pcode : P.code;
+  upload_code(pcode && resident_wanted ? *pcode : interval_code);
   if (!L.mems.empty())
     CK(cudaMemcpyAsync(dmems, L.mems.data(), L.mems.size() * sizeof(MemInfo), cudaMemcpyHostToDevice, s));
   int32_t *snap = W.snap.get<int32_t>(std::max<uint64_t>(L.keys, 1));
@@ -743,9 +786,6 @@ rc_report *run_instance(const Instance &I) {
     for (auto &e : W.sev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
   const std::string tkey = single_key(N, P.max_access_per_interval);
-  // resident run: every work-group on the GPU at once (one cooperative
-  // launch runs all intervals), shadow owner table, full warps
-  const bool resident_wanted = (g_strategy == 0 || g_strategy == 3) && !group && !I.explore && I.S % 32 == 0;
   uint32_t *owner = nullptr;
   if (fixed_strategy != 1 || resident_wanted) owner = shadow_table(W, L.keys, s);
   if (!fixed_strategy) tuner_events();
@@ -791,6 +831,7 @@ rc_report *run_instance(const Instance &I) {
     rc_report *r = run_resident(W, I, L, base, base_smem, owner, snap, errs2, hscratch, s);
     if (r) return r;
     load_snapshot();  // the resident run stopped early: start over interval by interval
+    if (pcode && &interval_code != pcode) upload_code(interval_code);
   }
   auto dbuf = [&](uint32_t k) { return dstats2 + (k & 1) * stat_words; };
   auto hbuf = [&](uint32_t k) { return hstats2 + (k & 1) * stat_words; };

@@ -153,7 +153,10 @@ def load() -> ctypes.CDLL:
         lib.rc_mlp_backend_error.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
         lib.rc_prove.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input),
                                  ctypes.POINTER(_ProveResult)]
-        for f in ("rc_prove", "rc_mlp_set_backend", "rc_mlp_backend_error", "rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
+        lib.rc_prove_private.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input),
+                                         ctypes.POINTER(ctypes.c_uint8), ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.c_uint32)]
+        for f in ("rc_prove", "rc_prove_private", "rc_mlp_set_backend", "rc_mlp_backend_error", "rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
                   "rc_mlp_forward", "rc_mlp_grad", "rc_mlp_train", "rc_search"):
             getattr(lib, f).restype = c_int
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
@@ -381,6 +384,22 @@ def prove(bc: Bytecode, groups: int, group_size: int, globals_) -> dict:
     return dict(race_free=bool(res.race_free), in_bounds=bool(res.in_bounds),
                 first=(res.first_pc_a, res.first_pc_b) if not res.race_free else None,
                 n_pairs=res.n_pairs, n_unresolved=res.n_unresolved)
+
+
+def prove_private(bc: Bytecode, groups: int, group_size: int, globals_) -> np.ndarray:
+    """Per bytecode instruction: 1 where the pre-filter proves the load or
+    store private for this launch shape (no other work-item touches its
+    cells in its interval), else 0 (host only)."""
+    inp, keep = _marshal(globals_, None, False)
+    n_insn = bc.info()["n_insn"]
+    flags = np.zeros(max(n_insn, 1), np.uint8)
+    n = ctypes.c_uint32()
+    rc = load().rc_prove_private(bc.handle, groups, group_size, ctypes.byref(inp),
+                                 flags.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n_insn, ctypes.byref(n))
+    del keep
+    if rc:
+        _raise(rc)
+    return flags[:n_insn]
 
 
 def explore(bc: Bytecode, groups: int, group_size: int, globals_, max_states: int = 0,

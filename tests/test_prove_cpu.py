@@ -176,3 +176,50 @@ def test_race_free_tiny_kernels_are_schedule_independent(rc, oracle):
         assert len(ex["finals"]) == 1
         n += 1
     assert n >= 10
+
+
+# ---------------------------------------------------------------- private accesses
+# (source, groups, group size, array lengths, expected private flags of the
+# kernel's loads/stores in program order)
+PRIVATE = [
+    ("kernel k(global int A[]) { A[gtid] = tid; }", 2, 8, (16,), [1]),
+    # the load reads the neighbour's cell the store writes: neither is private
+    ("kernel k(global int A[]) {\n A[gtid] = 1;\n x = A[gtid + 1];\n}", 1, 8, (9,), [0, 0]),
+    # one value written by everyone is benign, but not private
+    ("kernel k(global int A[]) { A[0] = 7; }", 1, 8, (1,), [0]),
+    # a barrier separates the two: both private
+    ("kernel k(global int A[]) {\n A[gtid] = 1;\n barrier;\n x = A[(gtid + 1) % 8];\n}", 1, 8, (8,), [1, 1]),
+    # reads of a cell nobody writes are private whoever reads them
+    ("kernel k(global int A[], global int B[]) {\n x = B[0];\n A[gtid] = x;\n}", 1, 8, (8, 1), [1, 1]),
+    # a loop's cells per work-item
+    ("kernel k(global int A[]) { for i in 0 .. 4 { A[gtid * 4 + i] = i; } }", 2, 8, (64,), [1]),
+    # local cells per group
+    ("kernel k(local int L[8]) {\n L[tid] = 1;\n x = L[tid];\n}", 4, 8, (), [1, 1]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(PRIVATE)))
+def test_private_accesses(rc, case):
+    src, G, S, lens, want = PRIVATE[case]
+    bc = rc.compile(src)
+    f = rc.prove_private(bc, G, S, zeros(*lens))
+    assert set(np.unique(f)) <= {0, 1}
+    assert int(f.sum()) == sum(want), (src, f)  # every case is all-private or all-shared
+
+
+def test_all_private_implies_race_free(rc):
+    """If every reached access is private, no pair can share a cell."""
+    for s in range(120):
+        inst = W.tiny_kernel(s) if s % 2 else W.small_kernel(s, group_size=8, n_stmts=12)
+        bc = rc.compile(inst.src)
+        f = rc.prove_private(bc, inst.groups, inst.group_size, inst.globals)
+        p = rc.prove(bc, inst.groups, inst.group_size, inst.globals)
+        if p["n_pairs"] and p["n_unresolved"]:
+            # an unresolved pair leaves both of its accesses shared
+            assert f[p["first"][0]] == 0 and f[p["first"][1]] == 0, inst.name
+
+
+def test_bench_kernel_has_private_accesses(rc):
+    inst = W.large_kernel(0)
+    f = rc.prove_private(rc.compile(inst.src), inst.groups, inst.group_size, inst.globals)
+    assert f.sum() >= 50
