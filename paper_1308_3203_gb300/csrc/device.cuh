@@ -179,6 +179,8 @@ void launch_shadow_compact(const LogRec *log, uint32_t n_slices, uint64_t slice,
                            cudaStream_t s);
 void launch_shadow_commit(const uint2 *ow, const uint32_t *ow_count, uint64_t N, uint32_t ow_stride,
                           const uint32_t *owner, uint32_t tag, int32_t *snap, cudaStream_t s);
+// n int32 values src -> dst by a kernel (src may be pinned host memory, read over the CPU-GPU link)
+void launch_copy_words(const int32_t *src, int32_t *dst, uint64_t n, cudaStream_t s);
 // copy the used part of every slice into one dense array (offs = exclusive scan of count)
 void launch_densify(const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
                     const uint32_t *offs, LogRec *out, cudaStream_t s);

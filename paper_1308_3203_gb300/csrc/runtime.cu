@@ -527,6 +527,19 @@ bool barrier_agreement(uint32_t interval, uint32_t n_barriers, const uint32_t *s
 // interval by interval from the initial state.
 constexpr uint32_t kResidentMaxIntervals = 4096;
 
+// A device-usable address of page-locked host memory (null for pageable or
+// device memory): kernels can read such memory directly over the CPU-GPU
+// link, which on this part outruns a copy-engine transfer.
+const int32_t *device_view(const int32_t *host) {
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (pa.type != cudaMemoryTypeHost || !pa.devicePointer) return nullptr;
+  return static_cast<const int32_t *>(pa.devicePointer);
+}
+
 // The bytecode with CTL_PRIV on every access the pre-filter proves private
 // for this launch shape and these input lengths (cached on the program).
 const std::vector<Insn> &private_code(const Program &P, uint32_t G, uint32_t S, const rc_input *in) {
@@ -757,8 +770,15 @@ rc_report *run_instance(const Instance &I) {
       const uint64_t len = I.in->global_len[gi];
       if (len) {
         if (!I.in->global_init || !I.in->global_init[gi]) throw Fail{RC_E_INVALID, "missing global input"};
-        CK(cudaMemcpyAsync(snap + L.mems[m].base, I.in->global_init[gi], len * 4,
-                           I.in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        const int32_t *src = I.in->global_init[gi];
+        const int32_t *mapped = I.in->on_device ? nullptr : device_view(src);
+        if (mapped) {  // pinned host memory: the SMs read it over the CPU-GPU link
+          launch_copy_words(mapped, snap + L.mems[m].base, len, s);
+          CK(cudaGetLastError());
+        } else {
+          CK(cudaMemcpyAsync(snap + L.mems[m].base, src, len * 4,
+                             I.in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        }
       }
       gi++;
     }

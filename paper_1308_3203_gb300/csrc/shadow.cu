@@ -8,6 +8,8 @@
 //  * the log records of every other written cell are compacted (one warp-
 //    aggregated atomic per warp and instruction) and classified exactly by
 //    the sort path.
+#include <algorithm>
+
 #include "device.cuh"
 
 namespace rc {
@@ -46,7 +48,31 @@ __global__ void densify_kernel(const LogRec *log, uint32_t n_slices, uint64_t sl
   for (uint32_t i = threadIdx.x & 31u; i < n; i += 32) dst[i] = src[i];
 }
 
+// n int32 values from src (pinned host memory the GPU reads over the
+// CPU-GPU link, or device memory) to dst; 16-byte loads and stores when
+// both are 16-byte aligned
+__global__ void copy_words_kernel(const int32_t *__restrict__ src, int32_t *__restrict__ dst, uint64_t n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
+    const uint64_t n4 = n / 4;
+    const int4 *s4 = reinterpret_cast<const int4 *>(src);
+    int4 *d4 = reinterpret_cast<int4 *>(dst);
+    for (uint64_t i = t; i < n4; i += stride) d4[i] = s4[i];
+    for (uint64_t i = n4 * 4 + t; i < n; i += stride) dst[i] = src[i];
+  } else {
+    for (uint64_t i = t; i < n; i += stride) dst[i] = src[i];
+  }
+}
+
 }  // namespace
+
+void launch_copy_words(const int32_t *src, int32_t *dst, uint64_t n, cudaStream_t s) {
+  if (!n) return;
+  count_launch();
+  const uint64_t blocks = std::min<uint64_t>((n / 4 + 255) / 256 + 1, (uint64_t)sm_count() * 16);
+  copy_words_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, n);
+}
 
 void launch_shadow_compact(const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
                            const uint32_t *owner, uint32_t tag, LogRec *out, unsigned long long *total,

@@ -234,3 +234,24 @@ def test_autotuner_decides_and_persists(rc, oracle, tmp_path):
         for g, w, i in zip(got, wants, insts):
             same(g, w, i.name)
     rc.autotune_config("")
+
+
+def test_pinned_host_inputs(rc, oracle):
+    """Page-locked host inputs are read by a copy kernel over the CPU-GPU
+    link; ragged lengths and offsets that are not 16-byte aligned."""
+    import torch
+    src = ("kernel t(global int A[], global int B[], global int C[]) {\n"
+           " x = A[gtid % 37];\n y = B[(gtid * 3) % 1001];\n C[gtid] = x + y;\n}\n")
+    arrs = [np.arange(37, dtype=np.int32) * 7, np.arange(1001, dtype=np.int32) - 500,
+            np.zeros(4 * 96, np.int32)]
+    want = oracle.check(src, 4, 96, arrs)
+    pinned = [torch.from_numpy(a.copy()).pin_memory() for a in arrs]
+    bc = rc.compile(src)
+    for s in STRATEGIES:
+        rc.set_strategy(s)
+        same(rc.check(bc, 4, 96, pinned), want, f"pinned strategy {s}")
+    rc.set_strategy(0)
+    inst = W.large_kernel(1, groups=8, group_size=256, global_len=65536, local_len=256)
+    want = oracle.check(inst.src, inst.groups, inst.group_size, inst.globals)
+    pinned = [torch.from_numpy(a.copy()).pin_memory() for a in inst.globals]
+    same(rc.check(rc.compile(inst.src), inst.groups, inst.group_size, pinned), want, "pinned large")
