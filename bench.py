@@ -39,17 +39,17 @@ SAMPLE_GROUPS = 96
 
 
 # DRAM traffic of interp_kernel per launch: dram__bytes_read.sum +
-# dram__bytes_write.sum, mean over the 108 interval launches of the command
-# below (the 18 speculative launches whose gate stayed closed, under 10 us
-# each, are left out: the bench's own timing runs with the gate off), from
+# dram__bytes_write.sum, mean over the 12 resident launches (one per check,
+# all nine intervals) of the command below, from
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
 #       --clock-control none -k regex:interp_kernel --csv \
 #       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --batch-kernels 0 --proposal-kernels 0
 # (profiles/interp_kernel_large_instance.md).  It holds only for the kernel
 # sources it was taken on; any change to them reports null.
-INTERP_TRAFFIC = {"sources_sha256": "eccde2675963590d6cbbb7ada022c1f3076cfd5b32dd827a06ce209a2c3975e4",
-                  "bytes_per_launch": 148552201}
-INTERP_SOURCES = ("paper_1308_3203_gb300/csrc/interp.cu", "paper_1308_3203_gb300/csrc/device.cuh")
+INTERP_TRAFFIC = {"sources_sha256": "8205570572642d34eb8705ad00cd1ed174848c0b221ac3fff1d3765fc9327fbb",
+                  "bytes_per_launch": 180778325}
+INTERP_SOURCES = ("paper_1308_3203_gb300/csrc/interp.cu", "paper_1308_3203_gb300/csrc/device.cuh",
+                  "paper_1308_3203_gb300/csrc/semantics.cuh", "paper_1308_3203_gb300/csrc/prove.cpp")
 
 
 def interp_sources_sha256() -> str:
@@ -342,10 +342,10 @@ def main():
     value = acc_all * args.steps / (t_max / 1e3)
     e2e = acc_all * args.steps / (ms_e2e / 1e3)
 
-    # roofline: the interpreter kernel (one launch per barrier interval).
-    # Algorithmic bytes: 12 B per global access logged (cell, work-item|rw,
-    # value) -- the log write half of the 24 B per global access the
-    # log/classify path must move.
+    # roofline: the interpreter kernel (resident runs: one launch per check,
+    # every interval; else one launch per interval).  Algorithmic bytes: 12 B
+    # per global access (cell, work-item|rw, value) -- the log write half of
+    # the 24 B per global access the log/classify path must move.
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     p0 = prof[0]
     interp_ms = p0["ms"] / max(p0["launches"], 1)
@@ -357,7 +357,8 @@ def main():
             "algorithmic_bytes_per_launch": p0["bytes"] / max(p0["launches"], 1),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s",
             "avg_launch_ms": interp_ms,
-            "classify_ms_per_interval": prof[1]["ms"] / max(prof[1]["launches"], 1),
+            "classify_ms_per_pass": prof[1]["ms"] / max(prof[1]["launches"], 1),
+            "classify_passes_per_check": prof[1]["launches"] / max(args.steps, 1),
             "classify_algorithmic_gbs": (prof[1]["bytes"] / max(prof[1]["ms"], 1e-9)) / 1e6}
 
     out = {
