@@ -221,6 +221,14 @@ int rc_sort_accesses_noalloc(const rc_access *in, rc_access *out, uint64_t n, ui
 /* Release every device workspace the library holds. */
 int rc_release_workspace(void);
 
+/* Diagnostic of the resident runs' failure path: one cooperative launch
+ * (a CTA per SM) waits at a grid-wide barrier that expects one arrival more
+ * than the launch has, so every wait must give up after limit_us (1 .. 10^7)
+ * microseconds.  *timed_out = 1 when the kernel reported the timeout (the
+ * status a resident run turns into RC_E_TIMEOUT); *seconds = host time of
+ * the call.  The device stays usable. */
+int rc_diag_grid_barrier(uint32_t limit_us, int32_t *timed_out, double *seconds);
+
 /* Classification strategy for later calls: 0 = automatic (resident when
  * possible, else size-based), 1 = radix sort of the whole log + segmented
  * scan, 2 = shadow-cell owner table + sort of shared cells only, both one

@@ -85,6 +85,7 @@ struct InterpArgs {
   uint32_t max_intervals;
   uint32_t *run_info;             // [0] intervals run, [1] owner-table tag of the last one
   unsigned long long owner_words; // size of the owner table (cleared in-kernel when the tag wraps)
+  unsigned long long barrier_limit_ns;  // longest wait at a grid barrier before the run gives up
 };
 
 // ---- shadow owner table (shadow.cu)
@@ -196,6 +197,8 @@ void launch_interp(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStre
 // this shape fit on one SM.
 cudaError_t launch_interp_resident(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStream_t s);
 int interp_resident_blocks_per_sm(uint32_t n_insn, uint32_t S, size_t smem);
+// Diagnostic cooperative launch whose grid barrier cannot complete (bar: 3 zeroed words).
+cudaError_t launch_grid_barrier_probe(unsigned *bar, uint32_t n_blocks, unsigned long long limit_ns, cudaStream_t s);
 // Gate of a speculatively queued interval: *proceed = 1 iff the previous
 // interval overflowed nothing, compacted no record for the exact sort, and
 // its work-items all stopped at one barrier (the run goes on unchanged).

@@ -39,15 +39,20 @@ __device__ __forceinline__ void append_err(const InterpArgs &A, const OutRec &r,
   else atomicOr(flags, FLAG_ERR_FULL);
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Grid-wide barrier of a cooperative launch (every CTA resident, so the
 // wait ends unless a CTA left early).  Each thread fences its own writes,
-// thread 0 arrives and waits for the generation to move, bounded by about
-// twenty seconds of SM clock (an interval's work is bounded by the host's
-// choice of resident runs, see run_resident); a CTA that
-// gives up (or sees another give up) sets bar[2] and the call returns
-// false, and the kernel then ends.  bar: [0] arrivals, [1] generation,
-// [2] timed out.
-__device__ __noinline__ bool grid_sync(unsigned *bar, unsigned nblocks) {
+// thread 0 arrives and waits for the generation to move, at most limit_ns
+// of wall-clock time (resident runs: 20 s; an interval's work is bounded by
+// the host's choice of resident runs, see run_resident); a CTA that gives up
+// (or sees another give up) sets bar[2] and the call returns false, and the
+// kernel then ends.  bar: [0] arrivals, [1] generation, [2] timed out.
+__device__ __noinline__ bool grid_sync(unsigned *bar, unsigned nblocks, unsigned long long limit_ns) {
   __shared__ uint32_t s_ok;
   __threadfence();
   __syncthreads();
@@ -60,9 +65,9 @@ __device__ __noinline__ bool grid_sync(unsigned *bar, unsigned nblocks) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
-      const long long t0 = clock64();
+      const unsigned long long t0 = global_ns();
       while (*gen == g) {
-        if (*(volatile unsigned *)(bar + 2) || clock64() - t0 > 40000000000ll) {
+        if (*(volatile unsigned *)(bar + 2) || global_ns() - t0 > limit_ns) {
           atomicExch(bar + 2, 1u);
           ok = 0;
           break;
@@ -353,7 +358,7 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
   }
   if constexpr (kResident) {
     // ---- the interval's end: commit and compaction between two grid barriers
-    if (!grid_sync(A.grid_bar, gridDim.x)) return;
+    if (!grid_sync(A.grid_bar, gridDim.x, A.barrier_limit_ns)) return;
     const uint32_t interval = s_iv[0], tag = s_iv[1];
     {
       const uint32_t hi = (tag << 26) | gtid;  // owner word of the cell's highest writer
@@ -379,7 +384,7 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
           A.stop_cnt[((interval + 1u) & 1u) * nstops + k] = 0;
         }
     }
-    if (!grid_sync(A.grid_bar, gridDim.x)) return;
+    if (!grid_sync(A.grid_bar, gridDim.x, A.barrier_limit_ns)) return;
     __shared__ uint32_t s_go;
     if (tid == 0) {  // every CTA reads the same final values: one decision for the grid
       uint32_t points = 0;
@@ -402,7 +407,7 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
     if (tag == 63) {  // the 6-bit tag wraps: clear the owner table first
       const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
       for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid; i < A.owner_words; i += stride) A.owner[i] = 0;
-      if (!grid_sync(A.grid_bar, gridDim.x)) return;
+      if (!grid_sync(A.grid_bar, gridDim.x, A.barrier_limit_ns)) return;
     }
     if (tid == 0) {  // every thread read s_iv before the last __syncthreads
       s_iv[0] = interval + 1;
@@ -463,6 +468,13 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
 #undef INTERVAL
 #undef TAG
 
+// Diagnostic: every CTA waits at a grid barrier that expects one more
+// arrival than the launch has, so each wait must run out after limit_ns and
+// report it in bar[2] (the status the host reads), leaving the context usable.
+__global__ void grid_barrier_probe_kernel(unsigned *bar, unsigned long long limit_ns) {
+  grid_sync(bar, gridDim.x + 1, limit_ns);
+}
+
 __global__ void interval_gate_kernel(const uint32_t *flags, const unsigned long long *compacted,
                                      const uint32_t *stop_cnt, uint32_t n_barriers, uint32_t *proceed) {
   uint32_t n_points = 0;
@@ -517,6 +529,14 @@ int interp_resident_blocks_per_sm(uint32_t n_insn, uint32_t S, size_t smem) {
     return 0;
   }
   return nb;
+}
+
+cudaError_t launch_grid_barrier_probe(unsigned *bar, uint32_t n_blocks, unsigned long long limit_ns,
+                                      cudaStream_t s) {
+  count_launch();
+  void *params[] = {&bar, &limit_ns};
+  return cudaLaunchCooperativeKernel((const void *)grid_barrier_probe_kernel, dim3(n_blocks), dim3(64), params, 0,
+                                     s);
 }
 
 cudaError_t launch_interp_resident(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStream_t s) {

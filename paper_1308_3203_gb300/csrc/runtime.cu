@@ -630,6 +630,7 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   // all of it, as the host's wrap does: words past this instance's cells may hold
   // tags of an earlier, larger instance that later calls would otherwise meet again
   a.owner_words = W.owner.cap / 4;
+  a.barrier_limit_ns = 20000000000ull;
   if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
   const cudaError_t e = launch_interp_resident(a, I.G, smem, s);
   if (e == cudaErrorCooperativeLaunchTooLarge) {
@@ -1658,6 +1659,28 @@ int rc_sort_accesses(const rc_access *in, rc_access *out, uint64_t n, uint32_t c
                   std::max<uint32_t>(item_bits, 1), cell_bits + std::max<uint32_t>(item_bits, 1), tmp, s);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
+    return RC_OK;
+  } catch (const Fail &f) {
+    return fail_code(f);
+  }
+}
+
+int rc_diag_grid_barrier(uint32_t limit_us, int32_t *timed_out, double *seconds) {
+  if (!timed_out || !seconds || limit_us == 0 || limit_us > 10000000u) return RC_E_INVALID;
+  std::lock_guard<std::mutex> lk(g_mu);
+  try {
+    int dev = 0, coop = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) throw Fail{RC_E_CUDA, "cooperative launches are not supported"};
+    unsigned *bar = g_ws.rstat.get<unsigned>(4);
+    CK(cudaMemset(bar, 0, 16));
+    const auto t0 = std::chrono::steady_clock::now();
+    CK(launch_grid_barrier_probe(bar, (uint32_t)sm_count(), (unsigned long long)limit_us * 1000ull, nullptr));
+    unsigned h[3] = {0, 0, 0};
+    CK(cudaMemcpy(h, bar, 12, cudaMemcpyDeviceToHost));
+    *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *timed_out = h[2] != 0;
     return RC_OK;
   } catch (const Fail &f) {
     return fail_code(f);

@@ -320,6 +320,20 @@ def release_workspace() -> None:
     load().rc_release_workspace()
 
 
+def diag_grid_barrier(limit_us: int) -> tuple:
+    """Run the resident runs' failure-path diagnostic: a grid barrier that
+    cannot complete must give up after limit_us; returns (timed_out, seconds)."""
+    lib = load()
+    lib.rc_diag_grid_barrier.argtypes = [ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_double)]
+    lib.rc_diag_grid_barrier.restype = ctypes.c_int
+    t, sec = ctypes.c_int32(), ctypes.c_double()
+    rc = lib.rc_diag_grid_barrier(limit_us, ctypes.byref(t), ctypes.byref(sec))
+    if rc:
+        _raise(rc)
+    return bool(t.value), sec.value
+
+
 def kernel_launches() -> int:
     """Kernels the library has launched since it was loaded."""
     return int(load().rc_kernel_launches())

@@ -132,3 +132,12 @@ def test_owner_table_reuse_across_instances(rc, oracle):
         same(rc.check(bb, big.groups, big.group_size, big.globals), wb, "big")
         same(rc.check(bw, 2, 32, [np.zeros(64, np.int32)]), ww, "wrap")
     rc.set_strategy(0)
+
+
+def test_grid_barrier_gives_up_and_reports(rc, oracle):
+    """A grid barrier that cannot complete (one arrival more than the launch
+    has) gives up after its limit and reports it; the device stays usable."""
+    timed_out, seconds = rc.diag_grid_barrier(2000)
+    assert timed_out and seconds < 5.0
+    inst = W.small_kernel(7)
+    check(rc, oracle, inst.src, inst.groups, inst.group_size, inst.globals, "after the probe")
