@@ -641,6 +641,10 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], s));
   std::vector<uint32_t> h(words);
   CK(cudaMemcpyAsync(h.data(), d, words * 4, cudaMemcpyDeviceToHost, s));
+  // the first record offsets come back with the same synchronisation
+  constexpr uint32_t kOffHead = 64;
+  std::vector<unsigned long long> off(kOffHead);
+  CK(cudaMemcpyAsync(off.data(), ivoff, kOffHead * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   W.epoch = h[R_INFO + 1];  // the owner-table tag of the last interval
   const uint32_t flags = h[R_FLAGS] | h[R_FLAGS + 1];
@@ -673,9 +677,11 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   const uint32_t *smin = &h[R_STOPS + (last & 1u) * nstops], *scnt = &h[R_STOPS + 2 * nstops + (last & 1u) * nstops];
   if (barrier_agreement(last, P.n_barriers, smin, scnt, errors)) return nullptr;  // stopped at the interval cap
   // the compacted records, classified interval by interval without commits
-  std::vector<unsigned long long> off(n_run + 1);
-  CK(cudaMemcpyAsync(off.data(), ivoff, (n_run + 1) * 8, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  if (n_run + 1 > kOffHead) {
+    off.resize(n_run + 1);
+    CK(cudaMemcpyAsync(off.data(), ivoff, (n_run + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
   if (g_prof.on) CK(cudaEventRecord(g_prof.ev[2], s));
   for (uint32_t k = 0; k < n_run; k++) {
     const uint64_t m = off[k + 1] - off[k];
