@@ -77,7 +77,7 @@ struct InterpArgs {
                                   // bytes of dynamic shared memory after the own-write slots)
   // Resident runs (one cooperative launch runs every interval):
   int32_t *commit;                // the snapshot the kernel commits to (== snap)
-  unsigned *grid_bar;             // [0] arrivals, [1] generation, [2] timed out (zero before the launch)
+  unsigned *grid_bar;             // kGridBarWords, zero before the launch ([2]: timed out; see interp.cu)
   LogRec *acc_out;                // records of cells that need the exact sort, all intervals
   unsigned long long *acc_total;  // records in acc_out
   unsigned long long acc_cap;
@@ -197,7 +197,8 @@ void launch_interp(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStre
 // this shape fit on one SM.
 cudaError_t launch_interp_resident(const InterpArgs &a, uint32_t n_groups, size_t smem, cudaStream_t s);
 int interp_resident_blocks_per_sm(uint32_t n_insn, uint32_t S, size_t smem);
-// Diagnostic cooperative launch whose grid barrier cannot complete (bar: 3 zeroed words).
+constexpr uint32_t kGridBarWords = 32 + 32 * 32;  // grid barrier: top counter, generation, flag, 32 sub-counters
+// Diagnostic cooperative launch whose grid barrier cannot complete (bar: kGridBarWords zeroed words).
 cudaError_t launch_grid_barrier_probe(unsigned *bar, uint32_t n_blocks, unsigned long long limit_ns, cudaStream_t s);
 // Gate of a speculatively queued interval: *proceed = 1 iff the previous
 // interval overflowed nothing, compacted no record for the exact sort, and

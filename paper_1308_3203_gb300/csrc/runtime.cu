@@ -106,7 +106,7 @@ struct Workspace {
   DevBuf code, mems, snap, regs, pc, st, ow, loga, logb, head, runidx, sum, khead, keyidx, nrec,
       recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff, sortscr, reckern,
       bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround, big, bigres, nbig, xg, xgcnt,
-      xgn, xgoff, xgtmp, xgout, rstat, rivoff;
+      xgn, xgoff, xgtmp, xgout, rstat, rivoff, rbar;
   HostBuf hstats, hrecs, hround, hdesc;
   cudaStream_t bstream = nullptr;
   cudaEvent_t sev[2] = {nullptr, nullptr};  // stats of an interval (by parity) reached the host
@@ -117,7 +117,7 @@ struct Workspace {
                       &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
                       &owcnt, &compact, &ctacnt, &ctaoff, &sortscr, &reckern, &bdesc, &bcode,
                       &bmems, &btask, &bkbase, &bkgt, &bklt, &berrk, &shared_acc, &bround, &big,
-                      &bigres, &nbig, &xg, &xgcnt, &xgn, &xgoff, &xgtmp, &xgout, &rstat, &rivoff})
+                      &bigres, &nbig, &xg, &xgcnt, &xgn, &xgoff, &xgtmp, &xgout, &rstat, &rivoff, &rbar})
       b->release();
     epoch = 0;
   }
@@ -592,7 +592,7 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   }
   if (slots < 0) return nullptr;
   const uint32_t nstops = P.n_barriers + 1;
-  // device words: [0..2] grid barrier (arrivals, generation, timed out), [3] error count,
+  // device words: [0..2] unused, [3] error count,
   // [4,5] intervals run / last tag, [6,7] flags by interval parity, [8,9] compacted records
   // (u64), [10..13] access counters (2 x u64), then two stop tables (smallest work-item, count)
   // by interval parity
@@ -600,6 +600,8 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   const size_t words = R_STOPS + 4 * nstops;
   uint32_t *d = W.rstat.get<uint32_t>(words);
   CK(cudaMemsetAsync(d, 0, words * 4, s));
+  unsigned *bar = W.rbar.get<unsigned>(kGridBarWords);
+  CK(cudaMemsetAsync(bar, 0, kGridBarWords * 4, s));
   CK(cudaMemsetAsync(d + R_STOPS, 0xFF, 2 * nstops * 4, s));
   unsigned long long *ivoff = W.rivoff.get<unsigned long long>(kResidentMaxIntervals + 1);
   CK(cudaMemsetAsync(ivoff, 0, 8, s));
@@ -620,7 +622,7 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   a.proceed = nullptr;
   a.group_div = nullptr;
   a.commit = snap;
-  a.grid_bar = d + R_BAR;
+  a.grid_bar = bar;
   a.acc_out = acc;
   a.acc_total = reinterpret_cast<unsigned long long *>(d + R_TOTAL);
   a.acc_cap = acc_cap;
@@ -641,6 +643,7 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], s));
   std::vector<uint32_t> h(words);
   CK(cudaMemcpyAsync(h.data(), d, words * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&h[R_BAR + 2], bar + 2, 4, cudaMemcpyDeviceToHost, s));  // the barrier's timeout word
   // the first record offsets come back with the same synchronisation
   constexpr uint32_t kOffHead = 64;
   std::vector<unsigned long long> off(kOffHead);
@@ -1679,8 +1682,8 @@ int rc_diag_grid_barrier(uint32_t limit_us, int32_t *timed_out, double *seconds)
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) throw Fail{RC_E_CUDA, "cooperative launches are not supported"};
-    unsigned *bar = g_ws.rstat.get<unsigned>(4);
-    CK(cudaMemset(bar, 0, 16));
+    unsigned *bar = g_ws.rbar.get<unsigned>(kGridBarWords);
+    CK(cudaMemset(bar, 0, kGridBarWords * 4));
     const auto t0 = std::chrono::steady_clock::now();
     CK(launch_grid_barrier_probe(bar, (uint32_t)sm_count(), (unsigned long long)limit_us * 1000ull, nullptr));
     unsigned h[3] = {0, 0, 0};
