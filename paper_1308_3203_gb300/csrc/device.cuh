@@ -306,14 +306,11 @@ ExploreResult explore_interval(const ExploreInput &in, uint64_t max_states, cuda
 size_t scan_tmp_words(uint64_t n);
 void scan_exclusive(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp, cudaStream_t s);
 // stable LSD radix sort of n log records by (key << gbits | gtid) over
-// `bits` key bits (8- or 11-bit digits, whichever takes fewer passes); tmp
-// holds sort_tmp_words(n); returns the buffer holding the result (a or b)
+// `bits` key bits; returns the buffer holding the result (a or b)
 size_t sort_tmp_words(uint64_t n);
 LogRec *sort_log(LogRec *a, LogRec *b, uint64_t n, uint32_t gbits, uint32_t bits, uint32_t *tmp,
                  cudaStream_t s);
-// the same order from `in` (not written) into `out`, ping-ponging through
-// scratch (n records), 8-bit digits only: tmp holds sort_tmp_words_narrow(n)
-size_t sort_tmp_words_narrow(uint64_t n);
+// same sort from `in` (not written) into `out`, ping-ponging through scratch (n records)
 void sort_log_into(const LogRec *in, LogRec *out, LogRec *scratch, uint64_t n, uint32_t gbits, uint32_t bits,
                    uint32_t *tmp, cudaStream_t s);
 

@@ -40,7 +40,7 @@ extern "C" int rc_sort_accesses_noalloc(const rc_access *in, rc_access *out, uin
   if (n == 0) return RC_OK;
   if (!in || !out || item_bits > 31 || cell_bits + item_bits > 58) return RC_E_INVALID;
   if (n > kNoAllocMaxRecords) return RC_E_CAPACITY;  // beyond the fixed scratch array
-  if (sort_tmp_words_narrow(n) > kNoAllocTmpWords) return RC_E_CAPACITY;
+  if (sort_tmp_words(n) > kNoAllocTmpWords) return RC_E_CAPACITY;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RC_E_CUDA;
   void *base = nullptr;

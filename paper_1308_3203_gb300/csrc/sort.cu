@@ -4,8 +4,8 @@
 // Scan: tiles of 2048 uint32 (256 threads x 8); per-tile sums are scanned
 // recursively, then each tile is scanned and offset.
 //
-// Radix sort: 8- or 11-bit digits of the composite key (key << gbits | gtid),
-// least significant first.  Per pass: (1) per-tile digit histograms, written digit-
+// Radix sort: 8-bit digits of the composite key (key << gbits | gtid), least
+// significant first.  Per pass: (1) per-tile digit histograms, written digit-
 // major so that (2) one exclusive scan gives every (digit, tile) its output
 // offset, (3) each tile ranks its records stably - warps own contiguous
 // 256-record segments, ranks within a warp come from __match_any_sync, and
@@ -80,38 +80,33 @@ __global__ void __launch_bounds__(kThreads) tile_scan_kernel(const uint32_t *in,
   }
 }
 
-template <uint32_t kBins>
 __device__ __forceinline__ uint32_t digit_of(const LogRec &r, uint32_t gbits, uint32_t shift) {
   const uint64_t k = ((uint64_t)r.key << gbits) | (uint64_t)(r.tw & 0x7FFFFFFFu);
-  return (uint32_t)(k >> shift) & (kBins - 1u);
+  return (uint32_t)(k >> shift) & 0xFFu;
 }
 
-template <uint32_t kBins>
 __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const LogRec *in, uint64_t n, uint32_t gbits,
                                                               uint32_t shift, uint32_t *hist,
                                                               uint32_t ntiles) {
-  __shared__ uint32_t h[kBins];
-  for (uint32_t d = threadIdx.x; d < kBins; d += kThreads) h[d] = 0;
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
   __syncthreads();
   const uint64_t base = (uint64_t)blockIdx.x * kTile;
 #pragma unroll
   for (int i = 0; i < kItems; i++) {
     const uint64_t k = base + (uint64_t)i * kThreads + threadIdx.x;
-    if (k < n) atomicAdd(&h[digit_of<kBins>(in[k], gbits, shift)], 1u);
+    if (k < n) atomicAdd(&h[digit_of(in[k], gbits, shift)], 1u);
   }
   __syncthreads();
-  for (uint32_t d = threadIdx.x; d < kBins; d += kThreads) hist[(uint64_t)d * ntiles + blockIdx.x] = h[d];
+  hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// per-warp digit counters [kWarps][kBins] in dynamic shared memory
-template <uint32_t kBins>
 __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const LogRec *in, LogRec *out, uint64_t n,
                                                                  uint32_t gbits, uint32_t shift,
                                                                  const uint32_t *offs, uint32_t ntiles) {
-  extern __shared__ uint32_t cnt_flat[];
-  uint32_t(*cnt)[kBins] = reinterpret_cast<uint32_t(*)[kBins]>(cnt_flat);
+  __shared__ uint32_t cnt[kWarps][256];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (uint32_t k = threadIdx.x; k < kWarps * kBins; k += kThreads) cnt_flat[k] = 0;
+  for (int k = threadIdx.x; k < kWarps * 256; k += kThreads) (&cnt[0][0])[k] = 0;
   __syncthreads();
   const uint64_t base = (uint64_t)blockIdx.x * kTile + (uint64_t)w * (32 * kItems);
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -122,7 +117,7 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const LogRec *i
     const uint64_t k = base + (uint64_t)i * 32 + lane;
     const bool valid = k < n;
     if (valid) rec[i] = in[k];
-    dig[i] = valid ? digit_of<kBins>(rec[i], gbits, shift) : kBins;
+    dig[i] = valid ? digit_of(rec[i], gbits, shift) : 256u;
     const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dig[i]);
     const uint32_t before = __popc(peers & lt_mask);
     const uint32_t c = valid ? cnt[w][dig[i]] : 0u;
@@ -132,18 +127,18 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const LogRec *i
     __syncwarp();
   }
   __syncthreads();
-  for (uint32_t d = threadIdx.x; d < kBins; d += kThreads) {  // prefix each digit's counts across warps
+  {  // prefix each digit's counts across warps
     uint32_t run = 0;
     for (int q = 0; q < kWarps; q++) {
-      const uint32_t t = cnt[q][d];
-      cnt[q][d] = run;
+      const uint32_t t = cnt[q][threadIdx.x];
+      cnt[q][threadIdx.x] = run;
       run += t;
     }
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kItems; i++) {
-    if (dig[i] < kBins) {
+    if (dig[i] < 256u) {
       const uint64_t pos = (uint64_t)offs[(uint64_t)dig[i] * ntiles + blockIdx.x] + cnt[w][dig[i]] + rank[i];
       out[pos] = rec[i];
     }
@@ -179,49 +174,11 @@ void scan_exclusive(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp
   tile_scan_kernel<<<(unsigned)t, kThreads, 0, s>>>(in, n, out, soffs);
 }
 
-// Digits: 8 bits (256 bins), or 11 bits (2048 bins) when that takes fewer
-// passes -- a wide pass costs about as much as a narrow one (the histograms
-// and their scan grow, the records move once either way).
-constexpr uint32_t kWideBits = 11, kWideBins = 1u << kWideBits;
-uint32_t digit_bits(uint32_t bits) { return (bits + kWideBits - 1) / kWideBits < (bits + 7) / 8 ? kWideBits : 8; }
-
-// one radix pass src -> dst on the digit at `shift`
-void radix_pass(const LogRec *src, LogRec *dst, uint64_t n, uint32_t gbits, uint32_t shift, uint32_t dbits,
-                uint32_t *tmp, cudaStream_t s) {
-  static bool configured[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || !configured[dev]) {  // the wide scatter's counters take 64 KiB of shared memory
-    cudaFuncSetAttribute(radix_scatter_kernel<kWideBins>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(kWarps * kWideBins * 4));
-    if (dev >= 0 && dev < 64) configured[dev] = true;
-  }
-  const uint32_t ntiles = (uint32_t)tiles_of(n);
-  const uint64_t h = (uint64_t)(1u << dbits) * ntiles;
-  uint32_t *hist = tmp, *offs = tmp + h, *stmp = tmp + 2 * h;
-  count_launch();
-  if (dbits == kWideBits) radix_hist_kernel<kWideBins><<<ntiles, kThreads, 0, s>>>(src, n, gbits, shift, hist, ntiles);
-  else radix_hist_kernel<256><<<ntiles, kThreads, 0, s>>>(src, n, gbits, shift, hist, ntiles);
-  scan_exclusive(hist, offs, h, stmp, s);
-  count_launch();
-  if (dbits == kWideBits)
-    radix_scatter_kernel<kWideBins><<<ntiles, kThreads, kWarps * kWideBins * 4, s>>>(src, dst, n, gbits, shift, offs,
-                                                                                     ntiles);
-  else
-    radix_scatter_kernel<256><<<ntiles, kThreads, kWarps * 256 * 4, s>>>(src, dst, n, gbits, shift, offs, ntiles);
-}
-
 size_t sort_tmp_words(uint64_t n) {
-  const uint64_t h = (uint64_t)kWideBins * tiles_of(n);
-  return 2 * h + scan_tmp_words(h);
-}
-
-size_t sort_tmp_words_narrow(uint64_t n) {
   const uint64_t h = 256 * tiles_of(n);
   return 2 * h + scan_tmp_words(h);
 }
 
-// 8-bit digits only (its caller's scratch is sized by sort_tmp_words_narrow)
 void sort_log_into(const LogRec *in, LogRec *out, LogRec *scratch, uint64_t n, uint32_t gbits, uint32_t bits,
                    uint32_t *tmp, cudaStream_t s) {
   const uint32_t passes = n <= 1 ? 0 : (bits + 7) / 8;
@@ -230,10 +187,17 @@ void sort_log_into(const LogRec *in, LogRec *out, LogRec *scratch, uint64_t n, u
     return;
   }
   // pass order chosen so that the last pass writes `out` and `in` is never written
+  const uint32_t ntiles = (uint32_t)tiles_of(n);
+  const uint64_t h = 256ull * ntiles;
+  uint32_t *hist = tmp, *offs = tmp + h, *stmp = tmp + 2 * h;
   const LogRec *src = in;
   LogRec *dst = (passes % 2) ? out : scratch;
   for (uint32_t p = 0, shift = 0; p < passes; p++, shift += 8) {
-    radix_pass(src, dst, n, gbits, shift, 8, tmp, s);
+    count_launch();
+    radix_hist_kernel<<<ntiles, kThreads, 0, s>>>(src, n, gbits, shift, hist, ntiles);
+    scan_exclusive(hist, offs, h, stmp, s);
+    count_launch();
+    radix_scatter_kernel<<<ntiles, kThreads, 0, s>>>(src, dst, n, gbits, shift, offs, ntiles);
     src = dst;
     dst = dst == out ? scratch : out;
   }
@@ -242,9 +206,15 @@ void sort_log_into(const LogRec *in, LogRec *out, LogRec *scratch, uint64_t n, u
 LogRec *sort_log(LogRec *a, LogRec *b, uint64_t n, uint32_t gbits, uint32_t bits, uint32_t *tmp,
                  cudaStream_t s) {
   if (n <= 1) return a;
-  const uint32_t dbits = digit_bits(bits);
-  for (uint32_t shift = 0; shift < bits; shift += dbits) {
-    radix_pass(a, b, n, gbits, shift, dbits, tmp, s);
+  const uint32_t ntiles = (uint32_t)tiles_of(n);
+  const uint64_t h = 256ull * ntiles;
+  uint32_t *hist = tmp, *offs = tmp + h, *stmp = tmp + 2 * h;
+  for (uint32_t shift = 0; shift < bits; shift += 8) {
+    count_launch();
+    radix_hist_kernel<<<ntiles, kThreads, 0, s>>>(a, n, gbits, shift, hist, ntiles);
+    scan_exclusive(hist, offs, h, stmp, s);
+    count_launch();
+    radix_scatter_kernel<<<ntiles, kThreads, 0, s>>>(a, b, n, gbits, shift, offs, ntiles);
     LogRec *t = a;
     a = b;
     b = t;
