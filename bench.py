@@ -67,7 +67,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--strategy", type=int, default=0, help="0 auto, 1 sort, 2 shadow")
+    p.add_argument("--strategy", type=int, default=0, help="0 auto, 1 sort, 2 shadow, 3 resident")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch-kernels", type=int, default=10_000,
                    help="size of the batched-checking measurement (0 skips it)")
@@ -367,7 +367,12 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "accesses_per_step": acc_step,
                    "global_accesses_per_step": rep["n_global"],
-                   "strategy": {0: "auto", 1: "sort", 2: "shadow"}[args.strategy],
+                   "strategy": {0: "auto", 1: "sort", 2: "shadow", 3: "resident"}[args.strategy],
+                   "run": "resident: one cooperative launch per check" if p0["launches"] == args.steps
+                          else "interval by interval",
+                   "private_access_insns": int(rc.prove_private(bc, inst.groups, inst.group_size,
+                                                                inst.globals).sum()),
+                   "private_accesses": "counted and committed, not logged (two-work-item pre-filter)",
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof,
