@@ -80,6 +80,50 @@ __global__ void __launch_bounds__(kThreads) tile_scan_kernel(const uint32_t *in,
   }
 }
 
+// One CTA of 1024 threads scans up to kSmallScan values in one launch (the
+// tiled scan takes three): warp w owns the contiguous chunk [w * 2048,
+// (w + 1) * 2048), read coalesced 32 values at a time; a first sweep sums
+// the chunk, the CTA scans the 32 warp sums, a second sweep writes the
+// running prefix.
+constexpr int kSmallThreads = 1024;
+constexpr uint64_t kSmallChunk = 2048;
+constexpr uint64_t kSmallScan = kSmallChunk * (kSmallThreads / 32);  // 65,536
+
+__global__ void __launch_bounds__(kSmallThreads) small_scan_kernel(const uint32_t *in, uint64_t n, uint32_t *out) {
+  __shared__ uint32_t wsum[32];
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const uint64_t lo = (uint64_t)w * kSmallChunk, hi = lo + kSmallChunk < n ? lo + kSmallChunk : n;
+  uint32_t part = 0;
+  for (uint64_t i = lo + lane; i < hi; i += 32) part += in[i];
+  part = __reduce_add_sync(0xFFFFFFFFu, part);
+  if (lane == 0) wsum[w] = part;
+  __syncthreads();
+  if (w == 0) {  // exclusive scan of the 32 warp sums
+    const uint32_t v = wsum[lane];
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= (uint32_t)o) x += y;
+    }
+    wsum[lane] = x - v;
+  }
+  __syncthreads();
+  uint32_t carry = wsum[w];
+  for (uint64_t base = lo; base < hi; base += 32) {
+    const uint64_t i = base + lane;
+    const uint32_t v = i < hi ? in[i] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= (uint32_t)o) x += y;
+    }
+    if (i < hi) out[i] = carry + x - v;
+    carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+  }
+}
+
 __device__ __forceinline__ uint32_t digit_of(const LogRec &r, uint32_t gbits, uint32_t shift) {
   const uint64_t k = ((uint64_t)r.key << gbits) | (uint64_t)(r.tw & 0x7FFFFFFFu);
   return (uint32_t)(k >> shift) & 0xFFu;
@@ -161,6 +205,11 @@ size_t scan_tmp_words(uint64_t n) {
 void scan_exclusive(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp, cudaStream_t s) {
   if (n == 0) return;
   const uint64_t t = tiles_of(n);
+  if (t > 1 && n <= kSmallScan) {  // one launch instead of three
+    count_launch();
+    small_scan_kernel<<<1, kSmallThreads, 0, s>>>(in, n, out);
+    return;
+  }
   if (t == 1) {
     count_launch();
     tile_scan_kernel<<<1, kThreads, 0, s>>>(in, n, out, nullptr);
