@@ -112,6 +112,7 @@ struct Workspace {
   cudaEvent_t sev[2] = {nullptr, nullptr};  // stats of an interval (by parity) reached the host
   bool configured = false, batch_configured = false;
   uint32_t epoch = 0;
+  uint64_t owner_hi = 0;  // owner-table words that may hold a tag; the rest are zero
   void release_all() {
     for (DevBuf *b : {&code, &mems, &snap, &regs, &pc, &st, &ow, &loga, &logb, &head, &runidx, &sum,
                       &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
@@ -120,6 +121,7 @@ struct Workspace {
                       &bigres, &nbig, &xg, &xgcnt, &xgn, &xgoff, &xgtmp, &xgout, &rstat, &rivoff, &rbar})
       b->release();
     epoch = 0;
+    owner_hi = 0;
   }
 };
 Workspace g_ws;
@@ -404,20 +406,31 @@ void classify_sorted(Workspace &W, LogRec *log, uint32_t n_slices, uint64_t slic
 // Owner table of 4 words per cell (see shadow_claim); words tagged with an
 // older tag count as empty, so the table is cleared only when it is
 // (re)allocated or the 6-bit tag wraps.
+// The table keeps the size of the largest instance (or batch) seen, which
+// can be gigabytes; only its first W.owner_hi words can hold tags, so a
+// clear covers those and no more.
 uint32_t *shadow_table(Workspace &W, uint64_t keys, cudaStream_t s) {
   const size_t before = W.owner.cap;
   uint32_t *t = W.owner.get<uint32_t>(4 * keys);
-  if (W.owner.cap != before || W.epoch == 0) {
+  if (W.owner.cap != before) {  // a new buffer
     CK(cudaMemsetAsync(t, 0, W.owner.cap, s));
     W.epoch = 0;
+    W.owner_hi = 0;
+  } else if (W.epoch == 0 && W.owner_hi) {
+    CK(cudaMemsetAsync(t, 0, W.owner_hi * 4, s));
+    W.owner_hi = 0;
   }
+  W.owner_hi = std::max<uint64_t>(W.owner_hi, 4 * keys);
   return t;
 }
 
-uint32_t shadow_next_tag(Workspace &W, cudaStream_t s) {
+// next interval tag; when the 6-bit tag wraps, the words in use are cleared
+// and `extent` (the running instance's words) becomes the range in use
+uint32_t shadow_next_tag(Workspace &W, cudaStream_t s, uint64_t extent) {
   if (W.epoch >= 63) {
-    CK(cudaMemsetAsync(W.owner.p, 0, W.owner.cap, s));
+    CK(cudaMemsetAsync(W.owner.p, 0, W.owner_hi * 4, s));
     W.epoch = 0;
+    W.owner_hi = extent;
   }
   return ++W.epoch;
 }
@@ -610,7 +623,7 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
 
   InterpArgs a = base;
   a.interval = 0;
-  a.tag = shadow_next_tag(W, s);
+  a.tag = shadow_next_tag(W, s, 4 * L.keys);
   a.owner = owner;
   a.ow_slots = (uint32_t)slots;
   a.errs = errs;
@@ -629,9 +642,9 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   a.iv_off = ivoff;
   a.max_intervals = kResidentMaxIntervals;
   a.run_info = d + R_INFO;
-  // all of it, as the host's wrap does: words past this instance's cells may hold
-  // tags of an earlier, larger instance that later calls would otherwise meet again
-  a.owner_words = W.owner.cap / 4;
+  // an in-kernel wrap clears this instance's words; the host clears the rest
+  // of the range in use after the run (below)
+  a.owner_words = 4 * L.keys;
   a.barrier_limit_ns = 20000000000ull;
   if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
   const cudaError_t e = launch_interp_resident(a, I.G, smem, s);
@@ -650,6 +663,12 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   CK(cudaMemcpyAsync(off.data(), ivoff, kOffHead * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   W.epoch = h[R_INFO + 1];  // the owner-table tag of the last interval
+  if (h[R_INFO] && a.tag + h[R_INFO] - 1 > 63 && W.owner_hi > 4 * L.keys) {
+    // the tag wrapped in-kernel: words past this instance's cells still hold
+    // tags of the earlier epoch, which later calls would meet again
+    CK(cudaMemsetAsync(owner + 4 * L.keys, 0, (W.owner_hi - 4 * L.keys) * 4, s));
+    W.owner_hi = 4 * L.keys;
+  }
   const uint32_t flags = h[R_FLAGS] | h[R_FLAGS + 1];
   if (h[R_BAR + 2]) throw Fail{RC_E_TIMEOUT, "a grid barrier of the resident run timed out"};
   if (flags & (FLAG_LOG_FULL | FLAG_OW_FULL | FLAG_ERR_FULL))
@@ -939,7 +958,7 @@ rc_report *run_instance(const Instance &I) {
   uint32_t interval = 0;
   int strategy = fixed_strategy ? fixed_strategy : g_tuner.choose(tkey);
   bool timed = !fixed_strategy && !g_tuner.decided(tkey);  // autotuner sample of this interval
-  uint32_t tag = strategy == 2 ? shadow_next_tag(W, s) : 0;
+  uint32_t tag = strategy == 2 ? shadow_next_tag(W, s, 4 * L.keys) : 0;
   enqueue_interp(0, strategy, tag, false, timed);
   enqueue_post(0, strategy, tag);
   for (;; interval++) {
@@ -953,7 +972,7 @@ rc_report *run_instance(const Instance &I) {
     if (strategy == 2 && !timed && !g_prof.on && !I.explore && !group) {
       const int ns = fixed_strategy ? fixed_strategy : g_tuner.choose(tkey);
       if (ns == 2 && (fixed_strategy || g_tuner.decided(tkey))) {
-        next_tag = shadow_next_tag(W, s);
+        next_tag = shadow_next_tag(W, s, 4 * L.keys);
         uint32_t *d = dbuf(interval);
         launch_interval_gate(d + ST_FLAGS, reinterpret_cast<const unsigned long long *>(d + ST_SCRATCH),
                              d + ST_STOPS + nstops, P.n_barriers, gate + ((interval + 1) & 1), s);
@@ -1030,7 +1049,7 @@ rc_report *run_instance(const Instance &I) {
     // the next interval starts after this one's classification
     strategy = fixed_strategy ? fixed_strategy : g_tuner.choose(tkey);
     timed = !fixed_strategy && !g_tuner.decided(tkey);
-    if (strategy == 2) tag = next_queued ? next_tag : shadow_next_tag(W, s);  // a closed gate used no claims
+    if (strategy == 2) tag = next_queued ? next_tag : shadow_next_tag(W, s, 4 * L.keys);  // a closed gate used no claims
     else tag = 0;
     enqueue_interp(interval + 1, strategy, tag, false, timed);
     enqueue_post(interval + 1, strategy, tag);
@@ -1280,7 +1299,7 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
     const bool tuning = !strategy && !g_tuner.decided(tkey);
     std::memcpy(hdesc, desc.data(), n * sizeof(BatchDesc));
     hround[0] = round;
-    hround[1] = strat == 2 ? shadow_next_tag(W, bs) : 0;
+    hround[1] = strat == 2 ? shadow_next_tag(W, bs, 4 * keys) : 0;
     hround[2] = strat == 2 ? 1u : 0u;
     CK(cudaMemcpyAsync(ddesc, hdesc, n * sizeof(BatchDesc), cudaMemcpyHostToDevice, bs));
     CK(cudaMemcpyAsync(dround, hround, 16, cudaMemcpyHostToDevice, bs));
