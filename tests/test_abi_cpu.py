@@ -94,3 +94,21 @@ def test_bad_arguments_rejected_without_gpu_work(rc):
         rc.check(b, 1, 32, [])
     with pytest.raises(rc.RaceCheckError):
         rc.set_strategy(7)
+
+
+def test_strategy_values(rc):
+    """0 auto, 1 sort, 2 shadow, 3 resident are accepted; nothing else."""
+    for s in (0, 1, 2, 3):
+        rc.set_strategy(s)
+    for bad in (4, -1):
+        with pytest.raises(rc.RaceCheckError):
+            rc.set_strategy(bad)
+    rc.set_strategy(0)
+
+
+def test_diag_grid_barrier_rejects_bad_limits(rc):
+    """The diagnostic checks its argument before touching a device."""
+    with pytest.raises(rc.RaceCheckError):
+        rc.diag_grid_barrier(0)
+    with pytest.raises(rc.RaceCheckError):
+        rc.diag_grid_barrier(20_000_000)
