@@ -120,14 +120,17 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
   const uint64_t N = (uint64_t)A.G * S;
   const uint32_t lt = gtid - A.group0 * S;  // index in this launch's own-write table
   const uint32_t slots = A.ow_slots;
-  uint32_t st = A.st[gtid];
-  uint32_t pc = A.pc[gtid];
+  // a resident run starts every work-item afresh (pc 0, registers 0); an
+  // interval launch resumes the state the previous one saved
+  uint32_t st = kResident ? (uint32_t)TS_RUN : A.st[gtid];
+  uint32_t pc = kResident ? 0u : A.pc[gtid];
   if (st == TS_BARRIER) {  // resume after the barrier it waited at
     st = TS_RUN;
     pc += 1;
   }
   if (st == TS_RUN) {
-    for (uint32_t r = kBuiltinRegs; r < A.n_regs; r++) rf[r * S + tid] = A.regs[(uint64_t)r * N + gtid];
+    for (uint32_t r = kBuiltinRegs; r < A.n_regs; r++)
+      rf[r * S + tid] = kResident ? 0 : A.regs[(uint64_t)r * N + gtid];
     rf[REG_TID * S + tid] = (int32_t)tid;
     rf[REG_WG * S + tid] = (int32_t)wg;
     rf[REG_GTID * S + tid] = (int32_t)gtid;

@@ -816,9 +816,12 @@ rc_report *run_instance(const Instance &I) {
   load_snapshot();
   int32_t *regs = W.regs.get<int32_t>(N * P.n_regs);
   uint32_t *pc = W.pc.get<uint32_t>(N), *st = W.st.get<uint32_t>(N);
-  CK(cudaMemsetAsync(regs, 0, N * P.n_regs * 4, s));
-  CK(cudaMemsetAsync(pc, 0, N * 4, s));
-  CK(cudaMemsetAsync(st, 0, N * 4, s));
+  // work-item state starts at zero; a resident run sets its own up in-kernel
+  auto clear_state = [&]() {
+    CK(cudaMemsetAsync(regs, 0, N * P.n_regs * 4, s));
+    CK(cudaMemsetAsync(pc, 0, N * 4, s));
+    CK(cudaMemsetAsync(st, 0, N * 4, s));
+  };
   uint2 *ow = W.ow.get<uint2>(N * capw);
   LogRec *log = W.loga.get<LogRec>(cap);
   const uint32_t err_cap = (uint32_t)std::min<uint64_t>(N, 1u << 24);
@@ -882,6 +885,7 @@ rc_report *run_instance(const Instance &I) {
     load_snapshot();  // the resident run stopped early: start over interval by interval
     if (pcode && &interval_code != pcode) upload_code(interval_code);
   }
+  clear_state();
   auto dbuf = [&](uint32_t k) { return dstats2 + (k & 1) * stat_words; };
   auto hbuf = [&](uint32_t k) { return hstats2 + (k & 1) * stat_words; };
   // one interval's interpreter launch (gated: runs only if gate[k & 1] is set on the device)
