@@ -336,8 +336,10 @@ int rc_explore_pairs(const rc_bytecode *bc, uint32_t groups, uint32_t group_size
  * can make a conflicting pair of accesses in one barrier interval under any
  * schedule: every pair of accesses to one array (one a store) in a common
  * barrier region has disjoint index ranges, or the same index form that is
- * one-to-one on the work-items (one group's, for local arrays), or both
- * store one constant.  race_free = 0 decides nothing (the checker does);
+ * one-to-one on the work-items (one group's, for local arrays), or -- when
+ * the work-items and loop counters of the pair can be enumerated (up to
+ * 2^16 points per access, 2^20 per call) -- no cell reached by two work-items,
+ * or both store one constant.  race_free = 0 decides nothing (the checker does);
  * first_pc_a/b name the first pair left open.  in_bounds = 1 means every
  * index is provably within its array. */
 typedef struct {
@@ -356,7 +358,9 @@ int rc_prove(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const 
  * a one-to-one index, not by equal values.  No other work-item touches the
  * cells such an access touches in its interval, so it is never part of a
  * race or benign record; the checker (owner-table and resident runs) skips
- * logging them and claims only their stores.  *n_private = the count. */
+ * logging them and claims only their stores.  This is the analysis the
+ * checker runs for every launch shape, without rc_prove's enumeration of
+ * small launches.  *n_private = the count. */
 int rc_prove_private(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in,
                      uint8_t *flags, uint32_t n_flags, uint32_t *n_private);
 

@@ -22,14 +22,17 @@
 // them a store, by two different work-items (each with its own loop
 // counters) is harmless when the index ranges are disjoint, or when both use
 // the same index form and equal values of it force equal work-items (for
-// local arrays: within one group), or when every work-item stores one and
-// the same value.  The verdict "race-free" holds for every schedule
+// local arrays: within one group), or -- on launches small enough to
+// enumerate every work-item and loop counter -- when no cell is reached by
+// two different work-items, or when every work-item stores one and the
+// same value.  The verdict "race-free" holds for every schedule
 // (Sec. 4's Definition); otherwise the pre-filter says nothing and the
 // checker decides.
 #include <algorithm>
 #include <array>
 #include <cstdint>
 #include <cstdlib>
+#include <unordered_map>
 #include <vector>
 
 #include "racecheck.h"
@@ -219,6 +222,81 @@ bool injective(const AF &f, const Shape &sh, bool same_group) {
     if (d[i].item && !d[i].fixed) return false;
   // distinct inner values stay distinct after the reduction when they span less than M
   return f.M == 0 || span < f.M;
+}
+
+// Every (work-item, loop counters) point of the box, with the form's value
+// there (the form is exact on the box).  Returns false, visiting nothing,
+// when the box has more than `limit` points.
+template <class F>
+bool enumerate(const AF &f, const Shape &sh, uint64_t limit, F visit) {
+  uint64_t n = (uint64_t)sh.nt() * (uint64_t)sh.nw();
+  int vars[kLoops], nv = 0;
+  for (int L = 0; L < kLoops; L++)
+    if (f.cv[L]) {
+      vars[nv++] = L;
+      n *= (uint64_t)(sh.vhi[L] - sh.vlo[L] + 1);
+      if (n > limit) return false;
+    }
+  if (n > limit || sh.empty()) return n <= limit;
+  int64_t v[kLoops];
+  for (int64_t w = sh.w0; w <= sh.w1; w++)
+    for (int64_t t = sh.t0; t <= sh.t1; t++) {
+      for (int k = 0; k < nv; k++) v[k] = sh.vlo[vars[k]];
+      for (;;) {
+        __int128 y = (__int128)f.c0 + (__int128)f.ct * t + (__int128)f.cw * w;
+        for (int k = 0; k < nv; k++) y += (__int128)f.cv[vars[k]] * v[k];
+        int64_t x = (int64_t)y;  // the form is exact on the box: the inner value fits int32
+        if (f.M > 0) x = x - fdiv(x, f.M) * f.M;  // Euclidean remainder
+        visit(t, w, x + f.off);
+        int k = 0;
+        while (k < nv && ++v[k] > sh.vhi[vars[k]]) v[k] = sh.vlo[vars[k]], k++;
+        if (k == nv) break;
+      }
+    }
+  return true;
+}
+
+// Exact check of a pair on small launches: can a work-item's access a and a
+// different work-item's access b reach one cell (for local arrays: one cell
+// of one group)?  a == b asks it of one instruction.  Returns 1 for "never",
+// 0 for "they can", -1 when the points to enumerate exceed *budget (which
+// the points visited are taken from).
+int never_meet(const AF &fa, const Shape &ba, const AF &fb, const Shape &bb, bool same, bool local,
+               uint64_t *budget) {
+  const uint64_t kLimit = std::min<uint64_t>(*budget, 1u << 16);
+  // cell (and group, for local arrays) -> the one work-item seen there, or kMany
+  constexpr int64_t kMany = -1;
+  std::unordered_map<uint64_t, int64_t> seen;
+  const auto cell = [&](int64_t w, int64_t x) {
+    return ((uint64_t)(local ? w : 0) << 32) ^ (uint64_t)(uint32_t)x;
+  };
+  const auto item = [&](int64_t t, int64_t w) { return w * (ba.S) + t; };
+  bool clash = false;
+  uint64_t visited = 0;
+  const auto spend = [&]() { *budget -= std::min(*budget, visited); };
+  if (!enumerate(fa, ba, kLimit, [&](int64_t t, int64_t w, int64_t x) {
+        visited++;
+        auto it = seen.emplace(cell(w, x), item(t, w));
+        if (!it.second && it.first->second != item(t, w)) {
+          if (same) clash = true;  // two work-items of the one instruction
+          it.first->second = kMany;
+        }
+      }))
+    return -1;
+  if (clash || same) {
+    spend();
+    return clash ? 0 : 1;
+  }
+  if (!enumerate(fb, bb, kLimit, [&](int64_t t, int64_t w, int64_t x) {
+        visited++;
+        auto it = seen.find(cell(w, x));
+        if (it != seen.end() && it->second != item(t, w)) clash = true;
+      })) {
+    spend();
+    return -1;
+  }
+  spend();
+  return clash ? 0 : 1;
 }
 
 // Restrict sh to the work-items where (x op imm) holds, op = 0 <, 1 <=, 2 >,
@@ -537,8 +615,11 @@ namespace rc {
 // disjoint cells or a one-to-one index (or cannot happen): no other
 // work-item touches the cells it touches in its interval, so it can never
 // be part of a race or benign record.
+// enum_budget: how many (work-item, loop counter) points the exact check of
+// small launches may enumerate in all (0: none).
 void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const std::vector<uint32_t> &lens,
-                   rc_prove_result *out, std::vector<uint8_t> *priv) {
+                   rc_prove_result *out, std::vector<uint8_t> *priv, uint64_t enum_budget) {
+  uint64_t budget = enum_budget;
   Prover pr(p, Shape(group_size, groups), lens);
   pr.dataflow();
   pr.regions();
@@ -589,6 +670,8 @@ void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const
         const Range ra = range_of(a.idx, a.box), rb = range_of(b.idx, b.box);
         ok = ra.hi < rb.lo || rb.hi < ra.lo;                            // disjoint cells
         ok = ok || (a.idx == b.idx && injective(a.idx, h, a.local));  // only with itself
+        // small launches: every work-item's cells, enumerated
+        ok = ok || (budget && never_meet(a.idx, a.box, b.idx, b.box, i == j, a.local, &budget) == 1);
       }
       if (!ok && priv) (*priv)[a.pc] = (*priv)[b.pc] = 0;  // the two may share a cell
       if (!ok && a.store && b.store && a.val.kind == AF::AFF && b.val.kind == AF::AFF) {
@@ -631,7 +714,7 @@ extern "C" int rc_prove(const rc_bytecode *bc, uint32_t groups, uint32_t group_s
     set_last_error("input count differs from the kernel's global declarations");
     return RC_E_INVALID;
   }
-  prove_analyze(bc->prog, groups, group_size, lens, out, nullptr);
+  prove_analyze(bc->prog, groups, group_size, lens, out, nullptr, 1u << 20);
   return RC_OK;
 }
 
@@ -649,7 +732,7 @@ extern "C" int rc_prove_private(const rc_bytecode *bc, uint32_t groups, uint32_t
   }
   rc_prove_result r;
   std::vector<uint8_t> priv;
-  prove_analyze(bc->prog, groups, group_size, lens, &r, &priv);
+  prove_analyze(bc->prog, groups, group_size, lens, &r, &priv, 0);  // as the checker does
   uint32_t n = 0;
   for (size_t k = 0; k < priv.size(); k++) {
     flags[k] = priv[k];

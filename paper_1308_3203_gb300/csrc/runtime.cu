@@ -29,7 +29,7 @@
 namespace rc {
 // The two-work-item pre-filter (prove.cpp).
 void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const std::vector<uint32_t> &lens,
-                   rc_prove_result *out, std::vector<uint8_t> *priv);
+                   rc_prove_result *out, std::vector<uint8_t> *priv, uint64_t enum_budget);
 bool prove_lengths(const Program &p, const rc_input *in, std::vector<uint32_t> &lens);
 
 namespace {
@@ -562,7 +562,7 @@ const std::vector<Insn> &private_code(const Program &P, uint32_t G, uint32_t S, 
   if (!(c.valid && c.G == G && c.S == S && c.lens == lens)) {
     rc_prove_result r;
     std::vector<uint8_t> flags;
-    prove_analyze(P, G, S, lens, &r, &flags);
+    prove_analyze(P, G, S, lens, &r, &flags, 0);  // the cheap analysis: it runs per launch shape
     c.code = P.code;
     c.n_private = 0;
     for (size_t k = 0; k < flags.size(); k++)

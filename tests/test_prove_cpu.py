@@ -78,6 +78,11 @@ HAND = [
      2, 8, (128,), True, True),
     # ... but 4 cells at a stride of 2 overlap the next work-item's: a race
     ("kernel k(global int A[]) { for i in 0 .. 4 { A[gtid * 2 + i] = i; } }", 2, 8, (64,), False, True),
+    # a permutation of the cells that crosses the period of the remainder:
+    # only the enumeration of the eight work-items shows it one-to-one
+    ("kernel k(global int A[]) { A[(3 * tid) % 8] = tid; }", 1, 8, (8,), True, True),
+    # ... and a remainder that sends two work-items to one cell
+    ("kernel k(global int A[]) { A[(2 * tid) % 8] = tid; }", 1, 8, (8,), False, True),
     # a loaded index says nothing
     ("kernel k(global int A[], global int B[]) { A[B[gtid]] = 1; }", 1, 8, (8, 8), True, False),
     ("kernel k(global int A[], global int B[]) { A[B[gtid]] = tid; }", 1, 8, (8, 8), False, False),
@@ -98,7 +103,7 @@ def test_hand_examples(rc, oracle, case):
         assert OOB not in cls
     # the racy examples are racy: the claims withheld above are not just imprecision
     if src.startswith("kernel k(global int A[]) { A[0] = tid") or "g = wg" in src or "tid - 8" in src \
-            or "gtid * 2 + i" in src:
+            or "gtid * 2 + i" in src or "(2 * tid) % 8" in src:
         assert cls & {WW_RACE, RW_RACE}
 
 
@@ -195,6 +200,9 @@ PRIVATE = [
     ("kernel k(global int A[]) { for i in 0 .. 4 { A[gtid * 4 + i] = i; } }", 2, 8, (64,), [1]),
     # local cells per group
     ("kernel k(local int L[8]) {\n L[tid] = 1;\n x = L[tid];\n}", 4, 8, (), [1, 1]),
+    # the checker's analysis does not enumerate work-items: the permutation
+    # rc_prove shows race-free stays shared here
+    ("kernel k(global int A[]) { A[(3 * tid) % 8] = tid; }", 1, 8, (8,), [0]),
 ]
 
 
