@@ -46,7 +46,7 @@ SAMPLE_GROUPS = 96
 #       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --batch-kernels 0 --proposal-kernels 0
 # (profiles/interp_kernel_large_instance.md).  It holds only for the kernel
 # sources it was taken on; any change to them reports null.
-INTERP_TRAFFIC = {"sources_sha256": "89d2d0da349e1710cc895ba0b663c8188af7fa4f3d14a805df73d46a9c60e9c9",
+INTERP_TRAFFIC = {"sources_sha256": "fdada85ee7a1f89e937a68a3a3c07021393370571e4e65bf491541e1aa86a60c",
                   "bytes_per_launch": 168407957}
 INTERP_SOURCES = ("paper_1308_3203_gb300/csrc/interp.cu", "paper_1308_3203_gb300/csrc/device.cuh",
                   "paper_1308_3203_gb300/csrc/semantics.cuh", "paper_1308_3203_gb300/csrc/prove.cpp")
