@@ -482,3 +482,22 @@ def test_group_scope_local_cells_stay_in_their_group(oracle):
     r = oracle.check(src, 3, 4, [np.zeros(12, np.int32)], group_barriers=True)
     assert _xg(r) == [] and r["status"] == 0
     np.testing.assert_array_equal(r["final"], np.repeat(np.arange(3), 4))
+
+
+def test_group_scope_barriers_in_a_loop_of_one_group(oracle):
+    # only group 0 loops over four barriers: five rounds, group 1 finished
+    # after the first; each round's four writers store one value
+    r = _grp(oracle, "if (wg == 0) { for i in 0 .. 4 { A[i] = wg; barrier; } }", 2, 4, [9] * 4)
+    assert r["status"] == 0 and r["n_intervals"] == 5
+    np.testing.assert_array_equal(r["records"], [rec(k, k, 2, 0, 1, 0, 4, 4) for k in range(4)])
+    np.testing.assert_array_equal(r["final"], [0, 0, 0, 0])
+
+
+def test_group_scope_read_rounds_before_the_write(oracle):
+    # group 1 reads in round 0, group 0 writes in round 2: ordered by the
+    # kernel-wide barriers, unordered by group-scoped ones; witness (r0, w0) = (4, 0)
+    body = "if (wg == 1) { x = A[0]; }\nbarrier;\nbarrier;\nif (wg == 0) { A[0] = 3; }"
+    r = _grp(oracle, body, 2, 4, [0], gb=False)
+    assert r["status"] == 0
+    r = _grp(oracle, body, 2, 4, [0])
+    assert r["status"] == 1 and _xg(r) == [rec(XG, 0, 6, 4, 0, 4, 4, 8)]
