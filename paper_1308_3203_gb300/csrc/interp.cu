@@ -10,8 +10,10 @@
 // Shared reads see the work-item's own latest write to the cell in this
 // interval if there is one, else the value committed at the last barrier
 // (delayed visibility); shared writes go to the work-item's own-write table.
-// Every access is appended to the interval's log with one warp-aggregated
-// atomic per instruction and one 16-byte store per work-item.
+// Every access is counted and, unless the pre-filter proved it private (no
+// other work-item touches its cells in the interval: CTL_PRIV), appended to
+// its warp's slice of the interval's log -- a 16-byte store at the slot the
+// ballot of the logging lanes gives it, no atomics.
 //
 // Resident runs: when every work-group of the instance fits on the GPU at
 // once, one cooperative launch runs all intervals.  Registers stay in shared
