@@ -95,6 +95,19 @@ struct Checker {
   Report rep;
   bool group_scope = false;
   std::map<uint32_t, std::vector<Access>> whole_run;  // group scope: every access to each global cell
+  // Address sharding (for instances too large to log whole): shard p of P
+  // logs and classifies only the cells with cell_hash % P == p; for every
+  // other cell it keeps just the write to commit (the highest writer's last
+  // one), so the run itself is the full run.  Only shard 0 reports errors.
+  // The union of the P reports' race records, in report order, with shard
+  // 0's error records is the unsharded report.
+  uint32_t shard = 0, n_shards = 1;
+  std::map<Cell, std::pair<uint32_t, int32_t>> pending;  // cell -> (writer, value), other shards' cells
+  bool mine(const Cell &c) const {
+    if (n_shards == 1) return true;
+    const uint32_t h = std::get<2>(c) * 0x9E3779B1u ^ std::get<1>(c) * 0x85EBCA77u ^ std::get<0>(c);
+    return h % n_shards == shard;
+  }
   std::vector<int32_t> initial_global;                // global memory before the run
 
   // per interval
@@ -185,11 +198,16 @@ struct Checker {
           Cell c{(uint32_t)m.space, m.space ? wg : 0u, (uint32_t)(mem_base[n.mem] + (uint64_t)idx)};
           if (n.kind == N_STORE) {
             own[c] = val;
-            log[c].push_back({gtid, true, val});
+            if (mine(c)) {
+              log[c].push_back({gtid, true, val});
+            } else {  // another shard's cell: only what the commit needs
+              auto it = pending.find(c);
+              if (it == pending.end() || gtid >= it->second.first) pending[c] = {gtid, val};
+            }
           } else {
             auto it = own.find(c);
             int32_t v = it != own.end() ? it->second : committed(c);
-            log[c].push_back({gtid, false, v});
+            if (mine(c)) log[c].push_back({gtid, false, v});
             t.vars[n.var] = v;
           }
           rep.n_access++;
@@ -405,6 +423,8 @@ struct Checker {
           if (a.write && a.gtid == top) v = a.value;
         commit_cell(kv.first, v);
       }
+      for (auto &kv : pending) commit_cell(kv.first, kv.second.second);
+      pending.clear();
       if (diverged || !any_barrier) break;
     }
     // report: race records already sorted by (interval, space, wg, addr, cls);
@@ -416,6 +436,7 @@ struct Checker {
     for (auto &r : rep.records)
       racy |= (r.cls == C_WW_RACE || r.cls == C_RW_RACE || r.cls == C_XG_WW_RACE || r.cls == C_XG_RW_RACE);
     for (auto &e : interval_errors) {
+      if (shard != 0) break;  // shard 0 reports the errors
       div |= e.cls == C_DIVERGENCE;
       as |= e.cls == C_ASSERT;
       oob |= e.cls == C_OOB;
@@ -442,7 +463,8 @@ extern "C" {
 // Run the checker.  global_len/global_init give one int32 array per `global`
 // declaration, in declaration order.  mode bit 0 runs the threads of every
 // interval in descending gtid order (the report must not change); bit 1
-// takes barriers as work-group scoped.
+// takes barriers as work-group scoped; bits 8-19 / 20-31 give the shard p
+// and the shard count P (0: unsharded) of an address-sharded run.
 // Returns 0 on success, 1 on a parse error (message in err), 2 on a bad
 // launch shape or input.
 int oracle_check(const char *src, uint32_t groups, uint32_t group_size, uint32_t n_global,
@@ -483,6 +505,12 @@ int oracle_check(const char *src, uint32_t groups, uint32_t group_size, uint32_t
     }
     ck.local_snap.assign((uint64_t)groups * ck.local_total, 0);
     ck.group_scope = (mode & 2) != 0;
+    const uint32_t shards = ((uint32_t)mode >> 20) & 0xFFFu;
+    if (shards > 1) {
+      ck.n_shards = shards;
+      ck.shard = ((uint32_t)mode >> 8) & 0xFFFu;
+      if (ck.shard >= shards) { snprintf(err, err_len, "bad shard"); return 2; }
+    }
     ck.run((mode & 1) != 0);
     auto *h = new OracleHandle{std::move(ck.rep)};
     *out = h;

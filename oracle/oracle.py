@@ -105,12 +105,14 @@ def _marshal(globals_):
 
 
 def check(src: str, groups: int, group_size: int, globals_, reverse: bool = False,
-          group_barriers: bool = False) -> dict:
+          group_barriers: bool = False, shard: tuple = (0, 1)) -> dict:
     """Run the reference checker on one instance.
 
     ``globals_`` is one int32 array per ``global`` declaration, in order.
     ``group_barriers`` takes barriers as work-group scoped (per-group barrier
-    agreement, cross-group records of the whole run).
+    agreement, cross-group records of the whole run).  ``shard = (p, P)``
+    logs and classifies only the cells of address shard p of P (the run is
+    the full one; only shard 0 reports errors); ``check_sharded`` merges.
     Returns dict(status, n_intervals, n_access, n_global, n_local,
     records (uint32 [n, 10]), final (int32, all global arrays concatenated)).
     """
@@ -119,7 +121,8 @@ def check(src: str, groups: int, group_size: int, globals_, reverse: bool = Fals
     h = ctypes.c_void_p()
     err = ctypes.create_string_buffer(512)
     rc = lib.oracle_check(src.encode(), groups, group_size, n, lens, ptrs,
-                          (1 if reverse else 0) | (2 if group_barriers else 0),
+                          (1 if reverse else 0) | (2 if group_barriers else 0) |
+                          ((shard[0] << 8) | (shard[1] << 20) if shard[1] > 1 else 0),
                           ctypes.byref(h), err, 512)
     if rc != 0:
         raise OracleError(f"oracle rc={rc}: {err.value.decode()}")
@@ -198,3 +201,25 @@ def explore_pairs(src: str, groups: int, group_size: int, globals_, max_states: 
         return out
     finally:
         lib.explore_free(h)
+
+
+def check_sharded(src: str, groups: int, group_size: int, globals_, n_shards: int,
+                  group_barriers: bool = False) -> dict:
+    """The report of an address-sharded run: the P shards run one after the
+    other (independent processes in a large run), their race records merged
+    in report order, shard 0's error records after them, the status from the
+    merged records."""
+    parts = [check(src, groups, group_size, globals_, group_barriers=group_barriers, shard=(p, n_shards))
+             for p in range(n_shards)]
+    races = np.concatenate([r["records"][r["records"][:, 4] < 16] for r in parts])
+    if len(races):
+        order = np.lexsort(tuple(races[:, k] for k in (4, 3, 2, 1, 0)))
+        races = races[order]
+    errs = parts[0]["records"][parts[0]["records"][:, 4] >= 16]
+    cls = set(int(c) for c in races[:, 4]) if len(races) else set()
+    ecl = set(int(c) for c in errs[:, 4]) if len(errs) else set()
+    status = 1 if cls & {1, 3, 4, 6} else 4 if 18 in ecl else 3 if 17 in ecl else 2 if 16 in ecl else 0
+    out = dict(parts[0])
+    out["records"] = np.concatenate([races.reshape(-1, 10), errs.reshape(-1, 10)]).astype(np.uint32)
+    out["status"] = status
+    return out

@@ -501,3 +501,19 @@ def test_group_scope_read_rounds_before_the_write(oracle):
     assert r["status"] == 0
     r = _grp(oracle, body, 2, 4, [0])
     assert r["status"] == 1 and _xg(r) == [rec(XG, 0, 6, 4, 0, 4, 4, 8)]
+
+
+@pytest.mark.parametrize("gb", [False, True])
+def test_address_sharded_runs_merge_to_the_full_report(oracle, gb):
+    """P address shards (each logging and classifying its cells, committing
+    all) merge to the unsharded report, record for record."""
+    insts = [W.tiny_kernel(s) for s in range(12)] + [W.small_kernel(s, group_size=32, groups=2) for s in range(4)]
+    insts += [W.large_kernel(1, groups=4, group_size=32, global_len=4096, local_len=64, n_stmts=40,
+                             n_barriers=3), W.group_kernel(2)]
+    for inst in insts:
+        want = oracle.check(inst.src, inst.groups, inst.group_size, inst.globals, group_barriers=gb)
+        for P in (2, 3):
+            got = oracle.check_sharded(inst.src, inst.groups, inst.group_size, inst.globals, P, group_barriers=gb)
+            assert got["status"] == want["status"], inst.name
+            np.testing.assert_array_equal(got["records"], want["records"], err_msg=inst.name)
+            np.testing.assert_array_equal(got["final"], want["final"], err_msg=inst.name)
