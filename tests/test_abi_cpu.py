@@ -112,3 +112,36 @@ def test_diag_grid_barrier_rejects_bad_limits(rc):
         rc.diag_grid_barrier(0)
     with pytest.raises(rc.RaceCheckError):
         rc.diag_grid_barrier(20_000_000)
+
+
+def test_group_scope_rejected_where_unsupported_without_gpu_work(rc):
+    """Batches and the explorers take kernel-wide barriers only: the request
+    is refused before any device work."""
+    import ctypes
+    bc = rc.compile("kernel k(global int A[]) { A[gtid] = 1; }")
+    A = np.zeros(8, np.int32)
+    inp, keep = rc._marshal([A], None, False)
+    inp.flags |= rc.RC_GROUP_BARRIERS
+    lib = rc.load()
+    out = (rc._ExploreInterval * 4)()
+    n = ctypes.c_uint32()
+    assert lib.rc_explore(bc.handle, 2, 4, ctypes.byref(inp), 0, out, 4, ctypes.byref(n)) == 2
+    pairs = (rc._PairInterval * 4)()
+    assert lib.rc_explore_pairs(bc.handle, 2, 4, ctypes.byref(inp), 0, pairs, 4, ctypes.byref(n), None) == 2
+    hs = (ctypes.c_void_p * 1)(bc.handle.value)
+    gs = (ctypes.c_uint32 * 1)(2)
+    ss = (ctypes.c_uint32 * 1)(4)
+    ins = (rc._Input * 1)(inp)
+    outs = (ctypes.POINTER(rc._Report) * 1)()
+    assert lib.rc_check_batch(hs, gs, ss, ins, 1, outs) == 2
+    del keep
+
+
+def test_prove_private_checks_its_flag_array(rc):
+    import ctypes
+    bc = rc.compile("kernel k(global int A[]) { A[gtid] = 1; }")
+    inp, keep = rc._marshal([np.zeros(8, np.int32)], None, False)
+    flags = (ctypes.c_uint8 * 1)()
+    n = ctypes.c_uint32()
+    assert rc.load().rc_prove_private(bc.handle, 1, 8, ctypes.byref(inp), flags, 1, ctypes.byref(n)) == 2
+    del keep
