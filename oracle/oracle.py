@@ -203,14 +203,25 @@ def explore_pairs(src: str, groups: int, group_size: int, globals_, max_states: 
         lib.explore_free(h)
 
 
+def _shard_job(args):
+    src, groups, group_size, globals_, group_barriers, p, n_shards = args
+    return check(src, groups, group_size, globals_, group_barriers=group_barriers, shard=(p, n_shards))
+
+
 def check_sharded(src: str, groups: int, group_size: int, globals_, n_shards: int,
-                  group_barriers: bool = False) -> dict:
+                  group_barriers: bool = False, processes: int = 1) -> dict:
     """The report of an address-sharded run: the P shards run one after the
-    other (independent processes in a large run), their race records merged
-    in report order, shard 0's error records after them, the status from the
-    merged records."""
-    parts = [check(src, groups, group_size, globals_, group_barriers=group_barriers, shard=(p, n_shards))
-             for p in range(n_shards)]
+    other, or in `processes` spawn-started processes, their race records
+    merged in report order, shard 0's error records after them, the status
+    from the merged records."""
+    jobs = [(src, groups, group_size, [np.asarray(g) for g in globals_], group_barriers, p, n_shards)
+            for p in range(n_shards)]
+    if processes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(processes, n_shards)) as pool:
+            parts = pool.map(_shard_job, jobs)
+    else:
+        parts = [_shard_job(j) for j in jobs]
     races = np.concatenate([r["records"][r["records"][:, 4] < 16] for r in parts])
     if len(races):
         order = np.lexsort(tuple(races[:, k] for k in (4, 3, 2, 1, 0)))

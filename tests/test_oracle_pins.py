@@ -517,3 +517,11 @@ def test_address_sharded_runs_merge_to_the_full_report(oracle, gb):
             assert got["status"] == want["status"], inst.name
             np.testing.assert_array_equal(got["records"], want["records"], err_msg=inst.name)
             np.testing.assert_array_equal(got["final"], want["final"], err_msg=inst.name)
+
+
+def test_address_sharded_runs_in_processes(oracle):
+    inst = W.large_kernel(2, groups=4, group_size=32, global_len=4096, local_len=64, n_stmts=40, n_barriers=3)
+    want = oracle.check(inst.src, inst.groups, inst.group_size, inst.globals)
+    got = oracle.check_sharded(inst.src, inst.groups, inst.group_size, inst.globals, 4, processes=2)
+    np.testing.assert_array_equal(got["records"], want["records"])
+    np.testing.assert_array_equal(got["final"], want["final"])
