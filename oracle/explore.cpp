@@ -69,7 +69,7 @@ struct Explorer {
   bool overflow = false;
 
   Env env_of(const GState &s, uint32_t g) const {
-    return Env{&s.th[g].vars, g % S, g / S, S, G, &mem_len};
+    return Env{s.th[g].vars.data(), g % S, g / S, S, G, &mem_len};
   }
 
   int next_node(int k, const Env &env) const {

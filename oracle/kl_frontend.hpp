@@ -642,7 +642,7 @@ class CfgBuilder {
 // [0, |m|)); division or modulus by zero yields 0; comparisons and logical
 // operators yield 0 or 1.
 struct Env {
-  const std::vector<int32_t> *vars;
+  const int32_t *vars;  // the work-item's private variables
   uint32_t tid, wg, gsize, ngroups;
   const std::vector<int64_t> *mem_len;
 };
@@ -652,7 +652,7 @@ static int32_t eval(const Expr &e, const Env &env) {
   auto B = [&]() { return eval(*e.b, env); };
   switch (e.kind) {
     case E_CONST: return e.value;
-    case E_VAR: return (*env.vars)[e.var];
+    case E_VAR: return env.vars[e.var];
     case E_TID: return (int32_t)env.tid;
     case E_WG: return (int32_t)env.wg;
     case E_GTID: return (int32_t)(uint32_t)((uint64_t)env.wg * env.gsize + env.tid);

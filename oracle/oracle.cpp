@@ -3,7 +3,8 @@
 // Only the test suite, __graft_entry__.smoke() and bench.py's CPU baseline
 // leg may build, load or call this file.  It shares no code with the GPU
 // path.  It is written for obviousness, not speed: threads run one after the
-// other, shared accesses go into std::map-based logs, and conflicts are
+// other, every shared access of an interval goes into one list (grouped by
+// cell with a sort that keeps their order within a cell), and conflicts are
 // classified by looking at the logged accesses of each cell directly.
 //
 // What it computes (Distefano & Dubreil, Sec. 4 "Concrete Semantics" and the
@@ -79,7 +80,12 @@ enum TStatus { RUNNING, AT_BARRIER, EXITED, DEAD };
 struct Thread {
   int node;  // node to execute next (AT_BARRIER: the barrier node)
   TStatus st;
-  std::vector<int32_t> vars;
+};
+
+// One logged access: its cell, the order it was logged in, what it did.
+struct Logged {
+  uint32_t space, wg, addr, order;
+  Access a;
 };
 
 struct Checker {
@@ -92,6 +98,7 @@ struct Checker {
   std::vector<int32_t> global_snap;  // committed global memory
   std::vector<int32_t> local_snap;   // committed local memory, G x local_total
   std::vector<Thread> th;
+  std::vector<int32_t> vars;  // private variables, work-item major: N x cfg.n_vars
   Report rep;
   bool group_scope = false;
   std::map<uint32_t, std::vector<Access>> whole_run;  // group scope: every access to each global cell
@@ -102,7 +109,11 @@ struct Checker {
   // The union of the P reports' race records, in report order, with shard
   // 0's error records is the unsharded report.
   uint32_t shard = 0, n_shards = 1;
-  std::map<Cell, std::pair<uint32_t, int32_t>> pending;  // cell -> (writer, value), other shards' cells
+  // the write to commit of each of other shards' cells: local cells in a map,
+  // global cells in arrays indexed by address (with the list of those touched)
+  std::map<Cell, std::pair<uint32_t, int32_t>> pending;
+  std::vector<uint32_t> pend_writer, pend_touched;
+  std::vector<int32_t> pend_value;
   bool mine(const Cell &c) const {
     if (n_shards == 1) return true;
     const uint32_t h = std::get<2>(c) * 0x9E3779B1u ^ std::get<1>(c) * 0x85EBCA77u ^ std::get<0>(c);
@@ -110,8 +121,9 @@ struct Checker {
   }
   std::vector<int32_t> initial_global;                // global memory before the run
 
-  // per interval
-  std::map<Cell, std::vector<Access>> log;
+  // per interval: every logged access in the order it happened (grouped by
+  // cell at the interval's end, keeping that order within a cell)
+  std::vector<Logged> log;
   std::vector<Record> errors;
 
   int32_t committed(const Cell &c) const {
@@ -143,7 +155,8 @@ struct Checker {
   void run_thread(uint32_t gtid, uint32_t interval) {
     Thread &t = th[gtid];
     const uint32_t wg = gtid / S, tid = gtid % S;
-    Env env{&t.vars, tid, wg, S, G, &mem_len};
+    int32_t *const my_vars = vars.data() + (uint64_t)gtid * cfg.n_vars;
+    Env env{my_vars, tid, wg, S, G, &mem_len};
     std::map<Cell, int32_t> own;  // this thread's writes in this interval
     uint64_t nacc = 0, nwr = 0;
     struct Tally {  // record this thread's counts however the run ends
@@ -171,7 +184,7 @@ struct Checker {
           t.node = k;
           return;
         case N_ASSIGN:
-          t.vars[n.var] = eval(*n.val, env);
+          my_vars[n.var] = eval(*n.val, env);
           break;
         case N_ASSUME:
           if (eval(*n.val, env) == 0) { t.st = DEAD; return; }  // ⊤
@@ -199,16 +212,24 @@ struct Checker {
           if (n.kind == N_STORE) {
             own[c] = val;
             if (mine(c)) {
-              log[c].push_back({gtid, true, val});
-            } else {  // another shard's cell: only what the commit needs
+              log.push_back({std::get<0>(c), std::get<1>(c), std::get<2>(c), (uint32_t)log.size(), {gtid, true, val}});
+            } else if (std::get<0>(c) == 0) {  // another shard's global cell: only what the commit needs
+              const uint32_t addr = std::get<2>(c);
+              if (pend_writer[addr] == 0xFFFFFFFFu) pend_touched.push_back(addr);
+              if (pend_writer[addr] == 0xFFFFFFFFu || gtid >= pend_writer[addr]) {
+                pend_writer[addr] = gtid;
+                pend_value[addr] = val;
+              }
+            } else {  // another shard's local cell
               auto it = pending.find(c);
               if (it == pending.end() || gtid >= it->second.first) pending[c] = {gtid, val};
             }
           } else {
             auto it = own.find(c);
             int32_t v = it != own.end() ? it->second : committed(c);
-            if (mine(c)) log[c].push_back({gtid, false, v});
-            t.vars[n.var] = v;
+            if (mine(c))
+              log.push_back({std::get<0>(c), std::get<1>(c), std::get<2>(c), (uint32_t)log.size(), {gtid, false, v}});
+            my_vars[n.var] = v;
           }
           rep.n_access++;
           nacc++;
@@ -365,9 +386,14 @@ struct Checker {
 
   void run(bool reverse) {
     const uint32_t N = G * S;
-    th.assign(N, Thread{cfg.start, RUNNING, std::vector<int32_t>(cfg.n_vars, 0)});
+    th.assign(N, Thread{cfg.start, RUNNING});
+    vars.assign((uint64_t)N * cfg.n_vars, 0);
     std::vector<char> done(G, 0);  // group scope: groups whose work-items all exited
-    initial_global = global_snap;
+    if (group_scope) initial_global = global_snap;
+    if (n_shards > 1) {
+      pend_writer.assign(global_total, 0xFFFFFFFFu);
+      pend_value.assign(global_total, 0);
+    }
     for (uint32_t interval = 0;; interval++) {
       log.clear();
       errors.clear();
@@ -376,14 +402,48 @@ struct Checker {
         if (th[g].st == RUNNING || th[g].st == AT_BARRIER) run_thread(g, interval);
       }
       rep.n_intervals = interval + 1;
-      // classify every touched cell, in (space, wg, addr) order
-      for (auto &kv : log) classify_cell(interval, kv.first, kv.second);
-      if (group_scope)
-        for (auto &kv : log)
-          if (std::get<0>(kv.first) == 0) {
-            auto &v = whole_run[std::get<2>(kv.first)];
-            v.insert(v.end(), kv.second.begin(), kv.second.end());
-          }
+      // group the interval's accesses by cell, keeping their order within a
+      // cell (a thread's accesses stay in program order); then, cell by cell
+      // in (space, wg, addr) order: classify it, add it to the whole-run
+      // table (group scope), and commit it -- each written cell takes the
+      // last write of its highest-gtid writer (the schedule that runs threads
+      // in gtid order).  Committing here, before the barrier agreement below,
+      // changes nothing: that reads no memory.
+      std::sort(log.begin(), log.end(), [](const Logged &x, const Logged &y) {
+        return std::tie(x.space, x.wg, x.addr, x.order) < std::tie(y.space, y.wg, y.addr, y.order);
+      });
+      std::vector<Access> acc;
+      for (size_t i = 0; i < log.size();) {
+        size_t j = i;
+        acc.clear();
+        for (; j < log.size() && log[j].space == log[i].space && log[j].wg == log[i].wg && log[j].addr == log[i].addr;
+             j++)
+          acc.push_back(log[j].a);
+        const Cell c{log[i].space, log[i].wg, log[i].addr};
+        i = j;
+        classify_cell(interval, c, acc);
+        if (group_scope && std::get<0>(c) == 0) {
+          auto &v = whole_run[std::get<2>(c)];
+          v.insert(v.end(), acc.begin(), acc.end());
+        }
+        bool any = false;
+        uint32_t top = 0;
+        for (const Access &a : acc)
+          if (a.write && (!any || a.gtid > top)) { top = a.gtid; any = true; }
+        if (!any) continue;
+        int32_t v = 0;
+        for (const Access &a : acc)  // a thread's accesses sit in program order
+          if (a.write && a.gtid == top) v = a.value;
+        commit_cell(c, v);
+      }
+      log.clear();
+      for (auto &kv : pending) commit_cell(kv.first, kv.second.second);
+      pending.clear();
+      for (uint32_t addr : pend_touched) {
+        global_snap[addr] = pend_value[addr];
+        pend_writer[addr] = 0xFFFFFFFFu;
+      }
+      pend_touched.clear();
       // barrier agreement (Sec. 4 barrier-release rule): every thread that
       // is still alive must stop at the same barrier, or all must exit
       // (group scope: within each work-group).
@@ -410,21 +470,6 @@ struct Checker {
         return std::tie(a.cls, a.t_a) < std::tie(b.cls, b.t_a);
       });
       interval_errors.insert(interval_errors.end(), errors.begin(), errors.end());
-      // commit: each written cell takes the last write of its highest-gtid
-      // writer (the schedule that runs threads in gtid order).
-      for (auto &kv : log) {
-        bool any = false;
-        uint32_t top = 0;
-        for (const Access &a : kv.second)
-          if (a.write && (!any || a.gtid > top)) { top = a.gtid; any = true; }
-        if (!any) continue;
-        int32_t v = 0;
-        for (const Access &a : kv.second)  // a thread's accesses sit in program order
-          if (a.write && a.gtid == top) v = a.value;
-        commit_cell(kv.first, v);
-      }
-      for (auto &kv : pending) commit_cell(kv.first, kv.second.second);
-      pending.clear();
       if (diverged || !any_barrier) break;
     }
     // report: race records already sorted by (interval, space, wg, addr, cls);
