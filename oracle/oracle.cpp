@@ -98,7 +98,13 @@ struct Checker {
   std::vector<int32_t> global_snap;  // committed global memory
   std::vector<int32_t> local_snap;   // committed local memory, G x local_total
   std::vector<Thread> th;
-  std::vector<int32_t> vars;  // private variables, work-item major: N x cfg.n_vars
+  // Named private variables, work-item major (N x n_named).  The front end's
+  // temporaries (one per array read inside an expression) are written by
+  // their load just before the statement that reads them and never live
+  // across a barrier, so a work-item runs on a scratch copy of all
+  // cfg.n_vars and only the named ones are kept between intervals.
+  uint32_t n_named = 0;
+  std::vector<int32_t> vars, scratch;
   Report rep;
   bool group_scope = false;
   std::map<uint32_t, std::vector<Access>> whole_run;  // group scope: every access to each global cell
@@ -155,7 +161,14 @@ struct Checker {
   void run_thread(uint32_t gtid, uint32_t interval) {
     Thread &t = th[gtid];
     const uint32_t wg = gtid / S, tid = gtid % S;
-    int32_t *const my_vars = vars.data() + (uint64_t)gtid * cfg.n_vars;
+    int32_t *const kept = vars.data() + (uint64_t)gtid * n_named;
+    int32_t *const my_vars = scratch.data();
+    std::copy(kept, kept + n_named, my_vars);
+    struct KeepNamed {  // copy the named variables back however the run ends
+      int32_t *from, *to;
+      uint32_t n;
+      ~KeepNamed() { std::copy(from, from + n, to); }
+    } keep_named{my_vars, kept, n_named};
     Env env{my_vars, tid, wg, S, G, &mem_len};
     std::map<Cell, int32_t> own;  // this thread's writes in this interval
     uint64_t nacc = 0, nwr = 0;
@@ -387,7 +400,9 @@ struct Checker {
   void run(bool reverse) {
     const uint32_t N = G * S;
     th.assign(N, Thread{cfg.start, RUNNING});
-    vars.assign((uint64_t)N * cfg.n_vars, 0);
+    n_named = (uint32_t)prog.vars.size();
+    vars.assign((uint64_t)N * n_named, 0);
+    scratch.assign(std::max<int>(cfg.n_vars, 1), 0);
     std::vector<char> done(G, 0);  // group scope: groups whose work-items all exited
     if (group_scope) initial_global = global_snap;
     if (n_shards > 1) {
