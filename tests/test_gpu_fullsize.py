@@ -67,3 +67,23 @@ def test_stress_instance_full_size(rc):
         key = races[:, 0].astype(np.uint64) << 40 | races[:, 3].astype(np.uint64) << 4 | races[:, 4]
         assert (np.diff(key.astype(np.int64)) > 0).all()  # canonical order, no duplicates
     assert r["status"] in (0, 1, 2)
+
+
+def test_stress_instance_full_size_against_the_oracle(rc):
+    """The full 2^26-work-item report against the oracle's, from the digests
+    tests/golden/make_config5_oracle.py wrote (an address-sharded oracle run):
+    counters, every record and the final memory."""
+    import hashlib
+    import json
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config5_oracle.json")
+    if not os.path.exists(path):
+        pytest.skip("no oracle digest of the full instance")
+    g = json.load(open(path))
+    inst = W.stress_kernel(0)
+    r = rc.check(rc.compile(inst.src), inst.groups, inst.group_size, inst.globals, want_final=True)
+    for k in ("status", "n_intervals", "n_access", "n_global", "n_local"):
+        assert r[k] == g[k], (k, r[k], g[k])
+    recs = np.ascontiguousarray(r["records"].astype(np.uint32))
+    assert len(recs) == g["n_race_records"] + g["n_error_records"]
+    assert hashlib.sha256(recs.tobytes()).hexdigest() == g["records_sha256"]
+    assert hashlib.sha256(np.ascontiguousarray(r["final"]).tobytes()).hexdigest() == g["final_sha256"]
