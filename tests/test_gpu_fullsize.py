@@ -1,7 +1,8 @@
 """Full-size workloads on the GPU: the 10,000-kernel batch (reports of
 sampled kernels against the oracle) and the 2^26-work-item stress instance
-(properties that hold at any size; its shapes up to 16 x 1024 are compared
-with the oracle record by record in test_gpu_parity.py)."""
+(properties that hold at any size, and the oracle's full-size report by
+digest; its shapes up to 16 x 1024 are compared with the oracle record by
+record in test_gpu_parity.py)."""
 import os
 import time
 
