@@ -28,8 +28,9 @@ def rc():
 
 
 def test_batch_of_10000_kernels(rc, oracle):
-    """10,000 kernels of uneven shape in one rc_check_batch call; 12 sampled
-    kernels (and every kernel's counters' sanity) against the oracle."""
+    """10,000 kernels of uneven shape in one rc_check_batch call: 12 sampled
+    kernels against the oracle record by record, every kernel against the
+    oracle's report by digest."""
     insts = W.batch_kernels(0, 10_000, processes=min(16, os.cpu_count() or 1))
     bcs = [rc.compile(i.src) for i in insts]
     t0 = time.perf_counter()
@@ -49,6 +50,20 @@ def test_batch_of_10000_kernels(rc, oracle):
         r = g["records"]
         if len(r):
             assert (r[:, 0] < g["n_intervals"]).all()
+    # every kernel against the oracle's report, by digest
+    # (tests/golden/make_batch_oracle.py wrote them from oracle runs)
+    import hashlib
+    import json
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch10000_oracle.json")
+    if os.path.exists(path):
+        want = json.load(open(path))["kernels"]
+        assert len(want) == len(got)
+        bad = []
+        for k, (g, w) in enumerate(zip(got, want)):
+            digest = hashlib.sha256(np.ascontiguousarray(g["records"].astype(np.uint32)).tobytes()).hexdigest()[:16]
+            if [g["status"], g["n_intervals"], g["n_access"], len(g["records"]), digest] != w:
+                bad.append(k)
+        assert not bad, f"{len(bad)} kernels differ from the oracle, first {bad[:5]}"
 
 
 def test_stress_instance_full_size(rc):
