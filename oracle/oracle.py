@@ -35,7 +35,15 @@ RACE_FREE, RACY, ERROR_OOB, ERROR_ASSERT, ERROR_DIVERGENCE = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so with g++ (plain -O2, no target-specific flags)."""
+    """Compile liboracle.so with g++ (plain -O2, no target-specific flags).
+
+    If the environment names a prebuilt library in ``RC_ORACLE_LIB``, that
+    library is used as it is: the mutation tests build copies of these
+    sources with one planted mistake each and run the pins against them.
+    """
+    override = os.environ.get("RC_ORACLE_LIB")
+    if override:
+        return override
     srcs = [os.path.join(_HERE, s) for s in _SRCS]
     deps = srcs + [os.path.join(_HERE, h) for h in _HDRS]
     if (not force and os.path.exists(_LIB_PATH)

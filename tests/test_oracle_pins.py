@@ -231,6 +231,15 @@ def test_errors_assert_assume_divergence(oracle):
     r = _run(oracle, "if (tid == 0) { barrier; }", 3, [0])
     np.testing.assert_array_equal(r["records"], [rec(0, 0, 18, 0, 0, 0, 0, 1),
                                                  rec(0, 0, 18, 1, 2**32 - 1, 0, 0, 2)])
+    # errors of one interval are ordered by kind, then work-item: work-item 2
+    # stores out of bounds (A[4] of 4 cells), work-item 0 fails the assert;
+    # the failed assert decides the status, the out-of-bounds store is not
+    # performed and not counted
+    r = _run(oracle, "assert(tid != 0);\nA[tid + 2] = 1;", 3, [0] * 4)
+    np.testing.assert_array_equal(r["records"], [rec(0, 4, 16, 2, 0, 0, 0, 0),
+                                                 rec(0, 0, 17, 0, 0, 0, 0, 0)])
+    assert r["status"] == 3 and r["n_access"] == 1
+    np.testing.assert_array_equal(r["final"], [0, 0, 0, 1])
 
 
 def test_local_memory_is_per_group(oracle):
@@ -397,6 +406,11 @@ def test_group_scope_read_of_a_value_held_all_along(oracle):
     # writers 0..3 and 4..7 both: (r0, w1) = (0, 7), and a cross-group WW
     r = _grp(oracle, "A[0] = wg;\nbarrier;\nif (wg == 0) { x = A[0]; }", 2, 4, [0])
     assert _xg(r) == [rec(XG, 0, 4, 0, 7, 4, 8, 12), rec(XG, 0, 6, 0, 7, 4, 8, 12)]
+    # reader 0 alone, writers 1..7 (value 1, read back as 1, 0 before the
+    # run): r0 = 0 and w0 = 1 are different work-items of one group, so the
+    # witness is (r0, w1) = (0, 7); the writes agree: XG_WW_BENIGN (1, 7)
+    r = _grp(oracle, "if (gtid != 0) { A[0] = 1; }\nbarrier;\nif (gtid == 0) { x = A[0]; }", 2, 4, [0])
+    assert _xg(r) == [rec(XG, 0, 5, 1, 7, 1, 7, 8), rec(XG, 0, 6, 0, 7, 1, 7, 8)]
 
 
 def test_group_scope_cross_round_writes(oracle):
