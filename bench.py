@@ -17,6 +17,7 @@ sample of the same instance (first groups only) on the host cores.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -45,15 +46,17 @@ SAMPLE_GROUPS = 96
 #       --clock-control none -k regex:interp_kernel --csv \
 #       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --batch-kernels 0 --proposal-kernels 0
 # (profiles/interp_kernel_large_instance.md).  It holds only for the kernel
-# sources it was taken on; any change to them reports null.
-INTERP_TRAFFIC = {"sources_sha256": "4f54350f0d4294c946d169d3a4a1f5312f2f2ec853bad64e5a34cbdfc0ae7685",
+# sources it was taken on and for the accesses of the bench instance that the
+# pre-filter proves private (those are not logged); a change to either
+# reports null.
+INTERP_TRAFFIC = {"sources_sha256": "097c36c1768c7862ad544a81c1a5a15cf4a8a963d09545da524c11bf94adcbea",
+                  "private_flags_sha256": "fe8aef1429b8b2cb0efc731eae2f5a5cd06da4274efbb49633e030f228d56b2b",
                   "bytes_per_launch": 168407957}
 INTERP_SOURCES = ("paper_1308_3203_gb300/csrc/interp.cu", "paper_1308_3203_gb300/csrc/device.cuh",
-                  "paper_1308_3203_gb300/csrc/semantics.cuh", "paper_1308_3203_gb300/csrc/prove.cpp")
+                  "paper_1308_3203_gb300/csrc/semantics.cuh")
 
 
 def interp_sources_sha256() -> str:
-    import hashlib
     h = hashlib.sha256()
     for f in INTERP_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
@@ -350,8 +353,10 @@ def main():
     p0 = prof[0]
     interp_ms = p0["ms"] / max(p0["launches"], 1)
     achieved = (p0["bytes"] / max(p0["launches"], 1)) / (interp_ms / 1e3) / 1e9 if interp_ms else 0.0
-    traffic = INTERP_TRAFFIC["bytes_per_launch"] \
-        if INTERP_TRAFFIC["sources_sha256"] == interp_sources_sha256() else None
+    priv = np.ascontiguousarray(rc.prove_private(bc, inst.groups, inst.group_size, inst.globals), dtype=np.uint8)
+    same_kernel = (INTERP_TRAFFIC["sources_sha256"] == interp_sources_sha256() and
+                   INTERP_TRAFFIC["private_flags_sha256"] == hashlib.sha256(priv.tobytes()).hexdigest())
+    traffic = INTERP_TRAFFIC["bytes_per_launch"] if same_kernel else None
     roof = {"kernel": "interp_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "algorithmic_bytes_per_launch": p0["bytes"] / max(p0["launches"], 1),
@@ -370,8 +375,7 @@ def main():
                    "strategy": {0: "auto", 1: "sort", 2: "shadow", 3: "resident"}[args.strategy],
                    "run": "resident: one cooperative launch per check" if p0["launches"] == args.steps
                           else "interval by interval",
-                   "private_access_insns": int(rc.prove_private(bc, inst.groups, inst.group_size,
-                                                                inst.globals).sum()),
+                   "private_access_insns": int(priv.sum()),
                    "private_accesses": "counted and committed, not logged (two-work-item pre-filter)",
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

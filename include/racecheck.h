@@ -352,17 +352,32 @@ typedef struct {
 int rc_prove(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in, rc_prove_result *out);
 
 /* Private accesses of the same analysis: flags[pc] = 1 (n_flags >= the
- * bytecode's instruction count) for a load or store none of whose pairs with
- * another work-item's access in a common barrier interval (one of the two a
- * store, same array) can share a cell -- cleared by disjoint index ranges or
- * a one-to-one index, not by equal values.  No other work-item touches the
- * cells such an access touches in its interval, so it is never part of a
- * race or benign record; the checker (owner-table and resident runs) skips
- * logging them and claims only their stores.  This is the analysis the
- * checker runs for every launch shape, without rc_prove's enumeration of
- * small launches.  *n_private = the count. */
+ * bytecode's instruction count) for a load or store whose cells never carry
+ * a race or benign record.  Pairs with another work-item's access in a
+ * common barrier interval (same array) are cleared only by disjoint index
+ * ranges or a one-to-one index, never by equal values.  A store: every pair
+ * with a load or store cleared, so no other work-item touches its cells in
+ * its interval.  A load: every pair with a store cleared, and every pair
+ * with another load L' cleared unless all of L''s pairs with stores are --
+ * other work-items may read its cells, but none of them reads a cell that
+ * a different work-item writes, so a work-item reading back its own store
+ * never meets a reader of that cell.  The checker (owner-table and resident
+ * runs) skips logging these accesses and claims only their stores.  This is
+ * the analysis the checker runs for every launch shape, without rc_prove's
+ * enumeration of small launches.  *n_private = the count. */
 int rc_prove_private(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in,
                      uint8_t *flags, uint32_t n_flags, uint32_t *n_private);
+
+/* The shared-access instructions of a compiled kernel (one per array read
+ * or store of the kernel text, Sec. 3's v:=a[v] and a[v]:=e), in bytecode
+ * order, which is text order: a statement's array reads left to right, an
+ * index before the read that uses it, a store after the reads in its index
+ * and value.  Entry k: pc[k] = the instruction's position (its index into
+ * rc_prove_private's flags), is_store[k], mem[k] = the memory object
+ * (declared order).  The caller owns the arrays; min(cap, count) entries
+ * are written (cap 0: the arrays may be NULL) and *n_sites = count. */
+int rc_access_sites(const rc_bytecode *bc, uint32_t *pc, uint8_t *is_store, uint32_t *mem, uint32_t cap,
+                    uint32_t *n_sites);
 
 /* ---- learned proposal: which candidate instances to check first
  *

@@ -65,6 +65,11 @@ struct Report {
   uint64_t max_acc = 0, max_wr = 0;  // most accesses / writes of one thread in one interval
   std::vector<Record> records;
   std::vector<int32_t> final_global;
+  // trace mode: every performed shared access as (interval, gtid, space, wg,
+  // addr, write, site); site k is the k-th load/store command of the kernel
+  // in text order, sites[k] = (write, memory object)
+  std::vector<uint32_t> trace;
+  std::vector<uint32_t> sites;
 };
 
 struct Access {
@@ -126,6 +131,8 @@ struct Checker {
     return h % n_shards == shard;
   }
   std::vector<int32_t> initial_global;                // global memory before the run
+  bool tracing = false;
+  std::vector<uint32_t> site_of;                       // CFG node -> site ordinal (trace mode)
 
   // per interval: every logged access in the order it happened (grouped by
   // cell at the interval's end, keeping that order within a cell)
@@ -222,6 +229,9 @@ struct Checker {
             return;
           }
           Cell c{(uint32_t)m.space, m.space ? wg : 0u, (uint32_t)(mem_base[n.mem] + (uint64_t)idx)};
+          if (tracing)
+            rep.trace.insert(rep.trace.end(), {interval, gtid, std::get<0>(c), std::get<1>(c), std::get<2>(c),
+                                               n.kind == N_STORE ? 1u : 0u, site_of[k]});
           if (n.kind == N_STORE) {
             own[c] = val;
             if (mine(c)) {
@@ -404,6 +414,16 @@ struct Checker {
     vars.assign((uint64_t)N * n_named, 0);
     scratch.assign(std::max<int>(cfg.n_vars, 1), 0);
     std::vector<char> done(G, 0);  // group scope: groups whose work-items all exited
+    if (tracing) {  // CFG nodes are created in text order, so their ids order the sites
+      site_of.assign(cfg.nodes.size(), 0xFFFFFFFFu);
+      for (size_t k = 0; k < cfg.nodes.size(); k++) {
+        const Node &nd = cfg.nodes[k];
+        if (nd.kind != N_LOAD && nd.kind != N_STORE) continue;
+        site_of[k] = (uint32_t)(rep.sites.size() / 2);
+        rep.sites.push_back(nd.kind == N_STORE ? 1u : 0u);
+        rep.sites.push_back((uint32_t)nd.mem);
+      }
+    }
     if (group_scope) initial_global = global_snap;
     if (n_shards > 1) {
       pend_writer.assign(global_total, 0xFFFFFFFFu);
@@ -523,8 +543,9 @@ extern "C" {
 // Run the checker.  global_len/global_init give one int32 array per `global`
 // declaration, in declaration order.  mode bit 0 runs the threads of every
 // interval in descending gtid order (the report must not change); bit 1
-// takes barriers as work-group scoped; bits 8-19 / 20-31 give the shard p
-// and the shard count P (0: unsharded) of an address-sharded run.
+// takes barriers as work-group scoped; bit 2 records the access trace;
+// bits 8-19 / 20-31 give the shard p and the shard count P (0: unsharded)
+// of an address-sharded run.
 // Returns 0 on success, 1 on a parse error (message in err), 2 on a bad
 // launch shape or input.
 int oracle_check(const char *src, uint32_t groups, uint32_t group_size, uint32_t n_global,
@@ -565,6 +586,7 @@ int oracle_check(const char *src, uint32_t groups, uint32_t group_size, uint32_t
     }
     ck.local_snap.assign((uint64_t)groups * ck.local_total, 0);
     ck.group_scope = (mode & 2) != 0;
+    ck.tracing = (mode & 4) != 0;
     const uint32_t shards = ((uint32_t)mode >> 20) & 0xFFFu;
     if (shards > 1) {
       ck.n_shards = shards;
@@ -595,6 +617,10 @@ uint64_t oracle_n_records(void *h) { return ((OracleHandle *)h)->rep.records.siz
 const void *oracle_records(void *h) { return ((OracleHandle *)h)->rep.records.data(); }
 uint64_t oracle_final_len(void *h) { return ((OracleHandle *)h)->rep.final_global.size(); }
 const int32_t *oracle_final(void *h) { return ((OracleHandle *)h)->rep.final_global.data(); }
+uint64_t oracle_trace_len(void *h) { return ((OracleHandle *)h)->rep.trace.size() / 7; }
+const uint32_t *oracle_trace(void *h) { return ((OracleHandle *)h)->rep.trace.data(); }
+uint64_t oracle_n_sites(void *h) { return ((OracleHandle *)h)->rep.sites.size() / 2; }
+const uint32_t *oracle_sites(void *h) { return ((OracleHandle *)h)->rep.sites.data(); }
 void oracle_free(void *h) { delete (OracleHandle *)h; }
 
 }  // extern "C"

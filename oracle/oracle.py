@@ -72,7 +72,8 @@ def _load():
                          ("oracle_n_local", u64), ("oracle_n_records", u64),
                          ("oracle_max_acc", u64), ("oracle_max_wr", u64),
                          ("oracle_records", vp), ("oracle_final_len", u64),
-                         ("oracle_final", vp)]:
+                         ("oracle_final", vp), ("oracle_trace_len", u64), ("oracle_trace", vp),
+                         ("oracle_n_sites", u64), ("oracle_sites", vp)]:
             getattr(lib, name).restype = rt
             getattr(lib, name).argtypes = [vp]
         lib.oracle_free.argtypes = [vp]
@@ -113,7 +114,7 @@ def _marshal(globals_):
 
 
 def check(src: str, groups: int, group_size: int, globals_, reverse: bool = False,
-          group_barriers: bool = False, shard: tuple = (0, 1)) -> dict:
+          group_barriers: bool = False, shard: tuple = (0, 1), trace: bool = False) -> dict:
     """Run the reference checker on one instance.
 
     ``globals_`` is one int32 array per ``global`` declaration, in order.
@@ -123,13 +124,16 @@ def check(src: str, groups: int, group_size: int, globals_, reverse: bool = Fals
     the full one; only shard 0 reports errors); ``check_sharded`` merges.
     Returns dict(status, n_intervals, n_access, n_global, n_local,
     records (uint32 [n, 10]), final (int32, all global arrays concatenated)).
+    ``trace`` adds every performed shared access, trace (uint32 [n, 7]:
+    interval, gtid, space, wg, addr, write, site), and sites (uint32 [k, 2]:
+    write, memory object of the k-th load/store command in text order).
     """
     lib = _load()
     arrs, n, lens, ptrs = _marshal(globals_)
     h = ctypes.c_void_p()
     err = ctypes.create_string_buffer(512)
     rc = lib.oracle_check(src.encode(), groups, group_size, n, lens, ptrs,
-                          (1 if reverse else 0) | (2 if group_barriers else 0) |
+                          (1 if reverse else 0) | (2 if group_barriers else 0) | (4 if trace else 0) |
                           ((shard[0] << 8) | (shard[1] << 20) if shard[1] > 1 else 0),
                           ctypes.byref(h), err, 512)
     if rc != 0:
@@ -143,10 +147,19 @@ def check(src: str, groups: int, group_size: int, globals_, reverse: bool = Fals
         fin = np.zeros(nfin, dtype=np.int32)
         if nfin:
             ctypes.memmove(fin.ctypes.data, lib.oracle_final(h), nfin * 4)
-        return dict(status=lib.oracle_status(h), n_intervals=lib.oracle_n_intervals(h),
-                    n_access=lib.oracle_n_access(h), n_global=lib.oracle_n_global(h),
-                    n_local=lib.oracle_n_local(h), records=recs, final=fin,
-                    max_acc=lib.oracle_max_acc(h), max_wr=lib.oracle_max_wr(h))
+        out = dict(status=lib.oracle_status(h), n_intervals=lib.oracle_n_intervals(h),
+                   n_access=lib.oracle_n_access(h), n_global=lib.oracle_n_global(h),
+                   n_local=lib.oracle_n_local(h), records=recs, final=fin,
+                   max_acc=lib.oracle_max_acc(h), max_wr=lib.oracle_max_wr(h))
+        if trace:
+            nt, ns = lib.oracle_trace_len(h), lib.oracle_n_sites(h)
+            out["trace"] = np.zeros((nt, 7), dtype=np.uint32)
+            out["sites"] = np.zeros((ns, 2), dtype=np.uint32)
+            if nt:
+                ctypes.memmove(out["trace"].ctypes.data, lib.oracle_trace(h), nt * 28)
+            if ns:
+                ctypes.memmove(out["sites"].ctypes.data, lib.oracle_sites(h), ns * 8)
+        return out
     finally:
         lib.oracle_free(h)
 

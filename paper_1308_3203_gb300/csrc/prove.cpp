@@ -609,12 +609,22 @@ struct Prover {
 namespace rc {
 
 // The pre-filter over one launch shape.  out: the verdicts (see rc_prove);
-// priv (if not null, one byte per instruction): 1 for a load or store every
-// pair of which, with any access by another work-item that may meet it in a
-// barrier interval (one of the two a store, same array), is cleared by
-// disjoint cells or a one-to-one index (or cannot happen): no other
-// work-item touches the cells it touches in its interval, so it can never
-// be part of a race or benign record.
+// priv (if not null, one byte per instruction): 1 for a load or store that
+// shares no cell with another work-item in its barrier interval, so that
+// the cells it touches never carry a race or benign record:
+//  * a store: every pair with an access of the same array that may meet it
+//    in an interval (its own instruction included, run by another
+//    work-item) is cleared by disjoint cells or a one-to-one index (or
+//    cannot happen);
+//  * a load: likewise every pair with a store; and no pair with another
+//    load L' left open where L' itself has a store pair left open.
+//    Otherwise a work-item t could read back its own store of a cell c
+//    while another work-item reads c through L': the writers of c are then
+//    {t} (the load's store pairs are cleared), but the cell carries a
+//    read/write record that counts t's read.  If every load L' that may
+//    meet the load has its store pairs cleared, no work-item reads a cell
+//    another one writes through L', so no such record exists.
+//  Equal values never clear a pair here.
 // enum_budget: how many (work-item, loop counter) points the exact check of
 // small launches may enumerate in all (0: none).
 void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const std::vector<uint32_t> &lens,
@@ -657,12 +667,15 @@ void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const
     const Range r = range_of(a.idx, a.box);
     if (a.idx.kind != AF::AFF || r.lo < 0 || r.hi >= (int64_t)lens[a.mem]) out->in_bounds = 0;
   }
+  std::vector<std::pair<uint32_t, uint32_t>> open_reads;  // load pairs that may share a cell
   for (size_t i = 0; i < acc.size(); i++)
     for (size_t j = i; j < acc.size(); j++) {
       const Acc &a = acc[i], &b = acc[j];
-      if (a.mem != b.mem || (!a.store && !b.store)) continue;
+      if (a.mem != b.mem) continue;
       if (!(pr.region[a.pc] & pr.region[b.pc])) continue;
-      out->n_pairs++;
+      const bool reads = !a.store && !b.store;
+      if (reads && !priv) continue;
+      if (!reads) out->n_pairs++;
       const Shape h = hull(a.box, b.box);
       // nobody executes one of them, or one work-item (per group, for local arrays) executes both
       bool ok = a.box.empty() || b.box.empty() || (h.nt() == 1 && (a.local || h.nw() == 1));
@@ -672,6 +685,10 @@ void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const
         ok = ok || (a.idx == b.idx && injective(a.idx, h, a.local));  // only with itself
         // small launches: every work-item's cells, enumerated
         ok = ok || (budget && never_meet(a.idx, a.box, b.idx, b.box, i == j, a.local, &budget) == 1);
+      }
+      if (reads) {
+        if (!ok && i != j) open_reads.push_back({a.pc, b.pc});
+        continue;
       }
       if (!ok && priv) (*priv)[a.pc] = (*priv)[b.pc] = 0;  // the two may share a cell
       if (!ok && a.store && b.store && a.val.kind == AF::AFF && b.val.kind == AF::AFF) {
@@ -687,6 +704,13 @@ void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const
         out->n_unresolved++;
       }
     }
+  if (priv) {
+    const std::vector<uint8_t> store_pairs_clear = *priv;
+    for (const auto &rr : open_reads) {
+      if (!store_pairs_clear[rr.second]) (*priv)[rr.first] = 0;
+      if (!store_pairs_clear[rr.first]) (*priv)[rr.second] = 0;
+    }
+  }
 }
 
 // per memory object: the input's length (global) or the declared one (local)
@@ -739,5 +763,28 @@ extern "C" int rc_prove_private(const rc_bytecode *bc, uint32_t groups, uint32_t
     n += priv[k];
   }
   *n_private = n;
+  return RC_OK;
+}
+
+extern "C" int rc_access_sites(const rc_bytecode *bc, uint32_t *pc, uint8_t *is_store, uint32_t *mem, uint32_t cap,
+                               uint32_t *n_sites) {
+  using namespace rc;
+  if (!bc || !n_sites || (cap && (!pc || !is_store || !mem))) {
+    set_last_error("null argument");
+    return RC_E_INVALID;
+  }
+  uint32_t n = 0;
+  for (uint32_t k = 0; k < bc->prog.code.size(); k++) {
+    const Insn &ins = bc->prog.code[k];
+    const uint32_t cls = insn_class(ins);
+    if (cls != CC_LD && cls != CC_ST) continue;
+    if (n < cap) {
+      pc[n] = k;
+      is_store[n] = cls == CC_ST;
+      mem[n] = ins.ctl >> CTL_MEM_SHIFT;
+    }
+    n++;
+  }
+  *n_sites = n;
   return RC_OK;
 }

@@ -156,7 +156,10 @@ def load() -> ctypes.CDLL:
         lib.rc_prove_private.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input),
                                          ctypes.POINTER(ctypes.c_uint8), ctypes.c_uint32,
                                          ctypes.POINTER(ctypes.c_uint32)]
-        for f in ("rc_prove", "rc_prove_private", "rc_mlp_set_backend", "rc_mlp_backend_error", "rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
+        lib.rc_access_sites.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint8),
+                                        ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
+                                        ctypes.POINTER(ctypes.c_uint32)]
+        for f in ("rc_prove", "rc_prove_private", "rc_access_sites", "rc_mlp_set_backend", "rc_mlp_backend_error", "rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
                   "rc_mlp_forward", "rc_mlp_grad", "rc_mlp_train", "rc_search"):
             getattr(lib, f).restype = c_int
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
@@ -402,8 +405,10 @@ def prove(bc: Bytecode, groups: int, group_size: int, globals_) -> dict:
 
 def prove_private(bc: Bytecode, groups: int, group_size: int, globals_) -> np.ndarray:
     """Per bytecode instruction: 1 where the pre-filter proves the load or
-    store private for this launch shape (no other work-item touches its
-    cells in its interval), else 0 (host only)."""
+    store private for this launch shape (its cells carry no race or benign
+    record in its interval: no other work-item touches a private store's
+    cells, none writes a private load's cells, and no other work-item reads
+    a private load's cell that a different one writes), else 0 (host only)."""
     inp, keep = _marshal(globals_, None, False)
     n_insn = bc.info()["n_insn"]
     flags = np.zeros(max(n_insn, 1), np.uint8)
@@ -414,6 +419,26 @@ def prove_private(bc: Bytecode, groups: int, group_size: int, globals_) -> np.nd
     if rc:
         _raise(rc)
     return flags[:n_insn]
+
+
+def access_sites(bc: Bytecode) -> np.ndarray:
+    """The kernel's shared-access instructions in bytecode (= text) order:
+    uint32 [n, 3] rows (pc, is_store, memory object) (host only)."""
+    lib = load()
+    n = ctypes.c_uint32()
+    rc = lib.rc_access_sites(bc.handle, None, None, None, 0, ctypes.byref(n))
+    if rc:
+        _raise(rc)
+    pc = np.zeros(max(n.value, 1), np.uint32)
+    st = np.zeros(max(n.value, 1), np.uint8)
+    mem = np.zeros(max(n.value, 1), np.uint32)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    rc = lib.rc_access_sites(bc.handle, pc.ctypes.data_as(u32p), st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                             mem.ctypes.data_as(u32p), n.value, ctypes.byref(n))
+    if rc:
+        _raise(rc)
+    k = n.value
+    return np.stack([pc[:k], st[:k].astype(np.uint32), mem[:k]], axis=1)
 
 
 def explore(bc: Bytecode, groups: int, group_size: int, globals_, max_states: int = 0,

@@ -136,6 +136,12 @@ EDGE = [
      2, 64, [np.zeros(128, np.int32)]),
     ("kernel e(global int A[]) { x = 2147483647; A[tid] = x + tid; A[tid + 4] = -2147483648 / -1; "
      "A[tid + 8] = -7 % 3; A[tid + 12] = 7 / 0; }", 1, 4, [np.zeros(16, np.int32)]),
+    # a work-item reads back its own store while its neighbour reads the
+    # same cell: the read-back is logged (the cell's read/write record counts it)
+    ("kernel e(global int A[]) { A[gtid] = 1; x = A[gtid]; y = A[(gtid + 1) % size(A)]; }",
+     2, 64, [np.zeros(128, np.int32)]),
+    ("kernel e(global int A[], local int L[64]) { L[tid] = tid; x = L[tid]; y = L[(tid + 1) % 64]; "
+     "A[gtid] = x + y; }", 2, 64, [np.zeros(128, np.int32)]),
 ]
 
 

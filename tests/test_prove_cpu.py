@@ -203,6 +203,13 @@ PRIVATE = [
     # the checker's analysis does not enumerate work-items: the permutation
     # rc_prove shows race-free stays shared here
     ("kernel k(global int A[]) { A[(3 * tid) % 8] = tid; }", 1, 8, (8,), [0]),
+    # work-item t reads back its own store of A[t] while t - 1 reads A[t]:
+    # cell t carries a read/write record whose readers include t, so the
+    # read-back is not private although no other work-item writes A[t]
+    ("kernel k(global int A[]) {\n A[gtid] = 1;\n x = A[gtid];\n y = A[(gtid + 1) % 8];\n}", 1, 8, (8,),
+     [0, 0, 0]),
+    # the same read-back with no other reader of the cell: all private
+    ("kernel k(global int A[]) {\n A[gtid] = 1;\n x = A[gtid];\n y = A[gtid];\n}", 1, 8, (8,), [1, 1, 1]),
 ]
 
 
@@ -231,3 +238,61 @@ def test_bench_kernel_has_private_accesses(rc):
     inst = W.large_kernel(0)
     f = rc.prove_private(rc.compile(inst.src), inst.groups, inst.group_size, inst.globals)
     assert f.sum() >= 50
+
+
+def _private_accesses_hold(rc, oracle, inst):
+    """Checks one instance against the oracle's access trace; returns how
+    many of its performed accesses were private."""
+    bc = rc.compile(inst.src)
+    sites = rc.access_sites(bc)
+    flags = rc.prove_private(bc, inst.groups, inst.group_size, inst.globals)
+    r = oracle.check(inst.src, inst.groups, inst.group_size, inst.globals, trace=True)
+    # both front ends number the kernel's load/store commands in text order
+    np.testing.assert_array_equal(sites[:, 1:], r["sites"], err_msg=inst.name)
+    t = r["trace"]
+    if not len(t):
+        return 0
+    priv = flags[sites[:, 0]][t[:, 6]] == 1
+    store = t[:, 5] == 1
+    gtid = t[:, 1].astype(np.int64)
+    _, cell = np.unique(t[:, [0, 2, 3, 4]], axis=0, return_inverse=True)
+    cell = cell.ravel()
+    n = int(cell.max()) + 1
+    lo = np.full(n, np.iinfo(np.int64).max)
+    hi = np.full(n, -1)
+    np.minimum.at(lo, cell, gtid)
+    np.maximum.at(hi, cell, gtid)
+    wlo = np.full(n, np.iinfo(np.int64).max)
+    whi = np.full(n, -1)
+    np.minimum.at(wlo, cell[store], gtid[store])
+    np.maximum.at(whi, cell[store], gtid[store])
+    # a private store: no other work-item touches the cell in the interval
+    bad = priv & store & ((lo[cell] != gtid) | (hi[cell] != gtid))
+    assert not bad.any(), (inst.name, t[bad][:4])
+    # a private load: no other work-item writes the cell in the interval
+    bad = priv & ~store & (whi[cell] >= 0) & ((wlo[cell] != gtid) | (whi[cell] != gtid))
+    assert not bad.any(), (inst.name, t[bad][:4])
+    # and no private access lies on a cell that carries a race or benign record
+    recs = r["records"]
+    recs = recs[(recs[:, 4] >= 1) & (recs[:, 4] <= 3)]
+    on = {tuple(int(v) for v in x) for x in recs[:, [0, 1, 2, 3]]}
+    hits = [tuple(int(v) for v in x) in on for x in t[priv][:, [0, 2, 3, 4]]]
+    assert not any(hits), inst.name
+    return int(priv.sum())
+
+
+def test_private_accesses_against_the_oracle_trace(rc, oracle):
+    """The private flags the checker uses, against every access the oracle's
+    run performs: on a private access's cell in its interval, no other
+    work-item stores (for a private store: touches) it, and no race or
+    benign record lies there, so leaving the access out of the log changes
+    no record.  The generated families, the hand cases and the bench
+    statement mix at a small shape."""
+    n_priv = 0
+    insts = [inst for _, inst in families()]
+    insts += [W.large_kernel(s, groups=2, group_size=64, global_len=8192, local_len=128) for s in range(4)]
+    for src, G, S, lens, _ in PRIVATE:
+        insts.append(W.Instance(name=src, src=src, groups=G, group_size=S, globals=zeros(*lens)))
+    for inst in insts:
+        n_priv += _private_accesses_hold(rc, oracle, inst)
+    assert n_priv > 10000
