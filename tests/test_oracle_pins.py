@@ -345,6 +345,59 @@ def test_bruteforce_schedules(oracle, chunk):
     assert seen["free"] and seen["rw"], seen
 
 
+# ---------------------------------------------------------------- interleaving product of two work-items
+# The explorer's pair mode runs two work-items over every schedule while the
+# others stay where the interval started (it is compared with the GPU's).
+
+def test_pair_product_fig2(oracle):
+    """Fig. 2, n = 4, pairs in order (0,1) (0,2) (0,3) (1,2) (1,3) (2,3).
+    Interval 0: writes only, one end state per pair.  Interval 1: in a pair
+    (k, k+1), k reads A[k+1] before or after k+1 writes it (a read that
+    depends on the schedule); only for (2, 3) does that change memory, since
+    work-item 3 reads A[4] = 1 and leaves g alone, while in (0, 1) and
+    (1, 2) the second work-item reads its frozen neighbour's 0 and sets g = 1
+    anyway.  Interval 2 starts from g = 0 or g = 1: no pair result."""
+    g = golden.load("fig2_n4.txt")
+    r = oracle.explore_pairs(g["src"], g["groups"], g["group_size"], g["globals"])
+    assert r[0] == [(1, False)] * 6
+    assert r[1] == [(1, True), (1, False), (1, False), (1, True), (1, False), (2, True)]
+    assert r[2] is None
+
+
+@pytest.mark.parametrize("S", [3, 4, 5])
+def test_pair_product_neighbour_copy(oracle, S):
+    """Each work-item copies its right neighbour's cell, which the neighbour
+    overwrites in the same interval: exactly the pairs (t, t + 1) reach two
+    memories and a schedule-dependent read; any other pair reads a cell of a
+    work-item that does not run.  (Work-item S - 1 reads A[S], where work-item
+    0 stores its copy; in the pair (0, S - 1) that copy is of a frozen cell,
+    0, the value A[S] already holds.  With S = 2 the pair (0, 1) is both.)"""
+    src = f"kernel k(global int A[]) {{ A[tid] = 0; barrier; A[tid] = 1; x = A[tid + 1]; A[tid + {S}] = x; }}"
+    r = oracle.explore_pairs(src, 1, S, [np.zeros(2 * S, np.int32)])
+    pairs = [(i, j) for i in range(S) for j in range(i + 1, S)]
+    assert r[0] == [(1, False)] * len(pairs)
+    assert r[1] == [(2, True) if j == i + 1 else (1, False) for i, j in pairs]
+
+
+def test_bruteforce_pair_product_of_two_work_items(oracle):
+    """With two work-items the only pair is the whole instance, so the pair
+    mode must agree with the full interleaving search interval by interval
+    (as long as the interval starts from one state)."""
+    n = 0
+    for seed in range(300):
+        i = W.tiny_kernel(seed)
+        if i.n_threads != 2:
+            continue
+        full = oracle.explore(i.src, i.groups, i.group_size, i.globals)
+        pairs = oracle.explore_pairs(i.src, i.groups, i.group_size, i.globals)
+        for k, p in enumerate(pairs):
+            if p is None:
+                break
+            assert p == [(full["end_states"][k], full["deviated"][k])], (seed, k, i.src)
+            n += 1
+    assert n >= 50
+
+
 # ---------------------------------------------------------------- work-group-scoped barriers
 # Closed forms for the cross-group classification of the whole run and the
 # per-group barrier-release rule (OpenCL barriers wait for their own group
