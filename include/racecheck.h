@@ -379,6 +379,22 @@ int rc_prove_private(const rc_bytecode *bc, uint32_t groups, uint32_t group_size
 int rc_access_sites(const rc_bytecode *bc, uint32_t *pc, uint8_t *is_store, uint32_t *mem, uint32_t cap,
                     uint32_t *n_sites);
 
+/* The kernel translated into C++ source text (the thread-local rules of
+ * Sec. 4 for one work-item, compiled instead of interpreted): one function
+ *   RC_JIT_FN void fn_name(RC_JIT_CTX &cx, int32_t (&r)[n_regs],
+ *                          uint32_t &pc, uint32_t &st)
+ * that runs a work-item from pc (0, or the instruction after a barrier) to
+ * its next barrier (st = 1, pc = where to resume), its exit (st = 2) or its
+ * end (st = 3: a failed assume or assert, an out-of-bounds access); r[0..4]
+ * hold tid, wg, gtid, group size and group count.  Shared memory is reached
+ * through hooks the including code defines (RC_LD, RC_ST, RC_SIZE,
+ * RC_ASSERT_FAIL, RC_AT_BARRIER; see translate.cpp), and the text calls
+ * rc::sem_div, rc::sem_mod and rc::sem_index.  fn_name must be a C
+ * identifier.  Writes min(len, cap - 1) bytes and a NUL into buf (cap 0:
+ * buf may be NULL); *len = the text's length.  The text compiles as CUDA
+ * C++ and as plain C++. */
+int rc_translate(const rc_bytecode *bc, const char *fn_name, char *buf, size_t cap, size_t *len);
+
 /* ---- learned proposal: which candidate instances to check first
  *
  * The method needs, per kernel, a set of candidate instances (launch shape

@@ -66,8 +66,9 @@ struct Report {
   std::vector<Record> records;
   std::vector<int32_t> final_global;
   // trace mode: every performed shared access as (interval, gtid, space, wg,
-  // addr, write, site); site k is the k-th load/store command of the kernel
-  // in text order, sites[k] = (write, memory object)
+  // addr, write, site, value: stored or loaded); site k is the k-th
+  // load/store command of the kernel in text order, sites[k] = (write,
+  // memory object)
   std::vector<uint32_t> trace;
   std::vector<uint32_t> sites;
 };
@@ -229,9 +230,10 @@ struct Checker {
             return;
           }
           Cell c{(uint32_t)m.space, m.space ? wg : 0u, (uint32_t)(mem_base[n.mem] + (uint64_t)idx)};
+          const size_t at = rep.trace.size();
           if (tracing)
             rep.trace.insert(rep.trace.end(), {interval, gtid, std::get<0>(c), std::get<1>(c), std::get<2>(c),
-                                               n.kind == N_STORE ? 1u : 0u, site_of[k]});
+                                               n.kind == N_STORE ? 1u : 0u, site_of[k], (uint32_t)val});
           if (n.kind == N_STORE) {
             own[c] = val;
             if (mine(c)) {
@@ -250,6 +252,7 @@ struct Checker {
           } else {
             auto it = own.find(c);
             int32_t v = it != own.end() ? it->second : committed(c);
+            if (tracing) rep.trace[at + 7] = (uint32_t)v;
             if (mine(c))
               log.push_back({std::get<0>(c), std::get<1>(c), std::get<2>(c), (uint32_t)log.size(), {gtid, false, v}});
             my_vars[n.var] = v;
@@ -617,7 +620,7 @@ uint64_t oracle_n_records(void *h) { return ((OracleHandle *)h)->rep.records.siz
 const void *oracle_records(void *h) { return ((OracleHandle *)h)->rep.records.data(); }
 uint64_t oracle_final_len(void *h) { return ((OracleHandle *)h)->rep.final_global.size(); }
 const int32_t *oracle_final(void *h) { return ((OracleHandle *)h)->rep.final_global.data(); }
-uint64_t oracle_trace_len(void *h) { return ((OracleHandle *)h)->rep.trace.size() / 7; }
+uint64_t oracle_trace_len(void *h) { return ((OracleHandle *)h)->rep.trace.size() / 8; }
 const uint32_t *oracle_trace(void *h) { return ((OracleHandle *)h)->rep.trace.data(); }
 uint64_t oracle_n_sites(void *h) { return ((OracleHandle *)h)->rep.sites.size() / 2; }
 const uint32_t *oracle_sites(void *h) { return ((OracleHandle *)h)->rep.sites.data(); }

@@ -124,9 +124,10 @@ def check(src: str, groups: int, group_size: int, globals_, reverse: bool = Fals
     the full one; only shard 0 reports errors); ``check_sharded`` merges.
     Returns dict(status, n_intervals, n_access, n_global, n_local,
     records (uint32 [n, 10]), final (int32, all global arrays concatenated)).
-    ``trace`` adds every performed shared access, trace (uint32 [n, 7]:
-    interval, gtid, space, wg, addr, write, site), and sites (uint32 [k, 2]:
-    write, memory object of the k-th load/store command in text order).
+    ``trace`` adds every performed shared access, trace (uint32 [n, 8]:
+    interval, gtid, space, wg, addr, write, site, value stored or loaded as
+    uint32), and sites (uint32 [k, 2]: write, memory object of the k-th
+    load/store command in text order).
     """
     lib = _load()
     arrs, n, lens, ptrs = _marshal(globals_)
@@ -153,10 +154,10 @@ def check(src: str, groups: int, group_size: int, globals_, reverse: bool = Fals
                    max_acc=lib.oracle_max_acc(h), max_wr=lib.oracle_max_wr(h))
         if trace:
             nt, ns = lib.oracle_trace_len(h), lib.oracle_n_sites(h)
-            out["trace"] = np.zeros((nt, 7), dtype=np.uint32)
+            out["trace"] = np.zeros((nt, 8), dtype=np.uint32)
             out["sites"] = np.zeros((ns, 2), dtype=np.uint32)
             if nt:
-                ctypes.memmove(out["trace"].ctypes.data, lib.oracle_trace(h), nt * 28)
+                ctypes.memmove(out["trace"].ctypes.data, lib.oracle_trace(h), nt * 32)
             if ns:
                 ctypes.memmove(out["sites"].ctypes.data, lib.oracle_sites(h), ns * 8)
         return out

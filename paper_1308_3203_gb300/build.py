@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libracecheck.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}"]
 SOURCES = ["compiler.cpp", "features.cpp", "prove.cpp", "interp.cu", "sort.cu", "classify.cu", "shadow.cu", "runtime.cu",
-           "noalloc.cu", "batch.cu", "mlp.cu", "explore.cu", "xgroup.cu"]
+           "noalloc.cu", "batch.cu", "mlp.cu", "explore.cu", "xgroup.cu", "translate.cpp"]
 
 
 def _nvcc() -> str:

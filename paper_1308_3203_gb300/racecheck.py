@@ -159,7 +159,9 @@ def load() -> ctypes.CDLL:
         lib.rc_access_sites.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint8),
                                         ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
                                         ctypes.POINTER(ctypes.c_uint32)]
-        for f in ("rc_prove", "rc_prove_private", "rc_access_sites", "rc_mlp_set_backend", "rc_mlp_backend_error", "rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
+        lib.rc_translate.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_size_t,
+                                     ctypes.POINTER(ctypes.c_size_t)]
+        for f in ("rc_prove", "rc_prove_private", "rc_access_sites", "rc_translate", "rc_mlp_set_backend", "rc_mlp_backend_error", "rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
                   "rc_mlp_forward", "rc_mlp_grad", "rc_mlp_train", "rc_search"):
             getattr(lib, f).restype = c_int
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
@@ -439,6 +441,21 @@ def access_sites(bc: Bytecode) -> np.ndarray:
         _raise(rc)
     k = n.value
     return np.stack([pc[:k], st[:k].astype(np.uint32), mem[:k]], axis=1)
+
+
+def translate(bc: Bytecode, fn_name: str = "rc_jit_run") -> str:
+    """The kernel as C++ source text: one function that runs one work-item
+    to its next barrier, exit or end (host only)."""
+    lib = load()
+    n = ctypes.c_size_t()
+    rc = lib.rc_translate(bc.handle, fn_name.encode(), None, 0, ctypes.byref(n))
+    if rc:
+        _raise(rc)
+    buf = ctypes.create_string_buffer(n.value + 1)
+    rc = lib.rc_translate(bc.handle, fn_name.encode(), buf, n.value + 1, ctypes.byref(n))
+    if rc:
+        _raise(rc)
+    return buf.value.decode()
 
 
 def explore(bc: Bytecode, groups: int, group_size: int, globals_, max_states: int = 0,
