@@ -89,3 +89,23 @@ def test_bf16_points_stay_close_to_exact():
     a, _ = M.forward(p, X, bf16_points=True)
     b, _ = M.forward(p, X, bf16_points=False, dtype=np.float64)
     assert np.max(np.abs(a - b)) < 0.02
+
+
+def test_bf16_rounding_points_on_one_path():
+    """The one-unit path with hidden biases 2^-9 and x_0 = 1 + 2^-8.  At the
+    BF16 points the input, the weights and every hidden activation are
+    rounded to bfloat16 (biases stay float32; the bfloat16 spacing at 1 is
+    2^-7): x_0 is a tie between 1 and 1 + 2^-7 and goes to the even 1, and
+    each hidden value 1 + 2^-9 rounds back to 1, so the score is
+    sigmoid(1 + b4).  Without rounding it is sigmoid(1 + 2^-8 + 3 * 2^-9 + b4)."""
+    d = {k: np.zeros(s) for k, s in M.SIZES}
+    d["W1"][0, 0] = d["W2"][0, 0] = d["W3"][0, 0] = d["w4"][0] = 1
+    d["b1"][0] = d["b2"][0] = d["b3"][0] = 2.0 ** -9
+    d["b4"][0] = -0.25
+    p = M.pack(d)
+    X = np.zeros((1, M.IN))
+    X[0, 0] = 1 + 2.0 ** -8
+    a, _ = M.forward(p, X, bf16_points=True)
+    assert a[0] == pytest.approx(1 / (1 + np.exp(-0.75)), rel=1e-6)
+    b, _ = M.forward(p, X, bf16_points=False, dtype=np.float64)
+    assert b[0] == pytest.approx(1 / (1 + np.exp(-(0.75 + 2.0 ** -8 + 3 * 2.0 ** -9))), rel=1e-14)

@@ -209,3 +209,66 @@ def test_planted_mistake_fails_a_pin(outcomes, name):
     # 1: some pin failed (2-5 would be an interrupted run or a harness error)
     assert rc == 1, (name, rc, out)
     assert " failed" in out, out
+
+
+# ---- the ranking network's reference (oracle/mlp_ref.py) against its pins
+# (tests/test_mlp_ref.py: finite differences, closed forms, torch's bfloat16
+# rounding)
+MLP_MUTANTS = {
+    "control": [],
+    "relu_derivative_always_one": [('dz = rnd(np.outer(dl, c["w4"]) * (c["h"][3] > 0))',
+                                    'dz = rnd(np.outer(dl, c["w4"]) * (c["h"][3] >= 0))')],
+    "backward_through_transposed_weights": [('dz = rnd((dz @ c["W"][l]) * (c["h"][l] > 0))',
+                                             'dz = rnd((dz @ c["W"][l].T) * (c["h"][l] > 0))')],
+    "bias_gradient_averaged_twice": [('g[f"b{l + 1}"] = dz.sum(axis=0)', 'g[f"b{l + 1}"] = dz.mean(axis=0)')],
+    "weight_gradient_from_wrong_layer": [('g = {"w4": dl @ c["h"][3]', 'g = {"w4": dl @ c["h"][2]')],
+    "loss_without_softplus_term": [("loss = np.mean(np.maximum(z, 0) + np.log1p(np.exp(-np.abs(z))) - y * z)",
+                                    "loss = np.mean(np.maximum(z, 0) - y * z)")],
+    "sigmoid_sign_flipped": [("prob = 1.0 / (1.0 + np.exp(-z))", "prob = 1.0 / (1.0 + np.exp(z))")],
+    "output_bias_dropped": [('z = hs[3] @ w4 + np.asarray(P["b4"], dtype=dtype)[0]', "z = hs[3] @ w4")],
+    "bf16_ties_away_from_zero": [("u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000", "u = (u + 0x8000) & 0xFFFF0000")],
+    "hidden_activation_not_rounded": [("hs.append(rnd(np.maximum(z, 0)))", "hs.append(np.maximum(z, 0))")],
+}
+
+MLP_CHILD = ("import importlib.util, sys\n"
+             "import oracle\n"
+             "spec = importlib.util.spec_from_file_location('oracle.mlp_ref', sys.argv[1])\n"
+             "m = importlib.util.module_from_spec(spec)\n"
+             "spec.loader.exec_module(m)\n"
+             "sys.modules['oracle.mlp_ref'] = m\n"
+             "oracle.mlp_ref = m\n"
+             "import pytest\n"
+             "sys.exit(pytest.main(sys.argv[2:]))\n")
+
+
+def _mlp_run(name, workdir):
+    text = open(os.path.join(ORACLE_DIR, "mlp_ref.py"), encoding="utf-8").read()
+    for old, new in MLP_MUTANTS[name]:
+        assert text.count(old) == 1, (name, old)
+        text = text.replace(old, new)
+    path = os.path.join(workdir, f"mlp_ref_{name}.py")
+    open(path, "w", encoding="utf-8").write(text)
+    p = subprocess.run([sys.executable, "-c", MLP_CHILD, path, os.path.join("tests", "test_mlp_ref.py"), "-x", "-q",
+                        "-p", "no:cacheprovider"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    return p.returncode, p.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mlp_outcomes(tmp_path_factory):
+    workdir = str(tmp_path_factory.mktemp("mlp_mutants"))
+    names = sorted(MLP_MUTANTS)
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        results = list(ex.map(lambda n: _mlp_run(n, workdir), names))
+    return dict(zip(names, results))
+
+
+def test_unmutated_network_reference_passes(mlp_outcomes):
+    rc, out = mlp_outcomes["control"]
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", sorted(n for n in MLP_MUTANTS if n != "control"))
+def test_planted_network_mistake_fails_a_pin(mlp_outcomes, name):
+    rc, out = mlp_outcomes[name]
+    assert rc == 1, (name, rc, out)
+    assert " failed" in out, out
