@@ -145,6 +145,14 @@ EDGE = [
 ]
 
 
+def test_every_opcode_on_its_boundaries(rc, oracle):
+    """Every expression and branch form the compiler emits, on values at
+    each comparison's boundary (the kernel of the translator's CPU test)."""
+    from tests.test_translate_cpu import opcode_kernel
+    for S in (8, 64):
+        run_both(rc, oracle, opcode_kernel(S))
+
+
 @pytest.mark.parametrize("case", range(len(EDGE)))
 def test_edge_cases(rc, oracle, case):
     src, G, S, glob = EDGE[case]

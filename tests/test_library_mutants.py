@@ -1,5 +1,6 @@
-"""How strong the pre-filter's soundness tests are: unsound mistakes planted
-in copies of prove.cpp must each fail tests/test_prove_cpu.py.
+"""How strong the host-side tests of the library are: mistakes planted in
+copies of prove.cpp must each fail tests/test_prove_cpu.py, and mistakes
+planted in copies of translate.cpp must each fail tests/test_translate_cpu.py.
 
 The pre-filter's claims (race freedom, bounds, private accesses) are
 one-sided: an unsound claim would let the checker skip logging an access or
@@ -7,9 +8,14 @@ declare an instance race-free that is not.  Each mutant below widens what
 the analysis claims (an off-by-one in a range or a guard, a check left out, a
 loop counter range cut short, a pair cleared by the benign-value rule where
 only cell disjointness may clear it).  The copy is compiled on the CPU and
-linked with the library's other objects; the pre-filter tests then run
-against it in a child process.  The unmutated copy, built the same way, must
-pass them.
+linked with the library's other objects; the tests then run against it in
+a child process.  The unmutated copies, built the same way, must pass them.
+
+The translator's mutants are plausible slips in writing a bytecode
+instruction as C++: a loop's back edge taken once more, operands of a
+reversed subtraction or a multiply-add swapped, a branch condition of the
+wrong sense, the resume point after a barrier, the constant part of an
+index, a logical not of the wrong sense.
 """
 import os
 import shutil
@@ -20,7 +26,8 @@ from concurrent.futures import ThreadPoolExecutor
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-TESTS = os.path.join("tests", "test_prove_cpu.py")
+TESTS = {"prove.cpp": os.path.join("tests", "test_prove_cpu.py"),
+         "translate.cpp": os.path.join("tests", "test_translate_cpu.py")}
 
 MUTANTS = {
     "control": [],
@@ -54,6 +61,27 @@ MUTANTS = {
     ],
 }
 
+TRANSLATE_MUTANTS = {
+    "translate_control": [],
+    "loop_back_edge_inclusive": [('line(o, "  if (%s < %s) goto L%d;", d.c_str(), I.c_str(), imm2);',
+                                  'line(o, "  if (%s <= %s) goto L%d;", d.c_str(), I.c_str(), imm2);')],
+    "rsubi_operands_swapped": [
+        ('case OP_RSUBI: line(o, "  %s = (int32_t)(%s%s - %s%s);", d.c_str(), U.c_str(), I.c_str(), U.c_str(), a.c_str());',
+         'case OP_RSUBI: line(o, "  %s = (int32_t)(%s%s - %s%s);", d.c_str(), U.c_str(), a.c_str(), U.c_str(), I.c_str());')],
+    "madi_operands_swapped": [
+        ('line(o, "  %s = (int32_t)(%s%s * %s%s + %s%s);", d.c_str(), U.c_str(), a.c_str(), U.c_str(), I.c_str(),\n'
+         '             U.c_str(), b.c_str());',
+         'line(o, "  %s = (int32_t)(%s%s * %s%s + %s%s);", d.c_str(), U.c_str(), b.c_str(), U.c_str(), I.c_str(),\n'
+         '             U.c_str(), a.c_str());')],
+    "branch_ge_as_gt": [('case OP_BFGEI: return ">=";', 'case OP_BFGEI: return ">";')],
+    "barrier_resumes_at_itself": [('line(o, "  RC_AT_BARRIER(cx, %d); pc = %u; st = %u; return;", imm, k + 1, (unsigned)TS_BARRIER);',
+                                   'line(o, "  RC_AT_BARRIER(cx, %d); pc = %u; st = %u; return;", imm, k + 2, (unsigned)TS_BARRIER);')],
+    "index_constant_dropped": [('"rc::sem_index(%s, %s, (int32_t)%" PRId32 "LL, %uu)", a.c_str(), I.c_str(), imm2,',
+                                '"rc::sem_index(%s, %s, (int32_t)%" PRId32 "LL * 0, %uu)", a.c_str(), I.c_str(), imm2,')],
+    "not_of_wrong_sense": [('case OP_NOT: line(o, "  %s = %s == 0;", d.c_str(), a.c_str()); break;',
+                            'case OP_NOT: line(o, "  %s = %s != 0;", d.c_str(), a.c_str()); break;')],
+}
+
 CHILD = ("import sys\n"
          "import paper_1308_3203_gb300.racecheck as r\n"
          "r.LIB_PATH = sys.argv[1]\n"
@@ -61,20 +89,25 @@ CHILD = ("import sys\n"
          "sys.exit(pytest.main(sys.argv[2:]))\n")
 
 
+def _target(name):
+    return ("translate.cpp", TRANSLATE_MUTANTS[name]) if name in TRANSLATE_MUTANTS else ("prove.cpp", MUTANTS[name])
+
+
 def _build(name, workdir, B):
+    fname, edits = _target(name)
     d = os.path.join(workdir, name)
     os.makedirs(d)
-    text = open(os.path.join(B.CSRC, "prove.cpp"), encoding="utf-8").read()
-    for old, new in MUTANTS[name]:
+    text = open(os.path.join(B.CSRC, fname), encoding="utf-8").read()
+    for old, new in edits:
         assert text.count(old) == 1, (name, old)
         text = text.replace(old, new)
-    src = os.path.join(d, "prove.cpp")
+    src = os.path.join(d, fname)
     open(src, "w", encoding="utf-8").write(text)
-    obj = os.path.join(d, "prove.o")
+    obj = os.path.join(d, fname.replace(".cpp", ".o"))
     nv = B._nvcc()
     subprocess.run([nv, "-x", "c++"] + B.NVFLAGS[len(B.ARCH):] + [f"-I{B.CSRC}", "-c", src, "-o", obj],
                    check=True, capture_output=True)
-    objs = [os.path.join(B.OUT_DIR, os.path.splitext(s)[0] + ".o") for s in B.SOURCES if s != "prove.cpp"]
+    objs = [os.path.join(B.OUT_DIR, os.path.splitext(s)[0] + ".o") for s in B.SOURCES if s != fname]
     lib = os.path.join(d, "libracecheck.so")
     subprocess.run([nv] + B.ARCH + ["-shared", "-o", lib, obj] + objs, check=True, capture_output=True)
     return lib
@@ -82,7 +115,7 @@ def _build(name, workdir, B):
 
 def _run(name, workdir, B):
     lib = _build(name, workdir, B)
-    p = subprocess.run([sys.executable, "-c", CHILD, lib, TESTS, "-x", "-q", "-p", "no:cacheprovider",
+    p = subprocess.run([sys.executable, "-c", CHILD, lib, TESTS[_target(name)[0]], "-x", "-q", "-p", "no:cacheprovider",
                         "-m", "not gpu"], cwd=ROOT, capture_output=True, text=True, timeout=900)
     return p.returncode, p.stdout[-2000:]
 
@@ -92,20 +125,21 @@ def outcomes(tmp_path_factory):
     from paper_1308_3203_gb300 import build as B
     B.build()  # the other objects of the library
     workdir = str(tmp_path_factory.mktemp("prove_mutants"))
-    names = sorted(MUTANTS)
+    names = sorted(MUTANTS) + sorted(TRANSLATE_MUTANTS)
     with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         results = list(ex.map(lambda n: _run(n, workdir, B), names))
     shutil.rmtree(workdir, ignore_errors=True)
     return dict(zip(names, results))
 
 
-def test_unmutated_copy_passes(outcomes):
-    rc, out = outcomes["control"]
+@pytest.mark.parametrize("name", ["control", "translate_control"])
+def test_unmutated_copy_passes(outcomes, name):
+    rc, out = outcomes[name]
     assert rc == 0, out
 
 
-@pytest.mark.parametrize("name", sorted(n for n in MUTANTS if n != "control"))
-def test_unsound_mistake_fails_a_test(outcomes, name):
+@pytest.mark.parametrize("name", sorted(n for n in list(MUTANTS) + list(TRANSLATE_MUTANTS) if "control" not in n))
+def test_planted_mistake_fails_a_test(outcomes, name):
     rc, out = outcomes[name]
     assert rc == 1, (name, rc, out)
     assert " failed" in out, out

@@ -34,8 +34,34 @@ def rc():
     return racecheck
 
 
+# every expression and branch form the compiler emits (register and
+# immediate comparisons, the six branch senses, not, and, or, negation,
+# division and remainder by negative numbers and zero, multiply-add, masks),
+# on values that sit on each comparison's boundary for some work-item
+OPCODE_EXPRS = ["x + 7", "x - tid", "x * -5", "x / 2", "x % 3", "10 / (x + 1)", "10 % (x - 1)", "7 - x", "-x",
+                "!x", "x < 1", "x <= 1", "x > 1", "x >= 1", "x == 1", "x != 1", "x < tid", "x <= tid - 3",
+                "x > tid - 4", "x >= tid", "x == tid - 3", "x != tid - 3", "(x > 0) && (tid < 5)",
+                "(x > 0) || (tid == 0)", "x * 3 + tid", "(x + 8) % 8", "(x + 8) % 4 + 1", "x / -2", "x % -3",
+                "-2147483647 - 1 - x", "size(A) - x", "!(x < 2)"]
+OPCODE_BRANCHES = ["x >= 1", "x > 1", "x <= 1", "x < 1", "x == 1", "x != 1", "!x", "x", "(x > 0) && (tid < 5)",
+                   "(x > 0) || (tid == 0)", "x >= tid", "x < tid - 2"]
+
+
+def opcode_kernel(group_size=8):
+    """x = tid - 3 runs over -3 .. group_size - 4; each work-item stores every
+    expression and the sense of every branch into its own 64 cells."""
+    body = ["  x = tid - 3;"]
+    body += [f"  A[gtid * 64 + {i}] = {e};" for i, e in enumerate(OPCODE_EXPRS)]
+    k0 = len(OPCODE_EXPRS)
+    body += [f"  if ({b}) {{ A[gtid * 64 + {k0 + j}] = {j + 1}; }} else {{ A[gtid * 64 + {k0 + j}] = -{j + 1}; }}"
+             for j, b in enumerate(OPCODE_BRANCHES)]
+    src = "kernel ops(global int A[]) {\n" + "\n".join(body) + "\n}\n"
+    return W.Instance("opcodes", src, 1, group_size, [np.zeros(64 * group_size, np.int32)])
+
+
 def instances():
-    out = [W.tiny_kernel(s) for s in range(120)]
+    out = [opcode_kernel()]
+    out += [W.tiny_kernel(s) for s in range(120)]
     out += [W.small_kernel(s, group_size=8, n_stmts=16) for s in range(60)]
     out += [W.small_kernel(s, group_size=4, groups=2, n_stmts=24, n_barriers=2, L=8) for s in range(30)]
     out += [W.large_kernel(s, groups=2, group_size=8, global_len=256, local_len=32, n_stmts=40, n_barriers=3)
