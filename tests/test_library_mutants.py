@@ -123,7 +123,8 @@ def _run(name, workdir, B):
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
     from paper_1308_3203_gb300 import build as B
-    B.build()  # the other objects of the library
+    objs = [os.path.join(B.OUT_DIR, os.path.splitext(s)[0] + ".o") for s in B.SOURCES]
+    B.build(force=not all(os.path.exists(o) for o in objs))  # the other objects of the library
     workdir = str(tmp_path_factory.mktemp("prove_mutants"))
     names = sorted(MUTANTS) + sorted(TRANSLATE_MUTANTS)
     with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
