@@ -343,6 +343,7 @@ struct Acc {
   bool store, local;
   AF idx, val;
   Shape box{1, 1};  // the work-items that can execute the access
+  Range ir{0, 0}, vr{0, 0};  // ranges of idx and val over box (known forms only)
 };
 
 // A counted loop: the back edge `reg = reg + 1; if reg < hi: goto head`
@@ -652,6 +653,8 @@ void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const
     if (!a.box.empty() && !exact(a.idx, a.box)) a.idx = top();
     a.val = a.store ? pr.in[pc][ins.b] : top();
     if (a.store && !a.box.empty() && !exact(a.val, a.box)) a.val = top();
+    if (a.idx.kind == AF::AFF) a.ir = range_of(a.idx, a.box);
+    if (a.val.kind == AF::AFF) a.vr = range_of(a.val, a.box);
     acc.push_back(a);
   }
   *out = rc_prove_result{};
@@ -664,8 +667,7 @@ void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const
   }
   for (const Acc &a : acc) {  // Table 1 bounds premise
     if (a.box.empty()) continue;  // no work-item gets there
-    const Range r = range_of(a.idx, a.box);
-    if (a.idx.kind != AF::AFF || r.lo < 0 || r.hi >= (int64_t)lens[a.mem]) out->in_bounds = 0;
+    if (a.idx.kind != AF::AFF || a.ir.lo < 0 || a.ir.hi >= (int64_t)lens[a.mem]) out->in_bounds = 0;
   }
   std::vector<std::pair<uint32_t, uint32_t>> open_reads;  // load pairs that may share a cell
   for (size_t i = 0; i < acc.size(); i++)
@@ -680,7 +682,7 @@ void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const
       // nobody executes one of them, or one work-item (per group, for local arrays) executes both
       bool ok = a.box.empty() || b.box.empty() || (h.nt() == 1 && (a.local || h.nw() == 1));
       if (!ok && a.idx.kind == AF::AFF && b.idx.kind == AF::AFF) {
-        const Range ra = range_of(a.idx, a.box), rb = range_of(b.idx, b.box);
+        const Range &ra = a.ir, &rb = b.ir;
         ok = ra.hi < rb.lo || rb.hi < ra.lo;                            // disjoint cells
         ok = ok || (a.idx == b.idx && injective(a.idx, h, a.local));  // only with itself
         // small launches: every work-item's cells, enumerated
@@ -692,7 +694,7 @@ void prove_analyze(const Program &p, uint32_t groups, uint32_t group_size, const
       }
       if (!ok && priv) (*priv)[a.pc] = (*priv)[b.pc] = 0;  // the two may share a cell
       if (!ok && a.store && b.store && a.val.kind == AF::AFF && b.val.kind == AF::AFF) {
-        const Range va = range_of(a.val, a.box), vb = range_of(b.val, b.box);
+        const Range &va = a.vr, &vb = b.vr;
         ok = va.lo == va.hi && vb.lo == vb.hi && va.lo == vb.lo;  // every writer stores one value: benign
       }
       if (!ok) {
