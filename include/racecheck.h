@@ -390,7 +390,7 @@ int rc_access_sites(const rc_bytecode *bc, uint32_t *pc, uint8_t *is_store, uint
  * through hooks the including code defines (RC_LD, RC_ST, RC_SIZE,
  * RC_ASSERT_FAIL, RC_AT_BARRIER; see translate.cpp), and the text calls
  * rc::sem_div, rc::sem_mod and rc::sem_index.  fn_name must be a C
- * identifier.  Writes min(len, cap - 1) bytes and a NUL into buf (cap 0:
+ * identifier of at most 128 characters (else RC_E_INVALID).  Writes min(len, cap - 1) bytes and a NUL into buf (cap 0:
  * buf may be NULL); *len = the text's length.  The text compiles as CUDA
  * C++ and as plain C++. */
 int rc_translate(const rc_bytecode *bc, const char *fn_name, char *buf, size_t cap, size_t *len);

@@ -200,7 +200,7 @@ extern "C" int rc_translate(const rc_bytecode *bc, const char *fn_name, char *bu
     return RC_E_INVALID;
   }
   const std::string name = fn_name;
-  bool ok = !name.empty() && !(name[0] >= '0' && name[0] <= '9');
+  bool ok = !name.empty() && name.size() <= 128 && !(name[0] >= '0' && name[0] <= '9');
   for (char c : name) ok = ok && ((c >= 'a' && c <= 'z') || (c >= 'A' && c <= 'Z') || (c >= '0' && c <= '9') || c == '_');
   if (!ok) {
     set_last_error("function name must be a C identifier");

@@ -195,7 +195,7 @@ def test_translated_kernels_follow_the_oracle(rc, oracle, harness):
 
 def test_translate_rejects_bad_names(rc):
     bc = rc.compile("kernel e() { }")
-    for bad in ("", "1x", "a-b", "a b"):
+    for bad in ("", "1x", "a-b", "a b", "x" * 129):
         with pytest.raises(Exception):
             rc.translate(bc, bad)
     assert "RC_JIT_FN void ok_name(" in rc.translate(bc, "ok_name")
