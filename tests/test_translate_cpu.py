@@ -64,6 +64,9 @@ def instances():
     out += [W.tiny_kernel(s) for s in range(120)]
     out += [W.small_kernel(s, group_size=8, n_stmts=16) for s in range(60)]
     out += [W.small_kernel(s, group_size=4, groups=2, n_stmts=24, n_barriers=2, L=8) for s in range(30)]
+    # the batch workload's long programs (hundreds of statements, up to 8 barriers) at a small shape
+    out += [W.small_kernel(500 + s, group_size=8, groups=2, n_stmts=300 + 10 * s, n_barriers=s % 9, L=64)
+            for s in range(20)]
     out += [W.large_kernel(s, groups=2, group_size=8, global_len=256, local_len=32, n_stmts=40, n_barriers=3)
             for s in range(10)]
     out += [W.stress_kernel(s, groups=2, group_size=8) for s in range(6)]
