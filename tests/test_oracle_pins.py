@@ -71,7 +71,7 @@ def test_fig1_closed_form(oracle, n, seed):
 
 
 def test_fig2_schedules_reach_both_values_of_g(oracle):
-    """Sec. 6.1: 'g can in practice have the value 0 or the value 1'."""
+    """Sec. 6.1 (Fig. 2): depending on the schedule, g ends as 0 or as 1."""
     n = 3
     e = oracle.explore(FIG2, 1, n, [np.ones(n + 1, np.int32), np.array([5], np.int32)])
     assert not e["overflow"]
