@@ -209,9 +209,15 @@ int rc_sort_accesses(const rc_access *in, rc_access *out, uint64_t n, uint32_t c
  * no cudaMalloc, cudaFree or allocating library routine.
  *  - n may not exceed 2^18 records (RC_E_CAPACITY beyond that); other
  *    arguments and results are those of rc_sort_accesses.
- *  - The first call on each device, with that device current, looks up the
- *    device address of the array (cudaGetSymbolAddress); make that first
- *    call before any stream capture.
+ *  - The first call on each device, with that device current, is the
+ *    set-up call: it looks up the device address of the array
+ *    (cudaGetSymbolAddress), and under lazy module loading (CUDA's default)
+ *    that is when the driver loads the module holding the array and creates
+ *    the array on the device.  Make that first call (an n = 1 sort will do)
+ *    before reserving the rest of the device budget and before any stream
+ *    capture; later calls allocate nothing.
+ *  - Errors also set rc_last_error(); a CUDA error already pending before
+ *    the call is reported as RC_E_CUDA without running the sort.
  *  - All calls share the one array and it keeps the last call's contents;
  *    calls whose work overlaps on the GPU (other streams, other host
  *    threads) race on it and must be serialised by the caller. */
