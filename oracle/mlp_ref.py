@@ -12,6 +12,8 @@ whose gradient with respect to z is (p - y) / n.  Backpropagation gives
     dW_l = dz_l h_{l-1}^T,  db_l = sum over rows of dz_l,
     dw4 = sum_r (dL/dz_r) h3_r,  db4 = sum_r dL/dz_r.
 
+``adam_step`` is the optimiser's update in float64.
+
 ``bf16=True`` rounds to bfloat16 (round to nearest even) exactly where the
 GPU kernels store BF16: the features, the weight copies W1..W3 and w4, each
 h_l, and each dz_l.  Biases, sums and the loss stay in the working precision
@@ -93,6 +95,43 @@ def loss_and_grad(p, X, y, bf16_points: bool = True, dtype=np.float32):
         if l > 0:
             dz = rnd((dz @ c["W"][l]) * (c["h"][l] > 0))
     return float(loss), pack(g)
+
+
+def adam_step(p, g, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    """One Adam update (Kingma & Ba, "Adam: A Method for Stochastic
+    Optimization", Algorithm 1), in float64: the moments decay by b1 and b2
+    and take in g and g^2; each is divided by its bias correction 1 - b^t
+    (t = 1 for the first update); the parameters move by lr times the
+    corrected first moment over (square root of the corrected second moment
+    + eps).  Returns the new (p, m, v)."""
+    p, g, m, v = (np.asarray(a, dtype=np.float64) for a in (p, g, m, v))
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    m_hat = m / (1.0 - b1 ** t)
+    v_hat = v / (1.0 - b2 ** t)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
+def shuffle(n: int, seed: int) -> np.ndarray:
+    """The training loop's row order for one epoch: a Fisher-Yates shuffle of
+    0..n-1 (from the last position down, position i swapped with the one at
+    splitmix64() mod (i + 1)), splitmix64 being Steele, Lea and Flood's
+    generator (state advanced by 0x9E3779B97F4A7C15, then three xor-shift /
+    multiply mixing rounds).  Returns the permutation and nothing of the
+    network's arithmetic; a test uses it to feed the reference the rows in
+    the order the library trains on them."""
+    mask = (1 << 64) - 1
+    state = seed & mask
+    perm = list(range(n))
+    for i in range(n - 1, 0, -1):
+        state = (state + 0x9E3779B97F4A7C15) & mask
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        z ^= z >> 31
+        j = z % (i + 1)
+        perm[i], perm[j] = perm[j], perm[i]
+    return np.asarray(perm, dtype=np.int64), state
 
 
 def init_params(seed: int) -> np.ndarray:

@@ -84,10 +84,32 @@ def test_tcgen05_forward_matches(rc, n):
     np.testing.assert_allclose(b, want, atol=4e-3, rtol=0)
 
 
+# Element-wise bar of a gradient against the reference with the same BF16
+# rounding points: 2^-6 of the largest magnitude in the element's parameter
+# block.  The kernels and the reference round at the same points and differ
+# in FP32 summation order only; the CPU evaluation of the same rounding
+# points in float32 against float64 (uniform features, 7-2500 rows) differs
+# by at most 3.5e-3 of the block maximum (the order moving a hidden value
+# across a BF16 rounding boundary, one BF16 ulp = 2^-8 relative, which the
+# later layers carry), so 2^-6 = 1.6e-2 leaves a margin of 4.5.
+GRAD_ATOL_OF_BLOCK_MAX = 2.0 ** -6
+
+
+def check_gradient(g, want, exact):
+    for name, (a, b, _) in M.offsets().items():
+        atol = GRAD_ATOL_OF_BLOCK_MAX * max(np.abs(want[a:b]).max(), 1e-30)
+        np.testing.assert_allclose(g[a:b], want[a:b], rtol=0, atol=atol, err_msg=name)
+        # against the exact float64 network: no farther than the rounding points
+        # themselves put the reference, plus the bar above (in the L2 norm)
+        gap, ref_gap = np.linalg.norm(g[a:b] - exact[a:b]), np.linalg.norm(want[a:b] - exact[a:b])
+        assert gap <= ref_gap + GRAD_ATOL_OF_BLOCK_MAX * np.linalg.norm(exact[a:b]), (name, gap, ref_gap)
+
+
 @pytest.mark.parametrize("backend", [0, 1])
 @pytest.mark.parametrize("n", [7, 777, 2500])
 def test_gradient_matches_reference(rc, n, backend):
-    """Both backends: mma.sync (0) and tcgen05 (1) for every product."""
+    """Both backends: mma.sync (0) and tcgen05 (1) for every product; every
+    gradient element against the BF16-point reference."""
     m = rc.MLP(seed=2, capacity=4096)
     m.set_backend(backend)
     p = M.init_params(11).astype(np.float32)
@@ -96,13 +118,44 @@ def test_gradient_matches_reference(rc, n, backend):
     y = (np.random.default_rng(n).random(n) < 0.3).astype(np.float32)
     g, loss = m.grad(cuda(X), cuda(y))
     want_loss, want = M.loss_and_grad(p, X, y, bf16_points=True)
+    _, exact = M.loss_and_grad(p, X, y, bf16_points=False, dtype=np.float64)
     assert loss == pytest.approx(want_loss, rel=2e-3)
-    for name, (a, b, _) in M.offsets().items():
-        d = np.linalg.norm(g[a:b] - want[a:b]) / max(np.linalg.norm(want[a:b]), 1e-12)
-        cos = np.dot(g[a:b], want[a:b]) / max(np.linalg.norm(g[a:b]) * np.linalg.norm(want[a:b]), 1e-30)
-        assert d < 2e-2 and cos > 0.9995, (name, d, cos)
+    check_gradient(g, want, exact)
     # the parameters did not move
     np.testing.assert_array_equal(m.params(), p)
+    assert m.backend_error() == 0
+
+
+@pytest.mark.parametrize("backend", [0, 1])
+def test_adam_steps_match_reference(rc, backend):
+    """Three training steps (one minibatch of all rows per call, rows in the
+    library's shuffled order) against the float64 Adam update of
+    oracle/mlp_ref.py applied to the gradient the GPU computes at each step
+    (rc_mlp_grad on the same rows in the same order, before the step):
+    parameters and moments carried from step to step.  The update is FP32 on
+    the GPU; the bar is one part in 10^5 of the learning rate per element on
+    top of 10^-6 relative to the parameter."""
+    n, lr = 600, 2e-3
+    m = rc.MLP(seed=4, capacity=1024)
+    m.set_backend(backend)
+    p = M.init_params(21).astype(np.float32)
+    m.set_params(p)
+    X = feature_rows(rc, n, 99)
+    y = (np.random.default_rng(5).random(n) < 0.3).astype(np.float32)
+    mom, vel = np.zeros(M.N_PARAMS), np.zeros(M.N_PARAMS)
+    cur = p.astype(np.float64)
+    for t in (1, 2, 3):
+        seed = 100 + t
+        perm, _ = M.shuffle(n, seed)
+        g, _ = m.grad(cuda(X[perm]), cuda(y[perm]))
+        _, want_g = M.loss_and_grad(cur.astype(np.float32), X[perm], y[perm], bf16_points=True)
+        _, exact_g = M.loss_and_grad(cur, X[perm], y[perm], bf16_points=False, dtype=np.float64)
+        check_gradient(g, want_g, exact_g)
+        m.train(cuda(X), cuda(y), epochs=1, batch=n, lr=lr, seed=seed)
+        cur, mom, vel = M.adam_step(cur, g.astype(np.float64), mom, vel, t, lr)
+        got = m.params().astype(np.float64)
+        np.testing.assert_allclose(got, cur, rtol=1e-6, atol=1e-5 * lr, err_msg=f"step {t}")
+        cur = got  # carry the GPU's FP32 parameters (its rounding) into the next step
     assert m.backend_error() == 0
 
 

@@ -109,3 +109,67 @@ def test_bf16_rounding_points_on_one_path():
     assert a[0] == pytest.approx(1 / (1 + np.exp(-0.75)), rel=1e-6)
     b, _ = M.forward(p, X, bf16_points=False, dtype=np.float64)
     assert b[0] == pytest.approx(1 / (1 + np.exp(-(0.75 + 2.0 ** -8 + 3 * 2.0 ** -9))), rel=1e-14)
+
+
+# ---- the optimiser's update (Adam, Kingma & Ba, Algorithm 1)
+
+LR, EPS = 1e-3, 1e-8
+
+
+def test_adam_first_step_closed_form():
+    """With zero moments and t = 1 the corrected moments are g and g^2
+    exactly, so every parameter moves by lr * g / (|g| + eps): lr times its
+    gradient's sign wherever |g| >> eps, nothing where g = 0."""
+    rng = np.random.default_rng(0)
+    p = rng.normal(size=1000)
+    g = rng.normal(size=1000) * 10.0 ** rng.integers(-9, 2, size=1000)
+    g[:10] = 0
+    z = np.zeros(1000)
+    p1, m1, v1 = M.adam_step(p, g, z, z, 1, LR)
+    np.testing.assert_allclose(p1, p - LR * g / (np.abs(g) + EPS), rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(p1[:10], p[:10])
+    np.testing.assert_allclose(m1, 0.1 * g, rtol=1e-15)
+    np.testing.assert_allclose(v1, 0.001 * g * g, rtol=1e-12)
+
+
+def test_adam_constant_gradient_moves_by_lr_every_step():
+    """A gradient held constant: the first moment after t steps is
+    (1 - 0.9^t) g and the second (1 - 0.999^t) g^2, which the bias
+    corrections divide back to g and g^2, so steps 1..6 each move by
+    lr * g / (|g| + eps)."""
+    g = np.array([3.0, -0.5, 2e-4, -7e-6])
+    p, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    for t in range(1, 7):
+        q, m, v = M.adam_step(p, g, m, v, t, LR)
+        np.testing.assert_allclose(q - p, -LR * g / (np.abs(g) + EPS), rtol=1e-9)
+        p = q
+
+
+def test_adam_alternating_gradient_closed_form():
+    """Gradients g then -g: after two steps the first moment is
+    0.9 * 0.1 g - 0.1 g = -0.01 g, corrected by 1 - 0.81 to -g / 19; the
+    second is (1 - 0.999^2) g^2, corrected to g^2 exactly.  So the second
+    step moves by +lr * (g / 19) / (|g| + eps)."""
+    g = np.array([1.0, -4.0, 0.25])
+    z = np.zeros(3)
+    p1, m, v = M.adam_step(z, g, z, z, 1, LR)
+    p2, m, v = M.adam_step(p1, -g, m, v, 2, LR)
+    np.testing.assert_allclose(m, -0.01 * g, rtol=1e-12)
+    np.testing.assert_allclose(p2 - p1, LR * (g / 19) / (np.abs(g) + EPS), rtol=1e-12)
+
+
+def test_shuffle_is_fisher_yates_over_splitmix64():
+    """The row order of a training epoch: a permutation, drawn from
+    splitmix64, whose first outputs from state 0 are the published
+    0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4, 0x06c45d188009454f (for n = 4
+    the swaps take those outputs mod 4, 3 and 2)."""
+    perm, state = M.shuffle(4, 0)
+    a = list(range(4))
+    for i, r in zip((3, 2, 1), (0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4, 0x06c45d188009454f)):
+        j = r % (i + 1)
+        a[i], a[j] = a[j], a[i]
+    assert perm.tolist() == a
+    assert state == 3 * 0x9E3779B97F4A7C15 % (1 << 64)
+    for n, seed in ((1, 5), (1000, 7), (4097, 1 << 63)):
+        perm, _ = M.shuffle(n, seed)
+        assert sorted(perm.tolist()) == list(range(n))

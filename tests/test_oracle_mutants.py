@@ -228,6 +228,10 @@ MLP_MUTANTS = {
     "output_bias_dropped": [('z = hs[3] @ w4 + np.asarray(P["b4"], dtype=dtype)[0]', "z = hs[3] @ w4")],
     "bf16_ties_away_from_zero": [("u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000", "u = (u + 0x8000) & 0xFFFF0000")],
     "hidden_activation_not_rounded": [("hs.append(rnd(np.maximum(z, 0)))", "hs.append(np.maximum(z, 0))")],
+    "adam_first_moment_not_decayed": [("m = b1 * m + (1.0 - b1) * g", "m = m + (1.0 - b1) * g")],
+    "adam_bias_corrections_swapped": [("m_hat = m / (1.0 - b1 ** t)", "m_hat = m / (1.0 - b2 ** t)")],
+    "adam_eps_inside_the_root": [("p - lr * m_hat / (np.sqrt(v_hat) + eps)", "p - lr * m_hat / np.sqrt(v_hat + eps)")],
+    "adam_correction_one_step_late": [("v_hat = v / (1.0 - b2 ** t)", "v_hat = v / (1.0 - b2 ** (t + 1))")],
 }
 
 MLP_CHILD = ("import importlib.util, sys\n"
