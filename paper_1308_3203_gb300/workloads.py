@@ -19,7 +19,8 @@ Kernel shapes follow the workloads the checker is built for:
   arrays 1K..1M).
 * ``stress_kernel`` 65,536 groups x 1024 (2^26 work-items), 16 barriers, 512
   statements, nested loops up to 32 trips, branches on loaded values, a 64M
-  global array.
+  global array; every interval that writes ends with a benign cell, a racy
+  cell and reads of the racy cell in each group.
 * ``tiny_kernel``   2-4 work-items with a handful of accesses and values in
   [0,4), small enough to enumerate every schedule.
 """
@@ -285,6 +286,31 @@ class _SlabGen:
         val = f"wg * 3 + {int(r.integers(8))}" if benign else f"tid + {int(r.integers(8))}"
         return [f"if (tid % {step} == 0) {{", f"  {tgt} = {val};", "}"], 2
 
+    def can_plant(self):
+        return self.S >= 2 and bool(self.wslabs or self.n_slab >= 3)
+
+    def closing_plants(self):
+        """Three statements that end a write interval, so that every group
+        carries each class of record whatever the random draws were: a
+        benign cell (its owner is among the writers, all of whom store one
+        value and write nothing after it), a racy cell (writers store
+        ``tid + c``: pairwise different values) and reads of the racy cell
+        by work-items that do not write it (every reader sees a value some
+        writer differs from)."""
+        r, S = self.rng, self.S
+        base = int(self.pslabs[0]) * self.N
+        off1 = int(r.integers(S))
+        off2 = (off1 + 1 + int(r.integers(S - 1))) % S
+        st1, st2, st3 = (min(int(r.choice([8, 16, 32, 64])), S) for _ in range(3))
+        c1, c2 = int(r.integers(8)), int(r.integers(8))
+        cell1 = self._plus(base, f"wg * {S} + {off1}")
+        cell2 = self._plus(base, f"wg * {S} + {off2}")
+        lines = [f"if (tid % {st1} == {off1 % st1}) {{", f"  A[{cell1}] = wg * 3 + {c1};", "}",
+                 f"if (tid % {st2} == 0) {{", f"  A[{cell2}] = tid + {c2};", "}"]
+        if st2 % 2 == 0 and st3 >= 2:  # readers are odd, writers even: disjoint
+            lines += [f"if (tid % {st3} == 1) {{", f"  {self.var()} = A[{cell2}];", "}"]
+        return lines, 3
+
     # cumulative thresholds: assign, neighbour load, own load, local load,
     # store, local store, loop; the rest are branches
     MIX = {"dense": (0.2, 0.42, 0.5, 0.56, 0.72, 0.78, 0.88),
@@ -335,23 +361,36 @@ class _SlabGen:
 
 
 def _slab_kernel(name, rng, G, S, L, LL, n_stmts, n_barriers, max_trip, plant, loads_on_branch,
-                 max_depth, n_vars=8, mix="dense"):
+                 max_depth, n_vars=8, mix="dense", closing_plants=False):
     N = G * S
     g = _SlabGen(rng, N, S, L, LL, n_vars, max_trip, plant, loads_on_branch, max_depth, mix)
     per = n_stmts / (n_barriers + 1)
     lines, count, next_bar, bars = [], 0, per, 0
+
+    def close_interval():
+        nonlocal count
+        if closing_plants and g.can_plant():
+            ls, c = g.closing_plants()
+            lines.extend(ls)
+            count += c
+
     while count < n_stmts:
         ls, c = g.stmt(0, False)
         lines += ls
         count += c
         if bars < n_barriers and count >= next_bar:
+            close_interval()
             lines.append("barrier;")
             bars += 1
             next_bar += per
             g.new_interval()
     while bars < n_barriers:
+        close_interval()
         lines.append("barrier;")
         bars += 1
+        if closing_plants:
+            g.new_interval()
+    close_interval()
     decl = "global int A[]" + (f", local int Lc[{LL}]" if LL else "")
     src = f"kernel {name}({decl}) {{\n" + "\n".join("  " + x for x in lines) + "\n}\n"
     return src
@@ -371,14 +410,16 @@ def large_kernel(seed: int, groups: int = 1024, group_size: int = 256,
 
 
 def stress_kernel(seed: int, groups: int = 65536, group_size: int = 1024, n_stmts: int = 512,
-                  n_barriers: int = 16, global_len: int | None = None) -> Instance:
-    """Config-5 instance (defaults: 65,536 x 1024, 16 barriers, 512 statements)."""
+                  n_barriers: int = 16, global_len: int | None = None, closing_plants: bool = True) -> Instance:
+    """Config-5 instance (defaults: 65,536 x 1024, 16 barriers, 512 statements).
+    ``closing_plants=False``: the same statement mix without the planted
+    cells that end each writing interval (often race-free)."""
     rng = np.random.default_rng([5, seed])
     N = groups * group_size
     L = global_len or N
     src = _slab_kernel("stress", rng, groups, group_size, L, 0, n_stmts, n_barriers,
                        max_trip=32, plant=0.02, loads_on_branch=True, max_depth=2,
-                       mix="sparse")
+                       mix="sparse", closing_plants=closing_plants)
     A = rng.integers(0, 1 << 10, size=L, dtype=np.int32)
     return Instance(f"stress-s{seed}-{groups}x{group_size}", src, groups, group_size, [A])
 
