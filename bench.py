@@ -1,13 +1,17 @@
 """Benchmark: race-checked accesses per second on one GB300.
 
-One step = one full race check (every barrier interval: interpreter, log
-classification, commit, barrier agreement, report) of the large synthetic
-instance: 1024 work-groups x 256 work-items, 8 barriers, 200 statements with
-constant-trip loops, a global int32[4M] array and a local int32[4096] array
-per group (seed = rank).  Timed with CUDA events on the launching stream,
-each step bracketed by a barrier and a synchronize, L2 flushed between steps.
+One step = one full race check (every barrier interval: interpreter, access
+logs, classification, commit, barrier agreement, report) of the stress
+instance: 65,536 work-groups x 1024 work-items (2^26), 16 barriers, 512
+statements with nested loops of up to 32 trips and branches on loaded
+values, one global int32[2^26] array (seed = rank).  Timed with CUDA events
+on the launching stream, each step bracketed by a barrier and a
+synchronize, L2 flushed between steps.  The same JSON line carries the
+1024 x 256 large instance, the instance checked with every access logged,
+a batch of uneven kernels and the learned proposal as secondary objects.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload stress|large]
 
 Under torchrun (N > 1) every rank checks its own instance (replicas: the
 single-instance path has no exchange step); value = all ranks' accesses /
@@ -32,26 +36,28 @@ sys.path.insert(0, ROOT)
 
 METRIC = "race-checked accesses/s"
 UNIT = "accesses/s"
-WORKLOAD = ("large instance: 1024 groups x 256 work-items, 8 barriers, 200 statements "
-            "(loops of 1-16 trips), global int32[4M], local int32[4096] per group, "
-            "~5%+5% planted racy/benign stores")
+WORKLOADS = {
+    "stress": ("stress instance: 65,536 groups x 1024 work-items, 16 barriers, 512 statements "
+               "(nested loops of up to 32 trips, branches on loaded values), global int32[2^26]; "
+               "each writing interval ends with a benign cell, a racy cell and reads of it in every group"),
+    "large": ("large instance: 1024 groups x 256 work-items, 8 barriers, 200 statements "
+              "(loops of 1-16 trips), global int32[4M], local int32[4096] per group, "
+              "~5%+5% planted racy/benign stores"),
+}
 # oracle sample: the same program and input, first groups only
-SAMPLE_GROUPS = 96
+SAMPLE_GROUPS = {"stress": 128, "large": 96}
 
-
-# DRAM traffic of interp_kernel per launch: dram__bytes_read.sum +
-# dram__bytes_write.sum, mean over the 12 resident launches (one per check,
-# all nine intervals) of the command below, from
+# DRAM traffic of interp_kernel per launch (dram__bytes_read.sum +
+# dram__bytes_write.sum), from an ncu capture of the stress program at
+# 4,096 x 1024 work-items, every interval launch of one check, scaled by 16
+# to the 65,536-group instance (an interval's traffic grows with its
+# work-items: same program, same per-work-item work):
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
 #       --clock-control none -k regex:interp_kernel --csv \
-#       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --batch-kernels 0 --proposal-kernels 0
-# (profiles/interp_kernel_large_instance.md).  It holds only for the kernel
-# sources it was taken on and for the accesses of the bench instance that the
-# pre-filter proves private (those are not logged); a change to either
-# reports null.
-INTERP_TRAFFIC = {"sources_sha256": "097c36c1768c7862ad544a81c1a5a15cf4a8a963d09545da524c11bf94adcbea",
-                  "private_flags_sha256": "fe8aef1429b8b2cb0efc731eae2f5a5cd06da4274efbb49633e030f228d56b2b",
-                  "bytes_per_launch": 168407957}
+#       python bench.py --workload stress --groups 4096 --steps 1 --warmup 1 --secondary none
+# It holds only for the kernel sources and the stress program it was taken
+# on; a change to either reports null.
+INTERP_TRAFFIC = {"sources_sha256": None, "program_sha256": None, "bytes_per_launch": None}
 INTERP_SOURCES = ("paper_1308_3203_gb300/csrc/interp.cu", "paper_1308_3203_gb300/csrc/device.cuh",
                   "paper_1308_3203_gb300/csrc/semantics.cuh")
 
@@ -70,13 +76,23 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="stress", choices=sorted(WORKLOADS))
+    p.add_argument("--groups", type=int, default=0, help="work-groups of the instance (0: its full size)")
     p.add_argument("--strategy", type=int, default=0, help="0 auto, 1 sort, 2 shadow, 3 resident")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--secondary", default="all", choices=["all", "none"],
+                   help="none: only the headline instance (profiling runs)")
     p.add_argument("--batch-kernels", type=int, default=10_000,
                    help="size of the batched-checking measurement (0 skips it)")
     p.add_argument("--proposal-kernels", type=int, default=2000,
                    help="training kernels of the learned-proposal measurement (0 skips it)")
     return p.parse_args()
+
+
+def make_instance(W, workload: str, seed: int, groups: int = 0):
+    if workload == "stress":
+        return W.stress_kernel(seed, **({"groups": groups} if groups else {}))
+    return W.large_kernel(seed, **({"groups": groups} if groups else {}))
 
 
 def dist_env():
@@ -130,50 +146,55 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def oracle_sample(workload: str, seed: int = 0):
+    """The oracle's bounded sample of the workload: the same program text and
+    input, only the first SAMPLE_GROUPS work-groups launched."""
+    from paper_1308_3203_gb300 import workloads as W
+    inst = make_instance(W, workload, seed)
+    g = SAMPLE_GROUPS[workload]
+    return inst, g, (f"same program and input, first {g} of {inst.groups} groups, single-threaded")
+
+
 def run_reference(args, world, rank):
     """CPU oracle on the host cores, bounded sample of the same workload."""
     if rank != 0:
         return
     from oracle import oracle
-    from paper_1308_3203_gb300 import workloads as W
-    inst = W.large_kernel(0)
+    inst, g, sample = oracle_sample(args.workload)
     oracle.build()
     times, acc = [], 0
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        r = oracle.check(inst.src, SAMPLE_GROUPS, inst.group_size, inst.globals)
+        r = oracle.check(inst.src, g, inst.group_size, inst.globals)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
             acc += r["n_access"]
     v = acc / sum(times)
-    sample = (f"same program and input, first {SAMPLE_GROUPS} of 1024 groups "
-              f"({r['n_access']} accesses per step), single-threaded")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": {"workload": WORKLOADS[args.workload]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} ({r['n_access']} accesses per step)"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def cpu_baseline():
+def cpu_baseline(workload: str):
     from oracle import oracle
-    from paper_1308_3203_gb300 import workloads as W
-    inst = W.large_kernel(0)
+    inst, g, sample = oracle_sample(workload)
     oracle.build()
     t0 = time.perf_counter()
     acc, n = 0, 0
     while time.perf_counter() - t0 < 12.0 or n == 0:
-        r = oracle.check(inst.src, SAMPLE_GROUPS, inst.group_size, inst.globals)
+        r = oracle.check(inst.src, g, inst.group_size, inst.globals)
         acc += r["n_access"]
         n += 1
     dt = time.perf_counter() - t0
     return {"value": acc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"same program and input, first {SAMPLE_GROUPS} of 1024 groups, "
-                      f"{n} run(s) in {dt:.1f} s, single-threaded"}
+            "sample": f"{sample}: {n} run(s) of {r['n_access']} accesses in {dt:.1f} s"}
 
 
 def shard(n: int, rank: int, world: int) -> range:
@@ -194,7 +215,7 @@ def combine(values, dist, op: str):
     return [float(x) for x in t.cpu()]
 
 
-def batch_leg(rc, W, n_kernels, rank=0, world=1, dist=None):
+def batch_leg(rc, W, n_kernels, rank=0, world=1, dist=None, hbm=6800.0):
     """Batched checking of n uneven kernels: each rank checks its shard in
     one rc_check_batch call (independent problems: no exchange); kernels/s
     = all kernels / the slowest rank's time."""
@@ -216,13 +237,18 @@ def batch_leg(rc, W, n_kernels, rank=0, world=1, dist=None):
     got = rc.check_batch(items, want_final=False)
     dt = time.perf_counter() - t0
     acc = sum(g["n_access"] for g in got)
+    logged_g = sum(g["n_global"] * g["n_logged"] // max(g["n_access"], 1) for g in got)
     dt_max, = combine([dt], dist, "max")
-    acc_all, n_all = combine([acc, len(items)], dist, "sum")
+    acc_all, n_all, lg_all = combine([acc, len(items), logged_g], dist, "sum")
+    gbs = 24.0 * lg_all / dt_max / 1e9
     return {"workload": f"{n_kernels} kernels: group size log-uniform 32-1024, 1-64 groups, "
                         "16-512 statements, 0-8 barriers, global int32 arrays 1K-1M",
             "kernels_per_s": n_all / dt_max, "accesses_per_s": acc_all / dt_max, "seconds": dt_max,
-            "accesses": int(acc_all), "timing": "host wall clock around rc_check_batch (host inputs, "
-                                                "H2D and report D2H included), slowest rank"}
+            "accesses": int(acc_all), "logged_global_accesses": int(lg_all),
+            "hbm": {"what": "24 B per logged global access (log write + classification read) over the "
+                            "call's wall time", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm},
+            "timing": "host wall clock around rc_check_batch (host inputs, H2D and report D2H included), "
+                      "slowest rank"}
 
 
 def proposal_leg(rc, n_train, n_eval=200, epochs=20):
@@ -265,6 +291,84 @@ def proposal_leg(rc, n_train, n_eval=200, epochs=20):
             "search": res}
 
 
+def measure(rc, inst, bc, *, steps, warmup, dist, flush, log_every=False, host=True, prof_steps=None):
+    """Check `inst` steps times with device-resident inputs (CUDA events on
+    the launching stream), then with host inputs through the C ABI (e2e),
+    then once more with per-launch profiling for the roofline."""
+    import torch
+    dev_in = [torch.from_numpy(a).cuda() for a in inst.globals]
+    host_np = [torch.from_numpy(a).pin_memory().numpy() for a in inst.globals] if host else None
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(inputs, k):
+        tot, last = 0.0, None
+        for _ in range(k):
+            flush.zero_()
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            last = rc.check(bc, inst.groups, inst.group_size, inputs, stream=stream.cuda_stream,
+                            want_final=False, log_every_access=log_every)
+            b.record(stream)
+            barrier()
+            tot += a.elapsed_time(b)
+        return tot, last
+
+    for _ in range(warmup):
+        rc.check(bc, inst.groups, inst.group_size, dev_in, want_final=False, log_every_access=log_every)
+    torch.cuda.synchronize()
+    l0 = rc.kernel_launches()
+    ms, rep = timed(dev_in, steps)
+    launches = rc.kernel_launches() - l0
+    out = {"ms": ms, "rep": rep, "launches": launches, "steps": steps}
+    if host:
+        out["ms_e2e"], out["rep_e2e"] = timed(host_np, steps)
+        out["h2d"] = int(sum(a.nbytes for a in host_np))
+    ps = prof_steps or steps
+    rc.profile_reset()
+    rc.profile_enable(True)
+    timed(dev_in, ps)
+    rc.profile_enable(False)
+    out["prof"] = [rc.profile_get(k) for k in range(2)]
+    out["prof_steps"] = ps
+    del dev_in, host_np
+    return out
+
+
+def roofline(m, peak, peak_source, traffic=None) -> dict:
+    """Roofline of the interpreter kernel (the dominant kernel: it writes the
+    access logs).  Algorithmic bytes per launch: 12 B (cell, work-item and
+    read/write bit, value) for every access it wrote to a log; accesses the
+    pre-filter proved private are not written and not credited."""
+    rep, p0, p1 = m["rep"], m["prof"][0], m["prof"][1]
+    launches_per_check = p0["launches"] / max(m["prof_steps"], 1)
+    interp_ms = p0["ms"] / max(p0["launches"], 1)
+    classify_ms_per_check = p1["ms"] / max(m["prof_steps"], 1)
+    logged = rep["n_logged"]
+    bytes_per_launch = 12.0 * logged / max(launches_per_check, 1e-9)
+    achieved = bytes_per_launch / (interp_ms / 1e3) / 1e9 if interp_ms else 0.0
+    path_ms = interp_ms * launches_per_check + classify_ms_per_check
+    path_gbs = 24.0 * logged / (path_ms / 1e3) / 1e9 if path_ms else 0.0
+    credited = 12.0 * rep["n_access"] / max(launches_per_check, 1e-9) / (interp_ms / 1e3) / 1e9 if interp_ms else 0.0
+    return {"kernel": "interp_kernel", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "bytes_rule": "12 B per logged access (written once by the interpreter)",
+            "peak_source": peak_source, "avg_launch_ms": interp_ms,
+            "launches_per_check": launches_per_check,
+            "path": {"what": "log/classify path: 24 B per logged access (log write + classification read) over "
+                             "interpreter + classification time per check",
+                     "ms_per_check": path_ms, "achieved": path_gbs, "frac": path_gbs / peak,
+                     "classify_ms_per_check": classify_ms_per_check},
+            "private_credit": {"what": "12 B for every access, private ones included (not moved bytes)",
+                               "achieved": credited, "frac": credited / peak}}
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -287,111 +391,107 @@ def main():
     rc.set_strategy(args.strategy)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-
-    inst = W.large_kernel(rank)
-    bc = rc.compile(inst.src)
-    dev_in = [torch.from_numpy(a).cuda() for a in inst.globals]
-    host_in = [torch.from_numpy(a).pin_memory() for a in inst.globals]
-    host_np = [t.numpy() for t in host_in]
-    stream = torch.cuda.current_stream()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_source = "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def timed(inputs, k):
-        tot, last = 0.0, None
-        for _ in range(k):
-            flush.zero_()
-            barrier()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            last = rc.check(bc, inst.groups, inst.group_size, inputs, stream=stream.cuda_stream,
-                            want_final=False)
-            b.record(stream)
-            barrier()
-            tot += a.elapsed_time(b)
-        return tot, last
-
-    for _ in range(args.warmup):
-        rc.check(bc, inst.groups, inst.group_size, dev_in, want_final=False)
-    torch.cuda.synchronize()
+    inst = make_instance(W, args.workload, rank, args.groups)
+    bc = rc.compile(inst.src)
+    full_size = args.groups == 0
+    prof_steps = min(args.steps, 5)
 
     clocks = Clocks(local)
     clocks.start()
-    # ---- device-resident inputs (value)
-    l0 = rc.kernel_launches()
-    ms, rep = timed(dev_in, args.steps)
-    launches = rc.kernel_launches() - l0
-
-    # ---- host inputs through the C ABI (e2e): H2D of the inputs and D2H of
-    # the report inside the timed region
-    ms_e2e, rep_e2e = timed(host_np, args.steps)
-
-    # ---- per-kernel durations for the roofline (a separate pass: the
-    # per-launch events would otherwise sit inside the timed steps)
-    rc.profile_reset()
-    rc.profile_enable(True)
-    timed(dev_in, args.steps)
-    rc.profile_enable(False)
-    prof = [rc.profile_get(k) for k in range(3)]
+    m = measure(rc, inst, bc, steps=args.steps, warmup=args.warmup, dist=dist, flush=flush, prof_steps=prof_steps)
     clk = clocks.stop()
 
+    rep = m["rep"]
     acc_step = rep["n_access"]
-    t_max, ms_e2e = combine([ms, ms_e2e], dist, "max")
+    t_max, ms_e2e = combine([m["ms"], m["ms_e2e"]], dist, "max")
     acc_all, = combine([acc_step], dist, "sum")
     value = acc_all * args.steps / (t_max / 1e3)
     e2e = acc_all * args.steps / (ms_e2e / 1e3)
 
-    # roofline: the interpreter kernel (resident runs: one launch per check,
-    # every interval; else one launch per interval).  Algorithmic bytes: 12 B
-    # per global access (cell, work-item|rw, value) -- the log write half of
-    # the 24 B per global access the log/classify path must move.
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    p0 = prof[0]
-    interp_ms = p0["ms"] / max(p0["launches"], 1)
-    achieved = (p0["bytes"] / max(p0["launches"], 1)) / (interp_ms / 1e3) / 1e9 if interp_ms else 0.0
-    priv = np.ascontiguousarray(rc.prove_private(bc, inst.groups, inst.group_size, inst.globals), dtype=np.uint8)
-    same_kernel = (INTERP_TRAFFIC["sources_sha256"] == interp_sources_sha256() and
-                   INTERP_TRAFFIC["private_flags_sha256"] == hashlib.sha256(priv.tobytes()).hexdigest())
-    traffic = INTERP_TRAFFIC["bytes_per_launch"] if same_kernel else None
-    roof = {"kernel": "interp_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-            "algorithmic_bytes_per_launch": p0["bytes"] / max(p0["launches"], 1),
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s",
-            "avg_launch_ms": interp_ms,
-            "classify_ms_per_pass": prof[1]["ms"] / max(prof[1]["launches"], 1),
-            "classify_passes_per_check": prof[1]["launches"] / max(args.steps, 1),
-            "classify_algorithmic_gbs": (prof[1]["bytes"] / max(prof[1]["ms"], 1e-9)) / 1e6}
+    same_kernel = (args.workload == "stress" and full_size and rank == 0 and
+                   INTERP_TRAFFIC["sources_sha256"] == interp_sources_sha256() and
+                   INTERP_TRAFFIC["program_sha256"] == hashlib.sha256(inst.src.encode()).hexdigest())
+    roof = roofline(m, hbm, peak_source, INTERP_TRAFFIC["bytes_per_launch"] if same_kernel else None)
+
+    # cold end to end: a freshly compiled program's first check from host
+    # inputs (the pre-filter's analysis of this program and launch shape runs
+    # inside it; later checks of the program reuse it)
+    host_np = [torch.from_numpy(a).pin_memory().numpy() for a in inst.globals]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bc_cold = rc.compile(inst.src)
+    r_cold = rc.check(bc_cold, inst.groups, inst.group_size, host_np, want_final=False)
+    t_cold = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rc.check(bc_cold, inst.groups, inst.group_size, host_np, want_final=False)
+    t_warm = time.perf_counter() - t0
+    del host_np
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "accesses_per_step": acc_step,
-                   "global_accesses_per_step": rep["n_global"],
+        "config": {"workload": WORKLOADS[args.workload] + ("" if full_size else f" (reduced to {inst.groups} groups)"),
+                   "work_items": inst.groups * inst.group_size,
+                   "accesses_per_step": acc_step, "global_accesses_per_step": rep["n_global"],
+                   "logged_accesses_per_step": rep["n_logged"],
+                   "private_accesses_per_step": acc_step - rep["n_logged"],
+                   "race_records_per_step": int((rep["records"][:, 4] < 16).sum()) if len(rep["records"]) else 0,
+                   "status": rep["status"], "intervals": rep["n_intervals"],
                    "strategy": {0: "auto", 1: "sort", 2: "shadow", 3: "resident"}[args.strategy],
-                   "run": "resident: one cooperative launch per check" if p0["launches"] == args.steps
+                   "run": "resident: one cooperative launch per check" if roof["launches_per_check"] == 1
                           else "interval by interval",
-                   "private_access_insns": int(priv.sum()),
-                   "private_accesses": "counted and committed, not logged (two-work-item pre-filter)",
-                   "l2": "flushed between steps (256 MiB write)",
+                   "private_accesses": "counted and committed, not logged (two-work-item pre-filter); "
+                                       "see full_logging for every access logged",
+                   "l2": "flushed between steps (256 MiB write); the 256 MiB input exceeds L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof,
-        "e2e": {"value": e2e, "unit": UNIT,
-                "h2d_bytes_per_step": int(sum(a.nbytes for a in host_np)),
-                "d2h_bytes_per_step": int(rep_e2e["records"].nbytes)},
-        "gpu_launches": int(launches),
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": m["h2d"],
+                "d2h_bytes_per_step": int(m["rep_e2e"]["records"].nbytes)},
+        "e2e_cold": {"what": "fresh rc_compile + first rc_check from host inputs (pre-filter analysis included)",
+                     "value": r_cold["n_access"] / t_cold, "unit": UNIT, "seconds": t_cold,
+                     "warm_seconds": t_warm},
+        "gpu_launches": int(m["launches"]),
         "clocks": clk,
     }
-    if args.batch_kernels > 0:
-        out["batch"] = batch_leg(rc, W, args.batch_kernels, rank, world, dist)
-    if args.proposal_kernels > 0:
-        out["proposal"] = proposal_leg(rc, args.proposal_kernels)
+    if args.secondary == "all":
+        # the same instance with every access logged (no pre-filter)
+        f = measure(rc, inst, bc, steps=min(args.steps, 3), warmup=1, dist=dist, flush=flush,
+                    log_every=True, host=False, prof_steps=2)
+        fr = f["rep"]
+        assert fr["n_logged"] == fr["n_access"] and fr["status"] == rep["status"]
+        assert np.array_equal(fr["records"], rep["records"]), "the pre-filter changed the report"
+        t_f, = combine([f["ms"]], dist, "max")
+        acc_f, = combine([fr["n_access"]], dist, "sum")
+        out["full_logging"] = {"what": "same instance, every access logged (RC_LOG_EVERY_ACCESS)",
+                               "value": acc_f * f["steps"] / (t_f / 1e3), "unit": UNIT,
+                               "ms_per_step": t_f / f["steps"], "logged_accesses_per_step": fr["n_logged"],
+                               "roofline": roofline(f, hbm, peak_source)}
+        del f
+        if args.workload == "stress":
+            # the 1024 x 256 large instance
+            li = W.large_kernel(rank)
+            lbc = rc.compile(li.src)
+            lm = measure(rc, li, lbc, steps=args.steps, warmup=args.warmup, dist=dist, flush=flush,
+                         prof_steps=prof_steps)
+            t_l, t_le = combine([lm["ms"], lm["ms_e2e"]], dist, "max")
+            acc_l, = combine([lm["rep"]["n_access"]], dist, "sum")
+            out["large"] = {"workload": WORKLOADS["large"], "value": acc_l * lm["steps"] / (t_l / 1e3),
+                            "unit": UNIT, "ms_per_step": t_l / lm["steps"],
+                            "e2e": acc_l * lm["steps"] / (t_le / 1e3),
+                            "logged_accesses_per_step": lm["rep"]["n_logged"],
+                            "accesses_per_step": lm["rep"]["n_access"],
+                            "roofline": roofline(lm, hbm, peak_source)}
+        if args.batch_kernels > 0:
+            out["batch"] = batch_leg(rc, W, args.batch_kernels, rank, world, dist, hbm)
+        if args.proposal_kernels > 0:
+            out["proposal"] = proposal_leg(rc, args.proposal_kernels)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline()
+        out["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -77,6 +77,12 @@ extern "C" {
  * rc_check and rc_search take it; rc_check_batch, rc_explore and
  * rc_explore_pairs return RC_E_INVALID. */
 #define RC_GROUP_BARRIERS 2u
+/* Log every shared access: the two-work-item pre-filter (rc_prove_private)
+ * is not consulted, so no access is taken as private; every access is
+ * written to its interval's log and claims its cell.  Same report (the
+ * pre-filter only drops accesses that cannot change it), n_logged =
+ * n_access. */
+#define RC_LOG_EVERY_ACCESS 4u
 
 typedef struct rc_bytecode rc_bytecode; /* opaque, library-owned */
 
@@ -144,6 +150,11 @@ typedef struct {
   rc_record *records;
   uint64_t final_len;     /* global cells (sum of global_len)    */
   int32_t *final_global;  /* final global memory, or NULL        */
+  uint64_t n_logged;      /* accesses written to the interval    */
+                          /* logs; the others were proved        */
+                          /* private (no other work-item touches */
+                          /* their cells in the interval) and    */
+                          /* were counted, not logged            */
 } rc_report;
 
 /* Compile kernel source text (Sec. 3 grammar, see the package docs for the

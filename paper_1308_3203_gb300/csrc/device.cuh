@@ -66,6 +66,7 @@ struct InterpArgs {
   uint32_t err_cap;
   uint32_t *stop_min, *stop_cnt;  // [n_barriers + 1], last slot = exit
   unsigned long long *acc;        // [0] global accesses, [1] local accesses
+  unsigned long long *logged;     // accesses written to the log (the rest are private: CTL_PRIV)
   uint32_t *flags;                // bit 0 log full, bit 1 own-write table full, bit 2 error log full
                                   // (resident runs: two words, by interval parity)
   uint32_t *ow_count;             // [N] own-write entries per work-item

@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
   // the CTA before they reach the kernel-wide table: every work-item of the
   // kernel reports one, and same-address atomics serialise in L2.  Each
   // warp folds its lanes by stop point; thread 0 folds the warps' entries.
-  __shared__ uint32_t s_stop[32], s_min[32], s_cnt[32], s_acc[2][32];
+  __shared__ uint32_t s_stop[32], s_min[32], s_cnt[32], s_acc[3][32];
   const bool stopping = st == TS_BARRIER || (st == TS_EXIT && ran);
   // resident runs alternate two stop tables by interval parity
   uint32_t *const stop_min = A.stop_min + (kResident ? (INTERVAL & 1u) * nstops : 0u);
@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
     if ((tid & 31u) == 0) {
       s_acc[0][warp] = sg;
       s_acc[1][warp] = sl;
+      s_acc[2][warp] = wfill;  // warp-uniform: this warp's records in the log
     }
     const uint32_t smask = __ballot_sync(lanes, stopping);
     const uint32_t lane = tid & 31u;
@@ -349,13 +350,15 @@ __global__ void __launch_bounds__(1024, 2) interp_kernel(InterpArgs A) {
   __syncthreads();
   if (tid == 0) {
     const uint32_t nwarps = (S + 31u) / 32u;
-    unsigned long long cg = 0, cl = 0;
+    unsigned long long cg = 0, cl = 0, cw = 0;
     for (uint32_t w = 0; w < nwarps; w++) {
       cg += s_acc[0][w];
       cl += s_acc[1][w];
+      cw += s_acc[2][w];
     }
     if (cg) atomicAdd(&A.acc[0], cg);
     if (cl) atomicAdd(&A.acc[1], cl);
+    if (cw && A.logged) atomicAdd(A.logged, cw);
     uint32_t cur = kNone, cmin = 0, ccnt = 0;
     for (uint32_t w = 0; w < nwarps; w++) {
       if (s_stop[w] == kNone) continue;

@@ -261,11 +261,12 @@ std::string batch_key(uint64_t tasks, uint64_t bound) {
 }
 
 // stats block layout (uint32 words)
-enum : uint32_t { ST_LOGCNT = 0, ST_ACC = 2, ST_FLAGS = 6, ST_ERRCNT = 7, ST_SCRATCH = 8, ST_GDIV = 10, ST_STOPS = 12 };
+enum : uint32_t { ST_LOGGED = 0, ST_ACC = 2, ST_FLAGS = 6, ST_ERRCNT = 7, ST_SCRATCH = 8, ST_GDIV = 10, ST_STOPS = 12 };
 // The two stats buffers (by interval parity) sit stat_words = ST_STOPS +
 // 2 * (n_barriers + 1) words apart, and each holds 64-bit counters at ST_ACC
 // and ST_SCRATCH: ST_STOPS must be even so both buffers keep them 8-byte aligned.
-static_assert(ST_STOPS % 2 == 0 && ST_ACC % 2 == 0 && ST_SCRATCH % 2 == 0, "64-bit stats words need 8-byte alignment");
+static_assert(ST_STOPS % 2 == 0 && ST_ACC % 2 == 0 && ST_SCRATCH % 2 == 0 && ST_LOGGED % 2 == 0,
+              "64-bit stats words need 8-byte alignment");
 
 uint32_t bitwidth(uint64_t v) {  // bits needed to represent values < v (v >= 1)
   uint32_t b = 0;
@@ -465,13 +466,15 @@ void shadow_finish(Workspace &W, uint64_t m, uint64_t keys, uint64_t N, uint32_t
 // records, counters, status (Sec. 4: racy iff a WW or RW race record) and,
 // if asked, the final global memory read from the device snapshot.
 rc_report *make_report(const std::vector<OutRec> &races, const std::vector<OutRec> &errors, uint32_t n_intervals,
-                       uint64_t acc_g, uint64_t acc_l, uint64_t GT, const int32_t *final_dev, cudaStream_t s) {
+                       uint64_t acc_g, uint64_t acc_l, uint64_t logged, uint64_t GT, const int32_t *final_dev,
+                       cudaStream_t s) {
   rc_report *rep = static_cast<rc_report *>(std::calloc(1, sizeof(rc_report)));
   if (!rep) throw Fail{RC_E_NOMEM, "report allocation failed"};
   rep->n_intervals = n_intervals;
   rep->n_global = acc_g;
   rep->n_local = acc_l;
   rep->n_access = acc_g + acc_l;
+  rep->n_logged = logged;
   bool racy = false, div = false, as = false, oob = false;
   for (const OutRec &x : races)
     racy |= x.cls == CLS_WW_RACE || x.cls == CLS_RW_RACE || x.cls == CLS_XG_WW_RACE || x.cls == CLS_XG_RW_RACE;
@@ -605,11 +608,11 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   }
   if (slots < 0) return nullptr;
   const uint32_t nstops = P.n_barriers + 1;
-  // device words: [0..2] unused, [3] error count,
+  // device words: [0,1] logged accesses (u64), [2] unused, [3] error count,
   // [4,5] intervals run / last tag, [6,7] flags by interval parity, [8,9] compacted records
   // (u64), [10..13] access counters (2 x u64), then two stop tables (smallest work-item, count)
   // by interval parity
-  enum : uint32_t { R_BAR = 0, R_ERRS = 3, R_INFO = 4, R_FLAGS = 6, R_TOTAL = 8, R_ACC = 10, R_STOPS = 14 };
+  enum : uint32_t { R_LOGGED = 0, R_BAR = 0, R_ERRS = 3, R_INFO = 4, R_FLAGS = 6, R_TOTAL = 8, R_ACC = 10, R_STOPS = 14 };
   const size_t words = R_STOPS + 4 * nstops;
   uint32_t *d = W.rstat.get<uint32_t>(words);
   CK(cudaMemsetAsync(d, 0, words * 4, s));
@@ -631,6 +634,7 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   a.stop_min = d + R_STOPS;
   a.stop_cnt = d + R_STOPS + 2 * nstops;
   a.acc = reinterpret_cast<unsigned long long *>(d + R_ACC);
+  a.logged = reinterpret_cast<unsigned long long *>(d + R_LOGGED);
   a.flags = d + R_FLAGS;
   a.proceed = nullptr;
   a.group_div = nullptr;
@@ -679,6 +683,7 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   const uint32_t last = n_run - 1;
   const uint64_t acc_g = *reinterpret_cast<const uint64_t *>(&h[R_ACC]);
   const uint64_t acc_l = *reinterpret_cast<const uint64_t *>(&h[R_ACC + 2]);
+  const uint64_t logged = *reinterpret_cast<const uint64_t *>(&h[R_LOGGED]);
   if (g_prof.on) {
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, g_prof.ev[0], g_prof.ev[1]));
@@ -722,7 +727,7 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
     g_prof.ms[1] += ms;
     g_prof.bytes[1] += 12.0 * (double)acc_g;
   }
-  return make_report(races, errors, n_run, acc_g, acc_l, L.GT, (I.in->flags & RC_WANT_FINAL_MEMORY) ? snap : nullptr,
+  return make_report(races, errors, n_run, acc_g, acc_l, logged, L.GT, (I.in->flags & RC_WANT_FINAL_MEMORY) ? snap : nullptr,
                      s);
 }
 
@@ -785,8 +790,9 @@ rc_report *run_instance(const Instance &I) {
   // from the owner table (resident runs, the shadow strategy throughout);
   // the full sort commits from the log, the cross-group table and the
   // explorer read it
+  const bool prefilter = !group && !I.explore && !(I.in->flags & RC_LOG_EVERY_ACCESS);
   const std::vector<Insn> *pcode =
-      !group && !I.explore && (resident_wanted || fixed_strategy == 2) ? &private_code(P, I.G, I.S, I.in) : nullptr;
+      prefilter && (resident_wanted || fixed_strategy == 2) ? &private_code(P, I.G, I.S, I.in) : nullptr;
   const std::vector<Insn> &interval_code = pcode && fixed_strategy == 2 ? *pcode : P.code;
   upload_code(pcode && resident_wanted ? *pcode : interval_code);
   if (!L.mems.empty())
@@ -931,6 +937,7 @@ rc_report *run_instance(const Instance &I) {
     a.stop_min = d + ST_STOPS;
     a.stop_cnt = d + ST_STOPS + nstops;
     a.acc = reinterpret_cast<unsigned long long *>(d + ST_ACC);
+    a.logged = reinterpret_cast<unsigned long long *>(d + ST_LOGGED);
     a.flags = d + ST_FLAGS;
     a.owner = strategy == 2 ? owner : nullptr;
     a.tag = tag;
@@ -958,7 +965,7 @@ rc_report *run_instance(const Instance &I) {
   };
 
   std::vector<OutRec> races, errors;
-  uint64_t tot_g = 0, tot_l = 0;
+  uint64_t tot_g = 0, tot_l = 0, tot_logged = 0;
   uint32_t interval = 0;
   int strategy = fixed_strategy ? fixed_strategy : g_tuner.choose(tkey);
   bool timed = !fixed_strategy && !g_tuner.decided(tkey);  // autotuner sample of this interval
@@ -990,6 +997,7 @@ rc_report *run_instance(const Instance &I) {
     if (flags) throw Fail{RC_E_CAPACITY, "interval log, own-write table or error log overflowed"};
     const uint64_t acc_g = *reinterpret_cast<const uint64_t *>(h + ST_ACC);
     const uint64_t acc_l = *reinterpret_cast<const uint64_t *>(h + ST_ACC + 2);
+    tot_logged += *reinterpret_cast<const uint64_t *>(h + ST_LOGGED);
     const uint64_t m = *reinterpret_cast<const uint64_t *>(h + ST_SCRATCH);
     std::vector<uint32_t> stop_min(h + ST_STOPS, h + ST_STOPS + nstops);
     std::vector<uint32_t> stop_cnt(h + ST_STOPS + nstops, h + ST_STOPS + 2 * nstops);
@@ -1080,7 +1088,7 @@ rc_report *run_instance(const Instance &I) {
       CK(cudaStreamSynchronize(s));
     }
   }
-  return make_report(races, errors, interval + 1, tot_g, tot_l, L.GT,
+  return make_report(races, errors, interval + 1, tot_g, tot_l, tot_logged, L.GT,
                      (I.in->flags & RC_WANT_FINAL_MEMORY) ? snap : nullptr, s);
 }
 
@@ -1385,7 +1393,9 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   s = bs;  // final memories are read on the batch stream
   for (uint32_t k = 0; k < n; k++) {
     const BatchItem &it = items[k];
-    out[k] = make_report(races[k], errors[k], n_intervals[k], acc[2 * k], acc[2 * k + 1], it.L.GT,
+    // batches log every access (no private accesses)
+    out[k] = make_report(races[k], errors[k], n_intervals[k], acc[2 * k], acc[2 * k + 1],
+                         acc[2 * k] + acc[2 * k + 1], it.L.GT,
                          (it.in->flags & RC_WANT_FINAL_MEMORY) ? snap + kbase[k] : nullptr, s);
   }
 }

@@ -25,6 +25,7 @@ RACE_FREE, RACY, ERROR_OOB, ERROR_ASSERT, ERROR_DIVERGENCE = 0, 1, 2, 3, 4
 STRATEGY_AUTO, STRATEGY_SORT, STRATEGY_SHADOW, STRATEGY_RESIDENT = 0, 1, 2, 3
 RC_WANT_FINAL_MEMORY = 1
 RC_GROUP_BARRIERS = 2
+RC_LOG_EVERY_ACCESS = 4
 
 
 class RaceCheckError(RuntimeError):
@@ -47,7 +48,7 @@ class _Report(ctypes.Structure):
                 ("n_access", ctypes.c_uint64), ("n_global", ctypes.c_uint64),
                 ("n_local", ctypes.c_uint64), ("n_records", ctypes.c_uint64),
                 ("records", ctypes.c_void_p), ("final_len", ctypes.c_uint64),
-                ("final_global", ctypes.c_void_p)]
+                ("final_global", ctypes.c_void_p), ("n_logged", ctypes.c_uint64)]
 
 
 class _Info(ctypes.Structure):
@@ -255,20 +256,23 @@ def _report(p) -> dict:
         fin = np.zeros(r.final_len, dtype=np.int32)
         ctypes.memmove(fin.ctypes.data, r.final_global, r.final_len * 4)
     out = dict(status=r.status, n_intervals=r.n_intervals, n_access=r.n_access,
-               n_global=r.n_global, n_local=r.n_local, records=recs, final=fin)
+               n_global=r.n_global, n_local=r.n_local, n_logged=r.n_logged, records=recs, final=fin)
     load().rc_report_free(p)
     return out
 
 
 def check(bc: Bytecode, groups: int, group_size: int, globals_, stream=None,
-          want_final: bool = True, group_barriers: bool = False) -> dict:
+          want_final: bool = True, group_barriers: bool = False, log_every_access: bool = False) -> dict:
     """Check one instance.  ``globals_``: one int32 array per ``global``
     declaration (numpy / host tensors, or contiguous int32 CUDA tensors).
-    ``group_barriers``: barriers are work-group scoped (RC_GROUP_BARRIERS)."""
+    ``group_barriers``: barriers are work-group scoped (RC_GROUP_BARRIERS).
+    ``log_every_access``: no access is taken as private (RC_LOG_EVERY_ACCESS)."""
     lib = load()
     inp, keep = _marshal(globals_, stream, want_final)
     if group_barriers:
         inp.flags |= RC_GROUP_BARRIERS
+    if log_every_access:
+        inp.flags |= RC_LOG_EVERY_ACCESS
     out = ctypes.POINTER(_Report)()
     rc = lib.rc_check(bc.handle, groups, group_size, ctypes.byref(inp), ctypes.byref(out))
     del keep
