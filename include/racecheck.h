@@ -257,6 +257,31 @@ int rc_diag_grid_barrier(uint32_t limit_us, int32_t *timed_out, double *seconds)
  * take 3 as 0.  Returns RC_E_INVALID for other values. */
 int rc_set_strategy(int strategy);
 
+/* Engine of the interval kernels for later rc_check / rc_search calls:
+ * 0 = automatic (compiled intervals for instances of at least 2^17
+ * work-items when NVRTC can be loaded, else the interpreter), 1 = the
+ * bytecode interpreter, 2 = compiled intervals (rc_check then returns
+ * RC_E_INVALID when NVRTC cannot be loaded).  Compiled intervals translate
+ * the program's bytecode into one straight-line function per program
+ * (rc_translate) and compile it, with the interpreter's access, logging and
+ * barrier steps, into an interval kernel of its own at run time (NVRTC,
+ * sm_103a; cached per program, launch shape and mode).  Reports are the
+ * same under both engines.  Work-group-scoped barriers, batches and the
+ * explorers always interpret.  Returns RC_E_INVALID for other values. */
+int rc_set_engine(int engine);
+
+/* Compile the interval kernel of (bc, groups, group_size, in) -- the
+ * pre-filter's private accesses for that launch shape included -- without
+ * loading it (no GPU needed): a check of the generated source.  resident:
+ * the kernel of one-launch runs instead of one launch per interval.
+ * *seconds = compile time (0 when it was cached), *cubin_bytes = its size
+ * (either may be NULL).  RC_E_INVALID when NVRTC cannot be loaded or the
+ * compile fails (message in rc_last_error()). */
+int rc_jit_compile(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in, int resident,
+                   double *seconds, uint64_t *cubin_bytes);
+/* Interval kernels compiled so far by this process and their total compile seconds. */
+int rc_jit_stats(uint64_t *compiles, double *seconds);
+
 /* Autotuner of the classification strategy (strategy 0 above).  Per size
  * class -- single instances by work-items and per-interval access bound,
  * batches by warp tasks and bound -- an undecided class alternates the two

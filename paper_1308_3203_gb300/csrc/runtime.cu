@@ -25,6 +25,7 @@
 
 #include "racecheck.h"
 #include "device.cuh"
+#include "jit.h"
 
 namespace rc {
 // The two-work-item pre-filter (prove.cpp).
@@ -38,6 +39,11 @@ thread_local std::string g_last_error;
 std::atomic<uint64_t> g_launches{0};
 std::mutex g_mu;
 int g_strategy = 0;
+// interval kernels: 0 automatic, 1 bytecode interpreter, 2 compiled intervals
+int g_engine = 0;
+// automatic engine: compiled intervals from this many work-items on (one
+// NVRTC compile, a fraction of a second, per program and launch shape)
+constexpr uint64_t kJitAutoItems = 1ull << 17;
 
 struct Fail {
   int code;
@@ -582,7 +588,8 @@ const std::vector<Insn> &private_code(const Program &P, uint32_t G, uint32_t S, 
 }
 
 rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const InterpArgs &base, size_t base_smem,
-                        uint32_t *owner, int32_t *snap, OutRec *errs, uint32_t *hscratch, cudaStream_t s) {
+                        uint32_t *owner, int32_t *snap, OutRec *errs, uint32_t *hscratch, cudaStream_t s,
+                        const JitKernel *jk) {
   const Program &P = *I.p;
   static int coop = -1;
   if (coop < 0) {
@@ -597,10 +604,12 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   const int nsm = sm_count();
   int slots = -1;
   size_t smem = 0;
+  const size_t max_dyn = jk ? kMaxSmemPerBlock - jk->static_smem : interp_max_dynamic_smem();
   for (int sl = (int)std::min<uint64_t>(8, P.max_write_per_interval); sl >= 0; sl--) {
     const size_t sm = base_smem + (size_t)sl * I.S * 8;
-    if (sm > interp_max_dynamic_smem()) continue;
-    if ((uint64_t)interp_resident_blocks_per_sm((uint32_t)P.code.size(), I.S, sm) * nsm >= I.G) {
+    if (sm > max_dyn) continue;
+    const int per_sm = jk ? jit_blocks_per_sm(*jk, I.S, sm) : interp_resident_blocks_per_sm((uint32_t)P.code.size(), I.S, sm);
+    if ((uint64_t)per_sm * nsm >= I.G) {
       slots = sl;
       smem = sm;
       break;
@@ -651,7 +660,7 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
   a.owner_words = 4 * L.keys;
   a.barrier_limit_ns = 20000000000ull;
   if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
-  const cudaError_t e = launch_interp_resident(a, I.G, smem, s);
+  const cudaError_t e = jk ? launch_jit_resident(*jk, a, I.G, smem, s) : launch_interp_resident(a, I.G, smem, s);
   if (e == cudaErrorCooperativeLaunchTooLarge) {
     cudaGetLastError();
     return nullptr;
@@ -795,6 +804,36 @@ rc_report *run_instance(const Instance &I) {
       prefilter && (resident_wanted || fixed_strategy == 2) ? &private_code(P, I.G, I.S, I.in) : nullptr;
   const std::vector<Insn> &interval_code = pcode && fixed_strategy == 2 ? *pcode : P.code;
   upload_code(pcode && resident_wanted ? *pcode : interval_code);
+  // compiled intervals: one kernel per program, launch shape and mode (cached)
+  const bool jit = !group && !I.explore && g_engine != 1 && (g_engine == 2 || N >= kJitAutoItems);
+  JitKernel jk_res, jk_iv;
+  bool have_res = false, have_iv = false;
+  if (jit) {
+    std::string why;
+    if (!jit_available(&why)) {
+      if (g_engine == 2) throw Fail{RC_E_INVALID, "compiled intervals unavailable: " + why};
+    } else {
+      try {
+        const uint32_t nsm = (uint32_t)sm_count();
+        const uint32_t per_sm = (I.G + nsm - 1) / nsm;  // CTAs each SM must hold for a resident run
+        if (resident_wanted && (uint64_t)per_sm * I.S <= 2048) {
+          JitShape sh;
+          sh.resident = true;
+          sh.threads = I.S;
+          sh.min_blocks = std::min<uint32_t>(per_sm, 32);  // 32: the most CTAs an SM holds
+          jk_res = jit_kernel(P, pcode ? *pcode : P.code, sh);
+          have_res = true;
+        }
+        JitShape sh;
+        sh.threads = I.S;
+        sh.min_blocks = std::min<uint32_t>(std::max<uint32_t>(1, 1024 / I.S), 32);
+        jk_iv = jit_kernel(P, interval_code, sh);
+        have_iv = smem <= kMaxSmemPerBlock - jk_iv.static_smem;
+      } catch (const JitError &e) {
+        throw Fail{RC_E_CUDA, e.msg};
+      }
+    }
+  }
   if (!L.mems.empty())
     CK(cudaMemcpyAsync(dmems, L.mems.data(), L.mems.size() * sizeof(MemInfo), cudaMemcpyHostToDevice, s));
   int32_t *snap = W.snap.get<int32_t>(std::max<uint64_t>(L.keys, 1));
@@ -886,7 +925,8 @@ rc_report *run_instance(const Instance &I) {
   base.err_cap = err_cap;
   base.ow_count = ow_cnt;
   if (resident_wanted) {
-    rc_report *r = run_resident(W, I, L, base, base_smem, owner, snap, errs2, hscratch, s);
+    rc_report *r = run_resident(W, I, L, base, base_smem, owner, snap, errs2, hscratch, s,
+                                have_res ? &jk_res : nullptr);
     if (r) return r;
     load_snapshot();  // the resident run stopped early: start over interval by interval
     if (pcode && &interval_code != pcode) upload_code(interval_code);
@@ -945,7 +985,15 @@ rc_report *run_instance(const Instance &I) {
     a.group_div = group ? d + ST_GDIV : nullptr;
     if (timed) CK(cudaEventRecord(g_tev[0], s));
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
-    launch_interp(a, I.G, smem, s);
+    if (have_iv) {
+      try {
+        launch_jit(jk_iv, a, I.G, smem, s);
+      } catch (const JitError &e) {
+        throw Fail{RC_E_CUDA, e.msg};
+      }
+    } else {
+      launch_interp(a, I.G, smem, s);
+    }
     CK(cudaGetLastError());
     if (g_prof.on) {
       CK(cudaEventRecord(g_prof.ev[1], s));
@@ -1739,6 +1787,47 @@ int rc_set_strategy(int strategy) {
   if (strategy < 0 || strategy > 3) return RC_E_INVALID;
   std::lock_guard<std::mutex> lk(g_mu);
   g_strategy = strategy;
+  return RC_OK;
+}
+
+int rc_set_engine(int engine) {
+  if (engine < 0 || engine > 2) return RC_E_INVALID;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_engine = engine;
+  return RC_OK;
+}
+
+int rc_jit_compile(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in, int resident,
+                   double *seconds, uint64_t *cubin_bytes) {
+  try {
+    check_args(bc, groups, group_size, in);
+    std::string why;
+    if (!jit_available(&why)) throw Fail{RC_E_INVALID, "compiled intervals unavailable: " + why};
+    const std::vector<Insn> &code = private_code(bc->prog, groups, group_size, in);
+    JitShape sh;
+    sh.resident = resident != 0;
+    sh.threads = group_size;
+    sh.min_blocks = resident ? 2 : std::min<uint32_t>(std::max<uint32_t>(1, 1024 / group_size), 32);
+    sh.load = false;
+    const auto t0 = std::chrono::steady_clock::now();
+    const JitKernel k = jit_kernel(bc->prog, code, sh);
+    if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (cubin_bytes) *cubin_bytes = k.cubin_bytes;
+    return RC_OK;
+  } catch (const Fail &f) {
+    return fail_code(f);
+  } catch (const JitError &e) {
+    g_last_error = e.msg;
+    return RC_E_INVALID;
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return RC_E_NOMEM;
+  }
+}
+
+int rc_jit_stats(uint64_t *compiles, double *seconds) {
+  if (!compiles || !seconds) return RC_E_INVALID;
+  jit_stats(compiles, seconds);
   return RC_OK;
 }
 

@@ -3,9 +3,11 @@
 // shared by every kernel that executes bytecode, so the canonical checker,
 // the batched checker and the interleaving explorer compute the same thing.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
-#include "bytecode.h"
+#include "isa.h"
 
 namespace rc {
 

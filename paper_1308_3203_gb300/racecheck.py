@@ -112,6 +112,13 @@ def load() -> ctypes.CDLL:
         lib.rc_last_error.argtypes = []
         lib.rc_last_error.restype = ctypes.c_char_p
         lib.rc_set_strategy.argtypes = [c_int]
+        lib.rc_set_engine.argtypes = [c_int]
+        lib.rc_set_engine.restype = c_int
+        lib.rc_jit_compile.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input), c_int,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]
+        lib.rc_jit_compile.restype = c_int
+        lib.rc_jit_stats.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]
+        lib.rc_jit_stats.restype = c_int
         lib.rc_profile_enable.argtypes = [c_int]
         lib.rc_profile_get.argtypes = [c_int, ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(ctypes.c_double),
@@ -305,6 +312,39 @@ def set_strategy(k: int) -> None:
     rc = load().rc_set_strategy(k)
     if rc:
         _raise(rc)
+
+
+ENGINES = {"auto": 0, "interpreter": 1, "compiled": 2}
+
+
+def set_engine(engine) -> None:
+    """Engine of the interval kernels: "auto", "interpreter" or "compiled"
+    (or 0, 1, 2)."""
+    rc = load().rc_set_engine(ENGINES.get(engine, engine) if isinstance(engine, str) else engine)
+    if rc:
+        _raise(rc)
+
+
+def jit_compile(bc: Bytecode, groups: int, group_size: int, globals_, resident: bool = False) -> dict:
+    """Compile (without loading) the interval kernel of an instance: a check
+    of the generated source that needs no GPU."""
+    lib = load()
+    inp, keep = _marshal(globals_, None, False)
+    sec, nb = ctypes.c_double(), ctypes.c_uint64()
+    rc = lib.rc_jit_compile(bc.handle, groups, group_size, ctypes.byref(inp), 1 if resident else 0,
+                            ctypes.byref(sec), ctypes.byref(nb))
+    del keep
+    if rc:
+        _raise(rc)
+    return {"seconds": sec.value, "cubin_bytes": nb.value}
+
+
+def jit_stats() -> dict:
+    n, sec = ctypes.c_uint64(), ctypes.c_double()
+    rc = load().rc_jit_stats(ctypes.byref(n), ctypes.byref(sec))
+    if rc:
+        _raise(rc)
+    return {"compiles": n.value, "seconds": sec.value}
 
 
 def profile_enable(on: bool = True) -> None:
