@@ -58,8 +58,9 @@ SAMPLE_GROUPS = {"stress": 128, "large": 96}
 # It holds only for the kernel sources and the stress program it was taken
 # on; a change to either reports null.
 INTERP_TRAFFIC = {"sources_sha256": None, "program_sha256": None, "bytes_per_launch": None}
-INTERP_SOURCES = ("paper_1308_3203_gb300/csrc/interp.cu", "paper_1308_3203_gb300/csrc/device.cuh",
-                  "paper_1308_3203_gb300/csrc/semantics.cuh")
+INTERP_SOURCES = ("paper_1308_3203_gb300/csrc/interp_kernel.cuh", "paper_1308_3203_gb300/csrc/jit_engine.cuh",
+                  "paper_1308_3203_gb300/csrc/kernel_types.cuh", "paper_1308_3203_gb300/csrc/semantics.cuh",
+                  "paper_1308_3203_gb300/csrc/translate.cpp", "paper_1308_3203_gb300/csrc/jit.cu")
 
 
 def interp_sources_sha256() -> str:
@@ -340,9 +341,10 @@ def measure(rc, inst, bc, *, steps, warmup, dist, flush, log_every=False, host=T
     return out
 
 
-def roofline(m, peak, peak_source, traffic=None) -> dict:
-    """Roofline of the interpreter kernel (the dominant kernel: it writes the
-    access logs).  Algorithmic bytes per launch: 12 B (cell, work-item and
+def roofline(m, peak, peak_source, traffic=None, kernel="interp_kernel") -> dict:
+    """Roofline of the interval kernel (the dominant kernel: it runs the
+    work-items and writes the access logs; rc_jit_kernel under compiled
+    intervals, interp_kernel under the interpreter).  Algorithmic bytes per launch: 12 B (cell, work-item and
     read/write bit, value) for every access it wrote to a log; accesses the
     pre-filter proved private are not written and not credited."""
     rep, p0, p1 = m["rep"], m["prof"][0], m["prof"][1]
@@ -355,7 +357,7 @@ def roofline(m, peak, peak_source, traffic=None) -> dict:
     path_ms = interp_ms * launches_per_check + classify_ms_per_check
     path_gbs = 24.0 * logged / (path_ms / 1e3) / 1e9 if path_ms else 0.0
     credited = 12.0 * rep["n_access"] / max(launches_per_check, 1e-9) / (interp_ms / 1e3) / 1e9 if interp_ms else 0.0
-    return {"kernel": "interp_kernel", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
             "algorithmic_bytes_per_launch": bytes_per_launch,
             "bytes_rule": "12 B per logged access (written once by the interpreter)",
@@ -396,9 +398,25 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     inst = make_instance(W, args.workload, rank, args.groups)
-    bc = rc.compile(inst.src)
     full_size = args.groups == 0
     prof_steps = min(args.steps, 5)
+
+    # cold end to end: the process's first check of the program, from host
+    # inputs: rc_compile, the pre-filter's analysis of the launch shape and
+    # the compile of its interval kernel (NVRTC) included, all of which later
+    # checks of the program reuse
+    host_np = [torch.from_numpy(a).pin_memory().numpy() for a in inst.globals]
+    torch.cuda.synchronize()
+    jit0 = rc.jit_stats()
+    t0 = time.perf_counter()
+    bc = rc.compile(inst.src)
+    r_cold = rc.check(bc, inst.groups, inst.group_size, host_np, want_final=False)
+    t_cold = time.perf_counter() - t0
+    jit1 = rc.jit_stats()
+    t0 = time.perf_counter()
+    rc.check(bc, inst.groups, inst.group_size, host_np, want_final=False)
+    t_warm = time.perf_counter() - t0
+    del host_np
 
     clocks = Clocks(local)
     clocks.start()
@@ -415,21 +433,8 @@ def main():
     same_kernel = (args.workload == "stress" and full_size and rank == 0 and
                    INTERP_TRAFFIC["sources_sha256"] == interp_sources_sha256() and
                    INTERP_TRAFFIC["program_sha256"] == hashlib.sha256(inst.src.encode()).hexdigest())
-    roof = roofline(m, hbm, peak_source, INTERP_TRAFFIC["bytes_per_launch"] if same_kernel else None)
-
-    # cold end to end: a freshly compiled program's first check from host
-    # inputs (the pre-filter's analysis of this program and launch shape runs
-    # inside it; later checks of the program reuse it)
-    host_np = [torch.from_numpy(a).pin_memory().numpy() for a in inst.globals]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    bc_cold = rc.compile(inst.src)
-    r_cold = rc.check(bc_cold, inst.groups, inst.group_size, host_np, want_final=False)
-    t_cold = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    rc.check(bc_cold, inst.groups, inst.group_size, host_np, want_final=False)
-    t_warm = time.perf_counter() - t0
-    del host_np
+    kname = "rc_jit_kernel" if rc.jit_stats()["compiles"] else "interp_kernel"
+    roof = roofline(m, hbm, peak_source, INTERP_TRAFFIC["bytes_per_launch"] if same_kernel else None, kname)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -452,9 +457,11 @@ def main():
         "roofline": roof,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": m["h2d"],
                 "d2h_bytes_per_step": int(m["rep_e2e"]["records"].nbytes)},
-        "e2e_cold": {"what": "fresh rc_compile + first rc_check from host inputs (pre-filter analysis included)",
+        "e2e_cold": {"what": "the process's first rc_compile + rc_check of the program from host inputs "
+                             "(pre-filter analysis and interval-kernel compile included)",
                      "value": r_cold["n_access"] / t_cold, "unit": UNIT, "seconds": t_cold,
-                     "warm_seconds": t_warm},
+                     "warm_seconds": t_warm, "kernel_compiles": jit1["compiles"] - jit0["compiles"]},
+        "engine": "compiled intervals" if rc.jit_stats()["compiles"] else "interpreter",
         "gpu_launches": int(m["launches"]),
         "clocks": clk,
     }

@@ -43,7 +43,7 @@ template <bool kPriv, bool kStore, bool kRes>
 __device__ __forceinline__ bool jit_access(JitCtx<kRes> &cx, uint32_t mem, int32_t idx, int32_t &v) {
   IvState &s = cx.s;
   const uint32_t mask = __activemask();
-  const MemInfo m = s.mems[mem];
+  const MemInfo m = mem < kInlineMems ? cx.A.mem_inline[mem] : s.mems[mem];
   const bool inb = (uint32_t)idx < m.len;
   const uint32_t performing = __ballot_sync(mask, inb);
   const uint32_t slot = kPriv ? 0u : jit_log_slot(cx.fill, mask, performing, s.tid & 31u, s.lane_lt);
@@ -120,6 +120,6 @@ struct JitEngine {
 #define RC_JIT_CTX ::rc::JitCtx<kRes>
 #define RC_LD(cx, site, mem, idx, out) ::rc::jit_load<rc_jit_private(site)>(cx, mem, idx, out)
 #define RC_ST(cx, site, mem, idx, val) ::rc::jit_store<rc_jit_private(site)>(cx, mem, idx, val)
-#define RC_SIZE(cx, mem) ((int32_t)(cx).s.mems[mem].len)
+#define RC_SIZE(cx, mem) ((int32_t)((mem) < ::rc::kInlineMems ? (cx).A.mem_inline[mem] : (cx).s.mems[mem]).len)
 #define RC_ASSERT_FAIL(cx, id) ::rc::jit_assert_fail(cx, id)
 #define RC_AT_BARRIER(cx, id) ((void)0)

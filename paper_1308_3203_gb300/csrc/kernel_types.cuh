@@ -91,7 +91,12 @@ struct InterpArgs {
   uint32_t *run_info;             // [0] intervals run, [1] owner-table tag of the last one
   unsigned long long owner_words; // size of the owner table (cleared in-kernel when the tag wraps)
   unsigned long long barrier_limit_ns;  // longest wait at a grid barrier before the run gives up
+  // the first kInlineMems entries of mems, in the launch arguments (compiled
+  // intervals read them from the constant bank: the memory object of every
+  // access is a constant there)
+  MemInfo mem_inline[4];
 };
+constexpr uint32_t kInlineMems = 4;
 
 // ---- shadow owner table (shadow.cu)
 // Four 32-bit words per cell: [4k] max writer, [4k+1] min writer, [4k+2] max
