@@ -198,6 +198,44 @@ def cpu_baseline(workload: str):
             "sample": f"{sample}: {n} run(s) of {r['n_access']} accesses in {dt:.1f} s"}
 
 
+SMALL_KERNELS = 200
+
+
+def small_leg(rc, W, n=SMALL_KERNELS):
+    """Latency of one check of a small kernel (1 group x 64 work-items, one
+    barrier, 32 statements over A[256]): n kernels, each checked from host
+    inputs through rc_check, host wall clock per check (report on the host
+    included); the automatic strategy takes the one-CTA path."""
+    import torch
+    insts = [W.small_kernel(s) for s in range(n)]
+    bcs = [rc.compile(i.src) for i in insts]
+    for b, i in zip(bcs[:10], insts[:10]):
+        rc.check(b, i.groups, i.group_size, i.globals, want_final=False)
+    torch.cuda.synchronize()
+    l0 = rc.kernel_launches()
+    t0 = time.perf_counter()
+    acc = 0
+    for b, i in zip(bcs, insts):
+        acc += rc.check(b, i.groups, i.group_size, i.globals, want_final=False)["n_access"]
+    dt = time.perf_counter() - t0
+    return {"workload": f"{n} small kernels: 1 group x 64 work-items, 1 barrier, 32 statements, global int32[256]",
+            "us_per_check": 1e6 * dt / n, "launches_per_check": (rc.kernel_launches() - l0) / n,
+            "accesses_per_check": acc / n,
+            "timing": "host wall clock around each rc_check (host inputs, H2D and report included)"}
+
+
+def small_oracle_ms(n=SMALL_KERNELS):
+    """The oracle's time per small kernel (the same n kernels), one core."""
+    from oracle import oracle
+    from paper_1308_3203_gb300 import workloads as W
+    insts = [W.small_kernel(s) for s in range(n)]
+    oracle.build()
+    t0 = time.perf_counter()
+    for i in insts:
+        oracle.check(i.src, i.groups, i.group_size, i.globals)
+    return 1e3 * (time.perf_counter() - t0) / n
+
+
 def shard(n: int, rank: int, world: int) -> range:
     """The units rank `rank` of `world` takes: every world-th, from rank."""
     return range(rank, n, world)
@@ -493,12 +531,17 @@ def main():
                             "logged_accesses_per_step": lm["rep"]["n_logged"],
                             "accesses_per_step": lm["rep"]["n_access"],
                             "roofline": roofline(lm, hbm, peak_source)}
+        out["small"] = small_leg(rc, W)
         if args.batch_kernels > 0:
             out["batch"] = batch_leg(rc, W, args.batch_kernels, rank, world, dist, hbm)
         if args.proposal_kernels > 0:
             out["proposal"] = proposal_leg(rc, args.proposal_kernels)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload)
+        if "small" in out:
+            ms = small_oracle_ms()
+            out["cpu_baseline"]["small"] = {"ms_per_kernel": ms, "kernels": SMALL_KERNELS, "cores": 1}
+            out["small"]["oracle_over_gpu"] = ms * 1e3 / out["small"]["us_per_check"]
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

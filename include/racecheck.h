@@ -246,15 +246,22 @@ int rc_release_workspace(void);
  * the call.  The device stays usable. */
 int rc_diag_grid_barrier(uint32_t limit_us, int32_t *timed_out, double *seconds);
 
-/* Classification strategy for later calls: 0 = automatic (resident when
- * possible, else size-based), 1 = radix sort of the whole log + segmented
- * scan, 2 = shadow-cell owner table + sort of shared cells only, both one
- * launch sequence per barrier interval; 3 = resident: when every work-group
- * fits on the GPU at once (and the group size is a multiple of 32, barriers
- * are kernel-wide), one cooperative launch runs every interval with the
- * owner table, committing in-kernel between grid-wide barriers, and the
- * shared cells' records are sorted after the run; otherwise as 0.  Batches
- * take 3 as 0.  Returns RC_E_INVALID for other values. */
+/* Classification strategy for later calls: 0 = automatic (one CTA for small
+ * instances, else resident when possible, else size-based), 1 = radix sort
+ * of the whole log + segmented scan, 2 = shadow-cell owner table + sort of
+ * shared cells only, both one launch sequence per barrier interval; 3 =
+ * resident: when every work-group fits on the GPU at once (and the group
+ * size is a multiple of 32, barriers are kernel-wide), one cooperative
+ * launch runs every interval with the owner table, committing in-kernel
+ * between grid-wide barriers, and the shared cells' records are sorted
+ * after the run; otherwise as 0; 4 = one CTA: when the instance has at most
+ * 1024 work-items, at most 4096 logged accesses per interval (its static
+ * bound) and at most 63 barriers, one launch of one CTA runs every
+ * interval, sorts and classifies each interval's log in shared memory by
+ * the same rules and applies the barrier-release rule, and writes the
+ * report to page-locked host memory (kernel-wide barriers; the
+ * interpreter); otherwise as 0.  Batches take 3 and 4 as 0.  Returns
+ * RC_E_INVALID for other values. */
 int rc_set_strategy(int strategy);
 
 /* Engine of the interval kernels for later rc_check / rc_search calls:

@@ -48,6 +48,35 @@ cudaError_t interp_upload_code(const Insn *host_code, uint32_t n_insn, cudaStrea
 constexpr size_t kMaxSmemPerBlock = 227 * 1024;  // opt-in shared memory per CTA on sm_103
 size_t interp_max_dynamic_smem();  // valid after interp_configure()
 
+// ---- one-CTA check of small instances (interp.cu): every work-item in one
+// CTA, every interval, its classification and barrier agreement in one launch
+constexpr uint32_t kSmallMaxItems = 1024;  // groups x group size
+constexpr uint32_t kSmallCap = 4096;       // records of one interval (sorted in shared memory)
+constexpr uint32_t kSmallMaxStops = 64;    // barriers + 1
+constexpr uint32_t kSmallBins = 16384;     // (cell, work-item) pairs the counting sort takes
+struct SmallArgs {
+  InterpArgs A;              // program, shape, snapshot (= commit), own-write spill, log slices, errors
+  LogRec *sorted;            // [cap] the interval's records, sorted (global; unused with smem_scratch)
+  Summary *sum;              // [cap] (likewise)
+  OutRec *out;               // [out_cap] race records in report order
+  uint32_t cap;              // records one interval may log (at most kSmallCap)
+  uint32_t out_cap, max_intervals, n_items;
+  uint32_t reg_stride;       // work-items rounded up to whole warps
+  uint32_t smem_scratch;     // sorted records and summaries in shared memory
+  uint32_t smem_snap;        // the snapshot in shared memory (n_cells cells)
+  uint32_t smem_log;         // the warp slices of the log in shared memory
+  uint32_t bins;             // cells x reg_stride counters in shared memory (counting sort), or 0 (bitonic)
+  uint32_t n_cells;
+  // page-locked host memory the kernel writes its results to: res [0] global,
+  // [1] local, [2] logged accesses, [3] intervals | flags << 32, [4] race
+  // records, [5] error records; then the records themselves
+  unsigned long long *res;
+  OutRec *host_out, *host_err;
+};
+size_t small_check_smem(uint32_t n_mems, uint32_t n_regs, uint32_t T, uint32_t ow_slots, uint32_t cap,
+                        uint32_t snap_cells);
+cudaError_t launch_small_check(const SmallArgs &a, uint32_t threads, size_t smem, cudaStream_t s);
+
 // ---- work-group-scoped barriers: cross-group classification (xgroup.cu)
 // One global cell over the whole run: smallest/largest writer and reader,
 // smallest/largest value written, smallest/largest value observed (seeded

@@ -310,14 +310,15 @@ void features_one(const Cand &c, float *out) {
 
   const Analysis an = analyse(p, S, G);
   // work-item sample: all of them when few, else both ends and an even spread
+  // (1024 in all: the ranking must cost less than the checks it saves)
   std::vector<uint32_t> smp;
-  if (N <= 4096) {
+  if (N <= 1024) {
     smp.resize(N);
     std::iota(smp.begin(), smp.end(), 0u);
   } else {
-    for (uint32_t i = 0; i < 1024; i++) smp.push_back(i);
-    for (uint32_t i = 0; i < 1024; i++) smp.push_back((uint32_t)(N - 1024 + i));
-    for (uint32_t i = 0; i < 2048; i++) smp.push_back((uint32_t)((N * (2 * i + 1)) / 4096));
+    for (uint32_t i = 0; i < 256; i++) smp.push_back(i);
+    for (uint32_t i = 0; i < 256; i++) smp.push_back((uint32_t)(N - 256 + i));
+    for (uint32_t i = 0; i < 512; i++) smp.push_back((uint32_t)((N * (2 * i + 1)) / 1024));
     std::sort(smp.begin(), smp.end());
     smp.erase(std::unique(smp.begin(), smp.end()), smp.end());
   }
@@ -540,7 +541,10 @@ int rc_features_batch(const rc_bytecode *const *bcs, const uint32_t *groups, con
     set_last_error("out of host memory");
     return RC_E_NOMEM;
   }
-  unsigned nt = n_threads > 0 ? (unsigned)n_threads : std::max(1u, std::thread::hardware_concurrency());
+  // one thread per 8 candidates at most: starting a thread costs about as
+  // much as a few candidates' features
+  unsigned nt = n_threads > 0 ? (unsigned)n_threads
+                              : std::max(1u, std::min(std::thread::hardware_concurrency(), (unsigned)(n / 8)));
   nt = (unsigned)std::min<size_t>(nt, std::max<size_t>(n, 1));
   if (nt <= 1) {
     for (size_t i = 0; i < n; i++) features_one(cands[i], out + i * RC_N_FEATURES);

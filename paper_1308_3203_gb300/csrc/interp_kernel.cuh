@@ -1,7 +1,7 @@
 // The body of the per-interval work-item kernel, shared by its two engines:
 // the bytecode interpreter (interp.cu) and compiled intervals (a program's
 // bytecode translated to straight-line code and compiled at run time, see
-// jit.cpp).  One CUDA thread per work-item, one CTA per work-group.
+// jit.cu).  One CUDA thread per work-item, one CTA per work-group.
 //
 // Semantics (Distefano & Dubreil, Sec. 4, thread-local rules): each command
 // updates the private stack (registers) or makes one shared access; assert
@@ -115,8 +115,15 @@ static __device__ __noinline__ bool grid_sync(unsigned *bar, unsigned nblocks, u
   return s_ok != 0;
 }
 
+// How the access step reads committed values: read-only through the
+// non-coherent cache (the snapshot does not change during an interval
+// launch), through L2 (resident runs commit in-kernel), or plainly (a
+// snapshot in shared memory).
+enum SnapRead : int { kSnapLdg = 0, kSnapLdcg = 1, kSnapPlain = 2 };
+
 // One work-item's state in one barrier interval, advanced by an engine.
 struct IvState {
+  const int32_t *snap;    // committed memory, indexed by cell
   const MemInfo *mems;    // the memory table (shared memory)
   int32_t *rf;            // registers [n_regs][S] (shared memory)
   uint32_t *owk;          // own-write slots in shared memory: keys [slots][S]
@@ -145,10 +152,16 @@ __device__ __forceinline__ void out_of_bounds(const InterpArgs &A, const IvState
 // committed value; writes update or add the entry), writes the log record
 // at slot_pos unless the access is private, counts it.  Returns the value
 // read or written.
-template <bool kResident>
+template <int kSnap>
 __device__ __forceinline__ int32_t shared_access(const InterpArgs &A, IvState &s, const MemInfo &m, uint32_t performing,
                                                  uint32_t key, bool store, bool priv, int32_t v, uint32_t slot_pos) {
   const uint32_t S = s.S, tid = s.tid, slots = s.slots, lt = s.lt;
+  // a read's committed value is requested first, so that its latency
+  // overlaps the claims and the own-write lookup (unused when the work-item
+  // reads back its own write)
+  int32_t committed = 0;
+  if (!store)
+    committed = kSnap == kSnapLdcg ? __ldcg(s.snap + key) : kSnap == kSnapLdg ? __ldg(s.snap + key) : s.snap[key];
   // a private access is counted but not logged, and only its stores claim
   // their cells (for the commit)
   if (A.owner && !(priv && !store)) shadow_claim_warp(A.owner, performing, key, store, s.tag, s.gtid, tid & 31u);
@@ -164,7 +177,7 @@ __device__ __forceinline__ int32_t shared_access(const InterpArgs &A, IvState &s
         if (A.ow[(uint64_t)k * A.ow_stride + lt].x == key) { slot = (int32_t)k; break; }
   }
   if (!store) {
-    if (slot < 0) v = kResident ? __ldcg(A.snap + key) : __ldg(A.snap + key);  // resident: committed in-kernel
+    if (slot < 0) v = committed;
     else if ((uint32_t)slot < slots) v = s.owv[slot * S + tid];
     else v = (int32_t)A.ow[(uint64_t)slot * A.ow_stride + lt].y;
   } else {
@@ -255,6 +268,7 @@ __device__ __forceinline__ void interp_body(const InterpArgs &A, const Engine &E
   uint32_t *const flags = A.flags + (kResident ? (interval & 1u) : 0u);
   const bool ran = st == TS_RUN;
   IvState s;
+  s.snap = A.snap;
   s.mems = mems;
   s.rf = rf;
   s.owk = owk;

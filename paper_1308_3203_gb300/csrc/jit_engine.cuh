@@ -1,7 +1,7 @@
 // Engine of compiled intervals: the work-item runs a program's bytecode
 // translated into one straight-line function (translate.cpp) instead of the
 // interpreter's fetch-decode-dispatch loop.  Compiled at run time (NVRTC)
-// together with the function; see jit.cpp for the source it is part of.
+// together with the function; see jit.cu for the source it is part of.
 //
 // The translated function keeps the registers in a constant-indexed array
 // (machine registers) and reaches shared memory through the hooks defined
@@ -53,7 +53,7 @@ __device__ __forceinline__ bool jit_access(JitCtx<kRes> &cx, uint32_t mem, int32
   }
   // inlined at every access site: one call shared by all sites measured
   // 10.5 against 6.2 ms per interval on the 2^26-work-item stress program
-  v = shared_access<kRes>(cx.A, s, m, performing, cell_of(s, m, idx), kStore, kPriv, v, slot);
+  v = shared_access<kRes ? kSnapLdcg : kSnapLdg>(cx.A, s, m, performing, cell_of(s, m, idx), kStore, kPriv, v, slot);
   return true;
 }
 

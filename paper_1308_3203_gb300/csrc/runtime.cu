@@ -113,7 +113,8 @@ struct Workspace {
       recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff, sortscr, reckern,
       bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround, big, bigres, nbig, xg, xgcnt,
       xgn, xgoff, xgtmp, xgout, rstat, rivoff, rbar;
-  HostBuf hstats, hrecs, hround, hdesc;
+  HostBuf hstats, hrecs, hround, hdesc, hsmall, hstage;
+  DevBuf stage;  // one-CTA checks: bytecode, memory table and snapshot in one block
   cudaStream_t bstream = nullptr;
   cudaEvent_t sev[2] = {nullptr, nullptr};  // stats of an interval (by parity) reached the host
   bool configured = false, batch_configured = false;
@@ -124,7 +125,7 @@ struct Workspace {
                       &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
                       &owcnt, &compact, &ctacnt, &ctaoff, &sortscr, &reckern, &bdesc, &bcode,
                       &bmems, &btask, &bkbase, &bkgt, &bklt, &berrk, &shared_acc, &bround, &big,
-                      &bigres, &nbig, &xg, &xgcnt, &xgn, &xgoff, &xgtmp, &xgout, &rstat, &rivoff, &rbar})
+                      &bigres, &nbig, &xg, &xgcnt, &xgn, &xgoff, &xgtmp, &xgout, &rstat, &rivoff, &rbar, &stage})
       b->release();
     epoch = 0;
     owner_hi = 0;
@@ -740,6 +741,147 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
                      s);
 }
 
+// One-CTA check of a small instance (interp.cu, small_check_kernel): every
+// interval, its classification and barrier agreement in one launch, results
+// written to page-locked host memory.  Returns null when the instance does
+// not fit it (too many work-items, records or barriers) or the run had to
+// stop early (more records than the CTA sorts, the interval cap); the
+// caller then checks it another way from the initial state.  The snapshot
+// must hold the inputs and the bytecode (without private flags: the CTA
+// classifies from the full log) must be uploaded.
+// The snapshot of an instance's start: the global inputs (pinned host
+// memory read by a copy kernel over the CPU-GPU link, other memory by
+// cudaMemcpyAsync) and zeroed local memory.
+void load_inputs(const Instance &I, const Layout &L, int32_t *snap, cudaStream_t s) {
+  const Program &P = *I.p;
+  uint32_t gi = 0;
+  for (size_t m = 0; m < P.mems.size(); m++) {
+    if (P.mems[m].space != 0) continue;
+    const uint64_t len = I.in->global_len[gi];
+    if (len) {
+      if (!I.in->global_init || !I.in->global_init[gi]) throw Fail{RC_E_INVALID, "missing global input"};
+      const int32_t *src = I.in->global_init[gi];
+      const int32_t *mapped = I.in->on_device ? nullptr : device_view(src);
+      if (mapped) {  // pinned host memory: the SMs read it over the CPU-GPU link
+        launch_copy_words(mapped, snap + L.mems[m].base, len, s);
+        CK(cudaGetLastError());
+      } else {
+        CK(cudaMemcpyAsync(snap + L.mems[m].base, src, len * 4,
+                           I.in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      }
+    }
+    gi++;
+  }
+  if (L.keys > L.GT) CK(cudaMemsetAsync(snap + L.GT, 0, (L.keys - L.GT) * 4, s));
+}
+
+bool small_fits(const Program &P, uint64_t N) {
+  const uint64_t B = std::max<uint64_t>(P.max_access_per_interval, 1);
+  const uint32_t T = (uint32_t)std::max<uint64_t>(32, (N + 31) / 32 * 32);
+  return N <= kSmallMaxItems && (uint64_t)T * B <= kSmallCap && P.n_barriers + 1 <= kSmallMaxStops &&
+         small_check_smem((uint32_t)P.mems.size(), P.n_regs, T, 0, kSmallCap, 0) <= kMaxSmemPerBlock - 4096;
+}
+
+rc_report *run_small(Workspace &W, const Instance &I, const Layout &L, int32_t *snap, const Insn *dcode,
+                     const MemInfo *dmems, cudaStream_t s) {
+  const Program &P = *I.p;
+  const uint32_t N = (uint32_t)I.N, RS = std::max<uint32_t>(32, (N + 31) / 32 * 32);
+  const uint64_t B = std::max<uint64_t>(P.max_access_per_interval, 1);
+  const uint64_t capw = std::max<uint64_t>(P.max_write_per_interval, 1);
+  const uint32_t cap = (uint32_t)std::min<uint64_t>(kSmallCap, (uint64_t)RS * B);
+  const size_t budget = kMaxSmemPerBlock - 4096;
+  uint32_t slots = 0;
+  while (slots < 8 && slots < capw &&
+         small_check_smem((uint32_t)P.mems.size(), P.n_regs, RS, slots + 1, cap, 0) <= budget)
+    slots++;
+  // the snapshot in shared memory first (the interpreter's reads wait on it),
+  // then the sort's records and summaries, as far as they fit
+  const bool smem_snap = L.keys <= (1u << 20) &&
+      small_check_smem((uint32_t)P.mems.size(), P.n_regs, RS, slots, cap, (uint32_t)L.keys) <= budget;
+  size_t smem = small_check_smem((uint32_t)P.mems.size(), P.n_regs, RS, slots, cap, smem_snap ? (uint32_t)L.keys : 0);
+  const size_t log_b = (size_t)RS * B * sizeof(LogRec);
+  const bool smem_log = smem + log_b <= budget;
+  if (smem_log) smem += log_b;
+  const bool smem_scratch = smem + (size_t)cap * (sizeof(LogRec) + sizeof(Summary)) <= budget;
+  if (smem_scratch) smem += (size_t)cap * (sizeof(LogRec) + sizeof(Summary));
+  // the sort: counting over (cell, work-item) when the pairs are few, else bitonic
+  const uint64_t pairs = L.keys * RS;
+  const bool bins = smem_scratch && pairs <= kSmallBins && smem + pairs * 4 <= budget;
+  if (bins) smem += pairs * 4;
+  const uint32_t out_cap = 16 * kSmallCap, err_cap = N + kSmallMaxStops;
+  SmallArgs a{};
+  InterpArgs &A = a.A;
+  A.code = dcode;
+  A.mems = dmems;
+  A.n_insn = (uint32_t)P.code.size();
+  A.n_regs = P.n_regs;
+  A.n_mems = (uint32_t)P.mems.size();
+  A.n_barriers = P.n_barriers;
+  A.S = I.S;
+  A.G = I.G;
+  A.GT = (uint32_t)L.GT;
+  A.LT = (uint32_t)L.LT;
+  A.snap = snap;
+  A.commit = snap;
+  A.ow = W.ow.get<uint2>(capw * RS);
+  A.capw = (uint32_t)std::min<uint64_t>(capw, 0xFFFFFFFFu);
+  A.ow_stride = RS;
+  A.ow_slots = slots;
+  A.warps_per_cta = RS / 32;
+  A.warp_slice = 32 * B;
+  A.log = W.loga.get<LogRec>((uint64_t)RS * B);
+  A.errs = W.errs.get<OutRec>(err_cap);
+  A.err_cap = err_cap;
+  uint32_t *cnt = W.rstat.get<uint32_t>(1);
+  A.err_count = cnt;
+  if (!smem_scratch) {
+    a.sorted = W.compact.get<LogRec>(cap);
+    a.sum = W.sum.get<Summary>(cap);
+  }
+  a.cap = cap;
+  a.out_cap = out_cap;
+  a.max_intervals = kResidentMaxIntervals;
+  a.n_items = N;
+  a.reg_stride = RS;
+  a.smem_scratch = smem_scratch ? 1u : 0u;
+  a.smem_snap = smem_snap ? 1u : 0u;
+  a.smem_log = smem_log ? 1u : 0u;
+  a.bins = bins ? (uint32_t)pairs : 0u;
+  a.n_cells = (uint32_t)L.keys;
+  unsigned char *h = W.hsmall.get<unsigned char>(64 + (size_t)(out_cap + err_cap) * sizeof(OutRec));
+  unsigned char *hd = nullptr;
+  CK(cudaHostGetDevicePointer(reinterpret_cast<void **>(&hd), h, 0));
+  a.res = reinterpret_cast<unsigned long long *>(hd);
+  a.host_out = reinterpret_cast<OutRec *>(hd + 64);
+  a.host_err = a.host_out + out_cap;
+  a.out = W.out.get<OutRec>(out_cap);
+  CK(cudaMemsetAsync(cnt, 0, 4, s));
+  if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
+  CK(launch_small_check(a, 1024, smem, s));
+  if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], s));
+  CK(cudaStreamSynchronize(s));
+  const unsigned long long *res = reinterpret_cast<const unsigned long long *>(h);
+  const uint32_t flags = (uint32_t)(res[3] >> 32), n_intervals = (uint32_t)res[3];
+  if (flags & (FLAG_LOG_FULL | FLAG_OW_FULL | FLAG_ERR_FULL))
+    throw Fail{RC_E_CAPACITY, "interval log, own-write table or error log overflowed"};
+  if (flags) return nullptr;  // more records or intervals than the CTA takes
+  if (g_prof.on) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, g_prof.ev[0], g_prof.ev[1]));
+    g_prof.launches[0]++;
+    g_prof.ms[0] += ms;
+    g_prof.bytes[0] += 12.0 * (double)res[0];
+  }
+  const OutRec *ho = reinterpret_cast<const OutRec *>(h + 64);
+  std::vector<OutRec> races(ho, ho + res[4]);
+  std::vector<OutRec> errors(ho + out_cap, ho + out_cap + res[5]);
+  std::sort(errors.begin(), errors.end(), [](const OutRec &x, const OutRec &y) {
+    return x.interval != y.interval ? x.interval < y.interval : x.cls != y.cls ? x.cls < y.cls : x.t_a < y.t_a;
+  });
+  return make_report(races, errors, n_intervals, res[0], res[1], res[2], L.GT,
+                     (I.in->flags & RC_WANT_FINAL_MEMORY) ? snap : nullptr, s);
+}
+
 rc_report *run_instance(const Instance &I) {
   Workspace &W = g_ws;
   const Program &P = *I.p;
@@ -754,6 +896,41 @@ rc_report *run_instance(const Instance &I) {
   // cross-group table over the global cells
   const bool group = (I.in->flags & RC_GROUP_BARRIERS) != 0;
   if (group && 2 * L.GT >= 0xFFFFFFFFull) throw Fail{RC_E_CAPACITY, "too many global cells for group scope"};
+  // small instances: one CTA, one launch (strategy 0 and 4), with the plain
+  // bytecode (the CTA classifies from the full log) and none of the other
+  // paths' set-up (no pre-filter, owner table or work-item state)
+  if ((g_strategy == 0 || g_strategy == 4) && !group && !I.explore && g_engine != 2 && small_fits(P, N)) {
+    // bytecode, memory table and (host) inputs packed into one page-locked
+    // block and sent with one copy; the snapshot is the block's tail
+    const size_t code_b = P.code.size() * sizeof(Insn), mems_b = std::max<size_t>(L.mems.size(), 1) * sizeof(MemInfo);
+    const size_t snap_off = (code_b + mems_b + 15) & ~(size_t)15, total = snap_off + std::max<uint64_t>(L.keys, 1) * 4;
+    unsigned char *hb = W.hstage.get<unsigned char>(total);
+    unsigned char *db = W.stage.get<unsigned char>(total);
+    std::memcpy(hb, P.code.data(), code_b);
+    if (!L.mems.empty()) std::memcpy(hb + code_b, L.mems.data(), L.mems.size() * sizeof(MemInfo));
+    int32_t *hsnap = reinterpret_cast<int32_t *>(hb + snap_off);
+    bool packed = !I.in->on_device;  // host inputs (pinned or not) are copied into the block
+    if (packed) {
+      uint32_t gi = 0;
+      for (size_t m = 0; m < P.mems.size(); m++) {
+        if (P.mems[m].space != 0) continue;
+        const uint64_t len = I.in->global_len[gi];
+        if (len) {
+          if (!I.in->global_init || !I.in->global_init[gi]) throw Fail{RC_E_INVALID, "missing global input"};
+          std::memcpy(hsnap + L.mems[m].base, I.in->global_init[gi], len * 4);
+        }
+        gi++;
+      }
+      if (L.keys > L.GT) std::memset(hsnap + L.GT, 0, (L.keys - L.GT) * 4);
+    }
+    CK(cudaMemcpyAsync(db, hb, packed ? total : snap_off, cudaMemcpyHostToDevice, s));
+    CK(interp_upload_code(reinterpret_cast<const Insn *>(hb), (uint32_t)P.code.size(), s));
+    int32_t *snap = reinterpret_cast<int32_t *>(db + snap_off);
+    if (!packed) load_inputs(I, L, snap, s);
+    rc_report *r = run_small(W, I, L, snap, reinterpret_cast<const Insn *>(db),
+                             reinterpret_cast<const MemInfo *>(db + code_b), s);
+    if (r) return r;  // else (too many records or intervals): the other paths, from the start
+  }
   // own-write slots in shared memory: as many as fit (up to 8) while keeping
   // at least two CTAs, or 2048 threads, per SM
   const size_t base_smem = interp_smem_bytes((uint32_t)P.mems.size(), P.n_regs, I.S, 0) +
@@ -781,7 +958,7 @@ rc_report *run_instance(const Instance &I) {
   const bool sort_fits = base_need + cap * (sizeof(Summary) + 24) <= mem_budget;
   if (base_need > mem_budget) throw Fail{RC_E_CAPACITY, "instance needs more than 200 GiB of workspace"};
   // strategy 3 (resident) runs like 0 when the instance cannot be resident
-  const int asked = g_strategy == 3 ? 0 : g_strategy;
+  const int asked = g_strategy == 3 || g_strategy == 4 ? 0 : g_strategy;
   const int fixed_strategy = asked ? asked : (sort_fits ? 0 : 2);
   if (fixed_strategy == 1 && !sort_fits) throw Fail{RC_E_CAPACITY, "the sort path does not fit this instance"};
 
@@ -794,7 +971,8 @@ rc_report *run_instance(const Instance &I) {
   };
   // resident run: every work-group on the GPU at once (one cooperative
   // launch runs all intervals), shadow owner table, full warps
-  const bool resident_wanted = (g_strategy == 0 || g_strategy == 3) && !group && !I.explore && I.S % 32 == 0;
+  const bool resident_wanted =
+      (g_strategy == 0 || g_strategy == 3 || g_strategy == 4) && !group && !I.explore && I.S % 32 == 0;
   // accesses the pre-filter proves private skip the log wherever commits come
   // from the owner table (resident runs, the shadow strategy throughout);
   // the full sort commits from the log, the cross-group table and the
@@ -840,27 +1018,7 @@ rc_report *run_instance(const Instance &I) {
   if (!L.mems.empty())
     CK(cudaMemcpyAsync(dmems, L.mems.data(), L.mems.size() * sizeof(MemInfo), cudaMemcpyHostToDevice, s));
   int32_t *snap = W.snap.get<int32_t>(std::max<uint64_t>(L.keys, 1));
-  auto load_snapshot = [&]() {
-    uint32_t gi = 0;
-    for (size_t m = 0; m < P.mems.size(); m++) {
-      if (P.mems[m].space != 0) continue;
-      const uint64_t len = I.in->global_len[gi];
-      if (len) {
-        if (!I.in->global_init || !I.in->global_init[gi]) throw Fail{RC_E_INVALID, "missing global input"};
-        const int32_t *src = I.in->global_init[gi];
-        const int32_t *mapped = I.in->on_device ? nullptr : device_view(src);
-        if (mapped) {  // pinned host memory: the SMs read it over the CPU-GPU link
-          launch_copy_words(mapped, snap + L.mems[m].base, len, s);
-          CK(cudaGetLastError());
-        } else {
-          CK(cudaMemcpyAsync(snap + L.mems[m].base, src, len * 4,
-                             I.in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-        }
-      }
-      gi++;
-    }
-    if (L.keys > L.GT) CK(cudaMemsetAsync(snap + L.GT, 0, (L.keys - L.GT) * 4, s));
-  };
+  auto load_snapshot = [&]() { load_inputs(I, L, snap, s); };
   load_snapshot();
   int32_t *regs = W.regs.get<int32_t>(N * P.n_regs);
   uint32_t *pc = W.pc.get<uint32_t>(N), *st = W.st.get<uint32_t>(N);
@@ -1692,7 +1850,7 @@ int rc_check_batch(const rc_bytecode *const *bcs, const uint32_t *groups, const 
       }
       if (cells >= (1ull << 31) || bytes > ((uint64_t)200 << 30)) throw Fail{RC_E_CAPACITY, "instance too large for a batch"};
       std::vector<BatchItem> sub(items.begin() + i, items.begin() + j);
-      run_batch(sub, static_cast<cudaStream_t>(inputs[i].cuda_stream), g_strategy == 3 ? 0 : g_strategy, out + i);
+      run_batch(sub, static_cast<cudaStream_t>(inputs[i].cuda_stream), g_strategy >= 3 ? 0 : g_strategy, out + i);
       i = j;
     }
     return RC_OK;
@@ -1788,7 +1946,7 @@ int rc_release_workspace(void) {
 }
 
 int rc_set_strategy(int strategy) {
-  if (strategy < 0 || strategy > 3) return RC_E_INVALID;
+  if (strategy < 0 || strategy > 4) return RC_E_INVALID;
   std::lock_guard<std::mutex> lk(g_mu);
   g_strategy = strategy;
   return RC_OK;

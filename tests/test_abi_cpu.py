@@ -97,10 +97,10 @@ def test_bad_arguments_rejected_without_gpu_work(rc):
 
 
 def test_strategy_values(rc):
-    """0 auto, 1 sort, 2 shadow, 3 resident are accepted; nothing else."""
-    for s in (0, 1, 2, 3):
+    """0 auto, 1 sort, 2 shadow, 3 resident, 4 one CTA are accepted; nothing else."""
+    for s in (0, 1, 2, 3, 4):
         rc.set_strategy(s)
-    for bad in (4, -1):
+    for bad in (5, -1):
         with pytest.raises(rc.RaceCheckError):
             rc.set_strategy(bad)
     rc.set_strategy(0)

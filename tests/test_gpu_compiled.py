@@ -12,7 +12,9 @@ import pytest
 
 from paper_1308_3203_gb300 import workloads as W
 from tests.golden import golden
-from tests.test_gpu_parity import EDGE, STRATEGIES, run_both, same
+from tests.test_gpu_parity import EDGE, run_both, same
+
+STRATEGIES = (1, 2, 3)
 
 pytestmark = pytest.mark.gpu
 
@@ -47,41 +49,41 @@ def test_golden(rc, name):
 
 def test_small_and_tiny_kernels(rc, oracle):
     for seed in range(8):
-        run_both(rc, oracle, W.small_kernel(seed))
+        run_both(rc, oracle, W.small_kernel(seed), STRATEGIES)
     for seed in range(8):
-        run_both(rc, oracle, W.tiny_kernel(seed))
+        run_both(rc, oracle, W.tiny_kernel(seed), STRATEGIES)
 
 
 @pytest.mark.parametrize("shape", [(8, 256), (3, 100), (5, 1), (33, 32)])
 def test_large_kernels_reduced(rc, oracle, shape):
     G, S = shape
     inst = W.large_kernel(shape[0], groups=G, group_size=S, global_len=max(16 * G * S, 4096), local_len=16 * S)
-    run_both(rc, oracle, inst)
+    run_both(rc, oracle, inst, STRATEGIES)
 
 
 @pytest.mark.parametrize("seed", range(2))
 def test_stress_kernels_reduced(rc, oracle, seed):
     """Nested loops and branches on loaded values: lanes diverge inside the
     compiled code."""
-    run_both(rc, oracle, W.stress_kernel(seed, groups=16, group_size=1024))
+    run_both(rc, oracle, W.stress_kernel(seed, groups=16, group_size=1024), STRATEGIES)
 
 
 def test_every_opcode_on_its_boundaries(rc, oracle):
     from tests.test_translate_cpu import opcode_kernel
     for S in (8, 64):
-        run_both(rc, oracle, opcode_kernel(S))
+        run_both(rc, oracle, opcode_kernel(S), STRATEGIES)
 
 
 @pytest.mark.parametrize("case", range(len(EDGE)))
 def test_edge_cases(rc, oracle, case):
     src, G, S, glob = EDGE[case]
-    run_both(rc, oracle, W.Instance(f"edge{case}", src, G, S, glob))
+    run_both(rc, oracle, W.Instance(f"edge{case}", src, G, S, glob), STRATEGIES)
 
 
 def test_large_kernel_full_size(rc, oracle):
     """The 1024 x 256 large instance, resident and interval by interval."""
     inst = W.large_kernel(0)
-    want = run_both(rc, oracle, inst)
+    want = run_both(rc, oracle, inst, STRATEGIES)
     assert want["n_access"] > 10_000_000
 
 

@@ -3,8 +3,9 @@
 Race reports are integer results, so the bar is bit-exact equality of every
 record (interval, cell, class, witness pair, counts), the status, the access
 counters and the final global memory.  Each case runs under both
-classification strategies (full sort, shadow owner table) and the resident
-run (one cooperative launch for every interval) where the shape allows it.
+classification strategies (full sort, shadow owner table), the resident
+run (one cooperative launch for every interval) and the one-CTA check of
+small instances, each where the shape allows it.
 """
 import numpy as np
 import pytest
@@ -14,7 +15,7 @@ from tests.golden import golden
 
 pytestmark = pytest.mark.gpu
 
-STRATEGIES = (1, 2, 3)
+STRATEGIES = (1, 2, 3, 4)
 
 
 @pytest.fixture(scope="module")
