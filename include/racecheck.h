@@ -293,7 +293,11 @@ int rc_jit_stats(uint64_t *compiles, double *seconds);
  * class -- single instances by work-items and per-interval access bound,
  * batches by warp tasks and bound -- an undecided class alternates the two
  * exact strategies on successive intervals (or batch rounds), times each,
- * and keeps the cheaper one after two samples of each.  Decisions persist in
+ * and keeps the cheaper one after two samples of each; a batch class then
+ * times each block shape of the batch interpreter (128, 256, 512 threads per
+ * CTA) on two rounds and keeps the fastest.  The log capacity is not a
+ * choice: every warp's slice holds the program's static per-interval bound,
+ * the least that makes overflow impossible.  Decisions persist in
  * a JSON file: cache_path, or NULL for the default ($RC_TUNE_CACHE, else
  * $XDG_CACHE_HOME/racecheck_autotune.json, else
  * ~/.cache/racecheck_autotune.json), or "" for no file. */
@@ -302,7 +306,10 @@ int rc_autotune_config(const char *cache_path);
 int rc_autotune_reset(void);
 /* Decision for a size class: kind 0 single (a = work-items, b = accesses per
  * work-item per interval bound), kind 1 batch (a = warp tasks, b = bound);
- * returns 1 (sort), 2 (shadow) or 0 if undecided. */
+ * returns 1 (sort), 2 (shadow) or 0 if undecided.  Kind 2: the batch size
+ * class's block shape -- threads per CTA of the batch interpreter, 128, 256
+ * or 512 (1024 threads per SM in every case), which the autotuner times on
+ * two batch rounds each once the strategy is decided -- or 0 if undecided. */
 int rc_autotune_lookup(int kind, uint64_t a, uint64_t b);
 
 /* Kernel timing: when enabled, the library brackets its work with CUDA

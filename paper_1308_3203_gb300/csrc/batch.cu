@@ -29,9 +29,10 @@ __device__ __forceinline__ void batch_err(const BatchArgs &A, uint32_t k, const 
   }
 }
 
-constexpr uint32_t kBatchThreads = 256;
-
-__global__ void __launch_bounds__(kBatchThreads, 4) batch_interp_kernel(BatchArgs A) {
+// Block shapes the autotuner chooses from: threads per CTA, always 1024
+// threads (32 warps) per SM
+template <uint32_t kBatchThreads>
+__global__ void __launch_bounds__(kBatchThreads, 1024 / kBatchThreads) batch_interp_kernel(BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t RS = kBatchThreads;  // register-file stride
   int32_t *rf = reinterpret_cast<int32_t *>(smem);                  // [max_regs][RS]
@@ -268,20 +269,27 @@ __global__ void batch_commit_kernel(BatchArgs A) {
 
 }  // namespace
 
-size_t batch_smem_bytes(uint32_t max_regs, uint32_t ow_slots) {
-  return ((size_t)max_regs + 2ull * ow_slots) * kBatchThreads * 4;
+size_t batch_smem_bytes(uint32_t max_regs, uint32_t ow_slots, uint32_t threads) {
+  return ((size_t)max_regs + 2ull * ow_slots) * threads * 4;
 }
 
 cudaError_t batch_configure() {
-  return cudaFuncSetAttribute(batch_interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kMaxSmemPerBlock);
+  cudaError_t e = cudaFuncSetAttribute(batch_interp_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kMaxSmemPerBlock);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_interp_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMaxSmemPerBlock);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_interp_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMaxSmemPerBlock);
+  return e;
 }
 
-uint32_t batch_threads() { return kBatchThreads; }
-
-void launch_batch_interp(const BatchArgs &a, uint32_t grid, size_t smem, cudaStream_t s) {
+void launch_batch_interp(const BatchArgs &a, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t s) {
   count_launch();
-  batch_interp_kernel<<<grid, kBatchThreads, smem, s>>>(a);
+  if (threads == 128) batch_interp_kernel<128><<<grid, 128, smem, s>>>(a);
+  else if (threads == 512) batch_interp_kernel<512><<<grid, 512, smem, s>>>(a);
+  else batch_interp_kernel<256><<<grid, 256, smem, s>>>(a);
 }
 
 void launch_batch_compact(const BatchArgs &a, LogRec *out, unsigned long long *total, cudaStream_t s) {

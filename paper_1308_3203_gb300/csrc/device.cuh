@@ -132,10 +132,10 @@ struct BatchArgs {
   uint32_t *owner;              // shadow owner table over the batch's cells
 };
 
-size_t batch_smem_bytes(uint32_t max_regs, uint32_t ow_slots);
+// block shapes of the batch interpreter: 128, 256 or 512 threads per CTA
+size_t batch_smem_bytes(uint32_t max_regs, uint32_t ow_slots, uint32_t threads);
 cudaError_t batch_configure();
-uint32_t batch_threads();
-void launch_batch_interp(const BatchArgs &a, uint32_t grid, size_t smem, cudaStream_t s);
+void launch_batch_interp(const BatchArgs &a, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t s);
 void launch_batch_compact(const BatchArgs &a, LogRec *out, unsigned long long *total, cudaStream_t s);
 void launch_batch_commit(const BatchArgs &a, cudaStream_t s);
 

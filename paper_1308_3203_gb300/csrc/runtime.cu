@@ -154,10 +154,15 @@ void prof_events() {
 // batch rounds), timing each interval per million accesses; after two
 // samples of each the cheaper one is kept and written to a JSON cache.
 struct Tuner {
+  // block shapes of the batch interpreter (threads per CTA)
+  static constexpr uint32_t kShapes[3] = {128, 256, 512};
   struct Entry {
     int best = 0;
     double cost[3] = {0, 0, 0};
     int n[3] = {0, 0, 0};
+    uint32_t threads = 0;  // decided block shape (batches), 0 = not yet
+    double scost[3] = {0, 0, 0};
+    int sn[3] = {0, 0, 0};
   };
   bool loaded = false;
   bool persist = true;
@@ -194,6 +199,11 @@ struct Tuner {
       if (b == std::string::npos || b > close) continue;
       const int best = std::atoi(text.c_str() + b + 7);
       if (best == 1 || best == 2) entries[key].best = best;
+      const size_t th = text.find("\"threads\":", q);
+      if (th != std::string::npos && th < close) {
+        const uint32_t v = (uint32_t)std::atoi(text.c_str() + th + 10);
+        if (v == 128 || v == 256 || v == 512) entries[key].threads = v;
+      }
     }
   }
   void save() {
@@ -213,9 +223,11 @@ struct Tuner {
     for (auto &kv : entries) {
       if (!kv.second.best) continue;
       const Entry &e = kv.second;
-      std::fprintf(f, "%s\n    \"%s\": {\"best\": %d, \"ms_per_maccess_sort\": %.6g, \"ms_per_maccess_shadow\": %.6g}",
+      std::fprintf(f, "%s\n    \"%s\": {\"best\": %d, \"ms_per_maccess_sort\": %.6g, \"ms_per_maccess_shadow\": %.6g",
                    first ? "" : ",", kv.first.c_str(), e.best, e.n[1] ? e.cost[1] / e.n[1] : 0.0,
                    e.n[2] ? e.cost[2] / e.n[2] : 0.0);
+      if (e.threads) std::fprintf(f, ", \"threads\": %u", e.threads);
+      std::fprintf(f, "}");
       first = false;
     }
     std::fprintf(f, "\n  }\n}\n");
@@ -231,6 +243,36 @@ struct Tuner {
   bool decided(const std::string &key) {
     load();
     return entries[key].best != 0;
+  }
+  // batches: once the strategy is decided, each block shape is timed on two
+  // rounds and the fastest kept (per million accesses)
+  uint32_t choose_threads(const std::string &key) {
+    load();
+    Entry &e = entries[key];
+    if (e.threads) return e.threads;
+    if (!e.best) return 256;
+    int k = 0;
+    for (int j = 1; j < 3; j++)
+      if (e.sn[j] < e.sn[k]) k = j;
+    return kShapes[k];
+  }
+  bool threads_decided(const std::string &key) {
+    load();
+    return entries[key].threads != 0;
+  }
+  void record_threads(const std::string &key, uint32_t threads, double ms, uint64_t accesses) {
+    Entry &e = entries[key];
+    if (e.threads || !e.best || accesses == 0) return;
+    const int k = threads == 128 ? 0 : threads == 256 ? 1 : 2;
+    e.scost[k] += ms * 1e6 / (double)accesses;
+    e.sn[k]++;
+    if (e.sn[0] >= 2 && e.sn[1] >= 2 && e.sn[2] >= 2) {
+      int b = 0;
+      for (int j = 1; j < 3; j++)
+        if (e.scost[j] / e.sn[j] < e.scost[b] / e.sn[b]) b = j;
+      e.threads = kShapes[b];
+      save();
+    }
   }
   void record(const std::string &key, int strategy, double ms, uint64_t accesses) {
     Entry &e = entries[key];
@@ -1435,14 +1477,12 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   uint32_t *owner = strategy != 1 ? shadow_table(W, keys, s) : W.owner.get<uint32_t>(4);
   const std::string tkey = batch_key(n_tasks, logrecs / std::max<uint64_t>(n_tasks, 1) / 32);
   if (!strategy) tuner_events();
-  // own-write slots in shared memory (up to 8) with 4 CTAs of the interpreter per SM
-  uint32_t ow_slots = 0;
-  while (ow_slots < 8 && ow_slots < max_writes && batch_smem_bytes(max_regs, ow_slots + 1) <= 50 * 1024) ow_slots++;
-  const size_t smem = batch_smem_bytes(max_regs, ow_slots);
-  if (smem > kMaxSmemPerBlock) throw Fail{RC_E_INVALID, "batch needs too many registers per work-item"};
+  // block shapes: CTAs of 128, 256 or 512 threads, 1024 threads per SM; own-write
+  // slots in shared memory (up to 8) within the SM's 200 KB shared among them
+  if (batch_smem_bytes(max_regs, 0, 512) > kMaxSmemPerBlock)
+    throw Fail{RC_E_INVALID, "batch needs too many registers per work-item"};
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
-  const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((n_tasks + 7) / 8, (uint32_t)sms * 4));
   uint32_t *dround = W.bround.get<uint32_t>(4);
   uint32_t *hround = W.hround.get<uint32_t>(4);
   BatchDesc *hdesc = W.hdesc.get<BatchDesc>(n);
@@ -1455,7 +1495,6 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   a.code = dcode;
   a.mems = dmems;
   a.max_regs = max_regs;
-  a.ow_slots = ow_slots;
   a.round = dround;
   a.snap = snap;
   a.regs = dregs;
@@ -1490,25 +1529,42 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
     CK(cudaStreamWaitEvent(bs, ready, 0));
     CK(cudaEventDestroy(ready));
   }
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  CK(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
-  cudaMemsetAsync(dstats, 0, 8 * 4, bs);
-  cudaMemsetAsync(dstats + 8, 0xFF, stops * 4, bs);
-  cudaMemsetAsync(dstats + 8 + stops, 0, stops * 4, bs);
-  launch_batch_interp(a, grid, smem, bs);
-  launch_batch_commit(a, bs);
-  launch_batch_compact(a, picked, cnt, bs);
-  CK(cudaStreamEndCapture(bs, &graph));
-  CK(cudaGraphInstantiate(&exec, graph, 0));
-  struct GraphGuard {
-    cudaGraph_t g;
-    cudaGraphExec_t e;
-    ~GraphGuard() {
-      if (e) cudaGraphExecDestroy(e);
-      if (g) cudaGraphDestroy(g);
+  // one graph per block shape, captured the first time a round takes it
+  struct Graphs {
+    cudaGraph_t g[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t e[3] = {nullptr, nullptr, nullptr};
+    ~Graphs() {
+      for (int k = 0; k < 3; k++) {
+        if (e[k]) cudaGraphExecDestroy(e[k]);
+        if (g[k]) cudaGraphDestroy(g[k]);
+      }
     }
-  } guard{graph, exec};
+  } graphs;
+  auto graph_for = [&](uint32_t threads) -> cudaGraphExec_t {
+    const int k = threads == 128 ? 0 : threads == 256 ? 1 : 2;
+    if (graphs.e[k]) return graphs.e[k];
+    const uint32_t ctas_per_sm = 1024 / threads;
+    const size_t budget = 200 * 1024 / ctas_per_sm;
+    uint32_t ow_slots = 0;
+    while (ow_slots < 8 && ow_slots < max_writes && batch_smem_bytes(max_regs, ow_slots + 1, threads) <= budget)
+      ow_slots++;
+    const size_t smem = batch_smem_bytes(max_regs, ow_slots, threads);
+    const uint32_t warps_per_cta = threads / 32;
+    const uint32_t grid = std::max<uint32_t>(
+        1, std::min<uint32_t>((n_tasks + warps_per_cta - 1) / warps_per_cta, (uint32_t)sms * ctas_per_sm));
+    BatchArgs ak = a;
+    ak.ow_slots = ow_slots;
+    CK(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(dstats, 0, 8 * 4, bs);
+    cudaMemsetAsync(dstats + 8, 0xFF, stops * 4, bs);
+    cudaMemsetAsync(dstats + 8 + stops, 0, stops * 4, bs);
+    launch_batch_interp(ak, grid, threads, smem, bs);
+    launch_batch_commit(ak, bs);
+    launch_batch_compact(ak, picked, cnt, bs);
+    CK(cudaStreamEndCapture(bs, &graphs.g[k]));
+    CK(cudaGraphInstantiate(&graphs.e[k], graphs.g[k], 0));
+    return graphs.e[k];
+  };
 
   std::vector<std::vector<OutRec>> races(n), errors(n);
   std::vector<uint32_t> n_intervals(n, 0);
@@ -1519,15 +1575,18 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   for (uint32_t round = 0; active; round++) {
     const int strat = strategy ? strategy : g_tuner.choose(tkey);
     const bool tuning = !strategy && !g_tuner.decided(tkey);
+    // block shape: the tuner's (tried in turn once the strategy is decided), 256 with a fixed strategy
+    const uint32_t threads = strategy ? 256u : g_tuner.choose_threads(tkey);
+    const bool shape_tuning = !strategy && !tuning && !g_tuner.threads_decided(tkey);
     std::memcpy(hdesc, desc.data(), n * sizeof(BatchDesc));
     hround[0] = round;
     hround[1] = strat == 2 ? shadow_next_tag(W, bs, 4 * keys) : 0;
     hround[2] = strat == 2 ? 1u : 0u;
     CK(cudaMemcpyAsync(ddesc, hdesc, n * sizeof(BatchDesc), cudaMemcpyHostToDevice, bs));
     CK(cudaMemcpyAsync(dround, hround, 16, cudaMemcpyHostToDevice, bs));
-    if (tuning) CK(cudaEventRecord(g_tev[0], bs));
+    if (tuning || shape_tuning) CK(cudaEventRecord(g_tev[0], bs));
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], bs));
-    CK(cudaGraphLaunch(exec, bs));
+    CK(cudaGraphLaunch(graph_for(threads), bs));
     for (int q = 0; q < 3; q++) count_launch();  // kernels replayed by the graph
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], bs));
     CK(cudaMemcpyAsync(hstats, dstats, stat_words * 4, cudaMemcpyDeviceToHost, bs));
@@ -1561,14 +1620,15 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
       g_prof.launches[1]++;
       g_prof.ms[1] += ms;
     }
-    if (tuning) {
+    if (tuning || shape_tuning) {
       CK(cudaEventRecord(g_tev[1], bs));
       CK(cudaEventSynchronize(g_tev[1]));
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, g_tev[0], g_tev[1]));
       uint64_t done = 0;
       for (size_t q = 0; q < acc.size(); q++) done += acc[q] - prev[q];
-      g_tuner.record(tkey, strat, ms, done);
+      if (tuning) g_tuner.record(tkey, strat, ms, done);
+      else g_tuner.record_threads(tkey, threads, ms, done);
     }
     prev = acc;
     for (size_t i = 0; i < rr.size(); i++) races[rk[i]].push_back(rr[i]);
@@ -2012,9 +2072,11 @@ int rc_autotune_reset(void) {
 int rc_autotune_lookup(int kind, uint64_t a, uint64_t b) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_tuner.load();
+  if (kind < 0 || kind > 2) return 0;
   const std::string key = kind == 0 ? single_key(a, b) : batch_key(a, b);
   auto it = g_tuner.entries.find(key);
-  return it == g_tuner.entries.end() ? 0 : it->second.best;
+  if (it == g_tuner.entries.end()) return 0;
+  return kind == 2 ? (int)it->second.threads : it->second.best;
 }
 
 int rc_profile_enable(int on) {

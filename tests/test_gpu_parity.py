@@ -241,13 +241,22 @@ def test_autotuner_decides_and_persists(rc, oracle, tmp_path):
     assert rc.autotune_lookup(0, inst.n_threads, bound) == 0
     rc.autotune_config(cache)  # reload from the file
     assert rc.autotune_lookup(0, inst.n_threads, bound) == best
-    # batches decide per round the same way
+    # batches decide per round the same way, then time each block shape
+    # (128, 256, 512 threads per CTA) on two rounds and keep the fastest
     insts = [W.small_kernel(s, n_barriers=3) for s in range(20)]
     wants = [oracle.check(i.src, i.groups, i.group_size, i.globals) for i in insts]
-    for _ in range(2):
-        got = rc.check_batch([(rc.compile(i.src), i.groups, i.group_size, i.globals) for i in insts])
+    bcs = [rc.compile(i.src) for i in insts]
+    tasks = sum((i.n_threads + 31) // 32 for i in insts)
+    bound = sum((i.n_threads + 31) // 32 * max(b.info()["max_access_per_interval"], 1)
+                for i, b in zip(insts, bcs)) // tasks
+    for _ in range(4):  # 4 rounds per call: strategy samples, then shape samples
+        got = rc.check_batch([(b, i.groups, i.group_size, i.globals) for b, i in zip(bcs, insts)])
         for g, w, i in zip(got, wants, insts):
             same(g, w, i.name)
+    assert rc.autotune_lookup(1, tasks, bound) in (1, 2)
+    threads = rc.autotune_lookup(2, tasks, bound)
+    assert threads in (128, 256, 512)
+    assert '"threads": %d' % threads in open(cache).read()
     rc.autotune_config("")
 
 
