@@ -310,15 +310,15 @@ void features_one(const Cand &c, float *out) {
 
   const Analysis an = analyse(p, S, G);
   // work-item sample: all of them when few, else both ends and an even spread
-  // (1024 in all: the ranking must cost less than the checks it saves)
+  // (256 in all: the ranking must cost less than the checks it saves)
   std::vector<uint32_t> smp;
-  if (N <= 1024) {
+  if (N <= 256) {
     smp.resize(N);
     std::iota(smp.begin(), smp.end(), 0u);
   } else {
-    for (uint32_t i = 0; i < 256; i++) smp.push_back(i);
-    for (uint32_t i = 0; i < 256; i++) smp.push_back((uint32_t)(N - 256 + i));
-    for (uint32_t i = 0; i < 512; i++) smp.push_back((uint32_t)((N * (2 * i + 1)) / 1024));
+    for (uint32_t i = 0; i < 64; i++) smp.push_back(i);
+    for (uint32_t i = 0; i < 64; i++) smp.push_back((uint32_t)(N - 64 + i));
+    for (uint32_t i = 0; i < 128; i++) smp.push_back((uint32_t)((N * (2 * i + 1)) / 256));
     std::sort(smp.begin(), smp.end());
     smp.erase(std::unique(smp.begin(), smp.end()), smp.end());
   }
@@ -457,14 +457,14 @@ void features_one(const Cand &c, float *out) {
       }
     }
     if (w0g >= 0) {
-      for (size_t q = i; q < j && !rrace; q++) {
-        if (evs[q].store) continue;
-        for (size_t u = i; u < j; u++)
-          if (evs[u].store && evs[u].gtid != evs[q].gtid) {
-            rrace = true;  // observed value unknown here: any other writer may differ
-            break;
-          }
-      }
+      // a read meets a write by another work-item (observed value unknown
+      // here: any other writer may differ): with two distinct writers every
+      // read does; with one, a read by anyone else does
+      int64_t w1g = -1;
+      for (size_t q = i; q < j && w1g < 0; q++)
+        if (evs[q].store && (int64_t)evs[q].gtid != w0g) w1g = evs[q].gtid;
+      for (size_t q = i; q < j && !rrace; q++)
+        if (!evs[q].store && (w1g >= 0 || (int64_t)evs[q].gtid != w0g)) rrace = true;
     }
     ww += wrace;
     benign += wben && !wrace;

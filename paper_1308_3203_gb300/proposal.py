@@ -54,20 +54,50 @@ def scores(model: rc.MLP, X: np.ndarray) -> np.ndarray:
     return model.forward(x).cpu().numpy()
 
 
+# Feature columns the rule-based ranking reads (rc_features' layout): some
+# access of the kernel must put two work-items of the candidate's launch
+# shape on one cell with a store whose value varies (108); a race among the
+# sampled work-items' accesses (107); sampled write/write and read/write
+# collisions (104, 105).
+F_PREDICTED, F_SAMPLED, F_WW, F_RW = 108, 107, 104, 105
+
+
+def rule_scores(X: np.ndarray) -> np.ndarray:
+    """The ranking without a network: candidates whose features predict a
+    race first, then those with sampled collisions, more collisions first;
+    ties keep the index order."""
+    return 4.0 * X[:, F_PREDICTED] + 2.0 * X[:, F_SAMPLED] + 0.1 * (X[:, F_WW] + X[:, F_RW])
+
+
 def compare_search(model: rc.MLP, seeds, n_cand: int = 64) -> dict:
-    """Ranked search vs plain enumeration on each kernel (the same GPU, the
-    same checker): checks and seconds to the first racy candidate, and
-    whether each search found a race where exhaustive enumeration does."""
+    """Three searches of each kernel's candidates on the same GPU with the
+    same checker: ranked by the trained network, ranked by the rule above
+    (no network), and plain enumeration (index order).  Per search: checks
+    and seconds to the first racy candidate, and whether it found a race
+    where exhaustive enumeration does; `*_total_s` adds the cost of ranking
+    (feature extraction, and the network's inference for the network)."""
+    import time
+    import torch
     rows = []
     for s in seeds:
         _, items = kernel_candidates(s, n_cand)
-        sc = scores(model, rc.features(items))
+        t0 = time.perf_counter()
+        X = rc.features(items)
+        t_feat = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        sc = scores(model, X)
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t0
         enum = rc.search(items)                   # index order = enumeration
         ranked = rc.search(items, scores=sc)
+        rule = rc.search(items, scores=rule_scores(X))
         rows.append(dict(seed=s, racy=enum["first"] >= 0, enum_checks=enum["checks"],
                          enum_s=enum["seconds"], ranked_checks=ranked["checks"], ranked_s=ranked["seconds"],
                          ranked_first=ranked["first"], enum_first=enum["first"],
-                         ranked_found=ranked["first"] >= 0))
+                         ranked_found=ranked["first"] >= 0,
+                         ranked_total_s=ranked["seconds"] + t_feat + t_inf,
+                         rule_checks=rule["checks"], rule_s=rule["seconds"], rule_found=rule["first"] >= 0,
+                         rule_total_s=rule["seconds"] + t_feat, features_s=t_feat, inference_s=t_inf))
     return summarize(rows)
 
 
@@ -83,4 +113,17 @@ def summarize(rows) -> dict:
                    recall=float(np.mean([r["ranked_found"] for r in racy])))
         for k in (1, 2, 4, 8):
             out[f"recall_at_{k}"] = float(np.mean([r["ranked_found"] and r["ranked_checks"] <= k for r in racy]))
+        if "rule_checks" in racy[0]:
+            tt = sum(r["ranked_total_s"] for r in racy)
+            tu = sum(r["rule_total_s"] for r in racy)
+            out.update(ranked_total_seconds=tt, speedup_total=te / tt if tt > 0 else float("inf"),
+                       features_seconds=sum(r["features_s"] for r in racy),
+                       inference_seconds=sum(r["inference_s"] for r in racy),
+                       rule_seconds=sum(r["rule_s"] for r in racy), rule_total_seconds=tu,
+                       rule_speedup_total=te / tu if tu > 0 else float("inf"),
+                       rule_checks_mean=float(np.mean([r["rule_checks"] for r in racy])),
+                       rule_recall=float(np.mean([r["rule_found"] for r in racy])))
+            for k in (1, 2, 4, 8):
+                out[f"rule_recall_at_{k}"] = float(np.mean([r["rule_found"] and r["rule_checks"] <= k
+                                                            for r in racy]))
     return out
