@@ -474,7 +474,9 @@ int rc_translate(const rc_bytecode *bc, const char *fn_name, char *buf, size_t c
  * inputs only (in->on_device must be 0).  Errors: RC_E_INVALID. */
 int rc_features(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in, float *out);
 /* rc_features for n candidates into out[n][RC_N_FEATURES], on n_threads host
- * threads (<= 0: all hardware threads). */
+ * threads (<= 0: one per 8 candidates, at most the host's cores; the
+ * library keeps its worker threads between calls).  The result does not
+ * depend on n_threads. */
 int rc_features_batch(const rc_bytecode *const *bcs, const uint32_t *groups, const uint32_t *group_size,
                       const rc_input *inputs, size_t n, float *out, int n_threads);
 
@@ -530,6 +532,36 @@ typedef struct {
 int rc_search(const rc_bytecode *const *bcs, const uint32_t *groups, const uint32_t *group_size,
               const rc_input *inputs, size_t n, const float *scores, uint32_t max_checks, rc_search_result *res,
               rc_report **found);
+
+/* Ranked search in one call: the candidates' features (rc_features) are
+ * computed on the host's worker threads, scored by `model` (rc_mlp_forward
+ * on the stream of inputs[0]) or, when model is NULL, by the rule
+ *   4 f[108] + 2 f[107] + (f[104] + f[105]) / 10   (float arithmetic)
+ * (a race predicted by the index analysis, then sampled collisions), and
+ * checked as rc_search does in descending score order (ties keep their
+ * index order) until one is racy or max_checks checks (0 = all) were made.
+ * With RC_RANK_OVERLAP the GPU does not wait for the ranking: candidates are
+ * checked in index order while the features are computed, and the ranked
+ * order takes over, skipping what was checked, once the scores exist (a
+ * race found first ends the search and the feature work is abandoned).
+ * Every reported race comes from an exact check.  res: the racy
+ * candidate's index or -1, checks made (checks_unranked of them in index
+ * order before the ranking), the call's host wall time and its parts.
+ * found as for rc_search.  Host inputs only; errors as rc_search and
+ * rc_features. */
+#define RC_RANK_OVERLAP 1u
+typedef struct {
+  int64_t first;
+  uint32_t checks;
+  uint32_t checks_unranked;
+  double seconds;          /* whole call */
+  double features_seconds; /* from the call's start until every feature vector existed */
+  double scoring_seconds;  /* network (or rule) scores and their order */
+  double check_seconds;    /* in exact checks */
+} rc_ranked_result;
+int rc_search_ranked(rc_mlp *model, const rc_bytecode *const *bcs, const uint32_t *groups,
+                     const uint32_t *group_size, const rc_input *inputs, size_t n, uint32_t max_checks,
+                     uint32_t flags, rc_ranked_result *res, rc_report **found);
 
 #ifdef __cplusplus
 }

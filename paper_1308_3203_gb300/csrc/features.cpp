@@ -19,10 +19,17 @@
 // the code up to their target.  Loops are read once, their counters unknown
 // afterwards.  The features only steer the order in which candidates are
 // checked: every race the search reports comes from the exact checker.
+#include <unistd.h>
+
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstdint>
 #include <cstring>
+#include <deque>
+#include <functional>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -30,6 +37,7 @@
 
 #include "racecheck.h"
 #include "bytecode.h"
+#include "candidate_features.h"
 
 namespace rc {
 namespace {
@@ -324,7 +332,8 @@ void features_one(const Cand &c, float *out) {
   }
   const double scale = (double)N / smp.size();
 
-  std::vector<Ev> evs;
+  thread_local std::vector<Ev> evs;
+  evs.clear();
   struct ClassAcc {
     double n = 0, uni = 0, tido = 0, wgi = 0, unk = 0, en = 0, dg = 0, maxen = 0, vv = 0, col = 0, race = 0, oob = 0;
   } cls[4];
@@ -372,18 +381,27 @@ void features_one(const Cand &c, float *out) {
     const double n_en = en * scale;
     C.maxen = std::max(C.maxen, (double)lg(n_en) / 16.0);
     if (en) C.oob += (double)oob / en;
-    // work-items of one group / groups that reach the access
-    uint64_t s_en = 0, g_en = 0;
-    if (first_wg >= 0) {
-      for (int64_t t = 0; t < S; t++) {
+    // work-items of the first enabled group that reach the access (counted
+    // over at most 64 of them spread evenly, then scaled to the group), and
+    // groups of its first work-item that do, counted as far as 2
+    auto group_items = [&]() {
+      const uint32_t n_t = std::min<uint32_t>(S, 64);
+      uint64_t k = 0;
+      for (uint32_t i = 0; i < n_t; i++) {
+        const int64_t t = S <= 64 ? i : ((int64_t)S * (2 * i + 1)) / 128;
         bool certain = true;
-        if (enabled(a, t, first_wg, an, c, certain)) s_en++;
+        if (enabled(a, t, first_wg, an, c, certain)) k++;
       }
-      for (int64_t w = 0; w < G; w++) {
+      return (double)k * S / n_t;
+    };
+    auto item_groups = [&](uint64_t limit) {  // G <= 64
+      uint64_t k = 0;
+      for (int64_t w = 0; w < G && k <= limit; w++) {
         bool certain = true;
-        if (enabled(a, first_tid, w, an, c, certain)) g_en++;
+        if (enabled(a, first_tid, w, an, c, certain)) k++;
       }
-    }
+      return k;
+    };
     // must two work-items meet on a cell?
     bool col = false, race = false;
     if (known_idx && n_en >= 2) {
@@ -393,16 +411,16 @@ void features_one(const Cand &c, float *out) {
         col = true;
         race = a.store && vvar;
       } else if (f.ct == 0) {  // depends on wg only: a whole group on one cell
-        if (s_en >= 2) {
+        if (group_items() >= 2) {
           col = true;
           race = a.store && v_tid;
         }
       } else if (f.cw == 0) {  // depends on tid only
-        if (g_en >= 2 && a.space == 0) {
+        if (a.space == 0 && item_groups(1) >= 2) {
           col = true;
           race = race || (a.store && v_wg);
         }
-        if (f.M > 0 && (int64_t)s_en > f.M / gcd64(f.ct, f.M)) {
+        if (f.M > 0 && f.M / gcd64(f.ct, f.M) < (int64_t)S && group_items() > (double)(f.M / gcd64(f.ct, f.M))) {
           col = true;
           race = race || (a.store && v_tid);
         }
@@ -434,42 +452,58 @@ void features_one(const Cand &c, float *out) {
     o[10] = (float)(C.race / n);
     o[11] = (float)(C.oob / n);
   }
-  // collisions among the sampled work-items, per interval and cell
-  std::sort(evs.begin(), evs.end(), [](const Ev &a, const Ev &b) {
-    return a.interval != b.interval ? a.interval < b.interval : a.cell < b.cell;
-  });
-  double ww = 0, rw = 0, benign = 0;
-  for (size_t i = 0; i < evs.size();) {
-    size_t j = i;
-    while (j < evs.size() && evs[j].interval == evs[i].interval && evs[j].cell == evs[i].cell) j++;
-    // writers: first writer's value vs others (different work-items)
-    bool wrace = false, wben = false, rrace = false;
-    int64_t w0v = 0;
-    int64_t w0g = -1;
-    for (size_t q = i; q < j; q++) {
-      if (!evs[q].store) continue;
-      if (w0g < 0) {
-        w0g = evs[q].gtid;
-        w0v = evs[q].val;
-      } else if ((int64_t)evs[q].gtid != w0g) {
-        if (!evs[q].vknown || evs[q].val != w0v) wrace = true;
-        else wben = true;
+  // collisions among the sampled work-items, per interval and cell: one
+  // pass over the events in evaluation order (access by access, work-items
+  // in sample order) into a table of cells (open addressing over indices
+  // into the list of cells met)
+  struct CellAcc {
+    uint64_t cell;
+    uint32_t interval;
+    bool wrace, wben, two_readers;
+    int64_t w0g, w0v, w1g, r0;
+  };
+  thread_local std::vector<CellAcc> cells;
+  thread_local std::vector<uint32_t> tab;
+  size_t cap = 16;
+  while (cap < 2 * evs.size()) cap <<= 1;
+  tab.assign(cap, 0xFFFFFFFFu);
+  cells.clear();
+  for (const Ev &e : evs) {
+    size_t h = (size_t)(((e.cell ^ ((uint64_t)e.interval << 52)) * 0x9E3779B97F4A7C15ull) >> 20) & (cap - 1);
+    while (tab[h] != 0xFFFFFFFFu && (cells[tab[h]].cell != e.cell || cells[tab[h]].interval != e.interval))
+      h = (h + 1) & (cap - 1);
+    if (tab[h] == 0xFFFFFFFFu) {
+      tab[h] = (uint32_t)cells.size();
+      cells.push_back(CellAcc{e.cell, e.interval, false, false, false, -1, 0, -1, -1});
+    }
+    CellAcc &t = cells[tab[h]];
+    const int64_t g = (int64_t)e.gtid;
+    if (e.store) {
+      // writers: the first writer's value against the others' (other work-items)
+      if (t.w0g < 0) {
+        t.w0g = g;
+        t.w0v = e.val;
+      } else if (g != t.w0g) {
+        if (t.w1g < 0) t.w1g = g;
+        if (!e.vknown || e.val != t.w0v) t.wrace = true;
+        else t.wben = true;
       }
+    } else if (t.r0 < 0) {
+      t.r0 = g;
+    } else if (g != t.r0) {
+      t.two_readers = true;
     }
-    if (w0g >= 0) {
-      // a read meets a write by another work-item (observed value unknown
-      // here: any other writer may differ): with two distinct writers every
-      // read does; with one, a read by anyone else does
-      int64_t w1g = -1;
-      for (size_t q = i; q < j && w1g < 0; q++)
-        if (evs[q].store && (int64_t)evs[q].gtid != w0g) w1g = evs[q].gtid;
-      for (size_t q = i; q < j && !rrace; q++)
-        if (!evs[q].store && (w1g >= 0 || (int64_t)evs[q].gtid != w0g)) rrace = true;
-    }
-    ww += wrace;
-    benign += wben && !wrace;
+  }
+  double ww = 0, rw = 0, benign = 0;
+  for (const CellAcc &t : cells) {
+    if (t.w0g < 0) continue;
+    // a read meets a write by another work-item (the value it observes is
+    // unknown here: any other writer may differ): with two distinct writers
+    // every read does; with one, a read by anyone else does
+    const bool rrace = t.r0 >= 0 && (t.w1g >= 0 || t.two_readers || t.r0 != t.w0g);
+    ww += t.wrace;
+    benign += t.wben && !t.wrace;
     rw += rrace;
-    i = j;
   }
   out[104] = lg(ww) / 10.0f;
   out[105] = lg(rw) / 10.0f;
@@ -514,7 +548,120 @@ Cand make_cand(const rc_bytecode *bc, uint32_t G, uint32_t S, const rc_input *in
   return c;
 }
 
+// Worker threads of the library, started on first use (one fewer than the
+// host's cores) and kept for the life of the process, so that a search pays
+// no thread start-up per kernel.  A process forked after they started gets a
+// pool of its own.
+class Pool {
+ public:
+  explicit Pool(unsigned n) : pid_(getpid()) {
+    for (unsigned i = 0; i < n; i++) std::thread([this] { loop(); }).detach();
+    size_ = n;
+  }
+  unsigned size() const { return size_; }
+  pid_t pid() const { return pid_; }
+  void submit(std::function<void()> f) {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      q_.push_back(std::move(f));
+    }
+    cv_.notify_one();
+  }
+
+ private:
+  void loop() {
+    for (;;) {
+      std::function<void()> f;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return !q_.empty(); });
+        f = std::move(q_.front());
+        q_.pop_front();
+      }
+      f();
+    }
+  }
+  std::mutex mu_;
+  std::condition_variable cv_;
+  std::deque<std::function<void()>> q_;
+  unsigned size_ = 0;
+  pid_t pid_;
+};
+
+Pool &pool() {
+  static std::mutex mu;
+  static Pool *p = nullptr;  // never destroyed: its threads outlive static destructors
+  std::lock_guard<std::mutex> lk(mu);
+  if (!p || p->pid() != getpid()) {
+    const unsigned hw = std::max(2u, std::thread::hardware_concurrency());
+    p = new Pool(hw - 1);
+  }
+  return *p;
+}
+
 }  // namespace
+
+struct FeatureJob {
+  size_t n = 0;
+  std::function<void(size_t)> one;  // features of candidate i
+  std::atomic<size_t> next{0}, finished{0};
+  std::atomic<unsigned> active{0};
+  std::atomic<bool> cancelled{false}, failed{false};
+  std::string error;
+  std::mutex mu;
+  std::condition_variable cv;
+
+  // takes candidates until none is left; the last thread out wakes the waiter
+  void work() {
+    active.fetch_add(1);
+    for (;;) {
+      const size_t i = next.fetch_add(1);
+      if (i >= n || cancelled.load(std::memory_order_relaxed)) break;
+      try {
+        one(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!failed.exchange(true)) error = "feature extraction failed (host memory)";
+      }
+      finished.fetch_add(1);
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    active.fetch_sub(1);
+    cv.notify_all();
+  }
+  bool done() const { return finished.load() == n; }
+};
+
+std::shared_ptr<FeatureJob> features_start(const rc_bytecode *const *bcs, const uint32_t *groups,
+                                           const uint32_t *group_size, const rc_input *inputs, size_t n,
+                                           float *out, unsigned participants, bool caller_helps) {
+  auto cands = std::make_shared<std::vector<Cand>>();
+  cands->reserve(n);
+  for (size_t i = 0; i < n; i++) cands->push_back(make_cand(bcs[i], groups[i], group_size[i], &inputs[i]));
+  auto job = std::make_shared<FeatureJob>();
+  job->n = n;
+  job->one = [cands, out](size_t i) { features_one((*cands)[i], out + i * RC_N_FEATURES); };
+  // one thread per 8 candidates at most: handing a candidate to a thread
+  // costs about as much as a few candidates' features
+  Pool &P = pool();
+  unsigned nt = participants ? participants : std::max<unsigned>(1, (unsigned)std::min<size_t>(n / 8, P.size() + 1));
+  nt = (unsigned)std::min<size_t>(nt, std::max<size_t>(n, 1));
+  const unsigned workers = std::min(P.size(), caller_helps ? nt - 1 : std::max(nt, 1u));
+  for (unsigned w = 0; w < workers; w++) P.submit([job] { job->work(); });
+  return job;
+}
+
+bool features_finished(const FeatureJob &j) { return j.done(); }
+
+void features_cancel(FeatureJob &j) { j.cancelled.store(true); }
+
+void features_wait(FeatureJob &j) {
+  j.work();  // the caller's share (nothing left when the workers took it all)
+  std::unique_lock<std::mutex> lk(j.mu);
+  j.cv.wait(lk, [&] { return j.active.load() == 0 && (j.done() || j.cancelled.load()); });
+  if (j.failed.load()) throw j.error;
+}
+
 }  // namespace rc
 
 extern "C" {
@@ -530,10 +677,10 @@ int rc_features_batch(const rc_bytecode *const *bcs, const uint32_t *groups, con
     set_last_error("null argument");
     return RC_E_INVALID;
   }
-  std::vector<Cand> cands;
   try {
-    cands.reserve(n);
-    for (size_t i = 0; i < n; i++) cands.push_back(make_cand(bcs[i], groups[i], group_size[i], &inputs[i]));
+    auto job = features_start(bcs, groups, group_size, inputs, n, out, n_threads > 0 ? (unsigned)n_threads : 0u,
+                              true);
+    features_wait(*job);
   } catch (const std::string &e) {
     set_last_error(e);
     return RC_E_INVALID;
@@ -541,21 +688,6 @@ int rc_features_batch(const rc_bytecode *const *bcs, const uint32_t *groups, con
     set_last_error("out of host memory");
     return RC_E_NOMEM;
   }
-  // one thread per 8 candidates at most: starting a thread costs about as
-  // much as a few candidates' features
-  unsigned nt = n_threads > 0 ? (unsigned)n_threads
-                              : std::max(1u, std::min(std::thread::hardware_concurrency(), (unsigned)(n / 8)));
-  nt = (unsigned)std::min<size_t>(nt, std::max<size_t>(n, 1));
-  if (nt <= 1) {
-    for (size_t i = 0; i < n; i++) features_one(cands[i], out + i * RC_N_FEATURES);
-    return RC_OK;
-  }
-  std::vector<std::thread> th;
-  for (unsigned t = 0; t < nt; t++)
-    th.emplace_back([&, t] {
-      for (size_t i = t; i < n; i += nt) features_one(cands[i], out + i * RC_N_FEATURES);
-    });
-  for (auto &x : th) x.join();
   return RC_OK;
 }
 

@@ -26,6 +26,7 @@
 #include "racecheck.h"
 #include "device.cuh"
 #include "jit.h"
+#include "candidate_features.h"
 
 namespace rc {
 // The two-work-item pre-filter (prove.cpp).
@@ -113,7 +114,8 @@ struct Workspace {
       recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff, sortscr, reckern,
       bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround, big, bigres, nbig, xg, xgcnt,
       xgn, xgoff, xgtmp, xgout, rstat, rivoff, rbar;
-  HostBuf hstats, hrecs, hround, hdesc, hsmall, hstage;
+  HostBuf hstats, hrecs, hround, hdesc, hsmall, hstage, hrank;
+  DevBuf rankx;  // ranked search: features and scores of the candidates
   DevBuf stage;  // one-CTA checks: bytecode, memory table and snapshot in one block
   cudaStream_t bstream = nullptr;
   cudaEvent_t sev[2] = {nullptr, nullptr};  // stats of an interval (by parity) reached the host
@@ -1872,6 +1874,115 @@ int rc_search(const rc_bytecode *const *bcs, const uint32_t *groups, const uint3
       rc_report_free(r);
     }
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return RC_OK;
+  } catch (const Fail &f) {
+    return fail_code(f);
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return RC_E_NOMEM;
+  }
+}
+
+int rc_search_ranked(rc_mlp *model, const rc_bytecode *const *bcs, const uint32_t *groups,
+                     const uint32_t *group_size, const rc_input *inputs, size_t n, uint32_t max_checks,
+                     uint32_t flags, rc_ranked_result *res, rc_report **found) {
+  if (!res || (n && (!bcs || !groups || !group_size || !inputs)) || (flags & ~RC_RANK_OVERLAP)) return RC_E_INVALID;
+  *res = rc_ranked_result{-1, 0, 0, 0, 0, 0, 0};
+  if (found) *found = nullptr;
+  if (n == 0) return RC_OK;
+  using clock = std::chrono::steady_clock;
+  const auto t0 = clock::now();
+  const auto secs = [](clock::time_point a, clock::time_point b) { return std::chrono::duration<double>(b - a).count(); };
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace &W = g_ws;
+  std::shared_ptr<FeatureJob> job;
+  try {
+    for (size_t i = 0; i < n; i++) {
+      check_args(bcs[i], groups[i], group_size[i], &inputs[i]);
+      if (inputs[i].on_device) throw Fail{RC_E_INVALID, "ranked search reads host inputs only"};
+    }
+    float *X = W.hrank.get<float>(n * RC_N_FEATURES + n);  // features, then scores
+    float *score = X + n * RC_N_FEATURES;
+    const size_t limit = max_checks ? std::min<size_t>(n, max_checks) : n;
+    std::vector<uint8_t> checked(n, 0);
+    // one exact check; true when it is racy (the search ends)
+    const auto check = [&](size_t i) {
+      const auto c0 = clock::now();
+      Instance I{&bcs[i]->prog, groups[i], group_size[i], (uint64_t)groups[i] * group_size[i], &inputs[i],
+                 static_cast<cudaStream_t>(inputs[i].cuda_stream)};
+      rc_report *r = run_instance(I);
+      checked[i] = 1;
+      res->checks++;
+      res->check_seconds += secs(c0, clock::now());
+      if (r->status == RC_RACY) {
+        res->first = (int64_t)i;
+        if (found) *found = r;
+        else rc_report_free(r);
+        return true;
+      }
+      rc_report_free(r);
+      return false;
+    };
+    const bool overlap = flags & RC_RANK_OVERLAP;
+    try {
+      job = features_start(bcs, groups, group_size, inputs, n, X, 0, !overlap);
+    } catch (const std::string &e) {
+      throw Fail{RC_E_INVALID, e};
+    }
+    // the job writes into X until features_wait returns: wait on every way out
+    struct Waiter {
+      std::shared_ptr<FeatureJob> &j;
+      ~Waiter() {
+        if (j) {
+          features_cancel(*j);
+          try {
+            features_wait(*j);
+          } catch (...) {
+          }
+        }
+      }
+    } waiter{job};
+    if (g_prof.on) prof_events();
+    bool racy = false;
+    if (overlap)
+      for (size_t i = 0; i < limit && !racy && !features_finished(*job); i++) racy = check(i);
+    res->checks_unranked = res->checks;
+    if (racy) features_cancel(*job);  // candidates in progress still finish
+    try {
+      features_wait(*job);
+    } catch (const std::string &e) {
+      if (!racy) throw Fail{RC_E_NOMEM, e};
+    }
+    job.reset();
+    if (!racy) {
+      const auto f1 = clock::now();
+      res->features_seconds = secs(t0, f1);
+      if (model) {
+        cudaStream_t s = static_cast<cudaStream_t>(inputs[0].cuda_stream);
+        float *dx = W.rankx.get<float>(n * RC_N_FEATURES + n);
+        CK(cudaMemcpyAsync(dx, X, n * RC_N_FEATURES * sizeof(float), cudaMemcpyHostToDevice, s));
+        const int e = rc_mlp_forward(model, dx, n, dx + n * RC_N_FEATURES, s);
+        if (e != RC_OK) throw Fail{e, "scoring the candidates failed: " + g_last_error};
+        CK(cudaMemcpyAsync(score, dx + n * RC_N_FEATURES, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+      } else {
+        for (size_t i = 0; i < n; i++) {
+          const float *f = X + i * RC_N_FEATURES;
+          // products by powers of two are exact and a division is never
+          // fused: the same float on every host and in numpy
+          score[i] = 4.0f * f[108] + 2.0f * f[107] + (f[104] + f[105]) / 10.0f;
+        }
+      }
+      std::vector<size_t> order(n);
+      for (size_t i = 0; i < n; i++) order[i] = i;
+      std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return score[a] > score[b]; });
+      res->scoring_seconds = secs(f1, clock::now());
+      for (size_t k = 0; k < n && res->checks < limit && !racy; k++)
+        if (!checked[order[k]]) racy = check(order[k]);
+    } else {
+      res->features_seconds = secs(t0, clock::now());
+    }
+    res->seconds = secs(t0, clock::now());
     return RC_OK;
   } catch (const Fail &f) {
     return fail_code(f);

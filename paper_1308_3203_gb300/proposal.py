@@ -7,10 +7,12 @@ Pipeline (every computation in the library; this module only moves arrays):
      (rc_check_batch; racy = report status RC_RACY);
   3. features: rc_features_batch (host C++ in the library);
   4. training: rc_mlp_train (BF16 tensor-core forward/backward, Adam);
-  5. search: scores from rc_mlp_forward, then rc_search checks candidates in
-     descending score order until the first racy report.  Plain enumeration
-     is rc_search without scores.  A race is claimed only from a checker
-     report, so the precision of every flag is that of the checker.
+  5. search: rc_search_ranked computes the features, scores them with
+     rc_mlp_forward and checks candidates in descending score order until
+     the first racy report (optionally checking in index order while the
+     ranking is computed).  Plain enumeration is rc_search without scores.
+     A race is claimed only from a checker report, so the precision of
+     every flag is that of the checker.
 """
 from __future__ import annotations
 
@@ -63,67 +65,71 @@ F_PREDICTED, F_SAMPLED, F_WW, F_RW = 108, 107, 104, 105
 
 
 def rule_scores(X: np.ndarray) -> np.ndarray:
-    """The ranking without a network: candidates whose features predict a
-    race first, then those with sampled collisions, more collisions first;
-    ties keep the index order."""
-    return 4.0 * X[:, F_PREDICTED] + 2.0 * X[:, F_SAMPLED] + 0.1 * (X[:, F_WW] + X[:, F_RW])
+    """The ranking rc_search_ranked uses without a network, in the same
+    float32 arithmetic: candidates whose features predict a race first, then
+    those with sampled collisions, more collisions first; ties keep the
+    index order."""
+    X = np.asarray(X, dtype=np.float32)
+    return (np.float32(4) * X[:, F_PREDICTED] + np.float32(2) * X[:, F_SAMPLED]
+            + (X[:, F_WW] + X[:, F_RW]) / np.float32(10))
 
 
-def compare_search(model: rc.MLP, seeds, n_cand: int = 64) -> dict:
-    """Three searches of each kernel's candidates on the same GPU with the
-    same checker: ranked by the trained network, ranked by the rule above
-    (no network), and plain enumeration (index order).  Per search: checks
-    and seconds to the first racy candidate, and whether it found a race
-    where exhaustive enumeration does; `*_total_s` adds the cost of ranking
-    (feature extraction, and the network's inference for the network)."""
-    import time
-    import torch
+def compare_search(model: rc.MLP, seeds, n_cand: int = 64, warmup_seed: int = 10**9) -> dict:
+    """Searches of each kernel's candidates on the same GPU with the same
+    checker, in this order:
+      enum      plain enumeration (index order, rc_search without scores);
+      ranked    rc_search_ranked with the trained network: features on the
+                host threads, then network scores, then checks in order;
+      overlap   the same with RC_RANK_OVERLAP (index-order checks while the
+                ranking is computed);
+      rule      rc_search_ranked without a network (the rule ranking);
+      rule_overlap  the rule with RC_RANK_OVERLAP.
+    Per search: checks and seconds to the first racy candidate (for the
+    ranked searches the whole call: features, scores and checks; `*_check_s`
+    the checks alone), and whether it found a race where exhaustive
+    enumeration does.  One kernel outside `seeds` is searched first, every
+    way, untimed (thread pool and workspace set-up)."""
+    kinds = dict(ranked=(model, False), overlap=(model, True), rule=(None, False), rule_overlap=(None, True))
+    _, items = kernel_candidates(warmup_seed, n_cand)
+    rc.search(items)
+    for m, ov in kinds.values():
+        rc.search_ranked(items, m, overlap=ov)
     rows = []
     for s in seeds:
         _, items = kernel_candidates(s, n_cand)
-        t0 = time.perf_counter()
-        X = rc.features(items)
-        t_feat = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        sc = scores(model, X)
-        torch.cuda.synchronize()
-        t_inf = time.perf_counter() - t0
         enum = rc.search(items)                   # index order = enumeration
-        ranked = rc.search(items, scores=sc)
-        rule = rc.search(items, scores=rule_scores(X))
-        rows.append(dict(seed=s, racy=enum["first"] >= 0, enum_checks=enum["checks"],
-                         enum_s=enum["seconds"], ranked_checks=ranked["checks"], ranked_s=ranked["seconds"],
-                         ranked_first=ranked["first"], enum_first=enum["first"],
-                         ranked_found=ranked["first"] >= 0,
-                         ranked_total_s=ranked["seconds"] + t_feat + t_inf,
-                         rule_checks=rule["checks"], rule_s=rule["seconds"], rule_found=rule["first"] >= 0,
-                         rule_total_s=rule["seconds"] + t_feat, features_s=t_feat, inference_s=t_inf))
+        row = dict(seed=s, racy=enum["first"] >= 0, enum_checks=enum["checks"], enum_s=enum["seconds"],
+                   enum_first=enum["first"])
+        for k, (m, ov) in kinds.items():
+            r = rc.search_ranked(items, m, overlap=ov)
+            row.update({f"{k}_checks": r["checks"], f"{k}_s": r["seconds"], f"{k}_check_s": r["check_seconds"],
+                        f"{k}_features_s": r["features_seconds"], f"{k}_scoring_s": r["scoring_seconds"],
+                        f"{k}_unranked": r["checks_unranked"], f"{k}_first": r["first"],
+                        f"{k}_found": r["first"] >= 0})
+        rows.append(row)
     return summarize(rows)
 
 
 def summarize(rows) -> dict:
+    """Totals over the kernels enumeration finds racy: seconds and speed-up
+    against enumeration per search, mean checks, recall and recall@k (a race
+    within k checks)."""
     racy = [r for r in rows if r["racy"]]
     out = dict(kernels=len(rows), racy_kernels=len(racy), rows=rows)
-    if racy:
-        te = sum(r["enum_s"] for r in racy)
-        tr = sum(r["ranked_s"] for r in racy)
-        out.update(enum_seconds=te, ranked_seconds=tr, speedup=te / tr if tr > 0 else float("inf"),
-                   enum_checks_mean=float(np.mean([r["enum_checks"] for r in racy])),
-                   ranked_checks_mean=float(np.mean([r["ranked_checks"] for r in racy])),
-                   recall=float(np.mean([r["ranked_found"] for r in racy])))
-        for k in (1, 2, 4, 8):
-            out[f"recall_at_{k}"] = float(np.mean([r["ranked_found"] and r["ranked_checks"] <= k for r in racy]))
-        if "rule_checks" in racy[0]:
-            tt = sum(r["ranked_total_s"] for r in racy)
-            tu = sum(r["rule_total_s"] for r in racy)
-            out.update(ranked_total_seconds=tt, speedup_total=te / tt if tt > 0 else float("inf"),
-                       features_seconds=sum(r["features_s"] for r in racy),
-                       inference_seconds=sum(r["inference_s"] for r in racy),
-                       rule_seconds=sum(r["rule_s"] for r in racy), rule_total_seconds=tu,
-                       rule_speedup_total=te / tu if tu > 0 else float("inf"),
-                       rule_checks_mean=float(np.mean([r["rule_checks"] for r in racy])),
-                       rule_recall=float(np.mean([r["rule_found"] for r in racy])))
-            for k in (1, 2, 4, 8):
-                out[f"rule_recall_at_{k}"] = float(np.mean([r["rule_found"] and r["rule_checks"] <= k
-                                                            for r in racy]))
+    if not racy:
+        return out
+    te = sum(r["enum_s"] for r in racy)
+    out.update(enum_seconds=te, enum_checks_mean=float(np.mean([r["enum_checks"] for r in racy])))
+    for k in ("ranked", "overlap", "rule", "rule_overlap"):
+        t = sum(r[f"{k}_s"] for r in racy)
+        tc = sum(r[f"{k}_check_s"] for r in racy)
+        out[k] = dict(seconds=t, speedup=te / t if t > 0 else float("inf"),
+                      check_seconds=tc, check_speedup=te / tc if tc > 0 else float("inf"),
+                      features_seconds=sum(r[f"{k}_features_s"] for r in racy),
+                      scoring_seconds=sum(r[f"{k}_scoring_s"] for r in racy),
+                      checks_mean=float(np.mean([r[f"{k}_checks"] for r in racy])),
+                      unranked_checks_mean=float(np.mean([r[f"{k}_unranked"] for r in racy])),
+                      recall=float(np.mean([r[f"{k}_found"] for r in racy])))
+        for j in (1, 2, 4, 8):
+            out[k][f"recall_at_{j}"] = float(np.mean([r[f"{k}_found"] and r[f"{k}_checks"] <= j for r in racy]))
     return out

@@ -78,6 +78,15 @@ class _SearchResult(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class _RankedResult(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_int64), ("checks", ctypes.c_uint32), ("checks_unranked", ctypes.c_uint32),
+                ("seconds", ctypes.c_double), ("features_seconds", ctypes.c_double),
+                ("scoring_seconds", ctypes.c_double), ("check_seconds", ctypes.c_double)]
+
+
+RC_RANK_OVERLAP = 1
+
+
 N_FEATURES = 128
 MLP_PARAMS = 164865
 
@@ -152,6 +161,10 @@ def load() -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_Input), ctypes.c_size_t,
                                   fp, ctypes.c_uint32, ctypes.POINTER(_SearchResult),
                                   ctypes.POINTER(ctypes.POINTER(_Report))]
+        lib.rc_search_ranked.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint32),
+                                         ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_Input), ctypes.c_size_t,
+                                         ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_RankedResult),
+                                         ctypes.POINTER(ctypes.POINTER(_Report))]
         lib.rc_explore.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input), ctypes.c_uint64,
                                    ctypes.POINTER(_ExploreInterval), ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
         lib.rc_explore_pairs.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Input),
@@ -170,7 +183,7 @@ def load() -> ctypes.CDLL:
         lib.rc_translate.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_size_t,
                                      ctypes.POINTER(ctypes.c_size_t)]
         for f in ("rc_prove", "rc_prove_private", "rc_access_sites", "rc_translate", "rc_mlp_set_backend", "rc_mlp_backend_error", "rc_explore", "rc_explore_pairs", "rc_features_batch", "rc_mlp_create", "rc_mlp_get_params", "rc_mlp_set_params",
-                  "rc_mlp_forward", "rc_mlp_grad", "rc_mlp_train", "rc_search"):
+                  "rc_mlp_forward", "rc_mlp_grad", "rc_mlp_train", "rc_search", "rc_search_ranked"):
             getattr(lib, f).restype = c_int
         for f in ("rc_compile", "rc_bytecode_info_get", "rc_check", "rc_check_batch",
                   "rc_set_strategy", "rc_profile_enable", "rc_profile_reset", "rc_profile_get",
@@ -601,6 +614,28 @@ def search(items, scores=None, max_checks: int = 0) -> dict:
         _raise(rc)
     return dict(first=int(res.first), checks=int(res.checks), seconds=float(res.seconds),
                 report=_report(found) if found else None)
+
+
+def search_ranked(items, model=None, overlap: bool = False, max_checks: int = 0) -> dict:
+    """Ranked search in one native call (rc_search_ranked): features on the
+    library's host threads, scores from `model` (an MLP) or, with None, the
+    rule ranking, then exact checks in score order; with overlap the GPU
+    checks candidates in index order until the ranking exists.  Returns
+    first, checks, checks_unranked, seconds (whole call), features_seconds,
+    scoring_seconds, check_seconds and the racy candidate's report."""
+    n = len(items)
+    hs, gs, ss, inputs, keep = _items_arrays(items)
+    res = _RankedResult()
+    found = ctypes.POINTER(_Report)()
+    rc = load().rc_search_ranked(model._h if model is not None else None, hs, gs, ss, inputs, n, max_checks,
+                                 RC_RANK_OVERLAP if overlap else 0, ctypes.byref(res), ctypes.byref(found))
+    del keep
+    if rc:
+        _raise(rc)
+    out = {k: getattr(res, k) for k, _ in _RankedResult._fields_}
+    out = {k: (int(v) if isinstance(v, int) else float(v)) for k, v in out.items()}
+    out["report"] = _report(found) if found else None
+    return out
 
 
 class MLP:

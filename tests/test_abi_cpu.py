@@ -145,3 +145,40 @@ def test_prove_private_checks_its_flag_array(rc):
     n = ctypes.c_uint32()
     assert rc.load().rc_prove_private(bc.handle, 1, 8, ctypes.byref(inp), flags, 1, ctypes.byref(n)) == 2
     del keep
+
+
+def test_search_ranked_checks_its_arguments_without_gpu_work(rc):
+    """Unknown flags and missing arrays are refused, and an empty candidate
+    list is an empty search, before any device or feature work."""
+    import ctypes
+    lib = rc.load()
+    res = rc._RankedResult()
+    assert lib.rc_search_ranked(None, None, None, None, None, 0, 0, 0, ctypes.byref(res), None) == 0
+    assert res.first == -1 and res.checks == 0
+    assert lib.rc_search_ranked(None, None, None, None, None, 0, 0, 2, ctypes.byref(res), None) == 2
+    assert lib.rc_search_ranked(None, None, None, None, None, 3, 0, 0, ctypes.byref(res), None) == 2
+    assert lib.rc_search_ranked(None, None, None, None, None, 0, 0, 0, None, None) == 2
+
+
+@pytest.mark.filterwarnings("ignore:This process .* is multi-threaded")
+def test_features_worker_pool_survives_a_fork(rc):
+    """The feature threads are per process: a child forked after they
+    started computes the same features with a pool of its own."""
+    import multiprocessing as mp
+    from paper_1308_3203_gb300 import proposal
+    _, items = proposal.kernel_candidates(7)
+    want = rc.features(items, n_threads=4)
+    ctx = mp.get_context("fork")
+    q = ctx.Queue()
+    p = ctx.Process(target=_features_in_child, args=(q, 7))
+    p.start()
+    got = q.get(timeout=120)
+    p.join(timeout=60)
+    assert p.exitcode == 0
+    np.testing.assert_array_equal(got, want)
+
+
+def _features_in_child(q, seed):
+    from paper_1308_3203_gb300 import proposal, racecheck
+    _, items = proposal.kernel_candidates(seed)
+    q.put(racecheck.features(items, n_threads=4))

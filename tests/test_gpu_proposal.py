@@ -172,8 +172,53 @@ def test_training_ranks_racy_candidates_first(rc):
     assert losses[-1] < 0.5 * losses[0], losses
     res = proposal.compare_search(m, range(100000, 100060))
     assert res["racy_kernels"] >= 20
-    assert res["ranked_checks_mean"] < res["enum_checks_mean"]
-    assert res["speedup"] > 1.5, res
-    assert res["recall"] == 1.0 and res["recall_at_2"] >= 0.7, res
+    rk = res["ranked"]
+    assert rk["checks_mean"] < res["enum_checks_mean"]
+    assert rk["check_speedup"] > 1.5, res
+    assert rk["recall"] == 1.0 and rk["recall_at_2"] >= 0.7, res
     for r in res["rows"]:
-        assert r["ranked_found"] == r["racy"]  # both searches see every candidate when needed
+        for k in ("ranked", "overlap", "rule", "rule_overlap"):
+            assert r[f"{k}_found"] == r["racy"]  # every search sees every candidate when needed
+
+
+def test_search_ranked_orders_as_rc_search_with_the_same_scores(rc):
+    """rc_search_ranked (features, scores and checks in one call) meets the
+    same first racy candidate after the same checks as rc_search given the
+    scores computed step by step: the network's (an untrained one will do)
+    and the rule's."""
+    from paper_1308_3203_gb300 import proposal
+    m = rc.MLP(seed=3, capacity=256)
+    for s in range(200000, 200012):
+        _, items = proposal.kernel_candidates(s)
+        X = rc.features(items)
+        for model, sc in ((m, proposal.scores(m, X)), (None, proposal.rule_scores(X))):
+            want = rc.search(items, scores=sc)
+            got = rc.search_ranked(items, model)
+            assert (got["first"], got["checks"]) == (want["first"], want["checks"]), (s, model)
+            assert got["checks_unranked"] == 0
+            if got["first"] >= 0:
+                assert got["report"]["status"] == rc.RACY
+            for lim in (1, 3):
+                g2 = rc.search_ranked(items, model, max_checks=lim)
+                w2 = rc.search(items, scores=sc, max_checks=lim)
+                assert (g2["first"], g2["checks"]) == (w2["first"], w2["checks"])
+
+
+def test_search_ranked_overlap_finds_what_enumeration_finds(rc):
+    """With RC_RANK_OVERLAP every race still comes from a check (the report
+    is racy), the search finds one exactly when enumeration does, and no
+    candidate is checked twice (checks <= candidates)."""
+    from paper_1308_3203_gb300 import proposal
+    m = rc.MLP(seed=4, capacity=256)
+    for s in range(200100, 200116):
+        _, items = proposal.kernel_candidates(s)
+        enum = rc.search(items)
+        for model in (m, None):
+            got = rc.search_ranked(items, model, overlap=True)
+            assert (got["first"] >= 0) == (enum["first"] >= 0), s
+            assert got["checks_unranked"] <= got["checks"] <= len(items)
+            if got["first"] >= 0:
+                assert got["report"]["status"] == rc.RACY
+                one = rc.check(items[got["first"]][0], items[got["first"]][1], items[got["first"]][2],
+                               items[got["first"]][3])
+                assert one["status"] == rc.RACY
