@@ -267,27 +267,43 @@ def batch_leg(rc, W, n_kernels, rank=0, world=1, dist=None, hbm=6800.0):
     else:
         insts = [W._batch_one(p) for p in mine]
     items = [(rc.compile(i.src), i.groups, i.group_size, i.globals) for i in insts]
-    rc.check_batch(items[:64], want_final=False)  # warm-up (and autotuner exploration)
     import torch
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    t0 = time.perf_counter()
-    got = rc.check_batch(items, want_final=False)
-    dt = time.perf_counter() - t0
-    acc = sum(g["n_access"] for g in got)
-    logged_g = sum(g["n_global"] * g["n_logged"] // max(g["n_access"], 1) for g in got)
-    dt_max, = combine([dt], dist, "max")
-    acc_all, n_all, lg_all = combine([acc, len(items), logged_g], dist, "sum")
-    gbs = 24.0 * lg_all / dt_max / 1e9
-    return {"workload": f"{n_kernels} kernels: group size log-uniform 32-1024, 1-64 groups, "
-                        "16-512 statements, 0-8 barriers, global int32 arrays 1K-1M",
-            "kernels_per_s": n_all / dt_max, "accesses_per_s": acc_all / dt_max, "seconds": dt_max,
-            "accesses": int(acc_all), "logged_global_accesses": int(lg_all),
-            "hbm": {"what": "24 B per logged global access (log write + classification read) over the "
-                            "call's wall time", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm},
-            "timing": "host wall clock around rc_check_batch (host inputs, H2D and report D2H included), "
-                      "slowest rank"}
+
+    def timed(strategy):
+        rc.set_strategy(strategy)
+        try:
+            rc.check_batch(items[:64], want_final=False)  # warm-up (and autotuner exploration)
+            torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
+            t0 = time.perf_counter()
+            got = rc.check_batch(items, want_final=False)
+            dt = time.perf_counter() - t0
+        finally:
+            rc.set_strategy(0)
+        return got, dt
+
+    def line(got, dt):
+        acc = sum(g["n_access"] for g in got)
+        logged_g = sum(g["n_global"] * g["n_logged"] // max(g["n_access"], 1) for g in got)
+        dt_max, = combine([dt], dist, "max")
+        acc_all, n_all, lg_all = combine([acc, len(items), logged_g], dist, "sum")
+        gbs = 24.0 * lg_all / dt_max / 1e9
+        return {"kernels_per_s": n_all / dt_max, "accesses_per_s": acc_all / dt_max, "seconds": dt_max,
+                "accesses": int(acc_all), "logged_global_accesses": int(lg_all),
+                "hbm": {"what": "24 B per logged global access (log write + classification read) over the "
+                                "call's wall time", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                        "frac": gbs / hbm}}
+
+    out = {"workload": f"{n_kernels} kernels: group size log-uniform 32-1024, 1-64 groups, "
+                       "16-512 statements, 0-8 barriers, global int32 arrays 1K-1M",
+           "run": "lock-step rounds, strategy and block shape autotuned"}
+    out.update(line(*timed(0)))
+    out["resident"] = dict(run="every round of a sub-batch in one cooperative launch (strategy 3)",
+                           **line(*timed(3)))
+    out["timing"] = ("host wall clock around rc_check_batch (host inputs, H2D and report D2H included), "
+                     "slowest rank")
+    return out
 
 
 def proposal_leg(rc, n_train, n_eval=200, epochs=20):
@@ -319,6 +335,7 @@ def proposal_leg(rc, n_train, n_eval=200, epochs=20):
     t_inf = (time.perf_counter() - t0) / 5
     res = proposal.compare_search(m, range(10**6, 10**6 + n_eval))
     res.pop("rows")
+    fam = batch_family_leg(rc, proposal)
     return {"workload": f"{n_train} training kernels x 64 candidates (group size 32..1024 step 32, "
                         f"1..64 groups, input seed), {n_eval} held-out kernels",
             "train_examples": int(len(y)), "racy_fraction": float(y.mean()),
@@ -327,7 +344,32 @@ def proposal_leg(rc, n_train, n_eval=200, epochs=20):
             "train_tflops": epochs * len(y) * flops / t_train / 1e12,
             "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1]),
             "inference_examples_per_s": len(y) / t_inf,
-            "search": res}
+            "search": res, "config3_family": fam}
+
+
+def batch_family_leg(rc, proposal, n_train=300, n_eval=100, epochs=20):
+    """The same pipeline on kernels of the config-3 generator (program fixed
+    per kernel, 64 candidate launch shapes and inputs each): how many
+    candidates are racy, whether the first one already is, and the searches
+    with a network trained on this family."""
+    import torch
+    t0 = time.perf_counter()
+    X, y, kid = proposal.dataset(range(2 * 10**6, 2 * 10**6 + n_train), family="batch")
+    t_data = time.perf_counter() - t0
+    per = [y[kid == k] for k in range(n_train)]
+    racy_k = [p for p in per if p.max() > 0]
+    m = rc.MLP(seed=0, capacity=8192)
+    losses = m.train(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), epochs=epochs, batch=2048,
+                     lr=2e-3, seed=1)
+    res = proposal.compare_search(m, range(3 * 10**6, 3 * 10**6 + n_eval), family="batch")
+    res.pop("rows")
+    return {"workload": f"{n_train} training kernels of the config-3 generator (16-512 statements, 0-8 barriers, "
+                        f"A[1K..1M]) x 64 candidates, {n_eval} held-out kernels",
+            "label_and_feature_seconds": t_data, "racy_fraction": float(y.mean()),
+            "racy_kernels_fraction": len(racy_k) / n_train,
+            "racy_candidates_per_racy_kernel": float(np.mean([p.mean() for p in racy_k])) if racy_k else 0.0,
+            "first_candidate_racy_fraction": float(np.mean([p[0] > 0 for p in racy_k])) if racy_k else 0.0,
+            "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1]), "search": res}
 
 
 def measure(rc, inst, bc, *, steps, warmup, dist, flush, log_every=False, host=True, prof_steps=None):

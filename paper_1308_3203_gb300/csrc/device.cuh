@@ -130,12 +130,30 @@ struct BatchArgs {
   unsigned long long *acc;      // [2 * instances]: global, local accesses
   uint32_t *flags;
   uint32_t *owner;              // shadow owner table over the batch's cells
+  // resident runs: every round of the batch in one cooperative launch
+  unsigned *grid_bar;           // kGridBarWords, zero before the launch
+  unsigned long long barrier_limit_ns;
+  LogRec *acc_out;              // records of shared cells, every round end to end
+  unsigned long long *acc_total;  // records in acc_out
+  unsigned long long *iv_off;   // [max_rounds + 1]: first record of each round
+  unsigned long long acc_cap;
+  uint64_t owner_words;         // owner-table words the batch's cells use (cleared in-kernel at a tag wrap)
+  uint32_t n_inst, max_rounds, tag0;
+  uint32_t *n_active;           // [2] instances active in the next round (by parity; zero before the launch)
+  uint32_t *inst_rounds;        // [n_inst] intervals each instance ran; [n_inst] rounds, [n_inst + 1] last tag
 };
 
 // block shapes of the batch interpreter: 128, 256 or 512 threads per CTA
 size_t batch_smem_bytes(uint32_t max_regs, uint32_t ow_slots, uint32_t threads);
 cudaError_t batch_configure();
 void launch_batch_interp(const BatchArgs &a, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t s);
+// Every round of the batch in one cooperative launch of `grid` CTAs (all
+// resident): the interpreter's round, then the commit of the owner table's
+// highest writers and the compaction of the records of shared cells into
+// acc_out, then each instance's barrier agreement, between grid barriers.
+cudaError_t launch_batch_resident(const BatchArgs &a, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t s);
+// CTAs of the resident batch kernel one SM holds with this block shape and shared memory
+int batch_resident_blocks_per_sm(uint32_t threads, size_t smem);
 void launch_batch_compact(const BatchArgs &a, LogRec *out, unsigned long long *total, cudaStream_t s);
 void launch_batch_commit(const BatchArgs &a, cudaStream_t s);
 

@@ -157,7 +157,8 @@ __device__ __forceinline__ void compact_slice(const uint4 *src, uint32_t n, cons
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       const uint32_t i = base + q * 32 + lane;
-      r[q] = i < n ? src[i] : make_uint4(0, 0, 0, 0);
+      // through L2: a resident batch compacts slices another SM wrote in the same launch
+      r[q] = i < n ? __ldcg(src + i) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int q = 0; q < 4; q++)

@@ -191,6 +191,16 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// 16-byte asynchronous copy global -> shared (zero fill when !valid; the
+// source must still be a mapped address): the staging loops keep every copy
+// of a thread in flight at once instead of waiting for each load
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(smem_dst)), "l"(gsrc),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // shared-memory matrix descriptor: start, leading and stride byte offsets
 // (all >> 4), descriptor version 1, no swizzle
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -216,18 +226,18 @@ __global__ void __launch_bounds__(kTcThreads) tc_fwd_kernel(const bf16 *__restri
   uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int m0 = blockIdx.x * kTcRows, n0 = blockIdx.y * kTcN;
-  // stage both operands, 16 bytes (8 elements along K) per copy
+  // stage both operands, 16 bytes (8 elements along K) per copy; rows past
+  // M are zero-filled
   for (int i = t; i < kTcRows * KC; i += kTcThreads) {
     const int r = i / KC, c = i % KC;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (m0 + r < M) v = *reinterpret_cast<const uint4 *>(act + (size_t)(m0 + r) * K + c * 8);
-    *reinterpret_cast<uint4 *>(As + ((r >> 3) * KC + c) * 128 + (r & 7) * 16) = v;
+    const bool in = m0 + r < M;
+    cp_async16(As + ((r >> 3) * KC + c) * 128 + (r & 7) * 16, act + (size_t)(in ? m0 + r : 0) * K + c * 8, in);
   }
   for (int i = t; i < kTcN * KC; i += kTcThreads) {
     const int n = i / KC, c = i % KC;
-    *reinterpret_cast<uint4 *>(Bs + ((n >> 3) * KC + c) * 128 + (n & 7) * 16) =
-        *reinterpret_cast<const uint4 *>(W + (size_t)(n0 + n) * K + c * 8);
+    cp_async16(Bs + ((n >> 3) * KC + c) * 128 + (n & 7) * 16, W + (size_t)(n0 + n) * K + c * 8, true);
   }
+  cp_async_wait_all();
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -417,11 +427,11 @@ __global__ void __launch_bounds__(kTcThreads) tc_dgrad_kernel(const bf16 *__rest
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31, m0 = blockIdx.x * kTcRows, n0 = blockIdx.y * kTcN;
   for (int i = t; i < kTcRows * KC; i += kTcThreads) {  // A = dz rows, K contiguous
     const int r = i / KC, c = i % KC;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (m0 + r < M) v = *reinterpret_cast<const uint4 *>(dz + (size_t)(m0 + r) * kHid + c * 8);
-    *reinterpret_cast<uint4 *>(As + ((r >> 3) * KC + c) * 128 + (r & 7) * 16) = v;
+    const bool in = m0 + r < M;
+    cp_async16(As + ((r >> 3) * KC + c) * 128 + (r & 7) * 16, dz + (size_t)(in ? m0 + r : 0) * kHid + c * 8, in);
   }
   tc_stage_mn(Bs, W, kHid, n0, kTcN, 0, kTcK);  // B[n][k] = W[k][n0 + n]
+  cp_async_wait_all();
   const uint32_t tmem = tc_begin(mbar, tslot);
   if (!tc_mma_tile(As, Bs, tmem, tc_idesc(kTcN), false, mbar, 0)) {
     if (t == 0) atomicOr(err, 1u);

@@ -115,6 +115,7 @@ struct Workspace {
       bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround, big, bigres, nbig, xg, xgcnt,
       xgn, xgoff, xgtmp, xgout, rstat, rivoff, rbar;
   HostBuf hstats, hrecs, hround, hdesc, hsmall, hstage, hrank;
+  DevBuf brounds;  // resident batch: intervals per instance, rounds, last tag
   DevBuf rankx;  // ranked search: features and scores of the candidates
   DevBuf stage;  // one-CTA checks: bytecode, memory table and snapshot in one block
   cudaStream_t bstream = nullptr;
@@ -1372,10 +1373,16 @@ BatchItem plan_item(const rc_bytecode *bc, uint32_t G, uint32_t S, const rc_inpu
   return it;
 }
 
-// Check instances [0, n) of `items` together: every round runs one barrier
-// interval of every instance still active, in one persistent interpreter
-// launch, then one classification over the shared cell space.
-void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy, rc_report **out) {
+// Check instances [0, n) of `items` together.  Lock-step rounds: every round
+// runs one barrier interval of every instance still active, in one
+// persistent interpreter launch (a captured graph with the commit and the
+// compaction), then one classification over the shared cell space, and the
+// host's barrier agreement.  Resident (strategy 3): every round in one
+// cooperative launch (batch.cu, batch_resident_kernel), then the
+// classification of each round's compacted records.  Returns false when a
+// resident run could not finish (not every CTA resident, the record buffer
+// or the round cap reached): the caller checks the batch again in lock-step.
+bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy, rc_report **out) {
   Workspace &W = g_ws;
   if (!W.batch_configured) {
     CK(batch_configure());
@@ -1516,6 +1523,142 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   a.flags = dstats;
   a.owner = owner;
   unsigned long long *cnt = reinterpret_cast<unsigned long long *>(dstats + 4);
+  if (strategy == 3) {
+    // ---- resident run: every round in one cooperative launch
+    const uint32_t threads = g_tuner.threads_decided(tkey) ? g_tuner.choose_threads(tkey) : 256u;
+    const uint32_t ctas_per_sm = 1024 / threads;
+    uint32_t ow_slots = 0;
+    while (ow_slots < 8 && ow_slots < max_writes &&
+           batch_smem_bytes(max_regs, ow_slots + 1, threads) <= 200 * 1024 / ctas_per_sm)
+      ow_slots++;
+    const size_t smem = batch_smem_bytes(max_regs, ow_slots, threads);
+    const int per_sm = batch_resident_blocks_per_sm(threads, smem);
+    if (per_sm <= 0) return false;
+    const uint32_t warps_per_cta = threads / 32;
+    const uint32_t grid = std::max<uint32_t>(
+        1, std::min<uint32_t>((n_tasks + warps_per_cta - 1) / warps_per_cta, (uint32_t)sms * (uint32_t)per_sm));
+    // compacted records of every round: twice one round's slice capacity, at
+    // least 4 Mi records, at most 2^31 (32 GiB); a run that needs more starts
+    // over in lock-step
+    const uint64_t acc_cap = std::min<uint64_t>(std::max<uint64_t>(2 * logrecs, 1ull << 22), 1ull << 31);
+    LogRec *acc_out = W.logb.get<LogRec>(acc_cap);
+    uint32_t *owner_r = owner;  // the shadow table (strategy 3 is not the sort path)
+    const uint32_t tag0 = shadow_next_tag(W, s, 4 * keys);
+    unsigned *bar = W.rbar.get<unsigned>(kGridBarWords);
+    unsigned long long *ivoff = W.rivoff.get<unsigned long long>(kResidentMaxIntervals + 1);
+    uint32_t *irounds = W.brounds.get<uint32_t>(n + 2);
+    CK(cudaMemsetAsync(dstats, 0, 8 * 4, s));
+    CK(cudaMemsetAsync(dstats + 8, 0xFF, stops * 4, s));
+    CK(cudaMemsetAsync(dstats + 8 + stops, 0, stops * 4, s));
+    CK(cudaMemsetAsync(bar, 0, kGridBarWords * 4, s));
+    CK(cudaMemsetAsync(ivoff, 0, 8, s));
+    CK(cudaMemsetAsync(dround, 0, 16, s));
+    CK(cudaMemsetAsync(irounds, 0, (n + 2) * 4, s));
+    CK(cudaMemcpyAsync(ddesc, desc.data(), n * sizeof(BatchDesc), cudaMemcpyHostToDevice, s));
+    BatchArgs ar = a;
+    ar.owner = owner_r;
+    ar.ow_slots = ow_slots;
+    ar.grid_bar = bar;
+    ar.barrier_limit_ns = 20000000000ull;
+    ar.acc_out = acc_out;
+    ar.acc_total = cnt;
+    ar.iv_off = ivoff;
+    ar.acc_cap = acc_cap;
+    ar.owner_words = 4 * keys;
+    ar.n_inst = n;
+    ar.max_rounds = kResidentMaxIntervals;
+    ar.tag0 = tag0;
+    ar.n_active = dround;
+    ar.inst_rounds = irounds;
+    if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
+    const cudaError_t e = launch_batch_resident(ar, grid, threads, smem, s);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+      cudaGetLastError();
+      return false;
+    }
+    CK(e);
+    if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], s));
+    std::vector<uint32_t> hr(n + 2), hs(8);
+    std::vector<uint64_t> acc(2ull * n);
+    uint32_t timed_out = 0;
+    CK(cudaMemcpyAsync(hs.data(), dstats, 8 * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hr.data(), irounds, (n + 2) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(acc.data(), dacc, 16ull * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&timed_out, bar + 2, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint32_t rounds = hr[n];
+    if (rounds) {
+      W.epoch = hr[n + 1];  // the owner-table tag of the last round
+      if (tag0 + rounds - 1 > 63 && W.owner_hi > 4 * keys) {
+        // the tag wrapped in-kernel: words past this batch's cells still hold
+        // tags of the earlier epoch, which later calls would meet again
+        CK(cudaMemsetAsync(owner_r + 4 * keys, 0, (W.owner_hi - 4 * keys) * 4, s));
+        W.owner_hi = 4 * keys;
+      }
+    }
+    if (timed_out) throw Fail{RC_E_TIMEOUT, "a grid barrier of the resident batch timed out"};
+    if (hs[0] & (FLAG_LOG_FULL | FLAG_OW_FULL | FLAG_ERR_FULL))
+      throw Fail{RC_E_CAPACITY, "batch log, own-write table or error log overflowed"};
+    if (hs[0] & FLAG_ACC_FULL) return false;
+    if (rounds == 0) throw Fail{RC_E_CUDA, "the resident batch reported no round"};
+    for (uint32_t k = 0; k < n; k++)
+      if (hr[k] == 0) return false;  // still active at the round cap
+    if (g_prof.on) {
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, g_prof.ev[0], g_prof.ev[1]));
+      g_prof.launches[0]++;
+      g_prof.ms[0] += ms;
+      CK(cudaEventRecord(g_prof.ev[2], s));
+    }
+    // errors by (interval, class, work-item) per instance: the lock-step order
+    std::vector<std::vector<OutRec>> races(n), errors(n);
+    const uint32_t nerr = std::min(hs[1], err_cap);
+    if (nerr) {
+      std::vector<OutRec> ev(nerr);
+      std::vector<uint32_t> ek(nerr);
+      CK(cudaMemcpyAsync(ev.data(), derrs, nerr * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(ek.data(), derrk, nerr * 4, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (uint32_t i = 0; i < nerr; i++) errors[ek[i]].push_back(ev[i]);
+      for (auto &v : errors)
+        std::sort(v.begin(), v.end(), [](const OutRec &x, const OutRec &y) {
+          return x.interval != y.interval ? x.interval < y.interval : x.cls != y.cls ? x.cls < y.cls : x.t_a < y.t_a;
+        });
+    }
+    // the compacted records, classified round by round (commits were made in-kernel)
+    std::vector<unsigned long long> off(rounds + 1);
+    CK(cudaMemcpyAsync(off.data(), ivoff, (rounds + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<OutRec> rr;
+    std::vector<uint32_t> rk;
+    for (uint32_t r = 0; r < rounds; r++) {
+      const uint64_t m = off[r + 1] - off[r];
+      if (!m) continue;
+      rr.clear();
+      rk.clear();
+      uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(m), scan_tmp_words(m)));
+      LogRec *other = W.compact.get<LogRec>(m);
+      LogRec *sorted = sort_log(acc_out + off[r], other, m, bitwidth(maxN), bitwidth(keys) + bitwidth(maxN), tmp, s);
+      Layout none;
+      BatchMap bm{n, dkbase, dkgt, dklt, &rk};
+      classify_run(W, sorted, m, r, none, nullptr, hstats + stat_words, rr, s, &bm);
+      for (size_t i = 0; i < rr.size(); i++) races[rk[i]].push_back(rr[i]);
+    }
+    if (g_prof.on) {
+      CK(cudaEventRecord(g_prof.ev[3], s));
+      CK(cudaEventSynchronize(g_prof.ev[3]));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, g_prof.ev[2], g_prof.ev[3]));
+      g_prof.launches[1]++;
+      g_prof.ms[1] += ms;
+    }
+    for (uint32_t k = 0; k < n; k++) {
+      const BatchItem &it = items[k];
+      out[k] = make_report(races[k], errors[k], hr[k], acc[2 * k], acc[2 * k + 1], acc[2 * k] + acc[2 * k + 1],
+                           it.L.GT, (it.in->flags & RC_WANT_FINAL_MEMORY) ? snap + kbase[k] : nullptr, s);
+    }
+    return true;
+  }
   LogRec *picked = W.logb.get<LogRec>(std::max<uint64_t>(logrecs, 1));
 
   // One round's fixed launch sequence -- stat resets, the persistent
@@ -1670,6 +1813,7 @@ void run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
                          acc[2 * k] + acc[2 * k + 1], it.L.GT,
                          (it.in->flags & RC_WANT_FINAL_MEMORY) ? snap + kbase[k] : nullptr, s);
   }
+  return true;
 }
 
 void check_args(const rc_bytecode *bc, uint32_t groups, uint32_t group_size, const rc_input *in) {
@@ -2021,7 +2165,12 @@ int rc_check_batch(const rc_bytecode *const *bcs, const uint32_t *groups, const 
       }
       if (cells >= (1ull << 31) || bytes > ((uint64_t)200 << 30)) throw Fail{RC_E_CAPACITY, "instance too large for a batch"};
       std::vector<BatchItem> sub(items.begin() + i, items.begin() + j);
-      run_batch(sub, static_cast<cudaStream_t>(inputs[i].cuda_stream), g_strategy >= 3 ? 0 : g_strategy, out + i);
+      // strategies 1 and 2 fix the classification of lock-step rounds, 3 asks
+      // for a resident run (lock-step when it cannot finish); 0 and 4 leave
+      // the choice to the autotuner
+      const cudaStream_t bs = static_cast<cudaStream_t>(inputs[i].cuda_stream);
+      if (g_strategy != 3 || !run_batch(sub, bs, 3, out + i))
+        run_batch(sub, bs, g_strategy == 1 || g_strategy == 2 ? g_strategy : 0, out + i);
       i = j;
     }
     return RC_OK;

@@ -20,6 +20,7 @@ constexpr int kThreads = 256;
 constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;  // 2048
 constexpr int kWarps = kThreads / 32;
+static_assert(kThreads == 256, "thread d owns radix digit d");
 
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_sums, uint32_t &total) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -149,6 +150,8 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const LogRec *i
                                                                  uint32_t gbits, uint32_t shift,
                                                                  const uint32_t *offs, uint32_t ntiles) {
   __shared__ uint32_t cnt[kWarps][256];
+  __shared__ uint32_t dstart[256], gstart[256], ws[kWarps];
+  __shared__ LogRec stage[kTile];  // 32 KB
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int k = threadIdx.x; k < kWarps * 256; k += kThreads) (&cnt[0][0])[k] = 0;
   __syncthreads();
@@ -171,21 +174,29 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const LogRec *i
     __syncwarp();
   }
   __syncthreads();
-  {  // prefix each digit's counts across warps
-    uint32_t run = 0;
-    for (int q = 0; q < kWarps; q++) {
-      const uint32_t t = cnt[q][threadIdx.x];
-      cnt[q][threadIdx.x] = run;
-      run += t;
-    }
+  // prefix each digit's counts across warps (thread d owns digit d), then
+  // over the digits: the tile's records in digit order in shared memory
+  uint32_t run = 0;
+  for (int q = 0; q < kWarps; q++) {
+    const uint32_t t = cnt[q][threadIdx.x];
+    cnt[q][threadIdx.x] = run;
+    run += t;
   }
+  uint32_t tile_n;
+  const uint32_t first = block_excl_scan(run, ws, tile_n);
+  dstart[threadIdx.x] = first;
+  gstart[threadIdx.x] = offs[(uint64_t)threadIdx.x * ntiles + blockIdx.x];
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < kItems; i++) {
-    if (dig[i] < 256u) {
-      const uint64_t pos = (uint64_t)offs[(uint64_t)dig[i] * ntiles + blockIdx.x] + cnt[w][dig[i]] + rank[i];
-      out[pos] = rec[i];
-    }
+  for (int i = 0; i < kItems; i++)
+    if (dig[i] < 256u) stage[dstart[dig[i]] + cnt[w][dig[i]] + rank[i]] = rec[i];
+  __syncthreads();
+  // consecutive threads write consecutive records of one digit's run:
+  // coalesced stores instead of one scattered 16-byte store per record
+  for (uint32_t i = threadIdx.x; i < tile_n; i += kThreads) {
+    const LogRec r = stage[i];
+    const uint32_t d = digit_of(r, gbits, shift);
+    out[(uint64_t)gstart[d] + (i - dstart[d])] = r;
   }
 }
 

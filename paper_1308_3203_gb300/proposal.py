@@ -22,9 +22,14 @@ from . import racecheck as rc
 from . import workloads as W
 
 
-def kernel_candidates(seed: int, n_cand: int = 64):
-    """(bytecode, candidate items) of proposal kernel `seed`."""
-    pk = W.proposal_kernel(seed)
+FAMILIES = {"proposal": W.proposal_kernel, "batch": W.batch_proposal_kernel}
+
+
+def kernel_candidates(seed: int, n_cand: int = 64, family: str = "proposal"):
+    """(bytecode, candidate items) of kernel `seed` of a family: "proposal"
+    (races that depend on the candidate) or "batch" (the config-3 generator's
+    programs)."""
+    pk = FAMILIES[family](seed)
     bc = rc.compile(pk.src)
     items = [(bc, G, S, pk.instance(G, S, i).globals) for (G, S, i) in W.proposal_candidates(seed, n_cand)]
     return bc, items
@@ -39,15 +44,26 @@ def label(items, chunk: int = 4096) -> np.ndarray:
     return np.asarray(out, dtype=np.float32)
 
 
-def dataset(seeds, n_cand: int = 64):
+def dataset(seeds, n_cand: int = 64, family: str = "proposal", chunk_kernels: int = 256):
     """Features [n, 128], labels [n], kernel index [n] for every candidate of
-    the given kernels."""
-    items, kid = [], []
-    for k, s in enumerate(seeds):
-        _, it = kernel_candidates(s, n_cand)
-        items += it
-        kid += [k] * len(it)
-    return rc.features(items), label(items), np.asarray(kid, dtype=np.int64)
+    the given kernels, built `chunk_kernels` kernels at a time (a chunk's
+    inputs are dropped once its features and labels exist, so the host holds
+    one chunk of inputs at most)."""
+    seeds = list(seeds)
+    Xs, ys, kids = [], [], []
+    for c0 in range(0, len(seeds), chunk_kernels):
+        items, kid = [], []
+        for k in range(c0, min(len(seeds), c0 + chunk_kernels)):
+            _, it = kernel_candidates(seeds[k], n_cand, family)
+            items += it
+            kid += [k] * len(it)
+        Xs.append(rc.features(items))
+        ys.append(label(items))
+        kids.append(np.asarray(kid, dtype=np.int64))
+        del items
+    if not Xs:
+        return np.zeros((0, rc.N_FEATURES), np.float32), np.zeros(0, np.float32), np.zeros(0, np.int64)
+    return np.concatenate(Xs), np.concatenate(ys), np.concatenate(kids)
 
 
 def scores(model: rc.MLP, X: np.ndarray) -> np.ndarray:
@@ -74,7 +90,8 @@ def rule_scores(X: np.ndarray) -> np.ndarray:
             + (X[:, F_WW] + X[:, F_RW]) / np.float32(10))
 
 
-def compare_search(model: rc.MLP, seeds, n_cand: int = 64, warmup_seed: int = 10**9) -> dict:
+def compare_search(model: rc.MLP, seeds, n_cand: int = 64, warmup_seed: int = 10**9,
+                   family: str = "proposal") -> dict:
     """Searches of each kernel's candidates on the same GPU with the same
     checker, in this order:
       enum      plain enumeration (index order, rc_search without scores);
@@ -90,13 +107,13 @@ def compare_search(model: rc.MLP, seeds, n_cand: int = 64, warmup_seed: int = 10
     enumeration does.  One kernel outside `seeds` is searched first, every
     way, untimed (thread pool and workspace set-up)."""
     kinds = dict(ranked=(model, False), overlap=(model, True), rule=(None, False), rule_overlap=(None, True))
-    _, items = kernel_candidates(warmup_seed, n_cand)
+    _, items = kernel_candidates(warmup_seed, n_cand, family)
     rc.search(items)
     for m, ov in kinds.values():
         rc.search_ranked(items, m, overlap=ov)
     rows = []
     for s in seeds:
-        _, items = kernel_candidates(s, n_cand)
+        _, items = kernel_candidates(s, n_cand, family)
         enum = rc.search(items)                   # index order = enumeration
         row = dict(seed=s, racy=enum["first"] >= 0, enum_checks=enum["checks"], enum_s=enum["seconds"],
                    enum_first=enum["first"])

@@ -565,6 +565,35 @@ def proposal_kernel(seed: int) -> ProposalKernel:
     return ProposalKernel(f"prop-s{seed}", src, L, LI, V, seed)
 
 
+@dataclasses.dataclass
+class BatchProposalKernel:
+    """A config-3 kernel as a proposal kernel: its program is fixed (drawn
+    for group size 1024, so `if (tid < k)` guards take k in [1, 1024]) and
+    each candidate brings its own launch shape and input."""
+    name: str
+    src: str
+    L: int
+    seed: int
+
+    def instance(self, groups: int, group_size: int, input_seed: int) -> Instance:
+        rng = np.random.default_rng([15, self.seed, input_seed])
+        A = rng.integers(0, 16, size=self.L, dtype=np.int32)
+        return Instance(f"{self.name}-G{groups}-S{group_size}-i{input_seed}", self.src, groups, group_size, [A])
+
+
+def batch_proposal_kernel(seed: int, max_stmts: int = 512) -> BatchProposalKernel:
+    """Proposal kernels from the config-3 generator: the config-1 statement
+    and index mix, 16..max_stmts statements, 0-8 barriers, A of length
+    log-uniform in [1K, 1M]."""
+    rng = np.random.default_rng([14, seed])
+    n_stmts = int(rng.integers(16, max_stmts + 1))
+    n_bar = int(rng.integers(0, 9))
+    L = int(round(math.exp(rng.uniform(math.log(1024), math.log(1 << 20)))))
+    inst = small_kernel(int(rng.integers(1 << 31)), group_size=1024, groups=1, n_stmts=n_stmts,
+                        n_barriers=n_bar, L=L)
+    return BatchProposalKernel(f"bprop-s{seed}", inst.src, L, seed)
+
+
 def proposal_candidates(seed: int, n: int = 64) -> list:
     """The candidate instances of a proposal kernel, in enumeration order:
     (groups, group_size, input_seed) with group size a multiple of 32 in

@@ -27,15 +27,21 @@ def rc():
     return racecheck
 
 
-def test_batch_of_10000_kernels(rc, oracle):
-    """10,000 kernels of uneven shape in one rc_check_batch call: 12 sampled
-    kernels against the oracle record by record, every kernel against the
-    oracle's report by digest."""
+@pytest.mark.parametrize("strategy", [0, 3])
+def test_batch_of_10000_kernels(rc, oracle, strategy):
+    """10,000 kernels of uneven shape in one rc_check_batch call, in
+    lock-step rounds (autotuned) and resident (every round of a sub-batch in
+    one launch): 12 sampled kernels against the oracle record by record,
+    every kernel against the oracle's report by digest."""
     insts = W.batch_kernels(0, 10_000, processes=min(16, os.cpu_count() or 1))
     bcs = [rc.compile(i.src) for i in insts]
+    rc.set_strategy(strategy)
     t0 = time.perf_counter()
-    got = rc.check_batch([(b, i.groups, i.group_size, i.globals) for b, i in zip(bcs, insts)],
-                         want_final=False)
+    try:
+        got = rc.check_batch([(b, i.groups, i.group_size, i.globals) for b, i in zip(bcs, insts)],
+                             want_final=False)
+    finally:
+        rc.set_strategy(0)
     dt = time.perf_counter() - t0
     total = sum(g["n_access"] for g in got)
     print(f"batch: {len(insts)} kernels, {total} accesses in {dt:.2f} s")

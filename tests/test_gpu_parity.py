@@ -218,6 +218,30 @@ def test_batch_mixed_instances(rc, oracle):
     rc.set_strategy(0)
 
 
+def test_resident_batch_is_one_launch(rc, oracle):
+    """Strategy 3 runs every round of a batch in one cooperative launch
+    (barriers up to 8, divergence, errors, crowded cells): one interpreter
+    launch for the call, reports equal to the oracle's, final memories
+    included."""
+    insts = [W.small_kernel(s, n_barriers=b) for s, b in zip(range(40), [0, 1, 2, 3, 5, 8] * 7)]
+    insts += [W.Instance(f"edge{i}", *EDGE[i]) for i in range(len(EDGE))]
+    insts += W.batch_kernels(11, 8)[:4]
+    insts = [i for i in insts if i.n_threads * 300 < 4_000_000]
+    want = [oracle.check(i.src, i.groups, i.group_size, i.globals) for i in insts]
+    bcs = [rc.compile(i.src) for i in insts]
+    rc.set_strategy(3)
+    rc.profile_enable(True)
+    rc.profile_reset()
+    try:
+        got = rc.check_batch([(b, i.groups, i.group_size, i.globals) for b, i in zip(bcs, insts)])
+        assert rc.profile_get(0)["launches"] == 1
+    finally:
+        rc.profile_enable(False)
+        rc.set_strategy(0)
+    for g, w, i in zip(got, want, insts):
+        same(g, w, i.name)
+
+
 def test_autotuner_decides_and_persists(rc, oracle, tmp_path):
     """Strategy 0 alternates both exact strategies per interval until it has
     two samples of each, then keeps the cheaper one and writes it to the
