@@ -234,8 +234,11 @@ __device__ __forceinline__ void batch_task(const BatchArgs &A, uint32_t task, ui
 #undef REG
 }
 
-// The owner table's highest writer of each cell commits its last write:
-// the lanes of one warp task (instance-local work-items).
+// Commits from the own-write tables of one warp task's lanes (instance-local
+// work-items), by the owner table.  Lock-step rounds: only cells with a
+// single writer (the classifier commits the others).  Resident runs: every
+// cell's highest writer commits its last write (the rule the classifier
+// applies), since the classification comes after the launch.
 template <bool kRes>
 __device__ __forceinline__ void commit_task(const BatchArgs &A, uint32_t task, uint32_t tag, uint32_t lane) {
   const uint32_t k = A.task_kernel[task];
@@ -247,7 +250,7 @@ __device__ __forceinline__ void commit_task(const BatchArgs &A, uint32_t task, u
   for (uint32_t q = 0; q < nw; q++) {
     const uint2 e = ld_state<kRes>(A.ow + D.ow_off + (uint64_t)q * D.N + gl);
     const uint2 w = __ldcg(reinterpret_cast<const uint2 *>(A.owner) + 2ull * e.x);
-    if (w.x == hi && w.y == lo) A.snap[e.x] = (int32_t)e.y;
+    if (w.x == hi && (kRes || w.y == lo)) A.snap[e.x] = (int32_t)e.y;
   }
 }
 
@@ -403,7 +406,12 @@ cudaError_t batch_configure() {
                        (const void *)batch_interp_kernel<512>, (const void *)batch_resident_kernel<128>,
                        (const void *)batch_resident_kernel<256>, (const void *)batch_resident_kernel<512>};
   for (const void *f : fns) {
-    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmemPerBlock);
+    // the resident kernels hold a few static bytes (the grid barrier's flag)
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kMaxSmemPerBlock - fa.sharedSizeBytes));
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

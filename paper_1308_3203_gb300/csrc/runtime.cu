@@ -1532,6 +1532,7 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
            batch_smem_bytes(max_regs, ow_slots + 1, threads) <= 200 * 1024 / ctas_per_sm)
       ow_slots++;
     const size_t smem = batch_smem_bytes(max_regs, ow_slots, threads);
+    if (smem + 256 > kMaxSmemPerBlock) return false;  // room for the grid barrier's static bytes
     const int per_sm = batch_resident_blocks_per_sm(threads, smem);
     if (per_sm <= 0) return false;
     const uint32_t warps_per_cta = threads / 32;
