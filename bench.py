@@ -81,8 +81,9 @@ def parse():
     p.add_argument("--groups", type=int, default=0, help="work-groups of the instance (0: its full size)")
     p.add_argument("--strategy", type=int, default=0, help="0 auto, 1 sort, 2 shadow, 3 resident")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--secondary", default="all", choices=["all", "none"],
-                   help="none: only the headline instance (profiling runs)")
+    p.add_argument("--secondary", default="all", choices=["all", "none", "batch", "proposal"],
+                   help="none: only the headline instance; batch / proposal: the headline and that leg "
+                        "alone (profiling runs)")
     p.add_argument("--batch-kernels", type=int, default=10_000,
                    help="size of the batched-checking measurement (0 skips it)")
     p.add_argument("--proposal-kernels", type=int, default=2000,
@@ -574,10 +575,10 @@ def main():
                             "accesses_per_step": lm["rep"]["n_access"],
                             "roofline": roofline(lm, hbm, peak_source)}
         out["small"] = small_leg(rc, W)
-        if args.batch_kernels > 0:
-            out["batch"] = batch_leg(rc, W, args.batch_kernels, rank, world, dist, hbm)
-        if args.proposal_kernels > 0:
-            out["proposal"] = proposal_leg(rc, args.proposal_kernels)
+    if args.secondary in ("all", "batch") and args.batch_kernels > 0:
+        out["batch"] = batch_leg(rc, W, args.batch_kernels, rank, world, dist, hbm)
+    if args.secondary in ("all", "proposal") and args.proposal_kernels > 0:
+        out["proposal"] = proposal_leg(rc, args.proposal_kernels)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload)
         if "small" in out:
