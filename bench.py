@@ -81,9 +81,9 @@ def parse():
     p.add_argument("--groups", type=int, default=0, help="work-groups of the instance (0: its full size)")
     p.add_argument("--strategy", type=int, default=0, help="0 auto, 1 sort, 2 shadow, 3 resident")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--secondary", default="all", choices=["all", "none", "batch", "proposal"],
-                   help="none: only the headline instance; batch / proposal: the headline and that leg "
-                        "alone (profiling runs)")
+    p.add_argument("--secondary", default="all", choices=["all", "none", "small", "batch", "proposal"],
+                   help="none: only the headline instance; small / batch / proposal: the headline and that "
+                        "leg alone (profiling runs)")
     p.add_argument("--batch-kernels", type=int, default=10_000,
                    help="size of the batched-checking measurement (0 skips it)")
     p.add_argument("--proposal-kernels", type=int, default=2000,
@@ -219,10 +219,21 @@ def small_leg(rc, W, n=SMALL_KERNELS):
     for b, i in zip(bcs, insts):
         acc += rc.check(b, i.groups, i.group_size, i.globals, want_final=False)["n_access"]
     dt = time.perf_counter() - t0
+    launches = (rc.kernel_launches() - l0) / n
+    # the same kernels in one rc_check_batch call: the time per kernel when
+    # many small kernels are checked at once
+    items = [(b, i.groups, i.group_size, i.globals) for b, i in zip(bcs, insts)]
+    rc.check_batch(items, want_final=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc.check_batch(items, want_final=False)
+    dtb = time.perf_counter() - t0
     return {"workload": f"{n} small kernels: 1 group x 64 work-items, 1 barrier, 32 statements, global int32[256]",
-            "us_per_check": 1e6 * dt / n, "launches_per_check": (rc.kernel_launches() - l0) / n,
+            "us_per_check": 1e6 * dt / n, "launches_per_check": launches,
             "accesses_per_check": acc / n,
-            "timing": "host wall clock around each rc_check (host inputs, H2D and report included)"}
+            "batched_us_per_kernel": 1e6 * dtb / n,
+            "timing": "host wall clock around each rc_check (host inputs, H2D and report included); "
+                      "batched: around one rc_check_batch of the same kernels"}
 
 
 def small_oracle_ms(n=SMALL_KERNELS):
@@ -574,6 +585,7 @@ def main():
                             "logged_accesses_per_step": lm["rep"]["n_logged"],
                             "accesses_per_step": lm["rep"]["n_access"],
                             "roofline": roofline(lm, hbm, peak_source)}
+    if args.secondary in ("all", "small"):
         out["small"] = small_leg(rc, W)
     if args.secondary in ("all", "batch") and args.batch_kernels > 0:
         out["batch"] = batch_leg(rc, W, args.batch_kernels, rank, world, dist, hbm)
@@ -585,6 +597,7 @@ def main():
             ms = small_oracle_ms()
             out["cpu_baseline"]["small"] = {"ms_per_kernel": ms, "kernels": SMALL_KERNELS, "cores": 1}
             out["small"]["oracle_over_gpu"] = ms * 1e3 / out["small"]["us_per_check"]
+            out["small"]["oracle_over_gpu_batched"] = ms * 1e3 / out["small"]["batched_us_per_kernel"]
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -295,9 +295,13 @@ int rc_jit_stats(uint64_t *compiles, double *seconds);
  * exact strategies on successive intervals (or batch rounds), times each,
  * and keeps the cheaper one after two samples of each; a batch class then
  * times each block shape of the batch interpreter (128, 256, 512 threads per
- * CTA) on two rounds and keeps the fastest.  The log capacity is not a
- * choice: every warp's slice holds the program's static per-interval bound,
- * the least that makes overflow impossible.  Decisions persist in
+ * CTA) on two rounds and keeps the fastest.  A batch class's log capacity:
+ * the first call gives every warp's slice the program's static per-interval
+ * bound (overflow impossible) and records the fullest slice; later calls of
+ * the class allocate twice the largest fill seen (in permille of the bound,
+ * at least 16); a call that overflows that capacity is checked again at the
+ * bound, which the class keeps (the reports are the same either way).
+ * Decisions persist in
  * a JSON file: cache_path, or NULL for the default ($RC_TUNE_CACHE, else
  * $XDG_CACHE_HOME/racecheck_autotune.json, else
  * ~/.cache/racecheck_autotune.json), or "" for no file. */
@@ -309,7 +313,9 @@ int rc_autotune_reset(void);
  * returns 1 (sort), 2 (shadow) or 0 if undecided.  Kind 2: the batch size
  * class's block shape -- threads per CTA of the batch interpreter, 128, 256
  * or 512 (1024 threads per SM in every case), which the autotuner times on
- * two batch rounds each once the strategy is decided -- or 0 if undecided. */
+ * two batch rounds each once the strategy is decided -- or 0 if undecided.
+ * Kind 3: the batch class's log capacity in permille of the static bound
+ * (1..1000), or 0 if no call of the class has finished. */
 int rc_autotune_lookup(int kind, uint64_t a, uint64_t b);
 
 /* Kernel timing: when enabled, the library brackets its work with CUDA
@@ -495,10 +501,11 @@ int rc_mlp_create(uint64_t seed, uint32_t capacity, rc_mlp **out);
 void rc_mlp_free(rc_mlp *m);
 int rc_mlp_get_params(const rc_mlp *m, float *host_out);
 /* Every product (forward, data and weight gradients) on the tcgen05 kernels
- * with TMEM accumulators (backend 1, the default) or on the mma.sync
- * m16n8k16 kernels (backend 0).  rc_mlp_backend_error sets *flag nonzero if
- * a tcgen05 launch gave up waiting for its MMAs (its outputs are then not
- * valid). */
+ * with TMEM accumulators -- the three forward layers in one launch (backend
+ * 1, the default) or one launch per layer (backend 2, the same values) -- or
+ * on the mma.sync m16n8k16 kernels (backend 0).  rc_mlp_backend_error sets
+ * *flag nonzero if a tcgen05 launch gave up waiting for its MMAs (its
+ * outputs are then not valid). */
 int rc_mlp_set_backend(rc_mlp *m, int backend);
 int rc_mlp_backend_error(rc_mlp *m, uint32_t *flag);
 int rc_mlp_set_params(rc_mlp *m, const float *host_in);

@@ -41,21 +41,23 @@ __device__ __forceinline__ T ld_state(const T *p) {
 
 // One warp task: one interval of 32 work-items of instance task_kernel[task]
 // (rf/owk/owv: this CTA's shared register file and own-write slots).
+// Returns how full the task's log slice got, in permille of its capacity
+// (warp-uniform; 0 for a task with nothing to run).
 template <uint32_t kBatchThreads, bool kRes>
-__device__ __forceinline__ void batch_task(const BatchArgs &A, uint32_t task, uint32_t interval, uint32_t tag,
-                                           uint32_t *owner, int32_t *rf, uint32_t *owk, int32_t *owv) {
+__device__ __forceinline__ uint32_t batch_task(const BatchArgs &A, uint32_t task, uint32_t interval, uint32_t tag,
+                                               uint32_t *owner, int32_t *rf, uint32_t *owk, int32_t *owv) {
   const uint32_t RS = kBatchThreads;  // register-file stride
   const uint32_t t = threadIdx.x, lane = t & 31u, lane_lt = (1u << lane) - 1u;
   const uint32_t slots = A.ow_slots;
 #define REG(i) rf[(uint32_t)(i) * RS + t]
   const uint32_t k = A.task_kernel[task];
   const BatchDesc D = A.desc[k];
-  if (!ld_state<kRes>(&A.desc[k].active)) return;  // finished instance: nothing to run, its slices stay unread
+  if (!ld_state<kRes>(&A.desc[k].active)) return 0;  // finished instance: nothing to run, its slices stay unread
   const uint32_t lw = task - D.task_off;                 // warp of the instance
   const uint32_t gl = lw * 32 + lane;                    // instance-local work-item id
   const bool exists = (uint64_t)gl < D.N;
   const uint32_t lanes = __ballot_sync(0xFFFFFFFFu, exists);
-  if (!exists) return;
+  if (!exists) return 0;
   const uint32_t S = D.S, tid = gl % S, wg = gl / S;
   const uint32_t lbase = (uint32_t)D.key_base + D.GT + wg * D.LT;
   const uint4 *code = reinterpret_cast<const uint4 *>(A.code) + D.code_off;
@@ -232,6 +234,12 @@ __device__ __forceinline__ void batch_task(const BatchArgs &A, uint32_t task, ui
     A.warp_count[task] = wfill < D.slice ? wfill : (uint32_t)D.slice;
   }
 #undef REG
+  return (uint32_t)(((wfill < D.slice ? wfill : D.slice) * 1000ull + D.slice - 1) / D.slice);
+}
+
+// the largest slice fill of this warp's tasks, one atomic per warp
+__device__ __forceinline__ void report_fill(const BatchArgs &A, uint32_t fill_pm) {
+  if ((threadIdx.x & 31u) == 0 && fill_pm) atomicMax(A.fill_max, fill_pm);
 }
 
 // Commits from the own-write tables of one warp task's lanes (instance-local
@@ -265,13 +273,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1024 / kBatchThreads) batch_int
   // round state lives in device memory so one captured launch serves every round
   const uint32_t interval = A.round[0], tag = A.round[1];
   uint32_t *const owner = A.round[2] ? A.owner : nullptr;
+  uint32_t fill = 0;
   for (;;) {
     uint32_t task = 0;
     if ((threadIdx.x & 31u) == 0) task = atomicAdd(A.next_task, 1u);
     task = __shfl_sync(0xFFFFFFFFu, task, 0);
     if (task >= A.n_tasks) break;
-    batch_task<kBatchThreads, false>(A, task, interval, tag, owner, rf, owk, owv);
+    fill = max(fill, batch_task<kBatchThreads, false>(A, task, interval, tag, owner, rf, owk, owv));
   }
+  report_fill(A, fill);
 }
 
 // Resident run: every round in one launch.  Round r (tag0 + r as the owner
@@ -295,6 +305,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1024 / kBatchThreads) batch_res
   const uint32_t warps = gridDim.x * (kBatchThreads / 32), gwarp = blockIdx.x * (kBatchThreads / 32) + (threadIdx.x >> 5);
   const uint32_t threads = gridDim.x * kBatchThreads, gthread = blockIdx.x * kBatchThreads + threadIdx.x;
   uint32_t tag = A.tag0;
+  uint32_t fill = 0;
   for (uint32_t r = 0;; r++) {
     // ---- 1. the round's warp tasks
     for (;;) {
@@ -302,7 +313,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1024 / kBatchThreads) batch_res
       if (lane == 0) task = atomicAdd(A.next_task + (r & 1u), 1u);
       task = __shfl_sync(0xFFFFFFFFu, task, 0);
       if (task >= A.n_tasks) break;
-      batch_task<kBatchThreads, true>(A, task, r, tag, A.owner, rf, owk, owv);
+      fill = max(fill, batch_task<kBatchThreads, true>(A, task, r, tag, A.owner, rf, owk, owv));
     }
     if (!grid_sync(A.grid_bar, gridDim.x, A.barrier_limit_ns)) return;
     // ---- 2. commit and compaction (no task of this round is running)
@@ -362,6 +373,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1024 / kBatchThreads) batch_res
         A.inst_rounds[A.n_inst] = r + 1;
         A.inst_rounds[A.n_inst + 1] = tag;
       }
+      report_fill(A, fill);
       return;
     }
     if (tag == 63) {  // the 6-bit tag wraps: clear the batch's owner words first

@@ -141,6 +141,7 @@ struct BatchArgs {
   uint32_t n_inst, max_rounds, tag0;
   uint32_t *n_active;           // [2] instances active in the next round (by parity; zero before the launch)
   uint32_t *inst_rounds;        // [n_inst] intervals each instance ran; [n_inst] rounds, [n_inst + 1] last tag
+  uint32_t *fill_max;           // largest fill of a warp task's log slice, in permille of its capacity
 };
 
 // block shapes of the batch interpreter: 128, 256 or 512 threads per CTA

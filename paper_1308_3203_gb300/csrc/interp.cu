@@ -190,6 +190,19 @@ __device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t *sh, uint
   return r;
 }
 
+// The warp whose log slice holds record i of the interval, the slices laid
+// end to end (woff: each warp's first record; a warp without records has
+// the next one's offset, so the largest w with woff[w] <= i is the holder).
+__device__ __forceinline__ uint32_t slice_of(const uint32_t *woff, uint32_t nw, uint32_t i) {
+  uint32_t lo = 0, hi = nw;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (woff[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 template <bool kConst>
 __global__ void __launch_bounds__(1024, 1) small_check_kernel(SmallArgs P) {
   const InterpArgs &A = P.A;
@@ -331,13 +344,12 @@ __global__ void __launch_bounds__(1024, 1) small_check_kernel(SmallArgs P) {
       // work-item's last write by sequence number, not by position)
       for (uint32_t i = t; i < P.bins; i += T) cbin[i] = 0;
       __syncthreads();
-      {
-        const uint32_t n = s_fill[warp];
-        const uint4 *src = logp + (uint64_t)warp * A.warp_slice;
-        for (uint32_t j = t & 31u; j < n; j += 32) {
-          const uint4 r = src[j];
-          atomicAdd(&cbin[r.x * RS + (r.y & 0x7FFFFFFFu)], 1u);
-        }
+      // every thread takes records of the interval (the slices of the few
+      // warps that ran work-items, end to end), not only those warps
+      for (uint32_t i = t; i < M; i += T) {
+        const uint32_t w = slice_of(s_woff, nwarps, i);
+        const uint4 r = logp[(uint64_t)w * A.warp_slice + (i - s_woff[w])];
+        atomicAdd(&cbin[r.x * RS + (r.y & 0x7FFFFFFFu)], 1u);
       }
       __syncthreads();
       {
@@ -353,25 +365,21 @@ __global__ void __launch_bounds__(1024, 1) small_check_kernel(SmallArgs P) {
         }
       }
       __syncthreads();
-      {
-        const uint32_t n = s_fill[warp];
-        const uint4 *src = logp + (uint64_t)warp * A.warp_slice;
-        for (uint32_t j = t & 31u; j < n; j += 32) {
-          const uint4 r = src[j];
-          reinterpret_cast<uint4 *>(sorted)[atomicAdd(&cbin[r.x * RS + (r.y & 0x7FFFFFFFu)], 1u)] = r;
-        }
+      for (uint32_t i = t; i < M; i += T) {
+        const uint32_t w = slice_of(s_woff, nwarps, i);
+        const uint4 r = logp[(uint64_t)w * A.warp_slice + (i - s_woff[w])];
+        reinterpret_cast<uint4 *>(sorted)[atomicAdd(&cbin[r.x * RS + (r.y & 0x7FFFFFFFu)], 1u)] = r;
       }
       __syncthreads();
     } else {
       uint32_t P2 = T;  // sort length: a power of two, at least one key per thread
       while (P2 < M) P2 <<= 1;
       {  // key: cell (32 bits), work-item (10), warp (5), slot in the warp's slice (12)
-        const uint32_t n = s_fill[warp], base = s_woff[warp];
-        const uint4 *src = logp + (uint64_t)warp * A.warp_slice;
-        for (uint32_t j = t & 31u; j < n; j += 32) {
-          const uint4 r = src[j];
-          keys[base + j] = ((unsigned long long)r.x << 27) | ((unsigned long long)(r.y & 0x3FFu) << 17) |
-                           ((unsigned long long)warp << 12) | j;
+        for (uint32_t i = t; i < M; i += T) {
+          const uint32_t w = slice_of(s_woff, nwarps, i), j = i - s_woff[w];
+          const uint4 r = logp[(uint64_t)w * A.warp_slice + j];
+          keys[i] = ((unsigned long long)r.x << 27) | ((unsigned long long)(r.y & 0x3FFu) << 17) |
+                    ((unsigned long long)w << 12) | j;
         }
         for (uint32_t j = M + t; j < P2; j += T) keys[j] = ~0ull;
       }

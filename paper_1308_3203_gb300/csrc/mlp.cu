@@ -413,6 +413,120 @@ __device__ __forceinline__ void tc_end(uint32_t tmem) {
   if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTcN));
 }
 
+// ---- the three hidden layers in one launch: one CTA per 128 rows keeps
+// the rows' activations in shared memory from layer to layer.  Per layer the
+// CTA stages the whole weight matrix (256 x K, K-major core matrices), one
+// thread issues K/16 MMAs of 128 x 256 x 16 into 256 TMEM columns, and after
+// the commit each warp reads its 32 rows back, adds the bias, applies the
+// ReLU, rounds to BF16 and writes the result both to H_l in global memory
+// (the backward pass reads it) and, in the operand layout, over the
+// activation tile that the next layer's MMAs read.  Each element is the
+// same FP32 sum of the same BF16 products as in tc_fwd_kernel, rounded at
+// the same point.
+constexpr int kTcFwd3N = 256;
+constexpr size_t kTcFwd3Smem = (size_t)kTcRows * kHid * 2 + (size_t)kTcFwd3N * kHid * 2 + 16;
+
+__global__ void __launch_bounds__(kTcThreads) tc_fwd3_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ Wb,
+                                                             const float *__restrict__ P, bf16 *__restrict__ H1,
+                                                             bf16 *__restrict__ H2, bf16 *__restrict__ H3, int M,
+                                                             uint32_t *err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char *As = tsm, *Bs = tsm + (size_t)kTcRows * kHid * 2;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(tsm + kTcFwd3Smem - 16);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, m0 = blockIdx.x * kTcRows;
+  const int r = warp * 32 + lane;  // accumulator row = TMEM lane
+  // layer 1's operand: the rows of X (K = 128), rows past M zero-filled
+  {
+    constexpr int KC = kIn / 8;
+    for (int i = t; i < kTcRows * KC; i += kTcThreads) {
+      const int rr = i / KC, c = i % KC;
+      const bool in = m0 + rr < M;
+      cp_async16(As + ((rr >> 3) * KC + c) * 128 + (rr & 7) * 16, X + (size_t)(in ? m0 + rr : 0) * kIn + c * 8, in);
+    }
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "n"(kTcFwd3N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  bool ok = true;
+  uint32_t tmem = 0;
+#pragma unroll 1
+  for (int l = 0; l < 3 && ok; l++) {
+    const int K = l == 0 ? kIn : kHid, KC = K / 8;
+    const bf16 *W = Wb + (l == 0 ? oW1 : l == 1 ? oW2 : oW3);
+    const float *bias = P + (l == 0 ? ob1 : l == 1 ? ob2 : ob3);
+    bf16 *H = l == 0 ? H1 : l == 1 ? H2 : H3;
+    for (int i = t; i < kTcFwd3N * KC; i += kTcThreads) {
+      const int n = i / KC, c = i % KC;
+      cp_async16(Bs + ((n >> 3) * KC + c) * 128 + (n & 7) * 16, W + (size_t)n * K + c * 8, true);
+    }
+    cp_async_wait_all();
+    // the staged operands (and the previous layer's activations written by
+    // the epilogue) visible to the tensor cores; the previous layer's TMEM
+    // reads finished before its accumulator is overwritten
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem = *tslot;
+    if (t == 0) {
+      const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+#pragma unroll 1
+      for (int k = 0; k < K / 16; k++) {
+        const uint64_t ad = tc_desc(a0 + k * 256, 128, KC * 128), bd = tc_desc(b0 + k * 256, 128, KC * 128);
+        const uint32_t acc = k > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(tc_idesc(kTcFwd3N)), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(mbar)));
+    }
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < kTcWaitLimit && !done; it++)
+      asm volatile(
+          "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
+          : "=r"(done)
+          : "r"(smem_addr(mbar)), "r"((uint32_t)(l & 1)));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(done) != 0;
+    if (!ok) break;
+    // epilogue: H_l rows, and the next layer's operand over the activation tile
+    constexpr int KCn = kHid / 8;
+#pragma unroll 1
+    for (int j = 0; j < kTcFwd3N / 32; j++) {
+      uint32_t v[32];
+      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32), v);
+      __align__(16) bf16 o[32];
+#pragma unroll
+      for (int q = 0; q < 32; q++)
+        o[q] = __float2bfloat16_rn(fmaxf(__uint_as_float(v[q]) + bias[j * 32 + q], 0.0f));
+      if (m0 + r < M) {
+        uint4 *dst = reinterpret_cast<uint4 *>(H + (size_t)(m0 + r) * kHid + j * 32);
+#pragma unroll
+        for (int q = 0; q < 4; q++) dst[q] = reinterpret_cast<const uint4 *>(o)[q];
+      }
+      if (l < 2) {
+#pragma unroll
+        for (int q = 0; q < 4; q++)  // 8 values along K = one 16-byte core-matrix row
+          *reinterpret_cast<uint4 *>(As + ((r >> 3) * KCn + j * 4 + q) * 128 + (r & 7) * 16) =
+              reinterpret_cast<const uint4 *>(o)[q];
+      }
+    }
+  }
+  if (!ok && t == 0) atomicOr(err, 1u);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "n"(kTcFwd3N));
+}
+
 constexpr size_t kTcBwdSmem = (size_t)kTcRows * kTcK * 2 + (size_t)kTcN * kTcK * 2 + 16;
 
 // dz_prev[M][256] = (dz[M][256] * W[256][256]) where h[M][256] > 0, as BF16
@@ -616,7 +730,7 @@ unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // ---------------------------------------------------------------- the network object
 struct rc_mlp {
   uint32_t cap = 0;  // rows per pass
-  int backend = 1;   // forward products: 0 mma.sync, 1 tcgen05
+  int backend = 1;   // products: 0 mma.sync, 1 tcgen05 (forward layers fused), 2 tcgen05 (a launch per layer)
   uint32_t *tc_err = nullptr;  // device flag: a tcgen05 CTA gave up waiting for its MMAs
   float *P = nullptr, *G = nullptr, *Mm = nullptr, *Vv = nullptr;
   rc::bf16 *Pb = nullptr;
@@ -645,7 +759,13 @@ int wgrad_splits(int rows) { return std::max(1, std::min(64, (rows + 511) / 512)
 // forward pass of rows [0, n) of the staged batch m->Xb (n <= cap)
 void forward(rc_mlp *m, int n, cudaStream_t s) {
   const bf16 *Wb = m->Pb;
-  if (m->backend == 1) {
+  if (m->backend == 1) {  // the three layers in one launch
+    count_launch();
+    tc_fwd3_kernel<<<(unsigned)((n + kTcRows - 1) / kTcRows), kTcThreads, kTcFwd3Smem, s>>>(
+        m->Xb, Wb, m->P, m->H1, m->H2, m->H3, n, m->tc_err);
+    return;
+  }
+  if (m->backend == 2) {  // one launch per layer
     const dim3 grid((unsigned)((n + kTcRows - 1) / kTcRows), kHid / kTcN);
     count_launch();
     tc_fwd_kernel<kIn><<<grid, kTcThreads, tc_smem<kIn>(), s>>>(m->Xb, Wb + oW1, m->P + ob1, m->H1, n, m->tc_err);
@@ -673,7 +793,7 @@ void forward(rc_mlp *m, int n, cudaStream_t s) {
 // dW = dz^T h (+ split-K partials), db = column sums of dz
 void weight_grads(rc_mlp *m, const bf16 *dz, const bf16 *h, int kin, int n, size_t oW, size_t ob, cudaStream_t s) {
   const int splits = wgrad_splits(n);
-  if (m->backend == 1) {
+  if (m->backend != 0) {
     const int kchunk = (((n + splits - 1) / splits) + 15) / 16 * 16;
     const int zs = (n + kchunk - 1) / kchunk;
     count_launch();
@@ -733,14 +853,14 @@ void backward(rc_mlp *m, int n, cudaStream_t s) {
   g.A = m->D2, g.B = m->Pb + oW3, g.mask = m->H2, g.out = m->D1;
   const dim3 tgrid((unsigned)((n + kTcRows - 1) / kTcRows), kHid / kTcN);
   count_launch();
-  if (m->backend == 1)
+  if (m->backend != 0)
     tc_dgrad_kernel<<<tgrid, kTcThreads, kTcBwdSmem, s>>>(m->D2, m->Pb + oW3, m->H2, m->D1, n, m->tc_err);
   else
     gemm_kernel<DGRAD><<<dim3(nblk(n, BM), kHid / BN), kGemmThreads, 0, s>>>(g);
   weight_grads(m, m->D1, m->H1, kHid, n, oW2, ob2, s);
   g.A = m->D1, g.B = m->Pb + oW2, g.mask = m->H1, g.out = m->D2;  // dz1 into D2
   count_launch();
-  if (m->backend == 1)
+  if (m->backend != 0)
     tc_dgrad_kernel<<<tgrid, kTcThreads, kTcBwdSmem, s>>>(m->D1, m->Pb + oW2, m->H1, m->D2, n, m->tc_err);
   else
     gemm_kernel<DGRAD><<<dim3(nblk(n, BM), kHid / BN), kGemmThreads, 0, s>>>(g);
@@ -832,6 +952,7 @@ int rc_mlp_create(uint64_t seed, uint32_t capacity, rc_mlp **out) {
     MK(cudaFuncSetAttribute(tc_fwd_kernel<kHid>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<kHid>()));
     MK(cudaFuncSetAttribute(tc_dgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcBwdSmem));
     MK(cudaFuncSetAttribute(tc_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcBwdSmem));
+    MK(cudaFuncSetAttribute(tc_fwd3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcFwd3Smem));
     // He-uniform weights for the ReLU layers, zero biases
     std::vector<float> p(kParams, 0.0f);
     uint64_t st = seed;
@@ -869,7 +990,7 @@ void rc_mlp_free(rc_mlp *m) {
 }
 
 int rc_mlp_set_backend(rc_mlp *m, int backend) {
-  if (!m || backend < 0 || backend > 1) return RC_E_INVALID;
+  if (!m || backend < 0 || backend > 2) return RC_E_INVALID;
   m->backend = backend;
   return RC_OK;
 }

@@ -156,6 +156,12 @@ void prof_events() {
 // an undecided class simply alternates them on successive intervals (or
 // batch rounds), timing each interval per million accesses; after two
 // samples of each the cheaper one is kept and written to a JSON cache.
+// Batches also get a block shape (timed like the strategy) and a log
+// capacity: the warp slices start at the compiler's static bound per
+// interval (always enough), the fullest slice of each call is recorded, and
+// later calls of the class allocate twice the largest fill seen; a call
+// whose slices overflow that is checked again at the static bound, which
+// the class then keeps.
 struct Tuner {
   // block shapes of the batch interpreter (threads per CTA)
   static constexpr uint32_t kShapes[3] = {128, 256, 512};
@@ -166,6 +172,8 @@ struct Tuner {
     uint32_t threads = 0;  // decided block shape (batches), 0 = not yet
     double scost[3] = {0, 0, 0};
     int sn[3] = {0, 0, 0};
+    uint32_t log_pm = 0;   // batches: log capacity in permille of the static bound, 0 = not yet
+    uint32_t fill_pm = 0;  // the fullest slice seen, in permille of the static bound
   };
   bool loaded = false;
   bool persist = true;
@@ -207,6 +215,11 @@ struct Tuner {
         const uint32_t v = (uint32_t)std::atoi(text.c_str() + th + 10);
         if (v == 128 || v == 256 || v == 512) entries[key].threads = v;
       }
+      const size_t lp = text.find("\"log_permille\":", q);
+      if (lp != std::string::npos && lp < close) {
+        const int v = std::atoi(text.c_str() + lp + 15);
+        if (v >= 1 && v <= 1000) entries[key].log_pm = (uint32_t)v;
+      }
     }
   }
   void save() {
@@ -230,6 +243,7 @@ struct Tuner {
                    first ? "" : ",", kv.first.c_str(), e.best, e.n[1] ? e.cost[1] / e.n[1] : 0.0,
                    e.n[2] ? e.cost[2] / e.n[2] : 0.0);
       if (e.threads) std::fprintf(f, ", \"threads\": %u", e.threads);
+      if (e.log_pm) std::fprintf(f, ", \"log_permille\": %u, \"fill_permille\": %u", e.log_pm, e.fill_pm);
       std::fprintf(f, "}");
       first = false;
     }
@@ -276,6 +290,29 @@ struct Tuner {
       e.threads = kShapes[b];
       save();
     }
+  }
+  // batches: log capacity, permille of the static bound
+  uint32_t log_permille(const std::string &key) {
+    load();
+    const uint32_t v = entries[key].log_pm;
+    return v ? v : 1000u;
+  }
+  // the fullest slice of a completed call (permille of the static bound)
+  void record_fill(const std::string &key, uint32_t fill_pm) {
+    Entry &e = entries[key];
+    e.fill_pm = std::max(e.fill_pm, std::min(fill_pm, 1000u));
+    const uint32_t want = std::min<uint32_t>(1000u, std::max<uint32_t>(2 * e.fill_pm, 16u));
+    if (e.log_pm == 0 || want > e.log_pm) {
+      e.log_pm = want;
+      save();
+    }
+  }
+  // a call overflowed its slices at the tuned capacity: the static bound from now on
+  void record_overflow(const std::string &key) {
+    Entry &e = entries[key];
+    e.log_pm = 1000;
+    e.fill_pm = 1000;
+    save();
   }
   void record(const std::string &key, int strategy, double ms, uint64_t accesses) {
     Entry &e = entries[key];
@@ -1398,6 +1435,15 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   uint64_t keys = 0, regs = 0, state = 0, owe = 0, logrecs = 0;
   uint32_t stops = 0, max_regs = kBuiltinRegs, max_writes = 1;
   uint64_t maxN = 1;
+  // the size class (warp tasks and the static bound per task) and its log
+  // capacity: slices of 32 x ceil(bound x log_pm / 1000) records
+  uint64_t tasks_all = 0, bound_recs = 0;
+  for (const BatchItem &it : items) {
+    tasks_all += it.warps;
+    bound_recs += it.warps * 32 * it.B;
+  }
+  const std::string tkey = batch_key(tasks_all, bound_recs / std::max<uint64_t>(tasks_all, 1) / 32);
+  const uint32_t log_pm = g_tuner.log_permille(tkey);
   for (uint32_t k = 0; k < n; k++) {
     const BatchItem &it = items[k];
     BatchDesc &D = desc[k];
@@ -1420,7 +1466,7 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
     D.reg_off = regs;
     D.state_off = state;
     D.ow_off = owe;
-    D.slice = 32 * it.B;
+    D.slice = 32 * std::max<uint64_t>(1, (it.B * log_pm + 999) / 1000);
     D.slice_off = logrecs;
     kbase[k] = keys;
     kGT[k] = D.GT;
@@ -1484,7 +1530,6 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   unsigned long long *dacc = reinterpret_cast<unsigned long long *>(W.shared_acc.get<uint64_t>(2ull * n));
   CK(cudaMemsetAsync(dacc, 0, 16ull * n, s));
   uint32_t *owner = strategy != 1 ? shadow_table(W, keys, s) : W.owner.get<uint32_t>(4);
-  const std::string tkey = batch_key(n_tasks, logrecs / std::max<uint64_t>(n_tasks, 1) / 32);
   if (!strategy) tuner_events();
   // block shapes: CTAs of 128, 256 or 512 threads, 1024 threads per SM; own-write
   // slots in shared memory (up to 8) within the SM's 200 KB shared among them
@@ -1522,6 +1567,7 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   a.acc = dacc;
   a.flags = dstats;
   a.owner = owner;
+  a.fill_max = dstats + 6;
   unsigned long long *cnt = reinterpret_cast<unsigned long long *>(dstats + 4);
   if (strategy == 3) {
     // ---- resident run: every round in one cooperative launch
@@ -1541,7 +1587,7 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
     // compacted records of every round: twice one round's slice capacity, at
     // least 4 Mi records, at most 2^31 (32 GiB); a run that needs more starts
     // over in lock-step
-    const uint64_t acc_cap = std::min<uint64_t>(std::max<uint64_t>(2 * logrecs, 1ull << 22), 1ull << 31);
+    const uint64_t acc_cap = std::min<uint64_t>(std::max<uint64_t>(2 * bound_recs, 1ull << 22), 1ull << 31);
     LogRec *acc_out = W.logb.get<LogRec>(acc_cap);
     uint32_t *owner_r = owner;  // the shadow table (strategy 3 is not the sort path)
     const uint32_t tag0 = shadow_next_tag(W, s, 4 * keys);
@@ -1598,12 +1644,17 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
       }
     }
     if (timed_out) throw Fail{RC_E_TIMEOUT, "a grid barrier of the resident batch timed out"};
+    if ((hs[0] & FLAG_LOG_FULL) && log_pm < 1000) {  // the tuned log capacity was too small
+      g_tuner.record_overflow(tkey);
+      return false;
+    }
     if (hs[0] & (FLAG_LOG_FULL | FLAG_OW_FULL | FLAG_ERR_FULL))
       throw Fail{RC_E_CAPACITY, "batch log, own-write table or error log overflowed"};
     if (hs[0] & FLAG_ACC_FULL) return false;
     if (rounds == 0) throw Fail{RC_E_CUDA, "the resident batch reported no round"};
     for (uint32_t k = 0; k < n; k++)
       if (hr[k] == 0) return false;  // still active at the round cap
+    g_tuner.record_fill(tkey, (uint32_t)(((uint64_t)hs[6] * log_pm + 999) / 1000));
     if (g_prof.on) {
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, g_prof.ev[0], g_prof.ev[1]));
@@ -1714,7 +1765,7 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
 
   std::vector<std::vector<OutRec>> races(n), errors(n);
   std::vector<uint32_t> n_intervals(n, 0);
-  uint32_t active = n;
+  uint32_t active = n, fill_seen = 0;
   std::vector<uint64_t> acc(2ull * n), prev(2ull * n, 0);
   std::vector<OutRec> rr;
   std::vector<uint32_t> rk;
@@ -1738,7 +1789,12 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
     CK(cudaMemcpyAsync(hstats, dstats, stat_words * 4, cudaMemcpyDeviceToHost, bs));
     CK(cudaMemcpyAsync(acc.data(), dacc, 16ull * n, cudaMemcpyDeviceToHost, bs));
     CK(cudaStreamSynchronize(bs));
+    if ((hstats[0] & FLAG_LOG_FULL) && log_pm < 1000) {  // the tuned log capacity was too small
+      g_tuner.record_overflow(tkey);
+      return false;
+    }
     if (hstats[0]) throw Fail{RC_E_CAPACITY, "batch log, own-write table or error log overflowed"};
+    fill_seen = std::max(fill_seen, hstats[6]);
     if (g_prof.on) {
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, g_prof.ev[0], g_prof.ev[1]));
@@ -1806,6 +1862,7 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
       }
     }
   }
+  g_tuner.record_fill(tkey, (uint32_t)(((uint64_t)fill_seen * log_pm + 999) / 1000));
   s = bs;  // final memories are read on the batch stream
   for (uint32_t k = 0; k < n; k++) {
     const BatchItem &it = items[k];
@@ -2170,8 +2227,12 @@ int rc_check_batch(const rc_bytecode *const *bcs, const uint32_t *groups, const 
       // for a resident run (lock-step when it cannot finish); 0 and 4 leave
       // the choice to the autotuner
       const cudaStream_t bs = static_cast<cudaStream_t>(inputs[i].cuda_stream);
-      if (g_strategy != 3 || !run_batch(sub, bs, 3, out + i))
-        run_batch(sub, bs, g_strategy == 1 || g_strategy == 2 ? g_strategy : 0, out + i);
+      const int lockstep = g_strategy == 1 || g_strategy == 2 ? g_strategy : 0;
+      bool done = g_strategy == 3 && run_batch(sub, bs, 3, out + i);
+      // a run whose slices overflowed the tuned log capacity returns false and
+      // goes again at the static bound, which the class keeps from then on
+      for (int attempt = 0; !done && attempt < 2; attempt++) done = run_batch(sub, bs, lockstep, out + i);
+      if (!done) throw Fail{RC_E_CAPACITY, "batch log overflowed at its static bound"};
       i = j;
     }
     return RC_OK;
@@ -2333,11 +2394,11 @@ int rc_autotune_reset(void) {
 int rc_autotune_lookup(int kind, uint64_t a, uint64_t b) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_tuner.load();
-  if (kind < 0 || kind > 2) return 0;
+  if (kind < 0 || kind > 3) return 0;
   const std::string key = kind == 0 ? single_key(a, b) : batch_key(a, b);
   auto it = g_tuner.entries.find(key);
   if (it == g_tuner.entries.end()) return 0;
-  return kind == 2 ? (int)it->second.threads : it->second.best;
+  return kind == 3 ? (int)it->second.log_pm : kind == 2 ? (int)it->second.threads : it->second.best;
 }
 
 int rc_profile_enable(int on) {

@@ -444,7 +444,9 @@ def autotune_reset() -> None:
 
 
 def autotune_lookup(kind: int, a: int, b: int) -> int:
-    """Decided strategy for a size class (0 undecided, 1 sort, 2 shadow)."""
+    """The autotuner's decision for a size class (kind 0 single, 1 batch:
+    strategy 1 sort / 2 shadow; kind 2 batch block shape in threads per CTA;
+    kind 3 batch log capacity in permille of the static bound; 0 undecided)."""
     return int(load().rc_autotune_lookup(kind, a, b))
 
 
@@ -668,7 +670,8 @@ class MLP:
         return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
     def set_backend(self, backend: int) -> None:
-        """Every product on tcgen05 with TMEM accumulators (1, the default) or on mma.sync (0)."""
+        """Every product on tcgen05 with TMEM accumulators -- forward layers in
+        one launch (1, the default) or one per layer (2) -- or on mma.sync (0)."""
         rc = load().rc_mlp_set_backend(self._h, backend)
         if rc:
             _raise(rc)

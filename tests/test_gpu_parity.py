@@ -281,6 +281,42 @@ def test_autotuner_decides_and_persists(rc, oracle, tmp_path):
     threads = rc.autotune_lookup(2, tasks, bound)
     assert threads in (128, 256, 512)
     assert '"threads": %d' % threads in open(cache).read()
+    # the log capacity: twice the fullest slice seen, in permille of the bound
+    log_pm = rc.autotune_lookup(3, tasks, bound)
+    assert 16 <= log_pm <= 1000
+    assert '"log_permille": %d' % log_pm in open(cache).read()
+    rc.autotune_config("")
+
+
+def test_batch_log_capacity_overflow_recovers(rc, oracle, tmp_path):
+    """A batch class whose tuned log capacity is too small (one record per
+    work-item and interval, planted in the cache file) overflows its slices:
+    the call is checked again at the static bound, the reports equal the
+    oracle's, and the class keeps the bound (1000 permille) from then on.
+    Both schedules: lock-step rounds and resident."""
+    insts = [W.small_kernel(s, n_barriers=2) for s in range(300, 312)]
+    wants = [oracle.check(i.src, i.groups, i.group_size, i.globals) for i in insts]
+    bcs = [rc.compile(i.src) for i in insts]
+    tasks = sum((i.n_threads + 31) // 32 for i in insts)
+    bound = sum((i.n_threads + 31) // 32 * max(b.info()["max_access_per_interval"], 1)
+                for i, b in zip(insts, bcs)) // tasks
+    key = "batch:T%d:B%d" % (tasks.bit_length(), bound.bit_length())
+    for strategy in (0, 3):
+        cache = tmp_path / f"tune{strategy}.json"
+        cache.write_text('{"racecheck_autotune": 1, "entries": {"%s": {"best": 2, "threads": 256, '
+                         '"log_permille": 1}}}' % key)
+        rc.autotune_reset()
+        rc.autotune_config(str(cache))
+        assert rc.autotune_lookup(3, tasks, bound) == 1
+        rc.set_strategy(strategy)
+        try:
+            got = rc.check_batch([(b, i.groups, i.group_size, i.globals) for b, i in zip(bcs, insts)])
+        finally:
+            rc.set_strategy(0)
+        for g, w, i in zip(got, wants, insts):
+            same(g, w, i.name)
+        assert rc.autotune_lookup(3, tasks, bound) == 1000
+    rc.autotune_reset()
     rc.autotune_config("")
 
 

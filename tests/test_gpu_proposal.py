@@ -67,21 +67,27 @@ def test_forward_matches_reference(rc, n):
 
 @pytest.mark.parametrize("n", [1, 127, 128, 1000, 4097])
 def test_tcgen05_forward_matches(rc, n):
-    """The tcgen05 forward (TMEM accumulators) against the mma.sync forward
-    and the CPU reference on the same parameters and rows (ragged 128-row
-    tiles, several passes over the capacity)."""
+    """The tcgen05 forward (TMEM accumulators), its three layers in one
+    launch and one launch per layer, against the mma.sync forward and the
+    CPU reference on the same parameters and rows (ragged 128-row tiles,
+    several passes over the capacity)."""
     m = rc.MLP(seed=1, capacity=2048)
     p = M.init_params(5).astype(np.float32)
     m.set_params(p)
     X = feature_rows(rc, n, 50 + n)
     m.set_backend(0)
     a = m.forward(cuda(X)).cpu().numpy()
+    m.set_backend(2)
+    c = m.forward(cuda(X)).cpu().numpy()
     m.set_backend(1)
     b = m.forward(cuda(X)).cpu().numpy()
     assert m.backend_error() == 0
     want, _ = M.forward(p, X, bf16_points=True)
     np.testing.assert_allclose(b, a, atol=4e-3, rtol=0)
     np.testing.assert_allclose(b, want, atol=4e-3, rtol=0)
+    # the fused layers compute the same FP32 sums of the same BF16 products
+    # and round them at the same points: the same bits
+    np.testing.assert_array_equal(b, c)
 
 
 # Element-wise bar of a gradient against the reference with the same BF16
@@ -126,7 +132,7 @@ def test_gradient_matches_reference(rc, n, backend):
     assert m.backend_error() == 0
 
 
-@pytest.mark.parametrize("backend", [0, 1])
+@pytest.mark.parametrize("backend", [0, 1, 2])
 def test_adam_steps_match_reference(rc, backend):
     """Three training steps (one minibatch of all rows per call, rows in the
     library's shuffled order) against the float64 Adam update of

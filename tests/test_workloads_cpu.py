@@ -21,6 +21,8 @@ GENS = {
     "large": lambda s: W.large_kernel(s, groups=4, group_size=64, global_len=4096, local_len=256),
     "stress": lambda s: W.stress_kernel(s, groups=4, group_size=64),
     "group": lambda s: W.group_kernel(s),
+    "proposal": lambda s: W.proposal_kernel(s).instance(*W.proposal_candidates(s)[0]),
+    "batch_proposal": lambda s: W.batch_proposal_kernel(s, max_stmts=64).instance(*W.proposal_candidates(s)[0]),
 }
 
 
@@ -58,3 +60,10 @@ def test_documented_shapes_and_ranges():
         assert 1024 <= L <= 1 << 20
     for (G, S, _) in W.proposal_candidates(0):
         assert 1 <= G <= 64 and S % 32 == 0 and 32 <= S <= 1024
+    # config-3 programs as proposal kernels: the program does not depend on
+    # the candidate, the input does (A of the kernel's length, values [0, 16))
+    bp = W.batch_proposal_kernel(5)
+    a, b = bp.instance(2, 64, 1), bp.instance(8, 1024, 2)
+    assert a.src == b.src and a.globals[0].size == b.globals[0].size == bp.L
+    assert 1024 <= bp.L <= 1 << 20 and 0 <= a.globals[0].min() and a.globals[0].max() < 16
+    assert not np.array_equal(a.globals[0], b.globals[0])
