@@ -226,9 +226,7 @@ struct Tuner {
     if (!persist || path.empty()) return;
     const size_t slash = path.rfind('/');
     if (slash != std::string::npos) {  // best effort: create the cache folder
-      std::string dir = path.substr(0, slash);
-      std::string cmd_free_dir;
-      (void)cmd_free_dir;
+      const std::string dir = path.substr(0, slash);
       mkdir(dir.c_str(), 0755);
     }
     const std::string tmp = path + ".tmp";
@@ -1068,6 +1066,14 @@ rc_report *run_instance(const Instance &I) {
   const bool jit = !group && !I.explore && g_engine != 1 && (g_engine == 2 || N >= kJitAutoItems);
   JitKernel jk_res, jk_iv;
   bool have_res = false, have_iv = false;
+  // the compiled interval kernel runs a work-group of 512 or more work-items
+  // (a multiple of 256) as CTAs of 256: the same registers per SM, four
+  // independent CTAs instead of one, so one CTA's tail overlaps the others'
+  // work
+  const uint32_t iv_split = !group && I.S >= 512 && I.S % 256 == 0 ? I.S / 256 : 1;
+  const uint32_t iv_threads = I.S / iv_split;
+  const size_t iv_smem = interp_smem_bytes((uint32_t)P.mems.size(), P.n_regs, iv_threads, ow_slots) +
+                         (group ? 8ull * (P.n_barriers + 1) : 0);
   if (jit) {
     std::string why;
     if (!jit_available(&why)) {
@@ -1085,13 +1091,13 @@ rc_report *run_instance(const Instance &I) {
           have_res = true;
         }
         JitShape sh;
-        sh.threads = I.S;
+        sh.threads = iv_threads;
         // 1024 threads per SM: up to 64 registers a thread (a 32-register
         // bound, two 1024-thread CTAs per SM, measured 6.26 against 5.99 ms
         // per interval on the 2^26-work-item stress program)
-        sh.min_blocks = std::min<uint32_t>(std::max<uint32_t>(1, 1024 / I.S), 32);
+        sh.min_blocks = std::min<uint32_t>(std::max<uint32_t>(1, 1024 / iv_threads), 32);
         jk_iv = jit_kernel(P, interval_code, sh);
-        have_iv = smem <= kMaxSmemPerBlock - jk_iv.static_smem;
+        have_iv = iv_smem <= kMaxSmemPerBlock - jk_iv.static_smem;
       } catch (const JitError &e) {
         throw Fail{RC_E_CUDA, e.msg};
       }
@@ -1152,6 +1158,7 @@ rc_report *run_instance(const Instance &I) {
   base.S = I.S;
   base.G = I.G;
   base.group0 = 0;
+  base.split = 1;
   base.GT = (uint32_t)L.GT;
   base.LT = (uint32_t)L.LT;
   base.snap = snap;
@@ -1230,8 +1237,10 @@ rc_report *run_instance(const Instance &I) {
     if (timed) CK(cudaEventRecord(g_tev[0], s));
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
     if (have_iv) {
+      a.split = iv_split;
+      a.warps_per_cta = iv_threads / 32;
       try {
-        launch_jit(jk_iv, a, I.G, smem, s);
+        launch_jit(jk_iv, a, I.G, iv_smem, s);
       } catch (const JitError &e) {
         throw Fail{RC_E_CUDA, e.msg};
       }
