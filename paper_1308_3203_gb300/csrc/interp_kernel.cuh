@@ -217,16 +217,23 @@ template <bool kResident, class Engine>
 __device__ __forceinline__ void interp_body(const InterpArgs &A, const Engine &E) {
   if (!kResident && A.proceed && *A.proceed == 0) return;  // a closed gate: the host runs this interval later
   extern __shared__ __align__(16) unsigned char smem[];
+  // Within an interval the work-items of a group do not interact (a read
+  // sees the snapshot and the work-item's own writes), so a group may run as
+  // `split` CTAs of consecutive work-items: T threads each, the register file
+  // and own-write slots in shared memory with stride T.  Resident runs and
+  // work-group-scoped barriers keep one CTA per group.
+  const uint32_t T = blockDim.x, t = threadIdx.x;
   MemInfo *mems = reinterpret_cast<MemInfo *>(smem);
-  int32_t *rf = reinterpret_cast<int32_t *>(mems + A.n_mems);  // [n_regs][S]
-  uint32_t *owk = reinterpret_cast<uint32_t *>(rf + A.n_regs * A.S);  // [ow_slots][S] keys
-  int32_t *owv = reinterpret_cast<int32_t *>(owk + A.ow_slots * A.S);  // [ow_slots][S] values
+  int32_t *rf = reinterpret_cast<int32_t *>(mems + A.n_mems);  // [n_regs][T]
+  uint32_t *owk = reinterpret_cast<uint32_t *>(rf + A.n_regs * T);  // [ow_slots][T] keys
+  int32_t *owv = reinterpret_cast<int32_t *>(owk + A.ow_slots * T);  // [ow_slots][T] values
 
   const uint32_t S = A.S;
-  const uint32_t tid = threadIdx.x;
-  for (uint32_t k = tid; k < A.n_mems; k += blockDim.x) mems[k] = A.mems[k];
+  const uint32_t split = kResident || A.split < 2 ? 1u : A.split;
+  for (uint32_t k = t; k < A.n_mems; k += T) mems[k] = A.mems[k];
 
-  const uint32_t wg = A.group0 + blockIdx.x;
+  const uint32_t wg = A.group0 + blockIdx.x / split;
+  const uint32_t tid = (blockIdx.x % split) * T + t;  // the work-item's id in its group
   const uint32_t gtid = wg * S + tid;
   const uint64_t N = (uint64_t)A.G * S;
   const uint32_t lt = gtid - A.group0 * S;  // index in this launch's own-write table
@@ -241,26 +248,26 @@ __device__ __forceinline__ void interp_body(const InterpArgs &A, const Engine &E
   }
   if (st == TS_RUN) {
     for (uint32_t r = kBuiltinRegs; r < A.n_regs; r++)
-      rf[r * S + tid] = kResident ? 0 : A.regs[(uint64_t)r * N + gtid];
-    rf[REG_TID * S + tid] = (int32_t)tid;
-    rf[REG_WG * S + tid] = (int32_t)wg;
-    rf[REG_GTID * S + tid] = (int32_t)gtid;
-    rf[REG_GSIZE * S + tid] = (int32_t)S;
-    rf[REG_NGROUPS * S + tid] = (int32_t)A.G;
+      rf[r * T + t] = kResident ? 0 : A.regs[(uint64_t)r * N + gtid];
+    rf[REG_TID * T + t] = (int32_t)tid;
+    rf[REG_WG * T + t] = (int32_t)wg;
+    rf[REG_GTID * T + t] = (int32_t)gtid;
+    rf[REG_GSIZE * T + t] = (int32_t)S;
+    rf[REG_NGROUPS * T + t] = (int32_t)A.G;
   }
   // resident: the current interval and owner-table tag live in shared
   // memory (CTA-uniform), which keeps the interpreter's registers free
   __shared__ uint32_t s_iv[2];
-  if (kResident && tid == 0) {
+  if (kResident && t == 0) {
     s_iv[0] = A.interval;
     s_iv[1] = A.tag;
   }
   __syncthreads();
 
-  const uint32_t wbase = tid & ~31u;
-  const uint32_t lanes = S - wbase >= 32 ? 0xFFFFFFFFu : ((1u << (S - wbase)) - 1u);
+  const uint32_t wbase = t & ~31u;
+  const uint32_t lanes = T - wbase >= 32 ? 0xFFFFFFFFu : ((1u << (T - wbase)) - 1u);
   const uint32_t nstops = A.n_barriers + 1;
-  const uint32_t warp = tid >> 5;
+  const uint32_t warp = t >> 5;
   for (;;) {  // resident: one pass per barrier interval; otherwise a single pass
   const uint32_t interval = kResident ? s_iv[0] : A.interval;
   // resident runs raise an interval's flags in the word of its parity, so a
@@ -275,15 +282,15 @@ __device__ __forceinline__ void interp_body(const InterpArgs &A, const Engine &E
   s.owv = owv;
   s.flags = flags;
   s.wlog = reinterpret_cast<uint4 *>(A.log) + ((uint64_t)blockIdx.x * A.warps_per_cta + warp) * A.warp_slice;
-  s.S = S;
-  s.tid = tid;
+  s.S = T;  // register and own-write slot stride
+  s.tid = t;
   s.gtid = gtid;
   s.wg = wg;
   s.lt = lt;
   s.slots = slots;
   s.lbase = A.GT + wg * A.LT;
   s.lanes = lanes;
-  s.lane_lt = (1u << (tid & 31u)) - 1u;
+  s.lane_lt = (1u << (t & 31u)) - 1u;
   s.warp = warp;
   s.interval = interval;
   s.tag = kResident ? s_iv[1] : A.tag;
@@ -313,13 +320,13 @@ __device__ __forceinline__ void interp_body(const InterpArgs &A, const Engine &E
   {
     // access counters of the warp (global, local)
     const uint32_t sg = __reduce_add_sync(lanes, seq - nloc), sl = __reduce_add_sync(lanes, nloc);
-    if ((tid & 31u) == 0) {
+    if ((t & 31u) == 0) {
       s_acc[0][warp] = sg;
       s_acc[1][warp] = sl;
       s_acc[2][warp] = wfill;  // warp-uniform: this warp's records in the log
     }
     const uint32_t smask = __ballot_sync(lanes, stopping);
-    const uint32_t lane = tid & 31u;
+    const uint32_t lane = t & 31u;
     uint32_t stop = kNone, gmin = 0, gcnt = 0;
     if (stopping) {
       stop = st == TS_BARRIER ? E.barrier_ordinal(A, pc) : A.n_barriers;
@@ -342,8 +349,8 @@ __device__ __forceinline__ void interp_body(const InterpArgs &A, const Engine &E
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    const uint32_t nwarps = (S + 31u) / 32u;
+  if (t == 0) {
+    const uint32_t nwarps = (T + 31u) / 32u;
     unsigned long long cg = 0, cl = 0, cw = 0;
     for (uint32_t w = 0; w < nwarps; w++) {
       cg += s_acc[0][w];
@@ -383,8 +390,8 @@ __device__ __forceinline__ void interp_body(const InterpArgs &A, const Engine &E
         uint32_t key;
         int32_t v;
         if (k < ns) {
-          key = owk[k * S + tid];
-          v = owv[k * S + tid];
+          key = owk[k * T + t];
+          v = owv[k * T + t];
         } else {
           const uint2 e = A.ow[(uint64_t)k * A.ow_stride + lt];
           key = e.x;
@@ -393,16 +400,16 @@ __device__ __forceinline__ void interp_body(const InterpArgs &A, const Engine &E
         if (__ldcg(A.owner + 4ull * key) == hi) A.commit[key] = v;
       }
       compact_slice(s.wlog, wfill < A.warp_slice ? wfill : (uint32_t)A.warp_slice, A.owner, tag,
-                    reinterpret_cast<uint4 *>(A.acc_out), A.acc_total, tid & 31u, A.acc_cap, flags);
+                    reinterpret_cast<uint4 *>(A.acc_out), A.acc_total, t & 31u, A.acc_cap, flags);
       if (blockIdx.x == 0)  // the next interval's stop table starts empty
-        for (uint32_t k = tid; k < nstops; k += blockDim.x) {
+        for (uint32_t k = t; k < nstops; k += blockDim.x) {
           A.stop_min[((interval + 1u) & 1u) * nstops + k] = kNone;
           A.stop_cnt[((interval + 1u) & 1u) * nstops + k] = 0;
         }
     }
     if (!grid_sync(A.grid_bar, gridDim.x, A.barrier_limit_ns)) return;
     __shared__ uint32_t s_go;
-    if (tid == 0) {  // every CTA reads the same final values: one decision for the grid
+    if (t == 0) {  // every CTA reads the same final values: one decision for the grid
       uint32_t points = 0;
       bool any_barrier = false;
       for (uint32_t k = 0; k < nstops; k++)
@@ -422,10 +429,10 @@ __device__ __forceinline__ void interp_body(const InterpArgs &A, const Engine &E
     if (!s_go) return;
     if (tag == 63) {  // the 6-bit tag wraps: clear the owner table first
       const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-      for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid; i < A.owner_words; i += stride) A.owner[i] = 0;
+      for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + t; i < A.owner_words; i += stride) A.owner[i] = 0;
       if (!grid_sync(A.grid_bar, gridDim.x, A.barrier_limit_ns)) return;
     }
-    if (tid == 0) {  // every thread read s_iv before the last __syncthreads
+    if (t == 0) {  // every thread read s_iv before the last __syncthreads
       s_iv[0] = interval + 1;
       s_iv[1] = tag == 63 ? 1u : tag + 1u;
     }
@@ -442,20 +449,20 @@ __device__ __forceinline__ void interp_body(const InterpArgs &A, const Engine &E
   {  // spill the shared-memory own-write slots so the commit kernel sees every entry
     const uint32_t ns = nw < slots ? nw : slots;
     for (uint32_t k = 0; k < ns; k++)
-      A.ow[(uint64_t)k * A.ow_stride + lt] = make_uint2(owk[k * S + tid], (uint32_t)owv[k * S + tid]);
+      A.ow[(uint64_t)k * A.ow_stride + lt] = make_uint2(owk[k * T + t], (uint32_t)owv[k * T + t]);
   }
   if (st == TS_BARRIER) {
-    for (uint32_t r = kBuiltinRegs; r < A.n_regs; r++) A.regs[(uint64_t)r * N + gtid] = rf[r * S + tid];
+    for (uint32_t r = kBuiltinRegs; r < A.n_regs; r++) A.regs[(uint64_t)r * N + gtid] = rf[r * T + t];
   }
-  if ((tid & 31u) == 0)
+  if ((t & 31u) == 0)
     A.warp_count[(uint64_t)blockIdx.x * A.warps_per_cta + warp] = wfill < A.warp_slice ? wfill : (uint32_t)A.warp_slice;
   // Work-group-scoped barriers: the barrier-release rule within this group,
   // from its own stop points (smallest work-item, count) gathered in the
   // dynamic shared memory after the own-write slots (8 * (n_barriers + 1)
   // bytes the host adds in this mode).
   if (A.group_div) {  // uniform over the grid
-    uint32_t *grp_min = reinterpret_cast<uint32_t *>(owv + slots * S), *grp_cnt = grp_min + (A.n_barriers + 1);
-    for (uint32_t k = tid; k <= A.n_barriers; k += blockDim.x) {
+    uint32_t *grp_min = reinterpret_cast<uint32_t *>(owv + slots * T), *grp_cnt = grp_min + (A.n_barriers + 1);
+    for (uint32_t k = t; k <= A.n_barriers; k += blockDim.x) {
       grp_min[k] = kNone;
       grp_cnt[k] = 0;
     }
@@ -466,7 +473,7 @@ __device__ __forceinline__ void interp_body(const InterpArgs &A, const Engine &E
       atomicAdd(&grp_cnt[stop], 1u);
     }
     __syncthreads();
-    if (tid == 0) {
+    if (t == 0) {
       uint32_t points = 0;
       for (uint32_t k = 0; k <= A.n_barriers; k++) points += grp_cnt[k] != 0;
       if (points >= 2) {

@@ -212,7 +212,8 @@ void launch_jit(const JitKernel &k, const InterpArgs &a, uint32_t n_groups, size
   count_launch();
   InterpArgs arg = a;
   void *params[] = {&arg};
-  const cudaError_t e = cudaLaunchKernel(k.fn, dim3(n_groups), dim3(a.S), params, smem, s);
+  const uint32_t split = a.split > 1 ? a.split : 1;  // CTAs per work-group
+  const cudaError_t e = cudaLaunchKernel(k.fn, dim3(n_groups * split), dim3(a.S / split), params, smem, s);
   if (e != cudaSuccess) throw JitError{std::string("launch of a compiled interval kernel: ") + cudaGetErrorString(e)};
 }
 

@@ -52,7 +52,9 @@ struct InterpArgs {
   const Insn *code;
   const MemInfo *mems;
   uint32_t n_insn, n_regs, n_mems, n_barriers;
-  uint32_t S, G, group0;   // block b runs work-group group0 + b
+  uint32_t S, G, group0;   // block b runs (a part of) work-group group0 + b / split
+  uint32_t split;          // CTAs per work-group (0 or 1: one CTA runs the whole group); the
+                           // parts are consecutive work-items, blockDim.x = S / split each
   uint32_t GT, LT;         // global cells, local cells per group
   uint32_t interval;
   const int32_t *snap;     // committed memory, indexed by key
