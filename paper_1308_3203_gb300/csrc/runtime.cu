@@ -1238,7 +1238,7 @@ rc_report *run_instance(const Instance &I) {
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], s));
     if (have_iv) {
       a.split = iv_split;
-      a.warps_per_cta = iv_threads / 32;
+      a.warps_per_cta = (iv_threads + 31) / 32;  // a partial warp when a group is not whole warps
       try {
         launch_jit(jk_iv, a, I.G, iv_smem, s);
       } catch (const JitError &e) {
