@@ -66,7 +66,9 @@ __global__ void key_classify_kernel(const Summary *sum, uint64_t nsum, const uin
   }
   const CellResult c = classify_cell(sum, i, nsum);
   if (c.wrote && a.snap) a.snap[sum[i].key] = c.commit;  // no snapshot: commits were made already
-  nrec[keyidx[i]] = (c.ww_cls ? 1u : 0u) + (c.rw_a != kNone ? 1u : 0u);
+  const uint32_t k = keyidx[i], nr = (c.ww_cls ? 1u : 0u) + (c.rw_a != kNone ? 1u : 0u);
+  nrec[k] = nr;
+  if (nr) a.cellres[k] = c;
 }
 
 __global__ void key_emit_kernel(const Summary *sum, uint64_t nsum, const uint32_t *khead,
@@ -78,7 +80,7 @@ __global__ void key_emit_kernel(const Summary *sum, uint64_t nsum, const uint32_
   const uint32_t k = keyidx[i];
   if (nrec[k] == 0) return;
   if (i + kBigCell < nsum && sum[i + kBigCell].key == sum[i].key) return;  // emitted by big_emit
-  emit_cell(a, sum[i].key, classify_cell(sum, i, nsum), recoff[k], out);
+  emit_cell(a, sum[i].key, a.cellres[k], recoff[k], out);
 }
 
 // ---- large cells: one CTA per cell, three sweeps over its summaries.

@@ -217,6 +217,9 @@ struct ClassifyArgs {
   // cells above kBigCell summaries: head index of each, how many, their results
   uint32_t *big = nullptr, *nbig = nullptr;
   CellResult *bigres = nullptr;
+  // the other cells' results by cell index (written by the classifier for
+  // cells with records, read by the emitter: one walk of each cell)
+  CellResult *cellres = nullptr;
   const uint32_t *nsum = nullptr;  // device: number of summaries (launches cover an upper bound)
   // batches: cells of several instances end to end; records name their instance
   uint32_t n_kernels = 0;

@@ -116,6 +116,7 @@ struct Workspace {
       xgn, xgoff, xgtmp, xgout, rstat, rivoff, rbar;
   HostBuf hstats, hrecs, hround, hdesc, hsmall, hstage, hrank;
   DevBuf brounds;  // resident batch: intervals per instance, rounds, last tag
+  DevBuf cellres;  // per-cell classification results between the classifier and the emitter
   DevBuf rankx;  // ranked search: features and scores of the candidates
   DevBuf stage;  // one-CTA checks: bytecode, memory table and snapshot in one block
   cudaStream_t bstream = nullptr;
@@ -448,6 +449,7 @@ void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t inter
   }
   ca.big = W.big.get<uint32_t>(big_cells_cap(n));
   ca.bigres = W.bigres.get<CellResult>(big_cells_cap(n));
+  ca.cellres = W.cellres.get<CellResult>(n);
   ca.nbig = counts;
   ca.nsum = counts + 1;
   launch_key_classify(sum, n, khead, keyidx, nrec, ca, s);
