@@ -433,6 +433,13 @@ def measure(rc, inst, bc, *, steps, warmup, dist, flush, log_every=False, host=T
     return out
 
 
+def interval_kernel(rc, n_items: int) -> str:
+    """The interval kernel the automatic engine runs for an instance of
+    n_items work-items: compiled intervals from 2^17 work-items (when this
+    process compiled any), else the interpreter."""
+    return "rc_jit_kernel" if n_items >= (1 << 17) and rc.jit_stats()["compiles"] else "interp_kernel"
+
+
 def roofline(m, peak, peak_source, traffic=None, kernel="interp_kernel") -> dict:
     """Roofline of the interval kernel (the dominant kernel: it runs the
     work-items and writes the access logs; rc_jit_kernel under compiled
@@ -525,7 +532,7 @@ def main():
     same_kernel = (args.workload == "stress" and full_size and rank == 0 and
                    INTERP_TRAFFIC["sources_sha256"] == interp_sources_sha256() and
                    INTERP_TRAFFIC["program_sha256"] == hashlib.sha256(inst.src.encode()).hexdigest())
-    kname = "rc_jit_kernel" if rc.jit_stats()["compiles"] else "interp_kernel"
+    kname = interval_kernel(rc, inst.groups * inst.group_size)
     roof = roofline(m, hbm, peak_source, INTERP_TRAFFIC["bytes_per_launch"] if same_kernel else None, kname)
 
     out = {
@@ -569,7 +576,8 @@ def main():
         out["full_logging"] = {"what": "same instance, every access logged (RC_LOG_EVERY_ACCESS)",
                                "value": acc_f * f["steps"] / (t_f / 1e3), "unit": UNIT,
                                "ms_per_step": t_f / f["steps"], "logged_accesses_per_step": fr["n_logged"],
-                               "roofline": roofline(f, hbm, peak_source)}
+                               "roofline": roofline(f, hbm, peak_source,
+                                                    kernel=interval_kernel(rc, inst.groups * inst.group_size))}
         del f
         if args.workload == "stress":
             # the 1024 x 256 large instance
@@ -584,7 +592,8 @@ def main():
                             "e2e": acc_l * lm["steps"] / (t_le / 1e3),
                             "logged_accesses_per_step": lm["rep"]["n_logged"],
                             "accesses_per_step": lm["rep"]["n_access"],
-                            "roofline": roofline(lm, hbm, peak_source)}
+                            "roofline": roofline(lm, hbm, peak_source,
+                                                 kernel=interval_kernel(rc, li.groups * li.group_size))}
     if args.secondary in ("all", "small"):
         out["small"] = small_leg(rc, W)
     if args.secondary in ("all", "batch") and args.batch_kernels > 0:
