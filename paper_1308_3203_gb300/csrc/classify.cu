@@ -55,32 +55,42 @@ __global__ void run_reduce_kernel(const LogRec *r, uint64_t n, const uint32_t *h
   if (j == n) *nsum = k + 1;  // the last run
 }
 
-__global__ void key_classify_kernel(const Summary *sum, uint64_t nsum, const uint32_t *khead,
-                                    const uint32_t *keyidx, uint32_t *nrec, ClassifyArgs a) {
+// The first summary of every cell, by cell index (keyidx: exclusive scan of
+// the cell heads), and the number of cells in *a.ncell: the per-cell kernels
+// then run one thread per cell, so that a warp's lanes all walk cells
+// instead of one lane in a cell's worth of summaries.
+__global__ void cell_starts_kernel(const uint32_t *khead, const uint32_t *keyidx, ClassifyArgs a) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  nsum = *a.nsum;  // the launch covers an upper bound
-  if (i >= nsum || !khead[i]) return;
+  const uint64_t nsum = *a.nsum;
+  if (i >= nsum) return;
+  const uint32_t h = khead[i], k = keyidx[i];
+  if (h) a.cstart[k] = (uint32_t)i;
+  if (i + 1 == nsum) *a.ncell = k + h;
+}
+
+// One thread per cell (launched over an upper bound).
+__global__ void key_classify_kernel(const Summary *sum, uint32_t *nrec, ClassifyArgs a) {
+  const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= *a.ncell) return;
+  const uint64_t nsum = *a.nsum, i = a.cstart[q];
   if (i + kBigCell < nsum && sum[i + kBigCell].key == sum[i].key) {  // a large cell: one CTA's work
     a.big[atomicAdd(a.nbig, 1u)] = (uint32_t)i;
     return;
   }
   const CellResult c = classify_cell(sum, i, nsum);
   if (c.wrote && a.snap) a.snap[sum[i].key] = c.commit;  // no snapshot: commits were made already
-  const uint32_t k = keyidx[i], nr = (c.ww_cls ? 1u : 0u) + (c.rw_a != kNone ? 1u : 0u);
-  nrec[k] = nr;
-  if (nr) a.cellres[k] = c;
+  const uint32_t nr = (c.ww_cls ? 1u : 0u) + (c.rw_a != kNone ? 1u : 0u);
+  nrec[q] = nr;
+  if (nr) a.cellres[q] = c;
 }
 
-__global__ void key_emit_kernel(const Summary *sum, uint64_t nsum, const uint32_t *khead,
-                                const uint32_t *keyidx, const uint32_t *nrec, const uint32_t *recoff,
-                                OutRec *out, ClassifyArgs a) {
-  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  nsum = *a.nsum;
-  if (i >= nsum || !khead[i]) return;
-  const uint32_t k = keyidx[i];
-  if (nrec[k] == 0) return;
+__global__ void key_emit_kernel(const Summary *sum, const uint32_t *nrec, const uint32_t *recoff, OutRec *out,
+                                ClassifyArgs a) {
+  const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= *a.ncell || nrec[q] == 0) return;
+  const uint64_t nsum = *a.nsum, i = a.cstart[q];
   if (i + kBigCell < nsum && sum[i + kBigCell].key == sum[i].key) return;  // emitted by big_emit
-  emit_cell(a, sum[i].key, a.cellres[k], recoff[k], out);
+  emit_cell(a, sum[i].key, a.cellres[q], recoff[q], out);
 }
 
 // ---- large cells: one CTA per cell, three sweeps over its summaries.
@@ -274,18 +284,19 @@ void launch_run_reduce(const LogRec *r, uint64_t n, const uint32_t *head, const 
   if (n) count_launch();
   if (n) run_reduce_kernel<<<blocks_for(n), kThreads, 0, s>>>(r, n, head, runidx, sum, khead, nsum);
 }
-void launch_key_classify(const Summary *sum, uint64_t nsum, const uint32_t *khead,
-                         const uint32_t *keyidx, uint32_t *nrec, const ClassifyArgs &a,
-                         cudaStream_t s) {
-  if (nsum) count_launch();
-  if (nsum) key_classify_kernel<<<blocks_for(nsum), kThreads, 0, s>>>(sum, nsum, khead, keyidx, nrec, a);
+void launch_cell_starts(const uint32_t *khead, const uint32_t *keyidx, uint64_t n, const ClassifyArgs &a,
+                        cudaStream_t s) {
+  if (n) count_launch();
+  if (n) cell_starts_kernel<<<blocks_for(n), kThreads, 0, s>>>(khead, keyidx, a);
 }
-void launch_key_emit(const Summary *sum, uint64_t nsum, const uint32_t *khead,
-                     const uint32_t *keyidx, const uint32_t *nrec, const uint32_t *recoff,
-                     OutRec *out, const ClassifyArgs &a, cudaStream_t s) {
-  if (nsum) count_launch();
-  if (nsum)
-    key_emit_kernel<<<blocks_for(nsum), kThreads, 0, s>>>(sum, nsum, khead, keyidx, nrec, recoff, out, a);
+void launch_key_classify(const Summary *sum, uint64_t n, uint32_t *nrec, const ClassifyArgs &a, cudaStream_t s) {
+  if (n) count_launch();
+  if (n) key_classify_kernel<<<blocks_for(n), kThreads, 0, s>>>(sum, nrec, a);
+}
+void launch_key_emit(const Summary *sum, uint64_t n, const uint32_t *nrec, const uint32_t *recoff, OutRec *out,
+                     const ClassifyArgs &a, cudaStream_t s) {
+  if (n) count_launch();
+  if (n) key_emit_kernel<<<blocks_for(n), kThreads, 0, s>>>(sum, nrec, recoff, out, a);
 }
 
 int sm_count() {

@@ -36,10 +36,12 @@ constexpr uint32_t kGridBarWords = 32 + 32 * 32;  // grid barrier: top counter, 
 // Diagnostic cooperative launch whose grid barrier cannot complete (bar: kGridBarWords zeroed words).
 cudaError_t launch_grid_barrier_probe(unsigned *bar, uint32_t n_blocks, unsigned long long limit_ns, cudaStream_t s);
 // Gate of a speculatively queued interval: *proceed = 1 iff the previous
-// interval overflowed nothing, compacted no record for the exact sort, and
-// its work-items all stopped at one barrier (the run goes on unchanged).
-void launch_interval_gate(const uint32_t *flags, const unsigned long long *compacted, const uint32_t *stop_cnt,
-                          uint32_t n_barriers, uint32_t *proceed, cudaStream_t s);
+// interval overflowed nothing and its work-items all stopped at one barrier
+// (the run goes on unchanged; the shadow path has committed every written
+// cell before the gate, so the exact classification of the previous
+// interval's shared cells is not needed first).
+void launch_interval_gate(const uint32_t *flags, const uint32_t *stop_cnt, uint32_t n_barriers, uint32_t *proceed,
+                          cudaStream_t s);
 size_t interp_smem_bytes(uint32_t n_mems, uint32_t n_regs, uint32_t S, uint32_t ow_slots);
 cudaError_t interp_configure();
 constexpr uint32_t kConstCodeInsns = 4000;  // programs up to this size run from constant memory
@@ -221,6 +223,8 @@ struct ClassifyArgs {
   // cells with records, read by the emitter: one walk of each cell)
   CellResult *cellres = nullptr;
   const uint32_t *nsum = nullptr;  // device: number of summaries (launches cover an upper bound)
+  uint32_t *cstart = nullptr;      // first summary of each cell, by cell index
+  uint32_t *ncell = nullptr;       // device: number of cells
   // batches: cells of several instances end to end; records name their instance
   uint32_t n_kernels = 0;
   const uint64_t *kbase = nullptr;  // sorted first cell of each instance
@@ -231,12 +235,13 @@ void launch_run_heads(const LogRec *r, uint64_t n, uint32_t *head, cudaStream_t 
 // also stores the number of summaries in *nsum (device)
 void launch_run_reduce(const LogRec *r, uint64_t n, const uint32_t *head, const uint32_t *runidx,
                        Summary *sum, uint32_t *khead, uint32_t *nsum, cudaStream_t s);
-void launch_key_classify(const Summary *sum, uint64_t nsum, const uint32_t *khead,
-                         const uint32_t *keyidx, uint32_t *nrec, const ClassifyArgs &a,
-                         cudaStream_t s);
-void launch_key_emit(const Summary *sum, uint64_t nsum, const uint32_t *khead,
-                     const uint32_t *keyidx, const uint32_t *nrec, const uint32_t *recoff,
-                     OutRec *out, const ClassifyArgs &a, cudaStream_t s);
+// a.cstart and *a.ncell from the cell heads and their exclusive scan
+void launch_cell_starts(const uint32_t *khead, const uint32_t *keyidx, uint64_t n, const ClassifyArgs &a,
+                        cudaStream_t s);
+// one thread per cell; n bounds the number of cells
+void launch_key_classify(const Summary *sum, uint64_t n, uint32_t *nrec, const ClassifyArgs &a, cudaStream_t s);
+void launch_key_emit(const Summary *sum, uint64_t n, const uint32_t *nrec, const uint32_t *recoff, OutRec *out,
+                     const ClassifyArgs &a, cudaStream_t s);
 // the large cells key_classify set aside (a.big, a.nbig): results, commit, record counts
 void launch_big_classify(const Summary *sum, uint64_t nsum, const uint32_t *keyidx, uint32_t *nrec,
                          const ClassifyArgs &a, cudaStream_t s);

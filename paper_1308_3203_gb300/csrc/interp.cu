@@ -135,8 +135,8 @@ __global__ void grid_barrier_probe_kernel(unsigned *bar, unsigned long long limi
   grid_sync(bar, gridDim.x + 1, limit_ns);
 }
 
-__global__ void interval_gate_kernel(const uint32_t *flags, const unsigned long long *compacted,
-                                     const uint32_t *stop_cnt, uint32_t n_barriers, uint32_t *proceed) {
+__global__ void interval_gate_kernel(const uint32_t *flags, const uint32_t *stop_cnt, uint32_t n_barriers,
+                                     uint32_t *proceed) {
   uint32_t n_points = 0;
   bool any_barrier = false;
   for (uint32_t k = 0; k <= n_barriers; k++) {
@@ -144,7 +144,7 @@ __global__ void interval_gate_kernel(const uint32_t *flags, const unsigned long 
     n_points++;
     if (k < n_barriers) any_barrier = true;
   }
-  *proceed = (*flags == 0 && *compacted == 0 && n_points == 1 && any_barrier) ? 1u : 0u;
+  *proceed = (*flags == 0 && n_points == 1 && any_barrier) ? 1u : 0u;
 }
 
 
@@ -515,10 +515,10 @@ __global__ void __launch_bounds__(1024, 1) small_check_kernel(SmallArgs P) {
 
 }  // namespace
 
-void launch_interval_gate(const uint32_t *flags, const unsigned long long *compacted, const uint32_t *stop_cnt,
-                          uint32_t n_barriers, uint32_t *proceed, cudaStream_t s) {
+void launch_interval_gate(const uint32_t *flags, const uint32_t *stop_cnt, uint32_t n_barriers, uint32_t *proceed,
+                          cudaStream_t s) {
   count_launch();
-  interval_gate_kernel<<<1, 1, 0, s>>>(flags, compacted, stop_cnt, n_barriers, proceed);
+  interval_gate_kernel<<<1, 1, 0, s>>>(flags, stop_cnt, n_barriers, proceed);
 }
 
 size_t interp_smem_bytes(uint32_t n_mems, uint32_t n_regs, uint32_t S, uint32_t ow_slots) {

@@ -117,9 +117,11 @@ struct Workspace {
   HostBuf hstats, hrecs, hround, hdesc, hsmall, hstage, hrank;
   DevBuf brounds;  // resident batch: intervals per instance, rounds, last tag
   DevBuf cellres;  // per-cell classification results between the classifier and the emitter
+  DevBuf cstart;   // first summary of each cell
   DevBuf rankx;  // ranked search: features and scores of the candidates
   DevBuf stage;  // one-CTA checks: bytecode, memory table and snapshot in one block
   cudaStream_t bstream = nullptr;
+  cudaStream_t cstream = nullptr;  // shadow-path classification beside the next interval
   cudaEvent_t sev[2] = {nullptr, nullptr};  // stats of an interval (by parity) reached the host
   bool configured = false, batch_configured = false;
   uint32_t epoch = 0;
@@ -129,7 +131,8 @@ struct Workspace {
                       &khead, &keyidx, &nrec, &recoff, &out, &scan, &errs, &stats, &owner,
                       &owcnt, &compact, &ctacnt, &ctaoff, &sortscr, &reckern, &bdesc, &bcode,
                       &bmems, &btask, &bkbase, &bkgt, &bklt, &berrk, &shared_acc, &bround, &big,
-                      &bigres, &nbig, &xg, &xgcnt, &xgn, &xgoff, &xgtmp, &xgout, &rstat, &rivoff, &rbar, &stage})
+                      &bigres, &nbig, &xg, &xgcnt, &xgn, &xgoff, &xgtmp, &xgout, &rstat, &rivoff, &rbar, &stage,
+                      &cellres, &cstart})
       b->release();
     epoch = 0;
     owner_hi = 0;
@@ -433,9 +436,9 @@ void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t inter
   scan_exclusive(head, runidx, n, tmp, s);
   Summary *sum = W.sum.get<Summary>(n);
   uint32_t *khead = W.khead.get<uint32_t>(n), *keyidx = W.keyidx.get<uint32_t>(n);
-  uint32_t *counts = W.nbig.get<uint32_t>(2);  // [0] large cells, [1] summaries
+  uint32_t *counts = W.nbig.get<uint32_t>(3);  // [0] large cells, [1] summaries, [2] cells
   CK(cudaMemsetAsync(khead, 0, n * 4, s));
-  CK(cudaMemsetAsync(counts, 0, 8, s));
+  CK(cudaMemsetAsync(counts, 0, 12, s));
   launch_run_reduce(sorted, n, head, runidx, sum, khead, counts + 1, s);
   scan_exclusive(khead, keyidx, n, tmp, s);
   uint32_t *nrec = W.nrec.get<uint32_t>(n), *recoff = W.recoff.get<uint32_t>(n);
@@ -452,7 +455,10 @@ void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t inter
   ca.cellres = W.cellres.get<CellResult>(n);
   ca.nbig = counts;
   ca.nsum = counts + 1;
-  launch_key_classify(sum, n, khead, keyidx, nrec, ca, s);
+  ca.ncell = counts + 2;
+  ca.cstart = W.cstart.get<uint32_t>(n);
+  launch_cell_starts(khead, keyidx, n, ca, s);
+  launch_key_classify(sum, n, nrec, ca, s);
   launch_big_classify(sum, n, keyidx, nrec, ca, s);
   scan_exclusive(nrec, recoff, n, tmp, s);
   CK(cudaMemcpyAsync(hstats, recoff + n - 1, 4, cudaMemcpyDeviceToHost, s));
@@ -462,7 +468,7 @@ void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t inter
   if (nrecs == 0) return;
   OutRec *out = W.out.get<OutRec>(nrecs);
   if (bm) ca.rec_kernel = W.reckern.get<uint32_t>(nrecs);
-  launch_key_emit(sum, n, khead, keyidx, nrec, recoff, out, ca, s);
+  launch_key_emit(sum, n, nrec, recoff, out, ca, s);
   launch_big_emit(sum, n, keyidx, nrec, recoff, out, ca, s);
   size_t old = races.size();
   races.resize(old + nrecs);
@@ -525,11 +531,11 @@ uint32_t shadow_next_tag(Workspace &W, cudaStream_t s, uint64_t extent) {
   return ++W.epoch;
 }
 
-// Shadow path: commit single-writer cells from the own-write tables, send
-// the log records of shared written cells through the exact sort path.
-// Shadow path, device half: commit the single-writer cells from the
-// own-write tables and compact the records of every other written cell into
-// W.logb; the number of compacted records lands in *dcount (64-bit).
+// Shadow path, device half: every written cell takes its highest writer's
+// last write, committed from that work-item's own-write table, and the
+// records of cells that need the exact classification (two or more writers,
+// or one writer and another reader) are compacted into W.logb; the number
+// of compacted records lands in *dcount (64-bit).
 void shadow_launch(Workspace &W, const LogRec *log, uint32_t n_slices, uint64_t slice, const uint32_t *count,
                    uint64_t N, int32_t *snap, const uint32_t *owner, uint32_t tag, const uint2 *ow,
                    const uint32_t *ow_count, uint32_t *dcount, cudaStream_t s) {
@@ -540,15 +546,30 @@ void shadow_launch(Workspace &W, const LogRec *log, uint32_t n_slices, uint64_t 
   launch_shadow_compact(log, n_slices, slice, count, owner, tag, shared, cnt, s);
 }
 
-// Shadow path, host half: the m compacted records are sorted and classified.
+// Shadow path, host half: the m compacted records are sorted and classified
+// (no commits: shadow_launch made them all).  Reads only W.logb and the
+// classification's own buffers, so it may run on another stream while the
+// next interval runs.
 void shadow_finish(Workspace &W, uint64_t m, uint64_t keys, uint64_t N, uint32_t interval, const Layout &L,
-                   int32_t *snap, uint32_t *hstats, std::vector<OutRec> &races, cudaStream_t s) {
+                   uint32_t *hstats, std::vector<OutRec> &races, cudaStream_t s) {
   if (m == 0) return;
   LogRec *shared = W.logb.as<LogRec>();
   uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(m), scan_tmp_words(m)));
   LogRec *other = W.compact.get<LogRec>(m);
   LogRec *sorted = sort_log(shared, other, m, bitwidth(N), bitwidth(keys) + bitwidth(N), tmp, s);
-  classify_run(W, sorted, m, interval, L, snap, hstats, races, s);
+  classify_run(W, sorted, m, interval, L, nullptr, hstats, races, s);
+}
+
+// The stream the shadow path classifies on while the next interval runs:
+// the highest priority, so that the classification's blocks are scheduled
+// as soon as the interval kernel's blocks leave room.
+cudaStream_t classify_stream(Workspace &W) {
+  if (!W.cstream) {
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&W.cstream, cudaStreamNonBlocking, greatest));
+  }
+  return W.cstream;
 }
 
 // Report of one instance: race records (already in cell order), error
@@ -1278,9 +1299,12 @@ rc_report *run_instance(const Instance &I) {
   for (;; interval++) {
     // Speculation: when this interval and the next take the shadow path and
     // nothing is being timed, the next interval's interpreter is queued now,
-    // behind a gate the device sets only if this interval compacted no
-    // record, overflowed nothing and its barrier agreement lets the run go
-    // on -- exactly the case in which the host would launch it unchanged.
+    // behind a gate the device sets only if this interval overflowed nothing
+    // and its barrier agreement lets the run go on -- exactly the case in
+    // which the host would launch it unchanged.  The shadow path commits
+    // every written cell before the gate, so the exact classification of
+    // this interval's shared cells then runs on a second stream beside the
+    // next interval.
     bool next_queued = false;
     uint32_t next_tag = 0;
     if (strategy == 2 && !timed && !g_prof.on && !I.explore && !group) {
@@ -1288,8 +1312,7 @@ rc_report *run_instance(const Instance &I) {
       if (ns == 2 && (fixed_strategy || g_tuner.decided(tkey))) {
         next_tag = shadow_next_tag(W, s, 4 * L.keys);
         uint32_t *d = dbuf(interval);
-        launch_interval_gate(d + ST_FLAGS, reinterpret_cast<const unsigned long long *>(d + ST_SCRATCH),
-                             d + ST_STOPS + nstops, P.n_barriers, gate + ((interval + 1) & 1), s);
+        launch_interval_gate(d + ST_FLAGS, d + ST_STOPS + nstops, P.n_barriers, gate + ((interval + 1) & 1), s);
         enqueue_interp(interval + 1, 2, next_tag, true, false);
         next_queued = true;
       }
@@ -1316,7 +1339,12 @@ rc_report *run_instance(const Instance &I) {
     }
     // ---- classification + commit
     if (strategy == 2) {
-      shadow_finish(W, m, L.keys, N, interval, L, snap, hscratch, races, s);
+      cudaStream_t cs = s;
+      if (next_queued && m) {  // beside the next interval (the compaction is done: its stats arrived)
+        cs = classify_stream(W);
+        CK(cudaStreamWaitEvent(cs, W.sev[interval & 1], 0));
+      }
+      shadow_finish(W, m, L.keys, N, interval, L, hscratch, races, cs);
     } else {
       classify_sorted(W, log, n_slices, slice, warp_count, L.keys, N, interval, L, snap, hscratch, races, s);
     }
@@ -1356,7 +1384,7 @@ rc_report *run_instance(const Instance &I) {
     } else if (!barrier_agreement(interval, P.n_barriers, stop_min.data(), stop_cnt.data(), errors)) {
       break;
     }
-    if (next_queued && m == 0) {  // the gate opened: the next interval is already running
+    if (next_queued) {  // the gate opened: the next interval is already running
       tag = next_tag;
       enqueue_post(interval + 1, 2, tag);
       continue;

@@ -2,12 +2,14 @@
 //
 // The interpreter claims, for every access, the cell's writer or reader word
 // in the owner table (see shadow_claim).  After the interval:
-//  * cells with one writer and no other reader are race-free; their new
-//    value is that work-item's last write, which its own-write table holds,
-//    so each work-item commits its own cells;
-//  * the log records of every other written cell are compacted (one warp-
-//    aggregated atomic per warp and instruction) and classified exactly by
-//    the sort path.
+//  * every written cell takes the last write of its highest writer (the
+//    value the sort path's classifier commits: the schedule that runs
+//    work-items in id order); that work-item's own-write table holds it, so
+//    each work-item commits the cells whose highest writer it is;
+//  * the log records of cells written by two or more work-items, or written
+//    by one and read by another, are compacted (one warp-aggregated atomic
+//    per 128 records) and classified exactly by the sort path, which then
+//    commits nothing: the next interval needs only the commits.
 #include <algorithm>
 
 #include "device.cuh"
@@ -30,11 +32,10 @@ __global__ void shadow_commit_kernel(const uint2 *ow, const uint32_t *ow_count, 
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N) return;
   const uint32_t nw = ow_count[t];
-  const uint32_t hi = (tag << 26) | (uint32_t)t, lo = (tag << 26) | (kIdMask - (uint32_t)t);
+  const uint32_t hi = (tag << 26) | (uint32_t)t;
   for (uint32_t k = 0; k < nw; k++) {
     const uint2 e = ow[(uint64_t)k * ow_stride + t];
-    const uint2 w = reinterpret_cast<const uint2 *>(owner)[2ull * e.x];  // writer max, writer min
-    if (w.x == hi && w.y == lo) snap[e.x] = (int32_t)e.y;  // this work-item is the only writer
+    if (owner[4ull * e.x] == hi) snap[e.x] = (int32_t)e.y;  // this work-item is the cell's highest writer
   }
 }
 
