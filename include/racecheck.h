@@ -324,7 +324,11 @@ int rc_autotune_lookup(int kind, uint64_t a, uint64_t b);
  * (12 per logged global access).  kind 0: the interpreter launch; kind 1:
  * everything after it until the interval's classification is done (owner-
  * table commit, compaction, sort and classification, and any wait for the
- * host in between); kind 2: reserved (zero).  Timing an interval
+ * host in between); kind 2: batch calls (rc_check_batch), wall-clock
+ * milliseconds of the host's own work in each call -- the set-up before the
+ * first round (layout, descriptors, uploads queued) and the reports after
+ * the last classification -- with launches counting the calls and bytes
+ * zero.  Timing an interval
  * synchronises it, so the speculative launch of the next interval is off
  * while enabled.  Reset clears the sums. */
 int rc_profile_enable(int on);

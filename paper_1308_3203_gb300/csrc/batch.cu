@@ -243,10 +243,10 @@ __device__ __forceinline__ void report_fill(const BatchArgs &A, uint32_t fill_pm
 }
 
 // Commits from the own-write tables of one warp task's lanes (instance-local
-// work-items), by the owner table.  Lock-step rounds: only cells with a
-// single writer (the classifier commits the others).  Resident runs: every
-// cell's highest writer commits its last write (the rule the classifier
-// applies), since the classification comes after the launch.
+// work-items), by the owner table: every cell's highest writer commits its
+// last write (the rule the classifier applies), so the next round needs
+// nothing from the classification, which in a resident run comes after the
+// launch and in lock-step rounds runs beside the next round.
 template <bool kRes>
 __device__ __forceinline__ void commit_task(const BatchArgs &A, uint32_t task, uint32_t tag, uint32_t lane) {
   const uint32_t k = A.task_kernel[task];
@@ -254,11 +254,10 @@ __device__ __forceinline__ void commit_task(const BatchArgs &A, uint32_t task, u
   const uint32_t gl = (task - D.task_off) * 32 + lane;
   if ((uint64_t)gl >= D.N) return;
   const uint32_t nw = ld_state<kRes>(A.ow_count + D.state_off + gl);
-  const uint32_t hi = (tag << 26) | gl, lo = (tag << 26) | (kIdMask - gl);
+  const uint32_t hi = (tag << 26) | gl;
   for (uint32_t q = 0; q < nw; q++) {
     const uint2 e = ld_state<kRes>(A.ow + D.ow_off + (uint64_t)q * D.N + gl);
-    const uint2 w = __ldcg(reinterpret_cast<const uint2 *>(A.owner) + 2ull * e.x);
-    if (w.x == hi && (kRes || w.y == lo)) A.snap[e.x] = (int32_t)e.y;
+    if (__ldcg(A.owner + 4ull * e.x) == hi) A.snap[e.x] = (int32_t)e.y;
   }
 }
 

@@ -21,6 +21,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "racecheck.h"
@@ -97,6 +98,10 @@ struct HostBuf {
   void *p = nullptr;
   size_t cap = 0;
   template <class T>
+  T *as() {
+    return static_cast<T *>(p);
+  }
+  template <class T>
   T *get(size_t n) {
     size_t bytes = std::max<size_t>(n * sizeof(T), 256);
     if (bytes > cap) {
@@ -114,7 +119,8 @@ struct Workspace {
       recoff, out, scan, errs, stats, owner, owcnt, compact, ctacnt, ctaoff, sortscr, reckern,
       bdesc, bcode, bmems, btask, bkbase, bkgt, bklt, berrk, shared_acc, bround, big, bigres, nbig, xg, xgcnt,
       xgn, xgoff, xgtmp, xgout, rstat, rivoff, rbar;
-  HostBuf hstats, hrecs, hround, hdesc, hsmall, hstage, hrank;
+  HostBuf hstats, hround, hdesc, hsmall, hstage, hrank;
+  HostBuf hrecs[2], hreck[2];  // batch race records and their instances, alternate rounds
   DevBuf brounds;  // resident batch: intervals per instance, rounds, last tag
   DevBuf cellres;  // per-cell classification results between the classifier and the emitter
   DevBuf cstart;   // first summary of each cell
@@ -416,11 +422,103 @@ Layout make_layout(const Program &p, const rc_input *in, uint32_t G) {
 
 // Classify records already sorted by (cell, work-item): run reduce, per-cell
 // classification with commit, and ordered emission of the records.
+// A growable malloc'd array of records: a batch instance's race records,
+// handed to its report without another copy (realloc of a large block
+// remaps its pages instead of copying them).
+struct RecList {
+  OutRec *p = nullptr;
+  size_t n = 0, cap = 0;
+  RecList() = default;
+  RecList(const RecList &) = delete;
+  RecList &operator=(const RecList &) = delete;
+  RecList(RecList &&o) noexcept : p(o.p), n(o.n), cap(o.cap) {
+    o.p = nullptr;
+    o.n = o.cap = 0;
+  }
+  ~RecList() { std::free(p); }
+  void append(const OutRec *src, size_t k) {
+    if (!k) return;
+    if (n + k > cap) {
+      const size_t c = std::max<size_t>({n + k, 2 * cap, 64});
+      OutRec *q = static_cast<OutRec *>(std::realloc(p, c * sizeof(OutRec)));
+      if (!q) throw Fail{RC_E_NOMEM, "record list allocation failed"};
+      p = q;
+      cap = c;
+    }
+    std::memcpy(p + n, src, k * sizeof(OutRec));
+    n += k;
+  }
+  OutRec *release() {
+    OutRec *q = p;
+    p = nullptr;
+    n = cap = 0;
+    return q;
+  }
+};
+
+struct RecordSink;
 struct BatchMap {  // cell space of a batch: instance first cells and sizes (device)
   uint32_t n = 0;
   const uint64_t *kbase = nullptr;
   const uint32_t *kGT = nullptr, *kLT = nullptr;
-  std::vector<uint32_t> *kernel_of = nullptr;  // receives the instance of every record
+  RecordSink *sink = nullptr;  // receives every record, for its instance's list
+};
+
+// A batch round's race records, in cell order (the instances' cells lie end
+// to end, so each instance's records form one run; kernel_of names each
+// record's instance), appended to the instances' lists run by run.
+void distribute_records(const OutRec *rr, const uint32_t *kernel_of, uint64_t n, std::vector<RecList> &races) {
+  for (uint64_t i = 0; i < n;) {
+    uint64_t j = i + 1;
+    while (j < n && kernel_of[j] == kernel_of[i]) j++;
+    races[kernel_of[i]].append(rr + i, j - i);
+    i = j;
+  }
+}
+
+// Appends each batch round's race records to the instances' lists on a
+// worker thread while the device classifies the next round.  Two page-
+// locked buffer pairs alternate; a round's job starts once the previous
+// one has ended, so the lists grow in round order, and the buffers a round
+// fills were last read by the job two rounds back, already joined.
+struct RecordSink {
+  std::vector<RecList> &races;
+  HostBuf *recs, *kern;  // [2] each, kept in the workspace
+  uint32_t next = 0;
+  std::thread job;
+  std::exception_ptr err;
+  RecordSink(std::vector<RecList> &r, HostBuf *rb, HostBuf *kb) : races(r), recs(rb), kern(kb) {}
+  RecordSink(const RecordSink &) = delete;
+  RecordSink &operator=(const RecordSink &) = delete;
+  ~RecordSink() {
+    if (job.joinable()) job.join();
+  }
+  // waits for the running job; rethrows its failure
+  void join() {
+    if (job.joinable()) job.join();
+    if (err) {
+      std::exception_ptr e = err;
+      err = nullptr;
+      std::rethrow_exception(e);
+    }
+  }
+  // the buffers for the next round's n records
+  OutRec *records(uint64_t n) { return recs[next & 1].get<OutRec>(n); }
+  uint32_t *kernels(uint64_t n) { return kern[next & 1].get<uint32_t>(n); }
+  // the next round's n records have arrived in its buffers
+  void submit(uint64_t n) {
+    join();
+    const OutRec *r = recs[next & 1].as<OutRec>();
+    const uint32_t *k = kern[next & 1].as<uint32_t>();
+    next++;
+    job = std::thread([this, r, k, n] {
+      try {
+        distribute_records(r, k, n, races);
+      } catch (...) {
+        err = std::current_exception();
+      }
+    });
+  }
 };
 
 void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t interval, const Layout &L,
@@ -470,13 +568,18 @@ void classify_run(Workspace &W, const LogRec *sorted, uint64_t n, uint32_t inter
   if (bm) ca.rec_kernel = W.reckern.get<uint32_t>(nrecs);
   launch_key_emit(sum, n, nrec, recoff, out, ca, s);
   launch_big_emit(sum, n, keyidx, nrec, recoff, out, ca, s);
+  if (bm) {  // through page-locked buffers into the instances' lists (on the sink's thread)
+    OutRec *hr = bm->sink->records(nrecs);
+    uint32_t *hk = bm->sink->kernels(nrecs);
+    CK(cudaMemcpyAsync(hr, out, nrecs * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hk, ca.rec_kernel, nrecs * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    bm->sink->submit(nrecs);
+    return;
+  }
   size_t old = races.size();
   races.resize(old + nrecs);
   CK(cudaMemcpyAsync(races.data() + old, out, nrecs * sizeof(OutRec), cudaMemcpyDeviceToHost, s));
-  if (bm) {
-    bm->kernel_of->resize(old + nrecs);
-    CK(cudaMemcpyAsync(bm->kernel_of->data() + old, ca.rec_kernel, nrecs * 4, cudaMemcpyDeviceToHost, s));
-  }
   CK(cudaStreamSynchronize(s));
 }
 
@@ -572,38 +675,46 @@ cudaStream_t classify_stream(Workspace &W) {
   return W.cstream;
 }
 
-// Report of one instance: race records (already in cell order), error
-// records, counters, status (Sec. 4: racy iff a WW or RW race record) and,
-// if asked, the final global memory read from the device snapshot.
-rc_report *make_report(const std::vector<OutRec> &races, const std::vector<OutRec> &errors, uint32_t n_intervals,
-                       uint64_t acc_g, uint64_t acc_l, uint64_t logged, uint64_t GT, const int32_t *final_dev,
-                       cudaStream_t s) {
+// Report of one instance from nr race records (already in cell order) and
+// the error records, which follow them.  owned: null, or a malloc'd array
+// that already holds the races and then the errors and becomes the
+// report's (no copy).
+rc_report *make_report_core(const OutRec *races, size_t nr, const std::vector<OutRec> &errors, OutRec *owned,
+                            uint32_t n_intervals, uint64_t acc_g, uint64_t acc_l, uint64_t logged, uint64_t GT,
+                            const int32_t *final_dev, cudaStream_t s) {
   rc_report *rep = static_cast<rc_report *>(std::calloc(1, sizeof(rc_report)));
-  if (!rep) throw Fail{RC_E_NOMEM, "report allocation failed"};
+  if (!rep) {
+    std::free(owned);
+    throw Fail{RC_E_NOMEM, "report allocation failed"};
+  }
   rep->n_intervals = n_intervals;
   rep->n_global = acc_g;
   rep->n_local = acc_l;
   rep->n_access = acc_g + acc_l;
   rep->n_logged = logged;
   bool racy = false, div = false, as = false, oob = false;
-  for (const OutRec &x : races)
-    racy |= x.cls == CLS_WW_RACE || x.cls == CLS_RW_RACE || x.cls == CLS_XG_WW_RACE || x.cls == CLS_XG_RW_RACE;
+  for (size_t i = 0; i < nr; i++) {
+    const uint32_t c = races[i].cls;
+    racy |= c == CLS_WW_RACE || c == CLS_RW_RACE || c == CLS_XG_WW_RACE || c == CLS_XG_RW_RACE;
+  }
   for (const OutRec &x : errors) {
     div |= x.cls == CLS_DIVERGENCE;
     as |= x.cls == CLS_ASSERT;
     oob |= x.cls == CLS_OOB;
   }
   rep->status = racy ? RC_RACY : div ? RC_ERROR_DIVERGENCE : as ? RC_ERROR_ASSERT : oob ? RC_ERROR_OOB : RC_RACE_FREE;
-  rep->n_records = races.size() + errors.size();
-  if (rep->n_records) {
+  rep->n_records = nr + errors.size();
+  static_assert(sizeof(rc_record) == sizeof(OutRec), "record layout");
+  if (owned) {
+    rep->records = reinterpret_cast<rc_record *>(owned);
+  } else if (rep->n_records) {
     rep->records = static_cast<rc_record *>(std::malloc(rep->n_records * sizeof(rc_record)));
     if (!rep->records) {
       std::free(rep);
       throw Fail{RC_E_NOMEM, "report allocation failed"};
     }
-    static_assert(sizeof(rc_record) == sizeof(OutRec), "record layout");
-    if (!races.empty()) std::memcpy(rep->records, races.data(), races.size() * sizeof(OutRec));
-    if (!errors.empty()) std::memcpy(rep->records + races.size(), errors.data(), errors.size() * sizeof(OutRec));
+    if (nr) std::memcpy(rep->records, races, nr * sizeof(OutRec));
+    if (!errors.empty()) std::memcpy(rep->records + nr, errors.data(), errors.size() * sizeof(OutRec));
   }
   rep->final_len = GT;
   if (final_dev && GT) {
@@ -617,6 +728,25 @@ rc_report *make_report(const std::vector<OutRec> &races, const std::vector<OutRe
   }
   CK(cudaStreamSynchronize(s));
   return rep;
+}
+
+// Report of one instance: race records (already in cell order), error
+// records, counters, status (Sec. 4: racy iff a WW or RW race record) and,
+// if asked, the final global memory read from the device snapshot.
+rc_report *make_report(const std::vector<OutRec> &races, const std::vector<OutRec> &errors, uint32_t n_intervals,
+                       uint64_t acc_g, uint64_t acc_l, uint64_t logged, uint64_t GT, const int32_t *final_dev,
+                       cudaStream_t s) {
+  return make_report_core(races.data(), races.size(), errors, nullptr, n_intervals, acc_g, acc_l, logged, GT,
+                          final_dev, s);
+}
+
+// The same from a batch instance's record list, whose array the report takes.
+rc_report *make_report(RecList &races, const std::vector<OutRec> &errors, uint32_t n_intervals, uint64_t acc_g,
+                       uint64_t acc_l, uint64_t logged, uint64_t GT, const int32_t *final_dev, cudaStream_t s) {
+  const size_t nr = races.n;
+  races.append(errors.data(), errors.size());
+  OutRec *arr = races.release();
+  return make_report_core(arr, nr, errors, arr, n_intervals, acc_g, acc_l, logged, GT, final_dev, s);
 }
 
 // Stop points of one interval -> divergence records (Sec. 4 barrier-release
@@ -855,6 +985,17 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
 // The snapshot of an instance's start: the global inputs (pinned host
 // memory read by a copy kernel over the CPU-GPU link, other memory by
 // cudaMemcpyAsync) and zeroed local memory.
+// One global input array of len int32 values into dst.
+void upload_global(const int32_t *src, int32_t *dst, uint64_t len, bool on_device, cudaStream_t s) {
+  const int32_t *mapped = on_device ? nullptr : device_view(src);
+  if (mapped) {  // pinned host memory: the SMs read it over the CPU-GPU link
+    launch_copy_words(mapped, dst, len, s);
+    CK(cudaGetLastError());
+  } else {
+    CK(cudaMemcpyAsync(dst, src, len * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  }
+}
+
 void load_inputs(const Instance &I, const Layout &L, int32_t *snap, cudaStream_t s) {
   const Program &P = *I.p;
   uint32_t gi = 0;
@@ -863,15 +1004,7 @@ void load_inputs(const Instance &I, const Layout &L, int32_t *snap, cudaStream_t
     const uint64_t len = I.in->global_len[gi];
     if (len) {
       if (!I.in->global_init || !I.in->global_init[gi]) throw Fail{RC_E_INVALID, "missing global input"};
-      const int32_t *src = I.in->global_init[gi];
-      const int32_t *mapped = I.in->on_device ? nullptr : device_view(src);
-      if (mapped) {  // pinned host memory: the SMs read it over the CPU-GPU link
-        launch_copy_words(mapped, snap + L.mems[m].base, len, s);
-        CK(cudaGetLastError());
-      } else {
-        CK(cudaMemcpyAsync(snap + L.mems[m].base, src, len * 4,
-                           I.in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-      }
+      upload_global(I.in->global_init[gi], snap + L.mems[m].base, len, I.in->on_device, s);
     }
     gi++;
   }
@@ -1460,6 +1593,19 @@ BatchItem plan_item(const rc_bytecode *bc, uint32_t G, uint32_t S, const rc_inpu
 // or the round cap reached): the caller checks the batch again in lock-step.
 bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy, rc_report **out) {
   Workspace &W = g_ws;
+  // profiling, kind 2: the host's own work of the call (set-up before the
+  // first round, reports after the last classification), wall clock
+  using Clock = std::chrono::steady_clock;
+  const Clock::time_point t_start = Clock::now();
+  double host_ms = 0;
+  auto ms_since = [](Clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(Clock::now() - t).count();
+  };
+  auto host_done = [&](Clock::time_point t_reports) {
+    if (!g_prof.on) return;
+    g_prof.launches[2]++;
+    g_prof.ms[2] += host_ms + ms_since(t_reports);
+  };
   if (!W.batch_configured) {
     CK(batch_configure());
     W.batch_configured = true;
@@ -1544,8 +1690,7 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
       const uint64_t len = it.in->global_len[gi];
       if (len) {
         if (!it.in->global_init || !it.in->global_init[gi]) throw Fail{RC_E_INVALID, "missing global input"};
-        CK(cudaMemcpyAsync(snap + kbase[k] + it.L.mems[m].base, it.in->global_init[gi], len * 4,
-                           it.in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        upload_global(it.in->global_init[gi], snap + kbase[k] + it.L.mems[m].base, len, it.in->on_device, s);
       }
       gi++;
     }
@@ -1608,6 +1753,7 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
   a.owner = owner;
   a.fill_max = dstats + 6;
   unsigned long long *cnt = reinterpret_cast<unsigned long long *>(dstats + 4);
+  host_ms = ms_since(t_start);
   if (strategy == 3) {
     // ---- resident run: every round in one cooperative launch
     const uint32_t threads = g_tuner.threads_decided(tkey) ? g_tuner.choose_threads(tkey) : 256u;
@@ -1702,7 +1848,9 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
       CK(cudaEventRecord(g_prof.ev[2], s));
     }
     // errors by (interval, class, work-item) per instance: the lock-step order
-    std::vector<std::vector<OutRec>> races(n), errors(n);
+    std::vector<RecList> races(n);
+    std::vector<std::vector<OutRec>> errors(n);
+    RecordSink sink(races, W.hrecs, W.hreck);
     const uint32_t nerr = std::min(hs[1], err_cap);
     if (nerr) {
       std::vector<OutRec> ev(nerr);
@@ -1721,19 +1869,16 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
     CK(cudaMemcpyAsync(off.data(), ivoff, (rounds + 1) * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     std::vector<OutRec> rr;
-    std::vector<uint32_t> rk;
     for (uint32_t r = 0; r < rounds; r++) {
       const uint64_t m = off[r + 1] - off[r];
       if (!m) continue;
       rr.clear();
-      rk.clear();
       uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(m), scan_tmp_words(m)));
       LogRec *other = W.compact.get<LogRec>(m);
       LogRec *sorted = sort_log(acc_out + off[r], other, m, bitwidth(maxN), bitwidth(keys) + bitwidth(maxN), tmp, s);
       Layout none;
-      BatchMap bm{n, dkbase, dkgt, dklt, &rk};
+      BatchMap bm{n, dkbase, dkgt, dklt, &sink};
       classify_run(W, sorted, m, r, none, nullptr, hstats + stat_words, rr, s, &bm);
-      for (size_t i = 0; i < rr.size(); i++) races[rk[i]].push_back(rr[i]);
     }
     if (g_prof.on) {
       CK(cudaEventRecord(g_prof.ev[3], s));
@@ -1743,11 +1888,14 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
       g_prof.launches[1]++;
       g_prof.ms[1] += ms;
     }
+    sink.join();  // every round's records are in the lists
+    const Clock::time_point t_reports = Clock::now();
     for (uint32_t k = 0; k < n; k++) {
       const BatchItem &it = items[k];
       out[k] = make_report(races[k], errors[k], hr[k], acc[2 * k], acc[2 * k + 1], acc[2 * k] + acc[2 * k + 1],
                            it.L.GT, (it.in->flags & RC_WANT_FINAL_MEMORY) ? snap + kbase[k] : nullptr, s);
     }
+    host_done(t_reports);
     return true;
   }
   LogRec *picked = W.logb.get<LogRec>(std::max<uint64_t>(logrecs, 1));
@@ -1796,34 +1944,48 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
     cudaMemsetAsync(dstats + 8 + stops, 0, stops * 4, bs);
     launch_batch_interp(ak, grid, threads, smem, bs);
     launch_batch_commit(ak, bs);
-    launch_batch_compact(ak, picked, cnt, bs);
     CK(cudaStreamEndCapture(bs, &graphs.g[k]));
     CK(cudaGraphInstantiate(&graphs.e[k], graphs.g[k], 0));
     return graphs.e[k];
   };
 
-  std::vector<std::vector<OutRec>> races(n), errors(n);
-  std::vector<uint32_t> n_intervals(n, 0);
-  uint32_t active = n, fill_seen = 0;
-  std::vector<uint64_t> acc(2ull * n), prev(2ull * n, 0);
-  std::vector<OutRec> rr;
-  std::vector<uint32_t> rk;
-  for (uint32_t round = 0; active; round++) {
-    const int strat = strategy ? strategy : g_tuner.choose(tkey);
-    const bool tuning = !strategy && !g_tuner.decided(tkey);
-    // block shape: the tuner's (tried in turn once the strategy is decided), 256 with a fixed strategy
-    const uint32_t threads = strategy ? 256u : g_tuner.choose_threads(tkey);
-    const bool shape_tuning = !strategy && !tuning && !g_tuner.threads_decided(tkey);
+  // One round: the descriptors and round words uploaded, then the graph.
+  auto launch_round = [&](uint32_t round, int strat, uint32_t threads, bool timed) {
     std::memcpy(hdesc, desc.data(), n * sizeof(BatchDesc));
     hround[0] = round;
     hround[1] = strat == 2 ? shadow_next_tag(W, bs, 4 * keys) : 0;
     hround[2] = strat == 2 ? 1u : 0u;
     CK(cudaMemcpyAsync(ddesc, hdesc, n * sizeof(BatchDesc), cudaMemcpyHostToDevice, bs));
     CK(cudaMemcpyAsync(dround, hround, 16, cudaMemcpyHostToDevice, bs));
-    if (tuning || shape_tuning) CK(cudaEventRecord(g_tev[0], bs));
+    if (timed) CK(cudaEventRecord(g_tev[0], bs));
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[0], bs));
     CK(cudaGraphLaunch(graph_for(threads), bs));
-    for (int q = 0; q < 3; q++) count_launch();  // kernels replayed by the graph
+    for (int q = 0; q < 2; q++) count_launch();  // kernels replayed by the graph
+  };
+
+  std::vector<RecList> races(n);
+  std::vector<std::vector<OutRec>> errors(n);
+  RecordSink sink(races, W.hrecs, W.hreck);
+  std::vector<uint32_t> n_intervals(n, 0);
+  uint32_t active = n, fill_seen = 0;
+  std::vector<uint64_t> acc(2ull * n), prev(2ull * n, 0);
+  std::vector<OutRec> rr;
+  int strat = 0;
+  uint32_t threads = 256;
+  bool tuning = false, shape_tuning = false, launched = false;
+  for (uint32_t round = 0; active; round++) {
+    if (!launched) {
+      strat = strategy ? strategy : g_tuner.choose(tkey);
+      tuning = !strategy && !g_tuner.decided(tkey);
+      // block shape: the tuner's (tried in turn once the strategy is decided), 256 with a fixed strategy
+      threads = strategy ? 256u : g_tuner.choose_threads(tkey);
+      shape_tuning = !strategy && !tuning && !g_tuner.threads_decided(tkey);
+      launch_round(round, strat, threads, tuning || shape_tuning);
+    }
+    launched = false;
+    // the round's compaction of the records to classify (queued after the
+    // previous round's classification, which read the same buffer, ended)
+    launch_batch_compact(a, picked, cnt, bs);
     if (g_prof.on) CK(cudaEventRecord(g_prof.ev[1], bs));
     CK(cudaMemcpyAsync(hstats, dstats, stat_words * 4, cudaMemcpyDeviceToHost, bs));
     CK(cudaMemcpyAsync(acc.data(), dacc, 16ull * n, cudaMemcpyDeviceToHost, bs));
@@ -1841,38 +2003,8 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
       g_prof.ms[0] += ms;
       CK(cudaEventRecord(g_prof.ev[2], bs));
     }
-    // ---- exact classification of the picked records over the shared cell space
     const uint64_t m = *reinterpret_cast<const uint64_t *>(hstats + 4);
-    rr.clear();
-    rk.clear();
-    if (m) {
-      uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(m), scan_tmp_words(m)));
-      LogRec *other = W.compact.get<LogRec>(m);
-      LogRec *sorted = sort_log(picked, other, m, bitwidth(maxN), bitwidth(keys) + bitwidth(maxN), tmp, bs);
-      Layout none;
-      BatchMap bm{n, dkbase, dkgt, dklt, &rk};
-      classify_run(W, sorted, m, round, none, snap, hstats + stat_words, rr, bs, &bm);
-    }
-    if (g_prof.on) {
-      CK(cudaEventRecord(g_prof.ev[3], bs));
-      CK(cudaEventSynchronize(g_prof.ev[3]));
-      float ms = 0;
-      CK(cudaEventElapsedTime(&ms, g_prof.ev[2], g_prof.ev[3]));
-      g_prof.launches[1]++;
-      g_prof.ms[1] += ms;
-    }
-    if (tuning || shape_tuning) {
-      CK(cudaEventRecord(g_tev[1], bs));
-      CK(cudaEventSynchronize(g_tev[1]));
-      float ms = 0;
-      CK(cudaEventElapsedTime(&ms, g_tev[0], g_tev[1]));
-      uint64_t done = 0;
-      for (size_t q = 0; q < acc.size(); q++) done += acc[q] - prev[q];
-      if (tuning) g_tuner.record(tkey, strat, ms, done);
-      else g_tuner.record_threads(tkey, threads, ms, done);
-    }
-    prev = acc;
-    for (size_t i = 0; i < rr.size(); i++) races[rk[i]].push_back(rr[i]);
+    // ---- error records of the round (the next round's launch reuses the buffer)
     const uint32_t nerr = std::min(hstats[1], err_cap);
     if (nerr) {
       std::vector<OutRec> e(nerr);
@@ -1900,8 +2032,59 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
         active--;
       }
     }
+    // ---- the next round beside this one's classification: a shadow round
+    // committed every written cell in its graph (highest writer), so the
+    // next round needs nothing from the classification; not while a round
+    // is timed for the autotuner or profiled
+    cudaStream_t cs = bs;
+    if (strat == 2 && m && active && !tuning && !shape_tuning && !g_prof.on) {
+      const int ns = strategy ? strategy : g_tuner.choose(tkey);
+      const uint32_t nth = strategy ? 256u : g_tuner.choose_threads(tkey);
+      if (strategy || (g_tuner.decided(tkey) && g_tuner.threads_decided(tkey))) {
+        launch_round(round + 1, ns, nth, false);
+        launched = true;
+        cs = classify_stream(W);  // the compaction it reads is complete: the host waited for it
+      }
+    }
+    // ---- exact classification of the picked records over the shared cell space
+    rr.clear();
+    if (m) {
+      uint32_t *tmp = W.scan.get<uint32_t>(std::max(sort_tmp_words(m), scan_tmp_words(m)));
+      LogRec *other = W.compact.get<LogRec>(m);
+      LogRec *sorted = sort_log(picked, other, m, bitwidth(maxN), bitwidth(keys) + bitwidth(maxN), tmp, cs);
+      Layout none;
+      BatchMap bm{n, dkbase, dkgt, dklt, &sink};
+      // shadow rounds: the commits were all made in the graph
+      classify_run(W, sorted, m, round, none, strat == 2 ? nullptr : snap, hstats + stat_words, rr, cs, &bm);
+    }
+    if (g_prof.on) {
+      CK(cudaEventRecord(g_prof.ev[3], bs));
+      CK(cudaEventSynchronize(g_prof.ev[3]));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, g_prof.ev[2], g_prof.ev[3]));
+      g_prof.launches[1]++;
+      g_prof.ms[1] += ms;
+    }
+    if (tuning || shape_tuning) {
+      CK(cudaEventRecord(g_tev[1], bs));
+      CK(cudaEventSynchronize(g_tev[1]));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, g_tev[0], g_tev[1]));
+      uint64_t done = 0;
+      for (size_t q = 0; q < acc.size(); q++) done += acc[q] - prev[q];
+      if (tuning) g_tuner.record(tkey, strat, ms, done);
+      else g_tuner.record_threads(tkey, threads, ms, done);
+    }
+    prev = acc;
+    if (launched) {  // the round already running
+      strat = strategy ? strategy : g_tuner.choose(tkey);
+      threads = strategy ? 256u : g_tuner.choose_threads(tkey);
+      tuning = shape_tuning = false;
+    }
   }
   g_tuner.record_fill(tkey, (uint32_t)(((uint64_t)fill_seen * log_pm + 999) / 1000));
+  sink.join();  // every round's records are in the lists
+  const Clock::time_point t_reports = Clock::now();
   s = bs;  // final memories are read on the batch stream
   for (uint32_t k = 0; k < n; k++) {
     const BatchItem &it = items[k];
@@ -1910,6 +2093,7 @@ bool run_batch(const std::vector<BatchItem> &items, cudaStream_t s, int strategy
                          acc[2 * k] + acc[2 * k + 1], it.L.GT,
                          (it.in->flags & RC_WANT_FINAL_MEMORY) ? snap + kbase[k] : nullptr, s);
   }
+  host_done(t_reports);
   return true;
 }
 

@@ -266,19 +266,36 @@ def _marshal(globals_, stream, want_final):
     return inp, (keep, clens, cptrs)
 
 
+class _ReportMemory:
+    """Owns an rc_report: the record and final-memory arrays of the Python
+    report are views of the library's own arrays (no copy), and the report
+    is freed when the last of them is gone."""
+
+    def __init__(self, lib, p):
+        self.lib, self.p = lib, p
+
+    def __del__(self):
+        if self.p is not None:
+            self.lib.rc_report_free(self.p)
+            self.p = None
+
+
+def _view(owner: _ReportMemory, addr: int, ctype, n: int, dtype) -> np.ndarray:
+    buf = (ctype * n).from_address(addr)
+    buf._owner = owner  # the view keeps the report alive
+    return np.frombuffer(buf, dtype=dtype)
+
+
 def _report(p) -> dict:
     r = p.contents
-    recs = np.zeros((r.n_records, 10), dtype=np.uint32)
+    owner = _ReportMemory(load(), p)
     if r.n_records:
-        ctypes.memmove(recs.ctypes.data, r.records, r.n_records * 40)
-    fin = None
-    if r.final_global:
-        fin = np.zeros(r.final_len, dtype=np.int32)
-        ctypes.memmove(fin.ctypes.data, r.final_global, r.final_len * 4)
-    out = dict(status=r.status, n_intervals=r.n_intervals, n_access=r.n_access,
-               n_global=r.n_global, n_local=r.n_local, n_logged=r.n_logged, records=recs, final=fin)
-    load().rc_report_free(p)
-    return out
+        recs = _view(owner, r.records, ctypes.c_uint32, r.n_records * 10, np.uint32).reshape(r.n_records, 10)
+    else:
+        recs = np.zeros((0, 10), dtype=np.uint32)
+    fin = _view(owner, r.final_global, ctypes.c_int32, r.final_len, np.int32) if r.final_global else None
+    return dict(status=r.status, n_intervals=r.n_intervals, n_access=r.n_access,
+                n_global=r.n_global, n_local=r.n_local, n_logged=r.n_logged, records=recs, final=fin)
 
 
 def check(bc: Bytecode, groups: int, group_size: int, globals_, stream=None,

@@ -182,3 +182,40 @@ def _features_in_child(q, seed):
     from paper_1308_3203_gb300 import proposal, racecheck
     _, items = proposal.kernel_candidates(seed)
     q.put(racecheck.features(items, n_threads=4))
+
+
+def test_report_arrays_view_the_library_report(monkeypatch):
+    """A Python report's record and final-memory arrays are views of the
+    library's arrays: the rc_report is freed once, when the last view is
+    gone, and not before."""
+    import gc
+    from paper_1308_3203_gb300 import racecheck
+    freed = []
+
+    class FakeLib:
+        def rc_report_free(self, p):
+            freed.append(p)
+
+    monkeypatch.setattr(racecheck, "load", lambda: FakeLib())
+    recs = (ctypes.c_uint32 * 30)(*range(30))
+    fin = (ctypes.c_int32 * 5)(-1, 2, 3, 4, 5)
+    r = racecheck._Report(1, 5, 1000, 900, 100, 3, ctypes.cast(recs, ctypes.c_void_p), 5,
+                          ctypes.cast(fin, ctypes.c_void_p), 800)
+    d = racecheck._report(ctypes.pointer(r))
+    assert d["records"].shape == (3, 10) and d["records"][2, 9] == 29
+    assert list(d["final"]) == [-1, 2, 3, 4, 5]
+    assert (d["status"], d["n_intervals"], d["n_access"], d["n_logged"]) == (1, 5, 1000, 800)
+    kept = d["records"]
+    del d
+    gc.collect()
+    assert not freed  # the records still view the report
+    assert kept[1, 0] == 10
+    del kept
+    gc.collect()
+    assert len(freed) == 1
+    empty = racecheck._Report(0, 1, 0, 0, 0, 0, None, 0, None, 0)
+    d = racecheck._report(ctypes.pointer(empty))
+    assert d["records"].shape == (0, 10) and d["final"] is None
+    del d
+    gc.collect()
+    assert len(freed) == 2

@@ -107,6 +107,26 @@ def test_batch_shapes(rc, oracle, seed):
     rc.set_strategy(0)
 
 
+def test_batch_pinned_inputs(rc, oracle):
+    """Inputs in page-locked host memory reach a batch through the copy kernel
+    (the SMs read them over the CPU-GPU link), pageable ones through
+    cudaMemcpyAsync: the same reports and final memories under each
+    strategy, in lock-step rounds (shadow rounds classify beside the next
+    round) and resident."""
+    import torch
+    insts = W.batch_kernels(7, 12)
+    insts = [i for i in insts if i.n_threads * 300 < 2_000_000][:6]
+    want = [oracle.check(i.src, i.groups, i.group_size, i.globals) for i in insts]
+    bcs = [rc.compile(i.src) for i in insts]
+    pinned = [[torch.from_numpy(g).pin_memory().numpy() for g in i.globals] for i in insts]
+    for s in (0, 1, 2, 3):
+        rc.set_strategy(s)
+        got = rc.check_batch([(b, i.groups, i.group_size, p) for b, i, p in zip(bcs, insts, pinned)])
+        for g, w, i in zip(got, want, insts):
+            same(g, w, f"{i.name} strategy {s}")
+    rc.set_strategy(0)
+
+
 @pytest.mark.parametrize("shape", [(1, 65, 8), (1, 66, 32), (3, 97, 16), (2, 200, 8), (1, 300, 64), (5, 129, 4)])
 def test_large_cells(rc, oracle, shape):
     """Cells touched by more than 64 work-items are classified by a whole
