@@ -21,6 +21,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -511,13 +512,17 @@ struct RecordSink {
     const OutRec *r = recs[next & 1].as<OutRec>();
     const uint32_t *k = kern[next & 1].as<uint32_t>();
     next++;
-    job = std::thread([this, r, k, n] {
-      try {
-        distribute_records(r, k, n, races);
-      } catch (...) {
-        err = std::current_exception();
-      }
-    });
+    try {
+      job = std::thread([this, r, k, n] {
+        try {
+          distribute_records(r, k, n, races);
+        } catch (...) {
+          err = std::current_exception();
+        }
+      });
+    } catch (const std::system_error &) {  // no thread to be had: the same work on this one
+      distribute_records(r, k, n, races);
+    }
   }
 };
 

@@ -276,24 +276,36 @@ class _ReportMemory:
 
     def __del__(self):
         if self.p is not None:
-            self.lib.rc_report_free(self.p)
+            try:
+                self.lib.rc_report_free(self.p)
+            except Exception:  # the library already unloaded at interpreter exit
+                pass
             self.p = None
 
 
-def _view(owner: _ReportMemory, addr: int, ctype, n: int, dtype) -> np.ndarray:
-    buf = (ctype * n).from_address(addr)
-    buf._owner = owner  # the view keeps the report alive
-    return np.frombuffer(buf, dtype=dtype)
+class _ArrayView:
+    """numpy's array interface over n values of dtype at addr; the array made
+    from it keeps this object, and so the report, alive."""
+    __slots__ = ("_owner", "__array_interface__")
+
+    def __init__(self, owner: _ReportMemory, addr: int, n: int, dtype):
+        self._owner = owner
+        self.__array_interface__ = {"data": (addr, False), "shape": (n,), "typestr": np.dtype(dtype).str,
+                                    "version": 3}
+
+
+def _view(owner: _ReportMemory, addr: int, n: int, dtype) -> np.ndarray:
+    return np.asarray(_ArrayView(owner, addr, n, dtype))
 
 
 def _report(p) -> dict:
     r = p.contents
     owner = _ReportMemory(load(), p)
     if r.n_records:
-        recs = _view(owner, r.records, ctypes.c_uint32, r.n_records * 10, np.uint32).reshape(r.n_records, 10)
+        recs = _view(owner, r.records, r.n_records * 10, np.uint32).reshape(r.n_records, 10)
     else:
         recs = np.zeros((0, 10), dtype=np.uint32)
-    fin = _view(owner, r.final_global, ctypes.c_int32, r.final_len, np.int32) if r.final_global else None
+    fin = _view(owner, r.final_global, r.final_len, np.int32) if r.final_global else None
     return dict(status=r.status, n_intervals=r.n_intervals, n_access=r.n_access,
                 n_global=r.n_global, n_local=r.n_local, n_logged=r.n_logged, records=recs, final=fin)
 
