@@ -392,9 +392,9 @@ __global__ void batch_compact_kernel(BatchArgs A, LogRec *out, unsigned long lon
   const uint32_t k = A.task_kernel[task];
   if (!A.desc[k].active) return;
   const BatchDesc &D = A.desc[k];
-  compact_slice(reinterpret_cast<const uint4 *>(A.log) + D.slice_off + (uint64_t)(task - D.task_off) * D.slice,
-                A.warp_count[task], A.round[2] ? A.owner : nullptr, A.round[1], reinterpret_cast<uint4 *>(out),
-                total, threadIdx.x & 31u);
+  compact_slice<8>(reinterpret_cast<const uint4 *>(A.log) + D.slice_off + (uint64_t)(task - D.task_off) * D.slice,
+                   A.warp_count[task], A.round[2] ? A.owner : nullptr, A.round[1], reinterpret_cast<uint4 *>(out),
+                   total, threadIdx.x & 31u);
 }
 
 // One thread per work-item of every active instance (task-major).

@@ -144,30 +144,32 @@ __device__ __forceinline__ bool shadow_needs_exact(const uint32_t *owner, uint32
 
 // One warp appends the records of its log slice src[0, n) that need the
 // exact classification (all of them when owner is null) to out, at
-// positions taken from *total.  Each lane holds four records in flight, so
+// positions taken from *total.  Each lane holds kPer records in flight, so
 // the owner-table lookups overlap, and the warp takes its positions with one
-// atomic per 128 records; a work-item's records keep their slice order.
-// Positions at or past cap are not written and raise FLAG_ACC_FULL in
-// *flags.  Called by all 32 lanes of a warp.
+// atomic per 32 x kPer records; a work-item's records keep their slice
+// order.  Positions at or past cap are not written and raise FLAG_ACC_FULL
+// in *flags.  Called by all 32 lanes of a warp.  (Kernels that run it in a
+// tight register budget, the resident ones, keep four per lane.)
+template <int kPer = 4>
 __device__ __forceinline__ void compact_slice(const uint4 *src, uint32_t n, const uint32_t *owner, uint32_t tag,
                                               uint4 *out, unsigned long long *total, uint32_t lane,
                                               unsigned long long cap = ~0ull, uint32_t *flags = nullptr) {
   const uint32_t lt = (1u << lane) - 1u;
-  for (uint32_t base = 0; base < n; base += 128) {
-    uint4 r[4];
-    bool need[4];
+  for (uint32_t base = 0; base < n; base += 32 * kPer) {
+    uint4 r[kPer];
+    bool need[kPer];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < kPer; q++) {
       const uint32_t i = base + q * 32 + lane;
       // through L2: a resident batch compacts slices another SM wrote in the same launch
       r[q] = i < n ? __ldcg(src + i) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
-    for (int q = 0; q < 4; q++)
+    for (int q = 0; q < kPer; q++)
       need[q] = base + q * 32 + lane < n && (!owner || shadow_needs_exact(owner, r[q].x, tag));
-    uint32_t bal[4], tot = 0;
+    uint32_t bal[kPer], tot = 0;
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < kPer; q++) {
       bal[q] = __ballot_sync(0xFFFFFFFFu, need[q]);
       tot += __popc(bal[q]);
     }
@@ -176,7 +178,7 @@ __device__ __forceinline__ void compact_slice(const uint4 *src, uint32_t n, cons
     if (lane == 0) pos = atomicAdd(total, (unsigned long long)tot);
     pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < kPer; q++) {
       if (need[q]) {
         const unsigned long long p = pos + __popc(bal[q] & lt);
         if (p < cap) out[p] = r[q];

@@ -23,8 +23,8 @@ __global__ void shadow_compact_kernel(const LogRec *log, uint32_t n_slices, uint
                                       unsigned long long *total) {
   const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= n_slices) return;
-  compact_slice(reinterpret_cast<const uint4 *>(log) + (uint64_t)w * slice, count[w], owner, tag,
-                reinterpret_cast<uint4 *>(out), total, threadIdx.x & 31u);
+  compact_slice<8>(reinterpret_cast<const uint4 *>(log) + (uint64_t)w * slice, count[w], owner, tag,
+                   reinterpret_cast<uint4 *>(out), total, threadIdx.x & 31u);
 }
 
 __global__ void shadow_commit_kernel(const uint2 *ow, const uint32_t *ow_count, uint64_t N, uint32_t ow_stride,
