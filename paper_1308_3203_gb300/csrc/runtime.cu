@@ -987,10 +987,9 @@ rc_report *run_resident(Workspace &W, const Instance &I, const Layout &L, const 
 // caller then checks it another way from the initial state.  The snapshot
 // must hold the inputs and the bytecode (without private flags: the CTA
 // classifies from the full log) must be uploaded.
-// The snapshot of an instance's start: the global inputs (pinned host
-// memory read by a copy kernel over the CPU-GPU link, other memory by
-// cudaMemcpyAsync) and zeroed local memory.
-// One global input array of len int32 values into dst.
+// One global input array of len int32 values into dst: pinned host memory
+// read by a copy kernel over the CPU-GPU link, other memory by
+// cudaMemcpyAsync.
 void upload_global(const int32_t *src, int32_t *dst, uint64_t len, bool on_device, cudaStream_t s) {
   const int32_t *mapped = on_device ? nullptr : device_view(src);
   if (mapped) {  // pinned host memory: the SMs read it over the CPU-GPU link
@@ -1001,6 +1000,8 @@ void upload_global(const int32_t *src, int32_t *dst, uint64_t len, bool on_devic
   }
 }
 
+// The snapshot of an instance's start: the global inputs and zeroed local
+// memory.
 void load_inputs(const Instance &I, const Layout &L, int32_t *snap, cudaStream_t s) {
   const Program &P = *I.p;
   uint32_t gi = 0;
