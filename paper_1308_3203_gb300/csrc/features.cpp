@@ -229,7 +229,10 @@ int64_t eval(const Form &f, int64_t tid, int64_t wg, const Analysis &an, const C
 
 int64_t eval_aff(const Form &f, int64_t tid, int64_t wg) {
   int64_t v = f.c0 + f.ct * tid + f.cw * wg;
-  if (f.M > 0) v = ((v % f.M) + f.M) % f.M;
+  if (f.M > 0) {  // Euclidean remainder
+    v %= f.M;
+    if (v < 0) v += f.M;
+  }
   return v + f.off;
 }
 
@@ -331,6 +334,14 @@ void features_one(const Cand &c, float *out) {
     smp.erase(std::unique(smp.begin(), smp.end()), smp.end());
   }
   const double scale = (double)N / smp.size();
+  // each sampled work-item's (tid, wg), once for every access
+  thread_local std::vector<int64_t> smp_tid, smp_wg;
+  smp_tid.resize(smp.size());
+  smp_wg.resize(smp.size());
+  for (size_t i = 0; i < smp.size(); i++) {
+    smp_tid[i] = smp[i] % S;
+    smp_wg[i] = smp[i] / S;
+  }
 
   thread_local std::vector<Ev> evs;
   evs.clear();
@@ -355,8 +366,9 @@ void features_one(const Cand &c, float *out) {
     // enabled work-items in the sample; enabled tids of the first enabled group, groups of the first tid
     uint64_t en = 0, oob = 0;
     int64_t first_wg = -1, first_tid = -1;
-    for (uint32_t g : smp) {
-      const int64_t tid = g % S, wg = g / S;
+    for (size_t si = 0; si < smp.size(); si++) {
+      const uint32_t g = smp[si];
+      const int64_t tid = smp_tid[si], wg = smp_wg[si];
       bool certain = true;
       if (!enabled(a, tid, wg, an, c, certain)) continue;
       en++;
