@@ -1590,9 +1590,9 @@ BatchItem plan_item(const rc_bytecode *bc, uint32_t G, uint32_t S, const rc_inpu
 
 // Check instances [0, n) of `items` together.  Lock-step rounds: every round
 // runs one barrier interval of every instance still active, in one
-// persistent interpreter launch (a captured graph with the commit and the
-// compaction), then one classification over the shared cell space, and the
-// host's barrier agreement.  Resident (strategy 3): every round in one
+// persistent interpreter launch (a captured graph with the commit), then the
+// compaction, the host's barrier agreement and one classification over the
+// shared cell space (on shadow rounds beside the next round's graph).  Resident (strategy 3): every round in one
 // cooperative launch (batch.cu, batch_resident_kernel), then the
 // classification of each round's compacted records.  Returns false when a
 // resident run could not finish (not every CTA resident, the record buffer
