@@ -321,15 +321,21 @@ void features_one(const Cand &c, float *out) {
 
   const Analysis an = analyse(p, S, G);
   // work-item sample: all of them when few, else both ends and an even spread
-  // (256 in all: the ranking must cost less than the checks it saves)
+  // -- 256 in all, fewer for long programs so that a candidate evaluates at
+  // most about kEvalBudget accesses (at least 32 work-items): the ranking
+  // must cost less than the checks it saves
+  constexpr uint64_t kEvalBudget = 4096;
+  const uint64_t n_acc = std::max<uint64_t>(an.acc.size(), 1);
+  const uint32_t m = (uint32_t)std::max<uint64_t>(32, std::min<uint64_t>(256, (kEvalBudget / n_acc) & ~(uint64_t)3));
   std::vector<uint32_t> smp;
-  if (N <= 256) {
+  if (N <= m) {
     smp.resize(N);
     std::iota(smp.begin(), smp.end(), 0u);
   } else {
-    for (uint32_t i = 0; i < 64; i++) smp.push_back(i);
-    for (uint32_t i = 0; i < 64; i++) smp.push_back((uint32_t)(N - 64 + i));
-    for (uint32_t i = 0; i < 128; i++) smp.push_back((uint32_t)((N * (2 * i + 1)) / 256));
+    const uint32_t q = m / 4;
+    for (uint32_t i = 0; i < q; i++) smp.push_back(i);
+    for (uint32_t i = 0; i < q; i++) smp.push_back((uint32_t)(N - q + i));
+    for (uint32_t i = 0; i < m / 2; i++) smp.push_back((uint32_t)((N * (2 * i + 1)) / m));
     std::sort(smp.begin(), smp.end());
     smp.erase(std::unique(smp.begin(), smp.end()), smp.end());
   }
